@@ -1,0 +1,220 @@
+"""ctypes binding of the plain FP64 C oracle (mbd_oracle.c) -- test infrastructure only.
+
+`build()` compiles mbd_oracle.c with gcc into oracle/_build/libmbd_oracle.so for the
+host it runs on (x86_64 here, aarch64 on the GPU host); `lib()` loads it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "mbd_oracle.c")
+OUT_DIR = os.path.join(HERE, "_build")
+SO = os.path.join(OUT_DIR, "libmbd_oracle.so")
+
+OK, ERR_INPUT, ERR_NEG_EIGENVALUE, ERR_SCS_NEG_ALPHA, ERR_SINGULAR, ERR_NOT_CONVERGED = range(6)
+
+_lock = threading.Lock()
+_lib = None
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle if the shared object is missing or older than its source."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(SO) or os.path.getmtime(SO) < os.path.getmtime(SRC):
+        tmp = SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, SO)
+    return SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            i, d = C.c_int, C.c_double
+            P = C.POINTER(C.c_double)
+            L.orc_gauss_legendre.argtypes = [i, _dp, _dp]
+            L.orc_freq_grid.argtypes = [i, _dp, _dp]
+            L.orc_T_bare.argtypes = [_dp, _dp]
+            L.orc_T_gg.argtypes = [_dp, d, _dp]
+            L.orc_T_erfc.argtypes = [_dp, d, _dp]
+            L.orc_T_gg_deriv.argtypes = [_dp, d, _dp, _dp]
+            L.orc_T_bare_deriv.argtypes = [_dp, _dp]
+            L.orc_fermi.argtypes = [d, d, d, d]
+            L.orc_fermi.restype = d
+            L.orc_gauss_jordan_inverse.argtypes = [i, _dp, _dp]
+            L.orc_jacobi_eigh.argtypes = [i, _dp, _dp, _dp]
+            L.orc_ts_scaling.argtypes = [i, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_scs_matrix.argtypes = [i, _dp, _dp, _dp, d, d, _dp]
+            L.orc_scs.argtypes = [i, _dp, _dp, _dp, _dp, d, d, i, _dp, _dp, P]
+            L.orc_screened_params.argtypes = [i, i, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_mbd_q.argtypes = [i, _dp, _dp, _dp, _dp, d, d, _dp]
+            L.orc_energy_from_q.argtypes = [i, _dp, _dp, P, P]
+            L.orc_mbd_energy.argtypes = [i, _dp, _dp, _dp, _dp, d, d, P]
+            L.orc_mbd_rsscs_energy.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, P, P]
+            L.orc_mbd_rsscs_gradient.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, i, P, _dp, _dp]
+            _lib = L
+    return _lib
+
+
+def _a(x, shape=None):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return a.reshape(shape) if shape is not None else a
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"oracle {where} failed with code {code}")
+        self.code = code
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise OracleError(rc, where)
+
+
+# ---- elementary pieces -------------------------------------------------------------
+def gauss_legendre(n):
+    x, w = np.zeros(n), np.zeros(n)
+    _check(lib().orc_gauss_legendre(n, x, w), "gauss_legendre")
+    return x, w
+
+
+def freq_grid(n_freq=15):
+    u, w = np.zeros(n_freq + 1), np.zeros(n_freq + 1)
+    _check(lib().orc_freq_grid(n_freq, u, w), "freq_grid")
+    return u, w
+
+
+def T_bare(r):
+    T = np.zeros(9); lib().orc_T_bare(_a(r), T); return T.reshape(3, 3)
+
+
+def T_gg(r, s):
+    T = np.zeros(9); lib().orc_T_gg(_a(r), float(s), T); return T.reshape(3, 3)
+
+
+def T_erfc(r, gamma):
+    T = np.zeros(9); lib().orc_T_erfc(_a(r), float(gamma), T); return T.reshape(3, 3)
+
+
+def T_gg_deriv(r, s):
+    dr, ds = np.zeros(27), np.zeros(9)
+    lib().orc_T_gg_deriv(_a(r), float(s), dr, ds)
+    return dr.reshape(3, 3, 3), ds.reshape(3, 3)
+
+
+def T_bare_deriv(r):
+    dr = np.zeros(27); lib().orc_T_bare_deriv(_a(r), dr); return dr.reshape(3, 3, 3)
+
+
+def fermi(rho, rsum, sr, a):
+    return lib().orc_fermi(float(rho), float(rsum), float(sr), float(a))
+
+
+def inverse(A):
+    A = _a(A); n = A.shape[0]; out = np.zeros_like(A)
+    _check(lib().orc_gauss_jordan_inverse(n, A, out), "gauss_jordan_inverse")
+    return out
+
+
+def eigh(A):
+    A = _a(A); n = A.shape[0]; lam = np.zeros(n); V = np.zeros_like(A)
+    _check(lib().orc_jacobi_eigh(n, A, lam, V), "jacobi_eigh")
+    return lam, V
+
+
+def ts_scaling(a0ref, c6ref, rref, ratio):
+    N = len(a0ref); a0, om, rv = np.zeros(N), np.zeros(N), np.zeros(N)
+    lib().orc_ts_scaling(N, _a(a0ref), _a(c6ref), _a(rref), _a(ratio), a0, om, rv)
+    return a0, om, rv
+
+
+def scs_matrix(R, alpha, rvdw, beta=0.83, a=6.0):
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    M = np.zeros((3 * N, 3 * N))
+    lib().orc_scs_matrix(N, R, _a(alpha), _a(rvdw), beta, a, M)
+    return M
+
+
+def scs(R, alpha0, omega, rvdw, beta=0.83, a=6.0, n_freq=15):
+    """alpha_bar[k, i] for k = 0..n_freq (u_0 = 0)."""
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    u, _ = freq_grid(n_freq)
+    ab = np.zeros((n_freq + 1, N))
+    _check(lib().orc_scs(N, R, _a(alpha0), _a(omega), _a(rvdw), beta, a, n_freq, u, ab, None), "scs")
+    return ab
+
+
+def screened_params(alpha_bar, alpha0, rvdw, n_freq=15):
+    N = alpha_bar.shape[1]; _, wu = freq_grid(n_freq)
+    outs = [np.zeros(N) for _ in range(4)]
+    rc = lib().orc_screened_params(N, n_freq, _a(alpha_bar), wu, _a(alpha0), _a(rvdw), *outs)
+    return rc, tuple(outs)  # abar0, c6bar, ombar, rbar
+
+
+def mbd_q(R, alpha0, omega, rdamp, beta=0.83, a=6.0):
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    Q = np.zeros((3 * N, 3 * N))
+    lib().orc_mbd_q(N, R, _a(alpha0), _a(omega), _a(rdamp), beta, a, Q)
+    return Q
+
+
+def energy_from_q(Q, omega, want_z=False):
+    Q = _a(Q); N = Q.shape[0] // 3
+    E = C.c_double()
+    Z = np.zeros_like(Q) if want_z else None
+    _check(lib().orc_energy_from_q(N, Q, _a(omega), C.byref(E),
+                                   Z.ctypes.data_as(C.POINTER(C.c_double)) if want_z else None),
+           "energy_from_q")
+    return (E.value, Z) if want_z else E.value
+
+
+def mbd_energy(R, alpha0, omega, rdamp, beta=0.83, a=6.0):
+    """Unscreened MBD energy of given oscillators (damping radii rdamp)."""
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    E = C.c_double()
+    _check(lib().orc_mbd_energy(N, R, _a(alpha0), _a(omega), _a(rdamp), beta, a, C.byref(E)),
+           "mbd_energy")
+    return E.value
+
+
+def mbd_rsscs_energy(R, a0ref, c6ref, rref, ratio, beta=0.83, a=6.0, n_freq=15, detail=False):
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    E = C.c_double()
+    det = np.zeros((n_freq + 4) * N)
+    rc = lib().orc_mbd_rsscs_energy(N, R, _a(a0ref), _a(c6ref), _a(rref), _a(ratio), beta, a,
+                                    n_freq, C.byref(E), det.ctypes.data_as(C.POINTER(C.c_double)))
+    _check(rc, "mbd_rsscs_energy")
+    if not detail:
+        return E.value
+    return E.value, dict(alpha_bar=det[:(n_freq + 1) * N].reshape(n_freq + 1, N),
+                         c6=det[(n_freq + 1) * N:(n_freq + 2) * N],
+                         omega=det[(n_freq + 2) * N:(n_freq + 3) * N],
+                         rvdw=det[(n_freq + 3) * N:])
+
+
+def mbd_rsscs_gradient(R, a0ref, c6ref, rref, ratio, beta=0.83, a=6.0, n_freq=15, mode="adjoint"):
+    """Energy, dE/dR [N,3], dE/d(alpha0_ref, C6_ref, R_ref, ratio) [4,N].
+    mode: "forward" (per-input forward mode with the paper's fused SCS formula) or
+    "adjoint"."""
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    E = C.c_double()
+    gR, gp = np.zeros((N, 3)), np.zeros((4, N))
+    rc = lib().orc_mbd_rsscs_gradient(N, R, _a(a0ref), _a(c6ref), _a(rref), _a(ratio), beta, a,
+                                      n_freq, 0 if mode == "forward" else 1, C.byref(E), gR, gp)
+    _check(rc, "mbd_rsscs_gradient")
+    return E.value, gR, gp
+
+
+def system_args(sys):
+    """(R, alpha0_ref, c6_ref, rvdw_ref, ratio) of a synthetic.System."""
+    return sys.coords, sys.alpha0_ref, sys.c6_ref, sys.rvdw_ref, sys.ratio
