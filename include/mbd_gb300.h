@@ -1,0 +1,123 @@
+/*
+ * mbd_gb300.h -- C ABI of the GB300 (sm_103a) MBD@rsSCS library (libmbdgb.so).
+ *
+ * The library evaluates the many-body-dispersion energy of the MBD@rsSCS method and its
+ * analytic gradients (arXiv 2308.03140):
+ *   - TS volume scaling of free-atom parameters, Eq. (ts-scaling), Sec. 2.6;
+ *   - range-separated self-consistent screening on an imaginary-frequency grid,
+ *     Eqs. (scs), (contraction), (casimir-polder), (dyn-pol), (tgg), (mayer),
+ *     (scs-sr-dipole), (scale-rvdw-scs), Secs. 2.3 and 2.6, grid of Sec. 3.3;
+ *   - the coupled-oscillator matrix Q, Eq. (q-matrix), and the energy, Eq. (mbd-energy),
+ *     through Q^{1/2} and Q^{-1/2} from coupled Newton-Schulz iterations;
+ *   - gradients, Eq. (mbd-gradient) and the SCS derivative of Eq. (scs-gradient) in
+ *     adjoint form, with respect to coordinates and the free-atom parameters.
+ * The calls follow the paper's statement of the problem and its Fortran API (Sec. 3.1,
+ * Listing fortran-api): a plain input set, an opaque handle, an evaluate call and an
+ * exception query.
+ *
+ * Units: Hartree atomic units (bohr, Hartree).  Arrays are row-major and owned by the
+ * caller; the library never keeps a caller pointer after a call returns.  The context
+ * owns its device workspace, allocated by mbd_set_geometry.  A context is not
+ * thread-safe: one call at a time per context.
+ *
+ * Every call returns MBD_OK (0) or an MBD_ERR_* code; the code, the name of the
+ * failing stage and a message are kept in the context for mbd_get_exception (the
+ * get_exception protocol of Sec. 3.1).  Outputs are written only on success.
+ */
+#ifndef MBD_GB300_H
+#define MBD_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define MBD_OK 0
+#define MBD_ERR_INPUT 1           /* invalid argument, NaN input, overlapping atoms   */
+#define MBD_ERR_NEG_EIGENVALUE 2  /* Q not positive definite: polarization catastrophe, Sec. 2.1 */
+#define MBD_ERR_SCS_NEG_ALPHA 3   /* screened static polarizability or C6 <= 0       */
+#define MBD_ERR_SCS_NOT_PD 4      /* SCS matrix alpha^-1 + T^scs not positive definite */
+#define MBD_ERR_NOT_CONVERGED 5   /* Newton-Schulz iteration cap reached             */
+#define MBD_ERR_CUDA 6            /* CUDA runtime error                              */
+#define MBD_ERR_STATE 7           /* call order (geometry/parameters not set)        */
+#define MBD_ERR_UNSUPPORTED 8     /* option not available in this build              */
+
+/* Arithmetic of the dense stages (screening solves and the matrix function). */
+#define MBD_PREC_FP64 0           /* plain FP64 throughout                           */
+
+typedef struct mbd_ctx mbd_ctx;
+
+/* Options.  Defaults (mbd_default_options): n_freq 15 (Sec. 3.3), beta 0.83, a 6
+ * (Sec. 2.6), precision FP64, ns_tol 1e-8 (Frobenius norm of I - Z Y at which one
+ * final Newton-Schulz step is taken), ns_max_iter 100. */
+typedef struct {
+    int n_freq;          /* Gauss-Legendre points of the Casimir-Polder integral     */
+    double beta;         /* damping scale s_R of the Fermi function, Eq. (fermi-damping) */
+    double a;            /* damping steepness                                          */
+    int precision;       /* MBD_PREC_*                                                 */
+    double ns_tol;
+    int ns_max_iter;
+} mbd_options;
+
+/* Fills *opt with the defaults above.  Returns MBD_ERR_INPUT if opt is NULL. */
+int mbd_default_options(mbd_options *opt);
+
+/* Creates a context on CUDA device `cuda_device` with options *opt (NULL: defaults).
+ * *out receives the handle.  Allocates no device memory yet. */
+int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt);
+
+/* Frees the context and all device memory it owns.  NULL is accepted. */
+int mbd_destroy(mbd_ctx *ctx);
+
+/* Sets a finite system of n_atoms atoms (coords [n_atoms][3], bohr, host memory) and
+ * allocates the device workspace for that size.  lattice and k_grid must be NULL:
+ * periodic systems are reported as MBD_ERR_UNSUPPORTED by this build. */
+int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const double *lattice,
+                     const int *k_grid);
+
+/* Free-atom parameters, host arrays of n_atoms each: alpha0_ref (bohr^3), c6_ref
+ * (Ha bohr^6), rvdw_ref (bohr) and the volume ratio V/V_ref of Eq. (ts-scaling), as in
+ * update_vdw_params_from_ratios of the Fortran API. */
+int mbd_set_free_atom_params(mbd_ctx *ctx, const double *alpha0_ref, const double *c6_ref,
+                             const double *rvdw_ref, const double *volume_ratio);
+
+/* Evaluates the energy (Ha) with host-memory inputs set above and host-memory outputs.
+ * grad_coords [n_atoms][3] (Ha/bohr), grad_params [4][n_atoms] (dE/d alpha0_ref,
+ * dE/d c6_ref, dE/d rvdw_ref, dE/d ratio) and alpha_scs [n_atoms] (screened static
+ * polarizability) may each be NULL; gradients are computed only if one of grad_coords
+ * or grad_params is given.  grad_lattice must be NULL (finite systems). */
+int mbd_evaluate(mbd_ctx *ctx, double *energy, double *grad_coords, double *grad_lattice,
+                 double *grad_params, double *alpha_scs);
+
+/* Device-memory variant for callers that keep tensors on the GPU (the PyTorch binding).
+ * All pointers are device pointers on the context's device: coords [n_atoms][3],
+ * the four parameter arrays [n_atoms] each, energy [1], grad_coords [n_atoms][3] or
+ * NULL, grad_params [4][n_atoms] or NULL, alpha_scs [n_atoms] or NULL.  `stream` is a
+ * cudaStream_t (NULL: the legacy default stream); the call enqueues its work there and
+ * returns after that stream has finished it.  n_atoms must equal the size given to
+ * mbd_set_geometry. */
+int mbd_evaluate_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coords,
+                     const double *alpha0_ref, const double *c6_ref, const double *rvdw_ref,
+                     const double *volume_ratio, double *energy, double *grad_coords,
+                     double *grad_params, double *alpha_scs);
+
+/* Screening detail of the last successful evaluation, host arrays: alpha_iu
+ * [n_freq+1][n_atoms] (row 0 is u = 0), c6 [n_atoms], omega [n_atoms] (screened
+ * frequencies), rvdw [n_atoms] (screened damping radii).  Any may be NULL. */
+int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega, double *rvdw);
+
+/* Statistics of the last evaluation: Newton-Schulz iterations, the scale s of
+ * Y0 = Q/s, and the final Frobenius norm of I - Z Y.  Any may be NULL. */
+int mbd_get_stats(mbd_ctx *ctx, int *ns_iterations, double *ns_scale, double *ns_residual);
+
+/* Last error of this context: code, the stage that failed (origin) and a message,
+ * each string truncated to len bytes including the terminator.  ctx may not be NULL. */
+int mbd_get_exception(const mbd_ctx *ctx, int *code, char *origin, char *msg, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBD_GB300_H */

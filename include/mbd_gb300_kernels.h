@@ -1,0 +1,47 @@
+/*
+ * mbd_gb300_kernels.h -- kernel-level C ABI of libmbdgb: the dense FP64 building blocks
+ * behind the screening solves of Eq. (scs) (one Cholesky factorisation per frequency
+ * point, Sec. 2.3) and the coupled Newton-Schulz iteration for Q^{1/2}, Q^{-1/2}
+ * (Eqs. diagonalization, mbd-energy, mbd-gradient).  They stand where the paper's
+ * implementation calls LAPACK/ScaLAPACK (Sec. 3.1).
+ *
+ * All matrix pointers are DEVICE pointers (FP64, row-major) on the current CUDA device;
+ * `stream` is a cudaStream_t (NULL: legacy default stream).  Calls are asynchronous on
+ * that stream; errors of the launch itself are returned (MBD_ERR_CUDA), numerical
+ * failures are written to the device status word.  Dimensions must be positive
+ * multiples of 64 (MBD_ERR_INPUT otherwise).  Buffers belong to the caller.
+ */
+#ifndef MBD_GB300_KERNELS_H
+#define MBD_GB300_KERNELS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C = alpha * A * op(B) + beta * D on the FP64 tensor path (mma.sync m8n8k4 f64).
+ * A is M x K (lda).  trans_b = 1: op(B) = B^T with B N x K; trans_b = 0: op(B) = B
+ * with B K x N (ldb).  C and D are M x N (ldc, ldd).  D may be NULL when beta == 0 and
+ * may alias C.  mode 0 computes every 64x64 tile; mode 1 only tiles on or below the
+ * diagonal (M == N); mode 2 only tiles on or above it and mirrors them into the lower
+ * half (M == N, for products that are symmetric).  Leading dimensions must be even
+ * (16-byte aligned rows).  The matrices must not overlap C except D == C. */
+int mbdk_gemm_f64(void *stream, int trans_b, int mode, int M, int N, int K, double alpha,
+                  const double *A, long long lda, const double *B, long long ldb, double beta,
+                  const double *D, long long ldd, double *C, long long ldc);
+
+/* In-place lower Cholesky factorisation of `batch` matrices of order ld (consecutive,
+ * stride ld*ld).  Reads the lower triangle only.  dinv receives the inverses of the
+ * 64x64 diagonal blocks of each factor: batch * (ld/64) * 4096 doubles.  status (device
+ * int) gets bit 2 set on a non-positive pivot; it is not cleared by the call. */
+int mbdk_cholesky_f64(void *stream, double *A, long long ld, int batch, double *dinv, int *status);
+
+/* Solves A X = B in place for 3 right-hand sides per matrix, X [batch][ld][3], with the
+ * factors and diagonal-block inverses from mbdk_cholesky_f64. */
+int mbdk_chol_solve3_f64(void *stream, const double *L, long long ld, int batch, const double *dinv,
+                         double *X);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBD_GB300_KERNELS_H */

@@ -1,0 +1,227 @@
+"""Thin ctypes binding of libmbdgb.so (C ABI in include/mbd_gb300.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  The functions keep the C names (mbd_create, mbd_set_geometry, ...); the
+class `MBD` bundles them for convenience.  There is no CPU fallback: if the library
+is missing, `load()` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+MBD_OK = 0
+ERRORS = {1: "MBD_ERR_INPUT", 2: "MBD_ERR_NEG_EIGENVALUE", 3: "MBD_ERR_SCS_NEG_ALPHA",
+          4: "MBD_ERR_SCS_NOT_PD", 5: "MBD_ERR_NOT_CONVERGED", 6: "MBD_ERR_CUDA",
+          7: "MBD_ERR_STATE", 8: "MBD_ERR_UNSUPPORTED"}
+MBD_PREC_FP64 = 0
+
+# Every symbol declared in include/mbd_gb300.h.
+EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
+           "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_get_scs_detail",
+           "mbd_get_stats", "mbd_get_exception",
+           "mbdk_gemm_f64", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64")
+
+
+class mbd_options(C.Structure):
+    _fields_ = [("n_freq", C.c_int), ("beta", C.c_double), ("a", C.c_double),
+                ("precision", C.c_int), ("ns_tol", C.c_double), ("ns_max_iter", C.c_int)]
+
+
+class MBDError(RuntimeError):
+    def __init__(self, code, origin, msg):
+        super().__init__(f"{ERRORS.get(code, code)} in {origin}: {msg}")
+        self.code, self.origin, self.msg = code, origin, msg
+
+
+_lib = None
+_P = C.POINTER(C.c_double)
+
+
+def load(path: str | None = None):
+    """Loads the CUDA library (built by `build.build()`); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmbdgb.so not built ({path}); run paper_2308_03140_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    L.mbd_default_options.argtypes = [C.POINTER(mbd_options)]
+    L.mbd_create.argtypes = [C.POINTER(vp), i, C.POINTER(mbd_options)]
+    L.mbd_destroy.argtypes = [vp]
+    L.mbd_set_geometry.argtypes = [vp, i, _P, _P, C.POINTER(C.c_int)]
+    L.mbd_set_free_atom_params.argtypes = [vp, _P, _P, _P, _P]
+    L.mbd_evaluate.argtypes = [vp, _P, _P, _P, _P, _P]
+    L.mbd_evaluate_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.mbd_get_scs_detail.argtypes = [vp, _P, _P, _P, _P]
+    L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P]
+    L.mbd_get_exception.argtypes = [vp, C.POINTER(C.c_int), C.c_char_p, C.c_char_p, sz]
+    ll = C.c_longlong
+    L.mbdk_gemm_f64.argtypes = [vp, i, i, i, i, i, d, vp, ll, vp, ll, d, vp, ll, vp, ll]
+    L.mbdk_cholesky_f64.argtypes = [vp, vp, ll, i, vp, vp]
+    L.mbdk_chol_solve3_f64.argtypes = [vp, vp, ll, i, vp, vp]
+    for name in EXPORTS:
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_P)
+
+
+def _f64(x, shape=None):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _tptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class MBD:
+    """One library context on one CUDA device (mirrors mbd_calc_t of the paper's API)."""
+
+    def __init__(self, device: int = 0, n_freq: int = 15, beta: float = 0.83, a: float = 6.0,
+                 ns_tol: float = 1e-8, ns_max_iter: int = 100):
+        self.lib = load()
+        opt = mbd_options()
+        self.lib.mbd_default_options(C.byref(opt))
+        opt.n_freq, opt.beta, opt.a, opt.ns_tol, opt.ns_max_iter = n_freq, beta, a, ns_tol, ns_max_iter
+        h = C.c_void_p()
+        rc = self.lib.mbd_create(C.byref(h), device, C.byref(opt))
+        if rc:
+            raise MBDError(rc, "mbd_create", "cannot create context")
+        self.h, self.n_freq, self.device = h, n_freq, device
+        self.n_atoms = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mbd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def exception(self):
+        code = C.c_int()
+        o, m = C.create_string_buffer(256), C.create_string_buffer(256)
+        self.lib.mbd_get_exception(self.h, C.byref(code), o, m, 256)
+        return code.value, o.value.decode(), m.value.decode()
+
+    def _check(self, rc):
+        if rc:
+            code, origin, msg = self.exception()
+            raise MBDError(rc, origin, msg)
+
+    def set_geometry(self, coords, lattice=None, k_grid=None):
+        R = _f64(coords, (-1, 3))
+        lat = None if lattice is None else _f64(lattice, (3, 3))
+        kg = None if k_grid is None else (C.c_int * 3)(*[int(k) for k in k_grid])
+        self._check(self.lib.mbd_set_geometry(self.h, R.shape[0], _ptr(R), _ptr(lat), kg))
+        self.n_atoms = R.shape[0]
+
+    def set_free_atom_params(self, alpha0_ref, c6_ref, rvdw_ref, volume_ratio):
+        arrs = [_f64(x) for x in (alpha0_ref, c6_ref, rvdw_ref, volume_ratio)]
+        self._check(self.lib.mbd_set_free_atom_params(self.h, *[_ptr(x) for x in arrs]))
+
+    def evaluate(self, gradients: bool = True):
+        """Host-memory evaluation.  Returns (energy, grad_coords [N,3] | None,
+        grad_params [4,N] | None, alpha_scs [N])."""
+        N = self.n_atoms
+        E = C.c_double()
+        gR = np.zeros((N, 3)) if gradients else None
+        gp = np.zeros((4, N)) if gradients else None
+        al = np.zeros(N)
+        self._check(self.lib.mbd_evaluate(self.h, C.byref(E), _ptr(gR), None, _ptr(gp), _ptr(al)))
+        return E.value, gR, gp, al
+
+    def evaluate_dev(self, coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio, energy,
+                     grad_coords=None, grad_params=None, alpha_scs=None, stream=None):
+        """Device-memory evaluation on torch CUDA float64 tensors (outputs preallocated).
+        `stream` is a torch.cuda.Stream or None for the current stream."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(coords.device)
+        for t in (coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio, energy, grad_coords,
+                  grad_params, alpha_scs):
+            if t is not None and (not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous()):
+                raise ValueError("device evaluation needs contiguous float64 CUDA tensors")
+        rc = self.lib.mbd_evaluate_dev(self.h, C.c_void_p(stream.cuda_stream), int(coords.shape[0]),
+                                       _tptr(coords), _tptr(alpha0_ref), _tptr(c6_ref), _tptr(rvdw_ref),
+                                       _tptr(volume_ratio), _tptr(energy), _tptr(grad_coords),
+                                       _tptr(grad_params), _tptr(alpha_scs))
+        self._check(rc)
+
+    def scs_detail(self):
+        N, nf1 = self.n_atoms, self.n_freq + 1
+        a, c6, om, rv = np.zeros((nf1, N)), np.zeros(N), np.zeros(N), np.zeros(N)
+        self._check(self.lib.mbd_get_scs_detail(self.h, _ptr(a), _ptr(c6), _ptr(om), _ptr(rv)))
+        return dict(alpha_bar=a, c6=c6, omega=om, rvdw=rv)
+
+    def stats(self):
+        it, sc, res = C.c_int(), C.c_double(), C.c_double()
+        self._check(self.lib.mbd_get_stats(self.h, C.byref(it), C.byref(sc), C.byref(res)))
+        return dict(ns_iterations=it.value, ns_scale=sc.value, ns_residual=res.value)
+
+
+def _stream(t, stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream(t.device)
+    return C.c_void_p(s.cuda_stream)
+
+
+def mbdk_gemm_f64(A, B, C_out, alpha=1.0, beta=0.0, D=None, mode=0, trans_b=True, stream=None):
+    """C_out = alpha A op(B) + beta D on torch float64 CUDA tensors (dims multiples of 64);
+    op(B) = B^T if trans_b else B."""
+    L = load()
+    M, K = A.shape
+    N = B.shape[0] if trans_b else B.shape[1]
+    rc = L.mbdk_gemm_f64(_stream(A, stream), int(bool(trans_b)), mode, M, N, K, alpha, _tptr(A), A.stride(0),
+                         _tptr(B), B.stride(0), beta, _tptr(D), D.stride(0) if D is not None else 0,
+                         _tptr(C_out), C_out.stride(0))
+    if rc:
+        raise MBDError(rc, "mbdk_gemm_f64", "launch rejected")
+
+
+def mbdk_cholesky_f64(A, dinv, status, stream=None):
+    """In-place batched Cholesky of A [batch, ld, ld] (float64 CUDA)."""
+    L = load()
+    rc = L.mbdk_cholesky_f64(_stream(A, stream), _tptr(A), A.shape[-1], A.shape[0], _tptr(dinv), _tptr(status))
+    if rc:
+        raise MBDError(rc, "mbdk_cholesky_f64", "launch rejected")
+
+
+def mbdk_chol_solve3_f64(Lf, dinv, X, stream=None):
+    L = load()
+    rc = L.mbdk_chol_solve3_f64(_stream(Lf, stream), _tptr(Lf), Lf.shape[-1], Lf.shape[0], _tptr(dinv), _tptr(X))
+    if rc:
+        raise MBDError(rc, "mbdk_chol_solve3_f64", "launch rejected")
+
+
+def evaluate_system(sys, device: int = 0, gradients: bool = True, **opts):
+    """One-shot host evaluation of a synthetic.System."""
+    with MBD(device, **opts) as m:
+        m.set_geometry(sys.coords, sys.lattice, sys.k_grid)
+        m.set_free_atom_params(sys.alpha0_ref, sys.c6_ref, sys.rvdw_ref, sys.ratio)
+        E, gR, gp, al = m.evaluate(gradients)
+        return E, gR, gp, al, m.stats()

@@ -1,0 +1,106 @@
+// Internal declarations of the sm_103a kernels of libmbdgb.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace mbdgb {
+
+constexpr int kTile = 64;          // dense tile edge; leading dimensions are multiples of it
+constexpr int kMaxFreq = 64;       // upper bound on n_freq + 1
+
+// Bits of the device status word.
+enum : int {
+    ST_INPUT = 1,          // NaN input or coincident atoms
+    ST_SCS_NOT_PD = 2,     // non-positive pivot in the SCS Cholesky factorisation
+    ST_NEG_ALPHA = 4,      // screened alpha0 or C6 not positive
+};
+
+// ---- dense FP64 (k_dense.cu) ----------------------------------------------------
+// C[b] = alpha * A[b] op(B[b]) + beta * D[b] on 64x64 tiles, FP64 DMMA (mma.sync m8n8k4).
+// A is M x K; op(B) = B^T with B N x K (trans_b = 1) or B with B K x N (trans_b = 0);
+// C and D are M x N; all row-major with leading dimensions.  M, N, K are multiples of
+// 64.  mode: 0 every tile; 1 lower tiles (tile row >= tile col) only; 2 upper tiles
+// only, each also written transposed into the lower half (for products known to be
+// symmetric).  D may alias C (each element is read before it is written).
+struct GemmArgs {
+    const double *A, *B, *D;
+    double *C;
+    long long lda, ldb, ldd, ldc;
+    long long sA, sB, sD, sC;   // batch strides (elements)
+    int M, N, K, batch;
+    double alpha, beta;
+    int mode;
+    int trans_b;
+};
+void gemm_f64(const GemmArgs &g, cudaStream_t s);
+// Z = a I + b P (ld x ld).
+void axpby_identity(double *Z, const double *P, long long ld, double a, double b, cudaStream_t s);
+
+// Batched right-looking blocked Cholesky (lower) of `batch` ld x ld matrices (stride
+// mstride), in place.  Diagonal-block inverses L_kk^{-1} (64x64 each, nb per matrix)
+// are written to dinv[b][k].  Sets ST_SCS_NOT_PD on a non-positive pivot.
+void cholesky_f64(double *A, long long ld, long long mstride, int batch, double *dinv,
+                  int *status, cudaStream_t s);
+
+// Batched triangular solves with 3 right-hand sides, in place on X [b][ld][3]:
+// forward L y = x, then backward L^T z = y (L from cholesky_f64).
+void chol_solve3_f64(const double *L, long long ld, long long mstride, int batch,
+                     const double *dinv, double *X, long long xstride, cudaStream_t s);
+
+// Sum of squares of (I - P) over the leading n x n block, written to out[0].
+void frob_dev_identity(const double *P, long long ld, int n, double *out, cudaStream_t s);
+// Y = Y * scale over the full ld x ld matrix.
+void scale_matrix(double *Y, long long ld, double scale, cudaStream_t s);
+// Z = I (ld x ld).
+void set_identity(double *Z, long long ld, cudaStream_t s);
+// Maximum absolute row sum over rows 0..n-1 (Gershgorin bound), written to out[0].
+void max_abs_rowsum(const double *Q, long long ld, int n, double *out, cudaStream_t s);
+
+// ---- per-atom and pair kernels (k_atoms.cu, k_pairs.cu) -----------------------
+struct AtomBufs {
+    int N, nf1;                 // atoms, frequency points (u_0 = 0 included)
+    const double *R;            // [N][3]
+    const double *a0ref, *c6ref, *rref, *ratio;
+    double *a0, *om, *rv;       // TS-scaled
+    double *al_u, *sig_u;       // [nf1][N]
+    double *abar;               // [nf1][N] screened alpha(iu)
+    double *abar0, *c6bar, *ombar, *rbar;
+    const double *u, *wu;       // [nf1] grid (device)
+};
+
+void prepare_atoms(const AtomBufs &b, int *status, cudaStream_t s);
+void build_scs(const AtomBufs &b, double beta, double a, double *M, long long ld,
+               long long mstride, int *status, cudaStream_t s);
+void init_rhs_identity(double *X, long long ld, int n, int nf1, long long xstride, cudaStream_t s);
+void contract_screen(const AtomBufs &b, const double *X, long long ld, long long xstride,
+                     int *status, cudaStream_t s);
+void build_q(const AtomBufs &b, double beta, double a, double *Q, long long ld, int *status,
+             cudaStream_t s);
+void energy_trace(const double *Y, long long ld, int n, const double *ombar, int N,
+                  double sqrt_s, double *out, cudaStream_t s);
+
+// MBD gradient pass (Eq. mbd-gradient): reads Z (Q^{-1/2} = zscale * Z) once.
+// Per atom: g_ombar (incl. the diagonal block and -3/2), g_abar0, g_rbar, gR [N][3].
+struct MbdGradOut { double *g_ombar, *g_abar0, *g_rbar, *gR; };
+void mbd_grad_pass(const AtomBufs &b, double beta, double a, const double *Z, long long ld,
+                   double zscale, const MbdGradOut &o, cudaStream_t s);
+
+// Chain through Eqs. (casimir-polder), (scale-rvdw-scs): h[k][i] = dE/d abar_i(u_k),
+// and the direct parts of dE/d alpha0, dE/d R_vdW (g_a0, g_rv, overwritten).  Also
+// writes the adjoint right-hand sides H[k][p][c] = h[k][p/3] delta_{p%3,c}.
+void chain_screen(const AtomBufs &b, const MbdGradOut &o, double *h, double *g_a0,
+                  double *g_rv, double *H, long long ld, long long xstride, cudaStream_t s);
+
+// SCS adjoint pair pass: with X = M^{-1} E and V = M^{-1} H per frequency, adds
+// -1/3 sum dM_pq (V X^T)_pq to dE/d alpha0, dE/d omega, dE/d R_vdW (g_a0, g_om, g_rv)
+// and dE/dR (gR, accumulated).
+void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, const double *V,
+                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR,
+                   cudaStream_t s);
+
+// TS-scaling chain to [4][N] parameter gradients.
+void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv,
+              double *gp, cudaStream_t s);
+
+}  // namespace mbdgb

@@ -1,0 +1,487 @@
+// Per-atom and pair kernels of MBD@rsSCS for sm_103a (FP64).
+//
+//  prepare_atoms   TS scaling, Eq. (ts-scaling); alpha(iu), Eq. (dyn-pol); Mayer width,
+//                  Eq. (mayer)
+//  build_scs       A = alpha^{-1} + T^scs per frequency, Eqs. (scs), (scs-sr-dipole), (tgg)
+//  contract_screen Eq. (contraction) and Eqs. (casimir-polder), (scale-rvdw-scs)
+//  build_q         Eq. (q-matrix) with T^lr = g(Rbar) T, Eq. (mbd-lr-dipole)
+//  energy_trace    Eq. (mbd-energy) from the trace of Q^{1/2}
+//  mbd_grad_pass   Eq. (mbd-gradient): 1/4 Tr(Q^{-1/2} dQ) - 3/2 sum d omega
+//  chain_screen    chain rule back through Eqs. (casimir-polder), (scale-rvdw-scs)
+//  scs_grad_pass   the derivative of Eq. (scs), d alpha_bar = -alpha_bar dA alpha_bar,
+//                  contracted as in Eq. (scs-gradient) but from the adjoint side
+//  ts_chain        chain rule back through Eq. (ts-scaling)
+//
+// The dipole tensors are written T_ab = P delta_ab + W r_a r_b with radial P, W.
+// Pair loops keep one CTA per "row" atom and stride over partner atoms, so every
+// per-atom sum is a fixed-order block reduction (deterministic, no atomics).
+#include "internal.h"
+
+namespace mbdgb {
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kTwoOverSqrtPi = 1.128379167095512573896158903121545172;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of NV values per thread (blockDim.x == 128); result valid in thread 0.
+template <int NV>
+__device__ void block_sum128(double (&v)[NV], double *scratch /* [4][NV] */) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) scratch[w * NV + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = scratch[k] + scratch[NV + k] + scratch[2 * NV + k] + scratch[3 * NV + k];
+    __syncthreads();
+}
+
+// Fermi function of Eq. (fermi-damping) and its derivatives with respect to the pair
+// distance rho and the radius sum S.
+struct Fermi { double f, df_drho, df_dS; };
+__device__ __forceinline__ Fermi fermi(double rho, double S, double beta, double a) {
+    const double x = rho / (beta * S);
+    const double f = 1.0 / (1.0 + exp(-a * (x - 1.0)));
+    const double dfx = a * f * (1.0 - f);
+    return {f, dfx / (beta * S), -dfx * x / S};
+}
+
+// Radial parts of T^GG(r; s) (Eq. tgg): P = F1/r^3, W = (2 z^2 Th - 3 F1)/r^5 with
+// z = r/s, Th = 2 z e^{-z^2}/sqrt(pi), F1 = erf z - Th; and d/dr, d/ds of both.
+struct Radial { double P, W, dP, dW, dPs, dWs; };
+__device__ __forceinline__ Radial tgg_radial(double rho, double s) {
+    const double z = rho / s, z2 = z * z;
+    const double th = kTwoOverSqrtPi * z * exp(-z2);
+    const double F1 = erf(z) - th;
+    const double G = 2.0 * z2 * th - 3.0 * F1;
+    const double ir = 1.0 / rho, ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+    Radial o;
+    o.P = F1 * ir3;
+    o.W = G * ir5;
+    o.dP = 2.0 * z * th / s * ir3 - 3.0 * F1 * ir3 * ir;
+    o.dW = -4.0 * z2 * z * th / s * ir5 - 5.0 * G * ir5 * ir;
+    o.dPs = -2.0 * z2 * th / s * ir3;
+    o.dWs = 4.0 * z2 * z2 * th / s * ir5;
+    return o;
+}
+
+// ---- per-atom preparation ------------------------------------------------------------
+__global__ void k_prepare(AtomBufs b, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const double a0r = b.a0ref[i], c6r = b.c6ref[i], rr = b.rref[i], v = b.ratio[i];
+    const double x = b.R[3 * i], y = b.R[3 * i + 1], z = b.R[3 * i + 2];
+    if (!(a0r > 0.0) || !(c6r > 0.0) || !(rr > 0.0) || !(v > 0.0) || !isfinite(x) ||
+        !isfinite(y) || !isfinite(z) || !isfinite(a0r * c6r * rr * v))
+        atomicOr(status, ST_INPUT);
+    const double a0 = a0r * v, om = 4.0 * c6r / (3.0 * a0r * a0r);
+    b.a0[i] = a0;
+    b.om[i] = om;
+    b.rv[i] = rr * cbrt(v);
+    const double cm = sqrt(2.0 / kPi) / 3.0;
+    for (int k = 0; k < b.nf1; ++k) {
+        const double uo = b.u[k] / om;
+        const double al = a0 / (1.0 + uo * uo);
+        b.al_u[k * b.N + i] = al;
+        b.sig_u[k * b.N + i] = cbrt(cm * al);
+    }
+}
+
+// ---- screening matrices ------------------------------------------------------------
+// Thread (i, j) with j <= i writes block (i, j) of every frequency's matrix (lower
+// triangle is all the Cholesky reads).  Rows >= n are padding: identity.
+__global__ void k_build_scs(AtomBufs b, double beta, double a, double *M, long long ld,
+                            long long mstride, int *status) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= b.N || j > i) return;
+    if (i == j) {
+        for (int k = 0; k < b.nf1; ++k) {
+            double *Mk = M + k * mstride;
+            const double d = 1.0 / b.al_u[k * b.N + i];
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y) Mk[(3LL * i + x) * ld + 3 * i + y] = (x == y) ? d : 0.0;
+        }
+        return;
+    }
+    const double rx = b.R[3 * j] - b.R[3 * i], ry = b.R[3 * j + 1] - b.R[3 * i + 1],
+                 rz = b.R[3 * j + 2] - b.R[3 * i + 2];
+    const double rho = sqrt(rx * rx + ry * ry + rz * rz);
+    if (!(rho > 1e-8)) atomicOr(status, ST_INPUT);
+    const Fermi fd = fermi(rho, b.rv[i] + b.rv[j], beta, a);
+    const double sr = 1.0 - fd.f;
+    const double r[3] = {rx, ry, rz};
+    for (int k = 0; k < b.nf1; ++k) {
+        const double si = b.sig_u[k * b.N + i], sj = b.sig_u[k * b.N + j];
+        const Radial t = tgg_radial(rho, sqrt(si * si + sj * sj));
+        double *Mk = M + k * mstride;
+        for (int x = 0; x < 3; ++x) {
+            double *row = Mk + (3LL * i + x) * ld + 3 * j;
+            for (int y = 0; y < 3; ++y) row[y] = sr * ((x == y ? t.P : 0.0) + t.W * r[x] * r[y]);
+        }
+    }
+}
+
+__global__ void k_pad_identity(double *M, long long ld, int n, long long mstride) {
+    // rows n..ld-1, all columns up to the row (lower part), per matrix (blockIdx.y)
+    double *Mk = M + blockIdx.y * mstride;
+    const long long rows = ld - n;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < rows * ld;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long r = n + e / ld, c = e % ld;
+        Mk[r * ld + c] = (r == c) ? 1.0 : 0.0;
+        if (c < n) Mk[c * ld + r] = 0.0;   // keep the upper half of the pad columns clean
+    }
+}
+
+__global__ void k_rhs_identity(double *X, long long ld, int n, long long xstride) {
+    double *Xk = X + blockIdx.y * xstride;
+    for (long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; p < ld;
+         p += static_cast<long long>(gridDim.x) * blockDim.x)
+        for (int c = 0; c < 3; ++c) Xk[3 * p + c] = (p < n && (p % 3) == c) ? 1.0 : 0.0;
+}
+
+// alpha_bar_i(u) = 1/3 sum_a X[3i+a][a]; then C6bar, omega_bar, Rbar per atom.
+__global__ void k_contract_screen(AtomBufs b, const double *X, long long xstride, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    double c6 = 0.0;
+    for (int k = 0; k < b.nf1; ++k) {
+        const double *Xk = X + k * xstride;
+        const double ab = (Xk[9LL * i] + Xk[9LL * i + 4] + Xk[9LL * i + 8]) / 3.0;
+        b.abar[k * b.N + i] = ab;
+        c6 += b.wu[k] * ab * ab;   // wu[0] = 0: the static point carries no weight
+    }
+    c6 *= 3.0 / kPi;
+    const double ab0 = b.abar[i];
+    if (!(ab0 > 0.0) || !(c6 > 0.0)) atomicOr(status, ST_NEG_ALPHA);
+    b.abar0[i] = ab0;
+    b.c6bar[i] = c6;
+    b.ombar[i] = 4.0 * c6 / (3.0 * ab0 * ab0);
+    b.rbar[i] = b.rv[i] * cbrt(ab0 / b.a0[i]);
+}
+
+// ---- coupled-oscillator matrix -------------------------------------------------------
+__global__ void k_build_q(AtomBufs b, double beta, double a, double *Q, long long ld, int *status) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= b.N || j >= b.N) return;
+    double blk[9];
+    if (i == j) {
+        const double w2 = b.ombar[i] * b.ombar[i];
+        for (int e = 0; e < 9; ++e) blk[e] = (e % 4 == 0) ? w2 : 0.0;
+    } else {
+        const double r[3] = {b.R[3 * j] - b.R[3 * i], b.R[3 * j + 1] - b.R[3 * i + 1],
+                             b.R[3 * j + 2] - b.R[3 * i + 2]};
+        const double rho2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2], rho = sqrt(rho2);
+        if (!(rho > 1e-8)) atomicOr(status, ST_INPUT);
+        const Fermi g = fermi(rho, b.rbar[i] + b.rbar[j], beta, a);
+        const double pre = b.ombar[i] * b.ombar[j] * sqrt(b.abar0[i] * b.abar0[j]) * g.f;
+        const double ir3 = 1.0 / (rho2 * rho), ir5 = ir3 / rho2;
+        for (int x = 0; x < 3; ++x)
+            for (int y = 0; y < 3; ++y)
+                blk[3 * x + y] = pre * ((x == y ? ir3 : 0.0) - 3.0 * r[x] * r[y] * ir5);
+    }
+    for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y) Q[(3LL * i + x) * ld + 3 * j + y] = blk[3 * x + y];
+}
+
+// Pad rows/columns n..ld-1 of Q: zero couplings and the diagonal value omega_bar_0^2.
+// Any diagonal entry of a symmetric matrix lies inside its spectrum, so the padded
+// eigenvalue never widens [lambda_min, lambda_max] and the blocks stay decoupled.
+__global__ void k_pad_q(double *Q, long long ld, int n, const double *ombar) {
+    const double d = ombar[0] * ombar[0];
+    const long long rows = ld - n;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < rows * ld;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long r = n + e / ld, c = e % ld;
+        Q[r * ld + c] = (r == c) ? d : 0.0;
+        Q[c * ld + r] = (r == c) ? d : 0.0;
+    }
+}
+
+// E = 1/2 sqrt(s) Tr Y - 3/2 sum omega_bar, Neumaier-compensated, one CTA.
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__global__ void k_energy(const double *Y, long long ld, int n, const double *ombar, int N,
+                         double sqrt_s, double *out) {
+    double s = 0.0, c = 0.0;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        double t, e;
+        two_sum(s, 0.5 * sqrt_s * Y[p * ld + p], t, e);
+        s = t; c += e;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double t, e;
+        two_sum(s, -1.5 * ombar[i], t, e);
+        s = t; c += e;
+    }
+    __shared__ double ss[256], cc[256];
+    ss[threadIdx.x] = s;
+    cc[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0, Cc = 0.0;
+        for (int k = 0; k < blockDim.x; ++k) {
+            double t, e;
+            two_sum(S, ss[k], t, e);
+            S = t;
+            Cc += e + cc[k];
+        }
+        out[0] = S + Cc;
+    }
+}
+
+// ---- gradients -------------------------------------------------------------------------
+// One CTA (128 threads) per row atom i; G = zscale * Z = Q^{-1/2}.
+// For ordered pairs (i, j):  g_c[i]    += 1/2 c_j g <G_ij, T>
+//                            g_rbar[i] += 1/2 c_i c_j dg/dS <G_ij, T>
+//                            gR[i]     -= 1/2 c_i c_j <G_ij, d(gT)/dr>,  r = R_j - R_i
+// (both blocks (i,j) and (j,i) of the symmetric sum are folded into the factor 1/2).
+__global__ void __launch_bounds__(128) k_mbd_grad(AtomBufs b, double beta, double a, const double *Z,
+                                                  long long ld, double zscale, MbdGradOut o) {
+    const int i = blockIdx.x;
+    const double ci = b.ombar[i] * sqrt(b.abar0[i]);
+    const double Ri[3] = {b.R[3 * i], b.R[3 * i + 1], b.R[3 * i + 2]};
+    double acc[5] = {0, 0, 0, 0, 0};   // g_c, g_rbar, gR x3
+    for (int j = threadIdx.x; j < b.N; j += 128) {
+        if (j == i) continue;
+        const double r[3] = {b.R[3 * j] - Ri[0], b.R[3 * j + 1] - Ri[1], b.R[3 * j + 2] - Ri[2]};
+        const double rho2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2], rho = sqrt(rho2);
+        const double cj = b.ombar[j] * sqrt(b.abar0[j]);
+        const Fermi g = fermi(rho, b.rbar[i] + b.rbar[j], beta, a);
+        double G[9];
+        for (int x = 0; x < 3; ++x)
+            for (int y = 0; y < 3; ++y) G[3 * x + y] = Z[(3LL * i + x) * ld + 3 * j + y];
+        const double tr = G[0] + G[4] + G[8];
+        double Gr[3], Gtr[3];
+        for (int x = 0; x < 3; ++x) {
+            Gr[x] = G[3 * x] * r[0] + G[3 * x + 1] * r[1] + G[3 * x + 2] * r[2];
+            Gtr[x] = G[x] * r[0] + G[3 + x] * r[1] + G[6 + x] * r[2];
+        }
+        const double rGr = r[0] * Gr[0] + r[1] * Gr[1] + r[2] * Gr[2];
+        const double ir = 1.0 / rho, ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+        const double P = ir3, W = -3.0 * ir5, dP = -3.0 * ir3 * ir, dW = 15.0 * ir5 * ir;
+        const double GT = P * tr + W * rGr;
+        acc[0] += 0.5 * zscale * cj * g.f * GT;
+        acc[1] += 0.5 * zscale * ci * cj * g.df_dS * GT;
+        const double pre = -0.5 * zscale * ci * cj;
+        for (int c = 0; c < 3; ++c) {
+            const double GdT = (dP * tr + dW * rGr) * r[c] * ir + W * (Gr[c] + Gtr[c]);
+            acc[2 + c] += pre * (g.f * GdT + g.df_drho * r[c] * ir * GT);
+        }
+    }
+    __shared__ double scratch[4 * 5];
+    block_sum128<5>(acc, scratch);
+    if (threadIdx.x == 0) {
+        const double sa = sqrt(b.abar0[i]);
+        const double trd = Z[(3LL * i) * ld + 3 * i] + Z[(3LL * i + 1) * ld + 3 * i + 1] +
+                           Z[(3LL * i + 2) * ld + 3 * i + 2];
+        const double g_om = 0.25 * zscale * trd * 2.0 * b.ombar[i] - 1.5 + acc[0] * sa;
+        o.g_ombar[i] = g_om;
+        o.g_abar0[i] = acc[0] * b.ombar[i] / (2.0 * sa);
+        o.g_rbar[i] = acc[1];
+        o.gR[3 * i] = acc[2];
+        o.gR[3 * i + 1] = acc[3];
+        o.gR[3 * i + 2] = acc[4];
+    }
+}
+
+__global__ void k_chain(AtomBufs b, MbdGradOut o, double *h, double *g_a0, double *g_rv, double *H,
+                        long long xstride) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const double ab0 = b.abar0[i], x = ab0 / b.a0[i], x13 = cbrt(x), x23 = x13 * x13;
+    const double g_om = o.g_ombar[i], g_rb = o.g_rbar[i];
+    const double g_c6 = g_om * 4.0 / (3.0 * ab0 * ab0);
+    const double g_ab0 = o.g_abar0[i] - g_om * 8.0 * b.c6bar[i] / (3.0 * ab0 * ab0 * ab0) +
+                         g_rb * b.rv[i] / (3.0 * x23 * b.a0[i]);
+    g_a0[i] = -g_rb * b.rv[i] / (3.0 * x23) * ab0 / (b.a0[i] * b.a0[i]);
+    g_rv[i] = g_rb * x13;
+    for (int k = 0; k < b.nf1; ++k) {
+        const double hk = (k == 0) ? g_ab0 : g_c6 * 3.0 / kPi * b.wu[k] * 2.0 * b.abar[k * b.N + i];
+        h[k * b.N + i] = hk;
+        double *Hk = H + k * xstride + 9LL * i;
+        for (int e = 0; e < 9; ++e) Hk[e] = (e % 4 == 0) ? hk : 0.0;
+    }
+}
+
+// One CTA (128 threads) per row atom i; all frequencies per pair.
+// With Ws = V_i X_j^T + X_i V_j^T (3x3, the blocks (i,j) and (j,i) of V X^T folded):
+//   dE/d alpha_i(u) += -1/3 <Ws, dB/d alpha_i>,  dE/dR_vdW,i += -1/3 <Ws, dB/dS>,
+//   dE/dR_i += +1/3 <Ws, dB/dr>  (r = R_j - R_i),  B = (1 - f) T^GG,
+// plus the diagonal block: dE/d alpha_i(u) += -1/3 sum_x (V X^T)_{ix,ix} (-1/alpha_i^2).
+// Dynamic shared memory: nf1 * 128 doubles of per-thread accumulators.
+__global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, double a, const double *X,
+                                                  const double *V, long long xstride, double *g_a0,
+                                                  double *g_om, double *g_rv, double *gR) {
+    extern __shared__ double gal_s[];   // [nf1][128]
+    const int i = blockIdx.x, t = threadIdx.x;
+    for (int k = 0; k < b.nf1; ++k) gal_s[k * 128 + t] = 0.0;
+    const double Ri[3] = {b.R[3 * i], b.R[3 * i + 1], b.R[3 * i + 2]};
+    double acc[4] = {0, 0, 0, 0};   // g_rv, gR x3
+    for (int j = t; j < b.N; j += 128) {
+        if (j == i) continue;
+        const double r[3] = {b.R[3 * j] - Ri[0], b.R[3 * j + 1] - Ri[1], b.R[3 * j + 2] - Ri[2]};
+        const double rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), ir = 1.0 / rho;
+        const Fermi f = fermi(rho, b.rv[i] + b.rv[j], beta, a);
+        const double sr = 1.0 - f.f;
+        for (int k = 0; k < b.nf1; ++k) {
+            const double *Vk = V + k * xstride, *Xk = X + k * xstride;
+            double Vi[9], Xi[9], Vj[9], Xj[9];
+            for (int e = 0; e < 9; ++e) {
+                Vi[e] = Vk[9LL * i + e]; Xi[e] = Xk[9LL * i + e];
+                Vj[e] = Vk[9LL * j + e]; Xj[e] = Xk[9LL * j + e];
+            }
+            double Ws[9];
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y) {
+                    double w = 0.0;
+                    for (int c = 0; c < 3; ++c) w += Vi[3 * x + c] * Xj[3 * y + c] + Xi[3 * x + c] * Vj[3 * y + c];
+                    Ws[3 * x + y] = w;
+                }
+            const double tr = Ws[0] + Ws[4] + Ws[8];
+            double Wr[3], Wtr[3];
+            for (int x = 0; x < 3; ++x) {
+                Wr[x] = Ws[3 * x] * r[0] + Ws[3 * x + 1] * r[1] + Ws[3 * x + 2] * r[2];
+                Wtr[x] = Ws[x] * r[0] + Ws[3 + x] * r[1] + Ws[6 + x] * r[2];
+            }
+            const double rWr = r[0] * Wr[0] + r[1] * Wr[1] + r[2] * Wr[2];
+            const double si = b.sig_u[k * b.N + i], sj = b.sig_u[k * b.N + j];
+            const double s = sqrt(si * si + sj * sj);
+            const Radial q = tgg_radial(rho, s);
+            const double WT = q.P * tr + q.W * rWr;            // <Ws, T^GG>
+            const double WTs = q.dPs * tr + q.dWs * rWr;       // <Ws, dT^GG/ds>
+            // ds/d alpha_i = (sigma_i / s) * sigma_i / (3 alpha_i)
+            const double dsda = si * si / (3.0 * s * b.al_u[k * b.N + i]);
+            gal_s[k * 128 + t] += -1.0 / 3.0 * sr * WTs * dsda;
+            acc[0] += -1.0 / 3.0 * (-f.df_dS) * WT;
+            for (int c = 0; c < 3; ++c) {
+                const double WdT = (q.dP * tr + q.dW * rWr) * r[c] * ir + q.W * (Wr[c] + Wtr[c]);
+                acc[1 + c] += 1.0 / 3.0 * (sr * WdT - f.df_drho * r[c] * ir * WT);
+            }
+        }
+    }
+    __syncthreads();
+    __shared__ double scratch[4 * 4];
+    block_sum128<4>(acc, scratch);
+    // reduce the per-frequency accumulators, add the diagonal block, chain to alpha0, omega
+    if (t < b.nf1) {
+        const int k = t;
+        double sacc = 0.0;
+        for (int e = 0; e < 128; ++e) sacc += gal_s[k * 128 + e];
+        const double *Vk = V + k * xstride, *Xk = X + k * xstride;
+        double wd = 0.0;
+        for (int e = 0; e < 9; ++e) wd += Vk[9LL * i + e] * Xk[9LL * i + e];
+        const double al = b.al_u[k * b.N + i];
+        sacc += -1.0 / 3.0 * wd * (-1.0 / (al * al));
+        gal_s[k * 128] = sacc;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double ga0 = 0.0, gom = 0.0;
+        const double a0 = b.a0[i], om = b.om[i];
+        for (int k = 0; k < b.nf1; ++k) {
+            const double u = b.u[k], q = 1.0 + u * u / (om * om);
+            const double gal = gal_s[k * 128];
+            ga0 += gal / q;
+            gom += gal * a0 * 2.0 * u * u / (om * om * om) / (q * q);
+        }
+        g_a0[i] += ga0;
+        g_om[i] += gom;
+        g_rv[i] += acc[0];
+        gR[3 * i] += acc[1];
+        gR[3 * i + 1] += acc[2];
+        gR[3 * i + 2] += acc[3];
+    }
+}
+
+__global__ void k_ts_chain(AtomBufs b, const double *g_a0, const double *g_om, const double *g_rv,
+                           double *gp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const int N = b.N;
+    const double v = b.ratio[i], a0r = b.a0ref[i], v13 = cbrt(v);
+    gp[i] = g_a0[i] * v - g_om[i] * 8.0 * b.c6ref[i] / (3.0 * a0r * a0r * a0r);
+    gp[N + i] = g_om[i] * 4.0 / (3.0 * a0r * a0r);
+    gp[2 * N + i] = g_rv[i] * v13;
+    gp[3 * N + i] = g_a0[i] * a0r + g_rv[i] * b.rref[i] / (3.0 * v13 * v13);
+}
+
+inline int cdiv(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
+
+}  // namespace
+
+void prepare_atoms(const AtomBufs &b, int *status, cudaStream_t s) {
+    k_prepare<<<cdiv(b.N, 128), 128, 0, s>>>(b, status);
+}
+
+void build_scs(const AtomBufs &b, double beta, double a, double *M, long long ld, long long mstride,
+               int *status, cudaStream_t s) {
+    dim3 grid(cdiv(b.N, 32), cdiv(b.N, 8));
+    k_build_scs<<<grid, dim3(32, 8), 0, s>>>(b, beta, a, M, ld, mstride, status);
+    const int n = 3 * b.N;
+    if (ld > n) k_pad_identity<<<dim3(cdiv((ld - n) * ld, 256), b.nf1), 256, 0, s>>>(M, ld, n, mstride);
+}
+
+void init_rhs_identity(double *X, long long ld, int n, int nf1, long long xstride, cudaStream_t s) {
+    k_rhs_identity<<<dim3(cdiv(ld, 256), nf1), 256, 0, s>>>(X, ld, n, xstride);
+}
+
+void contract_screen(const AtomBufs &b, const double *X, long long ld, long long xstride, int *status,
+                     cudaStream_t s) {
+    (void)ld;
+    k_contract_screen<<<cdiv(b.N, 128), 128, 0, s>>>(b, X, xstride, status);
+}
+
+void build_q(const AtomBufs &b, double beta, double a, double *Q, long long ld, int *status,
+             cudaStream_t s) {
+    dim3 grid(cdiv(b.N, 32), cdiv(b.N, 8));
+    k_build_q<<<grid, dim3(32, 8), 0, s>>>(b, beta, a, Q, ld, status);
+    const int n = 3 * b.N;
+    if (ld > n) k_pad_q<<<cdiv((ld - n) * ld, 256), 256, 0, s>>>(Q, ld, n, b.ombar);
+}
+
+void energy_trace(const double *Y, long long ld, int n, const double *ombar, int N, double sqrt_s,
+                  double *out, cudaStream_t s) {
+    k_energy<<<1, 256, 0, s>>>(Y, ld, n, ombar, N, sqrt_s, out);
+}
+
+void mbd_grad_pass(const AtomBufs &b, double beta, double a, const double *Z, long long ld,
+                   double zscale, const MbdGradOut &o, cudaStream_t s) {
+    k_mbd_grad<<<b.N, 128, 0, s>>>(b, beta, a, Z, ld, zscale, o);
+}
+
+void chain_screen(const AtomBufs &b, const MbdGradOut &o, double *h, double *g_a0, double *g_rv,
+                  double *H, long long ld, long long xstride, cudaStream_t s) {
+    // zero the padded rows of the adjoint right-hand sides, then fill the atom rows
+    for (int k = 0; k < b.nf1; ++k)
+        cudaMemsetAsync(H + k * xstride, 0, sizeof(double) * 3 * ld, s);
+    k_chain<<<cdiv(b.N, 128), 128, 0, s>>>(b, o, h, g_a0, g_rv, H, xstride);
+}
+
+void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, const double *V,
+                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR,
+                   cudaStream_t s) {
+    const size_t smem = sizeof(double) * b.nf1 * 128;
+    k_scs_grad<<<b.N, 128, smem, s>>>(b, beta, a, X, V, xstride, g_a0, g_om, g_rv, gR);
+}
+
+void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv, double *gp,
+              cudaStream_t s) {
+    k_ts_chain<<<cdiv(b.N, 128), 128, 0, s>>>(b, g_a0, g_om, g_rv, gp);
+}
+
+}  // namespace mbdgb

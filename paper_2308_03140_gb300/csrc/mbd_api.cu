@@ -1,0 +1,509 @@
+// Host orchestration and C ABI of libmbdgb (declared in include/mbd_gb300.h).
+//
+// One evaluation is one stream-ordered pass over the device:
+//   prepare_atoms -> build_scs (all frequencies) -> batched Cholesky -> X = A^{-1} E
+//   -> contract_screen -> build_q -> Gershgorin scale -> coupled Newton-Schulz
+//   -> energy; and for gradients: mbd_grad_pass -> chain_screen -> V = A^{-1} H
+//   -> scs_grad_pass -> ts_chain.
+// The host reads back one scalar per Newton-Schulz iteration (the convergence test)
+// and the status word after the screening stage.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mbd_gb300.h"
+#include "../../include/mbd_gb300_kernels.h"
+#include "internal.h"
+
+using namespace mbdgb;
+
+namespace {
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n, started from the
+// asymptotic root estimate of Tricomi.  Ascending nodes.
+void legendre_rule(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.141592653589793238462643383279502884;
+    for (int k = 1; k <= n; ++k) {
+        double t = std::cos(pi * (4.0 * k - 1.0) / (4.0 * n + 2.0)) *
+                   (1.0 - 1.0 / (8.0 * n * n) + 1.0 / (8.0 * n * n * n));
+        double deriv = 1.0;
+        for (int it = 0; it < 64; ++it) {
+            double pm1 = 1.0, p = t;   // P_0, P_1
+            for (int m = 2; m <= n; ++m) {
+                const double pn = ((2.0 * m - 1.0) * t * p - (m - 1.0) * pm1) / m;
+                pm1 = p;
+                p = pn;
+            }
+            if (n == 1) { p = t; pm1 = 1.0; }
+            deriv = n * (pm1 - t * p) / (1.0 - t * t);
+            const double step = p / deriv;
+            t -= step;
+            if (std::fabs(step) <= 1e-17) break;
+        }
+        {
+            double pm1 = 1.0, p = t;
+            for (int m = 2; m <= n; ++m) {
+                const double pn = ((2.0 * m - 1.0) * t * p - (m - 1.0) * pm1) / m;
+                pm1 = p;
+                p = pn;
+            }
+            if (n == 1) { p = t; pm1 = 1.0; }
+            deriv = n * (pm1 - t * p) / (1.0 - t * t);
+        }
+        x[n - k] = t;
+        w[n - k] = 2.0 / ((1.0 - t * t) * deriv * deriv);
+    }
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mbd_ctx {
+    int device = 0;
+    mbd_options opt{};
+    cudaStream_t stream = nullptr;
+    // problem
+    int N = 0, n = 0, nf1 = 0, nb = 0;
+    long long ld = 0;
+    bool have_geom = false, have_params = false;
+    std::vector<double> hR, ha0, hc6, hrr, hv;
+    std::vector<double> hu, hwu;
+    // device memory: one slab, carved
+    void *slab = nullptr;
+    size_t slab_bytes = 0;
+    double *dR, *da0ref, *dc6ref, *drref, *dratio;
+    double *da0, *dom, *drv, *dalu, *dsigu, *dabar, *dabar0, *dc6bar, *dombar, *drbar, *du, *dwu;
+    double *dM, *ddinv, *dX, *dV;
+    double *dQ, *dZ, *dP, *dY2, *dZ2;
+    double *dh, *dgomb, *dgab0, *dgrb, *dgR, *dga0, *dgom, *dgrv, *dgp;
+    double *dscal;   // [0] energy, [1] Gershgorin, [2] residual
+    int *dstatus;
+    // last results
+    int ns_iter = 0;
+    double ns_scale = 0.0, ns_resid = 0.0;
+    bool have_result = false;
+    bool have_screening = false;
+    // exception
+    int err_code = MBD_OK;
+    std::string err_origin, err_msg;
+};
+
+namespace {
+
+int fail(mbd_ctx *c, int code, const char *origin, const std::string &msg) {
+    if (c) {
+        c->err_code = code;
+        c->err_origin = origin;
+        c->err_msg = msg;
+    }
+    return code;
+}
+
+int cuda_fail(mbd_ctx *c, const char *origin, cudaError_t e) {
+    return fail(c, MBD_ERR_CUDA, origin, std::string("CUDA error: ") + cudaGetErrorString(e));
+}
+
+#define MBD_CUDA(call, origin)                                  \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, origin, e_); \
+    } while (0)
+
+void release(mbd_ctx *ctx) {
+    if (ctx->slab) cudaFree(ctx->slab);
+    ctx->slab = nullptr;
+    ctx->slab_bytes = 0;
+}
+
+// Carves the workspace out of one allocation (256-byte aligned pieces).
+int allocate(mbd_ctx *ctx) {
+    const long long ld = ctx->ld, N = ctx->N, nf1 = ctx->nf1, nb = ctx->nb;
+    const size_t mat = sizeof(double) * static_cast<size_t>(ld) * ld;
+    std::vector<std::pair<double **, size_t>> plan = {
+        {&ctx->dR, 3 * N}, {&ctx->da0ref, N}, {&ctx->dc6ref, N}, {&ctx->drref, N}, {&ctx->dratio, N},
+        {&ctx->da0, N}, {&ctx->dom, N}, {&ctx->drv, N}, {&ctx->dalu, nf1 * N}, {&ctx->dsigu, nf1 * N},
+        {&ctx->dabar, nf1 * N}, {&ctx->dabar0, N}, {&ctx->dc6bar, N}, {&ctx->dombar, N},
+        {&ctx->drbar, N}, {&ctx->du, nf1}, {&ctx->dwu, nf1},
+        {&ctx->ddinv, nf1 * nb * 4096}, {&ctx->dX, nf1 * ld * 3}, {&ctx->dV, nf1 * ld * 3},
+        {&ctx->dh, nf1 * N}, {&ctx->dgomb, N}, {&ctx->dgab0, N}, {&ctx->dgrb, N}, {&ctx->dgR, 3 * N},
+        {&ctx->dga0, N}, {&ctx->dgom, N}, {&ctx->dgrv, N}, {&ctx->dgp, 4 * N}, {&ctx->dscal, 8},
+    };
+    size_t bytes = 0;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    for (auto &p : plan) bytes += al(sizeof(double) * p.second);
+    bytes += al(sizeof(int) * 4);
+    const size_t small = bytes;
+    bytes += nf1 * mat;          // screening matrices / factors
+    bytes += 5 * mat;            // Q (= Y), Z, P, Y', Z'
+    release(ctx);
+    cudaError_t e = cudaMalloc(&ctx->slab, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, "mbd_set_geometry", e);
+    ctx->slab_bytes = bytes;
+    char *p = static_cast<char *>(ctx->slab);
+    for (auto &q : plan) {
+        *q.first = reinterpret_cast<double *>(p);
+        p += al(sizeof(double) * q.second);
+    }
+    ctx->dstatus = reinterpret_cast<int *>(p);
+    p = static_cast<char *>(ctx->slab) + small;
+    ctx->dM = reinterpret_cast<double *>(p);
+    p += nf1 * mat;
+    double **mats[5] = {&ctx->dQ, &ctx->dZ, &ctx->dP, &ctx->dY2, &ctx->dZ2};
+    for (auto m : mats) {
+        *m = reinterpret_cast<double *>(p);
+        p += mat;
+    }
+    // Untouched parts of the factor buffers (strict upper triangles) are read by no
+    // kernel; clearing them once keeps them finite.
+    e = cudaMemset(ctx->slab, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, "mbd_set_geometry", e);
+    e = cudaMemcpy(ctx->du, ctx->hu.data(), sizeof(double) * nf1, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->dwu, ctx->hwu.data(), sizeof(double) * nf1, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, "mbd_set_geometry", e);
+    return MBD_OK;
+}
+
+struct Inputs {
+    const double *R, *a0ref, *c6ref, *rref, *ratio;
+};
+struct Outputs {
+    double *energy, *grad_coords, *grad_params, *alpha_scs;   // device pointers or null
+};
+
+int read_status(mbd_ctx *ctx, cudaStream_t s, const char *origin) {
+    int st = 0;
+    MBD_CUDA(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s), origin);
+    MBD_CUDA(cudaStreamSynchronize(s), origin);
+    MBD_CUDA(cudaGetLastError(), origin);
+    if (st & ST_INPUT) return fail(ctx, MBD_ERR_INPUT, origin, "non-finite or non-positive input, or coincident atoms");
+    if (st & ST_SCS_NOT_PD)
+        return fail(ctx, MBD_ERR_SCS_NOT_PD, origin, "screening matrix alpha^-1 + T^scs is not positive definite");
+    if (st & ST_NEG_ALPHA)
+        return fail(ctx, MBD_ERR_SCS_NEG_ALPHA, origin, "screened static polarizability or C6 is not positive");
+    return MBD_OK;
+}
+
+int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool want_grad) {
+    const int N = ctx->N, n = ctx->n, nf1 = ctx->nf1;
+    const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;
+    const double beta = ctx->opt.beta, a = ctx->opt.a;
+    ctx->have_result = false;
+    ctx->have_screening = false;
+    AtomBufs b{N, nf1, in.R, in.a0ref, in.c6ref, in.rref, in.ratio,
+               ctx->da0, ctx->dom, ctx->drv, ctx->dalu, ctx->dsigu, ctx->dabar,
+               ctx->dabar0, ctx->dc6bar, ctx->dombar, ctx->drbar, ctx->du, ctx->dwu};
+    MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_evaluate");
+    // ---- screening (Sec. 2.3) ----
+    prepare_atoms(b, ctx->dstatus, s);
+    build_scs(b, beta, a, ctx->dM, ld, mat, ctx->dstatus, s);
+    cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
+    init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
+    chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, xs, s);
+    contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
+    int rc = read_status(ctx, s, "screening");
+    if (rc) return rc;
+    ctx->have_screening = true;
+    // ---- coupled-oscillator matrix and its square roots (Sec. 2.1) ----
+    build_q(b, beta, a, ctx->dQ, ld, ctx->dstatus, s);
+    max_abs_rowsum(ctx->dQ, ld, static_cast<int>(ld), ctx->dscal + 1, s);
+    double sc = 0.0;
+    MBD_CUDA(cudaMemcpyAsync(&sc, ctx->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz");
+    MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
+    rc = read_status(ctx, s, "coupled_oscillator_matrix");
+    if (rc) return rc;
+    if (!(sc > 0.0) || !std::isfinite(sc)) return fail(ctx, MBD_ERR_INPUT, "newton_schulz", "invalid Q scale");
+    ctx->ns_scale = sc;
+    double *Y = ctx->dQ, *Z = ctx->dZ, *P = ctx->dP, *Y2 = ctx->dY2, *Z2 = ctx->dZ2;
+    scale_matrix(Y, ld, 1.0 / sc, s);
+    set_identity(Z, ld, s);
+    const int M = static_cast<int>(ld);
+    bool converged = false;
+    double resid = 0.0;
+    int it = 0;
+    for (; it < ctx->opt.ns_max_iter; ++it) {
+        // P = Z Y (not symmetric once rounding separates Z and Y; computed in full)
+        const double *Pk = Y;   // Z_0 = I: P_0 = Y_0
+        if (it > 0) {
+            GemmArgs g{Z, Y, nullptr, P, ld, ld, 0, ld, 0, 0, 0, 0, M, M, M, 1, 1.0, 0.0, 0, 0};
+            gemm_f64(g, s);
+            Pk = P;
+        }
+        frob_dev_identity(Pk, ld, n, ctx->dscal + 2, s);
+        double r2 = 0.0;
+        MBD_CUDA(cudaMemcpyAsync(&r2, ctx->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz");
+        MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
+        resid = std::sqrt(r2);
+        if (!std::isfinite(resid) || resid > 2.0 * std::sqrt(static_cast<double>(n)) + 1.0) {
+            // For positive definite Q every eigenvalue of Z Y stays in (0, 1]; leaving that
+            // range means an eigenvalue of Q is not positive.
+            ctx->ns_iter = it;
+            ctx->ns_resid = resid;
+            return fail(ctx, MBD_ERR_NEG_EIGENVALUE, "newton_schulz",
+                        "Q has a non-positive eigenvalue (polarization catastrophe)");
+        }
+        const bool last = resid < ctx->opt.ns_tol;
+        // Y' = Y T, Z' = T Z with T = 3/2 I - 1/2 P: Y' = 3/2 Y - 1/2 Y (Z Y) and
+        // Z' = 3/2 Z - 1/2 (Z Y) Z.  Y Z Y and Z Y Z are symmetric for any symmetric Y, Z,
+        // so only their upper tiles are computed.  (Replacing Y P by the product with
+        // P^T, i.e. Y Y Z, breaks the coupling and makes rounding errors grow by about
+        // sqrt(cond Q)/2 per step.)
+        GemmArgs gy{Y, Pk, Y, Y2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, -0.5, 1.5, 2, 0};
+        gemm_f64(gy, s);
+        if (it == 0) {
+            axpby_identity(Z2, Pk, ld, 1.5, -0.5, s);
+        } else {
+            GemmArgs gz{Pk, Z, Z, Z2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, -0.5, 1.5, 2, 0};
+            gemm_f64(gz, s);
+        }
+        std::swap(Y, Y2);
+        std::swap(Z, Z2);
+        if (last) {
+            converged = true;
+            ++it;
+            break;
+        }
+    }
+    ctx->ns_iter = it;
+    ctx->ns_resid = resid;
+    if (!converged)
+        return fail(ctx, MBD_ERR_NOT_CONVERGED, "newton_schulz", "iteration cap reached");
+    const double ss = std::sqrt(sc);
+    energy_trace(Y, ld, n, ctx->dombar, N, ss, out.energy ? out.energy : ctx->dscal, s);
+    // ---- gradients (Sec. 2.4) ----
+    if (want_grad) {
+        MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
+        mbd_grad_pass(b, beta, a, Z, ld, 1.0 / ss, go, s);
+        chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, ctx->dV, ld, xs, s);
+        MBD_CUDA(cudaMemsetAsync(ctx->dgom, 0, sizeof(double) * N, s), "gradients");
+        chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dV, xs, s);
+        scs_grad_pass(b, beta, a, ctx->dX, ctx->dV, xs, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgR, s);
+        if (out.grad_params) ts_chain(b, ctx->dga0, ctx->dgom, ctx->dgrv, out.grad_params, s);
+        if (out.grad_coords)
+            MBD_CUDA(cudaMemcpyAsync(out.grad_coords, ctx->dgR, sizeof(double) * 3 * N,
+                                     cudaMemcpyDeviceToDevice, s), "gradients");
+    }
+    if (out.alpha_scs)
+        MBD_CUDA(cudaMemcpyAsync(out.alpha_scs, ctx->dabar0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s),
+                 "outputs");
+    MBD_CUDA(cudaStreamSynchronize(s), "mbd_evaluate");
+    MBD_CUDA(cudaGetLastError(), "mbd_evaluate");
+    ctx->have_result = true;
+    return MBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mbd_default_options(mbd_options *opt) {
+    if (!opt) return MBD_ERR_INPUT;
+    opt->n_freq = 15;
+    opt->beta = 0.83;
+    opt->a = 6.0;
+    opt->precision = MBD_PREC_FP64;
+    opt->ns_tol = 1e-8;
+    opt->ns_max_iter = 100;
+    return MBD_OK;
+}
+
+int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt) {
+    if (!out) return MBD_ERR_INPUT;
+    *out = nullptr;
+    mbd_options o;
+    if (opt) o = *opt; else mbd_default_options(&o);
+    if (o.n_freq < 1 || o.n_freq + 1 > kMaxFreq || !(o.beta > 0) || !(o.a > 0) || o.ns_max_iter < 1 ||
+        !(o.ns_tol > 0) || o.precision != MBD_PREC_FP64)
+        return MBD_ERR_INPUT;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev)
+        return MBD_ERR_CUDA;
+    mbd_ctx *c = new mbd_ctx();
+    c->device = cuda_device;
+    c->opt = o;
+    c->nf1 = o.n_freq + 1;
+    std::vector<double> x, w;
+    legendre_rule(o.n_freq, x, w);
+    c->hu.assign(c->nf1, 0.0);
+    c->hwu.assign(c->nf1, 0.0);
+    for (int k = 0; k < o.n_freq; ++k) {   // u = 0.6 (1+x)/(1-x), du = 1.2/(1-x)^2 dx (Sec. 3.3)
+        c->hu[k + 1] = 0.6 * (1.0 + x[k]) / (1.0 - x[k]);
+        c->hwu[k + 1] = w[k] * 1.2 / ((1.0 - x[k]) * (1.0 - x[k]));
+    }
+    if (cudaSetDevice(cuda_device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return MBD_ERR_CUDA;
+    }
+    *out = c;
+    return MBD_OK;
+}
+
+int mbd_destroy(mbd_ctx *ctx) {
+    if (!ctx) return MBD_OK;
+    cudaSetDevice(ctx->device);
+    release(ctx);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return MBD_OK;
+}
+
+int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const double *lattice,
+                     const int *k_grid) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (lattice || k_grid)
+        return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_set_geometry", "periodic systems are not available in this build");
+    if (n_atoms < 1 || !coords) return fail(ctx, MBD_ERR_INPUT, "mbd_set_geometry", "need n_atoms >= 1 and coords");
+    for (int k = 0; k < 3 * n_atoms; ++k)
+        if (!std::isfinite(coords[k])) return fail(ctx, MBD_ERR_INPUT, "mbd_set_geometry", "non-finite coordinate");
+    MBD_CUDA(cudaSetDevice(ctx->device), "mbd_set_geometry");
+    const bool realloc = (n_atoms != ctx->N) || !ctx->slab;
+    ctx->N = n_atoms;
+    ctx->n = 3 * n_atoms;
+    ctx->ld = (ctx->n + kTile - 1) / kTile * kTile;
+    ctx->nb = static_cast<int>(ctx->ld / kTile);
+    ctx->hR.assign(coords, coords + 3 * n_atoms);
+    if (realloc) {
+        ctx->have_params = false;
+        int rc = allocate(ctx);
+        if (rc) { ctx->have_geom = false; return rc; }
+    }
+    ctx->have_geom = true;
+    ctx->have_result = false;
+    return MBD_OK;
+}
+
+int mbd_set_free_atom_params(mbd_ctx *ctx, const double *alpha0_ref, const double *c6_ref,
+                             const double *rvdw_ref, const double *volume_ratio) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (!ctx->have_geom) return fail(ctx, MBD_ERR_STATE, "mbd_set_free_atom_params", "set the geometry first");
+    if (!alpha0_ref || !c6_ref || !rvdw_ref || !volume_ratio)
+        return fail(ctx, MBD_ERR_INPUT, "mbd_set_free_atom_params", "null parameter array");
+    const int N = ctx->N;
+    ctx->ha0.assign(alpha0_ref, alpha0_ref + N);
+    ctx->hc6.assign(c6_ref, c6_ref + N);
+    ctx->hrr.assign(rvdw_ref, rvdw_ref + N);
+    ctx->hv.assign(volume_ratio, volume_ratio + N);
+    ctx->have_params = true;
+    ctx->have_result = false;
+    return MBD_OK;
+}
+
+int mbd_evaluate(mbd_ctx *ctx, double *energy, double *grad_coords, double *grad_lattice,
+                 double *grad_params, double *alpha_scs) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (!ctx->have_geom || !ctx->have_params)
+        return fail(ctx, MBD_ERR_STATE, "mbd_evaluate", "set the geometry and the free-atom parameters first");
+    if (grad_lattice) return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_evaluate", "no lattice gradient for finite systems");
+    if (!energy) return fail(ctx, MBD_ERR_INPUT, "mbd_evaluate", "energy pointer is required");
+    MBD_CUDA(cudaSetDevice(ctx->device), "mbd_evaluate");
+    const int N = ctx->N;
+    cudaStream_t s = ctx->stream;
+    MBD_CUDA(cudaMemcpyAsync(ctx->dR, ctx->hR.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s), "mbd_evaluate");
+    MBD_CUDA(cudaMemcpyAsync(ctx->da0ref, ctx->ha0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_evaluate");
+    MBD_CUDA(cudaMemcpyAsync(ctx->dc6ref, ctx->hc6.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_evaluate");
+    MBD_CUDA(cudaMemcpyAsync(ctx->drref, ctx->hrr.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_evaluate");
+    MBD_CUDA(cudaMemcpyAsync(ctx->dratio, ctx->hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_evaluate");
+    const bool want_grad = grad_coords || grad_params;
+    Inputs in{ctx->dR, ctx->da0ref, ctx->dc6ref, ctx->drref, ctx->dratio};
+    Outputs o{ctx->dscal, nullptr, grad_params ? ctx->dgp : nullptr, nullptr};   // gradients stay in dgR
+    int rc = run(ctx, s, in, o, want_grad);
+    if (rc) return rc;
+    double e = 0.0;
+    MBD_CUDA(cudaMemcpyAsync(&e, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, s), "mbd_evaluate");
+    if (grad_coords)
+        MBD_CUDA(cudaMemcpyAsync(grad_coords, ctx->dgR, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s), "mbd_evaluate");
+    if (grad_params)
+        MBD_CUDA(cudaMemcpyAsync(grad_params, ctx->dgp, sizeof(double) * 4 * N, cudaMemcpyDeviceToHost, s), "mbd_evaluate");
+    if (alpha_scs)
+        MBD_CUDA(cudaMemcpyAsync(alpha_scs, ctx->dabar0, sizeof(double) * N, cudaMemcpyDeviceToHost, s), "mbd_evaluate");
+    MBD_CUDA(cudaStreamSynchronize(s), "mbd_evaluate");
+    *energy = e;
+    return MBD_OK;
+}
+
+int mbd_evaluate_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coords, const double *alpha0_ref,
+                     const double *c6_ref, const double *rvdw_ref, const double *volume_ratio, double *energy,
+                     double *grad_coords, double *grad_params, double *alpha_scs) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (!ctx->have_geom) return fail(ctx, MBD_ERR_STATE, "mbd_evaluate_dev", "set the geometry first");
+    if (n_atoms != ctx->N)
+        return fail(ctx, MBD_ERR_INPUT, "mbd_evaluate_dev", "n_atoms differs from the geometry's size");
+    if (!coords || !alpha0_ref || !c6_ref || !rvdw_ref || !volume_ratio || !energy)
+        return fail(ctx, MBD_ERR_INPUT, "mbd_evaluate_dev", "null device pointer");
+    MBD_CUDA(cudaSetDevice(ctx->device), "mbd_evaluate_dev");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool want_grad = grad_coords || grad_params;
+    Inputs in{coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio};
+    Outputs o{energy, grad_coords, grad_params, alpha_scs};
+    return run(ctx, s, in, o, want_grad);
+}
+
+int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega, double *rvdw) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (!ctx->have_screening) return fail(ctx, MBD_ERR_STATE, "mbd_get_scs_detail", "no screening result");
+    MBD_CUDA(cudaSetDevice(ctx->device), "mbd_get_scs_detail");
+    const size_t N = ctx->N;
+    if (alpha_iu) MBD_CUDA(cudaMemcpy(alpha_iu, ctx->dabar, sizeof(double) * N * ctx->nf1, cudaMemcpyDeviceToHost), "mbd_get_scs_detail");
+    if (c6) MBD_CUDA(cudaMemcpy(c6, ctx->dc6bar, sizeof(double) * N, cudaMemcpyDeviceToHost), "mbd_get_scs_detail");
+    if (omega) MBD_CUDA(cudaMemcpy(omega, ctx->dombar, sizeof(double) * N, cudaMemcpyDeviceToHost), "mbd_get_scs_detail");
+    if (rvdw) MBD_CUDA(cudaMemcpy(rvdw, ctx->drbar, sizeof(double) * N, cudaMemcpyDeviceToHost), "mbd_get_scs_detail");
+    return MBD_OK;
+}
+
+int mbd_get_stats(mbd_ctx *ctx, int *ns_iterations, double *ns_scale, double *ns_residual) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (ns_iterations) *ns_iterations = ctx->ns_iter;
+    if (ns_scale) *ns_scale = ctx->ns_scale;
+    if (ns_residual) *ns_residual = ctx->ns_resid;
+    return MBD_OK;
+}
+
+int mbd_get_exception(const mbd_ctx *ctx, int *code, char *origin, char *msg, size_t len) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (code) *code = ctx->err_code;
+    if (origin && len) {
+        std::strncpy(origin, ctx->err_origin.c_str(), len - 1);
+        origin[len - 1] = '\0';
+    }
+    if (msg && len) {
+        std::strncpy(msg, ctx->err_msg.c_str(), len - 1);
+        msg[len - 1] = '\0';
+    }
+    return MBD_OK;
+}
+
+int mbdk_gemm_f64(void *stream, int trans_b, int mode, int M, int N, int K, double alpha,
+                  const double *A, long long lda, const double *B, long long ldb, double beta,
+                  const double *D, long long ldd, double *C, long long ldc) {
+    if (M <= 0 || N <= 0 || K <= 0 || M % kTile || N % kTile || K % kTile || mode < 0 || mode > 2 ||
+        (mode && M != N) || !A || !B || !C || (beta != 0.0 && !D) || (lda | ldb | ldc) & 1 ||
+        (D && (ldd & 1)) || (trans_b != 0 && trans_b != 1))
+        return MBD_ERR_INPUT;
+    GemmArgs g{A, B, D, C, lda, ldb, ldd, ldc, 0, 0, 0, 0, M, N, K, 1, alpha, beta, mode, trans_b};
+    gemm_f64(g, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
+}
+
+int mbdk_cholesky_f64(void *stream, double *A, long long ld, int batch, double *dinv, int *status) {
+    if (ld <= 0 || ld % kTile || batch < 1 || !A || !dinv || !status) return MBD_ERR_INPUT;
+    cholesky_f64(A, ld, ld * ld, batch, dinv, status, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
+}
+
+int mbdk_chol_solve3_f64(void *stream, const double *L, long long ld, int batch, const double *dinv,
+                         double *X) {
+    if (ld <= 0 || ld % kTile || batch < 1 || !L || !dinv || !X) return MBD_ERR_INPUT;
+    chol_solve3_f64(L, ld, ld * ld, batch, dinv, X, 3 * ld, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
+}
+
+}  // extern "C"
