@@ -112,6 +112,29 @@ int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega
  * Y0 = Q/s, and the final Frobenius norm of I - Z Y.  Any may be NULL. */
 int mbd_get_stats(mbd_ctx *ctx, int *ns_iterations, double *ns_scale, double *ns_residual);
 
+/* Device-time profile of the last evaluation, gathered with CUDA events on the stream
+ * the work was launched on when profiling is enabled (mbd_set_profiling).  Times in
+ * milliseconds; flops are the algorithmic counts of the listed kernels (2 m n k for a
+ * full product, n^2 (n + 1) for a product whose symmetric result is formed from one
+ * triangle, n^3/3 per Cholesky factorisation). */
+typedef struct {
+    int launches;            /* CUDA kernels launched by the evaluation                  */
+    int gemm_launches;       /* FP64 tensor-path GEMM launches of the Newton-Schulz stage */
+    double gemm_ms;          /* summed device time of those launches                      */
+    double gemm_flops;       /* their summed algorithmic flops                            */
+    double screening_ms;     /* build + factorise + solve, all frequency points           */
+    double screening_flops;  /* (n_freq + 1) n^3 / 3                                      */
+    double newton_schulz_ms; /* Q build, scale, iterations, energy                        */
+    double gradient_ms;      /* all gradient passes and adjoint solves                    */
+    double total_ms;
+} mbd_profile;
+
+/* Enables (1) or disables (0) event timing of the following evaluations. */
+int mbd_set_profiling(mbd_ctx *ctx, int enable);
+
+/* Profile of the last evaluation; all zero if profiling was off. */
+int mbd_get_profile(mbd_ctx *ctx, mbd_profile *out);
+
 /* Last error of this context: code, the stage that failed (origin) and a message,
  * each string truncated to len bytes including the terminator.  ctx may not be NULL. */
 int mbd_get_exception(const mbd_ctx *ctx, int *code, char *origin, char *msg, size_t len);

@@ -25,13 +25,20 @@ MBD_PREC_FP64 = 0
 # Every symbol declared in include/mbd_gb300.h.
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
            "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_get_scs_detail",
-           "mbd_get_stats", "mbd_get_exception",
+           "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
            "mbdk_gemm_f64", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64")
 
 
 class mbd_options(C.Structure):
     _fields_ = [("n_freq", C.c_int), ("beta", C.c_double), ("a", C.c_double),
                 ("precision", C.c_int), ("ns_tol", C.c_double), ("ns_max_iter", C.c_int)]
+
+
+class mbd_profile(C.Structure):
+    _fields_ = [("launches", C.c_int), ("gemm_launches", C.c_int), ("gemm_ms", C.c_double),
+                ("gemm_flops", C.c_double), ("screening_ms", C.c_double),
+                ("screening_flops", C.c_double), ("newton_schulz_ms", C.c_double),
+                ("gradient_ms", C.c_double), ("total_ms", C.c_double)]
 
 
 class MBDError(RuntimeError):
@@ -64,6 +71,8 @@ def load(path: str | None = None):
     L.mbd_get_scs_detail.argtypes = [vp, _P, _P, _P, _P]
     L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P]
     L.mbd_get_exception.argtypes = [vp, C.POINTER(C.c_int), C.c_char_p, C.c_char_p, sz]
+    L.mbd_set_profiling.argtypes = [vp, i]
+    L.mbd_get_profile.argtypes = [vp, C.POINTER(mbd_profile)]
     ll = C.c_longlong
     L.mbdk_gemm_f64.argtypes = [vp, i, i, i, i, i, d, vp, ll, vp, ll, d, vp, ll, vp, ll]
     L.mbdk_cholesky_f64.argtypes = [vp, vp, ll, i, vp, vp]
@@ -177,6 +186,14 @@ class MBD:
         a, c6, om, rv = np.zeros((nf1, N)), np.zeros(N), np.zeros(N), np.zeros(N)
         self._check(self.lib.mbd_get_scs_detail(self.h, _ptr(a), _ptr(c6), _ptr(om), _ptr(rv)))
         return dict(alpha_bar=a, c6=c6, omega=om, rvdw=rv)
+
+    def set_profiling(self, enable: bool = True):
+        self._check(self.lib.mbd_set_profiling(self.h, int(bool(enable))))
+
+    def profile(self):
+        p = mbd_profile()
+        self._check(self.lib.mbd_get_profile(self.h, C.byref(p)))
+        return {k: getattr(p, k) for k, _ in mbd_profile._fields_}
 
     def stats(self):
         it, sc, res = C.c_int(), C.c_double(), C.c_double()

@@ -9,6 +9,10 @@ namespace mbdgb {
 constexpr int kTile = 64;          // dense tile edge; leading dimensions are multiples of it
 constexpr int kMaxFreq = 64;       // upper bound on n_freq + 1
 
+// Process-wide count of kernel launches made by this library (for profiles).
+void count_launches(int k);
+long long launch_count();
+
 // Bits of the device status word.
 enum : int {
     ST_INPUT = 1,          // NaN input or coincident atoms

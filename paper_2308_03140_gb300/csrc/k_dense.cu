@@ -41,7 +41,7 @@ __device__ __forceinline__ void tri_index(int bid, int &r, int &c) {
 
 // TB: B is N x K (C = A B^T) when true, K x N (C = A B) when false.
 template <bool TB>
-__global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int tiles_n) {
+__device__ __forceinline__ void gemm_tile(const GemmArgs &g, int tiles_n) {
     int tm, tn;
     if (g.mode == 0) {
         tm = blockIdx.x / tiles_n;
@@ -132,6 +132,9 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int tiles_n) {
             }
         }
 }
+
+__global__ void __launch_bounds__(128) k_gemm_nt(GemmArgs g, int tiles_n) { gemm_tile<true>(g, tiles_n); }
+__global__ void __launch_bounds__(128) k_gemm_nn(GemmArgs g, int tiles_n) { gemm_tile<false>(g, tiles_n); }
 
 // Unblocked Cholesky of the 64x64 diagonal block (lower part read), in shared memory,
 // followed by the inverse of the triangular factor.  L^{-1} (lower) is kept in the
@@ -328,8 +331,14 @@ void gemm_f64(const GemmArgs &g, cudaStream_t s) {
     dim3 grid;
     if (g.mode == 0) grid = dim3(tm * tn, 1, g.batch);
     else grid = dim3(tm * (tm + 1) / 2, 1, g.batch);   // square M == N for triangular modes
-    if (g.trans_b) k_gemm<true><<<grid, 128, 0, s>>>(g, tn);
-    else k_gemm<false><<<grid, 128, 0, s>>>(g, tn);
+    if (g.trans_b) {
+        count_launches(1);
+        k_gemm_nt<<<grid, 128, 0, s>>>(g, tn);
+    }
+    else {
+        count_launches(1);
+        k_gemm_nn<<<grid, 128, 0, s>>>(g, tn);
+    }
 }
 
 __global__ void k_axpby_identity(double *Z, const double *P, long long ld, double a, double b) {
@@ -340,6 +349,7 @@ __global__ void k_axpby_identity(double *Z, const double *P, long long ld, doubl
 }
 
 void axpby_identity(double *Z, const double *P, long long ld, double a, double b, cudaStream_t s) {
+    count_launches(1);
     k_axpby_identity<<<1216, 256, 0, s>>>(Z, P, ld, a, b);
 }
 
@@ -348,6 +358,7 @@ void cholesky_f64(double *A, long long ld, long long mstride, int batch, double 
     const int nb = static_cast<int>(ld / kTile);
     for (int k = 0; k < nb; ++k) {
         const long long k0 = static_cast<long long>(k) * kTile;
+        count_launches(1);
         k_potrf_diag<<<batch, 256, 0, s>>>(A + k0 * ld + k0, ld, mstride, dinv + k * 4096LL,
                                            static_cast<long long>(nb) * 4096, status);
         const int rem = static_cast<int>(ld - k0 - kTile);
@@ -368,23 +379,31 @@ void chol_solve3_f64(const double *L, long long ld, long long mstride, int batch
                      double *X, long long xstride, cudaStream_t s) {
     const int nb = static_cast<int>(ld / kTile);
     const long long dstride = static_cast<long long>(nb) * 4096;
+    count_launches(1);
     k_trsv_fwd3<<<batch, 256, 0, s>>>(L, ld, mstride, dinv, dstride, X, xstride, nb);
+    count_launches(1);
     k_trsv_bwd3<<<batch, 256, 0, s>>>(L, ld, mstride, dinv, dstride, X, xstride, nb);
 }
 
 void frob_dev_identity(const double *P, long long ld, int n, double *out, cudaStream_t s) {
     cudaMemsetAsync(out, 0, sizeof(double), s);
+    count_launches(1);
     k_frob_dev_identity<<<608, 256, 0, s>>>(P, ld, n, out);
 }
 
 void scale_matrix(double *Y, long long ld, double scale, cudaStream_t s) {
+    count_launches(1);
     k_scale<<<1216, 256, 0, s>>>(Y, ld * ld, scale);
 }
 
-void set_identity(double *Z, long long ld, cudaStream_t s) { k_identity<<<1216, 256, 0, s>>>(Z, ld); }
+void set_identity(double *Z, long long ld, cudaStream_t s) {
+    count_launches(1);
+    k_identity<<<1216, 256, 0, s>>>(Z, ld);
+}
 
 void max_abs_rowsum(const double *Q, long long ld, int n, double *out, cudaStream_t s) {
     cudaMemsetAsync(out, 0, sizeof(double), s);
+    count_launches(1);
     k_max_abs_rowsum<<<n, 256, 0, s>>>(Q, ld, n, reinterpret_cast<unsigned long long *>(out));
 }
 

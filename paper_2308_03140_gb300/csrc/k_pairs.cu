@@ -425,42 +425,55 @@ inline int cdiv(long long a, long long b) { return static_cast<int>((a + b - 1) 
 }  // namespace
 
 void prepare_atoms(const AtomBufs &b, int *status, cudaStream_t s) {
+    count_launches(1);
     k_prepare<<<cdiv(b.N, 128), 128, 0, s>>>(b, status);
 }
 
 void build_scs(const AtomBufs &b, double beta, double a, double *M, long long ld, long long mstride,
                int *status, cudaStream_t s) {
     dim3 grid(cdiv(b.N, 32), cdiv(b.N, 8));
+    count_launches(1);
     k_build_scs<<<grid, dim3(32, 8), 0, s>>>(b, beta, a, M, ld, mstride, status);
     const int n = 3 * b.N;
-    if (ld > n) k_pad_identity<<<dim3(cdiv((ld - n) * ld, 256), b.nf1), 256, 0, s>>>(M, ld, n, mstride);
+    if (ld > n) {
+        count_launches(1);
+        k_pad_identity<<<dim3(cdiv((ld - n) * ld, 256), b.nf1), 256, 0, s>>>(M, ld, n, mstride);
+    }
 }
 
 void init_rhs_identity(double *X, long long ld, int n, int nf1, long long xstride, cudaStream_t s) {
+    count_launches(1);
     k_rhs_identity<<<dim3(cdiv(ld, 256), nf1), 256, 0, s>>>(X, ld, n, xstride);
 }
 
 void contract_screen(const AtomBufs &b, const double *X, long long ld, long long xstride, int *status,
                      cudaStream_t s) {
     (void)ld;
+    count_launches(1);
     k_contract_screen<<<cdiv(b.N, 128), 128, 0, s>>>(b, X, xstride, status);
 }
 
 void build_q(const AtomBufs &b, double beta, double a, double *Q, long long ld, int *status,
              cudaStream_t s) {
     dim3 grid(cdiv(b.N, 32), cdiv(b.N, 8));
+    count_launches(1);
     k_build_q<<<grid, dim3(32, 8), 0, s>>>(b, beta, a, Q, ld, status);
     const int n = 3 * b.N;
-    if (ld > n) k_pad_q<<<cdiv((ld - n) * ld, 256), 256, 0, s>>>(Q, ld, n, b.ombar);
+    if (ld > n) {
+        count_launches(1);
+        k_pad_q<<<cdiv((ld - n) * ld, 256), 256, 0, s>>>(Q, ld, n, b.ombar);
+    }
 }
 
 void energy_trace(const double *Y, long long ld, int n, const double *ombar, int N, double sqrt_s,
                   double *out, cudaStream_t s) {
+    count_launches(1);
     k_energy<<<1, 256, 0, s>>>(Y, ld, n, ombar, N, sqrt_s, out);
 }
 
 void mbd_grad_pass(const AtomBufs &b, double beta, double a, const double *Z, long long ld,
                    double zscale, const MbdGradOut &o, cudaStream_t s) {
+    count_launches(1);
     k_mbd_grad<<<b.N, 128, 0, s>>>(b, beta, a, Z, ld, zscale, o);
 }
 
@@ -469,6 +482,7 @@ void chain_screen(const AtomBufs &b, const MbdGradOut &o, double *h, double *g_a
     // zero the padded rows of the adjoint right-hand sides, then fill the atom rows
     for (int k = 0; k < b.nf1; ++k)
         cudaMemsetAsync(H + k * xstride, 0, sizeof(double) * 3 * ld, s);
+    count_launches(1);
     k_chain<<<cdiv(b.N, 128), 128, 0, s>>>(b, o, h, g_a0, g_rv, H, xstride);
 }
 
@@ -476,11 +490,13 @@ void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, co
                    long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR,
                    cudaStream_t s) {
     const size_t smem = sizeof(double) * b.nf1 * 128;
+    count_launches(1);
     k_scs_grad<<<b.N, 128, smem, s>>>(b, beta, a, X, V, xstride, g_a0, g_om, g_rv, gR);
 }
 
 void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv, double *gp,
               cudaStream_t s) {
+    count_launches(1);
     k_ts_chain<<<cdiv(b.N, 128), 128, 0, s>>>(b, g_a0, g_om, g_rv, gp);
 }
 

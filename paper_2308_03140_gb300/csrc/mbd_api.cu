@@ -7,6 +7,7 @@
 //   -> scs_grad_pass -> ts_chain.
 // The host reads back one scalar per Newton-Schulz iteration (the convergence test)
 // and the status word after the screening stage.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -18,6 +19,13 @@
 #include "internal.h"
 
 using namespace mbdgb;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void mbdgb::count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long mbdgb::launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -94,6 +102,11 @@ struct mbd_ctx {
     // exception
     int err_code = MBD_OK;
     std::string err_origin, err_msg;
+    // profiling (CUDA events on the launch stream)
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    int ev_used = 0;
+    mbd_profile prof{};
 };
 
 namespace {
@@ -116,6 +129,30 @@ int cuda_fail(mbd_ctx *c, const char *origin, cudaError_t e) {
         cudaError_t e_ = (call);                                \
         if (e_ != cudaSuccess) return cuda_fail(ctx, origin, e_); \
     } while (0)
+
+// Next free timing event of the context (created on first use, reused per evaluation).
+cudaEvent_t next_event(mbd_ctx *ctx) {
+    if (ctx->ev_used == static_cast<int>(ctx->events.size())) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->events.push_back(e);
+    }
+    return ctx->events[ctx->ev_used++];
+}
+
+struct Span { cudaEvent_t a = nullptr, b = nullptr; double flops = 0.0; };
+
+void mark(mbd_ctx *ctx, cudaStream_t s, cudaEvent_t &e) {
+    if (!ctx->profiling) return;
+    e = next_event(ctx);
+    if (e) cudaEventRecord(e, s);
+}
+
+double span_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (a && b && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) return ms;
+    return 0.0;
+}
 
 void release(mbd_ctx *ctx) {
     if (ctx->slab) cudaFree(ctx->slab);
@@ -198,9 +235,25 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     const double beta = ctx->opt.beta, a = ctx->opt.a;
     ctx->have_result = false;
     ctx->have_screening = false;
+    ctx->ev_used = 0;
+    ctx->prof = mbd_profile{};
+    const long long launches0 = launch_count();
+    cudaEvent_t e_start = nullptr, e_scs = nullptr, e_ns = nullptr, e_grad = nullptr;
+    std::vector<Span> gemms;
+    auto timed_gemm = [&](const GemmArgs &g, double flops) {
+        Span sp;
+        sp.flops = flops;
+        mark(ctx, s, sp.a);
+        gemm_f64(g, s);
+        mark(ctx, s, sp.b);
+        if (ctx->profiling) gemms.push_back(sp);
+    };
+    const double nd = static_cast<double>(ctx->n);
+    const double flops_full = 2.0 * nd * nd * nd, flops_sym = nd * nd * (nd + 1.0);
     AtomBufs b{N, nf1, in.R, in.a0ref, in.c6ref, in.rref, in.ratio,
                ctx->da0, ctx->dom, ctx->drv, ctx->dalu, ctx->dsigu, ctx->dabar,
                ctx->dabar0, ctx->dc6bar, ctx->dombar, ctx->drbar, ctx->du, ctx->dwu};
+    mark(ctx, s, e_start);
     MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_evaluate");
     // ---- screening (Sec. 2.3) ----
     prepare_atoms(b, ctx->dstatus, s);
@@ -209,6 +262,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
     chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, xs, s);
     contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
+    mark(ctx, s, e_scs);
     int rc = read_status(ctx, s, "screening");
     if (rc) return rc;
     ctx->have_screening = true;
@@ -234,7 +288,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         const double *Pk = Y;   // Z_0 = I: P_0 = Y_0
         if (it > 0) {
             GemmArgs g{Z, Y, nullptr, P, ld, ld, 0, ld, 0, 0, 0, 0, M, M, M, 1, 1.0, 0.0, 0, 0};
-            gemm_f64(g, s);
+            timed_gemm(g, flops_full);
             Pk = P;
         }
         frob_dev_identity(Pk, ld, n, ctx->dscal + 2, s);
@@ -257,12 +311,12 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         // P^T, i.e. Y Y Z, breaks the coupling and makes rounding errors grow by about
         // sqrt(cond Q)/2 per step.)
         GemmArgs gy{Y, Pk, Y, Y2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, -0.5, 1.5, 2, 0};
-        gemm_f64(gy, s);
+        timed_gemm(gy, flops_sym);
         if (it == 0) {
             axpby_identity(Z2, Pk, ld, 1.5, -0.5, s);
         } else {
             GemmArgs gz{Pk, Z, Z, Z2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, -0.5, 1.5, 2, 0};
-            gemm_f64(gz, s);
+            timed_gemm(gz, flops_sym);
         }
         std::swap(Y, Y2);
         std::swap(Z, Z2);
@@ -278,6 +332,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         return fail(ctx, MBD_ERR_NOT_CONVERGED, "newton_schulz", "iteration cap reached");
     const double ss = std::sqrt(sc);
     energy_trace(Y, ld, n, ctx->dombar, N, ss, out.energy ? out.energy : ctx->dscal, s);
+    mark(ctx, s, e_ns);
     // ---- gradients (Sec. 2.4) ----
     if (want_grad) {
         MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
@@ -294,8 +349,23 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     if (out.alpha_scs)
         MBD_CUDA(cudaMemcpyAsync(out.alpha_scs, ctx->dabar0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s),
                  "outputs");
+    mark(ctx, s, e_grad);
     MBD_CUDA(cudaStreamSynchronize(s), "mbd_evaluate");
     MBD_CUDA(cudaGetLastError(), "mbd_evaluate");
+    ctx->prof.launches = static_cast<int>(launch_count() - launches0);
+    if (ctx->profiling) {
+        mbd_profile &p = ctx->prof;
+        p.gemm_launches = static_cast<int>(gemms.size());
+        for (const Span &sp : gemms) {
+            p.gemm_ms += span_ms(sp.a, sp.b);
+            p.gemm_flops += sp.flops;
+        }
+        p.screening_ms = span_ms(e_start, e_scs);
+        p.screening_flops = nf1 * nd * nd * nd / 3.0;
+        p.newton_schulz_ms = span_ms(e_scs, e_ns);
+        p.gradient_ms = span_ms(e_ns, e_grad);
+        p.total_ms = span_ms(e_start, e_grad);
+    }
     ctx->have_result = true;
     return MBD_OK;
 }
@@ -351,6 +421,7 @@ int mbd_destroy(mbd_ctx *ctx) {
     if (!ctx) return MBD_OK;
     cudaSetDevice(ctx->device);
     release(ctx);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return MBD_OK;
@@ -464,6 +535,18 @@ int mbd_get_stats(mbd_ctx *ctx, int *ns_iterations, double *ns_scale, double *ns
     if (ns_iterations) *ns_iterations = ctx->ns_iter;
     if (ns_scale) *ns_scale = ctx->ns_scale;
     if (ns_residual) *ns_residual = ctx->ns_resid;
+    return MBD_OK;
+}
+
+int mbd_set_profiling(mbd_ctx *ctx, int enable) {
+    if (!ctx) return MBD_ERR_INPUT;
+    ctx->profiling = enable != 0;
+    return MBD_OK;
+}
+
+int mbd_get_profile(mbd_ctx *ctx, mbd_profile *out) {
+    if (!ctx || !out) return MBD_ERR_INPUT;
+    *out = ctx->prof;
     return MBD_OK;
 }
 
