@@ -40,6 +40,26 @@ int mbdk_cholesky_f64(void *stream, double *A, long long ld, int batch, double *
 int mbdk_chol_solve3_f64(void *stream, const double *L, long long ld, int batch, const double *dinv,
                          double *X);
 
+/* Allocation-free factor-and-solve (the paper has no counterpart; this serves callers
+ * that cannot let a library allocate device memory -- codes that give the whole GPU to
+ * their own memory pool, or that must not incur the device-wide synchronisation
+ * cudaMalloc/cudaFree can cause inside a time step).
+ *
+ * Same result as mbdk_cholesky_f64 followed by mbdk_chol_solve3_f64 on the same
+ * stream: A [batch][ld][ld] is overwritten by its lower Cholesky factors and X
+ * [batch][ld][3] by the solutions of A X = B.  The diagonal-block inverses that those
+ * calls keep in the caller's dinv buffer live instead in one static 16 MiB device
+ * array inside the library (2^21 doubles), so the call allocates nothing and calls no
+ * allocating routine.  Limit: batch * (ld/64) * 4096 <= 2^21; larger requests return
+ * MBD_ERR_SCRATCH_LIMIT before any work is launched.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current, so
+ * make that first call before any stream capture.  All calls on a device share the
+ * array and it keeps the last call's contents; calls whose work overlaps on the GPU
+ * race on it and must be serialised by the caller.  status as in mbdk_cholesky_f64. */
+#define MBD_ERR_SCRATCH_LIMIT 9
+int mbdk_cholesky_solve3_f64_noalloc(void *stream, double *A, long long ld, int batch, double *X,
+                                     int *status);
+
 #ifdef __cplusplus
 }
 #endif

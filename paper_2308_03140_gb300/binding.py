@@ -19,14 +19,15 @@ LIB_PATH = _build.LIB
 MBD_OK = 0
 ERRORS = {1: "MBD_ERR_INPUT", 2: "MBD_ERR_NEG_EIGENVALUE", 3: "MBD_ERR_SCS_NEG_ALPHA",
           4: "MBD_ERR_SCS_NOT_PD", 5: "MBD_ERR_NOT_CONVERGED", 6: "MBD_ERR_CUDA",
-          7: "MBD_ERR_STATE", 8: "MBD_ERR_UNSUPPORTED"}
+          7: "MBD_ERR_STATE", 8: "MBD_ERR_UNSUPPORTED", 9: "MBD_ERR_SCRATCH_LIMIT"}
 MBD_PREC_FP64 = 0
 
 # Every symbol declared in include/mbd_gb300.h.
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
            "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_get_scs_detail",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
-           "mbdk_gemm_f64", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64")
+           "mbdk_gemm_f64", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
+           "mbdk_cholesky_solve3_f64_noalloc")
 
 
 class mbd_options(C.Structure):
@@ -77,6 +78,7 @@ def load(path: str | None = None):
     L.mbdk_gemm_f64.argtypes = [vp, i, i, i, i, i, d, vp, ll, vp, ll, d, vp, ll, vp, ll]
     L.mbdk_cholesky_f64.argtypes = [vp, vp, ll, i, vp, vp]
     L.mbdk_chol_solve3_f64.argtypes = [vp, vp, ll, i, vp, vp]
+    L.mbdk_cholesky_solve3_f64_noalloc.argtypes = [vp, vp, ll, i, vp, vp]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -233,6 +235,15 @@ def mbdk_chol_solve3_f64(Lf, dinv, X, stream=None):
     rc = L.mbdk_chol_solve3_f64(_stream(Lf, stream), _tptr(Lf), Lf.shape[-1], Lf.shape[0], _tptr(dinv), _tptr(X))
     if rc:
         raise MBDError(rc, "mbdk_chol_solve3_f64", "launch rejected")
+
+
+def mbdk_cholesky_solve3_f64_noalloc(A, X, status, stream=None):
+    """Factor A [batch, ld, ld] in place and solve A X = B in place (X [batch, ld, 3]),
+    with the factorisation's scratch in the library's static device array; returns the
+    C return code (0, or MBD_ERR_SCRATCH_LIMIT = 9 for requests beyond 2^21 doubles)."""
+    L = load()
+    return L.mbdk_cholesky_solve3_f64_noalloc(_stream(A, stream), _tptr(A), A.shape[-1], A.shape[0],
+                                              _tptr(X), _tptr(status))
 
 
 def evaluate_system(sys, device: int = 0, gradients: bool = True, **opts):
