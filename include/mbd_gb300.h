@@ -103,6 +103,19 @@ int mbd_evaluate_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
                      const double *volume_ratio, double *energy, double *grad_coords,
                      double *grad_params, double *alpha_scs);
 
+/* Hand-written backward of the last evaluation (the analytic gradient of Sec. 2.4 as a
+ * reverse-mode pass): from the device state the last mbd_evaluate or mbd_evaluate_dev
+ * left in the context (screening factors, M^{-1} 1 and Q^{-1/2}), computes
+ * grad_energy[0] * dE/dX for coordinates (grad_coords [n_atoms][3]) and free-atom
+ * parameters (grad_params [4][n_atoms]); either may be NULL.  All pointers are device
+ * pointers; grad_energy may be NULL (factor 1).  The inputs must be the ones of that
+ * evaluation (same values; they are read again).  MBD_ERR_STATE if no evaluation has
+ * succeeded since the context was created or its geometry last reallocated. */
+int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coords,
+                     const double *alpha0_ref, const double *c6_ref, const double *rvdw_ref,
+                     const double *volume_ratio, const double *grad_energy, double *grad_coords,
+                     double *grad_params);
+
 /* Screening detail of the last successful evaluation, host arrays: alpha_iu
  * [n_freq+1][n_atoms] (row 0 is u = 0), c6 [n_atoms], omega [n_atoms] (screened
  * frequencies), rvdw [n_atoms] (screened damping radii).  Any may be NULL. */

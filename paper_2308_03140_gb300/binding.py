@@ -24,7 +24,8 @@ MBD_PREC_FP64 = 0
 
 # Every symbol declared in include/mbd_gb300.h.
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
-           "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_get_scs_detail",
+           "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_backward_dev",
+           "mbd_get_scs_detail",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
            "mbdk_gemm_f64", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
            "mbdk_cholesky_solve3_f64_noalloc")
@@ -69,6 +70,7 @@ def load(path: str | None = None):
     L.mbd_set_free_atom_params.argtypes = [vp, _P, _P, _P, _P]
     L.mbd_evaluate.argtypes = [vp, _P, _P, _P, _P, _P]
     L.mbd_evaluate_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.mbd_backward_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mbd_get_scs_detail.argtypes = [vp, _P, _P, _P, _P]
     L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P]
     L.mbd_get_exception.argtypes = [vp, C.POINTER(C.c_int), C.c_char_p, C.c_char_p, sz]
@@ -181,6 +183,19 @@ class MBD:
                                        _tptr(coords), _tptr(alpha0_ref), _tptr(c6_ref), _tptr(rvdw_ref),
                                        _tptr(volume_ratio), _tptr(energy), _tptr(grad_coords),
                                        _tptr(grad_params), _tptr(alpha_scs))
+        self._check(rc)
+
+    def backward_dev(self, coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio, grad_energy=None,
+                     grad_coords=None, grad_params=None, stream=None):
+        """Hand-written backward of the last evaluation (device tensors, outputs
+        preallocated): grad_energy * dE/dX for coordinates and parameters."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(coords.device)
+        rc = self.lib.mbd_backward_dev(self.h, C.c_void_p(stream.cuda_stream), int(coords.shape[0]),
+                                       _tptr(coords), _tptr(alpha0_ref), _tptr(c6_ref), _tptr(rvdw_ref),
+                                       _tptr(volume_ratio), _tptr(grad_energy), _tptr(grad_coords),
+                                       _tptr(grad_params))
         self._check(rc)
 
     def scs_detail(self):

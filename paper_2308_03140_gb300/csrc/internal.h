@@ -58,6 +58,10 @@ void frob_dev_identity(const double *P, long long ld, int n, double *out, cudaSt
 void scale_matrix(double *Y, long long ld, double scale, cudaStream_t s);
 // Z = I (ld x ld).
 void set_identity(double *Z, long long ld, cudaStream_t s);
+// Lanczos tridiagonal coefficients of a symmetric ld x ld matrix from a fixed start
+// vector: coef[2j] = alpha_j, coef[2j+1] = beta_j, j < steps.  work: 3 ld doubles.
+void lanczos_coefficients(const double *A, long long ld, int steps, double *work, double *coef,
+                          cudaStream_t s);
 // Maximum absolute row sum over rows 0..n-1 (Gershgorin bound), written to out[0].
 void max_abs_rowsum(const double *Q, long long ld, int n, double *out, cudaStream_t s);
 
@@ -103,8 +107,10 @@ void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, co
                    long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR,
                    cudaStream_t s);
 
-// TS-scaling chain to [4][N] parameter gradients.
+// TS-scaling chain to [4][N] parameter gradients, times *scale (device) if given.
 void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv,
-              double *gp, cudaStream_t s);
+              const double *scale, double *gp, cudaStream_t s);
+// y = (*scale) x (scale device pointer, NULL for 1).
+void scale_copy(const double *x, int n, const double *scale, double *y, cudaStream_t s);
 
 }  // namespace mbdgb

@@ -324,7 +324,86 @@ __global__ void k_max_abs_rowsum(const double *Q, long long ld, int n, unsigned 
     }
 }
 
+// ---- Lanczos estimates of the extreme eigenvalues of a symmetric matrix ----
+// y = A x for an ld x ld row-major A: one warp per row, coalesced row reads.
+__global__ void k_gemv(const double *A, long long ld, const double *x, double *y) {
+    const long long row = blockIdx.x * static_cast<long long>(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= ld) return;
+    const double *a = A + row * ld;
+    double acc = 0.0;
+    for (long long c = lane; c < ld; c += 32) acc += a[c] * x[c];
+    acc = warp_sum(acc);
+    if (lane == 0) y[row] = acc;
+}
+
+__device__ double block_sum1024(double v, double *sh) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = (threadIdx.x < 32) ? sh[threadIdx.x] : 0.0;
+    if (threadIdx.x < 32) t = warp_sum(t);
+    __syncthreads();
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// v = a fixed pseudo-random unit vector, vprev = 0.
+__global__ void __launch_bounds__(1024) k_lanczos_init(double *v, double *vprev, long long ld) {
+    __shared__ double sh[32];
+    double ss = 0.0;
+    for (long long p = threadIdx.x; p < ld; p += 1024) {
+        const double x = sin(0.7548776662 * static_cast<double>(p) + 0.5698402910) + 0.25;
+        v[p] = x;
+        vprev[p] = 0.0;
+        ss += x * x;
+    }
+    const double nrm = sqrt(block_sum1024(ss, sh));
+    for (long long p = threadIdx.x; p < ld; p += 1024) v[p] /= nrm;
+}
+
+// One Lanczos step after w = A v: alpha = w.v; w -= alpha v + beta_prev vprev;
+// beta = |w|; vprev = v; v = w / beta.  coef[2j] = alpha, coef[2j+1] = beta.
+__global__ void __launch_bounds__(1024) k_lanczos_update(double *w, double *v, double *vprev, long long ld,
+                                                         double *coef, int j) {
+    __shared__ double sh[32];
+    double d = 0.0;
+    for (long long p = threadIdx.x; p < ld; p += 1024) d += w[p] * v[p];
+    const double alpha = block_sum1024(d, sh);
+    const double bprev = j > 0 ? coef[2 * j - 1] : 0.0;
+    double ss = 0.0;
+    for (long long p = threadIdx.x; p < ld; p += 1024) {
+        const double x = w[p] - alpha * v[p] - bprev * vprev[p];
+        w[p] = x;
+        ss += x * x;
+    }
+    const double beta = sqrt(block_sum1024(ss, sh));
+    const double inv = beta > 1e-300 ? 1.0 / beta : 0.0;
+    for (long long p = threadIdx.x; p < ld; p += 1024) {
+        vprev[p] = v[p];
+        v[p] = w[p] * inv;
+    }
+    if (threadIdx.x == 0) {
+        coef[2 * j] = alpha;
+        coef[2 * j + 1] = beta;
+    }
+}
+
 }  // namespace
+
+void lanczos_coefficients(const double *A, long long ld, int steps, double *work, double *coef, cudaStream_t s) {
+    double *v = work, *vprev = work + ld, *w = work + 2 * ld;
+    count_launches(1);
+    k_lanczos_init<<<1, 1024, 0, s>>>(v, vprev, ld);
+    for (int j = 0; j < steps; ++j) {
+        count_launches(2);
+        k_gemv<<<static_cast<int>((ld + 7) / 8), 256, 0, s>>>(A, ld, v, w);
+        k_lanczos_update<<<1, 1024, 0, s>>>(w, v, vprev, ld, coef, j);
+    }
+}
 
 void gemm_f64(const GemmArgs &g, cudaStream_t s) {
     const int tm = g.M / BM, tn = g.N / BN;

@@ -409,15 +409,21 @@ __global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, doubl
 }
 
 __global__ void k_ts_chain(AtomBufs b, const double *g_a0, const double *g_om, const double *g_rv,
-                           double *gp) {
+                           const double *scale, double *gp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
     const int N = b.N;
+    const double w = scale ? scale[0] : 1.0;
     const double v = b.ratio[i], a0r = b.a0ref[i], v13 = cbrt(v);
-    gp[i] = g_a0[i] * v - g_om[i] * 8.0 * b.c6ref[i] / (3.0 * a0r * a0r * a0r);
-    gp[N + i] = g_om[i] * 4.0 / (3.0 * a0r * a0r);
-    gp[2 * N + i] = g_rv[i] * v13;
-    gp[3 * N + i] = g_a0[i] * a0r + g_rv[i] * b.rref[i] / (3.0 * v13 * v13);
+    gp[i] = w * (g_a0[i] * v - g_om[i] * 8.0 * b.c6ref[i] / (3.0 * a0r * a0r * a0r));
+    gp[N + i] = w * (g_om[i] * 4.0 / (3.0 * a0r * a0r));
+    gp[2 * N + i] = w * (g_rv[i] * v13);
+    gp[3 * N + i] = w * (g_a0[i] * a0r + g_rv[i] * b.rref[i] / (3.0 * v13 * v13));
+}
+
+__global__ void k_scale_copy(const double *x, int n, const double *scale, double *y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (scale ? scale[0] : 1.0) * x[i];
 }
 
 inline int cdiv(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
@@ -494,10 +500,15 @@ void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, co
     k_scs_grad<<<b.N, 128, smem, s>>>(b, beta, a, X, V, xstride, g_a0, g_om, g_rv, gR);
 }
 
-void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv, double *gp,
-              cudaStream_t s) {
+void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv,
+              const double *scale, double *gp, cudaStream_t s) {
     count_launches(1);
-    k_ts_chain<<<cdiv(b.N, 128), 128, 0, s>>>(b, g_a0, g_om, g_rv, gp);
+    k_ts_chain<<<cdiv(b.N, 128), 128, 0, s>>>(b, g_a0, g_om, g_rv, scale, gp);
+}
+
+void scale_copy(const double *x, int n, const double *scale, double *y, cudaStream_t s) {
+    count_launches(1);
+    k_scale_copy<<<cdiv(n, 256), 256, 0, s>>>(x, n, scale, y);
 }
 
 }  // namespace mbdgb

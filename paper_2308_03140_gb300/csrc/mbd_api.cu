@@ -7,6 +7,7 @@
 //   -> scs_grad_pass -> ts_chain.
 // The host reads back one scalar per Newton-Schulz iteration (the convergence test)
 // and the status word after the screening stage.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -67,10 +68,42 @@ void legendre_rule(int n, std::vector<double> &x, std::vector<double> &w) {
     }
 }
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
+// Number of eigenvalues below x of the symmetric tridiagonal matrix (diag a, offdiag b)
+// by the Sturm sequence of its LDL^T pivots.
+int sturm_count(const std::vector<double> &a, const std::vector<double> &b, double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const double off = i ? b[i - 1] * b[i - 1] : 0.0;
+        d = a[i] - x - (i ? off / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// Smallest and largest eigenvalue of a symmetric tridiagonal matrix by bisection.
+void tridiag_extremes(const std::vector<double> &a, const std::vector<double> &b, double &lo, double &hi) {
+    double g0 = 1e300, g1 = -1e300;   // Gershgorin interval of the tridiagonal
+    for (size_t i = 0; i < a.size(); ++i) {
+        const double r = (i ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < a.size() ? std::fabs(b[i]) : 0.0);
+        g0 = std::min(g0, a[i] - r);
+        g1 = std::max(g1, a[i] + r);
+    }
+    const int m = static_cast<int>(a.size());
+    double l = g0, h = g1;
+    for (int it = 0; it < 200; ++it) {   // smallest: count(x) >= 1
+        const double mid = 0.5 * (l + h);
+        if (sturm_count(a, b, mid) >= 1) h = mid; else l = mid;
+    }
+    lo = h;
+    l = g0; h = g1;
+    for (int it = 0; it < 200; ++it) {   // largest: count(x) >= m
+        const double mid = 0.5 * (l + h);
+        if (sturm_count(a, b, mid) >= m) h = mid; else l = mid;
+    }
+    hi = h;
+}
 
 }  // namespace
 
@@ -99,6 +132,10 @@ struct mbd_ctx {
     double ns_scale = 0.0, ns_resid = 0.0;
     bool have_result = false;
     bool have_screening = false;
+    // state of the last forward evaluation, kept for mbd_backward_dev
+    bool have_forward = false;
+    double *Zlast = nullptr;   // Newton-Schulz Z (Q^{-1/2} = zscale * Z)
+    double zscale = 0.0;
     // exception
     int err_code = MBD_OK;
     std::string err_origin, err_msg;
@@ -171,7 +208,7 @@ int allocate(mbd_ctx *ctx) {
         {&ctx->drbar, N}, {&ctx->du, nf1}, {&ctx->dwu, nf1},
         {&ctx->ddinv, nf1 * nb * 4096}, {&ctx->dX, nf1 * ld * 3}, {&ctx->dV, nf1 * ld * 3},
         {&ctx->dh, nf1 * N}, {&ctx->dgomb, N}, {&ctx->dgab0, N}, {&ctx->dgrb, N}, {&ctx->dgR, 3 * N},
-        {&ctx->dga0, N}, {&ctx->dgom, N}, {&ctx->dgrv, N}, {&ctx->dgp, 4 * N}, {&ctx->dscal, 8},
+        {&ctx->dga0, N}, {&ctx->dgom, N}, {&ctx->dgrv, N}, {&ctx->dgp, 4 * N}, {&ctx->dscal, 8 + 2 * 64},
     };
     size_t bytes = 0;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -216,6 +253,30 @@ struct Outputs {
     double *energy, *grad_coords, *grad_params, *alpha_scs;   // device pointers or null
 };
 
+AtomBufs atom_bufs(mbd_ctx *ctx, const Inputs &in) {
+    return AtomBufs{ctx->N, ctx->nf1, in.R, in.a0ref, in.c6ref, in.rref, in.ratio,
+                    ctx->da0, ctx->dom, ctx->drv, ctx->dalu, ctx->dsigu, ctx->dabar,
+                    ctx->dabar0, ctx->dc6bar, ctx->dombar, ctx->drbar, ctx->du, ctx->dwu};
+}
+
+// Gradient passes (Sec. 2.4) from the state of the last forward evaluation: the MBD
+// pair pass on Q^{-1/2}, the chain through the screened parameters, the adjoint solves
+// V = A^{-1} H with the kept factors, the SCS pair pass and the TS chain.  Outputs are
+// scaled by *grad_energy (device scalar) when it is given.
+void backward_passes(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const double *grad_energy,
+                     double *grad_coords, double *grad_params) {
+    const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;
+    const double beta = ctx->opt.beta, a = ctx->opt.a;
+    MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
+    mbd_grad_pass(b, beta, a, ctx->Zlast, ld, ctx->zscale, go, s);
+    chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, ctx->dV, ld, xs, s);
+    cudaMemsetAsync(ctx->dgom, 0, sizeof(double) * ctx->N, s);
+    chol_solve3_f64(ctx->dM, ld, mat, ctx->nf1, ctx->ddinv, ctx->dV, xs, s);
+    scs_grad_pass(b, beta, a, ctx->dX, ctx->dV, xs, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgR, s);
+    if (grad_params) ts_chain(b, ctx->dga0, ctx->dgom, ctx->dgrv, grad_energy, grad_params, s);
+    if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
+}
+
 int read_status(mbd_ctx *ctx, cudaStream_t s, const char *origin) {
     int st = 0;
     MBD_CUDA(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s), origin);
@@ -250,9 +311,8 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     };
     const double nd = static_cast<double>(ctx->n);
     const double flops_full = 2.0 * nd * nd * nd, flops_sym = nd * nd * (nd + 1.0);
-    AtomBufs b{N, nf1, in.R, in.a0ref, in.c6ref, in.rref, in.ratio,
-               ctx->da0, ctx->dom, ctx->drv, ctx->dalu, ctx->dsigu, ctx->dabar,
-               ctx->dabar0, ctx->dc6bar, ctx->dombar, ctx->drbar, ctx->du, ctx->dwu};
+    ctx->have_forward = false;
+    const AtomBufs b = atom_bufs(ctx, in);
     mark(ctx, s, e_start);
     MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_evaluate");
     // ---- screening (Sec. 2.3) ----
@@ -275,9 +335,42 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     rc = read_status(ctx, s, "coupled_oscillator_matrix");
     if (rc) return rc;
     if (!(sc > 0.0) || !std::isfinite(sc)) return fail(ctx, MBD_ERR_INPUT, "newton_schulz", "invalid Q scale");
-    ctx->ns_scale = sc;
     double *Y = ctx->dQ, *Z = ctx->dZ, *P = ctx->dP, *Y2 = ctx->dY2, *Z2 = ctx->dZ2;
     scale_matrix(Y, ld, 1.0 / sc, s);
+    // Lanczos estimates of the extreme eigenvalues of Y0 = Q/s (workspace: rows of P).
+    // The largest tightens s (Lanczos converges fast at the top of the spectrum; a 5 %
+    // margin keeps Y0's spectrum inside (0, 1]); the smallest gives the lower bound l0
+    // for the scaled iteration below, halved for safety.
+    const int lz_steps = std::min(48, static_cast<int>(ld));
+    lanczos_coefficients(Y, ld, lz_steps, P, ctx->dscal + 8, s);
+    std::vector<double> lz(2 * lz_steps);
+    MBD_CUDA(cudaMemcpyAsync(lz.data(), ctx->dscal + 8, sizeof(double) * 2 * lz_steps, cudaMemcpyDeviceToHost, s),
+             "newton_schulz");
+    MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
+    double th_min = 0.0, th_max = 1.0;
+    {
+        std::vector<double> da, db;
+        for (int j = 0; j < lz_steps; ++j) {
+            da.push_back(lz[2 * j]);
+            if (j + 1 < lz_steps) db.push_back(lz[2 * j + 1]);
+            if (!(lz[2 * j + 1] > 1e-14)) break;   // invariant subspace reached
+        }
+        db.resize(da.size() > 0 ? da.size() - 1 : 0);
+        if (!da.empty()) tridiag_extremes(da, db, th_min, th_max);
+    }
+    // ubound: upper bound on sqrt(eig(Z Y)) for the first step: 1 under the Gershgorin
+    // scale; 1.05 after tightening by the Lanczos estimate (tolerates an underestimate
+    // of the largest eigenvalue by up to 16 %).
+    double ubound = 1.0;
+    if (std::isfinite(th_max) && th_max > 0.0 && 1.05 * th_max < 1.0) {
+        const double f = 1.05 * th_max;
+        scale_matrix(Y, ld, 1.0 / f, s);
+        sc *= f;
+        th_min /= f;
+        ubound = 1.05;
+    }
+    ctx->ns_scale = sc;
+    double lbound = std::sqrt(std::max(0.5 * th_min, 1e-12));   // lower bound on sqrt(eig(Z Y))
     set_identity(Z, ld, s);
     const int M = static_cast<int>(ld);
     bool converged = false;
@@ -305,17 +398,28 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
                         "Q has a non-positive eigenvalue (polarization catastrophe)");
         }
         const bool last = resid < ctx->opt.ns_tol;
-        // Y' = Y T, Z' = T Z with T = 3/2 I - 1/2 P: Y' = 3/2 Y - 1/2 Y (Z Y) and
-        // Z' = 3/2 Z - 1/2 (Z Y) Z.  Y Z Y and Z Y Z are symmetric for any symmetric Y, Z,
-        // so only their upper tiles are computed.  (Replacing Y P by the product with
-        // P^T, i.e. Y Y Z, breaks the coupling and makes rounding errors grow by about
-        // sqrt(cond Q)/2 per step.)
-        GemmArgs gy{Y, Pk, Y, Y2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, -0.5, 1.5, 2, 0};
+        // Scaled step (sign-function form of the coupled iteration): with x^2 the
+        // eigenvalues of P in [l^2, u^2], T = (al/2)(3 I - al^2 P) maps x to
+        // f(x) = (al x/2)(3 - al^2 x^2); al^2 = 3/(u^2 + u l + l^2) gives f(l) = f(u), so
+        // [l, u] goes onto [f(l), 1].  f stays positive for x < sqrt(3)/al, so any l
+        // below the true bound (and any u above it) only costs speed.  al = 1 near
+        // convergence.
+        double al = 1.0;
+        if (!last && lbound < 0.999)
+            al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
+        const double c1 = 1.5 * al, c3 = -0.5 * al * al * al;
+        lbound = std::min(1.0, 0.5 * al * lbound * (3.0 - al * al * lbound * lbound));
+        ubound = 1.0;
+        // Y' = Y T, Z' = T Z: Y' = c1 Y + c3 Y (Z Y) and Z' = c1 Z + c3 (Z Y) Z.  Y Z Y and
+        // Z Y Z are symmetric for any symmetric Y, Z, so only their upper tiles are
+        // computed.  (Using P^T in place of P, i.e. Y Y Z, breaks the coupling and makes
+        // rounding errors grow by about sqrt(cond Q)/2 per step.)
+        GemmArgs gy{Y, Pk, Y, Y2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, c3, c1, 2, 0};
         timed_gemm(gy, flops_sym);
         if (it == 0) {
-            axpby_identity(Z2, Pk, ld, 1.5, -0.5, s);
+            axpby_identity(Z2, Pk, ld, c1, c3, s);
         } else {
-            GemmArgs gz{Pk, Z, Z, Z2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, -0.5, 1.5, 2, 0};
+            GemmArgs gz{Pk, Z, Z, Z2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, c3, c1, 2, 0};
             timed_gemm(gz, flops_sym);
         }
         std::swap(Y, Y2);
@@ -333,19 +437,10 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     const double ss = std::sqrt(sc);
     energy_trace(Y, ld, n, ctx->dombar, N, ss, out.energy ? out.energy : ctx->dscal, s);
     mark(ctx, s, e_ns);
+    ctx->Zlast = Z;
+    ctx->zscale = 1.0 / ss;
     // ---- gradients (Sec. 2.4) ----
-    if (want_grad) {
-        MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
-        mbd_grad_pass(b, beta, a, Z, ld, 1.0 / ss, go, s);
-        chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, ctx->dV, ld, xs, s);
-        MBD_CUDA(cudaMemsetAsync(ctx->dgom, 0, sizeof(double) * N, s), "gradients");
-        chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dV, xs, s);
-        scs_grad_pass(b, beta, a, ctx->dX, ctx->dV, xs, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgR, s);
-        if (out.grad_params) ts_chain(b, ctx->dga0, ctx->dgom, ctx->dgrv, out.grad_params, s);
-        if (out.grad_coords)
-            MBD_CUDA(cudaMemcpyAsync(out.grad_coords, ctx->dgR, sizeof(double) * 3 * N,
-                                     cudaMemcpyDeviceToDevice, s), "gradients");
-    }
+    if (want_grad) backward_passes(ctx, s, b, nullptr, out.grad_coords, out.grad_params);
     if (out.alpha_scs)
         MBD_CUDA(cudaMemcpyAsync(out.alpha_scs, ctx->dabar0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s),
                  "outputs");
@@ -367,6 +462,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         p.total_ms = span_ms(e_start, e_grad);
     }
     ctx->have_result = true;
+    ctx->have_forward = true;
     return MBD_OK;
 }
 
@@ -444,6 +540,7 @@ int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const doub
     ctx->hR.assign(coords, coords + 3 * n_atoms);
     if (realloc) {
         ctx->have_params = false;
+        ctx->have_forward = false;
         int rc = allocate(ctx);
         if (rc) { ctx->have_geom = false; return rc; }
     }
@@ -516,6 +613,24 @@ int mbd_evaluate_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
     Inputs in{coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio};
     Outputs o{energy, grad_coords, grad_params, alpha_scs};
     return run(ctx, s, in, o, want_grad);
+}
+
+int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coords,
+                     const double *alpha0_ref, const double *c6_ref, const double *rvdw_ref,
+                     const double *volume_ratio, const double *grad_energy, double *grad_coords,
+                     double *grad_params) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (!ctx->have_forward)
+        return fail(ctx, MBD_ERR_STATE, "mbd_backward_dev", "no forward evaluation to differentiate");
+    if (n_atoms != ctx->N || !coords || !alpha0_ref || !c6_ref || !rvdw_ref || !volume_ratio)
+        return fail(ctx, MBD_ERR_INPUT, "mbd_backward_dev", "inputs must match the forward evaluation");
+    MBD_CUDA(cudaSetDevice(ctx->device), "mbd_backward_dev");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Inputs in{coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio};
+    backward_passes(ctx, s, atom_bufs(ctx, in), grad_energy, grad_coords, grad_params);
+    MBD_CUDA(cudaStreamSynchronize(s), "mbd_backward_dev");
+    MBD_CUDA(cudaGetLastError(), "mbd_backward_dev");
+    return MBD_OK;
 }
 
 int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega, double *rvdw) {
