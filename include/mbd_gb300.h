@@ -44,8 +44,15 @@ extern "C" {
 #define MBD_ERR_STATE 7           /* call order (geometry/parameters not set)        */
 #define MBD_ERR_UNSUPPORTED 8     /* option not available in this build              */
 
-/* Arithmetic of the dense stages (screening solves and the matrix function). */
+/* Arithmetic of the matrix function Q^{+-1/2}.  The mixed modes run the Newton-Schulz
+ * iterations on the 5th-generation tensor cores with FP32 accumulation, then one FP64
+ * correction: with Z ~ Q^{-1/2}, V = Q Z and W = Z V (FP64), Tr Q^{1/2} is taken as
+ * (3 Tr V - sum V o W)/2, whose error is second order in the error of Z; the energy
+ * subtraction and all sums stay in FP64 with compensation.  Gradients use Z. */
 #define MBD_PREC_FP64 0           /* plain FP64 throughout                           */
+#define MBD_PREC_TF32 1           /* TF32 tensor-core products, FP64 correction      */
+#define MBD_PREC_BF16X3 2         /* bf16 hi/lo split products (3 per GEMM), FP64 correction */
+#define MBD_PREC_TF32X3 3         /* TF32 hi/lo split products (3 per GEMM), FP64 correction */
 
 typedef struct mbd_ctx mbd_ctx;
 
@@ -56,7 +63,7 @@ typedef struct {
     int n_freq;          /* Gauss-Legendre points of the Casimir-Polder integral     */
     double beta;         /* damping scale s_R of the Fermi function, Eq. (fermi-damping) */
     double a;            /* damping steepness                                          */
-    int precision;       /* MBD_PREC_*                                                 */
+    int precision;       /* MBD_PREC_* (default FP64)                                  */
     double ns_tol;
     int ns_max_iter;
 } mbd_options;
@@ -122,8 +129,10 @@ int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
 int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega, double *rvdw);
 
 /* Statistics of the last evaluation: Newton-Schulz iterations, the scale s of
- * Y0 = Q/s, and the final Frobenius norm of I - Z Y.  Any may be NULL. */
-int mbd_get_stats(mbd_ctx *ctx, int *ns_iterations, double *ns_scale, double *ns_residual);
+ * Y0 = Q/s, the final Frobenius norm of I - Z Y, and (mixed modes) the Frobenius norm of
+ * Z Q Z - I in FP64 for the Z ~ Q^{-1/2} used (0 in FP64 mode).  Any may be NULL. */
+int mbd_get_stats(mbd_ctx *ctx, int *ns_iterations, double *ns_scale, double *ns_residual,
+                  double *correction_residual);
 
 /* Device-time profile of the last evaluation, gathered with CUDA events on the stream
  * the work was launched on when profiling is enabled (mbd_set_profiling).  Times in
@@ -140,6 +149,10 @@ typedef struct {
     double newton_schulz_ms; /* Q build, scale, iterations, energy                        */
     double gradient_ms;      /* all gradient passes and adjoint solves                    */
     double total_ms;
+    int tc_launches;         /* tensor-core (tcgen05) GEMM launches, mixed modes           */
+    double tc_ms;            /* their summed device time                                  */
+    double tc_flops;         /* their algorithmic flops (one product each)                */
+    double correction_ms;    /* FP64 correction of the mixed modes                        */
 } mbd_profile;
 
 /* Enables (1) or disables (0) event timing of the following evaluations. */

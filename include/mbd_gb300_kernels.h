@@ -40,6 +40,21 @@ int mbdk_cholesky_f64(void *stream, double *A, long long ld, int batch, double *
 int mbdk_chol_solve3_f64(void *stream, const double *L, long long ld, int batch, const double *dinv,
                          double *X);
 
+/* C = alpha * sum_p A_p B_p^T + beta * D on the 5th-generation tensor cores (tcgen05,
+ * TMA-staged operands, FP32 accumulation in tensor memory) -- the products of the
+ * mixed-precision Newton-Schulz iteration.  kind 0 (TF32): A0 = A and B0 = B are FP32,
+ * A1/B1 ignored.  kind 1 (BF16x3): A0/A1 = bf16 hi/lo parts of A (A = A0 + A1), likewise
+ * B; the three products A0 B0 + A0 B1 + A1 B0 are accumulated.  kind 2 (TF32x3): as kind
+ * 1 with 32-bit parts (A0 = TF32-rounded A, A1 = FP32 remainder).  A is M x K (lda), B is
+ * N x K (ldb); D (FP32, may be NULL when beta == 0), C (FP32, may be NULL), C_hi/C_lo
+ * (split of the result in the kind's part format, kinds 1 and 2, may be NULL) and CT (FP32 transpose of the result, mode 0
+ * and M == N only, may be NULL) share the leading dimension ldc.  M and N multiples of 128, K of 64,
+ * leading dimensions multiples of 8.  mode 0: all tiles; mode 2: upper tiles mirrored
+ * (M == N, symmetric results).  err (device int) gets bit 8 set if a wait timed out. */
+int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float alpha, const void *A0,
+                 const void *A1, long long lda, const void *B0, const void *B1, long long ldb, float beta,
+                 const float *D, float *C, void *C_hi, void *C_lo, float *CT, long long ldc, int *err);
+
 /* Allocation-free factor-and-solve (the paper has no counterpart; this serves callers
  * that cannot let a library allocate device memory -- codes that give the whole GPU to
  * their own memory pool, or that must not incur the device-wide synchronisation

@@ -20,14 +20,14 @@ MBD_OK = 0
 ERRORS = {1: "MBD_ERR_INPUT", 2: "MBD_ERR_NEG_EIGENVALUE", 3: "MBD_ERR_SCS_NEG_ALPHA",
           4: "MBD_ERR_SCS_NOT_PD", 5: "MBD_ERR_NOT_CONVERGED", 6: "MBD_ERR_CUDA",
           7: "MBD_ERR_STATE", 8: "MBD_ERR_UNSUPPORTED", 9: "MBD_ERR_SCRATCH_LIMIT"}
-MBD_PREC_FP64 = 0
+MBD_PREC_FP64, MBD_PREC_TF32, MBD_PREC_BF16X3, MBD_PREC_TF32X3 = 0, 1, 2, 3
 
 # Every symbol declared in include/mbd_gb300.h.
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
            "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_backward_dev",
            "mbd_get_scs_detail",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
-           "mbdk_gemm_f64", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
+           "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
            "mbdk_cholesky_solve3_f64_noalloc")
 
 
@@ -40,7 +40,8 @@ class mbd_profile(C.Structure):
     _fields_ = [("launches", C.c_int), ("gemm_launches", C.c_int), ("gemm_ms", C.c_double),
                 ("gemm_flops", C.c_double), ("screening_ms", C.c_double),
                 ("screening_flops", C.c_double), ("newton_schulz_ms", C.c_double),
-                ("gradient_ms", C.c_double), ("total_ms", C.c_double)]
+                ("gradient_ms", C.c_double), ("total_ms", C.c_double), ("tc_launches", C.c_int),
+                ("tc_ms", C.c_double), ("tc_flops", C.c_double), ("correction_ms", C.c_double)]
 
 
 class MBDError(RuntimeError):
@@ -72,13 +73,15 @@ def load(path: str | None = None):
     L.mbd_evaluate_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mbd_backward_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mbd_get_scs_detail.argtypes = [vp, _P, _P, _P, _P]
-    L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P]
+    L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P, _P]
     L.mbd_get_exception.argtypes = [vp, C.POINTER(C.c_int), C.c_char_p, C.c_char_p, sz]
     L.mbd_set_profiling.argtypes = [vp, i]
     L.mbd_get_profile.argtypes = [vp, C.POINTER(mbd_profile)]
     ll = C.c_longlong
     L.mbdk_gemm_f64.argtypes = [vp, i, i, i, i, i, d, vp, ll, vp, ll, d, vp, ll, vp, ll]
     L.mbdk_cholesky_f64.argtypes = [vp, vp, ll, i, vp, vp]
+    f = C.c_float
+    L.mbdk_gemm_tc.argtypes = [vp, i, i, i, i, i, f, vp, vp, ll, vp, vp, ll, f, vp, vp, vp, vp, vp, ll, vp]
     L.mbdk_chol_solve3_f64.argtypes = [vp, vp, ll, i, vp, vp]
     L.mbdk_cholesky_solve3_f64_noalloc.argtypes = [vp, vp, ll, i, vp, vp]
     for name in EXPORTS:
@@ -106,11 +109,12 @@ class MBD:
     """One library context on one CUDA device (mirrors mbd_calc_t of the paper's API)."""
 
     def __init__(self, device: int = 0, n_freq: int = 15, beta: float = 0.83, a: float = 6.0,
-                 ns_tol: float = 1e-8, ns_max_iter: int = 100):
+                 ns_tol: float = 1e-8, ns_max_iter: int = 100, precision: int = MBD_PREC_FP64):
         self.lib = load()
         opt = mbd_options()
         self.lib.mbd_default_options(C.byref(opt))
         opt.n_freq, opt.beta, opt.a, opt.ns_tol, opt.ns_max_iter = n_freq, beta, a, ns_tol, ns_max_iter
+        opt.precision = precision
         h = C.c_void_p()
         rc = self.lib.mbd_create(C.byref(h), device, C.byref(opt))
         if rc:
@@ -213,9 +217,10 @@ class MBD:
         return {k: getattr(p, k) for k, _ in mbd_profile._fields_}
 
     def stats(self):
-        it, sc, res = C.c_int(), C.c_double(), C.c_double()
-        self._check(self.lib.mbd_get_stats(self.h, C.byref(it), C.byref(sc), C.byref(res)))
-        return dict(ns_iterations=it.value, ns_scale=sc.value, ns_residual=res.value)
+        it, sc, res, cr = C.c_int(), C.c_double(), C.c_double(), C.c_double()
+        self._check(self.lib.mbd_get_stats(self.h, C.byref(it), C.byref(sc), C.byref(res), C.byref(cr)))
+        return dict(ns_iterations=it.value, ns_scale=sc.value, ns_residual=res.value,
+                    correction_residual=cr.value)
 
 
 def _stream(t, stream):
@@ -235,6 +240,19 @@ def mbdk_gemm_f64(A, B, C_out, alpha=1.0, beta=0.0, D=None, mode=0, trans_b=True
                          _tptr(C_out), C_out.stride(0))
     if rc:
         raise MBDError(rc, "mbdk_gemm_f64", "launch rejected")
+
+
+def mbdk_gemm_tc(kind, A0, B0, C_out=None, A1=None, B1=None, alpha=1.0, beta=0.0, D=None, C_hi=None,
+                 C_lo=None, CT=None, mode=0, err=None, stream=None):
+    """Tensor-core GEMM C = alpha sum A_p B_p^T + beta D (see mbdk_gemm_tc in the header);
+    torch CUDA tensors; returns the C return code."""
+    L = load()
+    M, K = A0.shape
+    N = B0.shape[0]
+    ref = C_out if C_out is not None else (CT if CT is not None else C_hi)
+    return L.mbdk_gemm_tc(_stream(A0, stream), kind, mode, M, N, K, alpha, _tptr(A0), _tptr(A1), A0.stride(0),
+                          _tptr(B0), _tptr(B1), B0.stride(0), beta, _tptr(D), _tptr(C_out), _tptr(C_hi),
+                          _tptr(C_lo), _tptr(CT), ref.stride(0), _tptr(err))
 
 
 def mbdk_cholesky_f64(A, dinv, status, stream=None):

@@ -1,5 +1,6 @@
 // Internal declarations of the sm_103a kernels of libmbdgb.  Not part of the C ABI.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -18,7 +19,46 @@ enum : int {
     ST_INPUT = 1,          // NaN input or coincident atoms
     ST_SCS_NOT_PD = 2,     // non-positive pivot in the SCS Cholesky factorisation
     ST_NEG_ALPHA = 4,      // screened alpha0 or C6 not positive
+    ST_TC_TIMEOUT = 8,     // a tensor-core GEMM wait ran out of its budget
 };
+
+// ---- tcgen05 GEMM (k_tc.cu) ------------------------------------------------------
+// C = alpha sum_p A_p B_p^T + beta D on 128x128 tiles.  kind 0: TF32, operands FP32
+// (A0, B0); kind 1: BF16x3, operands bf16 hi/lo pairs (A0 = A_hi, A1 = A_lo, same for
+// B); kind 2: TF32x3, operands TF32-rounded hi and FP32 remainder lo (32-bit each).  A is M x K, B is N x K (row pitch lda, ldb elements); C, D, transposes share ld.
+// mode 0: all tiles; mode 2: upper tiles mirrored (symmetric products).  Optional
+// outputs: C (FP32), Ch/Cl (bf16 hi/lo), CT/CTh/CTl (transposes, mode 0 only), and
+// resid += sum over the leading nvalid x nvalid block of (delta - C)^2 (mode 0 only).
+// Timeouts set ST_TC_TIMEOUT in *err.
+struct TcOperands {
+    const void *A0, *A1, *B0, *B1;
+    long long lda, ldb;
+};
+struct TcArgs {
+    int M, N, K;
+    float alpha, beta;
+    const float *D;
+    long long ld;
+    float *C;
+    void *Ch, *Cl;       // split outputs: bf16 (kind 1) or 32-bit (kind 2)
+    float *CT;
+    void *CTh, *CTl;
+    double *resid;
+    long long nvalid;
+    int mode;
+    int *err;
+};
+cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_t s);
+// Mixed-precision helpers: Y = scale Q (FP32 and, if Yh, bf16 hi/lo) and Z = I;
+// Z = a I + b P; Zd = scale Zf in FP64; and the variational energy
+// E = (1/4)(3 Tr V - sum V o W) - 3/2 sum omega (work: 608 doubles).
+void mixed_init(int kind, const double *Q, long long ld, double scale, float *Yf, void *Yh, void *Yl, float *Zf,
+                void *Zh, void *Zl, cudaStream_t s);
+void mixed_axpby_identity(int kind, const float *P, long long ld, float a, float b, float *Zf, void *Zh, void *Zl,
+                          cudaStream_t s);
+void to_f64(const float *Zf, long long ld, double scale, double *Zd, cudaStream_t s);
+void energy_variational(const double *V, const double *W, long long ld, int n, const double *ombar, int N,
+                        double *work, double *out, cudaStream_t s);
 
 // ---- dense FP64 (k_dense.cu) ----------------------------------------------------
 // C[b] = alpha * A[b] op(B[b]) + beta * D[b] on 64x64 tiles, FP64 DMMA (mma.sync m8n8k4).

@@ -1,0 +1,575 @@
+// 5th-generation tensor-core GEMM (tcgen05, sm_103a) for the mixed-precision
+// Newton-Schulz iteration behind Eqs. (diagonalization), (mbd-energy):
+//
+//   C = alpha * sum_p A_p B_p^T + beta * D      (FP32 accumulate in tensor memory)
+//
+// with K-major operands (rows of A and of B run along K).  Two operand kinds:
+//   TF32   one product, operands stored as FP32 (kind::tf32 uses their top 19 bits);
+//   BF16x3 three products A_hi B_hi + A_hi B_lo + A_lo B_hi, operands stored as bf16
+//          hi/lo pairs (X = X_hi + X_lo), about 16 significant bits per product.
+// One CTA computes one 128x128 output tile.  Operand tiles of 128 rows x 128 bytes
+// are staged in shared memory by TMA (128-byte swizzle) through an mbarrier ring;
+// thread 0 issues the TMA loads, thread 32 issues tcgen05.mma into a 128-column TMEM
+// accumulator, and all four warps read it back (tcgen05.ld 32x32b) for the epilogue:
+// alpha/beta, FP32 and/or bf16 hi/lo outputs, optional transposed copies, optional
+// mirrored write of upper tiles (symmetric products), optional sum of (I - C)^2.
+//
+// Every wait is bounded (clock64 budget); on a timeout the kernel raises the error
+// flag, stops issuing work, waits (bounded) for its own TMA copies and MMAs, frees its
+// tensor memory and returns.
+#include <algorithm>
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+
+namespace mbdgb {
+namespace {
+
+constexpr int TM = 128, TN = 128;
+constexpr int KB = 128;                         // bytes of K per stage per row (one swizzle atom)
+constexpr int TILE_BYTES = TM * KB;             // 16 KB
+constexpr long long kSpinCycles = 4000000000LL; // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false (and the error flag raised) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err) {
+    const long long t0 = clock64();
+    while (!mbar_try(b, parity)) {
+        if (clock64() - t0 > kSpinCycles) {
+            atomicOr(err, ST_TC_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            su32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset
+    d |= static_cast<uint64_t>(1) << 46;            // descriptor version
+    d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor: FP32 accumulator, A/B format fmt (1 = bf16, 2 = tf32), both
+// K-major, N = TN, M = TM.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(TN >> 3) << 17) |
+           (static_cast<uint32_t>(TM >> 4) << 24);
+}
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    if (TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(idesc(2)), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(idesc(1)), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// Element j of a packed split row (bf16 pairs for KIND 1, 32-bit words for KIND 2).
+template <int KIND>
+__device__ __forceinline__ void store_part(void *base, long long off, const uint32_t *w, int j) {
+    if (KIND == 2)
+        static_cast<uint32_t *>(base)[off] = w[j];
+    else
+        static_cast<unsigned short *>(base)[off] = static_cast<unsigned short>(w[j >> 1] >> (16 * (j & 1)));
+}
+
+__device__ __forceinline__ void tri_index(int bid, int &r, int &c) {
+    int x = static_cast<int>((sqrt(8.0 * bid + 1.0) - 1.0) * 0.5);
+    while ((x + 1) * (x + 2) / 2 <= bid) ++x;
+    while (x * (x + 1) / 2 > bid) --x;
+    r = x;
+    c = bid - x * (x + 1) / 2;
+}
+
+template <int KIND>   // 0: TF32 single product; 1: BF16x3; 2: TF32x3
+struct TcCfg {
+    static constexpr int PAIRS = KIND == 0 ? 1 : 3;
+    static constexpr int TILES = KIND == 0 ? 2 : 4;
+    static constexpr int STAGES = KIND == 0 ? 4 : 3;
+    static constexpr int STAGE_BYTES = TILES * TILE_BYTES;
+    static constexpr int ELEM = KIND == 1 ? 2 : 4;
+    static constexpr bool TF32 = KIND != 1;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+              const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs g,
+              int tiles_n) {
+    using Cfg = TcCfg<KIND>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+    uint64_t *empty = full + Cfg::STAGES;
+    uint64_t *done = empty + Cfg::STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    int tm, tn;
+    if (g.mode == 0) {
+        tm = blockIdx.x / tiles_n;
+        tn = blockIdx.x % tiles_n;
+    } else {
+        int r, c;
+        tri_index(blockIdx.x, r, c);
+        tm = c;
+        tn = r;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
+                     "r"(TN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nk = static_cast<int>((static_cast<long long>(g.K) * Cfg::ELEM) / KB);
+    constexpr int KELEM = KB / Cfg::ELEM;   // elements of K per stage
+
+    if (threadIdx.x == 0) {
+        // ---- TMA producer ----
+        int issued = 0;
+        for (int kt = 0; kt < nk && !*abort_flag; ++kt) {
+            const int s = kt % Cfg::STAGES;
+            const uint32_t ph = (kt / Cfg::STAGES) & 1;
+            if (kt >= Cfg::STAGES && !mbar_wait(&empty[s], ph ^ 1, g.err)) {
+                *abort_flag = 1;
+                break;
+            }
+            uint8_t *st = smem + s * Cfg::STAGE_BYTES;
+            mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+            const int kx = kt * KELEM;
+            tma_load_2d(st, &mA0, kx, tm * TM, &full[s]);
+            tma_load_2d(st + TILE_BYTES, &mB0, kx, tn * TN, &full[s]);
+            if (Cfg::TILES == 4) {
+                tma_load_2d(st + 2 * TILE_BYTES, &mA1, kx, tm * TM, &full[s]);
+                tma_load_2d(st + 3 * TILE_BYTES, &mB1, kx, tn * TN, &full[s]);
+            }
+            issued = kt + 1;
+        }
+        if (*abort_flag) {   // let this CTA's copies land before shared memory is released
+            for (int kt = (issued > Cfg::STAGES ? issued - Cfg::STAGES : 0); kt < issued; ++kt)
+                mbar_wait(&full[kt % Cfg::STAGES], (kt / Cfg::STAGES) & 1, g.err);
+        }
+    } else if (threadIdx.x == 32) {
+        // ---- MMA issuer ----
+        for (int kt = 0; kt < nk && !*abort_flag; ++kt) {
+            const int s = kt % Cfg::STAGES;
+            if (!mbar_wait(&full[s], (kt / Cfg::STAGES) & 1, g.err)) {
+                *abort_flag = 1;
+                break;
+            }
+            fence_after();
+            const uint32_t base = su32(smem + s * Cfg::STAGE_BYTES);
+#pragma unroll
+            for (int k = 0; k < KB / 32; ++k) {   // 32 bytes of K per instruction
+                const uint64_t a0 = sdesc(base + k * 32), b0 = sdesc(base + TILE_BYTES + k * 32);
+                mma<Cfg::TF32>(tmem, a0, b0, (kt | k) != 0);
+                if (Cfg::PAIRS == 3) {
+                    const uint64_t a1 = sdesc(base + 2 * TILE_BYTES + k * 32);
+                    const uint64_t b1 = sdesc(base + 3 * TILE_BYTES + k * 32);
+                    mma<Cfg::TF32>(tmem, a0, b1, 1u);
+                    mma<Cfg::TF32>(tmem, a1, b0, 1u);
+                }
+            }
+            mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
+        }
+        mma_commit(done);            // arrives when every MMA issued above has completed
+    }
+    __syncwarp();
+    // ---- epilogue: TMEM -> registers -> global ----
+    bool ok = mbar_wait(done, 0, g.err);
+    ok = __all_sync(0xffffffffu, ok && !*abort_flag);   // tcgen05.ld below is warp-collective
+    fence_after();
+    if (ok) {
+        const int row = warp * 32 + lane;
+        const long long m = static_cast<long long>(tm) * TM + row;
+        const bool mirror = (g.mode == 2) && (tm != tn);
+        double rs = 0.0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, r);
+            const long long n0 = static_cast<long long>(tn) * TN + c0;
+            float v[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = g.alpha * __uint_as_float(r[j]);
+            if (g.beta != 0.f) {
+                const float4 *dp = reinterpret_cast<const float4 *>(g.D + m * g.ld + n0);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 d = dp[q];
+                    v[4 * q] += g.beta * d.x;
+                    v[4 * q + 1] += g.beta * d.y;
+                    v[4 * q + 2] += g.beta * d.z;
+                    v[4 * q + 3] += g.beta * d.w;
+                }
+            }
+            if (g.resid && m < g.nvalid) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (n0 + j < g.nvalid) {
+                        const double e = (m == n0 + j ? 1.0 : 0.0) - static_cast<double>(v[j]);
+                        rs += e * e;
+                    }
+            }
+            // hi/lo split of the result for the next product's operands: bf16 pairs packed
+            // two per word (BF16x3), or TF32-rounded hi and FP32 remainder (TF32x3).
+            uint32_t hw[KIND == 2 ? 32 : 16], lw[KIND == 2 ? 32 : 16];
+            if (g.Ch) {
+                if (KIND == 2) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        uint32_t h;
+                        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v[j]));
+                        hw[j] = h;
+                        lw[j] = __float_as_uint(v[j] - __uint_as_float(h));
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+                        hw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
+                                (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+                        lw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
+                                (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+                    }
+                }
+            }
+            // Symmetric products (mode 2): upper tiles are mirrored into the lower half;
+            // diagonal tiles keep their upper triangle and mirror it, so the result is
+            // exactly symmetric whatever order the tensor cores summed in.
+            const bool diag = (g.mode == 2) && (tm == tn);
+            // row-major outputs
+            if (!diag) {
+                if (g.C) {
+                    float4 *cp = reinterpret_cast<float4 *>(g.C + m * g.ld + n0);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+                if (g.Ch) {
+                    constexpr int NV = KIND == 2 ? 8 : 4;   // uint4 vectors per 32 elements
+                    uint4 *hp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Ch) + (m * g.ld + n0) * Cfg::ELEM);
+                    uint4 *lp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Cl) + (m * g.ld + n0) * Cfg::ELEM);
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        hp[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                        lp[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (n0 + j < m) continue;
+                    const long long off = m * g.ld + n0 + j;
+                    if (g.C) g.C[off] = v[j];
+                    if (g.Ch) {
+                        store_part<KIND>(g.Ch, off, hw, j);
+                        store_part<KIND>(g.Cl, off, lw, j);
+                    }
+                }
+            }
+            // transposed copies (coalesced across the warp: consecutive rows m).  For a
+            // mirrored tile of a symmetric product the transpose goes into C itself.
+            const bool into_c = mirror || diag;
+            float *Tf = into_c ? g.C : g.CT;
+            void *Th = into_c ? g.Ch : g.CTh, *Tl = into_c ? g.Cl : g.CTl;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (diag && n0 + j <= m) continue;
+                const long long off = (n0 + j) * g.ld + m;
+                if (Tf) Tf[off] = v[j];
+                if (Th) {
+                    store_part<KIND>(Th, off, hw, j);
+                    store_part<KIND>(Tl, off, lw, j);
+                }
+            }
+        }
+        if (g.resid) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+            if (lane == 0 && rs != 0.0) atomicAdd(g.resid, rs);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TN));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a row-major rows x cols matrix (row pitch ld elements), box of 128 rows
+// by 128 bytes, 128-byte swizzle.
+bool make_map(CUtensorMap *m, const void *base, int kind, long long rows, long long cols, long long ld) {
+    auto fn = encode_fn();
+    if (!fn || !base) return false;
+    const int elem = kind == 1 ? 2 : 4;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * elem)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(KB / elem), static_cast<cuuint32_t>(TM)};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+              const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int KIND>
+cudaError_t launch_tc(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
+    using Cfg = TcCfg<KIND>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap a0, a1, b0, b1;
+    const long long lda = op.lda, ldb = op.ldb;
+    if (!make_map(&a0, op.A0, KIND, g.M, g.K, lda) || !make_map(&b0, op.B0, KIND, g.N, g.K, ldb))
+        return cudaErrorInvalidValue;
+    if (KIND != 0) {
+        if (!make_map(&a1, op.A1, KIND, g.M, g.K, lda) || !make_map(&b1, op.B1, KIND, g.N, g.K, ldb))
+            return cudaErrorInvalidValue;
+    } else {
+        a1 = a0;
+        b1 = b0;
+    }
+    const int tmt = g.M / TM, tnt = g.N / TN;
+    const int grid = g.mode == 0 ? tmt * tnt : tmt * (tmt + 1) / 2;
+    count_launches(1);
+    k_tc_gemm<KIND><<<grid, 128, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.M % TM || g.N % TN || g.K % 64 || (g.mode != 0 && g.mode != 2) ||
+        (g.mode == 2 && (g.M != g.N || g.CT || g.CTh || g.resid)) || ((g.CT || g.CTh) && g.M != g.N) ||
+        g.ld % 8 || op.lda % 8 || op.ldb % 8 ||
+        !g.err || (g.beta != 0.f && !g.D) || (g.Ch && !g.Cl) || (g.CTh && !g.CTl) || kind < 0 || kind > 2 ||
+        (kind != 0 && (!op.A1 || !op.B1)) || (kind == 0 && (g.Ch || g.CTh)))
+        return cudaErrorInvalidValue;
+    if (kind == 0) return launch_tc<0>(op, g, s);
+    if (kind == 1) return launch_tc<1>(op, g, s);
+    return launch_tc<2>(op, g, s);
+}
+
+}  // namespace mbdgb
+
+// ---- conversions and the variational energy of the mixed-precision path ----------
+namespace mbdgb {
+namespace {
+
+// Split v into the hi/lo operand pair of a split mode: kind 1 bf16 (hi, lo), kind 2
+// TF32-rounded hi and FP32 remainder; element e of the arrays H, L.
+__device__ __forceinline__ void split_store(int kind, float v, void *H, void *L, long long e) {
+    if (kind == 1) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        static_cast<__nv_bfloat16 *>(H)[e] = h;
+        static_cast<__nv_bfloat16 *>(L)[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    } else {
+        uint32_t h;
+        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v));
+        static_cast<uint32_t *>(H)[e] = h;
+        static_cast<float *>(L)[e] = v - __uint_as_float(h);
+    }
+}
+
+// Y = scale * Q (FP64 -> FP32, plus bf16 hi/lo when Yh is given); Z = I likewise.
+__global__ void k_mixed_init(int kind, const double *Q, long long total, long long ld, double scale, float *Yf,
+                             void *Yh, void *Yl, float *Zf, void *Zh, void *Zl) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float y = static_cast<float>(scale * Q[e]);
+        const float z = (e / ld == e % ld) ? 1.f : 0.f;
+        Yf[e] = y;
+        Zf[e] = z;
+        if (Yh) {
+            split_store(kind, y, Yh, Yl, e);
+            split_store(kind, z, Zh, Zl, e);
+        }
+    }
+}
+
+// Z = a I + b P (first scaled Newton-Schulz step, where P = Y0).
+__global__ void k_mixed_axpby_identity(int kind, const float *P, long long total, long long ld, float a, float b,
+                                       float *Zf, void *Zh, void *Zl) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float z = ((e / ld == e % ld) ? a : 0.f) + b * P[e];
+        Zf[e] = z;
+        if (Zh) split_store(kind, z, Zh, Zl, e);
+    }
+}
+
+// Zd = scale * Zf (FP32 -> FP64).
+__global__ void k_to_f64(const float *Zf, long long total, double scale, double *Zd) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        Zd[e] = scale * static_cast<double>(Zf[e]);
+}
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Per-block compensated partial sums of Tr V (diagonal of the leading n x n block) and
+// of sum_pq V_pq W_pq; out[2 * block + {0,1}].
+__global__ void __launch_bounds__(256) k_trace_dot_partials(const double *V, const double *W, long long ld, int n,
+                                                            double *out) {
+    double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
+    const long long total = static_cast<long long>(n) * n;
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < total; e += static_cast<long long>(gridDim.x) * 256) {
+        const long long i = e / n, j = e % n;
+        const double v = V[i * ld + j];
+        double t, r;
+        two_sum(s1, v * W[i * ld + j], t, r);
+        s1 = t; c1 += r;
+        if (i == j) {
+            two_sum(s0, v, t, r);
+            s0 = t; c0 += r;
+        }
+    }
+    __shared__ double sh[4][256];
+    sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = c0; sh[2][threadIdx.x] = s1; sh[3][threadIdx.x] = c1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, ac = 0.0, b = 0.0, bc = 0.0;
+        for (int k = 0; k < 256; ++k) {
+            double t, r;
+            two_sum(a, sh[0][k], t, r); a = t; ac += r + sh[1][k];
+            two_sum(b, sh[2][k], t, r); b = t; bc += r + sh[3][k];
+        }
+        out[2 * blockIdx.x] = a + ac;
+        out[2 * blockIdx.x + 1] = b + bc;
+    }
+}
+
+// E = 1/2 * (1/2)(3 Tr V - sum V o W) - 3/2 sum omega_bar, from the partials (one CTA).
+__global__ void k_energy_variational(const double *part, int nblocks, const double *ombar, int N, double *out) {
+    if (threadIdx.x != 0) return;
+    double a = 0.0, ac = 0.0, b = 0.0, bc = 0.0, w = 0.0, wc = 0.0;
+    for (int k = 0; k < nblocks; ++k) {
+        double t, r;
+        two_sum(a, part[2 * k], t, r); a = t; ac += r;
+        two_sum(b, part[2 * k + 1], t, r); b = t; bc += r;
+    }
+    for (int i = 0; i < N; ++i) {
+        double t, r;
+        two_sum(w, ombar[i], t, r); w = t; wc += r;
+    }
+    const double trv = a + ac, vw = b + bc, sw = w + wc;
+    out[0] = 0.25 * (3.0 * trv - vw) - 1.5 * sw;
+}
+
+inline int grid_for(long long total) { return static_cast<int>(std::min<long long>((total + 255) / 256, 152 * 16)); }
+
+}  // namespace
+
+void mixed_init(int kind, const double *Q, long long ld, double scale, float *Yf, void *Yh, void *Yl, float *Zf,
+                void *Zh, void *Zl, cudaStream_t s) {
+    count_launches(1);
+    k_mixed_init<<<grid_for(ld * ld), 256, 0, s>>>(kind, Q, ld * ld, ld, scale, Yf, Yh, Yl, Zf, Zh, Zl);
+}
+
+void mixed_axpby_identity(int kind, const float *P, long long ld, float a, float b, float *Zf, void *Zh, void *Zl,
+                          cudaStream_t s) {
+    count_launches(1);
+    k_mixed_axpby_identity<<<grid_for(ld * ld), 256, 0, s>>>(kind, P, ld * ld, ld, a, b, Zf, Zh, Zl);
+}
+
+void to_f64(const float *Zf, long long ld, double scale, double *Zd, cudaStream_t s) {
+    count_launches(1);
+    k_to_f64<<<grid_for(ld * ld), 256, 0, s>>>(Zf, ld * ld, scale, Zd);
+}
+
+void energy_variational(const double *V, const double *W, long long ld, int n, const double *ombar, int N,
+                        double *work, double *out, cudaStream_t s) {
+    const int nb = 304;   // work: 2 * nb doubles
+    count_launches(2);
+    k_trace_dot_partials<<<nb, 256, 0, s>>>(V, W, ld, n, work);
+    k_energy_variational<<<1, 32, 0, s>>>(work, nb, ombar, N, out);
+}
+
+}  // namespace mbdgb

@@ -124,6 +124,10 @@ struct mbd_ctx {
     double *da0, *dom, *drv, *dalu, *dsigu, *dabar, *dabar0, *dc6bar, *dombar, *drbar, *du, *dwu;
     double *dM, *ddinv, *dX, *dV;
     double *dQ, *dZ, *dP, *dY2, *dZ2;
+    // mixed-precision Newton-Schulz buffers (ld x ld each)
+    float *fY = nullptr, *fZ = nullptr, *fY2 = nullptr, *fZ2 = nullptr, *fP = nullptr, *fPT = nullptr;
+    void *hY[2] = {}, *hZ[2] = {}, *hY2[2] = {}, *hZ2[2] = {}, *hP[2] = {}, *hPT[2] = {};   // split operands
+    double corr_resid = 0.0;   // |Zd Q Zd - I|_F of the mixed modes' correction
     double *dh, *dgomb, *dgab0, *dgrb, *dgR, *dga0, *dgom, *dgrv, *dgp;
     double *dscal;   // [0] energy, [1] Gershgorin, [2] residual
     int *dstatus;
@@ -208,7 +212,7 @@ int allocate(mbd_ctx *ctx) {
         {&ctx->drbar, N}, {&ctx->du, nf1}, {&ctx->dwu, nf1},
         {&ctx->ddinv, nf1 * nb * 4096}, {&ctx->dX, nf1 * ld * 3}, {&ctx->dV, nf1 * ld * 3},
         {&ctx->dh, nf1 * N}, {&ctx->dgomb, N}, {&ctx->dgab0, N}, {&ctx->dgrb, N}, {&ctx->dgR, 3 * N},
-        {&ctx->dga0, N}, {&ctx->dgom, N}, {&ctx->dgrv, N}, {&ctx->dgp, 4 * N}, {&ctx->dscal, 8 + 2 * 64},
+        {&ctx->dga0, N}, {&ctx->dgom, N}, {&ctx->dgrv, N}, {&ctx->dgp, 4 * N}, {&ctx->dscal, 8 + 2 * 64 + 1024},
     };
     size_t bytes = 0;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -217,6 +221,11 @@ int allocate(mbd_ctx *ctx) {
     const size_t small = bytes;
     bytes += nf1 * mat;          // screening matrices / factors
     bytes += 5 * mat;            // Q (= Y), Z, P, Y', Z'
+    const size_t mat32 = mat / 2, mat16 = mat / 4;
+    const int prec = ctx->opt.precision;
+    const size_t split_mat = prec == MBD_PREC_BF16X3 ? mat16 : (prec == MBD_PREC_TF32X3 ? mat32 : 0);
+    if (prec != MBD_PREC_FP64) bytes += 6 * mat32;
+    bytes += 12 * split_mat;
     release(ctx);
     cudaError_t e = cudaMalloc(&ctx->slab, bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, "mbd_set_geometry", e);
@@ -234,6 +243,21 @@ int allocate(mbd_ctx *ctx) {
     for (auto m : mats) {
         *m = reinterpret_cast<double *>(p);
         p += mat;
+    }
+    if (prec != MBD_PREC_FP64) {
+        float **f32[6] = {&ctx->fY, &ctx->fZ, &ctx->fY2, &ctx->fZ2, &ctx->fP, &ctx->fPT};
+        for (auto m : f32) {
+            *m = reinterpret_cast<float *>(p);
+            p += mat32;
+        }
+    }
+    if (split_mat) {
+        void **parts[6] = {ctx->hY, ctx->hZ, ctx->hY2, ctx->hZ2, ctx->hP, ctx->hPT};
+        for (auto m : parts)
+            for (int k = 0; k < 2; ++k) {
+                m[k] = p;
+                p += split_mat;
+            }
     }
     // Untouched parts of the factor buffers (strict upper triangles) are read by no
     // kernel; clearing them once keeps them finite.
@@ -290,6 +314,129 @@ int read_status(mbd_ctx *ctx, cudaStream_t s, const char *origin) {
     return MBD_OK;
 }
 
+
+// Operand set of one matrix in the mixed modes: FP32 values and, for BF16x3, hi/lo.
+struct MixMat {
+    float *f;
+    void *h, *l;
+    const void *op0(bool split) const { return split ? static_cast<const void *>(h) : static_cast<const void *>(f); }
+    const void *op1(bool split) const { return split ? static_cast<const void *>(l) : static_cast<const void *>(f); }
+};
+
+// Mixed-precision coupled Newton-Schulz (same scaled steps as the FP64 loop) on the
+// tensor cores, stopped at the precision floor, then the FP64 correction:
+// Zd = Z/sqrt(s) ~ Q^{-1/2}, V = Q Zd, W = Zd V, E = (3 Tr V - sum V o W)/4 - 3/2 sum w.
+int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, double ubound, double *energy_out,
+                        std::vector<Span> &spans, cudaEvent_t &e_corr) {
+    const long long ld = ctx->ld;
+    const int n = ctx->n, N = ctx->N, M = static_cast<int>(ld);
+    const int kind = ctx->opt.precision == MBD_PREC_TF32 ? 0 : (ctx->opt.precision == MBD_PREC_BF16X3 ? 1 : 2);
+    const bool split = kind != 0;
+    const double nd = static_cast<double>(n);
+    const double flops_full = 2.0 * nd * nd * nd, flops_sym = nd * nd * (nd + 1.0);
+    MixMat Y{ctx->fY, ctx->hY[0], ctx->hY[1]}, Z{ctx->fZ, ctx->hZ[0], ctx->hZ[1]};
+    MixMat Y2{ctx->fY2, ctx->hY2[0], ctx->hY2[1]}, Z2{ctx->fZ2, ctx->hZ2[0], ctx->hZ2[1]};
+    MixMat P{ctx->fP, ctx->hP[0], ctx->hP[1]}, PT{ctx->fPT, ctx->hPT[0], ctx->hPT[1]};
+    mixed_init(kind, ctx->dQ, ld, 1.0 / sc, Y.f, split ? Y.h : nullptr, Y.l, Z.f, Z.h, Z.l, s);
+    auto tc = [&](const TcOperands &op, const TcArgs &g, double flops) -> int {
+        Span sp;
+        sp.flops = flops;
+        mark(ctx, s, sp.a);
+        const cudaError_t e = tc_gemm(kind, op, g, s);
+        mark(ctx, s, sp.b);
+        if (ctx->profiling) spans.push_back(sp);
+        return e == cudaSuccess ? MBD_OK : cuda_fail(ctx, "newton_schulz_tc", e);
+    };
+    double *resid_dev = ctx->dscal + 2;
+    double resid = 0.0, prev = 1e300;
+    bool floor_reached = false;
+    int it = 0;
+    for (; it < ctx->opt.ns_max_iter; ++it) {
+        MixMat Pk = Y, PTk = Y;   // P_0 = Y_0 (symmetric)
+        if (it > 0) {
+            MBD_CUDA(cudaMemsetAsync(resid_dev, 0, sizeof(double), s), "newton_schulz_tc");
+            TcOperands op{Z.op0(split), Z.op1(split), Y.op0(split), Y.op1(split), ld, ld};
+            TcArgs g{M, M, M, 1.f, 0.f, nullptr, ld, split ? nullptr : P.f, split ? P.h : nullptr,
+                     split ? P.l : nullptr, split ? nullptr : PT.f, split ? PT.h : nullptr, split ? PT.l : nullptr,
+                     resid_dev, n, 0, ctx->dstatus};
+            int rc = tc(op, g, flops_full);   // P = Z Y (and its transpose), resid = |I - P|_F^2
+            if (rc) return rc;
+            Pk = P;
+            PTk = PT;
+            double r2 = 0.0;
+            MBD_CUDA(cudaMemcpyAsync(&r2, resid_dev, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz_tc");
+            MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz_tc");
+            resid = std::sqrt(r2);
+            if (!std::isfinite(resid) || resid > 2.0 * std::sqrt(nd) + 1.0) {
+                ctx->ns_iter = it;
+                ctx->ns_resid = resid;
+                return fail(ctx, MBD_ERR_NEG_EIGENVALUE, "newton_schulz_tc",
+                            "Q has a non-positive eigenvalue (polarization catastrophe)");
+            }
+        }
+        // The tensor-core phase ends at its precision floor: below ns_tol, or when a step
+        // taken from inside the quadratic basin (|I - P| < 0.5, where an exact step gives at
+        // most 3/4 |I - P|^2) fails to halve the residual.
+        const bool last = it > 0 && (resid < ctx->opt.ns_tol || (prev < 0.5 && resid > 0.5 * prev));
+        double al = 1.0;
+        if (!last && lbound < 0.999) al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
+        const double c1 = 1.5 * al, c3 = -0.5 * al * al * al;
+        lbound = std::min(1.0, 0.5 * al * lbound * (3.0 - al * al * lbound * lbound));
+        ubound = 1.0;
+        {   // Y' = c1 Y + c3 Y P = NT(Y, P^T): symmetric
+            TcOperands op{Y.op0(split), Y.op1(split), PTk.op0(split), PTk.op1(split), ld, ld};
+            TcArgs g{M, M, M, static_cast<float>(c3), static_cast<float>(c1), Y.f, ld, Y2.f,
+                     split ? Y2.h : nullptr, split ? Y2.l : nullptr, nullptr, nullptr, nullptr, nullptr, 0, 2,
+                     ctx->dstatus};
+            int rc = tc(op, g, flops_sym);
+            if (rc) return rc;
+        }
+        if (it == 0) {
+            mixed_axpby_identity(kind, Y.f, ld, static_cast<float>(c1), static_cast<float>(c3), Z2.f,
+                                 split ? Z2.h : nullptr, Z2.l, s);
+        } else {   // Z' = c1 Z + c3 P Z = NT(P, Z): symmetric
+            TcOperands op{Pk.op0(split), Pk.op1(split), Z.op0(split), Z.op1(split), ld, ld};
+            TcArgs g{M, M, M, static_cast<float>(c3), static_cast<float>(c1), Z.f, ld, Z2.f,
+                     split ? Z2.h : nullptr, split ? Z2.l : nullptr, nullptr, nullptr, nullptr, nullptr, 0, 2,
+                     ctx->dstatus};
+            int rc = tc(op, g, flops_sym);
+            if (rc) return rc;
+        }
+        std::swap(Y, Y2);
+        std::swap(Z, Z2);
+        if (it > 0) prev = resid;
+        if (last) {
+            floor_reached = true;
+            ++it;
+            break;
+        }
+    }
+    ctx->ns_iter = it;
+    ctx->ns_resid = resid;
+    int st = 0;
+    MBD_CUDA(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s), "newton_schulz_tc");
+    MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz_tc");
+    if (st & ST_TC_TIMEOUT) return fail(ctx, MBD_ERR_CUDA, "newton_schulz_tc", "tensor-core GEMM wait timed out");
+    if (!floor_reached) return fail(ctx, MBD_ERR_NOT_CONVERGED, "newton_schulz_tc", "iteration cap reached");
+    // ---- FP64 correction ----
+    mark(ctx, s, e_corr);
+    double *Zd = ctx->dZ, *V = ctx->dP, *W = ctx->dY2;
+    to_f64(Z.f, ld, 1.0 / std::sqrt(sc), Zd, s);
+    GemmArgs gv{ctx->dQ, Zd, nullptr, V, ld, ld, 0, ld, 0, 0, 0, 0, M, M, M, 1, 1.0, 0.0, 0, 1};   // V = Q Zd
+    gemm_f64(gv, s);
+    GemmArgs gw{Zd, V, nullptr, W, ld, ld, 0, ld, 0, 0, 0, 0, M, M, M, 1, 1.0, 0.0, 2, 0};         // W = Zd V
+    gemm_f64(gw, s);
+    energy_variational(V, W, ld, n, ctx->dombar, N, ctx->dscal + 8 + 2 * 64, energy_out, s);
+    frob_dev_identity(W, ld, n, ctx->dscal + 3, s);   // the true accuracy of Zd: |Zd Q Zd - I|_F
+    double c2 = 0.0;
+    MBD_CUDA(cudaMemcpyAsync(&c2, ctx->dscal + 3, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz_tc");
+    MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz_tc");
+    ctx->corr_resid = std::sqrt(c2);
+    ctx->Zlast = Zd;
+    ctx->zscale = 1.0;
+    return MBD_OK;
+}
+
 int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool want_grad) {
     const int N = ctx->N, n = ctx->n, nf1 = ctx->nf1;
     const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;
@@ -299,8 +446,8 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     ctx->ev_used = 0;
     ctx->prof = mbd_profile{};
     const long long launches0 = launch_count();
-    cudaEvent_t e_start = nullptr, e_scs = nullptr, e_ns = nullptr, e_grad = nullptr;
-    std::vector<Span> gemms;
+    cudaEvent_t e_start = nullptr, e_scs = nullptr, e_ns = nullptr, e_grad = nullptr, e_corr = nullptr;
+    std::vector<Span> gemms, tc_spans;
     auto timed_gemm = [&](const GemmArgs &g, double flops) {
         Span sp;
         sp.flops = flops;
@@ -335,25 +482,23 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     rc = read_status(ctx, s, "coupled_oscillator_matrix");
     if (rc) return rc;
     if (!(sc > 0.0) || !std::isfinite(sc)) return fail(ctx, MBD_ERR_INPUT, "newton_schulz", "invalid Q scale");
-    double *Y = ctx->dQ, *Z = ctx->dZ, *P = ctx->dP, *Y2 = ctx->dY2, *Z2 = ctx->dZ2;
-    scale_matrix(Y, ld, 1.0 / sc, s);
-    // Lanczos estimates of the extreme eigenvalues of Y0 = Q/s (workspace: rows of P).
-    // The largest tightens s (Lanczos converges fast at the top of the spectrum; a 5 %
-    // margin keeps Y0's spectrum inside (0, 1]); the smallest gives the lower bound l0
-    // for the scaled iteration below, halved for safety.
+    // Lanczos estimates of the extreme eigenvalues of Q (workspace: rows of P).  The
+    // largest tightens the scale s of Y0 = Q/s (Lanczos converges fast at the top of the
+    // spectrum; a 5 % margin keeps Y0's spectrum inside (0, 1]); the smallest gives the
+    // lower bound for the scaled iteration, halved for safety.
     const int lz_steps = std::min(48, static_cast<int>(ld));
-    lanczos_coefficients(Y, ld, lz_steps, P, ctx->dscal + 8, s);
+    lanczos_coefficients(ctx->dQ, ld, lz_steps, ctx->dP, ctx->dscal + 8, s);
     std::vector<double> lz(2 * lz_steps);
     MBD_CUDA(cudaMemcpyAsync(lz.data(), ctx->dscal + 8, sizeof(double) * 2 * lz_steps, cudaMemcpyDeviceToHost, s),
              "newton_schulz");
     MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
-    double th_min = 0.0, th_max = 1.0;
+    double th_min = 0.0, th_max = sc;
     {
         std::vector<double> da, db;
         for (int j = 0; j < lz_steps; ++j) {
             da.push_back(lz[2 * j]);
             if (j + 1 < lz_steps) db.push_back(lz[2 * j + 1]);
-            if (!(lz[2 * j + 1] > 1e-14)) break;   // invariant subspace reached
+            if (!(lz[2 * j + 1] > 1e-14 * sc)) break;   // invariant subspace reached
         }
         db.resize(da.size() > 0 ? da.size() - 1 : 0);
         if (!da.empty()) tridiag_extremes(da, db, th_min, th_max);
@@ -362,83 +507,88 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     // scale; 1.05 after tightening by the Lanczos estimate (tolerates an underestimate
     // of the largest eigenvalue by up to 16 %).
     double ubound = 1.0;
-    if (std::isfinite(th_max) && th_max > 0.0 && 1.05 * th_max < 1.0) {
-        const double f = 1.05 * th_max;
-        scale_matrix(Y, ld, 1.0 / f, s);
-        sc *= f;
-        th_min /= f;
+    if (std::isfinite(th_max) && th_max > 0.0 && 1.05 * th_max < sc) {
+        sc = 1.05 * th_max;
         ubound = 1.05;
     }
     ctx->ns_scale = sc;
-    double lbound = std::sqrt(std::max(0.5 * th_min, 1e-12));   // lower bound on sqrt(eig(Z Y))
-    set_identity(Z, ld, s);
-    const int M = static_cast<int>(ld);
-    bool converged = false;
-    double resid = 0.0;
-    int it = 0;
-    for (; it < ctx->opt.ns_max_iter; ++it) {
-        // P = Z Y (not symmetric once rounding separates Z and Y; computed in full)
-        const double *Pk = Y;   // Z_0 = I: P_0 = Y_0
-        if (it > 0) {
-            GemmArgs g{Z, Y, nullptr, P, ld, ld, 0, ld, 0, 0, 0, 0, M, M, M, 1, 1.0, 0.0, 0, 0};
-            timed_gemm(g, flops_full);
-            Pk = P;
-        }
-        frob_dev_identity(Pk, ld, n, ctx->dscal + 2, s);
-        double r2 = 0.0;
-        MBD_CUDA(cudaMemcpyAsync(&r2, ctx->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz");
-        MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
-        resid = std::sqrt(r2);
-        if (!std::isfinite(resid) || resid > 2.0 * std::sqrt(static_cast<double>(n)) + 1.0) {
-            // For positive definite Q every eigenvalue of Z Y stays in (0, 1]; leaving that
-            // range means an eigenvalue of Q is not positive.
-            ctx->ns_iter = it;
-            ctx->ns_resid = resid;
-            return fail(ctx, MBD_ERR_NEG_EIGENVALUE, "newton_schulz",
-                        "Q has a non-positive eigenvalue (polarization catastrophe)");
-        }
-        const bool last = resid < ctx->opt.ns_tol;
-        // Scaled step (sign-function form of the coupled iteration): with x^2 the
-        // eigenvalues of P in [l^2, u^2], T = (al/2)(3 I - al^2 P) maps x to
-        // f(x) = (al x/2)(3 - al^2 x^2); al^2 = 3/(u^2 + u l + l^2) gives f(l) = f(u), so
-        // [l, u] goes onto [f(l), 1].  f stays positive for x < sqrt(3)/al, so any l
-        // below the true bound (and any u above it) only costs speed.  al = 1 near
-        // convergence.
-        double al = 1.0;
-        if (!last && lbound < 0.999)
-            al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
-        const double c1 = 1.5 * al, c3 = -0.5 * al * al * al;
-        lbound = std::min(1.0, 0.5 * al * lbound * (3.0 - al * al * lbound * lbound));
-        ubound = 1.0;
-        // Y' = Y T, Z' = T Z: Y' = c1 Y + c3 Y (Z Y) and Z' = c1 Z + c3 (Z Y) Z.  Y Z Y and
-        // Z Y Z are symmetric for any symmetric Y, Z, so only their upper tiles are
-        // computed.  (Using P^T in place of P, i.e. Y Y Z, breaks the coupling and makes
-        // rounding errors grow by about sqrt(cond Q)/2 per step.)
-        GemmArgs gy{Y, Pk, Y, Y2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, c3, c1, 2, 0};
-        timed_gemm(gy, flops_sym);
-        if (it == 0) {
-            axpby_identity(Z2, Pk, ld, c1, c3, s);
-        } else {
-            GemmArgs gz{Pk, Z, Z, Z2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, c3, c1, 2, 0};
-            timed_gemm(gz, flops_sym);
-        }
-        std::swap(Y, Y2);
-        std::swap(Z, Z2);
-        if (last) {
-            converged = true;
-            ++it;
-            break;
-        }
-    }
-    ctx->ns_iter = it;
-    ctx->ns_resid = resid;
-    if (!converged)
-        return fail(ctx, MBD_ERR_NOT_CONVERGED, "newton_schulz", "iteration cap reached");
+    double lbound = std::sqrt(std::max(0.5 * th_min / sc, 1e-12));   // lower bound on sqrt(eig(Z Y))
     const double ss = std::sqrt(sc);
-    energy_trace(Y, ld, n, ctx->dombar, N, ss, out.energy ? out.energy : ctx->dscal, s);
+    double *energy_out = out.energy ? out.energy : ctx->dscal;
+    if (ctx->opt.precision == MBD_PREC_FP64) {
+        double *Y = ctx->dQ, *Z = ctx->dZ, *P = ctx->dP, *Y2 = ctx->dY2, *Z2 = ctx->dZ2;
+        scale_matrix(Y, ld, 1.0 / sc, s);
+        set_identity(Z, ld, s);
+        const int M = static_cast<int>(ld);
+        bool converged = false;
+        double resid = 0.0;
+        int it = 0;
+        for (; it < ctx->opt.ns_max_iter; ++it) {
+            // P = Z Y (not symmetric once rounding separates Z and Y; computed in full)
+            const double *Pk = Y;   // Z_0 = I: P_0 = Y_0
+            if (it > 0) {
+                GemmArgs g{Z, Y, nullptr, P, ld, ld, 0, ld, 0, 0, 0, 0, M, M, M, 1, 1.0, 0.0, 0, 0};
+                timed_gemm(g, flops_full);
+                Pk = P;
+            }
+            frob_dev_identity(Pk, ld, n, ctx->dscal + 2, s);
+            double r2 = 0.0;
+            MBD_CUDA(cudaMemcpyAsync(&r2, ctx->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz");
+            MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
+            resid = std::sqrt(r2);
+            if (!std::isfinite(resid) || resid > 2.0 * std::sqrt(static_cast<double>(n)) + 1.0) {
+                // For positive definite Q every eigenvalue of Z Y stays in (0, 1]; leaving that
+                // range means an eigenvalue of Q is not positive.
+                ctx->ns_iter = it;
+                ctx->ns_resid = resid;
+                return fail(ctx, MBD_ERR_NEG_EIGENVALUE, "newton_schulz",
+                            "Q has a non-positive eigenvalue (polarization catastrophe)");
+            }
+            const bool last = resid < ctx->opt.ns_tol;
+            // Scaled step (sign-function form of the coupled iteration): with x^2 the
+            // eigenvalues of P in [l^2, u^2], T = (al/2)(3 I - al^2 P) maps x to
+            // f(x) = (al x/2)(3 - al^2 x^2); al^2 = 3/(u^2 + u l + l^2) gives f(l) = f(u), so
+            // [l, u] goes onto [f(l), 1].  f stays positive for x < sqrt(3)/al, so any l
+            // below the true bound (and any u above it) only costs speed.  al = 1 near
+            // convergence.
+            double al = 1.0;
+            if (!last && lbound < 0.999)
+                al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
+            const double c1 = 1.5 * al, c3 = -0.5 * al * al * al;
+            lbound = std::min(1.0, 0.5 * al * lbound * (3.0 - al * al * lbound * lbound));
+            ubound = 1.0;
+            // Y' = Y T, Z' = T Z: Y' = c1 Y + c3 Y (Z Y) and Z' = c1 Z + c3 (Z Y) Z.  Y Z Y and
+            // Z Y Z are symmetric for any symmetric Y, Z, so only their upper tiles are
+            // computed.  (Using P^T in place of P, i.e. Y Y Z, breaks the coupling and makes
+            // rounding errors grow by about sqrt(cond Q)/2 per step.)
+            GemmArgs gy{Y, Pk, Y, Y2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, c3, c1, 2, 0};
+            timed_gemm(gy, flops_sym);
+            if (it == 0) {
+                axpby_identity(Z2, Pk, ld, c1, c3, s);
+            } else {
+                GemmArgs gz{Pk, Z, Z, Z2, ld, ld, ld, ld, 0, 0, 0, 0, M, M, M, 1, c3, c1, 2, 0};
+                timed_gemm(gz, flops_sym);
+            }
+            std::swap(Y, Y2);
+            std::swap(Z, Z2);
+            if (last) {
+                converged = true;
+                ++it;
+                break;
+            }
+        }
+        ctx->ns_iter = it;
+        ctx->ns_resid = resid;
+        if (!converged)
+            return fail(ctx, MBD_ERR_NOT_CONVERGED, "newton_schulz", "iteration cap reached");
+        energy_trace(Y, ld, n, ctx->dombar, N, ss, energy_out, s);
+        ctx->Zlast = Z;
+        ctx->zscale = 1.0 / ss;
+    } else {
+        rc = newton_schulz_mixed(ctx, s, sc, lbound, ubound, energy_out, tc_spans, e_corr);
+        if (rc) return rc;
+    }
     mark(ctx, s, e_ns);
-    ctx->Zlast = Z;
-    ctx->zscale = 1.0 / ss;
     // ---- gradients (Sec. 2.4) ----
     if (want_grad) backward_passes(ctx, s, b, nullptr, out.grad_coords, out.grad_params);
     if (out.alpha_scs)
@@ -455,6 +605,12 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
             p.gemm_ms += span_ms(sp.a, sp.b);
             p.gemm_flops += sp.flops;
         }
+        p.tc_launches = static_cast<int>(tc_spans.size());
+        for (const Span &sp : tc_spans) {
+            p.tc_ms += span_ms(sp.a, sp.b);
+            p.tc_flops += sp.flops;
+        }
+        if (e_corr) p.correction_ms = span_ms(e_corr, e_ns);
         p.screening_ms = span_ms(e_start, e_scs);
         p.screening_flops = nf1 * nd * nd * nd / 3.0;
         p.newton_schulz_ms = span_ms(e_scs, e_ns);
@@ -487,7 +643,7 @@ int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt) {
     mbd_options o;
     if (opt) o = *opt; else mbd_default_options(&o);
     if (o.n_freq < 1 || o.n_freq + 1 > kMaxFreq || !(o.beta > 0) || !(o.a > 0) || o.ns_max_iter < 1 ||
-        !(o.ns_tol > 0) || o.precision != MBD_PREC_FP64)
+        !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_TF32X3)
         return MBD_ERR_INPUT;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev)
@@ -535,7 +691,7 @@ int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const doub
     const bool realloc = (n_atoms != ctx->N) || !ctx->slab;
     ctx->N = n_atoms;
     ctx->n = 3 * n_atoms;
-    ctx->ld = (ctx->n + kTile - 1) / kTile * kTile;
+    ctx->ld = (ctx->n + 127) / 128 * 128;   // 128: the tensor-core tile (also a multiple of 64)
     ctx->nb = static_cast<int>(ctx->ld / kTile);
     ctx->hR.assign(coords, coords + 3 * n_atoms);
     if (realloc) {
@@ -645,8 +801,10 @@ int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega
     return MBD_OK;
 }
 
-int mbd_get_stats(mbd_ctx *ctx, int *ns_iterations, double *ns_scale, double *ns_residual) {
+int mbd_get_stats(mbd_ctx *ctx, int *ns_iterations, double *ns_scale, double *ns_residual,
+                  double *correction_residual) {
     if (!ctx) return MBD_ERR_INPUT;
+    if (correction_residual) *correction_residual = ctx->opt.precision == MBD_PREC_FP64 ? 0.0 : ctx->corr_resid;
     if (ns_iterations) *ns_iterations = ctx->ns_iter;
     if (ns_scale) *ns_scale = ctx->ns_scale;
     if (ns_residual) *ns_residual = ctx->ns_resid;
@@ -689,6 +847,17 @@ int mbdk_gemm_f64(void *stream, int trans_b, int mode, int M, int N, int K, doub
     GemmArgs g{A, B, D, C, lda, ldb, ldd, ldc, 0, 0, 0, 0, M, N, K, 1, alpha, beta, mode, trans_b};
     gemm_f64(g, static_cast<cudaStream_t>(stream));
     return cudaGetLastError() == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
+}
+
+int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float alpha, const void *A0,
+                 const void *A1, long long lda, const void *B0, const void *B1, long long ldb, float beta,
+                 const float *D, float *C, void *C_hi, void *C_lo, float *CT, long long ldc, int *err) {
+    if (!A0 || !B0 || (kind != 0 && (!A1 || !B1)) || ((C_hi != nullptr) != (C_lo != nullptr))) return MBD_ERR_INPUT;
+    TcOperands op{A0, kind != 0 ? A1 : A0, B0, kind != 0 ? B1 : B0, lda, ldb};
+    TcArgs g{M, N, K, alpha, beta, D, ldc, C, C_hi, C_lo, CT, nullptr, nullptr, nullptr, 0, mode, err};
+    const cudaError_t e = tc_gemm(kind, op, g, static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorInvalidValue) return MBD_ERR_INPUT;
+    return e == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
 }
 
 int mbdk_cholesky_f64(void *stream, double *A, long long ld, int batch, double *dinv, int *status) {
