@@ -47,6 +47,7 @@ struct TcArgs {
     long long nvalid;
     int mode;
     int *err;
+    double *C64 = nullptr;   // optional FP64 output accumulated in place: C64 += result
 };
 cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_t s);
 // Mixed-precision helpers: Y = scale Q (FP32 and, if Yh, bf16 hi/lo) and Z = I;
@@ -57,6 +58,18 @@ void mixed_init(int kind, const double *Q, long long ld, double scale, float *Yf
 void mixed_axpby_identity(int kind, const float *P, long long ld, float a, float b, float *Zf, void *Zh, void *Zl,
                           cudaStream_t s);
 void to_f64(const float *Zf, long long ld, double scale, double *Zd, cudaStream_t s);
+// TF32x3 operand parts (32-bit hi, lo) of scale * Q (FP64) and of an FP32 matrix, with
+// the diagonal optionally set to zero; Out = scale diag(A) B in FP64.
+void split_tf32_f64(const double *Q, long long ld, double scale, int zero_diag, void *H, void *L, cudaStream_t s);
+void split_tf32_f32(const float *Z, long long ld, int zero_diag, void *H, void *L, cudaStream_t s);
+void diag_scale_rows_f64(const double *A, const float *B, long long ld, double scale, double *Out, cudaStream_t s);
+void diag_scale_rows_f32(const float *A, const double *B, long long ld, double *Out, cudaStream_t s);
+void split_tf32_f64_t(const double *A, long long ld, double scale, void *H, void *L, cudaStream_t s);   // of A^T
+// Energy of the mixed modes from T1 = Tr(scale Q Z) (FP64 dot), T2 = sum V o W:
+// E = (sqrt_s/4)(3 T1 - T2) - 3/2 sum omega; resid = |I - W|_F (work: 912 doubles).
+void energy_correction(const double *Q, double scale, const float *Z, const double *V, const double *W, long long ld,
+                       int n, double sqrt_s, const double *ombar, int N, double *work, double *out, double *resid,
+                       cudaStream_t s);
 void energy_variational(const double *V, const double *W, long long ld, int n, const double *ombar, int N,
                         double *work, double *out, cudaStream_t s);
 
@@ -91,6 +104,15 @@ void cholesky_f64(double *A, long long ld, long long mstride, int batch, double 
 // forward L y = x, then backward L^T z = y (L from cholesky_f64).
 void chol_solve3_f64(const double *L, long long ld, long long mstride, int batch,
                      const double *dinv, double *X, long long xstride, cudaStream_t s);
+
+// Mixed-precision screening solves (k_scs32.cu): FP32 copy of the batch, FP32 blocked
+// Cholesky with FP32 diagonal-block inverses; then X = A^{-1} B by FP32 solves and
+// `steps` iterative-refinement steps with residuals from the FP64 matrix (full, both
+// triangles; rows >= n are padding).  work: batch * 3 ld floats.
+void cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv, int *status,
+                           cudaStream_t s);
+void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,
+                   const double *B, double *X, float *work, int steps, cudaStream_t s);
 
 // Sum of squares of (I - P) over the leading n x n block, written to out[0].
 void frob_dev_identity(const double *P, long long ld, int n, double *out, cudaStream_t s);

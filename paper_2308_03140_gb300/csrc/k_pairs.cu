@@ -97,8 +97,9 @@ __global__ void k_prepare(AtomBufs b, int *status) {
 }
 
 // ---- screening matrices ------------------------------------------------------------
-// Thread (i, j) with j <= i writes block (i, j) of every frequency's matrix (lower
-// triangle is all the Cholesky reads).  Rows >= n are padding: identity.
+// Thread (i, j) with j <= i writes block (i, j) of every frequency's matrix and its
+// mirror (j, i) (the blocks are symmetric 3x3 tensors): the factorisations read the lower
+// triangle, the residuals of the refined solves the full matrix.  Rows >= n: identity.
 __global__ void k_build_scs(AtomBufs b, double beta, double a, double *M, long long ld,
                             long long mstride, int *status) {
     const int j = blockIdx.x * 32 + threadIdx.x;
@@ -126,7 +127,12 @@ __global__ void k_build_scs(AtomBufs b, double beta, double a, double *M, long l
         double *Mk = M + k * mstride;
         for (int x = 0; x < 3; ++x) {
             double *row = Mk + (3LL * i + x) * ld + 3 * j;
-            for (int y = 0; y < 3; ++y) row[y] = sr * ((x == y ? t.P : 0.0) + t.W * r[x] * r[y]);
+            double *mir = Mk + (3LL * j + x) * ld + 3 * i;
+            for (int y = 0; y < 3; ++y) {
+                const double v = sr * ((x == y ? t.P : 0.0) + t.W * r[x] * r[y]);
+                row[y] = v;
+                mir[y] = v;
+            }
         }
     }
 }

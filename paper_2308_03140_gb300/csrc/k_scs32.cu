@@ -1,0 +1,317 @@
+// Mixed-precision screening solves for Eq. (scs): the matrices A(u) = alpha(u)^{-1} +
+// T^scs (one per frequency point, Sec. 2.3) are factorised in FP32 (SIMT FFMA: the
+// FP32 rate of this part is about 70x its FP64 rate), and A X = B is solved by iterative
+// refinement: X <- X + A32^{-1} (B - A X), with the residual formed from the FP64
+// matrix.  For the moderately conditioned screening matrices (cond ~ 1e2 - 1e3) each
+// step gains about four digits; three steps reach FP64 accuracy.
+//
+// Layout as in k_dense.cu: batch of row-major ld x ld matrices, ld a multiple of 64,
+// right-hand sides [batch][ld][3].
+#include "internal.h"
+
+namespace mbdgb {
+namespace {
+
+constexpr int T64 = 64;
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sumd(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// C = alpha A B^T + beta C on 64x64 tiles, FP32 SIMT: 256 threads, 4x4 outputs each.
+// mode 0 all tiles, mode 1 lower tiles only (square).  Batched by blockIdx.z.
+__global__ void __launch_bounds__(256) k_sgemm_nt(const float *A, const float *B, float *C, long long lda,
+                                                  long long ldb, long long ldc, long long sA, long long sB,
+                                                  long long sC, int K, float alpha, float beta, int mode,
+                                                  int tiles_n) {
+    int tm, tn;
+    if (mode == 0) {
+        tm = blockIdx.x / tiles_n;
+        tn = blockIdx.x % tiles_n;
+    } else {
+        int x = static_cast<int>((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);
+        while ((x + 1) * (x + 2) / 2 <= static_cast<int>(blockIdx.x)) ++x;
+        while (x * (x + 1) / 2 > static_cast<int>(blockIdx.x)) --x;
+        tm = x;
+        tn = blockIdx.x - x * (x + 1) / 2;
+    }
+    const long long b = blockIdx.z;
+    const float *Ab = A + b * sA + static_cast<long long>(tm) * T64 * lda;
+    const float *Bb = B + b * sB + static_cast<long long>(tn) * T64 * ldb;
+    __shared__ float As[16][T64 + 4], Bs[16][T64 + 4];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    float acc[4][4] = {};
+    const int lr = t >> 2, lk = (t & 3) * 4;   // loader: row 0..63, k offset 0,4,8,12
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const float4 a = *reinterpret_cast<const float4 *>(Ab + static_cast<long long>(lr) * lda + k0 + lk);
+        const float4 c = *reinterpret_cast<const float4 *>(Bb + static_cast<long long>(lr) * ldb + k0 + lk);
+        As[lk][lr] = a.x; As[lk + 1][lr] = a.y; As[lk + 2][lr] = a.z; As[lk + 3][lr] = a.w;
+        Bs[lk][lr] = c.x; Bs[lk + 1][lr] = c.y; Bs[lk + 2][lr] = c.z; Bs[lk + 3][lr] = c.w;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float4 av = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float *Cb = C + b * sC;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long m = static_cast<long long>(tm) * T64 + ty * 4 + i;
+        float4 *cp = reinterpret_cast<float4 *>(Cb + m * ldc + static_cast<long long>(tn) * T64 + tx * 4);
+        float4 cv = beta != 0.f ? *cp : make_float4(0.f, 0.f, 0.f, 0.f);
+        cv.x = alpha * acc[i][0] + beta * cv.x;
+        cv.y = alpha * acc[i][1] + beta * cv.y;
+        cv.z = alpha * acc[i][2] + beta * cv.z;
+        cv.w = alpha * acc[i][3] + beta * cv.w;
+        *cp = cv;
+    }
+}
+
+// Unblocked FP32 Cholesky of the 64x64 diagonal block plus the inverse of its factor
+// (kept transposed in the strict upper triangle of S while it is built).
+__global__ void __launch_bounds__(256) k_spotrf_diag(float *A, long long ld, long long mstride, float *dinv,
+                                                     long long dstride, int *status) {
+    __shared__ float S[64][65];
+    __shared__ float dg[64];
+    __shared__ int bad;
+    float *Ab = A + static_cast<long long>(blockIdx.x) * mstride;
+    const int t = threadIdx.x;
+    if (t == 0) bad = 0;
+    for (int e = t; e < 4096; e += 256) {
+        const int r = e >> 6, c = e & 63;
+        S[r][c] = (c <= r) ? Ab[r * ld + c] : 0.f;
+    }
+    __syncthreads();
+    for (int j = 0; j < 64; ++j) {
+        if (t == 0) {
+            float d = S[j][j];
+            if (!(d > 0.f)) { bad = 1; d = 1.f; }
+            S[j][j] = sqrtf(d);
+        }
+        __syncthreads();
+        const float djj = S[j][j];
+        for (int i = j + 1 + t; i < 64; i += 256) S[i][j] /= djj;
+        __syncthreads();
+        const int m = 63 - j;
+        for (int e = t; e < m * m; e += 256) {
+            const int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) S[i][k] -= S[i][j] * S[k][j];
+        }
+        __syncthreads();
+    }
+    if (t < 64) {
+        const int c = t;
+        for (int i = c; i < 64; ++i) {
+            float acc = (i == c) ? 1.f : 0.f;
+            for (int k = c; k < i; ++k) acc -= S[i][k] * (k == c ? dg[c] : S[c][k]);
+            const float v = acc / S[i][i];
+            if (i == c) dg[c] = v; else S[c][i] = v;
+        }
+    }
+    __syncthreads();
+    float *Db = dinv + static_cast<long long>(blockIdx.x) * dstride;
+    for (int e = t; e < 4096; e += 256) {
+        const int r = e >> 6, c = e & 63;
+        if (c <= r) Ab[r * ld + c] = S[r][c];
+        Db[e] = (c > r) ? 0.f : (c == r ? dg[r] : S[c][r]);
+    }
+    if (t == 0 && bad) atomicOr(status, ST_SCS_NOT_PD);
+}
+
+// FP32 forward/backward substitution with 3 right-hand sides (FP32 in place).
+__global__ void __launch_bounds__(256) k_strsv_fwd3(const float *L, long long ld, long long mstride, const float *dinv,
+                                                    long long dstride, float *X, long long xstride, int nb) {
+    const long long b = blockIdx.x;
+    const float *Lb = L + b * mstride, *Db = dinv + b * dstride;
+    float *Xb = X + b * xstride;
+    __shared__ float s[64][3];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    for (int I = 0; I < nb; ++I) {
+        const int I0 = I * 64;
+        for (int rr = 0; rr < 8; ++rr) {
+            const int r = warp * 8 + rr;
+            const float *Lr = Lb + static_cast<long long>(I0 + r) * ld;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+            for (int c = lane; c < I0; c += 32) {
+                const float l = Lr[c];
+                a0 = fmaf(l, Xb[3 * c], a0);
+                a1 = fmaf(l, Xb[3 * c + 1], a1);
+                a2 = fmaf(l, Xb[3 * c + 2], a2);
+            }
+            a0 = warp_sumf(a0); a1 = warp_sumf(a1); a2 = warp_sumf(a2);
+            if (lane == 0) {
+                s[r][0] = Xb[3 * (I0 + r)] - a0;
+                s[r][1] = Xb[3 * (I0 + r) + 1] - a1;
+                s[r][2] = Xb[3 * (I0 + r) + 2] - a2;
+            }
+        }
+        __syncthreads();
+        if (t < 192) {
+            const int r = t / 3, c = t % 3;
+            const float *Di = Db + static_cast<long long>(I) * 4096 + r * 64;
+            float v = 0.f;
+            for (int k = 0; k <= r; ++k) v = fmaf(Di[k], s[k][c], v);
+            Xb[3 * (I0 + r) + c] = v;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_strsv_bwd3(const float *L, long long ld, long long mstride, const float *dinv,
+                                                    long long dstride, float *X, long long xstride, int nb) {
+    const long long b = blockIdx.x;
+    const float *Lb = L + b * mstride, *Db = dinv + b * dstride;
+    float *Xb = X + b * xstride;
+    __shared__ float part[4][64][3];
+    __shared__ float s[64][3];
+    const int t = threadIdx.x, r = t & 63, grp = t >> 6;
+    const long long n_rows = static_cast<long long>(nb) * 64;
+    for (int I = nb - 1; I >= 0; --I) {
+        const int I0 = I * 64;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        for (long long q = I0 + 64 + grp; q < n_rows; q += 4) {
+            const float l = Lb[q * ld + I0 + r];
+            a0 = fmaf(l, Xb[3 * q], a0);
+            a1 = fmaf(l, Xb[3 * q + 1], a1);
+            a2 = fmaf(l, Xb[3 * q + 2], a2);
+        }
+        part[grp][r][0] = a0; part[grp][r][1] = a1; part[grp][r][2] = a2;
+        __syncthreads();
+        if (t < 192) {
+            const int rr = t / 3, c = t % 3;
+            s[rr][c] = Xb[3 * (I0 + rr) + c] - (part[0][rr][c] + part[1][rr][c] + part[2][rr][c] + part[3][rr][c]);
+        }
+        __syncthreads();
+        if (t < 192) {
+            const int rr = t / 3, c = t % 3;
+            const float *Di = Db + static_cast<long long>(I) * 4096;
+            float v = 0.f;
+            for (int k = rr; k < 64; ++k) v = fmaf(Di[k * 64 + rr], s[k][c], v);
+            Xb[3 * (I0 + rr) + c] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// B32 = (float) A64, whole batch.
+__global__ void k_to_f32(const double *A, long long total, float *B) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        B[e] = static_cast<float>(A[e]);
+}
+
+// R = B - A X (FP64, A full row-major, 3 RHS), one warp per row; r32 = (float) R.
+__global__ void k_residual3(const double *A, long long ld, long long mstride, const double *Bv, const double *X,
+                            long long xstride, float *r32, int n) {
+    const int b = blockIdx.y;
+    const long long row = blockIdx.x * static_cast<long long>(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= ld) return;
+    const double *a = A + b * mstride + row * ld;
+    const double *x = X + b * xstride;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    if (row < n)
+        for (long long c = lane; c < n; c += 32) {
+            const double v = a[c];
+            a0 += v * x[3 * c];
+            a1 += v * x[3 * c + 1];
+            a2 += v * x[3 * c + 2];
+        }
+    a0 = warp_sumd(a0); a1 = warp_sumd(a1); a2 = warp_sumd(a2);
+    if (lane == 0) {
+        const double *bb = Bv + b * xstride + 3 * row;
+        float *rr = r32 + b * xstride + 3 * row;
+        rr[0] = static_cast<float>(bb[0] - a0);
+        rr[1] = static_cast<float>(bb[1] - a1);
+        rr[2] = static_cast<float>(bb[2] - a2);
+    }
+}
+
+// X64 (+)= (double) X32 over [batch][ld][3].
+__global__ void k_accumulate(double *X, const float *dx, long long total, int overwrite) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        X[e] = (overwrite ? 0.0 : X[e]) + static_cast<double>(dx[e]);
+}
+
+__global__ void k_rhs_to_f32(const double *B, long long total, float *b32) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        b32[e] = static_cast<float>(B[e]);
+}
+
+inline int gridn(long long total) { return static_cast<int>(std::min<long long>((total + 255) / 256, 152 * 16)); }
+
+void sgemm_nt(const float *A, const float *B, float *C, long long lda, long long ldb, long long ldc, long long sA,
+              long long sB, long long sC, int M, int N, int K, int batch, float alpha, float beta, int mode,
+              cudaStream_t s) {
+    const int tm = M / T64, tn = N / T64;
+    const dim3 grid(mode == 0 ? tm * tn : tm * (tm + 1) / 2, 1, batch);
+    count_launches(1);
+    k_sgemm_nt<<<grid, 256, 0, s>>>(A, B, C, lda, ldb, ldc, sA, sB, sC, K, alpha, beta, mode, tn);
+}
+
+void chol_solve3_f32(const float *L, long long ld, long long mstride, int batch, const float *dinv, float *X,
+                     long long xstride, cudaStream_t s) {
+    const int nb = static_cast<int>(ld / T64);
+    const long long dstride = static_cast<long long>(nb) * 4096;
+    count_launches(2);
+    k_strsv_fwd3<<<batch, 256, 0, s>>>(L, ld, mstride, dinv, dstride, X, xstride, nb);
+    k_strsv_bwd3<<<batch, 256, 0, s>>>(L, ld, mstride, dinv, dstride, X, xstride, nb);
+}
+
+}  // namespace
+
+void cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv, int *status,
+                           cudaStream_t s) {
+    const long long mstride = ld * ld;
+    count_launches(1);
+    k_to_f32<<<gridn(mstride * batch), 256, 0, s>>>(A64, mstride * batch, A32);
+    const int nb = static_cast<int>(ld / T64);
+    for (int k = 0; k < nb; ++k) {
+        const long long k0 = static_cast<long long>(k) * T64;
+        count_launches(1);
+        k_spotrf_diag<<<batch, 256, 0, s>>>(A32 + k0 * ld + k0, ld, mstride, dinv + k * 4096LL,
+                                            static_cast<long long>(nb) * 4096, status);
+        const int rem = static_cast<int>(ld - k0 - T64);
+        if (rem <= 0) continue;
+        float *A21 = A32 + (k0 + T64) * ld + k0, *A22 = A32 + (k0 + T64) * ld + k0 + T64;
+        sgemm_nt(A21, dinv + k * 4096LL, A21, ld, 64, ld, mstride, static_cast<long long>(nb) * 4096, mstride, rem,
+                 64, 64, batch, 1.f, 0.f, 0, s);
+        sgemm_nt(A21, A21, A22, ld, ld, ld, mstride, mstride, mstride, rem, rem, 64, batch, -1.f, 1.f, 1, s);
+    }
+}
+
+void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,
+                   const double *B, double *X, float *work, int steps, cudaStream_t s) {
+    const long long xs = 3 * ld, total = xs * batch;
+    count_launches(1);
+    k_rhs_to_f32<<<gridn(total), 256, 0, s>>>(B, total, work);
+    chol_solve3_f32(L32, ld, ld * ld, batch, dinv, work, xs, s);
+    count_launches(1);
+    k_accumulate<<<gridn(total), 256, 0, s>>>(X, work, total, 1);
+    for (int it = 0; it < steps; ++it) {
+        count_launches(1);
+        k_residual3<<<dim3(static_cast<unsigned>((ld + 7) / 8), batch), 256, 0, s>>>(A64, ld, ld * ld, B, X, xs,
+                                                                                     work, n);
+        chol_solve3_f32(L32, ld, ld * ld, batch, dinv, work, xs, s);
+        count_launches(1);
+        k_accumulate<<<gridn(total), 256, 0, s>>>(X, work, total, 0);
+    }
+}
+
+}  // namespace mbdgb

@@ -281,14 +281,15 @@ __global__ void __launch_bounds__(128, 1)
             // hi/lo split of the result for the next product's operands: bf16 pairs packed
             // two per word (BF16x3), or TF32-rounded hi and FP32 remainder (TF32x3).
             uint32_t hw[KIND == 2 ? 32 : 16], lw[KIND == 2 ? 32 : 16];
-            if (g.Ch) {
+            if (g.Ch || g.CTh) {
                 if (KIND == 2) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        uint32_t h;
+                    for (int j = 0; j < 32; ++j) {   // both parts rounded to nearest TF32: unbiased
+                        uint32_t h, l;
                         asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v[j]));
+                        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(v[j] - __uint_as_float(h)));
                         hw[j] = h;
-                        lw[j] = __float_as_uint(v[j] - __uint_as_float(h));
+                        lw[j] = l;
                     }
                 } else {
 #pragma unroll
@@ -301,6 +302,16 @@ __global__ void __launch_bounds__(128, 1)
                         lw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
                                 (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
                     }
+                }
+            }
+            // FP64 accumulation output (K split into chunks by the caller: C64 += result)
+            if (g.C64) {
+                const bool dg = (g.mode == 2) && (tm == tn);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (dg && n0 + j < m) continue;
+                    g.C64[m * g.ld + n0 + j] += static_cast<double>(v[j]);
+                    if ((mirror || dg) && n0 + j != m) g.C64[(n0 + j) * g.ld + m] += static_cast<double>(v[j]);
                 }
             }
             // Symmetric products (mode 2): upper tiles are mirrored into the lower half;
@@ -447,10 +458,62 @@ __device__ __forceinline__ void split_store(int kind, float v, void *H, void *L,
         static_cast<__nv_bfloat16 *>(H)[e] = h;
         static_cast<__nv_bfloat16 *>(L)[e] = __float2bfloat16_rn(v - __bfloat162float(h));
     } else {
-        uint32_t h;
+        uint32_t h, l;
         asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v));
+        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(v - __uint_as_float(h)));
         static_cast<uint32_t *>(H)[e] = h;
-        static_cast<float *>(L)[e] = v - __uint_as_float(h);
+        static_cast<uint32_t *>(L)[e] = l;
+    }
+}
+
+// TF32x3 parts of scale * Q for an FP64 Q: hi = tf32(q), lo = tf32(q - hi), both rounded
+// to nearest, the remainder taken in FP64.
+__global__ void k_split_tf32_f64(const double *Q, long long total, long long ld, double scale, int zero_diag,
+                                 uint32_t *H, uint32_t *L) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double q = (zero_diag && e / ld == e % ld) ? 0.0 : scale * Q[e];
+        uint32_t h, l;
+        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(static_cast<float>(q)));
+        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(static_cast<float>(q - static_cast<double>(__uint_as_float(h)))));
+        H[e] = h;
+        L[e] = l;
+    }
+}
+
+// TF32x3 parts of scale * A^T for an FP64 A (32x32 tiles through shared memory).
+__global__ void k_split_tf32_f64_t(const double *A, long long ld, double scale, uint32_t *H, uint32_t *L) {
+    __shared__ double t[32][33];
+    const long long r0 = static_cast<long long>(blockIdx.y) * 32, c0 = static_cast<long long>(blockIdx.x) * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) t[k][threadIdx.x] = A[(r0 + k) * ld + c0 + threadIdx.x];
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const double q = scale * t[threadIdx.x][k];
+        uint32_t h, l;
+        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(static_cast<float>(q)));
+        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(static_cast<float>(q - static_cast<double>(__uint_as_float(h)))));
+        const long long o = (c0 + k) * ld + r0 + threadIdx.x;
+        H[o] = h;
+        L[o] = l;
+    }
+}
+
+// TF32x3 parts of an FP32 matrix (optionally with its diagonal set to zero).
+__global__ void k_split_tf32_f32(const float *Z, long long total, long long ld, int zero_diag, uint32_t *H,
+                                 uint32_t *L) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        split_store(2, (zero_diag && e / ld == e % ld) ? 0.f : Z[e], H, L, e);
+}
+
+// Out[p][q] = scale * A[p][p] * B[p][q] (row scaling by a diagonal, FP64).
+template <typename TA, typename TB>
+__global__ void k_diag_scale_rows(const TA *A, const TB *B, long long ld, double scale, double *Out) {
+    const long long total = ld * ld;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long p = e / ld;
+        Out[e] = scale * static_cast<double>(A[p * ld + p]) * static_cast<double>(B[e]);
     }
 }
 
@@ -526,6 +589,62 @@ __global__ void __launch_bounds__(256) k_trace_dot_partials(const double *V, con
     }
 }
 
+// Per-block compensated partials over the leading n x n block of T1 = sum (scale Q) o Z
+// (FP64 x FP32, i.e. Tr(scale Q Z) for symmetric Z), T2 = sum V o W (FP32 x FP32) and
+// R = sum (delta - W)^2; out[3 * block + {0,1,2}].
+__global__ void __launch_bounds__(256) k_correction_partials(const double *Q, double scale, const float *Z,
+                                                             const double *V, const double *W, long long ld, int n,
+                                                             double *out) {
+    double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0, r2 = 0.0;
+    const long long total = static_cast<long long>(n) * n;
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < total; e += static_cast<long long>(gridDim.x) * 256) {
+        const long long i = e / n, j = e % n, o = i * ld + j;
+        double t, r;
+        two_sum(s0, scale * Q[o] * static_cast<double>(Z[o]), t, r);
+        s0 = t; c0 += r;
+        const double w = W[o];
+        two_sum(s1, V[o] * w, t, r);
+        s1 = t; c1 += r;
+        const double d = (i == j ? 1.0 : 0.0) - w;
+        r2 += d * d;
+    }
+    __shared__ double sh[5][256];
+    sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = c0; sh[2][threadIdx.x] = s1; sh[3][threadIdx.x] = c1;
+    sh[4][threadIdx.x] = r2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, ac = 0.0, b = 0.0, bc = 0.0, rr = 0.0;
+        for (int k = 0; k < 256; ++k) {
+            double t, r;
+            two_sum(a, sh[0][k], t, r); a = t; ac += r + sh[1][k];
+            two_sum(b, sh[2][k], t, r); b = t; bc += r + sh[3][k];
+            rr += sh[4][k];
+        }
+        out[3 * blockIdx.x] = a + ac;
+        out[3 * blockIdx.x + 1] = b + bc;
+        out[3 * blockIdx.x + 2] = rr;
+    }
+}
+
+// E = (sqrt(s)/4)(3 T1 - T2) - 3/2 sum omega_bar; resid = sqrt(R).
+__global__ void k_energy_correction(const double *part, int nblocks, double sqrt_s, const double *ombar, int N,
+                                    double *out, double *resid) {
+    if (threadIdx.x != 0) return;
+    double a = 0.0, ac = 0.0, b = 0.0, bc = 0.0, w = 0.0, wc = 0.0, rr = 0.0;
+    for (int k = 0; k < nblocks; ++k) {
+        double t, r;
+        two_sum(a, part[3 * k], t, r); a = t; ac += r;
+        two_sum(b, part[3 * k + 1], t, r); b = t; bc += r;
+        rr += part[3 * k + 2];
+    }
+    for (int i = 0; i < N; ++i) {
+        double t, r;
+        two_sum(w, ombar[i], t, r); w = t; wc += r;
+    }
+    out[0] = 0.25 * sqrt_s * (3.0 * (a + ac) - (b + bc)) - 1.5 * (w + wc);
+    resid[0] = sqrt(rr);
+}
+
 // E = 1/2 * (1/2)(3 Tr V - sum V o W) - 3/2 sum omega_bar, from the partials (one CTA).
 __global__ void k_energy_variational(const double *part, int nblocks, const double *ombar, int N, double *out) {
     if (threadIdx.x != 0) return;
@@ -562,6 +681,43 @@ void mixed_axpby_identity(int kind, const float *P, long long ld, float a, float
 void to_f64(const float *Zf, long long ld, double scale, double *Zd, cudaStream_t s) {
     count_launches(1);
     k_to_f64<<<grid_for(ld * ld), 256, 0, s>>>(Zf, ld * ld, scale, Zd);
+}
+
+void split_tf32_f64(const double *Q, long long ld, double scale, int zero_diag, void *H, void *L, cudaStream_t s) {
+    count_launches(1);
+    k_split_tf32_f64<<<grid_for(ld * ld), 256, 0, s>>>(Q, ld * ld, ld, scale, zero_diag, static_cast<uint32_t *>(H),
+                                                       static_cast<uint32_t *>(L));
+}
+
+void diag_scale_rows_f64(const double *A, const float *B, long long ld, double scale, double *Out, cudaStream_t s) {
+    count_launches(1);
+    k_diag_scale_rows<double, float><<<grid_for(ld * ld), 256, 0, s>>>(A, B, ld, scale, Out);
+}
+
+void diag_scale_rows_f32(const float *A, const double *B, long long ld, double *Out, cudaStream_t s) {
+    count_launches(1);
+    k_diag_scale_rows<float, double><<<grid_for(ld * ld), 256, 0, s>>>(A, B, ld, 1.0, Out);
+}
+
+void split_tf32_f64_t(const double *A, long long ld, double scale, void *H, void *L, cudaStream_t s) {
+    count_launches(1);
+    k_split_tf32_f64_t<<<dim3(static_cast<unsigned>(ld / 32), static_cast<unsigned>(ld / 32)), dim3(32, 8), 0, s>>>(
+        A, ld, scale, static_cast<uint32_t *>(H), static_cast<uint32_t *>(L));
+}
+
+void split_tf32_f32(const float *Z, long long ld, int zero_diag, void *H, void *L, cudaStream_t s) {
+    count_launches(1);
+    k_split_tf32_f32<<<grid_for(ld * ld), 256, 0, s>>>(Z, ld * ld, ld, zero_diag, static_cast<uint32_t *>(H),
+                                                       static_cast<uint32_t *>(L));
+}
+
+void energy_correction(const double *Q, double scale, const float *Z, const double *V, const double *W, long long ld,
+                       int n, double sqrt_s, const double *ombar, int N, double *work, double *out, double *resid,
+                       cudaStream_t s) {
+    const int nb = 304;   // work: 3 * nb doubles
+    count_launches(2);
+    k_correction_partials<<<nb, 256, 0, s>>>(Q, scale, Z, V, W, ld, n, work);
+    k_energy_correction<<<1, 32, 0, s>>>(work, nb, sqrt_s, ombar, N, out, resid);
 }
 
 void energy_variational(const double *V, const double *W, long long ld, int n, const double *ombar, int N,

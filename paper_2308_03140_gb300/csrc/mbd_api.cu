@@ -23,6 +23,8 @@ using namespace mbdgb;
 
 namespace {
 std::atomic<long long> g_launches{0};
+constexpr int kRefineSteps = 3;   // iterative-refinement steps of the mixed screening solves
+constexpr long long kCorrChunk = 256;   // K per tensor-core accumulation in the FP64 correction
 }  // namespace
 
 void mbdgb::count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -122,7 +124,8 @@ struct mbd_ctx {
     size_t slab_bytes = 0;
     double *dR, *da0ref, *dc6ref, *drref, *dratio;
     double *da0, *dom, *drv, *dalu, *dsigu, *dabar, *dabar0, *dc6bar, *dombar, *drbar, *du, *dwu;
-    double *dM, *ddinv, *dX, *dV;
+    double *dM, *ddinv, *dX, *dV, *dB;
+    float *sM = nullptr, *sdinv = nullptr, *swork = nullptr;   // FP32 factors of the mixed modes
     double *dQ, *dZ, *dP, *dY2, *dZ2;
     // mixed-precision Newton-Schulz buffers (ld x ld each)
     float *fY = nullptr, *fZ = nullptr, *fY2 = nullptr, *fZ2 = nullptr, *fP = nullptr, *fPT = nullptr;
@@ -211,6 +214,7 @@ int allocate(mbd_ctx *ctx) {
         {&ctx->dabar, nf1 * N}, {&ctx->dabar0, N}, {&ctx->dc6bar, N}, {&ctx->dombar, N},
         {&ctx->drbar, N}, {&ctx->du, nf1}, {&ctx->dwu, nf1},
         {&ctx->ddinv, nf1 * nb * 4096}, {&ctx->dX, nf1 * ld * 3}, {&ctx->dV, nf1 * ld * 3},
+        {&ctx->dB, nf1 * ld * 3},
         {&ctx->dh, nf1 * N}, {&ctx->dgomb, N}, {&ctx->dgab0, N}, {&ctx->dgrb, N}, {&ctx->dgR, 3 * N},
         {&ctx->dga0, N}, {&ctx->dgom, N}, {&ctx->dgrv, N}, {&ctx->dgp, 4 * N}, {&ctx->dscal, 8 + 2 * 64 + 1024},
     };
@@ -226,6 +230,11 @@ int allocate(mbd_ctx *ctx) {
     const size_t split_mat = prec == MBD_PREC_BF16X3 ? mat16 : (prec == MBD_PREC_TF32X3 ? mat32 : 0);
     if (prec != MBD_PREC_FP64) bytes += 6 * mat32;
     bytes += 12 * split_mat;
+    // FP32 screening factors, their diagonal-block inverses and solve workspace
+    const size_t scs32 = prec != MBD_PREC_FP64
+                             ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * nf1 * ld * 3)
+                             : 0;
+    bytes += scs32;
     release(ctx);
     cudaError_t e = cudaMalloc(&ctx->slab, bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, "mbd_set_geometry", e);
@@ -258,6 +267,14 @@ int allocate(mbd_ctx *ctx) {
                 m[k] = p;
                 p += split_mat;
             }
+    }
+    if (scs32) {
+        ctx->sM = reinterpret_cast<float *>(p);
+        p += nf1 * mat32;
+        ctx->sdinv = reinterpret_cast<float *>(p);
+        p += al(sizeof(float) * nf1 * nb * 4096);
+        ctx->swork = reinterpret_cast<float *>(p);
+        p += al(sizeof(float) * nf1 * ld * 3);
     }
     // Untouched parts of the factor buffers (strict upper triangles) are read by no
     // kernel; clearing them once keeps them finite.
@@ -293,9 +310,13 @@ void backward_passes(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const doub
     const double beta = ctx->opt.beta, a = ctx->opt.a;
     MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
     mbd_grad_pass(b, beta, a, ctx->Zlast, ld, ctx->zscale, go, s);
-    chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, ctx->dV, ld, xs, s);
+    const bool fp64 = ctx->opt.precision == MBD_PREC_FP64;
+    chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, fp64 ? ctx->dV : ctx->dB, ld, xs, s);
     cudaMemsetAsync(ctx->dgom, 0, sizeof(double) * ctx->N, s);
-    chol_solve3_f64(ctx->dM, ld, mat, ctx->nf1, ctx->ddinv, ctx->dV, xs, s);
+    if (fp64)
+        chol_solve3_f64(ctx->dM, ld, mat, ctx->nf1, ctx->ddinv, ctx->dV, xs, s);
+    else
+        refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, ctx->n, ctx->nf1, ctx->dB, ctx->dV, ctx->swork, kRefineSteps, s);
     scs_grad_pass(b, beta, a, ctx->dX, ctx->dV, xs, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgR, s);
     if (grad_params) ts_chain(b, ctx->dga0, ctx->dgom, ctx->dgrv, grad_energy, grad_params, s);
     if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
@@ -418,20 +439,60 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
     MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz_tc");
     if (st & ST_TC_TIMEOUT) return fail(ctx, MBD_ERR_CUDA, "newton_schulz_tc", "tensor-core GEMM wait timed out");
     if (!floor_reached) return fail(ctx, MBD_ERR_NOT_CONVERGED, "newton_schulz_tc", "iteration cap reached");
-    // ---- FP64 correction ----
+    // ---- correction ----
+    // With Zs ~ (Q/s)^{-1/2} (FP32 values of the iteration), Vs = (Q/s) Zs, Ws = Zs Vs:
+    // Tr Q^{1/2} ~ sqrt(s) (3 Tr Vs - sum Vs o Ws)/2, second order in the error of Zs.
+    // Tr Vs = sum (Q/s) o Zs is an exact FP64 dot.  Vs and Ws come from TF32x3
+    // tensor-core products with round-to-nearest operand parts, K split into chunks of
+    // kCorrChunk summed in FP64: the tensor core's FP32 accumulation truncates, and its
+    // bias grows with the number of terms summed in one accumulator.
     mark(ctx, s, e_corr);
-    double *Zd = ctx->dZ, *V = ctx->dP, *W = ctx->dY2;
-    to_f64(Z.f, ld, 1.0 / std::sqrt(sc), Zd, s);
-    GemmArgs gv{ctx->dQ, Zd, nullptr, V, ld, ld, 0, ld, 0, 0, 0, 0, M, M, M, 1, 1.0, 0.0, 0, 1};   // V = Q Zd
-    gemm_f64(gv, s);
-    GemmArgs gw{Zd, V, nullptr, W, ld, ld, 0, ld, 0, 0, 0, 0, M, M, M, 1, 1.0, 0.0, 2, 0};         // W = Zd V
-    gemm_f64(gw, s);
-    energy_variational(V, W, ld, n, ctx->dombar, N, ctx->dscal + 8 + 2 * 64, energy_out, s);
-    frob_dev_identity(W, ld, n, ctx->dscal + 3, s);   // the true accuracy of Zd: |Zd Q Zd - I|_F
+    {
+        // FP32 workspace: the iteration's matrices are free now.  Parts of offdiag(Q/s) and of
+        // the full Zs feed the first product; offdiag(Zs) (reusing the Q parts) and Vs^T the
+        // second.
+        float *Qh = Y.f, *Ql = Y2.f, *Zs_h = P.f, *Zs_l = PT.f, *Zh = Qh, *Zl = Ql;
+        float *VTh = reinterpret_cast<float *>(ctx->dY2), *VTl = VTh + ld * ld;
+        double *V64 = ctx->dP, *W64 = ctx->dZ2;
+        const float *Zs = Z.f;
+        // The diagonal scalings are exact FP64 elementwise products; the tensor cores only
+        // add the off-diagonal parts, so no accumulator sums a dominant term with many small
+        // ones: Vs = diag(Q/s) Zs + offdiag(Q/s) Zs, Ws = diag(Zs) Vs + offdiag(Zs) Vs.
+        split_tf32_f64(ctx->dQ, ld, 1.0 / sc, 1, Qh, Ql, s);
+        split_tf32_f32(Zs, ld, 0, Zs_h, Zs_l, s);
+        diag_scale_rows_f64(ctx->dQ, Zs, ld, 1.0 / sc, V64, s);
+        for (long long k0 = 0; k0 < ld; k0 += kCorrChunk) {   // Vs += offdiag(Q/s)[:, k] Zs[k, :]
+            const int kc = static_cast<int>(std::min<long long>(kCorrChunk, ld - k0));
+            TcOperands op{Qh + k0, Ql + k0, Zs_h + k0, Zs_l + k0, ld, ld};
+            TcArgs g{M, M, kc, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     0, 0, ctx->dstatus, V64};
+            const cudaError_t e = tc_gemm(2, op, g, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, "correction", e);
+        }
+        split_tf32_f64_t(V64, ld, 1.0, VTh, VTl, s);
+        split_tf32_f32(Zs, ld, 1, Zh, Zl, s);
+        diag_scale_rows_f32(Zs, V64, ld, W64, s);
+        for (long long k0 = 0; k0 < ld; k0 += kCorrChunk) {   // Ws += offdiag(Zs)[:, k] Vs[k, :]
+            const int kc = static_cast<int>(std::min<long long>(kCorrChunk, ld - k0));
+            TcOperands op{Zh + k0, Zl + k0, VTh + k0, VTl + k0, ld, ld};
+            TcArgs g{M, M, kc, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     0, 0, ctx->dstatus, W64};
+            const cudaError_t e = tc_gemm(2, op, g, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, "correction", e);
+        }
+        energy_correction(ctx->dQ, 1.0 / sc, Zs, V64, W64, ld, n, std::sqrt(sc), ctx->dombar, N,
+                          ctx->dscal + 8 + 2 * 64, energy_out, ctx->dscal + 3, s);
+    }
+    double *Zd = ctx->dZ;
+    to_f64(Z.f, ld, 1.0 / std::sqrt(sc), Zd, s);   // Q^{-1/2} for the gradient
     double c2 = 0.0;
-    MBD_CUDA(cudaMemcpyAsync(&c2, ctx->dscal + 3, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz_tc");
-    MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz_tc");
-    ctx->corr_resid = std::sqrt(c2);
+    MBD_CUDA(cudaMemcpyAsync(&c2, ctx->dscal + 3, sizeof(double), cudaMemcpyDeviceToHost, s), "correction");
+    MBD_CUDA(cudaStreamSynchronize(s), "correction");
+    int st2 = 0;
+    MBD_CUDA(cudaMemcpyAsync(&st2, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s), "correction");
+    MBD_CUDA(cudaStreamSynchronize(s), "correction");
+    if (st2 & ST_TC_TIMEOUT) return fail(ctx, MBD_ERR_CUDA, "correction", "tensor-core GEMM wait timed out");
+    ctx->corr_resid = c2;
     ctx->Zlast = Zd;
     ctx->zscale = 1.0;
     return MBD_OK;
@@ -465,9 +526,15 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     // ---- screening (Sec. 2.3) ----
     prepare_atoms(b, ctx->dstatus, s);
     build_scs(b, beta, a, ctx->dM, ld, mat, ctx->dstatus, s);
-    cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
-    init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
-    chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, xs, s);
+    if (ctx->opt.precision == MBD_PREC_FP64) {
+        cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
+        init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
+        chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, xs, s);
+    } else {   // FP32 factors, FP64-refined solutions
+        cholesky_f32_from_f64(ctx->dM, ctx->sM, ld, nf1, ctx->sdinv, ctx->dstatus, s);
+        init_rhs_identity(ctx->dB, ld, n, nf1, xs, s);
+        refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, n, nf1, ctx->dB, ctx->dX, ctx->swork, kRefineSteps, s);
+    }
     contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
     mark(ctx, s, e_scs);
     int rc = read_status(ctx, s, "screening");
@@ -612,7 +679,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         }
         if (e_corr) p.correction_ms = span_ms(e_corr, e_ns);
         p.screening_ms = span_ms(e_start, e_scs);
-        p.screening_flops = nf1 * nd * nd * nd / 3.0;
+        p.screening_flops = nf1 * nd * nd * nd / 3.0;   // FP64, or FP32 in the mixed modes
         p.newton_schulz_ms = span_ms(e_scs, e_ns);
         p.gradient_ms = span_ms(e_ns, e_grad);
         p.total_ms = span_ms(e_start, e_grad);
