@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64"), default="bf16x3",
+                    help="matrix-function arithmetic of the timed arm (the FP64 path is measured beside it)")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison arm (0: skip)")
     ap.add_argument("--cpu-sample-atoms", type=int, default=250,
                     help="atoms of the bounded oracle sample (same recipe, extrapolated by n^3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -206,7 +209,9 @@ def run_ours(args):
     gp = torch.zeros(4, N, dtype=torch.float64, device=dev)
     al = torch.zeros(N, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    m = binding.MBD(local)
+    precision = {"fp64": binding.MBD_PREC_FP64, "tf32": binding.MBD_PREC_TF32,
+                 "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3}[args.precision]
+    m = binding.MBD(local, precision=precision)
     m.set_geometry(sysm.coords)
     m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, sysm.rvdw_ref, sysm.ratio)
 
@@ -248,6 +253,34 @@ def run_ours(args):
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 8 * (3 * N + 4 * N),
            "d2h_bytes_per_step": 8 * (1 + 3 * N + 4 * N + N)}
+
+    gR_t, gp_t = gR.detach().cpu().numpy().copy(), gp.detach().cpu().numpy().copy()
+    # FP64 comparison arm (same workload and API; fewer steps: it is ~20x slower)
+    fp64 = None
+    if precision != binding.MBD_PREC_FP64 and args.fp64_steps > 0:
+        m64 = binding.MBD(local, precision=binding.MBD_PREC_FP64)
+        m64.set_geometry(sysm.coords)
+        e64 = torch.zeros(1, dtype=torch.float64, device=dev)
+        g64 = torch.zeros(N, 3, dtype=torch.float64, device=dev)
+        p64 = torch.zeros(4, N, dtype=torch.float64, device=dev)
+        m64.evaluate_dev(*inp, e64, g64, p64, None, stream=stream)   # warm-up
+        torch.cuda.synchronize(dev)
+        a0_, a1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0_.record(stream)
+        for _ in range(args.fp64_steps):
+            m64.evaluate_dev(*inp, e64, g64, p64, None, stream=stream)
+        a1_.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = max_over_ranks(a0_.elapsed_time(a1_))
+        E64 = e64.item()
+        g64n, p64n = g64.cpu().numpy(), p64.cpu().numpy()
+        fp64 = {"value": world * args.fp64_steps / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
+                "steps": args.fp64_steps, "warmup": 1, "energy_ha": E64,
+                "delta_e_per_atom_ha": (E - E64) / N,
+                "max_force_err_ha_bohr": float(abs(gR_t - g64n).max()),
+                "max_force_ha_bohr": float(abs(g64n).max()),
+                "max_param_grad_err": float(abs(gp_t - p64n).max())}
+        m64.close()
 
     gemm_ms = sum(p["gemm_ms"] for p in profs)
     gemm_flops = sum(p["gemm_flops"] for p in profs)

@@ -36,9 +36,10 @@ int mbdk_gemm_f64(void *stream, int trans_b, int mode, int M, int N, int K, doub
 int mbdk_cholesky_f64(void *stream, double *A, long long ld, int batch, double *dinv, int *status);
 
 /* Solves A X = B in place for 3 right-hand sides per matrix, X [batch][ld][3], with the
- * factors and diagonal-block inverses from mbdk_cholesky_f64. */
+ * factors and diagonal-block inverses from mbdk_cholesky_f64.  work: caller-owned
+ * device buffer of the same size as X (the intermediate L^{-1} B), not aliasing X. */
 int mbdk_chol_solve3_f64(void *stream, const double *L, long long ld, int batch, const double *dinv,
-                         double *X);
+                         double *X, double *work);
 
 /* C = alpha * sum_p A_p B_p^T + beta * D on the 5th-generation tensor cores (tcgen05,
  * TMA-staged operands, FP32 accumulation in tensor memory) -- the products of the
@@ -63,10 +64,10 @@ int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float al
  * Same result as mbdk_cholesky_f64 followed by mbdk_chol_solve3_f64 on the same
  * stream: A [batch][ld][ld] is overwritten by its lower Cholesky factors and X
  * [batch][ld][3] by the solutions of A X = B.  The diagonal-block inverses that those
- * calls keep in the caller's dinv buffer live instead in one static 16 MiB device
- * array inside the library (2^21 doubles), so the call allocates nothing and calls no
- * allocating routine.  Limit: batch * (ld/64) * 4096 <= 2^21; larger requests return
- * MBD_ERR_SCRATCH_LIMIT before any work is launched.  The first call on a device looks
+ * calls keep in the caller's dinv and work buffers live instead in one static 16 MiB
+ * device array inside the library (2^21 doubles), so the call allocates nothing and
+ * calls no allocating routine.  Limit: batch * ((ld/64) * 4096 + 3 * ld) <= 2^21; larger
+ * requests return MBD_ERR_SCRATCH_LIMIT before any work is launched.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device current, so
  * make that first call before any stream capture.  All calls on a device share the
  * array and it keeps the last call's contents; calls whose work overlaps on the GPU

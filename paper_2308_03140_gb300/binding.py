@@ -82,7 +82,7 @@ def load(path: str | None = None):
     L.mbdk_cholesky_f64.argtypes = [vp, vp, ll, i, vp, vp]
     f = C.c_float
     L.mbdk_gemm_tc.argtypes = [vp, i, i, i, i, i, f, vp, vp, ll, vp, vp, ll, f, vp, vp, vp, vp, vp, ll, vp]
-    L.mbdk_chol_solve3_f64.argtypes = [vp, vp, ll, i, vp, vp]
+    L.mbdk_chol_solve3_f64.argtypes = [vp, vp, ll, i, vp, vp, vp]
     L.mbdk_cholesky_solve3_f64_noalloc.argtypes = [vp, vp, ll, i, vp, vp]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int
@@ -263,9 +263,15 @@ def mbdk_cholesky_f64(A, dinv, status, stream=None):
         raise MBDError(rc, "mbdk_cholesky_f64", "launch rejected")
 
 
-def mbdk_chol_solve3_f64(Lf, dinv, X, stream=None):
+def mbdk_chol_solve3_f64(Lf, dinv, X, work=None, stream=None):
+    """Solves in place with the factors of mbdk_cholesky_f64; work: same shape as X
+    (allocated here with torch when not given)."""
+    import torch
     L = load()
-    rc = L.mbdk_chol_solve3_f64(_stream(Lf, stream), _tptr(Lf), Lf.shape[-1], Lf.shape[0], _tptr(dinv), _tptr(X))
+    if work is None:
+        work = torch.empty_like(X)
+    rc = L.mbdk_chol_solve3_f64(_stream(Lf, stream), _tptr(Lf), Lf.shape[-1], Lf.shape[0], _tptr(dinv), _tptr(X),
+                                _tptr(work))
     if rc:
         raise MBDError(rc, "mbdk_chol_solve3_f64", "launch rejected")
 

@@ -101,14 +101,19 @@ void cholesky_f64(double *A, long long ld, long long mstride, int batch, double 
                   int *status, cudaStream_t s);
 
 // Batched triangular solves with 3 right-hand sides, in place on X [b][ld][3]:
-// forward L y = x, then backward L^T z = y (L from cholesky_f64).
+// forward L y = x, then backward L^T z = y (L from cholesky_f64).  work: same shape
+// as X (the intermediate y).
 void chol_solve3_f64(const double *L, long long ld, long long mstride, int batch,
-                     const double *dinv, double *X, long long xstride, cudaStream_t s);
+                     const double *dinv, double *X, double *work, long long xstride, cudaStream_t s);
+// Block-column triangular solves (k_trsv.cu), T = double or float: X <- L^-T L^-1 X.
+template <typename T>
+void trsv_blocked(const T *L, long long ld, long long mstride, int batch, const T *dinv, T *X, T *W, long long xstride,
+                  cudaStream_t s);
 
 // Mixed-precision screening solves (k_scs32.cu): FP32 copy of the batch, FP32 blocked
 // Cholesky with FP32 diagonal-block inverses; then X = A^{-1} B by FP32 solves and
 // `steps` iterative-refinement steps with residuals from the FP64 matrix (full, both
-// triangles; rows >= n are padding).  work: batch * 3 ld floats.
+// triangles; rows >= n are padding).  work: 2 * batch * 3 ld floats.
 void cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv, int *status,
                            cudaStream_t s);
 void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,

@@ -195,86 +195,6 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Forward substitution L y = x, 3 right-hand sides, one CTA per matrix.
-__global__ void __launch_bounds__(256) k_trsv_fwd3(const double *L, long long ld, long long mstride,
-                                                   const double *dinv, long long dstride, double *X,
-                                                   long long xstride, int nb) {
-    const long long b = blockIdx.x;
-    const double *Lb = L + b * mstride;
-    const double *Db = dinv + b * dstride;
-    double *Xb = X + b * xstride;
-    __shared__ double s[64][3];
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    for (int I = 0; I < nb; ++I) {
-        const int I0 = I * 64;
-        for (int rr = 0; rr < 8; ++rr) {
-            const int r = warp * 8 + rr;
-            const double *Lr = Lb + static_cast<long long>(I0 + r) * ld;
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-            for (int c = lane; c < I0; c += 32) {
-                const double l = Lr[c];
-                a0 += l * Xb[3 * c];
-                a1 += l * Xb[3 * c + 1];
-                a2 += l * Xb[3 * c + 2];
-            }
-            a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
-            if (lane == 0) {
-                s[r][0] = Xb[3 * (I0 + r)] - a0;
-                s[r][1] = Xb[3 * (I0 + r) + 1] - a1;
-                s[r][2] = Xb[3 * (I0 + r) + 2] - a2;
-            }
-        }
-        __syncthreads();
-        if (t < 192) {
-            const int r = t / 3, c = t % 3;
-            const double *Di = Db + static_cast<long long>(I) * 4096 + r * 64;
-            double v = 0.0;
-            for (int k = 0; k <= r; ++k) v += Di[k] * s[k][c];
-            Xb[3 * (I0 + r) + c] = v;
-        }
-        __syncthreads();
-    }
-}
-
-// Backward substitution L^T x = y, 3 right-hand sides, one CTA per matrix.
-__global__ void __launch_bounds__(256) k_trsv_bwd3(const double *L, long long ld, long long mstride,
-                                                   const double *dinv, long long dstride, double *X,
-                                                   long long xstride, int nb) {
-    const long long b = blockIdx.x;
-    const double *Lb = L + b * mstride;
-    const double *Db = dinv + b * dstride;
-    double *Xb = X + b * xstride;
-    __shared__ double part[4][64][3];
-    __shared__ double s[64][3];
-    const int t = threadIdx.x, r = t & 63, grp = t >> 6;
-    const long long n_rows = static_cast<long long>(nb) * 64;
-    for (int I = nb - 1; I >= 0; --I) {
-        const int I0 = I * 64;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        for (long long q = I0 + 64 + grp; q < n_rows; q += 4) {
-            const double l = Lb[q * ld + I0 + r];
-            a0 += l * Xb[3 * q];
-            a1 += l * Xb[3 * q + 1];
-            a2 += l * Xb[3 * q + 2];
-        }
-        part[grp][r][0] = a0; part[grp][r][1] = a1; part[grp][r][2] = a2;
-        __syncthreads();
-        if (t < 192) {
-            const int rr = t / 3, c = t % 3;
-            s[rr][c] = Xb[3 * (I0 + rr) + c] - (part[0][rr][c] + part[1][rr][c] + part[2][rr][c] + part[3][rr][c]);
-        }
-        __syncthreads();
-        if (t < 192) {
-            const int rr = t / 3, c = t % 3;
-            const double *Di = Db + static_cast<long long>(I) * 4096;
-            double v = 0.0;
-            for (int k = rr; k < 64; ++k) v += Di[k * 64 + rr] * s[k][c];
-            Xb[3 * (I0 + rr) + c] = v;
-        }
-        __syncthreads();
-    }
-}
-
 __global__ void k_frob_dev_identity(const double *P, long long ld, int n, double *out) {
     double acc = 0.0;
     const long long total = static_cast<long long>(n) * n;
@@ -455,13 +375,8 @@ void cholesky_f64(double *A, long long ld, long long mstride, int batch, double 
 }
 
 void chol_solve3_f64(const double *L, long long ld, long long mstride, int batch, const double *dinv,
-                     double *X, long long xstride, cudaStream_t s) {
-    const int nb = static_cast<int>(ld / kTile);
-    const long long dstride = static_cast<long long>(nb) * 4096;
-    count_launches(1);
-    k_trsv_fwd3<<<batch, 256, 0, s>>>(L, ld, mstride, dinv, dstride, X, xstride, nb);
-    count_launches(1);
-    k_trsv_bwd3<<<batch, 256, 0, s>>>(L, ld, mstride, dinv, dstride, X, xstride, nb);
+                     double *X, double *work, long long xstride, cudaStream_t s) {
+    trsv_blocked<double>(L, ld, mstride, batch, dinv, X, work, xstride, s);
 }
 
 void frob_dev_identity(const double *P, long long ld, int n, double *out, cudaStream_t s) {

@@ -132,81 +132,6 @@ __global__ void __launch_bounds__(256) k_spotrf_diag(float *A, long long ld, lon
     if (t == 0 && bad) atomicOr(status, ST_SCS_NOT_PD);
 }
 
-// FP32 forward/backward substitution with 3 right-hand sides (FP32 in place).
-__global__ void __launch_bounds__(256) k_strsv_fwd3(const float *L, long long ld, long long mstride, const float *dinv,
-                                                    long long dstride, float *X, long long xstride, int nb) {
-    const long long b = blockIdx.x;
-    const float *Lb = L + b * mstride, *Db = dinv + b * dstride;
-    float *Xb = X + b * xstride;
-    __shared__ float s[64][3];
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    for (int I = 0; I < nb; ++I) {
-        const int I0 = I * 64;
-        for (int rr = 0; rr < 8; ++rr) {
-            const int r = warp * 8 + rr;
-            const float *Lr = Lb + static_cast<long long>(I0 + r) * ld;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-            for (int c = lane; c < I0; c += 32) {
-                const float l = Lr[c];
-                a0 = fmaf(l, Xb[3 * c], a0);
-                a1 = fmaf(l, Xb[3 * c + 1], a1);
-                a2 = fmaf(l, Xb[3 * c + 2], a2);
-            }
-            a0 = warp_sumf(a0); a1 = warp_sumf(a1); a2 = warp_sumf(a2);
-            if (lane == 0) {
-                s[r][0] = Xb[3 * (I0 + r)] - a0;
-                s[r][1] = Xb[3 * (I0 + r) + 1] - a1;
-                s[r][2] = Xb[3 * (I0 + r) + 2] - a2;
-            }
-        }
-        __syncthreads();
-        if (t < 192) {
-            const int r = t / 3, c = t % 3;
-            const float *Di = Db + static_cast<long long>(I) * 4096 + r * 64;
-            float v = 0.f;
-            for (int k = 0; k <= r; ++k) v = fmaf(Di[k], s[k][c], v);
-            Xb[3 * (I0 + r) + c] = v;
-        }
-        __syncthreads();
-    }
-}
-
-__global__ void __launch_bounds__(256) k_strsv_bwd3(const float *L, long long ld, long long mstride, const float *dinv,
-                                                    long long dstride, float *X, long long xstride, int nb) {
-    const long long b = blockIdx.x;
-    const float *Lb = L + b * mstride, *Db = dinv + b * dstride;
-    float *Xb = X + b * xstride;
-    __shared__ float part[4][64][3];
-    __shared__ float s[64][3];
-    const int t = threadIdx.x, r = t & 63, grp = t >> 6;
-    const long long n_rows = static_cast<long long>(nb) * 64;
-    for (int I = nb - 1; I >= 0; --I) {
-        const int I0 = I * 64;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        for (long long q = I0 + 64 + grp; q < n_rows; q += 4) {
-            const float l = Lb[q * ld + I0 + r];
-            a0 = fmaf(l, Xb[3 * q], a0);
-            a1 = fmaf(l, Xb[3 * q + 1], a1);
-            a2 = fmaf(l, Xb[3 * q + 2], a2);
-        }
-        part[grp][r][0] = a0; part[grp][r][1] = a1; part[grp][r][2] = a2;
-        __syncthreads();
-        if (t < 192) {
-            const int rr = t / 3, c = t % 3;
-            s[rr][c] = Xb[3 * (I0 + rr) + c] - (part[0][rr][c] + part[1][rr][c] + part[2][rr][c] + part[3][rr][c]);
-        }
-        __syncthreads();
-        if (t < 192) {
-            const int rr = t / 3, c = t % 3;
-            const float *Di = Db + static_cast<long long>(I) * 4096;
-            float v = 0.f;
-            for (int k = rr; k < 64; ++k) v = fmaf(Di[k * 64 + rr], s[k][c], v);
-            Xb[3 * (I0 + rr) + c] = v;
-        }
-        __syncthreads();
-    }
-}
-
 // B32 = (float) A64, whole batch.
 __global__ void k_to_f32(const double *A, long long total, float *B) {
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
@@ -266,12 +191,8 @@ void sgemm_nt(const float *A, const float *B, float *C, long long lda, long long
 }
 
 void chol_solve3_f32(const float *L, long long ld, long long mstride, int batch, const float *dinv, float *X,
-                     long long xstride, cudaStream_t s) {
-    const int nb = static_cast<int>(ld / T64);
-    const long long dstride = static_cast<long long>(nb) * 4096;
-    count_launches(2);
-    k_strsv_fwd3<<<batch, 256, 0, s>>>(L, ld, mstride, dinv, dstride, X, xstride, nb);
-    k_strsv_bwd3<<<batch, 256, 0, s>>>(L, ld, mstride, dinv, dstride, X, xstride, nb);
+                     float *W, long long xstride, cudaStream_t s) {
+    trsv_blocked<float>(L, ld, mstride, batch, dinv, X, W, xstride, s);
 }
 
 }  // namespace
@@ -299,16 +220,17 @@ void cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batc
 void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,
                    const double *B, double *X, float *work, int steps, cudaStream_t s) {
     const long long xs = 3 * ld, total = xs * batch;
+    float *work2 = work + total;   // intermediate of the triangular solves
     count_launches(1);
     k_rhs_to_f32<<<gridn(total), 256, 0, s>>>(B, total, work);
-    chol_solve3_f32(L32, ld, ld * ld, batch, dinv, work, xs, s);
+    chol_solve3_f32(L32, ld, ld * ld, batch, dinv, work, work2, xs, s);
     count_launches(1);
     k_accumulate<<<gridn(total), 256, 0, s>>>(X, work, total, 1);
     for (int it = 0; it < steps; ++it) {
         count_launches(1);
         k_residual3<<<dim3(static_cast<unsigned>((ld + 7) / 8), batch), 256, 0, s>>>(A64, ld, ld * ld, B, X, xs,
                                                                                      work, n);
-        chol_solve3_f32(L32, ld, ld * ld, batch, dinv, work, xs, s);
+        chol_solve3_f32(L32, ld, ld * ld, batch, dinv, work, work2, xs, s);
         count_launches(1);
         k_accumulate<<<gridn(total), 256, 0, s>>>(X, work, total, 0);
     }

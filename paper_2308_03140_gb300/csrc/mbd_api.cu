@@ -232,7 +232,7 @@ int allocate(mbd_ctx *ctx) {
     bytes += 12 * split_mat;
     // FP32 screening factors, their diagonal-block inverses and solve workspace
     const size_t scs32 = prec != MBD_PREC_FP64
-                             ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * nf1 * ld * 3)
+                             ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * 2 * nf1 * ld * 3)
                              : 0;
     bytes += scs32;
     release(ctx);
@@ -274,7 +274,7 @@ int allocate(mbd_ctx *ctx) {
         ctx->sdinv = reinterpret_cast<float *>(p);
         p += al(sizeof(float) * nf1 * nb * 4096);
         ctx->swork = reinterpret_cast<float *>(p);
-        p += al(sizeof(float) * nf1 * ld * 3);
+        p += al(sizeof(float) * 2 * nf1 * ld * 3);
     }
     // Untouched parts of the factor buffers (strict upper triangles) are read by no
     // kernel; clearing them once keeps them finite.
@@ -314,7 +314,7 @@ void backward_passes(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const doub
     chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, fp64 ? ctx->dV : ctx->dB, ld, xs, s);
     cudaMemsetAsync(ctx->dgom, 0, sizeof(double) * ctx->N, s);
     if (fp64)
-        chol_solve3_f64(ctx->dM, ld, mat, ctx->nf1, ctx->ddinv, ctx->dV, xs, s);
+        chol_solve3_f64(ctx->dM, ld, mat, ctx->nf1, ctx->ddinv, ctx->dV, ctx->dB, xs, s);
     else
         refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, ctx->n, ctx->nf1, ctx->dB, ctx->dV, ctx->swork, kRefineSteps, s);
     scs_grad_pass(b, beta, a, ctx->dX, ctx->dV, xs, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgR, s);
@@ -529,7 +529,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     if (ctx->opt.precision == MBD_PREC_FP64) {
         cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
         init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
-        chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, xs, s);
+        chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
     } else {   // FP32 factors, FP64-refined solutions
         cholesky_f32_from_f64(ctx->dM, ctx->sM, ld, nf1, ctx->sdinv, ctx->dstatus, s);
         init_rhs_identity(ctx->dB, ld, n, nf1, xs, s);
@@ -934,9 +934,9 @@ int mbdk_cholesky_f64(void *stream, double *A, long long ld, int batch, double *
 }
 
 int mbdk_chol_solve3_f64(void *stream, const double *L, long long ld, int batch, const double *dinv,
-                         double *X) {
-    if (ld <= 0 || ld % kTile || batch < 1 || !L || !dinv || !X) return MBD_ERR_INPUT;
-    chol_solve3_f64(L, ld, ld * ld, batch, dinv, X, 3 * ld, static_cast<cudaStream_t>(stream));
+                         double *X, double *work) {
+    if (ld <= 0 || ld % kTile || batch < 1 || !L || !dinv || !X || !work || work == X) return MBD_ERR_INPUT;
+    chol_solve3_f64(L, ld, ld * ld, batch, dinv, X, work, 3 * ld, static_cast<cudaStream_t>(stream));
     return cudaGetLastError() == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
 }
 

@@ -4,9 +4,10 @@
 // the GPU's memory to their own pool up front (an electronic-structure or MD code
 // with a fixed device-memory budget), and codes that must not pay the implicit
 // device-wide synchronisation that cudaMalloc and cudaFree can cause in the middle
-// of a time step.  For them this file keeps the factorisation's scratch (the
-// inverses of the 64x64 diagonal blocks of each Cholesky factor) in a file-scope
-// device array instead of caller- or library-allocated memory.
+// of a time step.  For them this file keeps the scratch of factor-and-solve (the
+// inverses of the 64x64 diagonal blocks of each Cholesky factor and the intermediate
+// of the triangular solves) in a file-scope device array instead of caller- or
+// library-allocated memory.
 //
 // The array is a fixed 16 MiB (2^21 doubles) that every GPU which loads the library
 // holds until the process exits.  All calls on a device share it: two calls whose
@@ -49,13 +50,14 @@ int scratch_address(double **out) {
 extern "C" int mbdk_cholesky_solve3_f64_noalloc(void *stream, double *A, long long ld, int batch,
                                                 double *X, int *status) {
     if (ld <= 0 || ld % mbdgb::kTile || batch < 1 || !A || !X || !status) return MBD_ERR_INPUT;
-    const long long need = static_cast<long long>(batch) * (ld / mbdgb::kTile) * 4096LL;
+    const long long dinv_n = static_cast<long long>(batch) * (ld / mbdgb::kTile) * 4096LL;
+    const long long need = dinv_n + static_cast<long long>(batch) * 3 * ld;
     if (need > kScratchDoubles) return MBD_ERR_SCRATCH_LIMIT;
     double *scratch = nullptr;
     const int rc = scratch_address(&scratch);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     mbdgb::cholesky_f64(A, ld, ld * ld, batch, scratch, status, s);
-    mbdgb::chol_solve3_f64(A, ld, ld * ld, batch, scratch, X, 3 * ld, s);
+    mbdgb::chol_solve3_f64(A, ld, ld * ld, batch, scratch, X, scratch + dinv_n, 3 * ld, s);
     return cudaGetLastError() == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
 }

@@ -52,7 +52,7 @@ def test_noalloc_rejects_requests_beyond_the_static_scratch():
     build.build()
     binding.load()
     dev = torch.device("cuda:0")
-    batch, ld = 513, 64     # 513 * 1 * 4096 doubles > 2^21
+    batch, ld = 512, 64     # 512 * (1 * 4096 + 3 * 64) doubles > 2^21
     A = torch.eye(ld, dtype=torch.float64, device=dev).repeat(batch, 1, 1).contiguous()
     X = torch.zeros(batch, ld, 3, dtype=torch.float64, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
