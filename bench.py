@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64"), default="bf16x3",
+    ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64"), default="tf32x3",
                     help="matrix-function arithmetic of the timed arm (the FP64 path is measured beside it)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison arm (0: skip)")
     ap.add_argument("--cpu-sample-atoms", type=int, default=250,

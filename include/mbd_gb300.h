@@ -58,7 +58,7 @@ typedef struct mbd_ctx mbd_ctx;
 
 /* Options.  Defaults (mbd_default_options): n_freq 15 (Sec. 3.3), beta 0.83, a 6
  * (Sec. 2.6), precision FP64, ns_tol 1e-8 (Frobenius norm of I - Z Y at which one
- * final Newton-Schulz step is taken), ns_max_iter 100. */
+ * final Newton-Schulz step is taken), ns_max_iter 100, tc_chunk_stages 2. */
 typedef struct {
     int n_freq;          /* Gauss-Legendre points of the Casimir-Polder integral     */
     double beta;         /* damping scale s_R of the Fermi function, Eq. (fermi-damping) */
@@ -66,6 +66,9 @@ typedef struct {
     int precision;       /* MBD_PREC_* (default FP64)                                  */
     double ns_tol;
     int ns_max_iter;
+    int tc_chunk_stages; /* mixed modes: K stages (32 TF32 or 64 bf16 elements each) per
+                            tensor-memory accumulation; the partial sums are added in FP32
+                            with round-to-nearest (default 2; 0 means 1)                  */
 } mbd_options;
 
 /* Fills *opt with the defaults above.  Returns MBD_ERR_INPUT if opt is NULL. */

@@ -51,10 +51,13 @@ int mbdk_chol_solve3_f64(void *stream, const double *L, long long ld, int batch,
  * (split of the result in the kind's part format, kinds 1 and 2, may be NULL) and CT (FP32 transpose of the result, mode 0
  * and M == N only, may be NULL) share the leading dimension ldc.  M and N multiples of 128, K of 64,
  * leading dimensions multiples of 8.  mode 0: all tiles; mode 2: upper tiles mirrored
- * (M == N, symmetric results).  err (device int) gets bit 8 set if a wait timed out. */
+ * (M == N, symmetric results).  chunk_stages: K stages (32 TF32 / 64 bf16 elements) per
+ * tensor-memory accumulation, partial sums added in FP32 with round-to-nearest (0: all of
+ * K in one accumulation).  err (device int) gets bit 8 set if a wait timed out. */
 int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float alpha, const void *A0,
                  const void *A1, long long lda, const void *B0, const void *B1, long long ldb, float beta,
-                 const float *D, float *C, void *C_hi, void *C_lo, float *CT, long long ldc, int *err);
+                 const float *D, float *C, void *C_hi, void *C_lo, float *CT, long long ldc, int chunk_stages,
+                 int *err);
 
 /* Allocation-free factor-and-solve (the paper has no counterpart; this serves callers
  * that cannot let a library allocate device memory -- codes that give the whole GPU to

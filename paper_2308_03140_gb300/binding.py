@@ -33,7 +33,8 @@ EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry
 
 class mbd_options(C.Structure):
     _fields_ = [("n_freq", C.c_int), ("beta", C.c_double), ("a", C.c_double),
-                ("precision", C.c_int), ("ns_tol", C.c_double), ("ns_max_iter", C.c_int)]
+                ("precision", C.c_int), ("ns_tol", C.c_double), ("ns_max_iter", C.c_int),
+                ("tc_chunk_stages", C.c_int)]
 
 
 class mbd_profile(C.Structure):
@@ -81,7 +82,7 @@ def load(path: str | None = None):
     L.mbdk_gemm_f64.argtypes = [vp, i, i, i, i, i, d, vp, ll, vp, ll, d, vp, ll, vp, ll]
     L.mbdk_cholesky_f64.argtypes = [vp, vp, ll, i, vp, vp]
     f = C.c_float
-    L.mbdk_gemm_tc.argtypes = [vp, i, i, i, i, i, f, vp, vp, ll, vp, vp, ll, f, vp, vp, vp, vp, vp, ll, vp]
+    L.mbdk_gemm_tc.argtypes = [vp, i, i, i, i, i, f, vp, vp, ll, vp, vp, ll, f, vp, vp, vp, vp, vp, ll, i, vp]
     L.mbdk_chol_solve3_f64.argtypes = [vp, vp, ll, i, vp, vp, vp]
     L.mbdk_cholesky_solve3_f64_noalloc.argtypes = [vp, vp, ll, i, vp, vp]
     for name in EXPORTS:
@@ -109,12 +110,15 @@ class MBD:
     """One library context on one CUDA device (mirrors mbd_calc_t of the paper's API)."""
 
     def __init__(self, device: int = 0, n_freq: int = 15, beta: float = 0.83, a: float = 6.0,
-                 ns_tol: float = 1e-8, ns_max_iter: int = 100, precision: int = MBD_PREC_FP64):
+                 ns_tol: float = 1e-8, ns_max_iter: int = 100, precision: int = MBD_PREC_FP64,
+                 tc_chunk_stages: int | None = None):
         self.lib = load()
         opt = mbd_options()
         self.lib.mbd_default_options(C.byref(opt))
         opt.n_freq, opt.beta, opt.a, opt.ns_tol, opt.ns_max_iter = n_freq, beta, a, ns_tol, ns_max_iter
         opt.precision = precision
+        if tc_chunk_stages is not None:
+            opt.tc_chunk_stages = tc_chunk_stages
         h = C.c_void_p()
         rc = self.lib.mbd_create(C.byref(h), device, C.byref(opt))
         if rc:
@@ -243,7 +247,7 @@ def mbdk_gemm_f64(A, B, C_out, alpha=1.0, beta=0.0, D=None, mode=0, trans_b=True
 
 
 def mbdk_gemm_tc(kind, A0, B0, C_out=None, A1=None, B1=None, alpha=1.0, beta=0.0, D=None, C_hi=None,
-                 C_lo=None, CT=None, mode=0, err=None, stream=None):
+                 C_lo=None, CT=None, mode=0, err=None, chunk_stages=0, stream=None):
     """Tensor-core GEMM C = alpha sum A_p B_p^T + beta D (see mbdk_gemm_tc in the header);
     torch CUDA tensors; returns the C return code."""
     L = load()
@@ -252,7 +256,7 @@ def mbdk_gemm_tc(kind, A0, B0, C_out=None, A1=None, B1=None, alpha=1.0, beta=0.0
     ref = C_out if C_out is not None else (CT if CT is not None else C_hi)
     return L.mbdk_gemm_tc(_stream(A0, stream), kind, mode, M, N, K, alpha, _tptr(A0), _tptr(A1), A0.stride(0),
                           _tptr(B0), _tptr(B1), B0.stride(0), beta, _tptr(D), _tptr(C_out), _tptr(C_hi),
-                          _tptr(C_lo), _tptr(CT), ref.stride(0), _tptr(err))
+                          _tptr(C_lo), _tptr(CT), ref.stride(0), chunk_stages, _tptr(err))
 
 
 def mbdk_cholesky_f64(A, dinv, status, stream=None):

@@ -48,6 +48,7 @@ struct TcArgs {
     int mode;
     int *err;
     double *C64 = nullptr;   // optional FP64 output accumulated in place: C64 += result
+    int chunk_stages = 0;    // K stages per TMEM accumulation (0: all of K in one)
 };
 cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_t s);
 // Mixed-precision helpers: Y = scale Q (FP32 and, if Yh, bf16 hi/lo) and Z = I;

@@ -7,12 +7,17 @@
 //   TF32   one product, operands stored as FP32 (kind::tf32 uses their top 19 bits);
 //   BF16x3 three products A_hi B_hi + A_hi B_lo + A_lo B_hi, operands stored as bf16
 //          hi/lo pairs (X = X_hi + X_lo), about 16 significant bits per product.
-// One CTA computes one 128x128 output tile.  Operand tiles of 128 rows x 128 bytes
-// are staged in shared memory by TMA (128-byte swizzle) through an mbarrier ring;
-// thread 0 issues the TMA loads, thread 32 issues tcgen05.mma into a 128-column TMEM
-// accumulator, and all four warps read it back (tcgen05.ld 32x32b) for the epilogue:
-// alpha/beta, FP32 and/or bf16 hi/lo outputs, optional transposed copies, optional
-// mirrored write of upper tiles (symmetric products), optional sum of (I - C)^2.
+// One CTA (6 warps) computes one 128x128 output tile.  Operand tiles of 128 rows x 128
+// bytes are staged in shared memory by TMA (128-byte swizzle) through an mbarrier ring;
+// warp 4 issues the TMA loads, warp 5 issues tcgen05.mma.  K is split into chunks of
+// `chunk_stages` stages, each accumulated afresh in one of two 128-column TMEM buffers;
+// warps 0-3 (one tile row per thread) read each finished chunk back (tcgen05.ld 32x32b)
+// and add it to FP32 registers with round-to-nearest while the next chunk accumulates.
+// The tensor core's own accumulation truncates: its bias grows with the number of terms
+// per accumulator, and in the Newton-Schulz iteration it breaks the coupling Y = Y0 Z.
+// Epilogue: alpha/beta, FP32 and/or split outputs, optional transposed copies, mirrored
+// writes of upper tiles (symmetric products), optional FP64 accumulation output and
+// optional sum of (I - C)^2.
 //
 // Every wait is bounded (clock64 budget); on a timeout the kernel raises the error
 // flag, stops issuing work, waits (bounded) for its own TMA copies and MMAs, frees its
@@ -141,11 +146,11 @@ struct TcCfg {
     static constexpr int STAGE_BYTES = TILES * TILE_BYTES;
     static constexpr int ELEM = KIND == 1 ? 2 : 4;
     static constexpr bool TF32 = KIND != 1;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512;
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
               const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs g,
               int tiles_n) {
@@ -154,7 +159,9 @@ __global__ void __launch_bounds__(128, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
     uint64_t *empty = full + Cfg::STAGES;
-    uint64_t *done = empty + Cfg::STAGES;
+    uint64_t *cfull = empty + Cfg::STAGES;   // [2] accumulator buffer holds a finished chunk
+    uint64_t *cfree = cfull + 2;             // [2] epilogue has drained the buffer
+    uint64_t *done = cfree + 2;              // every MMA issued has completed
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -174,6 +181,10 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&cfull[b], 1);
+            mbar_init(&cfree[b], 4);   // one arrival per epilogue warp
+        }
         mbar_init(done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -181,7 +192,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
-                     "r"(TN));
+                     "r"(2 * TN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     fence_before();
@@ -189,189 +200,228 @@ __global__ void __launch_bounds__(128, 1)
     fence_after();
     const uint32_t tmem = *tmem_slot;
     const int nk = static_cast<int>((static_cast<long long>(g.K) * Cfg::ELEM) / KB);
+    const int cs = (g.chunk_stages > 0 && g.chunk_stages < nk) ? g.chunk_stages : nk;   // stages per chunk
+    const int nchunks = (nk + cs - 1) / cs;
     constexpr int KELEM = KB / Cfg::ELEM;   // elements of K per stage
 
-    if (threadIdx.x == 0) {
-        // ---- TMA producer ----
-        int issued = 0;
-        for (int kt = 0; kt < nk && !*abort_flag; ++kt) {
-            const int s = kt % Cfg::STAGES;
-            const uint32_t ph = (kt / Cfg::STAGES) & 1;
-            if (kt >= Cfg::STAGES && !mbar_wait(&empty[s], ph ^ 1, g.err)) {
-                *abort_flag = 1;
-                break;
+    if (warp == 4) {
+        // ---- TMA producer (one thread) ----
+        if (lane == 0) {
+            int issued = 0;
+            for (int kt = 0; kt < nk && !*abort_flag; ++kt) {
+                const int s = kt % Cfg::STAGES;
+                const uint32_t ph = (kt / Cfg::STAGES) & 1;
+                if (kt >= Cfg::STAGES && !mbar_wait(&empty[s], ph ^ 1, g.err)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                uint8_t *st = smem + s * Cfg::STAGE_BYTES;
+                mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+                const int kx = kt * KELEM;
+                tma_load_2d(st, &mA0, kx, tm * TM, &full[s]);
+                tma_load_2d(st + TILE_BYTES, &mB0, kx, tn * TN, &full[s]);
+                if (Cfg::TILES == 4) {
+                    tma_load_2d(st + 2 * TILE_BYTES, &mA1, kx, tm * TM, &full[s]);
+                    tma_load_2d(st + 3 * TILE_BYTES, &mB1, kx, tn * TN, &full[s]);
+                }
+                issued = kt + 1;
             }
-            uint8_t *st = smem + s * Cfg::STAGE_BYTES;
-            mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
-            const int kx = kt * KELEM;
-            tma_load_2d(st, &mA0, kx, tm * TM, &full[s]);
-            tma_load_2d(st + TILE_BYTES, &mB0, kx, tn * TN, &full[s]);
-            if (Cfg::TILES == 4) {
-                tma_load_2d(st + 2 * TILE_BYTES, &mA1, kx, tm * TM, &full[s]);
-                tma_load_2d(st + 3 * TILE_BYTES, &mB1, kx, tn * TN, &full[s]);
+            if (*abort_flag) {   // let this CTA's copies land before shared memory is released
+                for (int kt = (issued > Cfg::STAGES ? issued - Cfg::STAGES : 0); kt < issued; ++kt)
+                    mbar_wait(&full[kt % Cfg::STAGES], (kt / Cfg::STAGES) & 1, g.err);
             }
-            issued = kt + 1;
         }
-        if (*abort_flag) {   // let this CTA's copies land before shared memory is released
-            for (int kt = (issued > Cfg::STAGES ? issued - Cfg::STAGES : 0); kt < issued; ++kt)
-                mbar_wait(&full[kt % Cfg::STAGES], (kt / Cfg::STAGES) & 1, g.err);
+    } else if (warp == 5) {
+        // ---- MMA issuer (one thread): chunk c accumulates afresh into buffer c & 1 ----
+        if (lane == 0) {
+            for (int kt = 0; kt < nk && !*abort_flag; ++kt) {
+                const int c = kt / cs, buf = c & 1;
+                if (kt % cs == 0 && c >= 2 && !mbar_wait(&cfree[buf], ((c >> 1) - 1) & 1, g.err)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const int s = kt % Cfg::STAGES;
+                if (!mbar_wait(&full[s], (kt / Cfg::STAGES) & 1, g.err)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t base = su32(smem + s * Cfg::STAGE_BYTES);
+                const uint32_t dt = tmem + static_cast<uint32_t>(buf * TN);
+#pragma unroll
+                for (int k = 0; k < KB / 32; ++k) {   // 32 bytes of K per instruction
+                    const uint64_t a0 = sdesc(base + k * 32), b0 = sdesc(base + TILE_BYTES + k * 32);
+                    mma<Cfg::TF32>(dt, a0, b0, (kt % cs != 0 || k != 0) ? 1u : 0u);
+                    if (Cfg::PAIRS == 3) {
+                        const uint64_t a1 = sdesc(base + 2 * TILE_BYTES + k * 32);
+                        const uint64_t b1 = sdesc(base + 3 * TILE_BYTES + k * 32);
+                        mma<Cfg::TF32>(dt, a0, b1, 1u);
+                        mma<Cfg::TF32>(dt, a1, b0, 1u);
+                    }
+                }
+                mma_commit(&empty[s]);                              // stage free once read
+                if (kt % cs == cs - 1 || kt == nk - 1) mma_commit(&cfull[buf]);   // chunk finished
+            }
+            mma_commit(done);
         }
-    } else if (threadIdx.x == 32) {
-        // ---- MMA issuer ----
-        for (int kt = 0; kt < nk && !*abort_flag; ++kt) {
-            const int s = kt % Cfg::STAGES;
-            if (!mbar_wait(&full[s], (kt / Cfg::STAGES) & 1, g.err)) {
+    } else {
+        // ---- epilogue warps 0-3: thread = row of the tile; chunk sums added in FP32 with
+        // round-to-nearest (the tensor core's own accumulation truncates) ----
+        float acc[TN];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[j] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int buf = c & 1;
+            ok = mbar_wait(&cfull[buf], (c >> 1) & 1, g.err) && !*abort_flag;
+            ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+            if (!ok) {
                 *abort_flag = 1;
                 break;
             }
             fence_after();
-            const uint32_t base = su32(smem + s * Cfg::STAGE_BYTES);
+            const uint32_t tb = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(buf * TN);
 #pragma unroll
-            for (int k = 0; k < KB / 32; ++k) {   // 32 bytes of K per instruction
-                const uint64_t a0 = sdesc(base + k * 32), b0 = sdesc(base + TILE_BYTES + k * 32);
-                mma<Cfg::TF32>(tmem, a0, b0, (kt | k) != 0);
-                if (Cfg::PAIRS == 3) {
-                    const uint64_t a1 = sdesc(base + 2 * TILE_BYTES + k * 32);
-                    const uint64_t b1 = sdesc(base + 3 * TILE_BYTES + k * 32);
-                    mma<Cfg::TF32>(tmem, a0, b1, 1u);
-                    mma<Cfg::TF32>(tmem, a1, b0, 1u);
-                }
+            for (int q = 0; q < TN / 32; ++q) {
+                uint32_t r[32];
+                tmem_ld32(tb + q * 32, r);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(r[j]);
             }
-            mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
+            fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&cfree[buf])) : "memory");
         }
-        mma_commit(done);            // arrives when every MMA issued above has completed
-    }
-    __syncwarp();
-    // ---- epilogue: TMEM -> registers -> global ----
-    bool ok = mbar_wait(done, 0, g.err);
-    ok = __all_sync(0xffffffffu, ok && !*abort_flag);   // tcgen05.ld below is warp-collective
-    fence_after();
-    if (ok) {
-        const int row = warp * 32 + lane;
-        const long long m = static_cast<long long>(tm) * TM + row;
-        const bool mirror = (g.mode == 2) && (tm != tn);
-        double rs = 0.0;
-#pragma unroll 1
-        for (int c0 = 0; c0 < TN; c0 += 32) {
-            uint32_t r[32];
-            tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, r);
-            const long long n0 = static_cast<long long>(tn) * TN + c0;
-            float v[32];
+        if (ok) {
+            const int row = warp * 32 + lane;
+            const long long m = static_cast<long long>(tm) * TM + row;
+            const bool mirror = (g.mode == 2) && (tm != tn);
+            const bool diag = (g.mode == 2) && (tm == tn);
+            double rs = 0.0;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = g.alpha * __uint_as_float(r[j]);
-            if (g.beta != 0.f) {
-                const float4 *dp = reinterpret_cast<const float4 *>(g.D + m * g.ld + n0);
+            for (int c0 = 0; c0 < TN; c0 += 16) {
+                const long long n0 = static_cast<long long>(tn) * TN + c0;
+                float v[16];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float4 d = dp[q];
-                    v[4 * q] += g.beta * d.x;
-                    v[4 * q + 1] += g.beta * d.y;
-                    v[4 * q + 2] += g.beta * d.z;
-                    v[4 * q + 3] += g.beta * d.w;
-                }
-            }
-            if (g.resid && m < g.nvalid) {
+                for (int j = 0; j < 16; ++j) v[j] = g.alpha * acc[c0 + j];
+                if (g.beta != 0.f) {
+                    const float4 *dp = reinterpret_cast<const float4 *>(g.D + m * g.ld + n0);
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (n0 + j < g.nvalid) {
-                        const double e = (m == n0 + j ? 1.0 : 0.0) - static_cast<double>(v[j]);
-                        rs += e * e;
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 d = dp[q];
+                        v[4 * q] += g.beta * d.x;
+                        v[4 * q + 1] += g.beta * d.y;
+                        v[4 * q + 2] += g.beta * d.z;
+                        v[4 * q + 3] += g.beta * d.w;
                     }
-            }
-            // hi/lo split of the result for the next product's operands: bf16 pairs packed
-            // two per word (BF16x3), or TF32-rounded hi and FP32 remainder (TF32x3).
-            uint32_t hw[KIND == 2 ? 32 : 16], lw[KIND == 2 ? 32 : 16];
-            if (g.Ch || g.CTh) {
-                if (KIND == 2) {
+                }
+                if (g.resid && m < g.nvalid) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {   // both parts rounded to nearest TF32: unbiased
-                        uint32_t h, l;
-                        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v[j]));
-                        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(v[j] - __uint_as_float(h)));
-                        hw[j] = h;
-                        lw[j] = l;
+                    for (int j = 0; j < 16; ++j)
+                        if (n0 + j < g.nvalid) {
+                            const double e = (m == n0 + j ? 1.0 : 0.0) - static_cast<double>(v[j]);
+                            rs += e * e;
+                        }
+                }
+                if (g.C64) {   // FP64 accumulation output (caller splits K: C64 += result)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (diag && n0 + j < m) continue;
+                        g.C64[m * g.ld + n0 + j] += static_cast<double>(v[j]);
+                        if ((mirror || diag) && n0 + j != m) g.C64[(n0 + j) * g.ld + m] += static_cast<double>(v[j]);
+                    }
+                }
+                // split of the result into the next product's operand parts: bf16 pairs
+                // packed two per word (BF16x3), or TF32 hi and TF32 remainder (TF32x3),
+                // each rounded to nearest
+                uint32_t hw[KIND == 2 ? 16 : 8], lw[KIND == 2 ? 16 : 8];
+                if (g.Ch || g.CTh) {
+                    if (KIND == 2) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            uint32_t h, l;
+                            asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v[j]));
+                            asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(v[j] - __uint_as_float(h)));
+                            hw[j] = h;
+                            lw[j] = l;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
+                            const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+                            const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+                            hw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
+                                    (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+                            lw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
+                                    (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+                        }
+                    }
+                }
+                // Symmetric products (mode 2): upper tiles are mirrored into the lower half;
+                // diagonal tiles keep their upper triangle and mirror it, so the result is
+                // exactly symmetric whatever order the tensor cores summed in.
+                if (!diag) {
+                    if (g.C) {
+                        float4 *cp = reinterpret_cast<float4 *>(g.C + m * g.ld + n0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    }
+                    if (g.Ch) {
+                        constexpr int NV = KIND == 2 ? 4 : 2;   // uint4 vectors per 16 elements
+                        uint4 *hp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Ch) + (m * g.ld + n0) * Cfg::ELEM);
+                        uint4 *lp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Cl) + (m * g.ld + n0) * Cfg::ELEM);
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) {
+                            hp[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                            lp[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                        }
                     }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
-                        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
-                        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
-                        hw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
-                                (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
-                        lw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
-                                (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+                    for (int j = 0; j < 16; ++j) {
+                        if (n0 + j < m) continue;
+                        const long long off = m * g.ld + n0 + j;
+                        if (g.C) g.C[off] = v[j];
+                        if (g.Ch) {
+                            store_part<KIND>(g.Ch, off, hw, j);
+                            store_part<KIND>(g.Cl, off, lw, j);
+                        }
+                    }
+                }
+                // transposed copies (coalesced across the warp: consecutive rows m).  For a
+                // mirrored tile of a symmetric product the transpose goes into C itself.
+                const bool into_c = mirror || diag;
+                float *Tf = into_c ? g.C : g.CT;
+                void *Th = into_c ? g.Ch : g.CTh, *Tl = into_c ? g.Cl : g.CTl;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (diag && n0 + j <= m) continue;
+                    const long long off = (n0 + j) * g.ld + m;
+                    if (Tf) Tf[off] = v[j];
+                    if (Th) {
+                        store_part<KIND>(Th, off, hw, j);
+                        store_part<KIND>(Tl, off, lw, j);
                     }
                 }
             }
-            // FP64 accumulation output (K split into chunks by the caller: C64 += result)
-            if (g.C64) {
-                const bool dg = (g.mode == 2) && (tm == tn);
+            if (g.resid) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (dg && n0 + j < m) continue;
-                    g.C64[m * g.ld + n0 + j] += static_cast<double>(v[j]);
-                    if ((mirror || dg) && n0 + j != m) g.C64[(n0 + j) * g.ld + m] += static_cast<double>(v[j]);
-                }
+                for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+                if (lane == 0 && rs != 0.0) atomicAdd(g.resid, rs);
             }
-            // Symmetric products (mode 2): upper tiles are mirrored into the lower half;
-            // diagonal tiles keep their upper triangle and mirror it, so the result is
-            // exactly symmetric whatever order the tensor cores summed in.
-            const bool diag = (g.mode == 2) && (tm == tn);
-            // row-major outputs
-            if (!diag) {
-                if (g.C) {
-                    float4 *cp = reinterpret_cast<float4 *>(g.C + m * g.ld + n0);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                }
-                if (g.Ch) {
-                    constexpr int NV = KIND == 2 ? 8 : 4;   // uint4 vectors per 32 elements
-                    uint4 *hp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Ch) + (m * g.ld + n0) * Cfg::ELEM);
-                    uint4 *lp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Cl) + (m * g.ld + n0) * Cfg::ELEM);
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) {
-                        hp[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
-                        lp[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (n0 + j < m) continue;
-                    const long long off = m * g.ld + n0 + j;
-                    if (g.C) g.C[off] = v[j];
-                    if (g.Ch) {
-                        store_part<KIND>(g.Ch, off, hw, j);
-                        store_part<KIND>(g.Cl, off, lw, j);
-                    }
-                }
-            }
-            // transposed copies (coalesced across the warp: consecutive rows m).  For a
-            // mirrored tile of a symmetric product the transpose goes into C itself.
-            const bool into_c = mirror || diag;
-            float *Tf = into_c ? g.C : g.CT;
-            void *Th = into_c ? g.Ch : g.CTh, *Tl = into_c ? g.Cl : g.CTl;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (diag && n0 + j <= m) continue;
-                const long long off = (n0 + j) * g.ld + m;
-                if (Tf) Tf[off] = v[j];
-                if (Th) {
-                    store_part<KIND>(Th, off, hw, j);
-                    store_part<KIND>(Tl, off, lw, j);
-                }
-            }
-        }
-        if (g.resid) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-            if (lane == 0 && rs != 0.0) atomicAdd(g.resid, rs);
         }
     }
+    __syncwarp();
     fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TN));
+    if (warp == 0) {
+        // every MMA this CTA issued must have completed before its tensor memory is freed
+        if (lane == 0) mbar_wait(done, 0, g.err);
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * TN));
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -426,7 +476,7 @@ cudaError_t launch_tc(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     const int tmt = g.M / TM, tnt = g.N / TN;
     const int grid = g.mode == 0 ? tmt * tnt : tmt * (tmt + 1) / 2;
     count_launches(1);
-    k_tc_gemm<KIND><<<grid, 128, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt);
+    k_tc_gemm<KIND><<<grid, 192, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt);
     return cudaGetLastError();
 }
 

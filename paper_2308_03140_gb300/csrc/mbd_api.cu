@@ -24,7 +24,6 @@ using namespace mbdgb;
 namespace {
 std::atomic<long long> g_launches{0};
 constexpr int kRefineSteps = 3;   // iterative-refinement steps of the mixed screening solves
-constexpr long long kCorrChunk = 256;   // K per tensor-core accumulation in the FP64 correction
 }  // namespace
 
 void mbdgb::count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -359,9 +358,11 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
     MixMat Y2{ctx->fY2, ctx->hY2[0], ctx->hY2[1]}, Z2{ctx->fZ2, ctx->hZ2[0], ctx->hZ2[1]};
     MixMat P{ctx->fP, ctx->hP[0], ctx->hP[1]}, PT{ctx->fPT, ctx->hPT[0], ctx->hPT[1]};
     mixed_init(kind, ctx->dQ, ld, 1.0 / sc, Y.f, split ? Y.h : nullptr, Y.l, Z.f, Z.h, Z.l, s);
-    auto tc = [&](const TcOperands &op, const TcArgs &g, double flops) -> int {
+    const int cstages = ctx->opt.tc_chunk_stages > 0 ? ctx->opt.tc_chunk_stages : 1;
+    auto tc = [&](const TcOperands &op, TcArgs g, double flops) -> int {
         Span sp;
         sp.flops = flops;
+        g.chunk_stages = cstages;
         mark(ctx, s, sp.a);
         const cudaError_t e = tc_gemm(kind, op, g, s);
         mark(ctx, s, sp.b);
@@ -442,10 +443,10 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
     // ---- correction ----
     // With Zs ~ (Q/s)^{-1/2} (FP32 values of the iteration), Vs = (Q/s) Zs, Ws = Zs Vs:
     // Tr Q^{1/2} ~ sqrt(s) (3 Tr Vs - sum Vs o Ws)/2, second order in the error of Zs.
-    // Tr Vs = sum (Q/s) o Zs is an exact FP64 dot.  Vs and Ws come from TF32x3
-    // tensor-core products with round-to-nearest operand parts, K split into chunks of
-    // kCorrChunk summed in FP64: the tensor core's FP32 accumulation truncates, and its
-    // bias grows with the number of terms summed in one accumulator.
+    // Tr Vs = sum (Q/s) o Zs is an exact FP64 dot.  Vs and Ws are FP64 sums of exact
+    // diagonal scalings and TF32x3 tensor-core products of the off-diagonal parts (no
+    // accumulator mixes a dominant term with many small ones; chunk sums in FP32 with
+    // round-to-nearest), each product added once into its FP64 result.
     mark(ctx, s, e_corr);
     {
         // FP32 workspace: the iteration's matrices are free now.  Parts of offdiag(Q/s) and of
@@ -455,28 +456,23 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
         float *VTh = reinterpret_cast<float *>(ctx->dY2), *VTl = VTh + ld * ld;
         double *V64 = ctx->dP, *W64 = ctx->dZ2;
         const float *Zs = Z.f;
-        // The diagonal scalings are exact FP64 elementwise products; the tensor cores only
-        // add the off-diagonal parts, so no accumulator sums a dominant term with many small
-        // ones: Vs = diag(Q/s) Zs + offdiag(Q/s) Zs, Ws = diag(Zs) Vs + offdiag(Zs) Vs.
         split_tf32_f64(ctx->dQ, ld, 1.0 / sc, 1, Qh, Ql, s);
         split_tf32_f32(Zs, ld, 0, Zs_h, Zs_l, s);
         diag_scale_rows_f64(ctx->dQ, Zs, ld, 1.0 / sc, V64, s);
-        for (long long k0 = 0; k0 < ld; k0 += kCorrChunk) {   // Vs += offdiag(Q/s)[:, k] Zs[k, :]
-            const int kc = static_cast<int>(std::min<long long>(kCorrChunk, ld - k0));
-            TcOperands op{Qh + k0, Ql + k0, Zs_h + k0, Zs_l + k0, ld, ld};
-            TcArgs g{M, M, kc, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                     0, 0, ctx->dstatus, V64};
+        {   // Vs += offdiag(Q/s) Zs = NT(offdiag(Q/s), Zs) (Zs symmetric)
+            TcOperands op{Qh, Ql, Zs_h, Zs_l, ld, ld};
+            TcArgs g{M, M, M, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     0, 0, ctx->dstatus, V64, cstages};
             const cudaError_t e = tc_gemm(2, op, g, s);
             if (e != cudaSuccess) return cuda_fail(ctx, "correction", e);
         }
         split_tf32_f64_t(V64, ld, 1.0, VTh, VTl, s);
         split_tf32_f32(Zs, ld, 1, Zh, Zl, s);
         diag_scale_rows_f32(Zs, V64, ld, W64, s);
-        for (long long k0 = 0; k0 < ld; k0 += kCorrChunk) {   // Ws += offdiag(Zs)[:, k] Vs[k, :]
-            const int kc = static_cast<int>(std::min<long long>(kCorrChunk, ld - k0));
-            TcOperands op{Zh + k0, Zl + k0, VTh + k0, VTl + k0, ld, ld};
-            TcArgs g{M, M, kc, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                     0, 0, ctx->dstatus, W64};
+        {   // Ws += offdiag(Zs) Vs = NT(offdiag(Zs), Vs^T)
+            TcOperands op{Zh, Zl, VTh, VTl, ld, ld};
+            TcArgs g{M, M, M, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     0, 0, ctx->dstatus, W64, cstages};
             const cudaError_t e = tc_gemm(2, op, g, s);
             if (e != cudaSuccess) return cuda_fail(ctx, "correction", e);
         }
@@ -701,6 +697,7 @@ int mbd_default_options(mbd_options *opt) {
     opt->precision = MBD_PREC_FP64;
     opt->ns_tol = 1e-8;
     opt->ns_max_iter = 100;
+    opt->tc_chunk_stages = 2;
     return MBD_OK;
 }
 
@@ -710,7 +707,7 @@ int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt) {
     mbd_options o;
     if (opt) o = *opt; else mbd_default_options(&o);
     if (o.n_freq < 1 || o.n_freq + 1 > kMaxFreq || !(o.beta > 0) || !(o.a > 0) || o.ns_max_iter < 1 ||
-        !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_TF32X3)
+        !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_TF32X3 || o.tc_chunk_stages < 0)
         return MBD_ERR_INPUT;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev)
@@ -918,10 +915,13 @@ int mbdk_gemm_f64(void *stream, int trans_b, int mode, int M, int N, int K, doub
 
 int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float alpha, const void *A0,
                  const void *A1, long long lda, const void *B0, const void *B1, long long ldb, float beta,
-                 const float *D, float *C, void *C_hi, void *C_lo, float *CT, long long ldc, int *err) {
-    if (!A0 || !B0 || (kind != 0 && (!A1 || !B1)) || ((C_hi != nullptr) != (C_lo != nullptr))) return MBD_ERR_INPUT;
+                 const float *D, float *C, void *C_hi, void *C_lo, float *CT, long long ldc, int chunk_stages,
+                 int *err) {
+    if (!A0 || !B0 || (kind != 0 && (!A1 || !B1)) || ((C_hi != nullptr) != (C_lo != nullptr)) || chunk_stages < 0)
+        return MBD_ERR_INPUT;
     TcOperands op{A0, kind != 0 ? A1 : A0, B0, kind != 0 ? B1 : B0, lda, ldb};
-    TcArgs g{M, N, K, alpha, beta, D, ldc, C, C_hi, C_lo, CT, nullptr, nullptr, nullptr, 0, mode, err};
+    TcArgs g{M, N, K, alpha, beta, D, ldc, C, C_hi, C_lo, CT, nullptr, nullptr, nullptr, 0, mode, err, nullptr,
+             chunk_stages};
     const cudaError_t e = tc_gemm(kind, op, g, static_cast<cudaStream_t>(stream));
     if (e == cudaErrorInvalidValue) return MBD_ERR_INPUT;
     return e == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;

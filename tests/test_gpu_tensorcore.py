@@ -35,9 +35,10 @@ def _split(x, kind=1):
 TOL = {0: 2e-3, 1: 5e-5, 2: 3e-5}
 
 
+@pytest.mark.parametrize("chunk", [0, 1, 3])
 @pytest.mark.parametrize("kind", [0, 1, 2])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 512), (384, 128, 1024)])
-def test_tc_gemm_full(kind, M, N, K):
+def test_tc_gemm_full(kind, M, N, K, chunk):
     import torch
     dev = torch.device("cuda:0")
     g = torch.Generator(device="cpu").manual_seed(M * 7 + N + K + kind)
@@ -48,12 +49,13 @@ def test_tc_gemm_full(kind, M, N, K):
     CT = torch.full((N, M), float("nan"), dtype=torch.float32, device=dev) if M == N else None
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     if kind == 0:
-        rc = binding.mbdk_gemm_tc(0, A.to(dev), B.to(dev), C, alpha=0.75, beta=-0.5, D=D.to(dev), CT=CT, err=err)
+        rc = binding.mbdk_gemm_tc(0, A.to(dev), B.to(dev), C, alpha=0.75, beta=-0.5, D=D.to(dev), CT=CT, err=err,
+                                  chunk_stages=chunk)
     else:
         Ah, Al = _split(A, kind)
         Bh, Bl = _split(B, kind)
         rc = binding.mbdk_gemm_tc(kind, Ah.to(dev), Bh.to(dev), C, A1=Al.to(dev), B1=Bl.to(dev), alpha=0.75,
-                                  beta=-0.5, D=D.to(dev), CT=CT, err=err)
+                                  beta=-0.5, D=D.to(dev), CT=CT, err=err, chunk_stages=chunk)
     torch.cuda.synchronize()
     assert rc == 0 and err.item() == 0
     ref = 0.75 * (A.double() @ B.double().T) - 0.5 * D.double()
@@ -77,11 +79,11 @@ def test_tc_gemm_symmetric_mirror_and_split_output(kind):
     Cl = torch.zeros(n, n, dtype=pdt, device=dev) if kind else None
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     if kind == 0:
-        rc = binding.mbdk_gemm_tc(0, S.to(dev), S.to(dev), C, mode=2, err=err)
+        rc = binding.mbdk_gemm_tc(0, S.to(dev), S.to(dev), C, mode=2, err=err, chunk_stages=1)
     else:
         Sh, Sl = _split(S, kind)
         rc = binding.mbdk_gemm_tc(kind, Sh.to(dev), Sh.to(dev), C, A1=Sl.to(dev), B1=Sl.to(dev), C_hi=Ch, C_lo=Cl,
-                                  mode=2, err=err)
+                                  mode=2, err=err, chunk_stages=1)
     torch.cuda.synchronize()
     assert rc == 0 and err.item() == 0
     Cc = C.cpu()
@@ -117,12 +119,13 @@ def _eval(sysm, precision):
 # iteration on 10-bit products, whose rounding breaks the coupling invariant Y = Y0 Z by
 # more than the FP64 correction can remove (a commutator error), so it is held to a
 # looser bound and reported, not used for the headline.
-# Measured (GB300, N = 500 and 2000): |dE|/N = 3.4e-6 / 4e-9 / 3e-9 Ha/atom for TF32 /
-# BF16x3 / TF32x3; force errors 2.5 / 0.25 / 0.18 (N = 500) and 20 / 0.5 / 0.47 (N = 2000)
-# of the largest force.  Forces of the mixed modes come from the tensor-core Q^{-1/2},
-# whose commutator drift enters the gradient at first order (the energy only at second).
+# Measured (GB300, 2-stage chunks, N = 500 / 2000): |dE|/N about 3.4e-6 (TF32), 6e-9
+# (BF16x3), 6e-9 (TF32x3) Ha/atom; largest force error 2.5 / 0.09 / 0.008 (N = 500) and
+# 20 / 0.17 / 0.011 (N = 2000) of the largest force.  Forces of the mixed modes come from
+# the tensor-core Q^{-1/2}, whose commutator drift enters the gradient at first order (the
+# energy only at second).
 E_BOUND = {binding.MBD_PREC_TF32: 2e-5, binding.MBD_PREC_BF16X3: 1e-6, binding.MBD_PREC_TF32X3: 1e-6}
-F_BOUND = {binding.MBD_PREC_TF32: 50.0, binding.MBD_PREC_BF16X3: 1.0, binding.MBD_PREC_TF32X3: 1.0}
+F_BOUND = {binding.MBD_PREC_TF32: 50.0, binding.MBD_PREC_BF16X3: 0.5, binding.MBD_PREC_TF32X3: 0.1}
 
 
 @pytest.mark.parametrize("precision", [binding.MBD_PREC_TF32, binding.MBD_PREC_BF16X3, binding.MBD_PREC_TF32X3])
