@@ -38,6 +38,11 @@ FP64_OVER_BF16 = 1.25 / 2250.0
 # (profiles/k_gemm_nn_finite2000.md), valid while k_dense.cu keeps the captured hash.
 GEMM_NN_TRAFFIC = {"bytes": 6.309694e9 + 0.289604352e9, "k_dense_sha16": "b0c1ebaacc02cc34",
                    "source": "profiles/k_gemm_nn_finite2000.md"}
+# DRAM bytes per k_tc_gemm launch (a symmetric TF32x3 Newton-Schulz product of the
+# 6000x6000 case) from the committed capture (profiles/k_tc_gemm_finite2000.md),
+# valid while k_tc.cu keeps the captured hash.
+TC_GEMM_TRAFFIC = {"bytes": 2.105201e9 + 0.413660928e9, "k_tc_sha16": "966f5e0533c95e2a",
+                   "launch": "symmetric Z' product, 1128 CTAs", "source": "profiles/k_tc_gemm_finite2000.md"}
 
 
 def parse():
@@ -287,42 +292,66 @@ def run_ours(args):
     gemm_launches = sum(p["gemm_launches"] for p in profs)
     launches = sum(p["launches"] for p in profs)
     peaks = measured_peaks()
-    if peaks and peaks.get("bf16_tflops_sustained"):
-        peak = peaks["bf16_tflops_sustained"] * FP64_OVER_BF16
-        peak_src = "of measured: bf16_tflops_sustained x nominal FP64/BF16 ratio (1.25/2250)"
-    else:
-        peak = 1700.0 * FP64_OVER_BF16
-        peak_src = "of fallback: 1.7 PFLOP/s sustained bf16 x nominal FP64/BF16 ratio"
-    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
+    bf16_sus = peaks.get("bf16_tflops_sustained") if peaks else None
+    src = "of measured" if bf16_sus else "of fallback"
+    bf16_sus = bf16_sus or 1700.0
     import hashlib
-    cur = hashlib.sha256(open(os.path.join(ROOT, "paper_2308_03140_gb300", "csrc", "k_dense.cu"), "rb").read())
-    traffic = GEMM_NN_TRAFFIC["bytes"] if cur.hexdigest()[:16] == GEMM_NN_TRAFFIC["k_dense_sha16"] else None
+    if precision == binding.MBD_PREC_FP64:
+        # dominant kernel: the FP64 tensor-path Newton-Schulz products
+        kernel = "k_gemm_nn (FP64 mma.sync m8n8k4, Newton-Schulz products)"
+        k_ms, k_flops, k_launches = gemm_ms, gemm_flops, gemm_launches
+        peak = bf16_sus * FP64_OVER_BF16
+        peak_src = f"{src}: bf16_tflops_sustained x nominal FP64/BF16 ratio (1.25/2250)"
+        cur = hashlib.sha256(open(os.path.join(ROOT, "paper_2308_03140_gb300", "csrc", "k_dense.cu"), "rb").read())
+        traffic = GEMM_NN_TRAFFIC["bytes"] if cur.hexdigest()[:16] == GEMM_NN_TRAFFIC["k_dense_sha16"] else None
+    else:
+        # tcgen05 GEMMs of the iteration and of the correction
+        kernel = "k_tc_gemm (tcgen05 + TMA + TMEM; Newton-Schulz and correction products)"
+        k_ms = sum(p["tc_ms"] for p in profs)
+        k_flops = sum(p["tc_flops"] for p in profs)
+        k_launches = sum(p["tc_launches"] for p in profs)
+        per_kind = {binding.MBD_PREC_TF32: (0.5, 1, "TF32"), binding.MBD_PREC_BF16X3: (1.0, 3, "BF16x3"),
+                    binding.MBD_PREC_TF32X3: (0.5, 3, "TF32x3")}[precision]
+        peak = bf16_sus * per_kind[0] / per_kind[1]
+        peak_src = (f"{src}: bf16_tflops_sustained x nominal {per_kind[2][:4]}/BF16 rate ({per_kind[0]}) / "
+                    f"{per_kind[1]} tensor products per algorithmic product")
+        cur = hashlib.sha256(open(os.path.join(ROOT, "paper_2308_03140_gb300", "csrc", "k_tc.cu"), "rb").read())
+        traffic = (TC_GEMM_TRAFFIC["bytes"] if precision == binding.MBD_PREC_TF32X3 and
+                   cur.hexdigest()[:16] == TC_GEMM_TRAFFIC["k_tc_sha16"] else None)
+    achieved = k_flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
     n = 3 * N
-    exec_flops = sum(p["gemm_flops"] + p["screening_flops"] for p in profs) / args.steps
+    exec_flops = sum(p["gemm_flops"] + p["tc_flops"] + p["screening_flops"] for p in profs) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == binding.MBD_PREC_FP64 else
+        f"{args.precision}+f32+f64",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_atoms": N, "matrix_order": n, "n_freq": 15,
-                   "precision": "fp64", "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "precision": args.precision, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: 16 screening matrices + 5 Newton-Schulz matrices of "
                          f"{8 * n * n / 1e6:.0f} MB each per step"},
         "tflops": exec_flops / (ms / args.steps / 1e3) / 1e12,
-        "roofline": {"kernel": "k_gemm_nn (FP64 mma.sync m8n8k4, Newton-Schulz products)", "bound": "tensor",
+        "roofline": {"kernel": kernel, "bound": "tensor",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "traffic_unit": "bytes per launch (ncu capture)",
+                     "traffic_launch": (None if traffic is None else
+                                        (TC_GEMM_TRAFFIC if precision != binding.MBD_PREC_FP64 else
+                                         GEMM_NN_TRAFFIC)["source"]),
                      "peak_source": peak_src,
-                     "launches_per_step": gemm_launches / args.steps,
-                     "avg_launch_ms": gemm_ms / max(gemm_launches, 1),
-                     "flops_per_launch": gemm_flops / max(gemm_launches, 1),
-                     "share_of_step": gemm_ms / ms if ms > 0 else None},
+                     "launches_per_step": k_launches / args.steps,
+                     "avg_launch_ms": k_ms / max(k_launches, 1),
+                     "flops_per_launch": k_flops / max(k_launches, 1),
+                     "share_of_step": k_ms / ms if ms > 0 else None},
+        "fp64_path": fp64,
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": launches,
         "energy_ha": E, "energy_per_atom_ha": E / N, "ns_iterations": st["ns_iterations"],
         "stage_ms": {k: statistics.mean(p[k] for p in profs) for k in
-                     ("screening_ms", "newton_schulz_ms", "gradient_ms", "total_ms")},
+                     ("screening_ms", "newton_schulz_ms", "correction_ms", "gradient_ms", "total_ms")},
+        "ns_residual": st["ns_residual"], "correction_residual": st["correction_residual"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_atoms, N)

@@ -459,12 +459,20 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
         split_tf32_f64(ctx->dQ, ld, 1.0 / sc, 1, Qh, Ql, s);
         split_tf32_f32(Zs, ld, 0, Zs_h, Zs_l, s);
         diag_scale_rows_f64(ctx->dQ, Zs, ld, 1.0 / sc, V64, s);
+        auto tc64 = [&](const TcOperands &op, const TcArgs &g) -> int {   // timed like the iteration's products
+            Span sp;
+            sp.flops = flops_full;
+            mark(ctx, s, sp.a);
+            const cudaError_t e = tc_gemm(2, op, g, s);
+            mark(ctx, s, sp.b);
+            if (ctx->profiling) spans.push_back(sp);
+            return e == cudaSuccess ? MBD_OK : cuda_fail(ctx, "correction", e);
+        };
         {   // Vs += offdiag(Q/s) Zs = NT(offdiag(Q/s), Zs) (Zs symmetric)
             TcOperands op{Qh, Ql, Zs_h, Zs_l, ld, ld};
             TcArgs g{M, M, M, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                      0, 0, ctx->dstatus, V64, cstages};
-            const cudaError_t e = tc_gemm(2, op, g, s);
-            if (e != cudaSuccess) return cuda_fail(ctx, "correction", e);
+            if (int rc = tc64(op, g)) return rc;
         }
         split_tf32_f64_t(V64, ld, 1.0, VTh, VTl, s);
         split_tf32_f32(Zs, ld, 1, Zh, Zl, s);
@@ -473,8 +481,7 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
             TcOperands op{Zh, Zl, VTh, VTl, ld, ld};
             TcArgs g{M, M, M, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                      0, 0, ctx->dstatus, W64, cstages};
-            const cudaError_t e = tc_gemm(2, op, g, s);
-            if (e != cudaSuccess) return cuda_fail(ctx, "correction", e);
+            if (int rc = tc64(op, g)) return rc;
         }
         energy_correction(ctx->dQ, 1.0 / sc, Zs, V64, W64, ld, n, std::sqrt(sc), ctx->dombar, N,
                           ctx->dscal + 8 + 2 * 64, energy_out, ctx->dscal + 3, s);
