@@ -29,25 +29,17 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define ORC_OK 0
-#define ORC_ERR_INPUT 1
-#define ORC_ERR_NEG_EIGENVALUE 2
-#define ORC_ERR_SCS_NEG_ALPHA 3
-#define ORC_ERR_SINGULAR 4
-#define ORC_ERR_NOT_CONVERGED 5
-
-static const double ORC_PI = 3.14159265358979323846264338327950288;
+#include "mbd_oracle_internal.h"
 
 /* ------------------------------------------------------------------------- */
 /* Compensated summation (Neumaier).                                         */
 /* ------------------------------------------------------------------------- */
-typedef struct { double s, c; } orc_sum;
-static void ksum_add(orc_sum *k, double x) {
+void ksum_add(orc_sum *k, double x) {
     double t = k->s + x;
     if (fabs(k->s) >= fabs(x)) k->c += (k->s - t) + x; else k->c += (x - t) + k->s;
     k->s = t;
 }
-static double ksum_get(const orc_sum *k) { return k->s + k->c; }
+double ksum_get(const orc_sum *k) { return k->s + k->c; }
 
 /* ------------------------------------------------------------------------- */
 /* Imaginary-frequency grid (Sec. 3.3): Gauss-Legendre on [-1,1] mapped by    */
@@ -166,7 +158,7 @@ static void tgg_radial(double rr, double s, double *A, double *Bf, double *dA, d
 }
 
 /* dT_ab/dr_c for a tensor A delta_ab + Bf r_a r_b with radial derivatives dA, dBf. */
-static void radial_tensor_deriv(const double *r, double rr, double A, double Bf, double dA,
+void radial_tensor_deriv(const double *r, double rr, double A, double Bf, double dA,
                                 double dBf, double *dT /* [3][3][3]: c, a, b */) {
     (void)A;
     for (int c = 0; c < 3; ++c)
@@ -289,8 +281,8 @@ void orc_ts_scaling(int N, const double *a0ref, const double *c6ref, const doubl
 }
 
 /* Dynamic polarizability, Eq. (dyn-pol), and Mayer width, Eq. (mayer). */
-static double alpha_iu(double a0, double om, double u) { return a0 / (1.0 + u * u / (om * om)); }
-static double mayer_sigma(double al) { return cbrt(sqrt(2.0 / ORC_PI) * al / 3.0); }
+double alpha_iu(double a0, double om, double u) { return a0 / (1.0 + u * u / (om * om)); }
+double mayer_sigma(double al) { return cbrt(sqrt(2.0 / ORC_PI) * al / 3.0); }
 
 /* SCS matrix at one frequency, Eq. (scs) with Eq. (scs-sr-dipole):
  * M = diag(1/alpha_i) x I3 + (1 - f_ij) T^GG_ij for i != j, row-major n x n, n = 3N. */
@@ -508,7 +500,7 @@ int orc_mbd_rsscs_energy(int N, const double *R, const double *a0ref, const doub
  * with r = R_j - R_i, with respect to the elementary inputs of the pair.
  * Outputs: dB/dr_c [27], dB/dalpha_i(u) [9], dB/dalpha_j(u) [9], dB/dS [9] where
  * S = R_vdW,i + R_vdW,j. */
-static void scs_block_derivs(const double *r, double al_i, double al_j, double rsum,
+void scs_block_derivs(const double *r, double al_i, double al_j, double rsum,
                              double beta, double a, double *dBdr, double *dBdai,
                              double *dBdaj, double *dBdS) {
     double rr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
@@ -558,7 +550,7 @@ void orc_T_bare_deriv(const double *r, double *dT) {
 
 /* TS-scaling chain (Eq. ts-scaling) from adjoints of (alpha0, omega, R_vdW) to the
  * adjoints of (alpha0_ref, C6_ref, R_ref, ratio), layout gp[4][N]. */
-static void ts_chain(int N, const double *a0ref, const double *c6ref, const double *rref,
+void ts_chain(int N, const double *a0ref, const double *c6ref, const double *rref,
                      const double *ratio, const double *g_a0, const double *g_om,
                      const double *g_rv, double *gp) {
     for (int i = 0; i < N; ++i) {

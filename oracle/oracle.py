@@ -1,6 +1,7 @@
-"""ctypes binding of the plain FP64 C oracle (mbd_oracle.c) -- test infrastructure only.
+"""ctypes binding of the plain FP64 C oracle (mbd_oracle.c: finite systems, mbd_periodic.c:
+periodic systems) -- test infrastructure only.
 
-`build()` compiles mbd_oracle.c with gcc into oracle/_build/libmbd_oracle.so for the
+`build()` compiles the oracle's C files with gcc into oracle/_build/libmbd_oracle.so for the
 host it runs on (x86_64 here, aarch64 on the GPU host); `lib()` loads it.
 """
 from __future__ import annotations
@@ -13,7 +14,8 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "mbd_oracle.c")
+SRCS = [os.path.join(HERE, f) for f in ("mbd_oracle.c", "mbd_periodic.c")]
+DEPS = SRCS + [os.path.join(HERE, "mbd_oracle_internal.h")]
 OUT_DIR = os.path.join(HERE, "_build")
 SO = os.path.join(OUT_DIR, "libmbd_oracle.so")
 
@@ -27,9 +29,9 @@ _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 def build(force: bool = False) -> str:
     """Compile the oracle if the shared object is missing or older than its source."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    if force or not os.path.exists(SO) or os.path.getmtime(SO) < os.path.getmtime(SRC):
+    if force or not os.path.exists(SO) or os.path.getmtime(SO) < max(map(os.path.getmtime, DEPS)):
         tmp = SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, *SRCS, "-lm"])
         os.replace(tmp, SO)
     return SO
 
@@ -61,6 +63,20 @@ def lib():
             L.orc_mbd_energy.argtypes = [i, _dp, _dp, _dp, _dp, d, d, P]
             L.orc_mbd_rsscs_energy.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, P, P]
             L.orc_mbd_rsscs_gradient.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, i, P, _dp, _dp]
+            # periodic
+            L.orc_cell_reciprocal.argtypes = [_dp, _dp, P]
+            L.orc_monkhorst_pack.argtypes = [C.POINTER(C.c_int), _dp]
+            L.orc_T_erfc_deriv.argtypes = [_dp, d, _dp]
+            L.orc_tlr_block.argtypes = [_dp, _dp, i, _dp, d, d, d, d, d, d, i, _dp, P, P, P]
+            L.orc_tlr_block.restype = None
+            L.orc_ewald_T.argtypes = [i, _dp, _dp, _dp, d, d, d, _dp]
+            L.orc_periodic_q.argtypes = [i, _dp, _dp, _dp, _dp, _dp, _dp, d, d, d, d, d, _dp]
+            L.orc_hermitian_sqrt.argtypes = [i, _dp, P, P, P]
+            L.orc_periodic_scs_matrix.argtypes = [i, _dp, _dp, _dp, _dp, d, d, d, _dp]
+            L.orc_periodic_rsscs_energy.argtypes = [i, _dp, _dp, i, _dp, _dp, _dp, _dp, _dp, d, d, i,
+                                                    d, d, d, P, P]
+            L.orc_periodic_rsscs_gradient.argtypes = [i, _dp, _dp, i, _dp, _dp, _dp, _dp, _dp, d, d, i,
+                                                      d, d, d, P, _dp, _dp, _dp]
             _lib = L
     return _lib
 
@@ -218,3 +234,107 @@ def mbd_rsscs_gradient(R, a0ref, c6ref, rref, ratio, beta=0.83, a=6.0, n_freq=15
 def system_args(sys):
     """(R, alpha0_ref, c6_ref, rvdw_ref, ratio) of a synthetic.System."""
     return sys.coords, sys.alpha0_ref, sys.c6_ref, sys.rvdw_ref, sys.ratio
+
+
+# ---- periodic systems (mbd_periodic.c) ---------------------------------------------
+def _ptr(x):
+    return None if x is None else x.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _cplx(buf, shape):
+    return buf.view(np.complex128).reshape(shape)
+
+
+def cell_reciprocal(A):
+    """(B, volume): rows of B are the reciprocal vectors, a_c . b_d = 2 pi delta_cd."""
+    B, vol = np.zeros(9), C.c_double()
+    _check(lib().orc_cell_reciprocal(_a(A).reshape(9), B, C.byref(vol)), "cell_reciprocal")
+    return B.reshape(3, 3), vol.value
+
+
+def monkhorst_pack(grid):
+    g = (C.c_int * 3)(*[int(x) for x in grid])
+    out = np.zeros(3 * int(np.prod(grid)))
+    lib().orc_monkhorst_pack(g, out)
+    return out.reshape(-1, 3)
+
+
+def T_erfc_deriv(r, gamma):
+    dr = np.zeros(27); lib().orc_T_erfc_deriv(_a(r), float(gamma), dr); return dr.reshape(3, 3, 3)
+
+
+def tlr_block(A, x, same, kappa, gamma, rc, kc, rsum=1.0, beta=0.83, a=6.0, damp=True, derivs=False):
+    """T^lr(q) block (3x3 complex) for separation x; with derivs also d/dx [3,3,3],
+    d/dS [3,3] and d/dA [3,3,3,3] (indices c, d, a, b)."""
+    T = np.zeros(18)
+    dx, dS, dA = (np.zeros(54), np.zeros(18), np.zeros(162)) if derivs else (None, None, None)
+    lib().orc_tlr_block(_a(A).reshape(9), _a(x), int(same), _a(kappa), float(gamma), float(rc), float(kc),
+                        float(rsum), float(beta), float(a), int(bool(damp)), T, _ptr(dx), _ptr(dS), _ptr(dA))
+    if not derivs:
+        return _cplx(T, (3, 3))
+    return _cplx(T, (3, 3)), _cplx(dx, (3, 3, 3)), _cplx(dS, (3, 3)), _cplx(dA, (3, 3, 3, 3))
+
+
+def ewald_T(R, A, kappa, gamma, rc, kc):
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    out = np.zeros(2 * (3 * N) ** 2)
+    lib().orc_ewald_T(N, R, _a(A).reshape(9), _a(kappa), float(gamma), float(rc), float(kc), out)
+    return _cplx(out, (3 * N, 3 * N))
+
+
+def periodic_q(R, A, kappa, alpha0, omega, rdamp, gamma, rc, kc, beta=0.83, a=6.0):
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    out = np.zeros(2 * (3 * N) ** 2)
+    lib().orc_periodic_q(N, R, _a(A).reshape(9), _a(kappa), _a(alpha0), _a(omega), _a(rdamp), beta, a,
+                         float(gamma), float(rc), float(kc), out)
+    return _cplx(out, (3 * N, 3 * N))
+
+
+def hermitian_sqrt(Q, want_z=False):
+    """(1/2 Tr Q^{1/2}, eigenvalues ascending[, Q^{-1/2}]) of a Hermitian matrix."""
+    Q = np.ascontiguousarray(np.asarray(Q, dtype=np.complex128))
+    n = Q.shape[0]
+    h, lam = C.c_double(), np.zeros(n)
+    Z = np.zeros(2 * n * n) if want_z else None
+    _check(lib().orc_hermitian_sqrt(n, Q.view(np.float64).reshape(-1), C.byref(h), _ptr(Z), _ptr(lam)),
+           "hermitian_sqrt")
+    return (h.value, lam, _cplx(Z, (n, n))) if want_z else (h.value, lam)
+
+
+def periodic_scs_matrix(R, A, alpha, rvdw, rc, beta=0.83, a=6.0):
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    M = np.zeros((3 * N, 3 * N))
+    _check(lib().orc_periodic_scs_matrix(N, R, _a(A).reshape(9), _a(alpha), _a(rvdw), beta, a, float(rc), M),
+           "periodic_scs_matrix")
+    return M
+
+
+def periodic_rsscs_energy(R, A, kappa, a0ref, c6ref, rref, ratio, gamma, rc, kc, beta=0.83, a=6.0,
+                          n_freq=15, detail=False):
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    kappa = _a(kappa).reshape(-1, 3); nk = kappa.shape[0]
+    E = C.c_double()
+    det = np.zeros((n_freq + 4) * N + nk)
+    rc0 = lib().orc_periodic_rsscs_energy(N, R, _a(A).reshape(9), nk, kappa, _a(a0ref), _a(c6ref), _a(rref),
+                                          _a(ratio), beta, a, n_freq, float(gamma), float(rc), float(kc),
+                                          C.byref(E), _ptr(det))
+    _check(rc0, "periodic_rsscs_energy")
+    if not detail:
+        return E.value
+    o = (n_freq + 1) * N
+    return E.value, dict(alpha_bar=det[:o].reshape(n_freq + 1, N), c6=det[o:o + N], omega=det[o + N:o + 2 * N],
+                         rvdw=det[o + 2 * N:o + 3 * N], e_q=det[o + 3 * N:])
+
+
+def periodic_rsscs_gradient(R, A, kappa, a0ref, c6ref, rref, ratio, gamma, rc, kc, beta=0.83, a=6.0,
+                            n_freq=15):
+    """Energy, dE/dR [N,3], dE/dA [3,3] (Cartesian positions fixed), dE/dparams [4,N]."""
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    kappa = _a(kappa).reshape(-1, 3); nk = kappa.shape[0]
+    E = C.c_double()
+    gR, gA, gp = np.zeros((N, 3)), np.zeros((3, 3)), np.zeros((4, N))
+    rc0 = lib().orc_periodic_rsscs_gradient(N, R, _a(A).reshape(9), nk, kappa, _a(a0ref), _a(c6ref), _a(rref),
+                                            _a(ratio), beta, a, n_freq, float(gamma), float(rc), float(kc),
+                                            C.byref(E), gR, gA, gp)
+    _check(rc0, "periodic_rsscs_gradient")
+    return E.value, gR, gA, gp
