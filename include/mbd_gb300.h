@@ -58,7 +58,9 @@ typedef struct mbd_ctx mbd_ctx;
 
 /* Options.  Defaults (mbd_default_options): n_freq 15 (Sec. 3.3), beta 0.83, a 6
  * (Sec. 2.6), precision FP64, ns_tol 1e-8 (Frobenius norm of I - Z Y at which one
- * final Newton-Schulz step is taken), ns_max_iter 100, tc_chunk_stages 2. */
+ * final Newton-Schulz step is taken; periodic systems: of all Bloch vectors' matrices
+ * together), ns_max_iter 100, tc_chunk_stages 2, ewald_gamma, real_cutoff and
+ * recip_cutoff 0 (automatic, see below). */
 typedef struct {
     int n_freq;          /* Gauss-Legendre points of the Casimir-Polder integral     */
     double beta;         /* damping scale s_R of the Fermi function, Eq. (fermi-damping) */
@@ -69,6 +71,14 @@ typedef struct {
     int tc_chunk_stages; /* mixed modes: K stages (32 TF32 or 64 bf16 elements each) per
                             tensor-memory accumulation; the partial sums are added in FP32
                             with round-to-nearest (default 2; 0 means 1)                  */
+    /* Periodic systems (Sec. 2.3, Ewald summation of the dipole tensor).  <= 0 selects:
+     * real_cutoff = 6/ewald_gamma; ewald_gamma = 6/real_cutoff when only the cutoff is
+     * given, else 2.5/Omega^(1/3); recip_cutoff = 10 ewald_gamma.  real_cutoff (bohr) also
+     * bounds the lattice sums of the damped tensors (screening and the damped-away part of
+     * T^lr), where (1 - f) decays exponentially.                                         */
+    double ewald_gamma;   /* Ewald splitting parameter (1/bohr)                          */
+    double real_cutoff;   /* real-space cutoff (bohr)                                    */
+    double recip_cutoff;  /* reciprocal-space cutoff on |G + q| (1/bohr)                 */
 } mbd_options;
 
 /* Fills *opt with the defaults above.  Returns MBD_ERR_INPUT if opt is NULL. */
@@ -81,9 +91,12 @@ int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt);
 /* Frees the context and all device memory it owns.  NULL is accepted. */
 int mbd_destroy(mbd_ctx *ctx);
 
-/* Sets a finite system of n_atoms atoms (coords [n_atoms][3], bohr, host memory) and
- * allocates the device workspace for that size.  lattice and k_grid must be NULL:
- * periodic systems are reported as MBD_ERR_UNSUPPORTED by this build. */
+/* Sets the system: n_atoms atoms at coords [n_atoms][3] (bohr, host memory), and for a
+ * periodic system the lattice [3][3] (rows are the lattice vectors, bohr) and the
+ * Monkhorst-Pack grid k_grid [3] (k-points (2m - n_c - 1)/(2 n_c) in fractional
+ * reciprocal coordinates, m = 1..n_c, Sec. 2.3); lattice and k_grid are both NULL for a
+ * finite system.  Allocates the device workspace for that size.  Periodic systems run in
+ * FP64 only (MBD_ERR_UNSUPPORTED for the reduced-precision modes). */
 int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const double *lattice,
                      const int *k_grid);
 
@@ -97,7 +110,8 @@ int mbd_set_free_atom_params(mbd_ctx *ctx, const double *alpha0_ref, const doubl
  * grad_coords [n_atoms][3] (Ha/bohr), grad_params [4][n_atoms] (dE/d alpha0_ref,
  * dE/d c6_ref, dE/d rvdw_ref, dE/d ratio) and alpha_scs [n_atoms] (screened static
  * polarizability) may each be NULL; gradients are computed only if one of grad_coords
- * or grad_params is given.  grad_lattice must be NULL (finite systems). */
+ * or grad_params is given.  grad_lattice [3][3] (dE/dA_cd for lattice vector c, component d,
+ * with the Cartesian atom positions held fixed) is for periodic systems only. */
 int mbd_evaluate(mbd_ctx *ctx, double *energy, double *grad_coords, double *grad_lattice,
                  double *grad_params, double *alpha_scs);
 
@@ -125,6 +139,11 @@ int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
                      const double *alpha0_ref, const double *c6_ref, const double *rvdw_ref,
                      const double *volume_ratio, const double *grad_energy, double *grad_coords,
                      double *grad_params);
+
+/* Lattice gradient [3][3] (host) of the last gradient evaluation of a periodic system
+ * (mbd_evaluate with gradients, mbd_evaluate_dev with gradients, or mbd_backward_dev,
+ * scaled like its other outputs).  MBD_ERR_STATE if there is none. */
+int mbd_get_lattice_gradient(mbd_ctx *ctx, double *grad_lattice);
 
 /* Screening detail of the last successful evaluation, host arrays: alpha_iu
  * [n_freq+1][n_atoms] (row 0 is u = 0), c6 [n_atoms], omega [n_atoms] (screened

@@ -25,7 +25,7 @@ MBD_PREC_FP64, MBD_PREC_TF32, MBD_PREC_BF16X3, MBD_PREC_TF32X3 = 0, 1, 2, 3
 # Every symbol declared in include/mbd_gb300.h.
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
            "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_backward_dev",
-           "mbd_get_scs_detail",
+           "mbd_get_lattice_gradient", "mbd_get_scs_detail",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
            "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
            "mbdk_cholesky_solve3_f64_noalloc")
@@ -34,7 +34,8 @@ EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry
 class mbd_options(C.Structure):
     _fields_ = [("n_freq", C.c_int), ("beta", C.c_double), ("a", C.c_double),
                 ("precision", C.c_int), ("ns_tol", C.c_double), ("ns_max_iter", C.c_int),
-                ("tc_chunk_stages", C.c_int)]
+                ("tc_chunk_stages", C.c_int), ("ewald_gamma", C.c_double), ("real_cutoff", C.c_double),
+                ("recip_cutoff", C.c_double)]
 
 
 class mbd_profile(C.Structure):
@@ -74,6 +75,7 @@ def load(path: str | None = None):
     L.mbd_evaluate_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mbd_backward_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mbd_get_scs_detail.argtypes = [vp, _P, _P, _P, _P]
+    L.mbd_get_lattice_gradient.argtypes = [vp, _P]
     L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P, _P]
     L.mbd_get_exception.argtypes = [vp, C.POINTER(C.c_int), C.c_char_p, C.c_char_p, sz]
     L.mbd_set_profiling.argtypes = [vp, i]
@@ -111,7 +113,8 @@ class MBD:
 
     def __init__(self, device: int = 0, n_freq: int = 15, beta: float = 0.83, a: float = 6.0,
                  ns_tol: float = 1e-8, ns_max_iter: int = 100, precision: int = MBD_PREC_FP64,
-                 tc_chunk_stages: int | None = None):
+                 tc_chunk_stages: int | None = None, ewald_gamma: float = 0.0, real_cutoff: float = 0.0,
+                 recip_cutoff: float = 0.0):
         self.lib = load()
         opt = mbd_options()
         self.lib.mbd_default_options(C.byref(opt))
@@ -119,6 +122,7 @@ class MBD:
         opt.precision = precision
         if tc_chunk_stages is not None:
             opt.tc_chunk_stages = tc_chunk_stages
+        opt.ewald_gamma, opt.real_cutoff, opt.recip_cutoff = ewald_gamma, real_cutoff, recip_cutoff
         h = C.c_void_p()
         rc = self.lib.mbd_create(C.byref(h), device, C.byref(opt))
         if rc:
@@ -160,6 +164,7 @@ class MBD:
         kg = None if k_grid is None else (C.c_int * 3)(*[int(k) for k in k_grid])
         self._check(self.lib.mbd_set_geometry(self.h, R.shape[0], _ptr(R), _ptr(lat), kg))
         self.n_atoms = R.shape[0]
+        self.periodic = lattice is not None
 
     def set_free_atom_params(self, alpha0_ref, c6_ref, rvdw_ref, volume_ratio):
         arrs = [_f64(x) for x in (alpha0_ref, c6_ref, rvdw_ref, volume_ratio)]
@@ -167,14 +172,24 @@ class MBD:
 
     def evaluate(self, gradients: bool = True):
         """Host-memory evaluation.  Returns (energy, grad_coords [N,3] | None,
-        grad_params [4,N] | None, alpha_scs [N])."""
+        grad_params [4,N] | None, alpha_scs [N]); for a periodic system the lattice
+        gradient [3,3] is available afterwards from lattice_gradient()."""
         N = self.n_atoms
         E = C.c_double()
         gR = np.zeros((N, 3)) if gradients else None
         gp = np.zeros((4, N)) if gradients else None
+        gA = np.zeros((3, 3)) if gradients and getattr(self, "periodic", False) else None
         al = np.zeros(N)
-        self._check(self.lib.mbd_evaluate(self.h, C.byref(E), _ptr(gR), None, _ptr(gp), _ptr(al)))
+        self._check(self.lib.mbd_evaluate(self.h, C.byref(E), _ptr(gR), _ptr(gA), _ptr(gp), _ptr(al)))
+        self._last_gA = gA
         return E.value, gR, gp, al
+
+    def lattice_gradient(self):
+        """dE/dA [3,3] (rows: lattice vectors) of the last gradient evaluation of a periodic
+        system, with the Cartesian positions held fixed."""
+        gA = np.zeros((3, 3))
+        self._check(self.lib.mbd_get_lattice_gradient(self.h, _ptr(gA)))
+        return gA
 
     def evaluate_dev(self, coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio, energy,
                      grad_coords=None, grad_params=None, alpha_scs=None, stream=None):

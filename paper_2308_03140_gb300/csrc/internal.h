@@ -148,6 +148,8 @@ struct AtomBufs {
 void prepare_atoms(const AtomBufs &b, int *status, cudaStream_t s);
 void build_scs(const AtomBufs &b, double beta, double a, double *M, long long ld,
                long long mstride, int *status, cudaStream_t s);
+// Rows and columns n..ld-1 of nf1 matrices: identity on the diagonal, zero couplings.
+void pad_identity(double *M, long long ld, int n, int nf1, long long mstride, cudaStream_t s);
 void init_rhs_identity(double *X, long long ld, int n, int nf1, long long xstride, cudaStream_t s);
 void contract_screen(const AtomBufs &b, const double *X, long long ld, long long xstride,
                      int *status, cudaStream_t s);
@@ -180,5 +182,60 @@ void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const d
               const double *scale, double *gp, cudaStream_t s);
 // y = (*scale) x (scale device pointer, NULL for 1).
 void scale_copy(const double *x, int n, const double *scale, double *y, cudaStream_t s);
+
+// ---- periodic systems (k_periodic.cu) --------------------------------------------
+// Cell: rows of A are the lattice vectors; Ainv = A^{-1}; rows of B are the reciprocal
+// vectors (a_c . b_d = 2 pi delta_cd); vol = |det A|.  Ewald split gamma, real-space
+// cutoff rc (also the cutoff of the damped and screening lattice sums), reciprocal
+// cutoff kc.
+struct CellGeom {
+    double A[9], Ainv[9], B[9];
+    double vol, gamma, rc, kc;
+};
+// Bloch vectors and reciprocal lattice: kq [nk][3] (Cartesian q), G [nG][3] (every G
+// with |G + q| < kc for some q), glist [nk][maxG] indices into G of the vectors with
+// 0 < |G + q_k| < kc (gcount[k] of them), S [nG][N] structure factors e^{i G.R_i}.
+struct PeriodicBufs {
+    CellGeom cell;
+    int nk, nG, maxG;
+    const double *kq, *G;
+    const int *glist, *gcount;
+    double2 *S;
+};
+// Complex matrices are planar: matrix k has its real part at base + k * 2 ld^2 and its
+// imaginary part ld^2 further on.
+void structure_factors(const AtomBufs &b, const PeriodicBufs &p, cudaStream_t s);
+// Gamma-point screening matrices: alpha^{-1} + sum over lattice images of (1 - f) T^GG.
+void build_scs_periodic(const AtomBufs &b, const CellGeom &c, double beta, double a, double *M, long long ld,
+                        long long mstride, int *status, cudaStream_t s);
+// Q(q_k) for every Bloch vector: diag(omega^2) + c_i c_j T^lr(q), T^lr = Ewald[T] minus the
+// damped-away part, both triangles; rows >= n padded with omega_0^2 on the diagonal.
+void build_q_periodic(const AtomBufs &b, const PeriodicBufs &p, double beta, double a, double *Q, long long ld,
+                      int n, int *status, cudaStream_t s);
+// Batched complex helpers (nk planar matrices of order ld).
+void cscale(double *Y, long long ld, int nk, double scale, cudaStream_t s);
+void cset_identity(double *Z, long long ld, int nk, cudaStream_t s);
+void caxpby_identity(double *Z, const double *P, long long ld, int nk, double a, double b, cudaStream_t s);
+void cfrob_dev_identity(const double *P, long long ld, int n, int nk, double *out, cudaStream_t s);
+void cmax_abs_rowsum(const double *Q, long long ld, int nk, double *out, cudaStream_t s);
+// C = alpha A B + beta D for nk planar complex matrices (4 real FP64 GEMMs; D may be C).
+void cgemm_f64(const double *A, const double *B, const double *D, double *C, long long ld, int nk, double alpha,
+               double beta, cudaStream_t s);
+// Lanczos coefficients of every Q_k: coef[k][2j] = alpha_j, coef[k][2j+1] = beta_j.
+// work: 3 nk 2 ld doubles.
+void clanczos_coefficients(const double *Q, long long ld, int nk, int steps, double *work, double *coef,
+                           cudaStream_t s);
+// E = sqrt_s/(2 nk) sum_k Re Tr Y_k - 3/2 sum omega_bar (compensated).
+void energy_trace_periodic(const double *Y, long long ld, int n, int nk, const double *ombar, int N,
+                           double sqrt_s, double *out, cudaStream_t s);
+// MBD gradient of the periodic energy from Z_k (Q(q_k)^{-1/2} = zscale Z_k): per atom
+// g_ombar, g_abar0, g_rbar, gR (o), and dE/dA accumulated into gA [9].  work: 2N doubles.
+void periodic_mbd_grad(const AtomBufs &b, const PeriodicBufs &p, double beta, double a, const double *Z,
+                       long long ld, double zscale, const MbdGradOut &o, double *work, double *gA, cudaStream_t s);
+// SCS adjoint pair pass over lattice images (as scs_grad_pass), with the lattice part
+// accumulated into gA [9].  gA_part: N x 9 doubles of workspace.
+void scs_grad_periodic(const AtomBufs &b, const CellGeom &c, double beta, double a, const double *X,
+                       const double *V, long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR,
+                       double *gA_part, double *gA, cudaStream_t s);
 
 }  // namespace mbdgb

@@ -24,6 +24,7 @@ using namespace mbdgb;
 namespace {
 std::atomic<long long> g_launches{0};
 constexpr int kRefineSteps = 3;   // iterative-refinement steps of the mixed screening solves
+constexpr int kLanczosSteps = 48; // Lanczos steps of the spectrum estimate of Q
 }  // namespace
 
 void mbdgb::count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -131,6 +132,17 @@ struct mbd_ctx {
     void *hY[2] = {}, *hZ[2] = {}, *hY2[2] = {}, *hZ2[2] = {}, *hP[2] = {}, *hPT[2] = {};   // split operands
     double corr_resid = 0.0;   // |Zd Q Zd - I|_F of the mixed modes' correction
     double *dh, *dgomb, *dgab0, *dgrb, *dgR, *dga0, *dgom, *dgrv, *dgp;
+    // periodic systems: cell, Bloch vectors and reciprocal lattice (host lists, device copies)
+    bool periodic = false;
+    int nk = 1, nG = 0, maxG = 0;
+    CellGeom cell{};
+    std::vector<double> hkq, hG;
+    std::vector<int> hglist, hgcount;
+    double *dkq = nullptr, *dG = nullptr, *dcoef = nullptr, *dlzw = nullptr, *dgA = nullptr, *dgAout = nullptr,
+           *dgApart = nullptr, *dgc = nullptr;
+    int *dglist = nullptr, *dgcount = nullptr;
+    double2 *dS = nullptr;
+    bool have_lattice_grad = false;
     double *dscal;   // [0] energy, [1] Gershgorin, [2] residual
     int *dstatus;
     // last results
@@ -217,13 +229,29 @@ int allocate(mbd_ctx *ctx) {
         {&ctx->dh, nf1 * N}, {&ctx->dgomb, N}, {&ctx->dgab0, N}, {&ctx->dgrb, N}, {&ctx->dgR, 3 * N},
         {&ctx->dga0, N}, {&ctx->dgom, N}, {&ctx->dgrv, N}, {&ctx->dgp, 4 * N}, {&ctx->dscal, 8 + 2 * 64 + 1024},
     };
+    const long long nk = ctx->nk;
+    if (ctx->periodic) {
+        plan.push_back({&ctx->dkq, 3 * nk});
+        plan.push_back({&ctx->dG, 3LL * ctx->nG});
+        plan.push_back({&ctx->dcoef, nk * 2 * kLanczosSteps});
+        plan.push_back({&ctx->dlzw, 3 * nk * 2 * ld});
+        plan.push_back({&ctx->dgA, 9});
+        plan.push_back({&ctx->dgAout, 9});
+        plan.push_back({&ctx->dgApart, 9 * N});
+        plan.push_back({&ctx->dgc, N});
+        plan.push_back({reinterpret_cast<double **>(&ctx->dS), 2LL * ctx->nG * N});
+        plan.push_back({reinterpret_cast<double **>(&ctx->dglist), (nk * ctx->maxG + 1) / 2});
+        plan.push_back({reinterpret_cast<double **>(&ctx->dgcount), (nk + 1) / 2});
+    }
     size_t bytes = 0;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     for (auto &p : plan) bytes += al(sizeof(double) * p.second);
     bytes += al(sizeof(int) * 4);
     const size_t small = bytes;
     bytes += nf1 * mat;          // screening matrices / factors
-    bytes += 5 * mat;            // Q (= Y), Z, P, Y', Z'
+    // Q (= Y), Z, P, Y', Z': real, or nk planar complex matrices for a periodic system
+    const size_t matq = ctx->periodic ? mat * 2 * static_cast<size_t>(nk) : mat;
+    bytes += 5 * matq;
     const size_t mat32 = mat / 2, mat16 = mat / 4;
     const int prec = ctx->opt.precision;
     const size_t split_mat = prec == MBD_PREC_BF16X3 ? mat16 : (prec == MBD_PREC_TF32X3 ? mat32 : 0);
@@ -250,7 +278,7 @@ int allocate(mbd_ctx *ctx) {
     double **mats[5] = {&ctx->dQ, &ctx->dZ, &ctx->dP, &ctx->dY2, &ctx->dZ2};
     for (auto m : mats) {
         *m = reinterpret_cast<double *>(p);
-        p += mat;
+        p += matq;
     }
     if (prec != MBD_PREC_FP64) {
         float **f32[6] = {&ctx->fY, &ctx->fZ, &ctx->fY2, &ctx->fZ2, &ctx->fP, &ctx->fPT};
@@ -283,6 +311,106 @@ int allocate(mbd_ctx *ctx) {
     if (e == cudaSuccess)
         e = cudaMemcpy(ctx->dwu, ctx->hwu.data(), sizeof(double) * nf1, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, "mbd_set_geometry", e);
+    return MBD_OK;
+}
+
+// Uploads the Bloch vectors and reciprocal-vector lists of a periodic geometry.
+int upload_periodic(mbd_ctx *ctx) {
+    cudaError_t e = cudaMemcpy(ctx->dkq, ctx->hkq.data(), sizeof(double) * ctx->hkq.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->dG, ctx->hG.data(), sizeof(double) * ctx->hG.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->dglist, ctx->hglist.data(), sizeof(int) * ctx->hglist.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->dgcount, ctx->hgcount.data(), sizeof(int) * ctx->hgcount.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, "mbd_set_geometry", e);
+    return MBD_OK;
+}
+
+PeriodicBufs periodic_bufs(mbd_ctx *ctx) {
+    return PeriodicBufs{ctx->cell, ctx->nk, ctx->nG, ctx->maxG, ctx->dkq, ctx->dG, ctx->dglist, ctx->dgcount, ctx->dS};
+}
+
+// Host preparation of a periodic geometry: cell inverse and reciprocal vectors, Ewald
+// parameters, Monkhorst-Pack Bloch vectors and the reciprocal vectors of each.
+struct PeriodicSetup {
+    CellGeom cell{};
+    int nk = 0, nG = 0, maxG = 0;
+    std::vector<double> kq, G;
+    std::vector<int> glist, gcount;
+    std::string msg;
+};
+
+int periodic_setup(const mbd_options &o, const double *A, const int *grid, PeriodicSetup &ps) {
+    const double pi = 3.141592653589793238462643383279502884;
+    for (int e = 0; e < 9; ++e)
+        if (!std::isfinite(A[e])) { ps.msg = "non-finite lattice"; return MBD_ERR_INPUT; }
+    for (int c = 0; c < 3; ++c)
+        if (grid[c] < 1 || grid[c] > 64) { ps.msg = "k_grid entries must lie in 1..64"; return MBD_ERR_INPUT; }
+    CellGeom &c = ps.cell;
+    for (int e = 0; e < 9; ++e) c.A[e] = A[e];
+    const double co[9] = {A[4] * A[8] - A[5] * A[7], -(A[3] * A[8] - A[5] * A[6]), A[3] * A[7] - A[4] * A[6],
+                          -(A[1] * A[8] - A[2] * A[7]), A[0] * A[8] - A[2] * A[6], -(A[0] * A[7] - A[1] * A[6]),
+                          A[1] * A[5] - A[2] * A[4], -(A[0] * A[5] - A[2] * A[3]), A[0] * A[4] - A[1] * A[3]};
+    const double det = A[0] * co[0] + A[1] * co[1] + A[2] * co[2];
+    if (!(std::fabs(det) > 1e-12)) { ps.msg = "singular lattice"; return MBD_ERR_INPUT; }
+    for (int e = 0; e < 3; ++e)
+        for (int k = 0; k < 3; ++k) c.Ainv[3 * e + k] = co[3 * k + e] / det;   // (A^{-1})_{ek}
+    for (int k = 0; k < 3; ++k)
+        for (int e = 0; e < 3; ++e) c.B[3 * k + e] = 2.0 * pi * c.Ainv[3 * e + k];
+    c.vol = std::fabs(det);
+    double g = o.ewald_gamma, rc = o.real_cutoff, kc = o.recip_cutoff;
+    if (!(g > 0.0)) g = rc > 0.0 ? 6.0 / rc : 2.5 / std::cbrt(c.vol);
+    if (!(rc > 0.0)) rc = 6.0 / g;
+    if (!(kc > 0.0)) kc = 10.0 * g;
+    c.gamma = g;
+    c.rc = rc;
+    c.kc = kc;
+    auto norm = [](const double *v) { return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); };
+    // Monkhorst-Pack: kappa_c = (2m - n_c - 1)/(2 n_c), q = kappa B
+    ps.nk = grid[0] * grid[1] * grid[2];
+    double qmax = 0.0;
+    for (int m0 = 1; m0 <= grid[0]; ++m0)
+        for (int m1 = 1; m1 <= grid[1]; ++m1)
+            for (int m2 = 1; m2 <= grid[2]; ++m2) {
+                const double kap[3] = {(2.0 * m0 - grid[0] - 1) / (2.0 * grid[0]),
+                                       (2.0 * m1 - grid[1] - 1) / (2.0 * grid[1]),
+                                       (2.0 * m2 - grid[2] - 1) / (2.0 * grid[2])};
+                double q[3];
+                for (int e = 0; e < 3; ++e) q[e] = kap[0] * c.B[e] + kap[1] * c.B[3 + e] + kap[2] * c.B[6 + e];
+                for (int e = 0; e < 3; ++e) ps.kq.push_back(q[e]);
+                qmax = std::max(qmax, norm(q));
+            }
+    // every G = m B with |G + q| < kc for some q: |G| < kc + qmax, |m_c| <= (kc + qmax)|a_c|/(2 pi)
+    const double gr = kc + qmax;
+    int mm[3];
+    for (int k = 0; k < 3; ++k) mm[k] = static_cast<int>(std::floor(gr * norm(c.A + 3 * k) / (2.0 * pi))) + 1;
+    const long long box = (2LL * mm[0] + 1) * (2LL * mm[1] + 1) * (2LL * mm[2] + 1);
+    if (box > 20000000LL) { ps.msg = "reciprocal cutoff too large for this cell"; return MBD_ERR_INPUT; }
+    for (int m0 = -mm[0]; m0 <= mm[0]; ++m0)
+        for (int m1 = -mm[1]; m1 <= mm[1]; ++m1)
+            for (int m2 = -mm[2]; m2 <= mm[2]; ++m2) {
+                double G[3];
+                for (int e = 0; e < 3; ++e) G[e] = m0 * c.B[e] + m1 * c.B[3 + e] + m2 * c.B[6 + e];
+                if (norm(G) < gr) for (int e = 0; e < 3; ++e) ps.G.push_back(G[e]);
+            }
+    ps.nG = static_cast<int>(ps.G.size() / 3);
+    std::vector<std::vector<int>> lists(ps.nk);
+    for (int k = 0; k < ps.nk; ++k)
+        for (int gi = 0; gi < ps.nG; ++gi) {
+            double kv[3];
+            for (int e = 0; e < 3; ++e) kv[e] = ps.G[3 * gi + e] + ps.kq[3 * k + e];
+            const double kk = norm(kv);
+            if (kk < kc && kk > 1e-12) lists[k].push_back(gi);
+        }
+    ps.maxG = 1;
+    for (auto &l : lists) ps.maxG = std::max(ps.maxG, static_cast<int>(l.size()));
+    ps.glist.assign(static_cast<size_t>(ps.nk) * ps.maxG, 0);
+    ps.gcount.assign(ps.nk, 0);
+    for (int k = 0; k < ps.nk; ++k) {
+        ps.gcount[k] = static_cast<int>(lists[k].size());
+        for (size_t t = 0; t < lists[k].size(); ++t) ps.glist[static_cast<size_t>(k) * ps.maxG + t] = lists[k][t];
+    }
+    if (ps.nG == 0) ps.nG = 1, ps.G.assign(3, 0.0);   // keeps the device arrays non-empty
     return MBD_OK;
 }
 
@@ -501,7 +629,183 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
     return MBD_OK;
 }
 
+// Gradient passes of a periodic system: the MBD pair pass over Bloch vectors (atoms,
+// screened parameters, lattice), the chain through the screened parameters, the adjoint
+// solves on the Gamma-point factors and the SCS pass over lattice images.
+void backward_periodic(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const double *grad_energy,
+                       double *grad_coords, double *grad_params) {
+    const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;
+    const double beta = ctx->opt.beta, a = ctx->opt.a;
+    const PeriodicBufs pb = periodic_bufs(ctx);
+    MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
+    periodic_mbd_grad(b, pb, beta, a, ctx->Zlast, ld, ctx->zscale, go, ctx->dgc, ctx->dgA, s);
+    chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, ctx->dV, ld, xs, s);
+    cudaMemsetAsync(ctx->dgom, 0, sizeof(double) * ctx->N, s);
+    chol_solve3_f64(ctx->dM, ld, mat, ctx->nf1, ctx->ddinv, ctx->dV, ctx->dB, xs, s);
+    scs_grad_periodic(b, ctx->cell, beta, a, ctx->dX, ctx->dV, xs, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgR,
+                      ctx->dgApart, ctx->dgA, s);
+    if (grad_params) ts_chain(b, ctx->dga0, ctx->dgom, ctx->dgrv, grad_energy, grad_params, s);
+    if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
+    scale_copy(ctx->dgA, 9, grad_energy, ctx->dgAout, s);
+    ctx->have_lattice_grad = true;
+}
+
+// Periodic evaluation (Sec. 2.3): Gamma-point screening, Q(q) for every Bloch vector of
+// the grid, batched complex coupled Newton-Schulz (FP64, 4 real GEMMs per complex
+// product), E = (1/nk) sum_q 1/2 Tr Q(q)^{1/2} - 3/2 sum omega_bar.
+int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool want_grad) {
+    const int N = ctx->N, n = ctx->n, nf1 = ctx->nf1, nk = ctx->nk;
+    const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;
+    const double beta = ctx->opt.beta, a = ctx->opt.a;
+    ctx->have_result = false;
+    ctx->have_screening = false;
+    ctx->have_forward = false;
+    ctx->have_lattice_grad = false;
+    ctx->ev_used = 0;
+    ctx->prof = mbd_profile{};
+    const long long launches0 = launch_count();
+    cudaEvent_t e_start = nullptr, e_scs = nullptr, e_ns = nullptr, e_grad = nullptr;
+    std::vector<Span> gemms;
+    const double nd = static_cast<double>(n);
+    const double flops_cplx = 8.0 * nd * nd * nd * nk;   // one complex product per Bloch vector
+    auto timed_cgemm = [&](const double *A, const double *B, const double *D, double *C, double alpha, double bt) {
+        Span sp;
+        sp.flops = flops_cplx;
+        mark(ctx, s, sp.a);
+        cgemm_f64(A, B, D, C, ld, nk, alpha, bt, s);
+        mark(ctx, s, sp.b);
+        if (ctx->profiling) gemms.push_back(sp);
+    };
+    const AtomBufs b = atom_bufs(ctx, in);
+    const PeriodicBufs pb = periodic_bufs(ctx);
+    mark(ctx, s, e_start);
+    MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_evaluate");
+    // ---- Gamma-point screening ----
+    prepare_atoms(b, ctx->dstatus, s);
+    structure_factors(b, pb, s);
+    build_scs_periodic(b, ctx->cell, beta, a, ctx->dM, ld, mat, ctx->dstatus, s);
+    cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
+    init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
+    chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
+    contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
+    mark(ctx, s, e_scs);
+    int rc = read_status(ctx, s, "screening");
+    if (rc) return rc;
+    ctx->have_screening = true;
+    // ---- Q(q) and the spectrum bounds ----
+    build_q_periodic(b, pb, beta, a, ctx->dQ, ld, n, ctx->dstatus, s);
+    cmax_abs_rowsum(ctx->dQ, ld, nk, ctx->dscal + 1, s);
+    double sc = 0.0;
+    MBD_CUDA(cudaMemcpyAsync(&sc, ctx->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz");
+    rc = read_status(ctx, s, "coupled_oscillator_matrix");
+    if (rc) return rc;
+    if (!(sc > 0.0) || !std::isfinite(sc)) return fail(ctx, MBD_ERR_INPUT, "newton_schulz", "invalid Q scale");
+    const int lz_steps = std::min(kLanczosSteps, static_cast<int>(2 * ld));
+    clanczos_coefficients(ctx->dQ, ld, nk, lz_steps, ctx->dlzw, ctx->dcoef, s);
+    std::vector<double> lz(static_cast<size_t>(nk) * 2 * lz_steps);
+    MBD_CUDA(cudaMemcpyAsync(lz.data(), ctx->dcoef, sizeof(double) * lz.size(), cudaMemcpyDeviceToHost, s),
+             "newton_schulz");
+    MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
+    double th_min = 1e300, th_max = 0.0;
+    for (int k = 0; k < nk; ++k) {
+        std::vector<double> da, db;
+        const double *c = lz.data() + static_cast<size_t>(k) * 2 * lz_steps;
+        for (int j = 0; j < lz_steps; ++j) {
+            da.push_back(c[2 * j]);
+            if (!(c[2 * j + 1] > 1e-14 * sc)) break;
+            if (j + 1 < lz_steps) db.push_back(c[2 * j + 1]);
+        }
+        db.resize(da.empty() ? 0 : da.size() - 1);
+        double lo = 0.0, hi = sc;
+        if (!da.empty()) tridiag_extremes(da, db, lo, hi);
+        th_min = std::min(th_min, lo);
+        th_max = std::max(th_max, hi);
+    }
+    double ubound = 1.0;
+    if (std::isfinite(th_max) && th_max > 0.0 && 1.05 * th_max < sc) {
+        sc = 1.05 * th_max;
+        ubound = 1.05;
+    }
+    ctx->ns_scale = sc;
+    double lbound = std::sqrt(std::max(0.5 * th_min / sc, 1e-12));
+    const double ss = std::sqrt(sc);
+    // ---- batched complex coupled Newton-Schulz (same scaled steps as the finite path) ----
+    double *Y = ctx->dQ, *Z = ctx->dZ, *P = ctx->dP, *Y2 = ctx->dY2, *Z2 = ctx->dZ2;
+    cscale(Y, ld, nk, 1.0 / sc, s);
+    cset_identity(Z, ld, nk, s);
+    bool converged = false;
+    double resid = 0.0;
+    int it = 0;
+    for (; it < ctx->opt.ns_max_iter; ++it) {
+        const double *Pk = Y;
+        if (it > 0) {
+            timed_cgemm(Z, Y, nullptr, P, 1.0, 0.0);
+            Pk = P;
+        }
+        cfrob_dev_identity(Pk, ld, n, nk, ctx->dscal + 2, s);
+        double r2 = 0.0;
+        MBD_CUDA(cudaMemcpyAsync(&r2, ctx->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz");
+        MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
+        resid = std::sqrt(r2);
+        if (!std::isfinite(resid) || resid > 2.0 * std::sqrt(nd * nk) + 1.0) {
+            ctx->ns_iter = it;
+            ctx->ns_resid = resid;
+            return fail(ctx, MBD_ERR_NEG_EIGENVALUE, "newton_schulz",
+                        "Q(q) has a non-positive eigenvalue (polarization catastrophe)");
+        }
+        const bool last = resid < ctx->opt.ns_tol;
+        double al = 1.0;
+        if (!last && lbound < 0.999) al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
+        const double c1 = 1.5 * al, c3 = -0.5 * al * al * al;
+        lbound = std::min(1.0, 0.5 * al * lbound * (3.0 - al * al * lbound * lbound));
+        ubound = 1.0;
+        timed_cgemm(Y, Pk, Y, Y2, c3, c1);                 // Y' = c1 Y + c3 Y P
+        if (it == 0) caxpby_identity(Z2, Pk, ld, nk, c1, c3, s);
+        else timed_cgemm(Pk, Z, Z, Z2, c3, c1);            // Z' = c1 Z + c3 P Z
+        std::swap(Y, Y2);
+        std::swap(Z, Z2);
+        if (last) {
+            converged = true;
+            ++it;
+            break;
+        }
+    }
+    ctx->ns_iter = it;
+    ctx->ns_resid = resid;
+    if (!converged) return fail(ctx, MBD_ERR_NOT_CONVERGED, "newton_schulz", "iteration cap reached");
+    double *energy_out = out.energy ? out.energy : ctx->dscal;
+    energy_trace_periodic(Y, ld, n, nk, ctx->dombar, N, ss, energy_out, s);
+    ctx->Zlast = Z;
+    ctx->zscale = 1.0 / ss;
+    mark(ctx, s, e_ns);
+    if (want_grad) backward_periodic(ctx, s, b, nullptr, out.grad_coords, out.grad_params);
+    if (out.alpha_scs)
+        MBD_CUDA(cudaMemcpyAsync(out.alpha_scs, ctx->dabar0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s),
+                 "outputs");
+    mark(ctx, s, e_grad);
+    MBD_CUDA(cudaStreamSynchronize(s), "mbd_evaluate");
+    MBD_CUDA(cudaGetLastError(), "mbd_evaluate");
+    ctx->prof.launches = static_cast<int>(launch_count() - launches0);
+    if (ctx->profiling) {
+        mbd_profile &p = ctx->prof;
+        p.gemm_launches = 4 * static_cast<int>(gemms.size());
+        for (const Span &sp : gemms) {
+            p.gemm_ms += span_ms(sp.a, sp.b);
+            p.gemm_flops += sp.flops;
+        }
+        p.screening_ms = span_ms(e_start, e_scs);
+        p.screening_flops = nf1 * nd * nd * nd / 3.0;
+        p.newton_schulz_ms = span_ms(e_scs, e_ns);
+        p.gradient_ms = span_ms(e_ns, e_grad);
+        p.total_ms = span_ms(e_start, e_grad);
+    }
+    ctx->have_result = true;
+    ctx->have_forward = true;
+    return MBD_OK;
+}
+
 int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool want_grad) {
+    if (ctx->periodic) return run_periodic(ctx, s, in, out, want_grad);
     const int N = ctx->N, n = ctx->n, nf1 = ctx->nf1;
     const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;
     const double beta = ctx->opt.beta, a = ctx->opt.a;
@@ -556,7 +860,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     // largest tightens the scale s of Y0 = Q/s (Lanczos converges fast at the top of the
     // spectrum; a 5 % margin keeps Y0's spectrum inside (0, 1]); the smallest gives the
     // lower bound for the scaled iteration, halved for safety.
-    const int lz_steps = std::min(48, static_cast<int>(ld));
+    const int lz_steps = std::min(kLanczosSteps, static_cast<int>(ld));
     lanczos_coefficients(ctx->dQ, ld, lz_steps, ctx->dP, ctx->dscal + 8, s);
     std::vector<double> lz(2 * lz_steps);
     MBD_CUDA(cudaMemcpyAsync(lz.data(), ctx->dscal + 8, sizeof(double) * 2 * lz_steps, cudaMemcpyDeviceToHost, s),
@@ -705,6 +1009,9 @@ int mbd_default_options(mbd_options *opt) {
     opt->ns_tol = 1e-8;
     opt->ns_max_iter = 100;
     opt->tc_chunk_stages = 2;
+    opt->ewald_gamma = 0.0;
+    opt->real_cutoff = 0.0;
+    opt->recip_cutoff = 0.0;
     return MBD_OK;
 }
 
@@ -753,22 +1060,50 @@ int mbd_destroy(mbd_ctx *ctx) {
 int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const double *lattice,
                      const int *k_grid) {
     if (!ctx) return MBD_ERR_INPUT;
-    if (lattice || k_grid)
-        return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_set_geometry", "periodic systems are not available in this build");
+    if ((lattice == nullptr) != (k_grid == nullptr))
+        return fail(ctx, MBD_ERR_INPUT, "mbd_set_geometry", "lattice and k_grid are given together or not at all");
     if (n_atoms < 1 || !coords) return fail(ctx, MBD_ERR_INPUT, "mbd_set_geometry", "need n_atoms >= 1 and coords");
     for (int k = 0; k < 3 * n_atoms; ++k)
         if (!std::isfinite(coords[k])) return fail(ctx, MBD_ERR_INPUT, "mbd_set_geometry", "non-finite coordinate");
+    const bool periodic = lattice != nullptr;
+    PeriodicSetup ps;
+    if (periodic) {
+        if (ctx->opt.precision != MBD_PREC_FP64)
+            return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_set_geometry", "periodic systems run in FP64 only");
+        const int rc = periodic_setup(ctx->opt, lattice, k_grid, ps);
+        if (rc) return fail(ctx, rc, "mbd_set_geometry", ps.msg);
+    }
     MBD_CUDA(cudaSetDevice(ctx->device), "mbd_set_geometry");
-    const bool realloc = (n_atoms != ctx->N) || !ctx->slab;
+    const bool realloc = (n_atoms != ctx->N) || !ctx->slab || periodic != ctx->periodic ||
+                         (periodic && (ps.nk != ctx->nk || ps.nG != ctx->nG || ps.maxG != ctx->maxG));
     ctx->N = n_atoms;
     ctx->n = 3 * n_atoms;
     ctx->ld = (ctx->n + 127) / 128 * 128;   // 128: the tensor-core tile (also a multiple of 64)
     ctx->nb = static_cast<int>(ctx->ld / kTile);
     ctx->hR.assign(coords, coords + 3 * n_atoms);
+    ctx->periodic = periodic;
+    if (periodic) {
+        ctx->cell = ps.cell;
+        ctx->nk = ps.nk;
+        ctx->nG = ps.nG;
+        ctx->maxG = ps.maxG;
+        ctx->hkq = ps.kq;
+        ctx->hG = ps.G;
+        ctx->hglist = ps.glist;
+        ctx->hgcount = ps.gcount;
+    } else {
+        ctx->nk = 1;
+        ctx->nG = ctx->maxG = 0;
+    }
+    ctx->have_lattice_grad = false;
     if (realloc) {
         ctx->have_params = false;
         ctx->have_forward = false;
         int rc = allocate(ctx);
+        if (rc) { ctx->have_geom = false; return rc; }
+    }
+    if (periodic) {
+        const int rc = upload_periodic(ctx);
         if (rc) { ctx->have_geom = false; return rc; }
     }
     ctx->have_geom = true;
@@ -797,7 +1132,8 @@ int mbd_evaluate(mbd_ctx *ctx, double *energy, double *grad_coords, double *grad
     if (!ctx) return MBD_ERR_INPUT;
     if (!ctx->have_geom || !ctx->have_params)
         return fail(ctx, MBD_ERR_STATE, "mbd_evaluate", "set the geometry and the free-atom parameters first");
-    if (grad_lattice) return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_evaluate", "no lattice gradient for finite systems");
+    if (grad_lattice && !ctx->periodic)
+        return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_evaluate", "no lattice gradient for finite systems");
     if (!energy) return fail(ctx, MBD_ERR_INPUT, "mbd_evaluate", "energy pointer is required");
     MBD_CUDA(cudaSetDevice(ctx->device), "mbd_evaluate");
     const int N = ctx->N;
@@ -807,7 +1143,7 @@ int mbd_evaluate(mbd_ctx *ctx, double *energy, double *grad_coords, double *grad
     MBD_CUDA(cudaMemcpyAsync(ctx->dc6ref, ctx->hc6.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_evaluate");
     MBD_CUDA(cudaMemcpyAsync(ctx->drref, ctx->hrr.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_evaluate");
     MBD_CUDA(cudaMemcpyAsync(ctx->dratio, ctx->hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_evaluate");
-    const bool want_grad = grad_coords || grad_params;
+    const bool want_grad = grad_coords || grad_params || grad_lattice;
     Inputs in{ctx->dR, ctx->da0ref, ctx->dc6ref, ctx->drref, ctx->dratio};
     Outputs o{ctx->dscal, nullptr, grad_params ? ctx->dgp : nullptr, nullptr};   // gradients stay in dgR
     int rc = run(ctx, s, in, o, want_grad);
@@ -820,6 +1156,8 @@ int mbd_evaluate(mbd_ctx *ctx, double *energy, double *grad_coords, double *grad
         MBD_CUDA(cudaMemcpyAsync(grad_params, ctx->dgp, sizeof(double) * 4 * N, cudaMemcpyDeviceToHost, s), "mbd_evaluate");
     if (alpha_scs)
         MBD_CUDA(cudaMemcpyAsync(alpha_scs, ctx->dabar0, sizeof(double) * N, cudaMemcpyDeviceToHost, s), "mbd_evaluate");
+    if (grad_lattice)
+        MBD_CUDA(cudaMemcpyAsync(grad_lattice, ctx->dgAout, sizeof(double) * 9, cudaMemcpyDeviceToHost, s), "mbd_evaluate");
     MBD_CUDA(cudaStreamSynchronize(s), "mbd_evaluate");
     *energy = e;
     return MBD_OK;
@@ -854,9 +1192,19 @@ int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
     MBD_CUDA(cudaSetDevice(ctx->device), "mbd_backward_dev");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Inputs in{coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio};
-    backward_passes(ctx, s, atom_bufs(ctx, in), grad_energy, grad_coords, grad_params);
+    if (ctx->periodic) backward_periodic(ctx, s, atom_bufs(ctx, in), grad_energy, grad_coords, grad_params);
+    else backward_passes(ctx, s, atom_bufs(ctx, in), grad_energy, grad_coords, grad_params);
     MBD_CUDA(cudaStreamSynchronize(s), "mbd_backward_dev");
     MBD_CUDA(cudaGetLastError(), "mbd_backward_dev");
+    return MBD_OK;
+}
+
+int mbd_get_lattice_gradient(mbd_ctx *ctx, double *grad_lattice) {
+    if (!ctx || !grad_lattice) return MBD_ERR_INPUT;
+    if (!ctx->periodic || !ctx->have_lattice_grad)
+        return fail(ctx, MBD_ERR_STATE, "mbd_get_lattice_gradient", "no lattice gradient has been computed");
+    MBD_CUDA(cudaSetDevice(ctx->device), "mbd_get_lattice_gradient");
+    MBD_CUDA(cudaMemcpy(grad_lattice, ctx->dgAout, sizeof(double) * 9, cudaMemcpyDeviceToHost), "mbd_get_lattice_gradient");
     return MBD_OK;
 }
 

@@ -181,14 +181,6 @@ def triclinic_cell(n_atoms=256, edge=(20.0, 26.0), angle=(80.0, 100.0), dmin=2.5
                   meta=dict(seed=seed, dmin=dmin))
 
 
-def monkhorst_pack(k_grid) -> np.ndarray:
-    """Fractional k-points of an unshifted-by-Gamma uniform grid: (2m - n_d - 1)/(2 n_d)
-    per axis, which never contains Gamma for even n_d."""
-    axes = [(2.0 * np.arange(1, n + 1) - n - 1) / (2.0 * n) for n in k_grid]
-    g = np.array(np.meshgrid(*axes, indexing="ij")).reshape(3, -1).T
-    return np.ascontiguousarray(g)
-
-
 def cluster_batch(n_clusters=4096, n_range=(50, 500), density=DENSITY_CLUSTER, dmin=2.2,
                   seed0=4000):
     """Varlen batch of sphere clusters, cluster i seeded 4000 + i, size U{lo..hi}."""
