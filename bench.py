@@ -32,6 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = "MBD energy+gradient solves/s & TFLOP/s vs FP64 GPU path at |ΔE|≤1e-6 Ha/atom"
 UNIT = "solves/s"
 WORKLOAD = "finite2000"
+# Ewald split, real-space and reciprocal cutoffs of the periodic workload (real-space cutoff
+# 30 bohr; gamma = 6/30, k_c = 10 gamma)
+PERIODIC_EWALD = (0.2, 30.0, 2.0)
+N_TARGET = {"finite2000": 2000, "cell256": 256, "finite8000": 8000}
 # nominal FP64 : dense BF16 tensor rate of the part (1.25 TFLOP/s : 2250 TFLOP/s)
 FP64_OVER_BF16 = 1.25 / 2250.0
 # DRAM bytes (read + write) per k_gemm_nn launch from the committed ncu capture
@@ -51,6 +55,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("finite2000", "cell256", "finite8000"), default=WORKLOAD,
+                    help="finite2000: the headline cluster; cell256: the periodic cell (FP64 only); "
+                         "finite8000: the large cluster")
     ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64"), default="tf32x3",
                     help="matrix-function arithmetic of the timed arm (the FP64 path is measured beside it)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison arm (0: skip)")
@@ -126,19 +133,39 @@ def measured_peaks():
         return None
 
 
-def cpu_baseline(n_sample: int, n_target: int, seed: int = 1000):
-    """Times the CPU oracle (as it stands) on a same-recipe cluster of n_sample atoms and
-    extrapolates to n_target atoms by the cubic cost of its dense stages."""
-    import oracle as o
+def sample_system(workload: str, n_sample: int):
+    """Bounded same-recipe sample of a workload for the CPU oracle: a cluster of n_sample
+    atoms (finite), or a cell of n_sample atoms with edges scaled to keep the density and the
+    same k-grid and cutoffs (periodic)."""
     from paper_2308_03140_gb300 import synthetic as syn
-    sysm = syn.sphere_cluster(n_sample, seed=seed)
+    if workload == "cell256":
+        f = (n_sample / 256.0) ** (1.0 / 3.0)
+        return syn.triclinic_cell(n_sample, edge=(20.0 * f, 26.0 * f), seed=2000)
+    return syn.sphere_cluster(n_sample, seed=1000)
+
+
+def oracle_solve(sysm):
+    """One energy+gradient by the CPU oracle (as it stands)."""
+    import oracle as o
+    if sysm.lattice is not None:
+        g, rc, kc = PERIODIC_EWALD
+        return o.periodic_rsscs_gradient(sysm.coords, sysm.lattice, o.monkhorst_pack(sysm.k_grid),
+                                         sysm.alpha0_ref, sysm.c6_ref, sysm.rvdw_ref, sysm.ratio, g, rc, kc)
+    return o.mbd_rsscs_gradient(*o.system_args(sysm), mode="adjoint")
+
+
+def cpu_baseline(workload: str, n_sample: int, n_target: int):
+    """Times the CPU oracle (as it stands) on a same-recipe sample of n_sample atoms and
+    extrapolates to n_target atoms by the cubic cost of its dense stages."""
+    sysm = sample_system(workload, n_sample)
     t0 = time.perf_counter()
-    o.mbd_rsscs_gradient(*o.system_args(sysm), mode="adjoint")
+    oracle_solve(sysm)
     dt = time.perf_counter() - t0
     scale = (n_target / n_sample) ** 3
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    kind = "cell" if sysm.lattice is not None else "cluster"
     return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"energy+gradient of a {n_sample}-atom cluster of the same recipe in "
+            "sample": f"energy+gradient of a {n_sample}-atom {kind} of the same recipe in "
                       f"{dt:.2f} s, extrapolated by (n/{n_sample})^3 to {n_target} atoms",
             "sample_seconds": dt}
 
@@ -147,32 +174,30 @@ def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
-    import oracle as o
-    from paper_2308_03140_gb300 import synthetic as syn
-    n_target = 2000
-    n_s = min(args.cpu_sample_atoms, 200)
-    sysm = syn.sphere_cluster(n_s, seed=1000)
-    a = o.system_args(sysm)
+    n_target = N_TARGET[args.workload]
+    n_s = min(args.cpu_sample_atoms, 200) if args.workload != "cell256" else 32
+    sysm = sample_system(args.workload, n_s)
     for _ in range(args.warmup):
-        o.mbd_rsscs_gradient(*a, mode="adjoint")
+        oracle_solve(sysm)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.mbd_rsscs_gradient(*a, mode="adjoint")
+        oracle_solve(sysm)
         times.append(time.perf_counter() - t0)
     dt = sum(times)
     scale = (n_target / n_s) ** 3
     value = args.steps / (dt * scale)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    kind = "cell" if sysm.lattice is not None else "cluster"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt * scale / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_atoms": n_target, "n_freq": 15, "precision": "fp64",
+            "config": {"workload": args.workload, "n_atoms": n_target, "n_freq": 15, "precision": "fp64",
                        "sample_atoms": n_s},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step one energy+gradient of a {n_s}-atom cluster of the same "
-                                       f"recipe, extrapolated by (2000/{n_s})^3"},
+                             "sample": f"each step one energy+gradient of a {n_s}-atom {kind} of the same "
+                                       f"recipe, extrapolated by ({n_target}/{n_s})^3"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -205,7 +230,10 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return t.item()
 
-    sysm = syn.workload(WORKLOAD)
+    sysm = syn.workload(args.workload)
+    periodic = sysm.lattice is not None
+    if periodic and args.precision != "fp64":
+        args.precision = "fp64"   # periodic systems run in FP64
     N = sysm.n_atoms
     T = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
     inp = [T(sysm.coords), T(sysm.alpha0_ref), T(sysm.c6_ref), T(sysm.rvdw_ref), T(sysm.ratio)]
@@ -216,8 +244,10 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     precision = {"fp64": binding.MBD_PREC_FP64, "tf32": binding.MBD_PREC_TF32,
                  "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3}[args.precision]
-    m = binding.MBD(local, precision=precision)
-    m.set_geometry(sysm.coords)
+    ewald = dict(ewald_gamma=PERIODIC_EWALD[0], real_cutoff=PERIODIC_EWALD[1],
+                 recip_cutoff=PERIODIC_EWALD[2]) if periodic else {}
+    m = binding.MBD(local, precision=precision, **ewald)
+    m.set_geometry(sysm.coords, sysm.lattice, sysm.k_grid)
     m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, sysm.rvdw_ref, sysm.ratio)
 
     def step():
@@ -251,13 +281,15 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        m.set_geometry(sysm.coords)
+        m.set_geometry(sysm.coords, sysm.lattice, sysm.k_grid)
         m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, sysm.rvdw_ref, sysm.ratio)
         E_h, gR_h, gp_h, al_h = m.evaluate(True)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 8 * (3 * N + 4 * N),
-           "d2h_bytes_per_step": 8 * (1 + 3 * N + 4 * N + N)}
+           "d2h_bytes_per_step": 8 * (1 + 3 * N + 4 * N + N + (9 if periodic else 0))}
+    if periodic:
+        e2e["h2d_bytes_per_step"] += 8 * 9 + 4 * 3   # lattice and k-grid
 
     gR_t, gp_t = gR.detach().cpu().numpy().copy(), gp.detach().cpu().numpy().copy()
     # FP64 comparison arm (same workload and API; fewer steps: it is ~20x slower)
@@ -303,7 +335,8 @@ def run_ours(args):
         peak = bf16_sus * FP64_OVER_BF16
         peak_src = f"{src}: bf16_tflops_sustained x nominal FP64/BF16 ratio (1.25/2250)"
         cur = hashlib.sha256(open(os.path.join(ROOT, "paper_2308_03140_gb300", "csrc", "k_dense.cu"), "rb").read())
-        traffic = GEMM_NN_TRAFFIC["bytes"] if cur.hexdigest()[:16] == GEMM_NN_TRAFFIC["k_dense_sha16"] else None
+        traffic = (GEMM_NN_TRAFFIC["bytes"] if args.workload == "finite2000" and
+                   cur.hexdigest()[:16] == GEMM_NN_TRAFFIC["k_dense_sha16"] else None)
     else:
         # tcgen05 GEMMs of the iteration and of the correction
         kernel = "k_tc_gemm (tcgen05 + TMA + TMEM; Newton-Schulz and correction products)"
@@ -316,8 +349,8 @@ def run_ours(args):
         peak_src = (f"{src}: bf16_tflops_sustained x nominal {per_kind[2][:4]}/BF16 rate ({per_kind[0]}) / "
                     f"{per_kind[1]} tensor products per algorithmic product")
         cur = hashlib.sha256(open(os.path.join(ROOT, "paper_2308_03140_gb300", "csrc", "k_tc.cu"), "rb").read())
-        traffic = (TC_GEMM_TRAFFIC["bytes"] if precision == binding.MBD_PREC_TF32X3 and
-                   cur.hexdigest()[:16] == TC_GEMM_TRAFFIC["k_tc_sha16"] else None)
+        traffic = (TC_GEMM_TRAFFIC["bytes"] if precision == binding.MBD_PREC_TF32X3 and args.workload == "finite2000"
+                   and cur.hexdigest()[:16] == TC_GEMM_TRAFFIC["k_tc_sha16"] else None)
     achieved = k_flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
     n = 3 * N
     exec_flops = sum(p["gemm_flops"] + p["tc_flops"] + p["screening_flops"] for p in profs) / args.steps
@@ -327,10 +360,15 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == binding.MBD_PREC_FP64 else
         f"{args.precision}+f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_atoms": N, "matrix_order": n, "n_freq": 15,
+        "config": {"workload": args.workload, "n_atoms": N, "matrix_order": n, "n_freq": 15,
                    "precision": args.precision, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2: 16 screening matrices + 5 Newton-Schulz matrices of "
-                         f"{8 * n * n / 1e6:.0f} MB each per step"},
+                   "l2": ("inputs larger than L2: 16 screening matrices + 5 Newton-Schulz matrices of "
+                          f"{8 * n * n / 1e6:.0f} MB each per step" if not periodic else
+                          f"inputs larger than L2: 5 Newton-Schulz sets of {len(sysm.k_grid and range(int(np.prod(sysm.k_grid))))} "
+                          f"complex {n}x{n} matrices ({16 * n * n * int(np.prod(sysm.k_grid)) / 1e6:.0f} MB each set)"),
+                   **({"lattice_bohr": np.asarray(sysm.lattice).round(4).tolist(), "k_grid": list(sysm.k_grid),
+                       "ewald_gamma": PERIODIC_EWALD[0], "real_cutoff_bohr": PERIODIC_EWALD[1],
+                       "recip_cutoff_per_bohr": PERIODIC_EWALD[2]} if periodic else {})},
         "tflops": exec_flops / (ms / args.steps / 1e3) / 1e12,
         "roofline": {"kernel": kernel, "bound": "tensor",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -354,7 +392,7 @@ def run_ours(args):
         "ns_residual": st["ns_residual"], "correction_residual": st["correction_residual"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_atoms, N)
+        line["cpu_baseline"] = cpu_baseline(args.workload, 32 if periodic else args.cpu_sample_atoms, N)
     if rank == 0:
         print(json.dumps(line), flush=True)
     m.close()

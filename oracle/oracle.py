@@ -63,6 +63,8 @@ def lib():
             L.orc_mbd_energy.argtypes = [i, _dp, _dp, _dp, _dp, d, d, P]
             L.orc_mbd_rsscs_energy.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, P, P]
             L.orc_mbd_rsscs_gradient.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, i, P, _dp, _dp]
+            L.alpha_iu.argtypes = [d, d, d]
+            L.alpha_iu.restype = d
             # periodic
             L.orc_cell_reciprocal.argtypes = [_dp, _dp, P]
             L.orc_monkhorst_pack.argtypes = [C.POINTER(C.c_int), _dp]
@@ -152,6 +154,11 @@ def ts_scaling(a0ref, c6ref, rref, ratio):
     N = len(a0ref); a0, om, rv = np.zeros(N), np.zeros(N), np.zeros(N)
     lib().orc_ts_scaling(N, _a(a0ref), _a(c6ref), _a(rref), _a(ratio), a0, om, rv)
     return a0, om, rv
+
+
+def dyn_alpha(alpha0, omega, u):
+    """alpha_i(iu), Eq. (dyn-pol), per atom."""
+    return np.array([lib().alpha_iu(float(a0), float(w), float(u)) for a0, w in zip(alpha0, omega)])
 
 
 def scs_matrix(R, alpha, rvdw, beta=0.83, a=6.0):
