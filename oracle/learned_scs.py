@@ -1,0 +1,151 @@
+"""Plain FP64 oracle of the learned screening model (NumPy, explicit definitions).
+
+TEST INFRASTRUCTURE ONLY, like the rest of oracle/: used by the tests and the benchmark's
+CPU leg, never by the product path; it shares no code with the CUDA kernels.
+
+The paper has no learned part; the model below is this project's reading of the task it
+stands in for (the screening of Eqs. scs and contraction, Sec. 2.3):
+- features of atom i (68): for every other atom j of the same system at distance d < 24 bohr,
+  alpha0_j fc(d) G_m(d) summed over j, for 64 Gaussians G_m(d) = exp(-(d - mu_m)^2 / (2 w^2)),
+  mu_m = (m + 1/2) w, w = 0.375 bohr (4 radial shells of 6 bohr x 16 Gaussians, width =
+  spacing), fc(d) = (1 + cos(pi d / 24)) / 2 (smooth cutoff); then the atom's own TS-scaled
+  alpha0, omega, R_vdW and its volume ratio;
+- standardisation x' = (x - mean) / std with stored mean and std;
+- MLP 68 -> 128 -> 128 -> 16, SiLU activations, FP16 weights (rounded; the oracle evaluates
+  them exactly in FP64);
+- output y_k = log(alpha_bar_i(u_k) / alpha_i(u_k)) at the 16 grid points (u_0 = 0);
+- ensemble of members: the prediction is the mean of y over members; the spread s_i(u) of the
+  predicted alpha_bar over members gives the energy error estimate
+  |dE| ~ sum_{i,u} |dE/d alpha_bar_i(u)| s_i(u) (the adjoints of the screened-parameter chain).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+N_SHELL, N_GAUSS = 4, 16
+SHELL = 6.0
+CUTOFF = N_SHELL * SHELL
+WIDTH = SHELL / N_GAUSS
+N_FEAT = N_SHELL * N_GAUSS + 4
+HIDDEN = 128
+N_OUT = 16
+LAYERS = ((N_FEAT, HIDDEN), (HIDDEN, HIDDEN), (HIDDEN, N_OUT))
+
+
+def centers():
+    return (np.arange(N_SHELL * N_GAUSS) + 0.5) * WIDTH
+
+
+def cutoff_fn(d):
+    """fc(d) = (1 + cos(pi d / 24)) / 2 for d < 24, else 0."""
+    return np.where(d < CUTOFF, 0.5 * (1.0 + np.cos(np.pi * d / CUTOFF)), 0.0)
+
+
+def features(R, a0, om, rv, ratio):
+    """Raw features [N, 68] of one system (TS-scaled a0, om, rv), by the definition above,
+    one atom pair at a time."""
+    R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
+    N = R.shape[0]
+    mu = centers()
+    X = np.zeros((N, N_FEAT))
+    for i in range(N):
+        for j in range(N):
+            if j == i:
+                continue
+            d = np.linalg.norm(R[j] - R[i])
+            if d >= CUTOFF:
+                continue
+            X[i, :64] += a0[j] * cutoff_fn(d) * np.exp(-(d - mu) ** 2 / (2.0 * WIDTH ** 2))
+        X[i, 64:] = (a0[i], om[i], rv[i], ratio[i])
+    return X
+
+
+def feature_position_jacobian(R, a0):
+    """dX[i, m] / dR[k, c] for the 64 radial features: [N, 64, N, 3] (for the force pins)."""
+    R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
+    N = R.shape[0]
+    mu = centers()
+    J = np.zeros((N, 64, N, 3))
+    for i in range(N):
+        for j in range(N):
+            if j == i:
+                continue
+            r = R[j] - R[i]
+            d = np.linalg.norm(r)
+            if d >= CUTOFF:
+                continue
+            g = np.exp(-(d - mu) ** 2 / (2.0 * WIDTH ** 2))
+            fc = cutoff_fn(d)
+            dfc = -0.5 * np.pi / CUTOFF * np.sin(np.pi * d / CUTOFF)
+            dval = a0[j] * (dfc * g + fc * g * (-(d - mu) / WIDTH ** 2))   # d/dd
+            for c in range(3):
+                J[i, :, j, c] += dval * r[c] / d
+                J[i, :, i, c] -= dval * r[c] / d
+    return J
+
+
+def silu(z):
+    return z / (1.0 + np.exp(-z))
+
+
+def dsilu(z):
+    s = 1.0 / (1.0 + np.exp(-z))
+    return s * (1.0 + z * (1.0 - s))
+
+
+def round_fp16(params):
+    """Weights and biases as the GPU stores them (FP16), returned in FP64."""
+    return [(np.asarray(W, np.float16).astype(np.float64), np.asarray(b, np.float16).astype(np.float64))
+            for W, b in params]
+
+
+def forward(Xs, params):
+    """MLP on standardised features Xs [B, 68]; params [(W [in, out], b [out])] x 3.
+    Returns y [B, 16] and the cache for backward."""
+    z1 = Xs @ params[0][0] + params[0][1]
+    h1 = silu(z1)
+    z2 = h1 @ params[1][0] + params[1][1]
+    h2 = silu(z2)
+    y = h2 @ params[2][0] + params[2][1]
+    return y, (Xs, z1, h1, z2, h2)
+
+
+def backward(dy, params, cache):
+    """Gradients of sum(dy * y) with respect to the weights, biases and the inputs."""
+    Xs, z1, h1, z2, h2 = cache
+    gW3, gb3 = h2.T @ dy, dy.sum(0)
+    dz2 = (dy @ params[2][0].T) * dsilu(z2)
+    gW2, gb2 = h1.T @ dz2, dz2.sum(0)
+    dz1 = (dz2 @ params[1][0].T) * dsilu(z1)
+    gW1, gb1 = Xs.T @ dz1, dz1.sum(0)
+    dX = dz1 @ params[0][0].T
+    return [(gW1, gb1), (gW2, gb2), (gW3, gb3)], dX
+
+
+def mse_loss_grad(y, t):
+    """Loss mean((y - t)^2) over all entries and its gradient with respect to y."""
+    diff = y - t
+    return float(np.mean(diff ** 2)), 2.0 * diff / diff.size
+
+
+def adam_step(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba), in place; step counts from 1."""
+    m[...] = b1 * m + (1 - b1) * g
+    v[...] = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** step)
+    vh = v / (1 - b2 ** step)
+    p[...] = p - lr * mh / (np.sqrt(vh) + eps)
+
+
+def predict_alpha_bar(Xs, members, alpha_u):
+    """Ensemble prediction: alpha_bar [16, N] = alpha(u) exp(mean_m y_m) and the spread
+    s [16, N] of alpha(u) exp(y_m) over the members (population standard deviation)."""
+    ys = np.stack([forward(Xs, p)[0] for p in members])          # [M, N, 16]
+    ab_m = alpha_u.T[None, :, :] * np.exp(ys)                   # [M, N, 16]
+    ab = alpha_u.T * np.exp(ys.mean(0))
+    return ab.T, ab_m.std(0).T
+
+
+def estimated_error_per_atom(h, spread):
+    """|dE| estimate per atom: sum_{i,u} |dE/d alpha_bar_i(u)| s_i(u) / N."""
+    return float(np.abs(h * spread).sum() / h.shape[1])
