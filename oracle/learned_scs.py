@@ -5,13 +5,17 @@ CPU leg, never by the product path; it shares no code with the CUDA kernels.
 
 The paper has no learned part; the model below is this project's reading of the task it
 stands in for (the screening of Eqs. scs and contraction, Sec. 2.3):
-- features of atom i (68): for every other atom j of the same system at distance d < 24 bohr,
+- features of atom i (74): for every other atom j of the same system at distance d < 24 bohr,
   alpha0_j fc(d) G_m(d) summed over j, for 64 Gaussians G_m(d) = exp(-(d - mu_m)^2 / (2 w^2)),
   mu_m = (m + 1/2) w, w = 0.375 bohr (4 radial shells of 6 bohr x 16 Gaussians, width =
   spacing), fc(d) = (1 + cos(pi d / 24)) / 2 (smooth cutoff); then the atom's own TS-scaled
-  alpha0, omega, R_vdW and its volume ratio;
+  alpha0, omega, R_vdW and its volume ratio; then the screening moments of the static
+  Dyson series (Eqs. scs, contraction at u = 0): with M_i = sum_{j, d<24} alpha0_j
+  (1 - f_ij) T^GG_ij (the SCS coupling of Eq. scs-sr-dipole, widths of Eq. mayer),
+  m1 = Tr M_i / 3 (first order), m2 = Tr(sum_j alpha0_j (1 - f_ij) T^GG_ij M_j) / 3 (second
+  order, two hops), m3 = Tr(M_i M_i) / 3, each also times alpha0_i (m1) or alpha0_i^2 (m2, m3);
 - standardisation x' = (x - mean) / std with stored mean and std;
-- MLP 68 -> 128 -> 128 -> 16, SiLU activations, FP16 weights (rounded; the oracle evaluates
+- MLP 74 -> 128 -> 128 -> 16, SiLU activations, FP16 weights (rounded; the oracle evaluates
   them exactly in FP64);
 - output y_k = log(alpha_bar_i(u_k) / alpha_i(u_k)) at the 16 grid points (u_0 = 0);
 - ensemble of members: the prediction is the mean of y over members; the spread s_i(u) of the
@@ -26,7 +30,7 @@ N_SHELL, N_GAUSS = 4, 16
 SHELL = 6.0
 CUTOFF = N_SHELL * SHELL
 WIDTH = SHELL / N_GAUSS
-N_FEAT = N_SHELL * N_GAUSS + 4
+N_FEAT = N_SHELL * N_GAUSS + 4 + 6
 HIDDEN = 128
 N_OUT = 16
 LAYERS = ((N_FEAT, HIDDEN), (HIDDEN, HIDDEN), (HIDDEN, N_OUT))
@@ -41,13 +45,29 @@ def cutoff_fn(d):
     return np.where(d < CUTOFF, 0.5 * (1.0 + np.cos(np.pi * d / CUTOFF)), 0.0)
 
 
+def scs_coupling(r, a0_i, a0_j, rv_i, rv_j, beta=0.83, a=6.0):
+    """(1 - f) T^GG of one pair at u = 0 (Eqs. scs-sr-dipole, tgg, mayer, fermi-damping), by the
+    finite oracle's own tensor and damping routines."""
+    from oracle import oracle as orc
+    s = np.hypot(orc_sigma(a0_i), orc_sigma(a0_j))
+    d = np.linalg.norm(r)
+    return (1.0 - orc.fermi(d, rv_i + rv_j, beta, a)) * orc.T_gg(r, s)
+
+
+def orc_sigma(alpha):
+    """Mayer width of Eq. (mayer): (sqrt(2/pi) alpha / 3)^(1/3)."""
+    return np.cbrt(np.sqrt(2.0 / np.pi) * alpha / 3.0)
+
+
 def features(R, a0, om, rv, ratio):
-    """Raw features [N, 68] of one system (TS-scaled a0, om, rv), by the definition above,
+    """Raw features [N, 74] of one system (TS-scaled a0, om, rv), by the definition above,
     one atom pair at a time."""
     R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
     N = R.shape[0]
     mu = centers()
     X = np.zeros((N, N_FEAT))
+    M = np.zeros((N, 3, 3))
+    B = {}
     for i in range(N):
         for j in range(N):
             if j == i:
@@ -56,12 +76,21 @@ def features(R, a0, om, rv, ratio):
             if d >= CUTOFF:
                 continue
             X[i, :64] += a0[j] * cutoff_fn(d) * np.exp(-(d - mu) ** 2 / (2.0 * WIDTH ** 2))
-        X[i, 64:] = (a0[i], om[i], rv[i], ratio[i])
+            B[i, j] = scs_coupling(R[j] - R[i], a0[i], a0[j], rv[i], rv[j])
+            M[i] += a0[j] * B[i, j]
+        X[i, 64:68] = (a0[i], om[i], rv[i], ratio[i])
+    for i in range(N):
+        two_hop = np.zeros((3, 3))
+        for j in range(N):
+            if (i, j) in B:
+                two_hop += a0[j] * B[i, j] @ M[j]
+        m1, m2, m3 = np.trace(M[i]) / 3.0, np.trace(two_hop) / 3.0, np.trace(M[i] @ M[i]) / 3.0
+        X[i, 68:] = (m1, m2, m3, a0[i] * m1, a0[i] ** 2 * m2, a0[i] ** 2 * m3)
     return X
 
 
 def feature_position_jacobian(R, a0):
-    """dX[i, m] / dR[k, c] for the 64 radial features: [N, 64, N, 3] (for the force pins)."""
+    """dX[i, m] / dR[k, c] for the 64 radial features: [N, 64, N, 3]."""
     R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
     N = R.shape[0]
     mu = centers()
@@ -100,7 +129,7 @@ def round_fp16(params):
 
 
 def forward(Xs, params):
-    """MLP on standardised features Xs [B, 68]; params [(W [in, out], b [out])] x 3.
+    """MLP on standardised features Xs [B, 74]; params [(W [in, out], b [out])] x 3.
     Returns y [B, 16] and the cache for backward."""
     z1 = Xs @ params[0][0] + params[0][1]
     h1 = silu(z1)

@@ -19,14 +19,23 @@ def test_two_atom_features_closed_form():
     fc = 0.5 * (1 + np.cos(np.pi * 5.5 / 24))
     assert np.allclose(X[0, :64], 9.0 * fc * np.exp(-(5.5 - mu) ** 2 / (2 * 0.375 ** 2)), rtol=1e-14, atol=0)
     assert np.allclose(X[1, :64], 7.0 * fc * np.exp(-(5.5 - mu) ** 2 / (2 * 0.375 ** 2)), rtol=1e-14, atol=0)
-    assert np.allclose(X[0, 64:], [7.0, 0.4, 3.1, 0.8]) and np.allclose(X[1, 64:], [9.0, 0.6, 3.6, 0.9])
+    assert np.allclose(X[0, 64:68], [7.0, 0.4, 3.1, 0.8]) and np.allclose(X[1, 64:68], [9.0, 0.6, 3.6, 0.9])
     assert np.argmax(X[0, :64]) == 14                          # mu_14 = 5.4375 is the nearest centre
+    # screening moments of one pair: M_0 = a0_1 B, M_1 = a0_0 B with B = (1 - f) T^GG (even in r)
+    from oracle import oracle as orc
+    s = np.hypot(*np.cbrt(np.sqrt(2 / np.pi) * a0 / 3))
+    Bm = (1 - orc.fermi(5.5, 3.1 + 3.6, 0.83, 6.0)) * orc.T_gg(R[1] - R[0], s)
+    tr, tr2 = np.trace(Bm), np.trace(Bm @ Bm)
+    # two hops: alpha0_j B (alpha0_i B) = 63 B^2 for either atom
+    assert np.allclose(X[0, 68:], [9 * tr / 3, 63 * tr2 / 3, 81 * tr2 / 3, 7 * 9 * tr / 3,
+                                   49 * 63 * tr2 / 3, 49 * 81 * tr2 / 3], rtol=1e-12)
+    assert np.allclose(X[1, 68:71], [7 * tr / 3, 63 * tr2 / 3, 49 * tr2 / 3], rtol=1e-12)
 
 
 def test_features_vanish_beyond_cutoff_and_are_continuous_there():
     a0, om, rv, v = np.ones(2) * 6, np.ones(2) * 0.5, np.ones(2) * 3.5, np.ones(2)
     far = L.features(np.array([[0, 0, 0], [0, 0, 24.0]]), a0, om, rv, v)
-    assert np.all(far[:, :64] == 0)
+    assert np.all(far[:, :64] == 0) and np.all(far[:, 68:] == 0)
     near = L.features(np.array([[0, 0, 0], [0, 0, 24.0 - 1e-6]]), a0, om, rv, v)
     assert np.abs(near[:, :64]).max() < 1e-10                  # smooth cutoff: fc(24) = fc'(24) = 0
 
@@ -82,7 +91,7 @@ def test_mlp_backward_vs_fd():
         Bm = [(w.copy(), bb.copy()) for w, bb in P]
         Bp[li][1][1] += h; Bm[li][1][1] -= h
         assert (f(Bp, X) - f(Bm, X)) / (2 * h) == pytest.approx(grads[li][1][1], rel=1e-6, abs=1e-9)
-    for (a, c) in [(0, 0), (3, 67), (5, 20)]:
+    for (a, c) in [(0, 0), (3, 73), (5, 20)]:
         Xp, Xm = X.copy(), X.copy()
         Xp[a, c] += h; Xm[a, c] -= h
         assert (f(P, Xp) - f(P, Xm)) / (2 * h) == pytest.approx(dX[a, c], rel=1e-6, abs=1e-9)
