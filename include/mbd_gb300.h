@@ -79,7 +79,16 @@ typedef struct {
     double ewald_gamma;   /* Ewald splitting parameter (1/bohr)                          */
     double real_cutoff;   /* real-space cutoff (bohr)                                    */
     double recip_cutoff;  /* reciprocal-space cutoff on |G + q| (1/bohr)                 */
+    /* Screening: MBD_SCS_PLAIN (the Dyson solves of Eq. (scs)) or MBD_SCS_LEARNED (the model
+     * set by mbd_set_scs_model predicts alpha_bar(iu); when its estimated energy error per
+     * atom exceeds learned_max_error (Ha, default 1e-6) the evaluation is redone with plain
+     * screening).  The learned model is not part of the paper.                          */
+    int scs_mode;
+    double learned_max_error;
 } mbd_options;
+
+#define MBD_SCS_PLAIN 0
+#define MBD_SCS_LEARNED 1
 
 /* Fills *opt with the defaults above.  Returns MBD_ERR_INPUT if opt is NULL. */
 int mbd_default_options(mbd_options *opt);
@@ -139,6 +148,25 @@ int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
                      const double *alpha0_ref, const double *c6_ref, const double *rvdw_ref,
                      const double *volume_ratio, const double *grad_energy, double *grad_coords,
                      double *grad_params);
+
+/* Learned screening model for MBD_SCS_LEARNED (host arrays, copied): n_members ensemble
+ * members of MBD_LEARNED_PARAMS FP16 values each (layout in include/mbd_gb300_kernels.h),
+ * feature mean and std [MBD_LEARNED_FEATURES = 74] (FP32).  The prediction is the members' mean of
+ * y = log(alpha_bar/alpha); their spread s_i(u) gives the energy-error estimate
+ * sum_{i,u} |dE/d alpha_bar_i(u)| s_i(u) / N.  Finite systems only; energies only (a
+ * gradient request in learned mode returns MBD_ERR_UNSUPPORTED). */
+int mbd_set_scs_model(mbd_ctx *ctx, int n_members, const void *params_fp16, const float *mean, const float *std);
+
+/* Outcome of the last learned-mode evaluation: the estimated energy error per atom (Ha) and
+ * whether the evaluation fell back to plain screening (1) or kept the model's result (0). */
+int mbd_get_learned_stats(mbd_ctx *ctx, double *estimated_error, int *fell_back);
+
+/* Screening only (Sec. 2.3: Eqs. ts-scaling, scs, contraction, casimir-polder,
+ * scale-rvdw-scs) with plain Dyson solves, for the geometry and parameters set above: host
+ * outputs alpha_iu [n_freq+1][n_atoms] (screened), alpha_free_iu [n_freq+1][n_atoms] (the
+ * unscreened alpha_i(iu) of Eq. dyn-pol), c6, omega, rvdw [n_atoms]; any may be NULL.
+ * Finite and periodic (Gamma-point) systems. */
+int mbd_screen(mbd_ctx *ctx, double *alpha_iu, double *alpha_free_iu, double *c6, double *omega, double *rvdw);
 
 /* Lattice gradient [3][3] (host) of the last gradient evaluation of a periodic system
  * (mbd_evaluate with gradients, mbd_evaluate_dev with gradients, or mbd_backward_dev,

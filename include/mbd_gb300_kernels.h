@@ -79,6 +79,67 @@ int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float al
 int mbdk_cholesky_solve3_f64_noalloc(void *stream, double *A, long long ld, int batch, double *X,
                                      int *status);
 
+/* ---- Learned screening model -------------------------------------------------------
+ * The paper has no learned part.  This per-atom model stands in for the screening solves
+ * of Eqs. (scs) and (contraction) (Sec. 2.3): features of the local geometry -> MLP ->
+ * y_k = log(alpha_bar(u_k) / alpha(u_k)) at the 16 grid points (u_0 = 0 and the 15 nodes).
+ * All pointers are device pointers; every call enqueues on `stream` (a cudaStream_t) and
+ * returns MBD_OK, MBD_ERR_INPUT for bad sizes or null pointers, or MBD_ERR_CUDA.
+ *
+ * Features (MBD_LEARNED_FEATURES per atom, FP32): for every other atom j of the same system
+ * at distance d < 24 bohr, alpha0_j fc(d) exp(-(d - mu_m)^2 / (2 w^2)) summed over j, for
+ * m = 0..63, mu_m = (m + 1/2) w, w = 0.375 bohr (4 radial shells of 6 bohr x 16 Gaussians),
+ * fc(d) = (1 + cos(pi d / 24)) / 2, alpha0_j TS-scaled (Eq. ts-scaling); then the atom's own
+ * TS-scaled alpha0, omega, R_vdW and its volume ratio; then the static screening moments
+ * (the terms of the Dyson series of Eq. scs at u = 0): with B_ij = (1 - f_ij) T^GG_ij
+ * (Eqs. scs-sr-dipole, tgg, mayer, fermi-damping; beta 0.83, a 6) and
+ * M_i = sum_{j, d<24} alpha0_j B_ij: m1 = Tr M_i / 3, m2 = Tr(sum_j alpha0_j B_ij M_j) / 3,
+ * m3 = Tr(M_i M_i) / 3, alpha0_i m1, alpha0_i^2 m2, alpha0_i^2 m3.
+ * Network: MLP 74 -> 128 -> 128 -> 16 on standardised features (x - mean) / std, SiLU
+ * activations, FP16 weights and biases, FP32 accumulation.  One ensemble member's
+ * parameters are MBD_LEARNED_PARAMS halves: W1 [74][128], b1 [128], W2 [128][128], b2 [128],
+ * W3 [128][16], b3 [16] (W[in][out], row-major); members are stored one after another. */
+#define MBD_LEARNED_FEATURES 74
+#define MBD_LEARNED_OUTPUTS 16
+#define MBD_LEARNED_PARAMS 28176
+
+/* Features of n_atoms atoms of n_systems systems stored one after another: system s holds
+ * atoms offsets[s] .. offsets[s+1]-1 (offsets [n_systems + 1], offsets[0] = 0,
+ * offsets[n_systems] = n_atoms).  coords [n_atoms][3] (bohr) and the free-atom parameters
+ * [n_atoms] each as in mbd_set_free_atom_params (FP64); X [n_atoms][74] (FP32); work
+ * [n_atoms][6] FP64 scratch (the moments M_i). */
+int mbdk_scs_features(void *stream, int n_atoms, int n_systems, const int *offsets, const double *coords,
+                      const double *alpha0_ref, const double *c6_ref, const double *rvdw_ref,
+                      const double *volume_ratio, float *X, double *work);
+
+/* Forward pass of n_members members on n_atoms rows of raw features X [n_atoms][74]:
+ * Y [n_members][n_atoms][16]; mean, std [74]; params_fp16 [n_members][MBD_LEARNED_PARAMS].
+ * zcache (optional, [n_members][2][n_atoms][128] FP32) keeps the pre-activations of both
+ * hidden layers for mbdk_mlp_backward. */
+int mbdk_mlp_forward(void *stream, int n_atoms, int n_members, const float *X, const float *mean,
+                     const float *std, const void *params_fp16, float *Y, float *zcache);
+
+/* Backward pass of sum(dY * Y) after mbdk_mlp_forward with a zcache, dY [n_members][n_atoms]
+ * [16]: dX (optional) [n_members][n_atoms][74] receives the gradient with respect to the raw
+ * features; grad (optional) [n_members][MBD_LEARNED_PARAMS] FP32 is ACCUMULATED with the
+ * gradient with respect to the parameters (clear it first for a fresh gradient). */
+int mbdk_mlp_backward(void *stream, int n_atoms, int n_members, const float *X, const float *mean,
+                      const float *std, const void *params_fp16, const float *zcache, const float *dY,
+                      float *dX, float *grad);
+
+/* Mean squared error of y against t (n entries): dy = 2 (y - t) / n and, if loss is not
+ * NULL, *loss = mean((y - t)^2) (FP64). */
+int mbdk_mse_grad(void *stream, long long n, const float *y, const float *t, float *dy, double *loss);
+
+/* One Adam step (b1 0.9, b2 0.999, eps 1e-8; step counts from 1) on n FP32 parameters with
+ * moments m, v (updated in place); params_fp16 (optional) receives the updated parameters
+ * rounded to FP16 (to nearest). */
+int mbdk_adam_step(void *stream, long long n, float *params, const float *grad, float *m, float *v, int step,
+                   float lr, void *params_fp16);
+
+/* dst[r][c] = src[idx[r]][c] for r < rows, c < width (FP32). */
+int mbdk_gather_rows(void *stream, long long rows, int width, const int *idx, const float *src, float *dst);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,17 +25,21 @@ MBD_PREC_FP64, MBD_PREC_TF32, MBD_PREC_BF16X3, MBD_PREC_TF32X3 = 0, 1, 2, 3
 # Every symbol declared in include/mbd_gb300.h.
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
            "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_backward_dev",
-           "mbd_get_lattice_gradient", "mbd_get_scs_detail",
+           "mbd_get_lattice_gradient", "mbd_set_scs_model", "mbd_get_learned_stats", "mbd_screen",
+           "mbd_get_scs_detail",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
            "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
-           "mbdk_cholesky_solve3_f64_noalloc")
+           "mbdk_cholesky_solve3_f64_noalloc", "mbdk_scs_features", "mbdk_mlp_forward", "mbdk_mlp_backward",
+           "mbdk_mse_grad", "mbdk_adam_step", "mbdk_gather_rows")
+LEARNED_FEATURES, LEARNED_OUTPUTS, LEARNED_PARAMS = 74, 16, 28176
 
 
 class mbd_options(C.Structure):
     _fields_ = [("n_freq", C.c_int), ("beta", C.c_double), ("a", C.c_double),
                 ("precision", C.c_int), ("ns_tol", C.c_double), ("ns_max_iter", C.c_int),
                 ("tc_chunk_stages", C.c_int), ("ewald_gamma", C.c_double), ("real_cutoff", C.c_double),
-                ("recip_cutoff", C.c_double)]
+                ("recip_cutoff", C.c_double), ("scs_mode", C.c_int), ("learned_max_error", C.c_double)]
+MBD_SCS_PLAIN, MBD_SCS_LEARNED = 0, 1
 
 
 class mbd_profile(C.Structure):
@@ -76,6 +80,9 @@ def load(path: str | None = None):
     L.mbd_backward_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mbd_get_scs_detail.argtypes = [vp, _P, _P, _P, _P]
     L.mbd_get_lattice_gradient.argtypes = [vp, _P]
+    L.mbd_set_scs_model.argtypes = [vp, i, vp, vp, vp]
+    L.mbd_get_learned_stats.argtypes = [vp, _P, C.POINTER(C.c_int)]
+    L.mbd_screen.argtypes = [vp, _P, _P, _P, _P, _P]
     L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P, _P]
     L.mbd_get_exception.argtypes = [vp, C.POINTER(C.c_int), C.c_char_p, C.c_char_p, sz]
     L.mbd_set_profiling.argtypes = [vp, i]
@@ -87,6 +94,12 @@ def load(path: str | None = None):
     L.mbdk_gemm_tc.argtypes = [vp, i, i, i, i, i, f, vp, vp, ll, vp, vp, ll, f, vp, vp, vp, vp, vp, ll, i, vp]
     L.mbdk_chol_solve3_f64.argtypes = [vp, vp, ll, i, vp, vp, vp]
     L.mbdk_cholesky_solve3_f64_noalloc.argtypes = [vp, vp, ll, i, vp, vp]
+    L.mbdk_scs_features.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.mbdk_mlp_forward.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
+    L.mbdk_mlp_backward.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.mbdk_mse_grad.argtypes = [vp, ll, vp, vp, vp, vp]
+    L.mbdk_adam_step.argtypes = [vp, ll, vp, vp, vp, vp, i, f, vp]
+    L.mbdk_gather_rows.argtypes = [vp, ll, i, vp, vp, vp]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -105,7 +118,13 @@ def _f64(x, shape=None):
 
 
 def _tptr(t):
-    return None if t is None else C.c_void_p(t.data_ptr())
+    """Device pointer of a torch tensor; the library reads every array densely in row-major
+    order, so strided views are refused."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor passed to the library must be contiguous")
+    return C.c_void_p(t.data_ptr())
 
 
 class MBD:
@@ -114,7 +133,7 @@ class MBD:
     def __init__(self, device: int = 0, n_freq: int = 15, beta: float = 0.83, a: float = 6.0,
                  ns_tol: float = 1e-8, ns_max_iter: int = 100, precision: int = MBD_PREC_FP64,
                  tc_chunk_stages: int | None = None, ewald_gamma: float = 0.0, real_cutoff: float = 0.0,
-                 recip_cutoff: float = 0.0):
+                 recip_cutoff: float = 0.0, scs_mode: int = MBD_SCS_PLAIN, learned_max_error: float = 1e-6):
         self.lib = load()
         opt = mbd_options()
         self.lib.mbd_default_options(C.byref(opt))
@@ -123,6 +142,7 @@ class MBD:
         if tc_chunk_stages is not None:
             opt.tc_chunk_stages = tc_chunk_stages
         opt.ewald_gamma, opt.real_cutoff, opt.recip_cutoff = ewald_gamma, real_cutoff, recip_cutoff
+        opt.scs_mode, opt.learned_max_error = scs_mode, learned_max_error
         h = C.c_void_p()
         rc = self.lib.mbd_create(C.byref(h), device, C.byref(opt))
         if rc:
@@ -183,6 +203,28 @@ class MBD:
         self._check(self.lib.mbd_evaluate(self.h, C.byref(E), _ptr(gR), _ptr(gA), _ptr(gp), _ptr(al)))
         self._last_gA = gA
         return E.value, gR, gp, al
+
+    def set_scs_model(self, params16, mean, std):
+        """Learned screening model: params16 [members, LEARNED_PARAMS] (float16 values), feature
+        mean and std [LEARNED_FEATURES]."""
+        p = np.ascontiguousarray(np.asarray(params16, dtype=np.float16).reshape(-1, LEARNED_PARAMS))
+        mean = np.ascontiguousarray(np.asarray(mean, dtype=np.float32))
+        std = np.ascontiguousarray(np.asarray(std, dtype=np.float32))
+        self._check(self.lib.mbd_set_scs_model(self.h, p.shape[0], p.ctypes.data_as(C.c_void_p),
+                                               mean.ctypes.data_as(C.c_void_p), std.ctypes.data_as(C.c_void_p)))
+
+    def learned_stats(self):
+        est, fb = C.c_double(), C.c_int()
+        self._check(self.lib.mbd_get_learned_stats(self.h, C.byref(est), C.byref(fb)))
+        return dict(estimated_error_per_atom=est.value, fell_back=bool(fb.value))
+
+    def screen(self):
+        """Plain screening only: dict(alpha_bar, alpha_free [n_freq+1, N], c6, omega, rvdw)."""
+        N = self.n_atoms
+        ab, af = np.zeros((self.n_freq + 1, N)), np.zeros((self.n_freq + 1, N))
+        c6, om, rv = np.zeros(N), np.zeros(N), np.zeros(N)
+        self._check(self.lib.mbd_screen(self.h, _ptr(ab), _ptr(af), _ptr(c6), _ptr(om), _ptr(rv)))
+        return dict(alpha_bar=ab, alpha_free=af, c6=c6, omega=om, rvdw=rv)
 
     def lattice_gradient(self):
         """dE/dA [3,3] (rows: lattice vectors) of the last gradient evaluation of a periodic
@@ -302,6 +344,56 @@ def mbdk_cholesky_solve3_f64_noalloc(A, X, status, stream=None):
     L = load()
     return L.mbdk_cholesky_solve3_f64_noalloc(_stream(A, stream), _tptr(A), A.shape[-1], A.shape[0],
                                               _tptr(X), _tptr(status))
+
+
+def _chk(rc, name):
+    if rc:
+        raise MBDError(rc, name, "launch rejected")
+
+
+def mbdk_scs_features(offsets, coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio, X, work=None, stream=None):
+    """Learned-model features X [n_atoms, LEARNED_FEATURES] (float32 CUDA) of systems stored
+    back to back (offsets int32 [n_systems + 1]); inputs float64 CUDA tensors; work [n_atoms, 6]
+    float64 scratch (allocated here with torch when not given)."""
+    import torch
+    L = load()
+    if work is None:
+        work = torch.empty(X.shape[0], 6, dtype=torch.float64, device=X.device)
+    _chk(L.mbdk_scs_features(_stream(X, stream), X.shape[0], offsets.shape[0] - 1, _tptr(offsets), _tptr(coords),
+                             _tptr(alpha0_ref), _tptr(c6_ref), _tptr(rvdw_ref), _tptr(volume_ratio), _tptr(X),
+                             _tptr(work)), "mbdk_scs_features")
+
+
+def mbdk_mlp_forward(X, mean, std, params16, Y, zcache=None, stream=None):
+    """Y [members, B, 16] = MLP(X [B, LEARNED_FEATURES]) for params16 [members, LEARNED_PARAMS] (float16)."""
+    L = load()
+    _chk(L.mbdk_mlp_forward(_stream(X, stream), X.shape[0], params16.shape[0], _tptr(X), _tptr(mean), _tptr(std),
+                            _tptr(params16), _tptr(Y), _tptr(zcache)), "mbdk_mlp_forward")
+
+
+def mbdk_mlp_backward(X, mean, std, params16, zcache, dY, dX=None, grad=None, stream=None):
+    """Backward of sum(dY * Y): dX [members, B, LEARNED_FEATURES] and/or grad [members, LEARNED_PARAMS]
+    (float32, accumulated)."""
+    L = load()
+    _chk(L.mbdk_mlp_backward(_stream(X, stream), X.shape[0], params16.shape[0], _tptr(X), _tptr(mean), _tptr(std),
+                             _tptr(params16), _tptr(zcache), _tptr(dY), _tptr(dX), _tptr(grad)), "mbdk_mlp_backward")
+
+
+def mbdk_mse_grad(y, t, dy, loss=None, stream=None):
+    L = load()
+    _chk(L.mbdk_mse_grad(_stream(y, stream), y.numel(), _tptr(y), _tptr(t), _tptr(dy), _tptr(loss)), "mbdk_mse_grad")
+
+
+def mbdk_adam_step(params, grad, m, v, step, lr, params16=None, stream=None):
+    L = load()
+    _chk(L.mbdk_adam_step(_stream(params, stream), params.numel(), _tptr(params), _tptr(grad), _tptr(m), _tptr(v),
+                          int(step), float(lr), _tptr(params16)), "mbdk_adam_step")
+
+
+def mbdk_gather_rows(idx, src, dst, stream=None):
+    L = load()
+    _chk(L.mbdk_gather_rows(_stream(src, stream), idx.shape[0], src.shape[1], _tptr(idx), _tptr(src), _tptr(dst)),
+         "mbdk_gather_rows")
 
 
 def evaluate_system(sys, device: int = 0, gradients: bool = True, **opts):

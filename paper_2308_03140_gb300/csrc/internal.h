@@ -153,6 +153,8 @@ void pad_identity(double *M, long long ld, int n, int nf1, long long mstride, cu
 void init_rhs_identity(double *X, long long ld, int n, int nf1, long long xstride, cudaStream_t s);
 void contract_screen(const AtomBufs &b, const double *X, long long ld, long long xstride,
                      int *status, cudaStream_t s);
+// Eqs. (casimir-polder), (scale-rvdw-scs) from alpha_bar(u) already in b.abar.
+void screened_params(const AtomBufs &b, int *status, cudaStream_t s);
 void build_q(const AtomBufs &b, double beta, double a, double *Q, long long ld, int *status,
              cudaStream_t s);
 void energy_trace(const double *Y, long long ld, int n, const double *ombar, int N,
@@ -237,5 +239,26 @@ void periodic_mbd_grad(const AtomBufs &b, const PeriodicBufs &p, double beta, do
 void scs_grad_periodic(const AtomBufs &b, const CellGeom &c, double beta, double a, const double *X,
                        const double *V, long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR,
                        double *gA_part, double *gA, cudaStream_t s);
+
+// ---- learned screening model (k_learned.cu) ---------------------------------------
+int learned_param_count();
+void scs_features(int n_atoms, int n_sys, const int *offsets, const double *R, const double *a0ref,
+                  const double *c6ref, const double *rref, const double *ratio, float *X, double *work,
+                  cudaStream_t s);
+cudaError_t mlp_forward(int B, int members, const float *X, const float *mean, const float *stdv,
+                        const void *params16, float *Y, float *zcache, cudaStream_t s);
+cudaError_t mlp_backward(int B, int members, const float *X, const float *mean, const float *stdv,
+                         const void *params16, const float *zcache, const float *dY, float *dX, float *grad,
+                         cudaStream_t s);
+void mse_grad(long long n, const float *y, const float *t, float *dy, double *loss, cudaStream_t s);
+void adam_step(long long n, float *p, const float *g, float *m, float *v, int step, float lr, void *p16,
+               cudaStream_t s);
+void gather_rows(long long rows, int width, const int *idx, const float *src, float *dst, cudaStream_t s);
+// alpha_bar[k][i] = alpha_i(u_k) exp(mean over members of Y[m][i][k]) and the member spread
+// spread[k][i] (population standard deviation of alpha_i(u_k) exp(Y[m][i][k])).
+void learned_alpha(int N, int members, int nf1, const double *al_u, const float *Y, double *abar, double *spread,
+                   cudaStream_t s);
+// out[0] = sum_{k,i} |h[k][i]| spread[k][i] / N (the energy-error estimate per atom).
+void learned_estimate(int N, int nf1, const double *h, const double *spread, double *out, cudaStream_t s);
 
 }  // namespace mbdgb

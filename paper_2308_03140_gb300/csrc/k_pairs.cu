@@ -105,15 +105,12 @@ __global__ void k_rhs_identity(double *X, long long ld, int n, long long xstride
         for (int c = 0; c < 3; ++c) Xk[3 * p + c] = (p < n && (p % 3) == c) ? 1.0 : 0.0;
 }
 
-// alpha_bar_i(u) = 1/3 sum_a X[3i+a][a]; then C6bar, omega_bar, Rbar per atom.
-__global__ void k_contract_screen(AtomBufs b, const double *X, long long xstride, int *status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.N) return;
+// Eqs. (casimir-polder), (scale-rvdw-scs) for atom i from its alpha_bar(u) row: C6bar,
+// omega_bar, Rbar; flags a non-positive alpha_bar0 or C6bar.
+__device__ __forceinline__ void screened_params_atom(const AtomBufs &b, int i, int *status) {
     double c6 = 0.0;
     for (int k = 0; k < b.nf1; ++k) {
-        const double *Xk = X + k * xstride;
-        const double ab = (Xk[9LL * i] + Xk[9LL * i + 4] + Xk[9LL * i + 8]) / 3.0;
-        b.abar[k * b.N + i] = ab;
+        const double ab = b.abar[k * b.N + i];
         c6 += b.wu[k] * ab * ab;   // wu[0] = 0: the static point carries no weight
     }
     c6 *= 3.0 / kPi;
@@ -123,6 +120,23 @@ __global__ void k_contract_screen(AtomBufs b, const double *X, long long xstride
     b.c6bar[i] = c6;
     b.ombar[i] = 4.0 * c6 / (3.0 * ab0 * ab0);
     b.rbar[i] = b.rv[i] * cbrt(ab0 / b.a0[i]);
+}
+
+// alpha_bar_i(u) = 1/3 sum_a X[3i+a][a]; then C6bar, omega_bar, Rbar per atom.
+__global__ void k_contract_screen(AtomBufs b, const double *X, long long xstride, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    for (int k = 0; k < b.nf1; ++k) {
+        const double *Xk = X + k * xstride;
+        b.abar[k * b.N + i] = (Xk[9LL * i] + Xk[9LL * i + 4] + Xk[9LL * i + 8]) / 3.0;
+    }
+    screened_params_atom(b, i, status);
+}
+
+// Screened parameters from alpha_bar(u) rows already in b.abar (the learned model's path).
+__global__ void k_screened_params(AtomBufs b, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < b.N) screened_params_atom(b, i, status);
 }
 
 // ---- coupled-oscillator matrix -------------------------------------------------------
@@ -418,6 +432,11 @@ void contract_screen(const AtomBufs &b, const double *X, long long ld, long long
     (void)ld;
     count_launches(1);
     k_contract_screen<<<cdiv(b.N, 128), 128, 0, s>>>(b, X, xstride, status);
+}
+
+void screened_params(const AtomBufs &b, int *status, cudaStream_t s) {
+    count_launches(1);
+    k_screened_params<<<cdiv(b.N, 128), 128, 0, s>>>(b, status);
 }
 
 void build_q(const AtomBufs &b, double beta, double a, double *Q, long long ld, int *status,

@@ -25,6 +25,7 @@ namespace {
 std::atomic<long long> g_launches{0};
 constexpr int kRefineSteps = 3;   // iterative-refinement steps of the mixed screening solves
 constexpr int kLanczosSteps = 48; // Lanczos steps of the spectrum estimate of Q
+constexpr int kLF = MBD_LEARNED_FEATURES;   // inputs of the learned screening model
 }  // namespace
 
 void mbdgb::count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -143,6 +144,19 @@ struct mbd_ctx {
     int *dglist = nullptr, *dgcount = nullptr;
     double2 *dS = nullptr;
     bool have_lattice_grad = false;
+    // learned screening model (host copy; device buffers in their own allocation)
+    int members = 0;
+    std::vector<uint16_t> hmodel;
+    std::vector<float> hmean, hstd;
+    bool model_dirty = false, force_plain = false;
+    void *lslab = nullptr;
+    int lN = 0, lM = 0;
+    void *dmodel = nullptr;
+    float *dmeanstd = nullptr, *dfeat = nullptr, *dYl = nullptr;
+    double *dspread = nullptr, *dmoments = nullptr;
+    int *doffs = nullptr;
+    double learned_est = 0.0;
+    int learned_fallback = 0;
     double *dscal;   // [0] energy, [1] Gershgorin, [2] residual
     int *dstatus;
     // last results
@@ -213,6 +227,46 @@ void release(mbd_ctx *ctx) {
     if (ctx->slab) cudaFree(ctx->slab);
     ctx->slab = nullptr;
     ctx->slab_bytes = 0;
+}
+
+// Device buffers of the learned model for N atoms and M members (own allocation, resized on
+// demand); uploads the model when it changed.
+int ensure_learned(mbd_ctx *ctx) {
+    const int N = ctx->N, M = ctx->members, nf1 = ctx->nf1;
+    const size_t P = static_cast<size_t>(learned_param_count());
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    if (!ctx->lslab || ctx->lN != N || ctx->lM != M) {
+        if (ctx->lslab) cudaFree(ctx->lslab);
+        ctx->lslab = nullptr;
+        const size_t bytes = al(2 * P * M) + al(sizeof(float) * 2 * kLF) + al(sizeof(float) * kLF * N) +
+                             al(sizeof(float) * M * N * 16) + al(sizeof(double) * nf1 * N) + al(sizeof(double) * 6 * N) +
+                             al(sizeof(int) * 2);
+        cudaError_t e = cudaMalloc(&ctx->lslab, bytes);
+        if (e != cudaSuccess) return cuda_fail(ctx, "learned_screening", e);
+        char *p = static_cast<char *>(ctx->lslab);
+        ctx->dmodel = p; p += al(2 * P * M);
+        ctx->dmeanstd = reinterpret_cast<float *>(p); p += al(sizeof(float) * 2 * kLF);
+        ctx->dfeat = reinterpret_cast<float *>(p); p += al(sizeof(float) * kLF * N);
+        ctx->dYl = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * N * 16);
+        ctx->dspread = reinterpret_cast<double *>(p); p += al(sizeof(double) * nf1 * N);
+        ctx->dmoments = reinterpret_cast<double *>(p); p += al(sizeof(double) * 6 * N);
+        ctx->doffs = reinterpret_cast<int *>(p);
+        const int offs[2] = {0, N};
+        e = cudaMemcpy(ctx->doffs, offs, sizeof(offs), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, "learned_screening", e);
+        ctx->lN = N;
+        ctx->lM = M;
+        ctx->model_dirty = true;
+    }
+    if (ctx->model_dirty) {
+        cudaError_t e = cudaMemcpy(ctx->dmodel, ctx->hmodel.data(), 2 * P * M, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->dmeanstd, ctx->hmean.data(), sizeof(float) * kLF, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ctx->dmeanstd + kLF, ctx->hstd.data(), sizeof(float) * kLF, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, "learned_screening", e);
+        ctx->model_dirty = false;
+    }
+    return MBD_OK;
 }
 
 // Carves the workspace out of one allocation (256-byte aligned pieces).
@@ -654,6 +708,8 @@ void backward_periodic(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const do
 // the grid, batched complex coupled Newton-Schulz (FP64, 4 real GEMMs per complex
 // product), E = (1/nk) sum_q 1/2 Tr Q(q)^{1/2} - 3/2 sum omega_bar.
 int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool want_grad) {
+    if (ctx->opt.scs_mode == MBD_SCS_LEARNED)
+        return fail(ctx, MBD_ERR_UNSUPPORTED, "learned_screening", "learned screening is for finite systems");
     const int N = ctx->N, n = ctx->n, nf1 = ctx->nf1, nk = ctx->nk;
     const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;
     const double beta = ctx->opt.beta, a = ctx->opt.a;
@@ -831,18 +887,34 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     mark(ctx, s, e_start);
     MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_evaluate");
     // ---- screening (Sec. 2.3) ----
-    prepare_atoms(b, ctx->dstatus, s);
-    build_scs(b, beta, a, ctx->dM, ld, mat, ctx->dstatus, s);
-    if (ctx->opt.precision == MBD_PREC_FP64) {
-        cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
-        init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
-        chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
-    } else {   // FP32 factors, FP64-refined solutions
-        cholesky_f32_from_f64(ctx->dM, ctx->sM, ld, nf1, ctx->sdinv, ctx->dstatus, s);
-        init_rhs_identity(ctx->dB, ld, n, nf1, xs, s);
-        refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, n, nf1, ctx->dB, ctx->dX, ctx->swork, kRefineSteps, s);
+    const bool learned = ctx->opt.scs_mode == MBD_SCS_LEARNED && !ctx->force_plain;
+    if (learned) {   // model prediction of alpha_bar(iu) in place of the Dyson solves
+        if (want_grad)
+            return fail(ctx, MBD_ERR_UNSUPPORTED, "learned_screening", "learned screening gives energies only");
+        if (ctx->members < 1) return fail(ctx, MBD_ERR_STATE, "learned_screening", "no model set");
+        int rc0 = ensure_learned(ctx);
+        if (rc0) return rc0;
+        prepare_atoms(b, ctx->dstatus, s);
+        scs_features(N, 1, ctx->doffs, in.R, in.a0ref, in.c6ref, in.rref, in.ratio, ctx->dfeat, ctx->dmoments, s);
+        const cudaError_t ef = mlp_forward(N, ctx->members, ctx->dfeat, ctx->dmeanstd, ctx->dmeanstd + kLF, ctx->dmodel,
+                                           ctx->dYl, nullptr, s);
+        if (ef != cudaSuccess) return cuda_fail(ctx, "learned_screening", ef);
+        learned_alpha(N, ctx->members, nf1, ctx->dalu, ctx->dYl, ctx->dabar, ctx->dspread, s);
+        screened_params(b, ctx->dstatus, s);
+    } else {
+        prepare_atoms(b, ctx->dstatus, s);
+        build_scs(b, beta, a, ctx->dM, ld, mat, ctx->dstatus, s);
+        if (ctx->opt.precision == MBD_PREC_FP64) {
+            cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
+            init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
+            chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
+        } else {   // FP32 factors, FP64-refined solutions
+            cholesky_f32_from_f64(ctx->dM, ctx->sM, ld, nf1, ctx->sdinv, ctx->dstatus, s);
+            init_rhs_identity(ctx->dB, ld, n, nf1, xs, s);
+            refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, n, nf1, ctx->dB, ctx->dX, ctx->swork, kRefineSteps, s);
+        }
+        contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
     }
-    contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
     mark(ctx, s, e_scs);
     int rc = read_status(ctx, s, "screening");
     if (rc) return rc;
@@ -963,6 +1035,27 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         if (rc) return rc;
     }
     mark(ctx, s, e_ns);
+    if (learned) {
+        // energy-error estimate from the adjoints h = dE/d alpha_bar(u) and the members' spread;
+        // above the threshold the evaluation is redone with plain screening
+        MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
+        mbd_grad_pass(b, beta, a, ctx->Zlast, ld, ctx->zscale, go, s);
+        chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, ctx->dV, ld, xs, s);
+        learned_estimate(N, nf1, ctx->dh, ctx->dspread, ctx->dscal + 5, s);
+        double est = 0.0;
+        MBD_CUDA(cudaMemcpyAsync(&est, ctx->dscal + 5, sizeof(double), cudaMemcpyDeviceToHost, s), "learned_screening");
+        MBD_CUDA(cudaStreamSynchronize(s), "learned_screening");
+        ctx->learned_est = est;
+        ctx->learned_fallback = 0;
+        if (!(est <= ctx->opt.learned_max_error)) {
+            ctx->force_plain = true;
+            const int rc2 = run(ctx, s, in, out, want_grad);
+            ctx->force_plain = false;
+            ctx->learned_est = est;
+            ctx->learned_fallback = 1;
+            return rc2;
+        }
+    }
     // ---- gradients (Sec. 2.4) ----
     if (want_grad) backward_passes(ctx, s, b, nullptr, out.grad_coords, out.grad_params);
     if (out.alpha_scs)
@@ -1012,6 +1105,8 @@ int mbd_default_options(mbd_options *opt) {
     opt->ewald_gamma = 0.0;
     opt->real_cutoff = 0.0;
     opt->recip_cutoff = 0.0;
+    opt->scs_mode = MBD_SCS_PLAIN;
+    opt->learned_max_error = 1e-6;
     return MBD_OK;
 }
 
@@ -1021,7 +1116,8 @@ int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt) {
     mbd_options o;
     if (opt) o = *opt; else mbd_default_options(&o);
     if (o.n_freq < 1 || o.n_freq + 1 > kMaxFreq || !(o.beta > 0) || !(o.a > 0) || o.ns_max_iter < 1 ||
-        !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_TF32X3 || o.tc_chunk_stages < 0)
+        !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_TF32X3 || o.tc_chunk_stages < 0 ||
+        (o.scs_mode != MBD_SCS_PLAIN && o.scs_mode != MBD_SCS_LEARNED) || !(o.learned_max_error > 0))
         return MBD_ERR_INPUT;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev)
@@ -1051,6 +1147,7 @@ int mbd_destroy(mbd_ctx *ctx) {
     if (!ctx) return MBD_OK;
     cudaSetDevice(ctx->device);
     release(ctx);
+    if (ctx->lslab) cudaFree(ctx->lslab);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1197,6 +1294,67 @@ int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
     MBD_CUDA(cudaStreamSynchronize(s), "mbd_backward_dev");
     MBD_CUDA(cudaGetLastError(), "mbd_backward_dev");
     return MBD_OK;
+}
+
+int mbd_set_scs_model(mbd_ctx *ctx, int n_members, const void *params_fp16, const float *mean, const float *std) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (n_members < 1 || n_members > 64 || !params_fp16 || !mean || !std)
+        return fail(ctx, MBD_ERR_INPUT, "mbd_set_scs_model", "need 1..64 members, parameters, mean and std");
+    for (int k = 0; k < kLF; ++k)
+        if (!(std[k] > 0.0f) || !std::isfinite(mean[k]))
+            return fail(ctx, MBD_ERR_INPUT, "mbd_set_scs_model", "feature std must be positive and mean finite");
+    const size_t P = static_cast<size_t>(learned_param_count()) * n_members;
+    const uint16_t *src = static_cast<const uint16_t *>(params_fp16);
+    ctx->hmodel.assign(src, src + P);
+    ctx->hmean.assign(mean, mean + kLF);
+    ctx->hstd.assign(std, std + kLF);
+    ctx->members = n_members;
+    ctx->model_dirty = true;
+    return MBD_OK;
+}
+
+int mbd_get_learned_stats(mbd_ctx *ctx, double *estimated_error, int *fell_back) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (estimated_error) *estimated_error = ctx->learned_est;
+    if (fell_back) *fell_back = ctx->learned_fallback;
+    return MBD_OK;
+}
+
+int mbd_screen(mbd_ctx *ctx, double *alpha_iu, double *alpha_free_iu, double *c6, double *omega, double *rvdw) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (!ctx->have_geom || !ctx->have_params)
+        return fail(ctx, MBD_ERR_STATE, "mbd_screen", "set the geometry and the free-atom parameters first");
+    MBD_CUDA(cudaSetDevice(ctx->device), "mbd_screen");
+    const int N = ctx->N, n = ctx->n, nf1 = ctx->nf1;
+    const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;
+    cudaStream_t s = ctx->stream;
+    MBD_CUDA(cudaMemcpyAsync(ctx->dR, ctx->hR.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s), "mbd_screen");
+    MBD_CUDA(cudaMemcpyAsync(ctx->da0ref, ctx->ha0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_screen");
+    MBD_CUDA(cudaMemcpyAsync(ctx->dc6ref, ctx->hc6.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_screen");
+    MBD_CUDA(cudaMemcpyAsync(ctx->drref, ctx->hrr.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_screen");
+    MBD_CUDA(cudaMemcpyAsync(ctx->dratio, ctx->hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_screen");
+    const AtomBufs b = atom_bufs(ctx, Inputs{ctx->dR, ctx->da0ref, ctx->dc6ref, ctx->drref, ctx->dratio});
+    ctx->have_screening = false;
+    MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_screen");
+    prepare_atoms(b, ctx->dstatus, s);
+    if (ctx->periodic) build_scs_periodic(b, ctx->cell, ctx->opt.beta, ctx->opt.a, ctx->dM, ld, mat, ctx->dstatus, s);
+    else build_scs(b, ctx->opt.beta, ctx->opt.a, ctx->dM, ld, mat, ctx->dstatus, s);
+    if (ctx->opt.precision == MBD_PREC_FP64 || ctx->periodic) {
+        cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
+        init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
+        chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
+    } else {
+        cholesky_f32_from_f64(ctx->dM, ctx->sM, ld, nf1, ctx->sdinv, ctx->dstatus, s);
+        init_rhs_identity(ctx->dB, ld, n, nf1, xs, s);
+        refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, n, nf1, ctx->dB, ctx->dX, ctx->swork, kRefineSteps, s);
+    }
+    contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
+    int rc = read_status(ctx, s, "mbd_screen");
+    if (rc) return rc;
+    ctx->have_screening = true;
+    if (alpha_free_iu)
+        MBD_CUDA(cudaMemcpy(alpha_free_iu, ctx->dalu, sizeof(double) * N * nf1, cudaMemcpyDeviceToHost), "mbd_screen");
+    return mbd_get_scs_detail(ctx, alpha_iu, c6, omega, rvdw);
 }
 
 int mbd_get_lattice_gradient(mbd_ctx *ctx, double *grad_lattice) {

@@ -1,0 +1,151 @@
+"""Learned screening model: training data from plain screening, training on the GPU with the
+library's own kernels, and packing for mbd_set_scs_model.
+
+The paper has no learned part.  The model (features, network, output encoding) is described
+in include/mbd_gb300_kernels.h: per-atom features of the local geometry, an MLP
+74 -> 128 -> 128 -> 16 with FP16 weights and FP32 accumulation, output
+y = log(alpha_bar(iu) / alpha(iu)) on the 16 grid points, an ensemble whose spread drives the
+fallback to plain screening.  Training minimises the mean squared error of y against the
+plain-screening targets with Adam; every forward, backward, loss and update step runs in the
+library's kernels (mbdk_scs_features, mbdk_mlp_forward/backward, mbdk_mse_grad,
+mbdk_adam_step, mbdk_gather_rows); PyTorch provides device memory, and the feature
+standardisation statistics are computed once on the host.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding
+from . import synthetic as syn
+
+P = binding.LEARNED_PARAMS
+F = binding.LEARNED_FEATURES
+LAYERS = ((F, 128), (128, 128), (128, 16))
+
+
+def init_params(members: int, seed: int) -> np.ndarray:
+    """FP32 parameters [members, P]: weights N(0, 1/fan_in) (the last layer scaled by 0.1, so
+    an untrained member predicts y close to 0, i.e. no screening), zero biases."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((members, P), dtype=np.float32)
+    for m in range(members):
+        parts = []
+        for li, (fi, fo) in enumerate(LAYERS):
+            W = rng.normal(0.0, 1.0 / np.sqrt(fi), (fi, fo)) * (0.1 if li == 2 else 1.0)
+            parts += [W.ravel(), np.zeros(fo)]
+        out[m] = np.concatenate(parts)
+    return out
+
+
+def perturbed_cluster(index: int, seed0: int = 4000, n_range=(50, 500)):
+    """Cluster `index` of the batch recipe (sphere cluster, size U{50..500}, seed seed0 + index)
+    with positions moved by N(0, 0.1 bohr) and parameters scaled by U[0.95, 1.05]."""
+    rng = np.random.default_rng(10_000_000 + seed0 + index)
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    s = syn.sphere_cluster(n, seed=seed0 + index, name=f"cluster{index}")
+    s.coords = s.coords + rng.normal(0.0, 0.1, s.coords.shape)
+    for f in ("alpha0_ref", "c6_ref", "rvdw_ref", "ratio"):
+        setattr(s, f, getattr(s, f) * rng.uniform(0.95, 1.05, s.n_atoms))
+    return s
+
+
+def training_data(systems, device: int = 0):
+    """Features X [n_atoms, F] (torch float32, CUDA) and targets y [n_atoms, 16] of the
+    systems, with plain screening (mixed-precision factorisation with FP64 refinement) as the
+    teacher."""
+    import torch
+    dev = torch.device(f"cuda:{device}")
+    feats, targets = [], []
+    m = binding.MBD(device, precision=binding.MBD_PREC_TF32X3)
+    for s in systems:
+        m.set_geometry(s.coords)
+        m.set_free_atom_params(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
+        d = m.screen()
+        targets.append(np.ascontiguousarray(np.log(d["alpha_bar"] / d["alpha_free"]).T))
+        feats.append(features([s], dev))
+    m.close()
+    Y = torch.tensor(np.ascontiguousarray(np.concatenate(targets)), dtype=torch.float32, device=dev).contiguous()
+    return torch.cat(feats).contiguous(), Y
+
+
+def features(systems, dev):
+    import torch
+    offsets = np.concatenate([[0], np.cumsum([s.n_atoms for s in systems])]).astype(np.int32)
+    cat = lambda f: torch.tensor(np.concatenate([np.ravel(getattr(s, f)) for s in systems]), dtype=torch.float64,
+                                 device=dev)
+    X = torch.zeros(int(offsets[-1]), F, dtype=torch.float32, device=dev)
+    binding.mbdk_scs_features(torch.tensor(offsets, device=dev), cat("coords"), cat("alpha0_ref"), cat("c6_ref"),
+                              cat("rvdw_ref"), cat("ratio"), X)
+    return X
+
+
+class Ensemble:
+    """Ensemble of members trained on the same data from different initial weights and batch
+    orders; FP32 master parameters with FP16 copies on the GPU."""
+
+    def __init__(self, members: int = 4, seed: int = 0, device: int = 0):
+        import torch
+        self.dev = torch.device(f"cuda:{device}")
+        self.members = members
+        self.p32 = torch.tensor(init_params(members, seed), device=self.dev)
+        self.p16 = self.p32.to(torch.float16)
+        self.mean = torch.zeros(F, dtype=torch.float32, device=self.dev)
+        self.std = torch.ones(F, dtype=torch.float32, device=self.dev)
+        self.seed = seed
+
+    def set_standardisation(self, X):
+        """Feature mean and standard deviation over the training set (a floor of 1e-3 keeps
+        constant features finite)."""
+        import torch
+        Xh = X.cpu().numpy().astype(np.float64)
+        self.mean = torch.tensor(Xh.mean(0), dtype=torch.float32, device=self.dev)
+        self.std = torch.tensor(np.maximum(Xh.std(0), 1e-3), dtype=torch.float32, device=self.dev)
+
+    def fit(self, X, Y, steps: int = 2000, batch: int = 4096, lr: float = 2e-3, log_every: int = 0):
+        """Adam on the mean squared error of y; every member draws its own batches.
+        Returns the loss history (one value per step, mean over members)."""
+        import torch
+        M, B = self.members, min(batch, X.shape[0])
+        m = torch.zeros_like(self.p32)
+        v = torch.zeros_like(self.p32)
+        grad = torch.zeros_like(self.p32)
+        Xb = torch.zeros(B, F, dtype=torch.float32, device=self.dev)
+        Yb = torch.zeros(B, 16, dtype=torch.float32, device=self.dev)
+        Yp = torch.zeros(M, B, 16, dtype=torch.float32, device=self.dev)
+        dY = torch.zeros(M, B, 16, dtype=torch.float32, device=self.dev)
+        z = torch.zeros(M, 2, B, 128, dtype=torch.float32, device=self.dev)
+        loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
+        rng = np.random.default_rng(self.seed + 17)
+        hist = []
+        for step in range(1, steps + 1):
+            grad.zero_()
+            total = 0.0
+            for k in range(M):   # each member: its own batch, forward with cache, backward
+                idx = torch.tensor(rng.integers(0, X.shape[0], B).astype(np.int32), device=self.dev)
+                binding.mbdk_gather_rows(idx, X, Xb)
+                binding.mbdk_gather_rows(idx, Y, Yb)
+                pk = self.p16[k:k + 1]
+                binding.mbdk_mlp_forward(Xb, self.mean, self.std, pk, Yp[k:k + 1], z[k:k + 1])
+                binding.mbdk_mse_grad(Yp[k], Yb, dY[k], loss)
+                binding.mbdk_mlp_backward(Xb, self.mean, self.std, pk, z[k:k + 1], dY[k:k + 1], None,
+                                          grad[k:k + 1])
+                total += loss.item() if (log_every or step == steps) else 0.0
+            binding.mbdk_adam_step(self.p32, grad, m, v, step, lr, self.p16)
+            hist.append(total / M)
+            if log_every and step % log_every == 0:
+                print(f"step {step} loss {total / M:.3e}", flush=True)
+        return hist
+
+    def predict(self, X):
+        import torch
+        Y = torch.zeros(self.members, X.shape[0], 16, dtype=torch.float32, device=self.dev)
+        binding.mbdk_mlp_forward(X, self.mean, self.std, self.p16, Y)
+        return Y
+
+    def model(self):
+        """(params16 [members, P] float16, mean [F], std [F]) for MBD.set_scs_model."""
+        return self.p16.cpu().numpy(), self.mean.cpu().numpy(), self.std.cpu().numpy()
+
+    def save(self, path: str):
+        p16, mean, std = self.model()
+        np.savez(path, params16=p16, mean=mean, std=std)
