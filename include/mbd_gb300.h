@@ -153,8 +153,9 @@ int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
  * members of MBD_LEARNED_PARAMS FP16 values each (layout in include/mbd_gb300_kernels.h),
  * feature mean and std [MBD_LEARNED_FEATURES = 74] (FP32).  The prediction is the members' mean of
  * y = log(alpha_bar/alpha); their spread s_i(u) gives the energy-error estimate
- * sum_{i,u} |dE/d alpha_bar_i(u)| s_i(u) / N.  Finite systems only; energies only (a
- * gradient request in learned mode returns MBD_ERR_UNSUPPORTED). */
+ * sum_{i,u} |dE/d alpha_bar_i(u)| s_i(u) / N.  Finite systems only; energies and coordinate
+ * gradients (through the network and the features); a request for parameter gradients in
+ * learned mode returns MBD_ERR_UNSUPPORTED. */
 int mbd_set_scs_model(mbd_ctx *ctx, int n_members, const void *params_fp16, const float *mean, const float *std);
 
 /* Outcome of the last learned-mode evaluation: the estimated energy error per atom (Ha) and

@@ -190,14 +190,14 @@ class MBD:
         arrs = [_f64(x) for x in (alpha0_ref, c6_ref, rvdw_ref, volume_ratio)]
         self._check(self.lib.mbd_set_free_atom_params(self.h, *[_ptr(x) for x in arrs]))
 
-    def evaluate(self, gradients: bool = True):
+    def evaluate(self, gradients: bool = True, param_gradients: bool = True):
         """Host-memory evaluation.  Returns (energy, grad_coords [N,3] | None,
         grad_params [4,N] | None, alpha_scs [N]); for a periodic system the lattice
         gradient [3,3] is available afterwards from lattice_gradient()."""
         N = self.n_atoms
         E = C.c_double()
         gR = np.zeros((N, 3)) if gradients else None
-        gp = np.zeros((4, N)) if gradients else None
+        gp = np.zeros((4, N)) if gradients and param_gradients else None
         gA = np.zeros((3, 3)) if gradients and getattr(self, "periodic", False) else None
         al = np.zeros(N)
         self._check(self.lib.mbd_evaluate(self.h, C.byref(E), _ptr(gR), _ptr(gA), _ptr(gp), _ptr(al)))

@@ -258,6 +258,12 @@ void gather_rows(long long rows, int width, const int *idx, const float *src, fl
 // spread[k][i] (population standard deviation of alpha_i(u_k) exp(Y[m][i][k])).
 void learned_alpha(int N, int members, int nf1, const double *al_u, const float *Y, double *abar, double *spread,
                    cudaStream_t s);
+// Learned path gradients: dY[m][i][k] = h[k][i] alpha_bar[k][i] / members (member outputs'
+// upstream gradient); gR[i] += dE/dR_i through the features, from dX [members][N][74]
+// (mlp_backward), the moments M [N][6] of scs_features and workspace adjoint [N][6].
+void learned_dy(int N, int members, int nf1, const double *h, const double *abar, float *dY, cudaStream_t s);
+void learned_forces(int N, const double *R, const double *a0ref, const double *rref, const double *ratio,
+                    const double *moments, const float *dX, int members, double *adjoint, double *gR, cudaStream_t s);
 // out[0] = sum_{k,i} |h[k][i]| spread[k][i] / N (the energy-error estimate per atom).
 void learned_estimate(int N, int nf1, const double *h, const double *spread, double *out, cudaStream_t s);
 

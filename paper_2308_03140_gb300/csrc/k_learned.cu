@@ -404,11 +404,135 @@ __global__ void k_learned_estimate(int n, int N, const double *h, const double *
     }
 }
 
+
+// ---- forces of the learned path --------------------------------------------------------
+// dY[m][i][k] = h[k][i] alpha_bar[k][i] / M: the upstream gradient of each member's output
+// (alpha_bar = alpha exp(mean_m y_m)).
+__global__ void k_learned_dy(int N, int members, int nf1, const double *h, const double *abar, float *dY) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e >= static_cast<long long>(members) * N * kO) return;
+    const int k = static_cast<int>(e % kO), i = static_cast<int>((e / kO) % N);
+    dY[e] = k < nf1 ? static_cast<float>(h[k * N + i] * abar[k * N + i] / members) : 0.0f;
+}
+
+// Upstream gradients of the moments of atom i from the summed feature gradient gx.
+struct MomentGrad { double g1, g2, g3; };
+__device__ __forceinline__ MomentGrad moment_grad(const float *dX, int members, int N, int i, double a0i) {
+    double g[6] = {0, 0, 0, 0, 0, 0};
+    for (int m = 0; m < members; ++m)
+        for (int e = 0; e < 6; ++e) g[e] += dX[(static_cast<long long>(m) * N + i) * kF + 68 + e];
+    return {g[0] + a0i * g[3], g[1] + a0i * a0i * g[4], g[2] + a0i * a0i * g[5]};
+}
+
+// A_i = dE/dM_i = g1_i I/3 + 2 g3_i M_i/3 + (alpha0_i/3) sum_k g2_k B_ik (one warp per atom).
+__global__ void k_moment_adjoint(int N, const double *R, const double *a0ref, const double *rref, const double *ratio,
+                                 const double *Mw, const float *dX, int members, double *Aw) {
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    const double a0i = a0ref[i] * ratio[i], rvi = rref[i] * cbrt(ratio[i]);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = lane; k < N; k += 32) {
+        if (k == i) continue;
+        const double r[3] = {R[3 * k] - R[3 * i], R[3 * k + 1] - R[3 * i + 1], R[3 * k + 2] - R[3 * i + 2]};
+        const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (d >= kCut) continue;
+        const double a0k = a0ref[k] * ratio[k];
+        double B[6];
+        scs_coupling(r, d, a0i, a0k, rvi, rref[k] * cbrt(ratio[k]), B);
+        const double g2k = moment_grad(dX, members, N, k, a0k).g2;
+        for (int e = 0; e < 6; ++e) acc[e] += g2k * B[e];
+    }
+    for (int e = 0; e < 6; ++e) acc[e] = warp_sum_d(acc[e]);
+    if (lane == 0) {
+        const MomentGrad gi = moment_grad(dX, members, N, i, a0i);
+        const double *M = Mw + 6LL * i;
+        for (int e = 0; e < 6; ++e)
+            Aw[6LL * i + e] = (e < 3 ? gi.g1 / 3.0 : 0.0) + 2.0 * gi.g3 * M[e] / 3.0 + a0i / 3.0 * acc[e];
+    }
+}
+
+// <C, dB/dr_c> for symmetric C (6 components) and B = (1 - f) T^GG at separation r.
+__device__ __forceinline__ void coupling_grad(const double *r, double d, double a0i, double a0j, double rvi,
+                                              double rvj, const double *C, double *out) {
+    const double cm = sqrt(2.0 / kPiL) / 3.0;
+    const double si = cbrt(cm * a0i), sj = cbrt(cm * a0j);
+    const Fermi f = pairs::fermi(d, rvi + rvj, 0.83, 6.0);
+    const Radial t = pairs::tgg_radial(d, sqrt(si * si + sj * sj));
+    const double sr = 1.0 - f.f, ir = 1.0 / d;
+    double Cr[3];
+    Cr[0] = C[0] * r[0] + C[3] * r[1] + C[4] * r[2];
+    Cr[1] = C[3] * r[0] + C[1] * r[1] + C[5] * r[2];
+    Cr[2] = C[4] * r[0] + C[5] * r[1] + C[2] * r[2];
+    const double tr = C[0] + C[1] + C[2], rCr = r[0] * Cr[0] + r[1] * Cr[1] + r[2] * Cr[2];
+    const double CT = t.P * tr + t.W * rCr;
+    for (int c = 0; c < 3; ++c)
+        out[c] = -f.df_drho * r[c] * ir * CT + sr * ((t.dP * tr + t.dW * rCr) * r[c] * ir + 2.0 * t.W * Cr[c]);
+}
+
+// gR[i] += dE/dR_i through the features (one warp per atom, fixed order):
+//   radial:  -sum_j sum_k (gx_ik alpha0_j + gx_jk alpha0_i) phi_k'(d_ij) r^_ij
+//   moments: -sum_j <C_ij + C_ji, dB/dr (r_ij)>,  C_ij = alpha0_j (A_i + g2_i M_j / 3)
+__global__ void k_learned_forces(int N, const double *R, const double *a0ref, const double *rref,
+                                 const double *ratio, const double *Mw, const double *Aw, const float *dX,
+                                 int members, double *gR) {
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    const double a0i = a0ref[i] * ratio[i], rvi = rref[i] * cbrt(ratio[i]);
+    const double g2i = moment_grad(dX, members, N, i, a0i).g2;
+    const double *Mi = Mw + 6LL * i, *Ai = Aw + 6LL * i;
+    const double i2w2 = 0.5 / (kWidth * kWidth);
+    double f[3] = {0, 0, 0};
+    for (int j = lane; j < N; j += 32) {
+        if (j == i) continue;
+        const double r[3] = {R[3 * j] - R[3 * i], R[3 * j + 1] - R[3 * i + 1], R[3 * j + 2] - R[3 * i + 2]};
+        const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (d >= kCut) continue;
+        const double a0j = a0ref[j] * ratio[j], rvj = rref[j] * cbrt(ratio[j]);
+        // radial features
+        const double fc = 0.5 * (1.0 + cos(kPiL * d / kCut)), dfc = -0.5 * kPiL / kCut * sin(kPiL * d / kCut);
+        double s = 0.0;
+        for (int k = 0; k < 64; ++k) {
+            double gi = 0.0, gj = 0.0;
+            for (int m = 0; m < members; ++m) {
+                gi += dX[(static_cast<long long>(m) * N + i) * kF + k];
+                gj += dX[(static_cast<long long>(m) * N + j) * kF + k];
+            }
+            const double mu = (k + 0.5) * kWidth, G = exp(-(d - mu) * (d - mu) * i2w2);
+            s += (gi * a0j + gj * a0i) * (dfc * G + fc * G * (-(d - mu) * 2.0 * i2w2));
+        }
+        for (int c = 0; c < 3; ++c) f[c] -= s * r[c] / d;
+        // moments
+        const double g2j = moment_grad(dX, members, N, j, a0j).g2;
+        const double *Mj = Mw + 6LL * j, *Aj = Aw + 6LL * j;
+        double C[6], dB[3];
+        for (int e = 0; e < 6; ++e) C[e] = a0j * (Ai[e] + g2i * Mj[e] / 3.0) + a0i * (Aj[e] + g2j * Mi[e] / 3.0);
+        coupling_grad(r, d, a0i, a0j, rvi, rvj, C, dB);
+        for (int c = 0; c < 3; ++c) f[c] -= dB[c];
+    }
+    for (int c = 0; c < 3; ++c) f[c] = warp_sum_d(f[c]);
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) gR[3 * i + c] += f[c];
+}
+
 inline int cdiv(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
 
 }  // namespace
 
 int learned_param_count() { return kParams; }
+
+void learned_dy(int N, int members, int nf1, const double *h, const double *abar, float *dY, cudaStream_t s) {
+    count_launches(1);
+    k_learned_dy<<<cdiv(static_cast<long long>(members) * N * kO, 256), 256, 0, s>>>(N, members, nf1, h, abar, dY);
+}
+
+void learned_forces(int N, const double *R, const double *a0ref, const double *rref, const double *ratio,
+                    const double *moments, const float *dX, int members, double *adjoint, double *gR, cudaStream_t s) {
+    count_launches(2);
+    k_moment_adjoint<<<cdiv(N, 8), 256, 0, s>>>(N, R, a0ref, rref, ratio, moments, dX, members, adjoint);
+    k_learned_forces<<<cdiv(N, 8), 256, 0, s>>>(N, R, a0ref, rref, ratio, moments, adjoint, dX, members, gR);
+}
 
 void learned_alpha(int N, int members, int nf1, const double *al_u, const float *Y, double *abar, double *spread,
                    cudaStream_t s) {

@@ -153,10 +153,12 @@ struct mbd_ctx {
     int lN = 0, lM = 0;
     void *dmodel = nullptr;
     float *dmeanstd = nullptr, *dfeat = nullptr, *dYl = nullptr;
-    double *dspread = nullptr, *dmoments = nullptr;
+    double *dspread = nullptr, *dmoments = nullptr, *dadj = nullptr;
+    float *dzc = nullptr, *dXl = nullptr;   // MLP cache and feature gradient (learned forces)
     int *doffs = nullptr;
     double learned_est = 0.0;
     int learned_fallback = 0;
+    bool last_learned = false;   // the last forward kept the learned model's screening
     double *dscal;   // [0] energy, [1] Gershgorin, [2] residual
     int *dstatus;
     // last results
@@ -240,7 +242,8 @@ int ensure_learned(mbd_ctx *ctx) {
         ctx->lslab = nullptr;
         const size_t bytes = al(2 * P * M) + al(sizeof(float) * 2 * kLF) + al(sizeof(float) * kLF * N) +
                              al(sizeof(float) * M * N * 16) + al(sizeof(double) * nf1 * N) + al(sizeof(double) * 6 * N) +
-                             al(sizeof(int) * 2);
+                             al(sizeof(double) * 6 * N) + al(sizeof(float) * M * 2 * N * 128) +
+                             al(sizeof(float) * M * N * kLF) + al(sizeof(int) * 2);
         cudaError_t e = cudaMalloc(&ctx->lslab, bytes);
         if (e != cudaSuccess) return cuda_fail(ctx, "learned_screening", e);
         char *p = static_cast<char *>(ctx->lslab);
@@ -250,6 +253,9 @@ int ensure_learned(mbd_ctx *ctx) {
         ctx->dYl = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * N * 16);
         ctx->dspread = reinterpret_cast<double *>(p); p += al(sizeof(double) * nf1 * N);
         ctx->dmoments = reinterpret_cast<double *>(p); p += al(sizeof(double) * 6 * N);
+        ctx->dadj = reinterpret_cast<double *>(p); p += al(sizeof(double) * 6 * N);
+        ctx->dzc = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * 2 * N * 128);
+        ctx->dXl = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * N * kLF);
         ctx->doffs = reinterpret_cast<int *>(p);
         const int offs[2] = {0, N};
         e = cudaMemcpy(ctx->doffs, offs, sizeof(offs), cudaMemcpyHostToDevice);
@@ -888,16 +894,18 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_evaluate");
     // ---- screening (Sec. 2.3) ----
     const bool learned = ctx->opt.scs_mode == MBD_SCS_LEARNED && !ctx->force_plain;
+    ctx->last_learned = false;
     if (learned) {   // model prediction of alpha_bar(iu) in place of the Dyson solves
-        if (want_grad)
-            return fail(ctx, MBD_ERR_UNSUPPORTED, "learned_screening", "learned screening gives energies only");
+        if (out.grad_params)
+            return fail(ctx, MBD_ERR_UNSUPPORTED, "learned_screening",
+                        "learned screening gives energies and coordinate gradients only");
         if (ctx->members < 1) return fail(ctx, MBD_ERR_STATE, "learned_screening", "no model set");
         int rc0 = ensure_learned(ctx);
         if (rc0) return rc0;
         prepare_atoms(b, ctx->dstatus, s);
         scs_features(N, 1, ctx->doffs, in.R, in.a0ref, in.c6ref, in.rref, in.ratio, ctx->dfeat, ctx->dmoments, s);
         const cudaError_t ef = mlp_forward(N, ctx->members, ctx->dfeat, ctx->dmeanstd, ctx->dmeanstd + kLF, ctx->dmodel,
-                                           ctx->dYl, nullptr, s);
+                                           ctx->dYl, want_grad ? ctx->dzc : nullptr, s);
         if (ef != cudaSuccess) return cuda_fail(ctx, "learned_screening", ef);
         learned_alpha(N, ctx->members, nf1, ctx->dalu, ctx->dYl, ctx->dabar, ctx->dspread, s);
         screened_params(b, ctx->dstatus, s);
@@ -1047,6 +1055,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         MBD_CUDA(cudaStreamSynchronize(s), "learned_screening");
         ctx->learned_est = est;
         ctx->learned_fallback = 0;
+        ctx->last_learned = est <= ctx->opt.learned_max_error;
         if (!(est <= ctx->opt.learned_max_error)) {
             ctx->force_plain = true;
             const int rc2 = run(ctx, s, in, out, want_grad);
@@ -1055,9 +1064,20 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
             ctx->learned_fallback = 1;
             return rc2;
         }
+        if (want_grad) {
+            // dE/dR = (MBD term at fixed screened parameters, in dgR) + sum h dalpha_bar/dR through
+            // the members' outputs, the network and the features
+            learned_dy(N, ctx->members, nf1, ctx->dh, ctx->dabar, ctx->dYl, s);
+            const cudaError_t eb = mlp_backward(N, ctx->members, ctx->dfeat, ctx->dmeanstd, ctx->dmeanstd + kLF,
+                                                ctx->dmodel, ctx->dzc, ctx->dYl, ctx->dXl, nullptr, s);
+            if (eb != cudaSuccess) return cuda_fail(ctx, "learned_screening", eb);
+            learned_forces(N, in.R, in.a0ref, in.rref, in.ratio, ctx->dmoments, ctx->dXl, ctx->members, ctx->dadj,
+                           ctx->dgR, s);
+            if (out.grad_coords) scale_copy(ctx->dgR, 3 * N, nullptr, out.grad_coords, s);
+        }
     }
     // ---- gradients (Sec. 2.4) ----
-    if (want_grad) backward_passes(ctx, s, b, nullptr, out.grad_coords, out.grad_params);
+    if (want_grad && !learned) backward_passes(ctx, s, b, nullptr, out.grad_coords, out.grad_params);
     if (out.alpha_scs)
         MBD_CUDA(cudaMemcpyAsync(out.alpha_scs, ctx->dabar0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s),
                  "outputs");
@@ -1284,6 +1304,9 @@ int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
     if (!ctx) return MBD_ERR_INPUT;
     if (!ctx->have_forward)
         return fail(ctx, MBD_ERR_STATE, "mbd_backward_dev", "no forward evaluation to differentiate");
+    if (ctx->last_learned)
+        return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_backward_dev",
+                    "the last evaluation used learned screening; request its gradients from the evaluation");
     if (n_atoms != ctx->N || !coords || !alpha0_ref || !c6_ref || !rvdw_ref || !volume_ratio)
         return fail(ctx, MBD_ERR_INPUT, "mbd_backward_dev", "inputs must match the forward evaluation");
     MBD_CUDA(cudaSetDevice(ctx->device), "mbd_backward_dev");

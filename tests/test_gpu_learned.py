@@ -187,8 +187,46 @@ def test_learned_mode_rejects_gradients_and_periodic_systems():
         assert e.value.code == 7                      # no model set
         m.set_scs_model(np.zeros((1, binding.LEARNED_PARAMS), np.float16), np.zeros(74), np.ones(74))
         with pytest.raises(binding.MBDError) as e:
-            m.evaluate(True)
+            m.evaluate(True)                          # parameter gradients: not in learned mode
         assert e.value.code == 8
+
+
+def oracle_learned_energy(R, s, members, mean, std):
+    """FP64 oracle of the learned path: features -> members (FP16 weights) -> alpha_bar -> MBD."""
+    a0, om, rv = o.ts_scaling(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
+    X = LS.features(R, a0, om, rv, s.ratio)
+    Xs = (X - mean.astype(np.float32).astype(np.float64)) / std.astype(np.float32).astype(np.float64)
+    u, _ = o.freq_grid(15)
+    alpha_u = np.stack([o.dyn_alpha(a0, om, uk) for uk in u])
+    ab, _ = LS.predict_alpha_bar(Xs, [LS.round_fp16(mp) for mp in members], alpha_u)
+    rc, (abar0, c6, ombar, rbar) = o.screened_params(ab, a0, rv)
+    return o.mbd_energy(R, abar0, ombar, rbar)
+
+
+def test_learned_forces_match_oracle_finite_differences():
+    s = syn.sphere_cluster(14, seed=8)
+    members = [[(W * 0.05, b * 0.05) for W, b in mp] for mp in random_params(2, seed=21)]
+    p16 = np.stack([pack16(mp) for mp in members])
+    a0, om, rv = o.ts_scaling(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
+    X = LS.features(s.coords, a0, om, rv, s.ratio)
+    mean, std = X.mean(0), np.maximum(X.std(0), 1e-3)
+    with binding.MBD(0, scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1.0) as m:
+        m.set_geometry(s.coords)
+        m.set_free_atom_params(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
+        m.set_scs_model(p16, mean, std)
+        E, gR, gp, _ = m.evaluate(True, param_gradients=False)
+        assert gp is None and not m.learned_stats()["fell_back"]
+    assert E == pytest.approx(oracle_learned_energy(s.coords, s, members, mean, std), rel=1e-5)
+    h = 1e-4
+    fd = np.zeros_like(gR)
+    for i in range(s.n_atoms):
+        for c in range(3):
+            Rp, Rm = s.coords.copy(), s.coords.copy()
+            Rp[i, c] += h; Rm[i, c] -= h
+            fd[i, c] = (oracle_learned_energy(Rp, s, members, mean, std) -
+                        oracle_learned_energy(Rm, s, members, mean, std)) / (2 * h)
+    assert np.abs(gR - fd).max() <= 1e-4 * np.abs(fd).max() + 1e-9, (np.abs(gR - fd).max(), np.abs(fd).max())
+    assert np.abs(gR.sum(0)).max() < 1e-6 * np.abs(gR).max()
 
 
 def test_training_on_the_gpu_gains_over_the_unscreened_model():
