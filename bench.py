@@ -35,7 +35,7 @@ WORKLOAD = "finite2000"
 # Ewald split, real-space and reciprocal cutoffs of the periodic workload (real-space cutoff
 # 30 bohr; gamma = 6/30, k_c = 10 gamma)
 PERIODIC_EWALD = (0.2, 30.0, 2.0)
-N_TARGET = {"finite2000": 2000, "cell256": 256, "finite8000": 8000}
+N_TARGET = {"finite2000": 2000, "cell256": 256, "finite8000": 8000, "batch4096": 275}
 # nominal FP64 : dense BF16 tensor rate of the part (1.25 TFLOP/s : 2250 TFLOP/s)
 FP64_OVER_BF16 = 1.25 / 2250.0
 # DRAM bytes (read + write) per k_gemm_nn launch from the committed ncu capture
@@ -55,9 +55,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("finite2000", "cell256", "finite8000"), default=WORKLOAD,
+    ap.add_argument("--workload", choices=("finite2000", "cell256", "finite8000", "batch4096"), default=WORKLOAD,
                     help="finite2000: the headline cluster; cell256: the periodic cell (FP64 only); "
-                         "finite8000: the large cluster")
+                         "finite8000: the large cluster; batch4096: the varlen cluster batch with the learned "
+                         "screening model beside plain screening")
+    ap.add_argument("--batch-clusters", type=int, default=64,
+                    help="batch4096: clusters of the batch evaluated per step (the first ones of the recipe)")
     ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64"), default="tf32x3",
                     help="matrix-function arithmetic of the timed arm (the FP64 path is measured beside it)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison arm (0: skip)")
@@ -402,10 +405,123 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Varlen cluster batch: energy + coordinate gradients per cluster through the library API,
+    plain screening against the learned model (with its fallback at 1e-6 Ha/atom, and without
+    fallback), on the same clusters."""
+    import numpy as np
+    import torch
+    from paper_2308_03140_gb300 import binding, build
+    from paper_2308_03140_gb300 import synthetic as syn
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    build.build()
+    binding.load()
+    K = args.batch_clusters
+    systems = syn.cluster_batch(K)
+    model = np.load(os.path.join(ROOT, "paper_2308_03140_gb300", "learned_scs_model.npz"))
+    precision = {"fp64": binding.MBD_PREC_FP64, "tf32": binding.MBD_PREC_TF32,
+                 "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3}[args.precision]
+    arms = {"plain": dict(), "learned": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e-6),
+            "learned_no_fallback": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e300)}
+    ctxs = {}
+    for name, opt in arms.items():
+        m = binding.MBD(local, precision=precision, **opt)
+        if name != "plain":
+            m.set_scs_model(model["params16"], model["mean"], model["std"])
+        ctxs[name] = m
+
+    launches = {}
+
+    def one_pass(name, record=None):
+        m = ctxs[name]
+        dev_ms, fb = 0.0, 0
+        for i, s in enumerate(systems):
+            m.set_geometry(s.coords)
+            m.set_free_atom_params(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
+            E, gR, _, _ = m.evaluate(True, param_gradients=(name == "plain"))
+            prof = m.profile()
+            dev_ms += prof["total_ms"]
+            launches[name] = launches.get(name, 0) + prof["launches"]
+            if name != "plain":
+                fb += int(m.learned_stats()["fell_back"])
+            if record is not None:
+                record.append((E, gR))
+        return dev_ms, fb
+
+    for m in ctxs.values():
+        m.set_profiling(True)
+    results = {}
+    ref = []
+    one_pass("plain", ref)                       # reference energies and forces (also a warm-up)
+    for name in arms:
+        for _ in range(args.warmup):
+            one_pass(name)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local) if name == "learned" else None
+        if clocks:
+            clocks.start()
+        launches[name] = 0
+        t0 = time.perf_counter()
+        dev_ms, fb, rec = 0.0, 0, []
+        for _ in range(args.steps):
+            d, f = one_pass(name, rec if not rec else None)
+            dev_ms += d
+            fb += f
+        wall = time.perf_counter() - t0
+        results[name] = {"solves_per_s_device": K * args.steps / (dev_ms / 1e3), "solves_per_s_e2e": K * args.steps / wall,
+                         "fallback_fraction": fb / (K * args.steps) if name != "plain" else None,
+                         "clocks": clocks.stop() if clocks else None}
+        if name != "plain":
+            dE = [abs(e - er) / s.n_atoms for (e, _), (er, _), s in zip(rec, ref, systems)]
+            dF = [float(np.abs(g - gr).max()) for (_, g), (_, gr) in zip(rec, ref)]
+            results[name].update({"mean_abs_de_per_atom_ha": float(np.mean(dE)), "max_abs_de_per_atom_ha": float(np.max(dE)),
+                                  "max_force_err_ha_bohr": float(np.max(dF))})
+    for m in ctxs.values():
+        m.close()
+    n_mean = float(np.mean([s.n_atoms for s in systems]))
+    line = {
+        "metric": METRIC, "value": results["learned"]["solves_per_s_device"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * K / results["learned"]["solves_per_s_device"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": f"{args.precision}+f32+f16", "data": "synthetic",
+        "config": {"workload": "batch4096", "clusters_per_step": K, "mean_atoms": n_mean,
+                   "sizes": "U{50..500}, the first clusters of the 4096-cluster recipe", "precision": args.precision,
+                   "learned_model": "paper_2308_03140_gb300/learned_scs_model.npz (4 members, trained on 20000 "
+                                    "perturbed plain-screening solves)",
+                   "l2": "per-cluster working sets below L2; timed as whole evaluations per cluster"},
+        "arms": results,
+        "e2e": {"value": results["learned"]["solves_per_s_e2e"], "unit": UNIT,
+                "h2d_bytes_per_step": int(8 * sum(7 * s.n_atoms for s in systems)),
+                "d2h_bytes_per_step": int(8 * sum(1 + 3 * s.n_atoms + s.n_atoms for s in systems))},
+        "clocks": results["learned"]["clocks"],
+        "gpu_launches": launches.get("learned", 0),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        small = next(s for s in systems if s.n_atoms <= 250)
+        import oracle as o
+        t0 = time.perf_counter()
+        o.mbd_rsscs_gradient(*o.system_args(small), mode="adjoint")
+        dt = time.perf_counter() - t0
+        scale = (n_mean / small.n_atoms) ** 3
+        line["cpu_baseline"] = {"value": 1.0 / (dt * scale), "unit": UNIT,
+                                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                                "kind": "oracle", "sample": f"plain energy+gradient of one {small.n_atoms}-atom cluster "
+                                f"of the batch in {dt:.2f} s, extrapolated by (n/{small.n_atoms})^3 to the mean size"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch4096":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -150,6 +150,7 @@ struct mbd_ctx {
     std::vector<float> hmean, hstd;
     bool model_dirty = false, force_plain = false;
     void *lslab = nullptr;
+    size_t lbytes = 0;
     int lN = 0, lM = 0;
     void *dmodel = nullptr;
     float *dmeanstd = nullptr, *dfeat = nullptr, *dYl = nullptr;
@@ -238,14 +239,18 @@ int ensure_learned(mbd_ctx *ctx) {
     const size_t P = static_cast<size_t>(learned_param_count());
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     if (!ctx->lslab || ctx->lN != N || ctx->lM != M) {
-        if (ctx->lslab) cudaFree(ctx->lslab);
-        ctx->lslab = nullptr;
         const size_t bytes = al(2 * P * M) + al(sizeof(float) * 2 * kLF) + al(sizeof(float) * kLF * N) +
                              al(sizeof(float) * M * N * 16) + al(sizeof(double) * nf1 * N) + al(sizeof(double) * 6 * N) +
                              al(sizeof(double) * 6 * N) + al(sizeof(float) * M * 2 * N * 128) +
                              al(sizeof(float) * M * N * kLF) + al(sizeof(int) * 2);
-        cudaError_t e = cudaMalloc(&ctx->lslab, bytes);
-        if (e != cudaSuccess) return cuda_fail(ctx, "learned_screening", e);
+        cudaError_t e = cudaSuccess;
+        if (!ctx->lslab || ctx->lbytes < bytes) {   // re-carved in place when large enough
+            if (ctx->lslab) cudaFree(ctx->lslab);
+            ctx->lslab = nullptr;
+            e = cudaMalloc(&ctx->lslab, bytes);
+            if (e != cudaSuccess) return cuda_fail(ctx, "learned_screening", e);
+            ctx->lbytes = bytes;
+        }
         char *p = static_cast<char *>(ctx->lslab);
         ctx->dmodel = p; p += al(2 * P * M);
         ctx->dmeanstd = reinterpret_cast<float *>(p); p += al(sizeof(float) * 2 * kLF);
@@ -322,10 +327,15 @@ int allocate(mbd_ctx *ctx) {
                              ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * 2 * nf1 * ld * 3)
                              : 0;
     bytes += scs32;
-    release(ctx);
-    cudaError_t e = cudaMalloc(&ctx->slab, bytes);
-    if (e != cudaSuccess) return cuda_fail(ctx, "mbd_set_geometry", e);
-    ctx->slab_bytes = bytes;
+    // A slab large enough for the new size is re-carved in place (systems of varying size in
+    // a batch then reuse one allocation); otherwise it is replaced.
+    cudaError_t e = cudaSuccess;
+    if (!ctx->slab || ctx->slab_bytes < bytes) {
+        release(ctx);
+        e = cudaMalloc(&ctx->slab, bytes);
+        if (e != cudaSuccess) return cuda_fail(ctx, "mbd_set_geometry", e);
+        ctx->slab_bytes = bytes;
+    }
     char *p = static_cast<char *>(ctx->slab);
     for (auto &q : plan) {
         *q.first = reinterpret_cast<double *>(p);

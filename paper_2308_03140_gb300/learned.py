@@ -37,9 +37,10 @@ def init_params(members: int, seed: int) -> np.ndarray:
     return out
 
 
-def perturbed_cluster(index: int, seed0: int = 4000, n_range=(50, 500)):
-    """Cluster `index` of the batch recipe (sphere cluster, size U{50..500}, seed seed0 + index)
-    with positions moved by N(0, 0.1 bohr) and parameters scaled by U[0.95, 1.05]."""
+def perturbed_cluster(index: int, seed0: int = 100_000, n_range=(50, 500)):
+    """Training cluster `index`: a sphere cluster of the batch recipe (size U{50..500}, seed
+    seed0 + index, disjoint from the evaluation batch's seeds 4000 + i) with positions moved by
+    N(0, 0.1 bohr) and parameters scaled by U[0.95, 1.05]."""
     rng = np.random.default_rng(10_000_000 + seed0 + index)
     n = int(rng.integers(n_range[0], n_range[1] + 1))
     s = syn.sphere_cluster(n, seed=seed0 + index, name=f"cluster{index}")
@@ -149,3 +150,69 @@ class Ensemble:
     def save(self, path: str):
         p16, mean, std = self.model()
         np.savez(path, params16=p16, mean=mean, std=std)
+
+
+def evaluate_accuracy(ens, systems, device: int = 0, threshold: float = 1e-6):
+    """Learned against plain screening (FP64 path) on the systems: per system |dE|/N, the
+    estimate per atom and whether the learned evaluation would fall back at `threshold`."""
+    p16, mean, std = ens.model()
+    rows = []
+    with binding.MBD(device) as plain, binding.MBD(device, scs_mode=binding.MBD_SCS_LEARNED,
+                                                   learned_max_error=1e300) as lm:
+        lm.set_scs_model(p16, mean, std)
+        for s in systems:
+            for m in (plain, lm):
+                m.set_geometry(s.coords)
+                m.set_free_atom_params(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
+            E0 = plain.evaluate(False)[0]
+            E1 = lm.evaluate(False)[0]
+            est = lm.learned_stats()["estimated_error_per_atom"]
+            rows.append((s.n_atoms, abs(E1 - E0) / s.n_atoms, est, est > threshold))
+    return rows
+
+
+def main(argv=None):
+    """Train the learned screening model on the GPU and save it:
+    python -m paper_2308_03140_gb300.learned --solves 20000 --out model.npz"""
+    import argparse
+    import time
+    import torch
+    from . import build
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--solves", type=int, default=20000)
+    ap.add_argument("--members", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--eval", type=int, default=64, help="held-out clusters of the batch recipe")
+    ap.add_argument("--out", required=True)
+    a = ap.parse_args(argv)
+    build.build()
+    binding.load()
+    t0 = time.time()
+    Xs, Ys = [], []
+    for c0 in range(0, a.solves, 500):
+        X, Y = training_data([perturbed_cluster(i) for i in range(c0, min(a.solves, c0 + 500))])
+        Xs.append(X)
+        Ys.append(Y)
+    X, Y = torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
+    t1 = time.time()
+    ens = Ensemble(members=a.members, seed=0)
+    ens.set_standardisation(X)
+    hist = ens.fit(X, Y, steps=a.steps, batch=a.batch, lr=a.lr, log_every=500)
+    t2 = time.time()
+    ens.save(a.out)
+    var = float(((Y - Y.mean(0)) ** 2).mean())
+    print(f"training set: {a.solves} solves, {X.shape[0]} atoms, {t1 - t0:.1f} s; training {t2 - t1:.1f} s; "
+          f"final loss {hist[-1]:.3e} (target variance {var:.3e})", flush=True)
+    rows = evaluate_accuracy(ens, syn.cluster_batch(a.eval) if a.eval else [])
+    if rows:
+        err = np.array([r[1] for r in rows])
+        est = np.array([r[2] for r in rows])
+        fb = np.mean([r[3] for r in rows])
+        print(f"held-out {len(rows)} clusters: |dE|/atom mean {err.mean():.3e} max {err.max():.3e}; "
+              f"estimate mean {est.mean():.3e}; fallback fraction at 1e-6: {fb:.2f}", flush=True)
+
+
+if __name__ == "__main__":
+    main()
