@@ -1067,11 +1067,20 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         ctx->learned_fallback = 0;
         ctx->last_learned = est <= ctx->opt.learned_max_error;
         if (!(est <= ctx->opt.learned_max_error)) {
+            // the profile of the plain re-run also counts the discarded learned attempt
+            const int attempt_launches = static_cast<int>(launch_count() - launches0);
+            double attempt_ms = 0.0;
+            if (ctx->profiling && e_start && e_ns) {
+                MBD_CUDA(cudaEventSynchronize(e_ns), "learned_screening");
+                attempt_ms = span_ms(e_start, e_ns);
+            }
             ctx->force_plain = true;
             const int rc2 = run(ctx, s, in, out, want_grad);
             ctx->force_plain = false;
             ctx->learned_est = est;
             ctx->learned_fallback = 1;
+            ctx->prof.launches += attempt_launches;
+            ctx->prof.total_ms += attempt_ms;
             return rc2;
         }
         if (want_grad) {
