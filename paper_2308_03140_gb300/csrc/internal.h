@@ -174,9 +174,10 @@ void chain_screen(const AtomBufs &b, const MbdGradOut &o, double *h, double *g_a
 
 // SCS adjoint pair pass: with X = M^{-1} E and V = M^{-1} H per frequency, adds
 // -1/3 sum dM_pq (V X^T)_pq to dE/d alpha0, dE/d omega, dE/d R_vdW (g_a0, g_om, g_rv)
-// and dE/dR (gR, accumulated).
+// and dE/dR (gR, accumulated).  fp32: per-pair arithmetic in single precision (sums FP64),
+// for the reduced-precision modes.
 void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, const double *V,
-                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR,
+                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR, bool fp32,
                    cudaStream_t s);
 
 // TS-scaling chain to [4][N] parameter gradients, times *scale (device) if given.

@@ -292,7 +292,20 @@ __global__ void k_chain(AtomBufs b, MbdGradOut o, double *h, double *g_a0, doubl
 //   dE/d alpha_i(u) += -1/3 <Ws, dB/d alpha_i>,  dE/dR_vdW,i += -1/3 <Ws, dB/dS>,
 //   dE/dR_i += +1/3 <Ws, dB/dr>  (r = R_j - R_i),  B = (1 - f) T^GG,
 // plus the diagonal block: dE/d alpha_i(u) += -1/3 sum_x (V X^T)_{ix,ix} (-1/alpha_i^2).
+// The per-pair arithmetic runs in T (double, or float in the reduced-precision modes);
+// the per-thread and block sums are FP64.
 // Dynamic shared memory: nf1 * 128 doubles of per-thread accumulators.
+template <typename T> struct PairMath;
+template <> struct PairMath<double> {
+    static __device__ __forceinline__ Fermi fermi(double r, double S, double b, double a) { return pairs::fermi(r, S, b, a); }
+    static __device__ __forceinline__ Radial radial(double r, double s) { return pairs::tgg_radial(r, s); }
+};
+template <> struct PairMath<float> {
+    static __device__ __forceinline__ FermiF fermi(float r, float S, float b, float a) { return pairs::fermi_f(r, S, b, a); }
+    static __device__ __forceinline__ RadialF radial(float r, float s) { return pairs::tgg_radial_f(r, s); }
+};
+
+template <typename T>
 __global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, double a, const double *X,
                                                   const double *V, long long xstride, double *g_a0,
                                                   double *g_om, double *g_rv, double *gR) {
@@ -303,45 +316,45 @@ __global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, doubl
     double acc[4] = {0, 0, 0, 0};   // g_rv, gR x3
     for (int j = t; j < b.N; j += 128) {
         if (j == i) continue;
-        const double r[3] = {b.R[3 * j] - Ri[0], b.R[3 * j + 1] - Ri[1], b.R[3 * j + 2] - Ri[2]};
-        const double rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), ir = 1.0 / rho;
-        const Fermi f = fermi(rho, b.rv[i] + b.rv[j], beta, a);
-        const double sr = 1.0 - f.f;
+        const T r[3] = {static_cast<T>(b.R[3 * j] - Ri[0]), static_cast<T>(b.R[3 * j + 1] - Ri[1]),
+                        static_cast<T>(b.R[3 * j + 2] - Ri[2])};
+        const T rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), ir = T(1) / rho;
+        const auto f = PairMath<T>::fermi(rho, static_cast<T>(b.rv[i] + b.rv[j]), static_cast<T>(beta), static_cast<T>(a));
+        const T sr = T(1) - f.f;
+        T pacc[4] = {0, 0, 0, 0};
         for (int k = 0; k < b.nf1; ++k) {
             const double *Vk = V + k * xstride, *Xk = X + k * xstride;
-            double Vi[9], Xi[9], Vj[9], Xj[9];
-            for (int e = 0; e < 9; ++e) {
-                Vi[e] = Vk[9LL * i + e]; Xi[e] = Xk[9LL * i + e];
-                Vj[e] = Vk[9LL * j + e]; Xj[e] = Xk[9LL * j + e];
-            }
-            double Ws[9];
+            T Ws[9];
             for (int x = 0; x < 3; ++x)
                 for (int y = 0; y < 3; ++y) {
                     double w = 0.0;
-                    for (int c = 0; c < 3; ++c) w += Vi[3 * x + c] * Xj[3 * y + c] + Xi[3 * x + c] * Vj[3 * y + c];
-                    Ws[3 * x + y] = w;
+                    for (int c = 0; c < 3; ++c)
+                        w += Vk[9LL * i + 3 * x + c] * Xk[9LL * j + 3 * y + c] + Xk[9LL * i + 3 * x + c] * Vk[9LL * j + 3 * y + c];
+                    Ws[3 * x + y] = static_cast<T>(w);
                 }
-            const double tr = Ws[0] + Ws[4] + Ws[8];
-            double Wr[3], Wtr[3];
+            const T tr = Ws[0] + Ws[4] + Ws[8];
+            T Wr[3], Wtr[3];
             for (int x = 0; x < 3; ++x) {
                 Wr[x] = Ws[3 * x] * r[0] + Ws[3 * x + 1] * r[1] + Ws[3 * x + 2] * r[2];
                 Wtr[x] = Ws[x] * r[0] + Ws[3 + x] * r[1] + Ws[6 + x] * r[2];
             }
-            const double rWr = r[0] * Wr[0] + r[1] * Wr[1] + r[2] * Wr[2];
+            const T rWr = r[0] * Wr[0] + r[1] * Wr[1] + r[2] * Wr[2];
             const double si = b.sig_u[k * b.N + i], sj = b.sig_u[k * b.N + j];
             const double s = sqrt(si * si + sj * sj);
-            const Radial q = tgg_radial(rho, s);
-            const double WT = q.P * tr + q.W * rWr;            // <Ws, T^GG>
-            const double WTs = q.dPs * tr + q.dWs * rWr;       // <Ws, dT^GG/ds>
+            const auto q = PairMath<T>::radial(rho, static_cast<T>(s));
+            const T WT = q.P * tr + q.W * rWr;            // <Ws, T^GG>
+            const T WTs = q.dPs * tr + q.dWs * rWr;       // <Ws, dT^GG/ds>
             // ds/d alpha_i = (sigma_i / s) * sigma_i / (3 alpha_i)
             const double dsda = si * si / (3.0 * s * b.al_u[k * b.N + i]);
-            gal_s[k * 128 + t] += -1.0 / 3.0 * sr * WTs * dsda;
-            acc[0] += -1.0 / 3.0 * (-f.df_dS) * WT;
+            gal_s[k * 128 + t] += -1.0 / 3.0 * static_cast<double>(sr * WTs) * dsda;
+            pacc[0] += -f.df_dS * WT;
             for (int c = 0; c < 3; ++c) {
-                const double WdT = (q.dP * tr + q.dW * rWr) * r[c] * ir + q.W * (Wr[c] + Wtr[c]);
-                acc[1 + c] += 1.0 / 3.0 * (sr * WdT - f.df_drho * r[c] * ir * WT);
+                const T WdT = (q.dP * tr + q.dW * rWr) * r[c] * ir + q.W * (Wr[c] + Wtr[c]);
+                pacc[1 + c] += sr * WdT - f.df_drho * r[c] * ir * WT;
             }
         }
+        acc[0] += -1.0 / 3.0 * static_cast<double>(pacc[0]);
+        for (int c = 0; c < 3; ++c) acc[1 + c] += 1.0 / 3.0 * static_cast<double>(pacc[1 + c]);
     }
     __syncthreads();
     __shared__ double scratch[4 * 4];
@@ -473,11 +486,12 @@ void chain_screen(const AtomBufs &b, const MbdGradOut &o, double *h, double *g_a
 }
 
 void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, const double *V,
-                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR,
+                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR, bool fp32,
                    cudaStream_t s) {
     const size_t smem = sizeof(double) * b.nf1 * 128;
     count_launches(1);
-    k_scs_grad<<<b.N, 128, smem, s>>>(b, beta, a, X, V, xstride, g_a0, g_om, g_rv, gR);
+    if (fp32) k_scs_grad<float><<<b.N, 128, smem, s>>>(b, beta, a, X, V, xstride, g_a0, g_om, g_rv, gR);
+    else k_scs_grad<double><<<b.N, 128, smem, s>>>(b, beta, a, X, V, xstride, g_a0, g_om, g_rv, gR);
 }
 
 void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv,

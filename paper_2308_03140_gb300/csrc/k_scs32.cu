@@ -139,30 +139,50 @@ __global__ void k_to_f32(const double *A, long long total, float *B) {
         B[e] = static_cast<float>(A[e]);
 }
 
-// R = B - A X (FP64, A full row-major, 3 RHS), one warp per row; r32 = (float) R.
-__global__ void k_residual3(const double *A, long long ld, long long mstride, const double *Bv, const double *X,
-                            long long xstride, float *r32, int n) {
-    const int b = blockIdx.y;
-    const long long row = blockIdx.x * static_cast<long long>(blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= ld) return;
-    const double *a = A + b * mstride + row * ld;
+// R = B - A X (FP64, A full row-major, 3 RHS); r32 = (float) R.  A CTA of 8 warps owns 32
+// consecutive rows (4 per warp) and stages X in chunks of 256 rows in shared memory, so X is
+// read from L2 once per 32 rows while A streams from HBM once.
+constexpr int kResRows = 4, kResChunk = 256;
+__global__ void __launch_bounds__(256) k_residual3(const double *A, long long ld, long long mstride, const double *Bv,
+                                                   const double *X, long long xstride, float *r32, int n) {
+    __shared__ double xs[kResChunk * 3];
+    const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long row0 = blockIdx.x * 32LL + warp * kResRows;
+    const double *Ab = A + b * mstride;
     const double *x = X + b * xstride;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    if (row < n)
-        for (long long c = lane; c < n; c += 32) {
-            const double v = a[c];
-            a0 += v * x[3 * c];
-            a1 += v * x[3 * c + 1];
-            a2 += v * x[3 * c + 2];
+    double acc[kResRows][3];
+#pragma unroll
+    for (int r = 0; r < kResRows; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0.0;
+    for (int c0 = 0; c0 < n; c0 += kResChunk) {
+        const int m = min(kResChunk, n - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 3 * m; e += 256) xs[e] = x[3LL * c0 + e];
+        __syncthreads();
+        for (int c = lane; c < m; c += 32) {
+            const double x0 = xs[3 * c], x1 = xs[3 * c + 1], x2 = xs[3 * c + 2];
+#pragma unroll
+            for (int r = 0; r < kResRows; ++r) {
+                const long long row = row0 + r;
+                if (row < n) {
+                    const double v = Ab[row * ld + c0 + c];
+                    acc[r][0] += v * x0;
+                    acc[r][1] += v * x1;
+                    acc[r][2] += v * x2;
+                }
+            }
         }
-    a0 = warp_sumd(a0); a1 = warp_sumd(a1); a2 = warp_sumd(a2);
-    if (lane == 0) {
-        const double *bb = Bv + b * xstride + 3 * row;
-        float *rr = r32 + b * xstride + 3 * row;
-        rr[0] = static_cast<float>(bb[0] - a0);
-        rr[1] = static_cast<float>(bb[1] - a1);
-        rr[2] = static_cast<float>(bb[2] - a2);
+    }
+#pragma unroll
+    for (int r = 0; r < kResRows; ++r) {
+        const double s0 = warp_sumd(acc[r][0]), s1 = warp_sumd(acc[r][1]), s2 = warp_sumd(acc[r][2]);
+        const long long row = row0 + r;
+        if (lane == 0 && row < ld) {
+            const double *bb = Bv + b * xstride + 3 * row;
+            float *rr = r32 + b * xstride + 3 * row;
+            rr[0] = static_cast<float>(bb[0] - (row < n ? s0 : 0.0));
+            rr[1] = static_cast<float>(bb[1] - (row < n ? s1 : 0.0));
+            rr[2] = static_cast<float>(bb[2] - (row < n ? s2 : 0.0));
+        }
     }
 }
 
@@ -228,8 +248,8 @@ void refine_solve3(const double *A64, const float *L32, const float *dinv, long 
     k_accumulate<<<gridn(total), 256, 0, s>>>(X, work, total, 1);
     for (int it = 0; it < steps; ++it) {
         count_launches(1);
-        k_residual3<<<dim3(static_cast<unsigned>((ld + 7) / 8), batch), 256, 0, s>>>(A64, ld, ld * ld, B, X, xs,
-                                                                                     work, n);
+        k_residual3<<<dim3(static_cast<unsigned>((ld + 31) / 32), batch), 256, 0, s>>>(A64, ld, ld * ld, B, X, xs,
+                                                                                      work, n);
         chol_solve3_f32(L32, ld, ld * ld, batch, dinv, work, work2, xs, s);
         count_launches(1);
         k_accumulate<<<gridn(total), 256, 0, s>>>(X, work, total, 0);

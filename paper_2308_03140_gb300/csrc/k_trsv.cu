@@ -27,19 +27,22 @@ __device__ __forceinline__ T wsum(T v) {
     return v;
 }
 
-// x (64x3, shared) = D^{-1} b_I (forward) or D^{-T} b_I (backward).
+// x (64x3, shared) = D^{-1} b_I (forward) or D^{-T} b_I (backward).  The 64x64 inverse is
+// first staged into shared memory with coalesced loads (all in flight at once), so the
+// triangular products read on-chip memory instead of chaining 64 dependent global loads.
 template <typename T, bool BWD>
-__device__ void diag_solve(const T *Di, const T *bI, T (*s)[3], T (*x)[3]) {
+__device__ void diag_solve(const T *Di, const T *bI, T (*D)[65], T (*s)[3], T (*x)[3]) {
     const int t = threadIdx.x;
+    for (int e = t; e < 64 * 64; e += blockDim.x) D[e >> 6][e & 63] = Di[e];
     if (t < 192) s[t / 3][t % 3] = bI[t];
     __syncthreads();
     if (t < 192) {
         const int r = t / 3, c = t % 3;
         T v = 0;
         if (!BWD)
-            for (int k = 0; k <= r; ++k) v += Di[r * 64 + k] * s[k][c];
+            for (int k = 0; k <= r; ++k) v += D[r][k] * s[k][c];
         else
-            for (int k = r; k < 64; ++k) v += Di[k * 64 + r] * s[k][c];
+            for (int k = r; k < 64; ++k) v += D[k][r] * s[k][c];
         x[r][c] = v;
     }
     __syncthreads();
@@ -51,22 +54,30 @@ __global__ void __launch_bounds__(256) k_trsv_fwd_block(const T *L, long long ld
     const long long b = blockIdx.y;
     const T *Lb = L + b * mstride;
     T *Xb = X + b * xstride, *Wb = W + b * xstride;
-    __shared__ T s[64][3], x[64][3];
+    __shared__ T D[64][65], s[64][3], x[64][3];
     const long long I0 = static_cast<long long>(I) * 64;
-    diag_solve<T, false>(dinv + b * dstride + static_cast<long long>(I) * 4096, Xb + 3 * I0, s, x);
-    // rows of this CTA: 64 rows starting after block I
+    diag_solve<T, false>(dinv + b * dstride + static_cast<long long>(I) * 4096, Xb + 3 * I0, D, s, x);
+    // rows of this CTA: 64 rows starting after block I; warp w owns rows w, w + 8, ...
     const long long r0 = I0 + 64 + static_cast<long long>(blockIdx.x) * 64;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (r0 < ld) {
-        for (int rr = warp; rr < 64; rr += 8) {
-            const long long q = r0 + rr;
-            const T *Lq = Lb + q * ld + I0;
-            const T l0 = Lq[lane], l1 = Lq[lane + 32];
-            T a0 = l0 * x[lane][0] + l1 * x[lane + 32][0];
-            T a1 = l0 * x[lane][1] + l1 * x[lane + 32][1];
-            T a2 = l0 * x[lane][2] + l1 * x[lane + 32][2];
+        T l0[8], l1[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {   // issue all loads of the warp's rows first
+            const T *Lq = Lb + (r0 + warp + 8 * k) * ld + I0;
+            l0[k] = Lq[lane];
+            l1[k] = Lq[lane + 32];
+        }
+        const T y0a = x[lane][0], y0b = x[lane + 32][0], y1a = x[lane][1], y1b = x[lane + 32][1];
+        const T y2a = x[lane][2], y2b = x[lane + 32][2];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            T a0 = l0[k] * y0a + l1[k] * y0b;
+            T a1 = l0[k] * y1a + l1[k] * y1b;
+            T a2 = l0[k] * y2a + l1[k] * y2b;
             a0 = wsum(a0); a1 = wsum(a1); a2 = wsum(a2);
             if (lane == 0) {
+                const long long q = r0 + warp + 8 * k;
                 Xb[3 * q] -= a0;
                 Xb[3 * q + 1] -= a1;
                 Xb[3 * q + 2] -= a2;
@@ -83,20 +94,24 @@ __global__ void __launch_bounds__(256) k_trsv_bwd_block(const T *L, long long ld
     const long long b = blockIdx.y;
     const T *Lb = L + b * mstride;
     T *Xb = X + b * xstride, *Wb = W + b * xstride;
-    __shared__ T s[64][3], x[64][3];
+    __shared__ T D[64][65], s[64][3], x[64][3];
     __shared__ T part[4][64][3];
     const long long I0 = static_cast<long long>(I) * 64;
-    diag_solve<T, true>(dinv + b * dstride + static_cast<long long>(I) * 4096, Wb + 3 * I0, s, x);
+    diag_solve<T, true>(dinv + b * dstride + static_cast<long long>(I) * 4096, Wb + 3 * I0, D, s, x);
     // columns of this CTA: 64 columns j < I0
     const long long c0 = static_cast<long long>(blockIdx.x) * 64;
     const int t = threadIdx.x, col = t & 63, grp = t >> 6;
     if (c0 < I0) {
+        T l[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) l[k] = Lb[(I0 + grp + 4 * k) * ld + c0 + col];   // rows of block I
         T a0 = 0, a1 = 0, a2 = 0;
-        for (int i = grp; i < 64; i += 4) {   // rows of block I, coalesced along j
-            const T l = Lb[(I0 + i) * ld + c0 + col];
-            a0 += l * x[i][0];
-            a1 += l * x[i][1];
-            a2 += l * x[i][2];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int i = grp + 4 * k;
+            a0 += l[k] * x[i][0];
+            a1 += l[k] * x[i][1];
+            a2 += l[k] * x[i][2];
         }
         part[grp][col][0] = a0; part[grp][col][1] = a1; part[grp][col][2] = a2;
     }

@@ -79,5 +79,31 @@ __device__ __forceinline__ RadialT erfc_radial(double rho, double gamma) {
             4.0 * gamma * x * x * x * ex * ir5 + 5.0 * Cx * ir5 * ir};
 }
 
+// Single-precision versions of fermi and tgg_radial for the pair passes of the
+// reduced-precision modes (same formulas).
+struct FermiF { float f, df_drho, df_dS; };
+__device__ __forceinline__ FermiF fermi_f(float rho, float S, float beta, float a) {
+    const float x = rho / (beta * S);
+    const float f = 1.0f / (1.0f + expf(-a * (x - 1.0f)));
+    const float dfx = a * f * (1.0f - f);
+    return {f, dfx / (beta * S), -dfx * x / S};
+}
+struct RadialF { float P, W, dP, dW, dPs, dWs; };
+__device__ __forceinline__ RadialF tgg_radial_f(float rho, float s) {
+    const float z = rho / s, z2 = z * z;
+    const float th = static_cast<float>(kTwoOverSqrtPi) * z * expf(-z2);
+    const float F1 = erff(z) - th;
+    const float G = 2.0f * z2 * th - 3.0f * F1;
+    const float ir = 1.0f / rho, ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+    RadialF o;
+    o.P = F1 * ir3;
+    o.W = G * ir5;
+    o.dP = 2.0f * z * th / s * ir3 - 3.0f * F1 * ir3 * ir;
+    o.dW = -4.0f * z2 * z * th / s * ir5 - 5.0f * G * ir5 * ir;
+    o.dPs = -2.0f * z2 * th / s * ir3;
+    o.dWs = 4.0f * z2 * z2 * th / s * ir5;
+    return o;
+}
+
 }  // namespace pairs
 }  // namespace mbdgb
