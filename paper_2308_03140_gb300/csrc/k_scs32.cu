@@ -140,9 +140,10 @@ __global__ void k_to_f32(const double *A, long long total, float *B) {
 }
 
 // R = B - A X (FP64, A full row-major, 3 RHS); r32 = (float) R.  A CTA of 8 warps owns 32
-// consecutive rows (4 per warp) and stages X in chunks of 256 rows in shared memory, so X is
-// read from L2 once per 32 rows while A streams from HBM once.
-constexpr int kResRows = 4, kResChunk = 256;
+// consecutive rows (4 per warp) and stages X in chunks of 1024 rows in shared memory, so X is
+// read from L2 once per 32 rows while A streams from HBM once; the column loop is unrolled so
+// that each lane keeps 16 loads of A in flight.
+constexpr int kResRows = 4, kResChunk = 1024;
 __global__ void __launch_bounds__(256) k_residual3(const double *A, long long ld, long long mstride, const double *Bv,
                                                    const double *X, long long xstride, float *r32, int n) {
     __shared__ double xs[kResChunk * 3];
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(256) k_residual3(const double *A, long long ld
         __syncthreads();
         for (int e = threadIdx.x; e < 3 * m; e += 256) xs[e] = x[3LL * c0 + e];
         __syncthreads();
+#pragma unroll 4
         for (int c = lane; c < m; c += 32) {
             const double x0 = xs[3 * c], x1 = xs[3 * c + 1], x2 = xs[3 * c + 2];
 #pragma unroll

@@ -130,12 +130,43 @@ __device__ __forceinline__ void store_part(void *base, long long off, const uint
         static_cast<unsigned short *>(base)[off] = static_cast<unsigned short>(w[j >> 1] >> (16 * (j & 1)));
 }
 
-__device__ __forceinline__ void tri_index(int bid, int &r, int &c) {
-    int x = static_cast<int>((sqrt(8.0 * bid + 1.0) - 1.0) * 0.5);
-    while ((x + 1) * (x + 2) / 2 <= bid) ++x;
-    while (x * (x + 1) / 2 > bid) --x;
-    r = x;
-    c = bid - x * (x + 1) / 2;
+// Tile of CTA `bid` in a grouped order, so that the CTAs resident at one time share operand
+// panels in L2.  mode 0 (tiles_m x tiles_n tiles): groups of kGroup tile rows, walked column
+// by column inside a group.  mode 2 (upper triangle tm <= tn of a square T x T grid): kGroup x
+// kGroup super-tiles of the triangle taken in order, column-major inside each.
+constexpr int kGroup = 8;
+__device__ __forceinline__ void grouped_tile(int bid, int mode, int tiles_m, int tiles_n, int &tm, int &tn) {
+    if (mode == 0) {
+        const int per_group = kGroup * tiles_n;
+        const int g = bid / per_group, first = g * kGroup;
+        const int rows = min(kGroup, tiles_m - first), local = bid - g * per_group;
+        tm = first + local % rows;
+        tn = local / rows;
+        return;
+    }
+    const int T = tiles_n, S = (T + kGroup - 1) / kGroup;
+    int left = bid;
+    for (int R = 0; R < S; ++R) {        // super column of tn
+        const int nr = min(kGroup, T - R * kGroup);
+        for (int C = 0; C <= R; ++C) {   // super row of tm
+            const int nc = min(kGroup, T - C * kGroup);
+            const int cnt = (C == R) ? nc * (nc + 1) / 2 : nc * nr;
+            if (left < cnt) {
+                if (C == R) {            // triangle of the diagonal super-tile: local c <= r
+                    int r = 0;
+                    while ((r + 1) * (r + 2) / 2 <= left) ++r;
+                    tn = R * kGroup + r;
+                    tm = C * kGroup + (left - r * (r + 1) / 2);
+                } else {
+                    tm = C * kGroup + left % nc;
+                    tn = R * kGroup + left / nc;
+                }
+                return;
+            }
+            left -= cnt;
+        }
+    }
+    tm = tn = 0;   // not reached for bid < T (T + 1) / 2
 }
 
 template <int KIND>   // 0: TF32 single product; 1: BF16x3; 2: TF32x3
@@ -166,15 +197,7 @@ __global__ void __launch_bounds__(192, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     int tm, tn;
-    if (g.mode == 0) {
-        tm = blockIdx.x / tiles_n;
-        tn = blockIdx.x % tiles_n;
-    } else {
-        int r, c;
-        tri_index(blockIdx.x, r, c);
-        tm = c;
-        tn = r;
-    }
+    grouped_tile(static_cast<int>(blockIdx.x), g.mode, g.M / TM, tiles_n, tm, tn);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {

@@ -23,7 +23,7 @@ using namespace mbdgb;
 
 namespace {
 std::atomic<long long> g_launches{0};
-constexpr int kRefineSteps = 3;   // iterative-refinement steps of the mixed screening solves
+constexpr int kRefineSteps = 2;   // refinement steps of the mixed screening solves (error x ~kappa eps32 each)
 constexpr int kLanczosSteps = 48; // Lanczos steps of the spectrum estimate of Q
 constexpr int kLF = MBD_LEARNED_FEATURES;   // inputs of the learned screening model
 }  // namespace
