@@ -49,6 +49,11 @@ struct TcArgs {
     int *err;
     double *C64 = nullptr;   // optional FP64 output accumulated in place: C64 += result
     int chunk_stages = 0;    // K stages per TMEM accumulation (0: all of K in one)
+    // Batch of independent products (blockIdx.y): A and B stacked as [batch][M][lda] and
+    // [batch][N][ldb]; D and C of item b at D + b sC, C + b sC.  batch > 1 allows no other
+    // output than C.
+    int batch = 1;
+    long long sC = 0;
 };
 cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_t s);
 // Mixed-precision helpers: Y = scale Q (FP32 and, if Yh, bf16 hi/lo) and Z = I;
@@ -63,6 +68,11 @@ void to_f64(const float *Zf, long long ld, double scale, double *Zd, cudaStream_
 // the diagonal optionally set to zero; Out = scale diag(A) B in FP64.
 void split_tf32_f64(const double *Q, long long ld, double scale, int zero_diag, void *H, void *L, cudaStream_t s);
 void split_tf32_f32(const float *Z, long long ld, int zero_diag, void *H, void *L, cudaStream_t s);
+// TF32x3 parts (hi = tf32(a), lo = tf32(a - hi)) of a rows x cols panel of each FP32 matrix
+// of a batch (A at the panel's first element, row pitch ld, matrices mstride apart) into H
+// and L, each stacked [batch][rows][cols].
+void split_panel_tf32(const float *A, long long ld, long long mstride, int batch, long long rows, int cols,
+                      uint32_t *H, uint32_t *L, cudaStream_t s);
 void diag_scale_rows_f64(const double *A, const float *B, long long ld, double scale, double *Out, cudaStream_t s);
 void diag_scale_rows_f32(const float *A, const double *B, long long ld, double *Out, cudaStream_t s);
 void split_tf32_f64_t(const double *A, long long ld, double scale, void *H, void *L, cudaStream_t s);   // of A^T
@@ -115,8 +125,15 @@ void trsv_blocked(const T *L, long long ld, long long mstride, int batch, const 
 // Cholesky with FP32 diagonal-block inverses; then X = A^{-1} B by FP32 solves and
 // `steps` iterative-refinement steps with residuals from the FP64 matrix (full, both
 // triangles; rows >= n are padding).  work: 2 * batch * 3 ld floats.
-void cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv, int *status,
-                           cudaStream_t s);
+// The factorisation is blocked in panels of 256 columns (the first panel takes ld mod 256
+// when that is not 0, so every trailing matrix is a multiple of 128): inside a panel 64-wide
+// steps on the SIMT cores, the trailing update A22 -= L21 L21^T on the tensor cores
+// (TF32x3, k_tc_gemm).  panel: scratch of 2 * batch * ld * 256 32-bit words.  A32 must
+// start symmetric (both triangles): the tensor-core update reads the upper triangle of
+// A22 and writes both.  Tensor-core timeouts set ST_TC_TIMEOUT in *status; a launch error
+// is returned.
+cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv,
+                                  uint32_t *panel, int *status, cudaStream_t s);
 void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,
                    const double *B, double *X, float *work, int steps, cudaStream_t s);
 

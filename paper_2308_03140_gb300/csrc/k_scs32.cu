@@ -3,7 +3,7 @@
 // FP32 rate of this part is about 70x its FP64 rate), and A X = B is solved by iterative
 // refinement: X <- X + A32^{-1} (B - A X), with the residual formed from the FP64
 // matrix.  For the moderately conditioned screening matrices (cond ~ 1e2 - 1e3) each
-// step gains about four digits; three steps reach FP64 accuracy.
+// step gains about four digits; two steps reach FP64 accuracy.
 //
 // Layout as in k_dense.cu: batch of row-major ld x ld matrices, ld a multiple of 64,
 // right-hand sides [batch][ld][3].
@@ -219,24 +219,49 @@ void chol_solve3_f32(const float *L, long long ld, long long mstride, int batch,
 
 }  // namespace
 
-void cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv, int *status,
-                           cudaStream_t s) {
-    const long long mstride = ld * ld;
+cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv,
+                                  uint32_t *panel, int *status, cudaStream_t s) {
+    const long long mstride = ld * ld, dstride = (ld / T64) * 4096;
     count_launches(1);
     k_to_f32<<<gridn(mstride * batch), 256, 0, s>>>(A64, mstride * batch, A32);
-    const int nb = static_cast<int>(ld / T64);
-    for (int k = 0; k < nb; ++k) {
-        const long long k0 = static_cast<long long>(k) * T64;
-        count_launches(1);
-        k_spotrf_diag<<<batch, 256, 0, s>>>(A32 + k0 * ld + k0, ld, mstride, dinv + k * 4096LL,
-                                            static_cast<long long>(nb) * 4096, status);
-        const int rem = static_cast<int>(ld - k0 - T64);
-        if (rem <= 0) continue;
-        float *A21 = A32 + (k0 + T64) * ld + k0, *A22 = A32 + (k0 + T64) * ld + k0 + T64;
-        sgemm_nt(A21, dinv + k * 4096LL, A21, ld, 64, ld, mstride, static_cast<long long>(nb) * 4096, mstride, rem,
-                 64, 64, batch, 1.f, 0.f, 0, s);
-        sgemm_nt(A21, A21, A22, ld, ld, ld, mstride, mstride, mstride, rem, rem, 64, batch, -1.f, 1.f, 1, s);
+    constexpr int kPanel = 256;
+    const int first = static_cast<int>(ld % kPanel) ? static_cast<int>(ld % kPanel) : kPanel;
+    for (long long p0 = 0; p0 < ld;) {
+        const int pw = p0 == 0 ? first : kPanel;   // panel columns [p0, p0 + pw)
+        // right-looking 64-wide steps restricted to the panel's columns
+        for (long long k0 = p0; k0 < p0 + pw; k0 += T64) {
+            const int k = static_cast<int>(k0 / T64);
+            count_launches(1);
+            k_spotrf_diag<<<batch, 256, 0, s>>>(A32 + k0 * ld + k0, ld, mstride, dinv + k * 4096LL, dstride, status);
+            const int rem = static_cast<int>(ld - k0 - T64);   // rows below the diagonal block
+            if (rem <= 0) continue;
+            float *A21 = A32 + (k0 + T64) * ld + k0;
+            sgemm_nt(A21, dinv + k * 4096LL, A21, ld, 64, ld, mstride, dstride, mstride, rem, 64, 64, batch, 1.f, 0.f,
+                     0, s);
+            const int w = static_cast<int>(p0 + pw - k0 - T64);   // panel columns right of the block
+            if (w > 0)
+                sgemm_nt(A21, A21, A21 + T64, ld, ld, ld, mstride, mstride, mstride, rem, w, 64, batch, -1.f, 1.f, 0,
+                         s);
+        }
+        const long long t0 = p0 + pw, rem = ld - t0;   // trailing matrix [t0, ld)^2
+        if (rem > 0) {
+            // A22 -= L21 L21^T with L21 = A[t0:, p0:t0] as TF32x3 parts on the tensor cores;
+            // the upper tiles of A22 are computed and mirrored
+            uint32_t *H = panel, *L = panel + static_cast<long long>(batch) * rem * pw;
+            split_panel_tf32(A32 + t0 * ld + p0, ld, mstride, batch, rem, pw, H, L, s);
+            float *A22 = A32 + t0 * ld + t0;
+            TcOperands op{H, L, H, L, pw, pw};
+            TcArgs g{static_cast<int>(rem), static_cast<int>(rem), pw, -1.f, 1.f, A22, ld, A22, nullptr, nullptr,
+                     nullptr, nullptr, nullptr, nullptr, 0, 2, status};
+            g.chunk_stages = 2;
+            g.batch = batch;
+            g.sC = mstride;
+            const cudaError_t e = tc_gemm(2, op, g, s);
+            if (e != cudaSuccess) return e;
+        }
+        p0 += pw;
     }
+    return cudaGetLastError();
 }
 
 void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,

@@ -198,6 +198,9 @@ __global__ void __launch_bounds__(192, 1)
 
     int tm, tn;
     grouped_tile(static_cast<int>(blockIdx.x), g.mode, g.M / TM, tiles_n, tm, tn);
+    const int bz = blockIdx.y;   // item of a batched product (0 otherwise)
+    const float *Dp = g.D ? g.D + bz * g.sC : nullptr;
+    float *Cp = g.C ? g.C + bz * g.sC : nullptr;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -241,11 +244,12 @@ __global__ void __launch_bounds__(192, 1)
                 uint8_t *st = smem + s * Cfg::STAGE_BYTES;
                 mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
                 const int kx = kt * KELEM;
-                tma_load_2d(st, &mA0, kx, tm * TM, &full[s]);
-                tma_load_2d(st + TILE_BYTES, &mB0, kx, tn * TN, &full[s]);
+                const int ya = bz * g.M + tm * TM, yb = bz * g.N + tn * TN;
+                tma_load_2d(st, &mA0, kx, ya, &full[s]);
+                tma_load_2d(st + TILE_BYTES, &mB0, kx, yb, &full[s]);
                 if (Cfg::TILES == 4) {
-                    tma_load_2d(st + 2 * TILE_BYTES, &mA1, kx, tm * TM, &full[s]);
-                    tma_load_2d(st + 3 * TILE_BYTES, &mB1, kx, tn * TN, &full[s]);
+                    tma_load_2d(st + 2 * TILE_BYTES, &mA1, kx, ya, &full[s]);
+                    tma_load_2d(st + 3 * TILE_BYTES, &mB1, kx, yb, &full[s]);
                 }
                 issued = kt + 1;
             }
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = g.alpha * acc[c0 + j];
                 if (g.beta != 0.f) {
-                    const float4 *dp = reinterpret_cast<const float4 *>(g.D + m * g.ld + n0);
+                    const float4 *dp = reinterpret_cast<const float4 *>(Dp + m * g.ld + n0);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const float4 d = dp[q];
@@ -385,8 +389,8 @@ __global__ void __launch_bounds__(192, 1)
                 // diagonal tiles keep their upper triangle and mirror it, so the result is
                 // exactly symmetric whatever order the tensor cores summed in.
                 if (!diag) {
-                    if (g.C) {
-                        float4 *cp = reinterpret_cast<float4 *>(g.C + m * g.ld + n0);
+                    if (Cp) {
+                        float4 *cp = reinterpret_cast<float4 *>(Cp + m * g.ld + n0);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                     }
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(192, 1)
                     for (int j = 0; j < 16; ++j) {
                         if (n0 + j < m) continue;
                         const long long off = m * g.ld + n0 + j;
-                        if (g.C) g.C[off] = v[j];
+                        if (Cp) Cp[off] = v[j];
                         if (g.Ch) {
                             store_part<KIND>(g.Ch, off, hw, j);
                             store_part<KIND>(g.Cl, off, lw, j);
@@ -415,7 +419,7 @@ __global__ void __launch_bounds__(192, 1)
                 // transposed copies (coalesced across the warp: consecutive rows m).  For a
                 // mirrored tile of a symmetric product the transpose goes into C itself.
                 const bool into_c = mirror || diag;
-                float *Tf = into_c ? g.C : g.CT;
+                float *Tf = into_c ? Cp : g.CT;
                 void *Th = into_c ? g.Ch : g.CTh, *Tl = into_c ? g.Cl : g.CTl;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -487,10 +491,11 @@ cudaError_t launch_tc(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     }
     CUtensorMap a0, a1, b0, b1;
     const long long lda = op.lda, ldb = op.ldb;
-    if (!make_map(&a0, op.A0, KIND, g.M, g.K, lda) || !make_map(&b0, op.B0, KIND, g.N, g.K, ldb))
+    const long long rows_a = static_cast<long long>(g.batch) * g.M, rows_b = static_cast<long long>(g.batch) * g.N;
+    if (!make_map(&a0, op.A0, KIND, rows_a, g.K, lda) || !make_map(&b0, op.B0, KIND, rows_b, g.K, ldb))
         return cudaErrorInvalidValue;
     if (KIND != 0) {
-        if (!make_map(&a1, op.A1, KIND, g.M, g.K, lda) || !make_map(&b1, op.B1, KIND, g.N, g.K, ldb))
+        if (!make_map(&a1, op.A1, KIND, rows_a, g.K, lda) || !make_map(&b1, op.B1, KIND, rows_b, g.K, ldb))
             return cudaErrorInvalidValue;
     } else {
         a1 = a0;
@@ -499,7 +504,7 @@ cudaError_t launch_tc(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     const int tmt = g.M / TM, tnt = g.N / TN;
     const int grid = g.mode == 0 ? tmt * tnt : tmt * (tmt + 1) / 2;
     count_launches(1);
-    k_tc_gemm<KIND><<<grid, 192, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt);
+    k_tc_gemm<KIND><<<dim3(grid, g.batch), 192, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt);
     return cudaGetLastError();
 }
 
@@ -510,7 +515,8 @@ cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_
         (g.mode == 2 && (g.M != g.N || g.CT || g.CTh || g.resid)) || ((g.CT || g.CTh) && g.M != g.N) ||
         g.ld % 8 || op.lda % 8 || op.ldb % 8 ||
         !g.err || (g.beta != 0.f && !g.D) || (g.Ch && !g.Cl) || (g.CTh && !g.CTl) || kind < 0 || kind > 2 ||
-        (kind != 0 && (!op.A1 || !op.B1)) || (kind == 0 && (g.Ch || g.CTh)))
+        (kind != 0 && (!op.A1 || !op.B1)) || (kind == 0 && (g.Ch || g.CTh)) || g.batch < 1 || g.batch > 65535 ||
+        (g.batch > 1 && (g.Ch || g.CT || g.CTh || g.C64 || g.resid || g.sC < static_cast<long long>(g.M) * g.ld)))
         return cudaErrorInvalidValue;
     if (kind == 0) return launch_tc<0>(op, g, s);
     if (kind == 1) return launch_tc<1>(op, g, s);
@@ -577,6 +583,19 @@ __global__ void k_split_tf32_f32(const float *Z, long long total, long long ld, 
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x)
         split_store(2, (zero_diag && e / ld == e % ld) ? 0.f : Z[e], H, L, e);
+}
+
+// TF32x3 parts of a rows x cols panel of each matrix of a batch (A points at the panel's
+// first element, row pitch ld, matrices mstride apart) into H, L stacked as
+// [batch][rows][cols].
+__global__ void k_split_panel_tf32(const float *A, long long ld, long long mstride, long long rows, int cols,
+                                   long long total, uint32_t *H, uint32_t *L) {
+    const long long per = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long b = e / per, r = e - b * per, i = r / cols, c = r - i * cols;
+        split_store(2, A[b * mstride + i * ld + c], H, L, e);
+    }
 }
 
 // Out[p][q] = scale * A[p][p] * B[p][q] (row scaling by a diagonal, FP64).
@@ -782,6 +801,13 @@ void split_tf32_f32(const float *Z, long long ld, int zero_diag, void *H, void *
     count_launches(1);
     k_split_tf32_f32<<<grid_for(ld * ld), 256, 0, s>>>(Z, ld * ld, ld, zero_diag, static_cast<uint32_t *>(H),
                                                        static_cast<uint32_t *>(L));
+}
+
+void split_panel_tf32(const float *A, long long ld, long long mstride, int batch, long long rows, int cols,
+                      uint32_t *H, uint32_t *L, cudaStream_t s) {
+    const long long total = static_cast<long long>(batch) * rows * cols;
+    count_launches(1);
+    k_split_panel_tf32<<<grid_for(total), 256, 0, s>>>(A, ld, mstride, rows, cols, total, H, L);
 }
 
 void energy_correction(const double *Q, double scale, const float *Z, const double *V, const double *W, long long ld,

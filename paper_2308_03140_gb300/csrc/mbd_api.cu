@@ -127,6 +127,7 @@ struct mbd_ctx {
     double *da0, *dom, *drv, *dalu, *dsigu, *dabar, *dabar0, *dc6bar, *dombar, *drbar, *du, *dwu;
     double *dM, *ddinv, *dX, *dV, *dB;
     float *sM = nullptr, *sdinv = nullptr, *swork = nullptr;   // FP32 factors of the mixed modes
+    uint32_t *spanel = nullptr;   // TF32x3 parts of the factor panels (tensor-core trailing updates)
     double *dQ, *dZ, *dP, *dY2, *dZ2;
     // mixed-precision Newton-Schulz buffers (ld x ld each)
     float *fY = nullptr, *fZ = nullptr, *fY2 = nullptr, *fZ2 = nullptr, *fP = nullptr, *fPT = nullptr;
@@ -323,8 +324,10 @@ int allocate(mbd_ctx *ctx) {
     if (prec != MBD_PREC_FP64) bytes += 6 * mat32;
     bytes += 12 * split_mat;
     // FP32 screening factors, their diagonal-block inverses and solve workspace
+    const size_t panel_words = 2 * nf1 * static_cast<size_t>(ld) * 256;
     const size_t scs32 = prec != MBD_PREC_FP64
-                             ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * 2 * nf1 * ld * 3)
+                             ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * 2 * nf1 * ld * 3) +
+                                   al(sizeof(uint32_t) * panel_words)
                              : 0;
     bytes += scs32;
     // A slab large enough for the new size is re-carved in place (systems of varying size in
@@ -372,6 +375,8 @@ int allocate(mbd_ctx *ctx) {
         p += al(sizeof(float) * nf1 * nb * 4096);
         ctx->swork = reinterpret_cast<float *>(p);
         p += al(sizeof(float) * 2 * nf1 * ld * 3);
+        ctx->spanel = reinterpret_cast<uint32_t *>(p);
+        p += al(sizeof(uint32_t) * panel_words);
     }
     // Untouched parts of the factor buffers (strict upper triangles) are read by no
     // kernel; clearing them once keeps them finite.
@@ -927,7 +932,8 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
             init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
             chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
         } else {   // FP32 factors, FP64-refined solutions
-            cholesky_f32_from_f64(ctx->dM, ctx->sM, ld, nf1, ctx->sdinv, ctx->dstatus, s);
+            MBD_CUDA(cholesky_f32_from_f64(ctx->dM, ctx->sM, ld, nf1, ctx->sdinv, ctx->spanel, ctx->dstatus, s),
+                     "screening");
             init_rhs_identity(ctx->dB, ld, n, nf1, xs, s);
             refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, n, nf1, ctx->dB, ctx->dX, ctx->swork, kRefineSteps, s);
         }
@@ -1386,7 +1392,8 @@ int mbd_screen(mbd_ctx *ctx, double *alpha_iu, double *alpha_free_iu, double *c6
         init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
         chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
     } else {
-        cholesky_f32_from_f64(ctx->dM, ctx->sM, ld, nf1, ctx->sdinv, ctx->dstatus, s);
+        MBD_CUDA(cholesky_f32_from_f64(ctx->dM, ctx->sM, ld, nf1, ctx->sdinv, ctx->spanel, ctx->dstatus, s),
+                 "mbd_screen");
         init_rhs_identity(ctx->dB, ld, n, nf1, xs, s);
         refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, n, nf1, ctx->dB, ctx->dX, ctx->swork, kRefineSteps, s);
     }

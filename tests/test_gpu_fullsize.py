@@ -110,10 +110,13 @@ def test_finite2000_fp64_energy_and_screening(finite_ref):
 
 
 def test_finite2000_tf32x3_energy_and_forces(finite_ref):
-    s, E_ref, _ = finite_ref
+    s, E_ref, ab = finite_ref
     m, E, gR, gp = gpu(s, binding.MBD_PREC_TF32X3)
+    ab_tc = m.scs_detail()["alpha_bar"]
     m.close()
     assert abs(E - E_ref) / s.n_atoms <= 1e-7, (E, E_ref)
+    # FP32 factorization refined twice against the FP64 screening matrices
+    assert np.allclose(ab_tc, ab, rtol=1e-10, atol=0)
     m64, E64, gR64, _ = gpu(s)
     m64.close()
     # forces of the mixed mode come from the Newton-Schulz Z of the tensor-core iteration
