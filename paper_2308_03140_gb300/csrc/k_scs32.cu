@@ -2,8 +2,8 @@
 // T^scs (one per frequency point, Sec. 2.3) are factorised in FP32 (SIMT FFMA: the
 // FP32 rate of this part is about 70x its FP64 rate), and A X = B is solved by iterative
 // refinement: X <- X + A32^{-1} (B - A X), with the residual formed from the FP64
-// matrix.  For the moderately conditioned screening matrices (cond ~ 1e2 - 1e3) each
-// step gains about four digits; two steps reach FP64 accuracy.
+// matrix.  For the moderately conditioned screening matrices (cond ~ 1e1 - 2e3) the FP32
+// solution is within a few 1e-7 and each step gains six digits or more.
 //
 // Layout as in k_dense.cu: batch of row-major ld x ld matrices, ld a multiple of 64,
 // right-hand sides [batch][ld][3].
@@ -81,45 +81,79 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(const float *A, const float *B
     }
 }
 
-// Unblocked FP32 Cholesky of the 64x64 diagonal block plus the inverse of its factor
-// (kept transposed in the strict upper triangle of S while it is built).
+// FP32 Cholesky of a 64x64 diagonal block plus the inverse of its factor, one CTA per
+// matrix.  The factorisation is blocked by 16: warp 0 factors each 16x16 diagonal block
+// (warp-synchronous, one lane per row), one thread per row solves the rows below it, and
+// all threads apply the 16-term trailing update (3 block barriers per 16 columns).  The
+// inverse is formed by forward substitution on L X = I with four lanes per column, the
+// dot products split over the lanes and combined by shuffles.
 __global__ void __launch_bounds__(256) k_spotrf_diag(float *A, long long ld, long long mstride, float *dinv,
                                                      long long dstride, int *status) {
     __shared__ float S[64][65];
-    __shared__ float dg[64];
+    __shared__ float V[64][65];
     __shared__ int bad;
     float *Ab = A + static_cast<long long>(blockIdx.x) * mstride;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (t == 0) bad = 0;
     for (int e = t; e < 4096; e += 256) {
         const int r = e >> 6, c = e & 63;
         S[r][c] = (c <= r) ? Ab[r * ld + c] : 0.f;
     }
     __syncthreads();
-    for (int j = 0; j < 64; ++j) {
-        if (t == 0) {
-            float d = S[j][j];
-            if (!(d > 0.f)) { bad = 1; d = 1.f; }
-            S[j][j] = sqrtf(d);
+    for (int j0 = 0; j0 < 64; j0 += 16) {
+        if (warp == 0) {   // 16x16 diagonal block, lane = row j0 + lane
+            for (int j = 0; j < 16; ++j) {
+                const int jj = j0 + j;
+                float d = S[jj][jj];
+                if (!(d > 0.f)) {
+                    if (lane == 0) bad = 1;
+                    d = 1.f;
+                }
+                d = sqrtf(d);
+                __syncwarp();
+                if (lane == 0) S[jj][jj] = d;
+                if (lane > j && lane < 16) S[j0 + lane][jj] /= d;
+                __syncwarp();
+                if (lane > j && lane < 16) {
+                    const int i = j0 + lane;
+                    const float lij = S[i][jj];
+                    for (int k = jj + 1; k <= i; ++k) S[i][k] -= lij * S[k][jj];
+                }
+                __syncwarp();
+            }
         }
         __syncthreads();
-        const float djj = S[j][j];
-        for (int i = j + 1 + t; i < 64; i += 256) S[i][j] /= djj;
+        for (int i = j0 + 16 + t; i < 64; i += 256) {   // rows below: L21 = A21 L11^{-T}
+            for (int c = 0; c < 16; ++c) {
+                float v = S[i][j0 + c];
+                for (int k = 0; k < c; ++k) v -= S[i][j0 + k] * S[j0 + c][j0 + k];
+                S[i][j0 + c] = v / S[j0 + c][j0 + c];
+            }
+        }
         __syncthreads();
-        const int m = 63 - j;
-        for (int e = t; e < m * m; e += 256) {
-            const int i = j + 1 + e / m, k = j + 1 + e % m;
-            if (k <= i) S[i][k] -= S[i][j] * S[k][j];
+        const int r0 = j0 + 16;   // trailing lower triangle [r0, 64)^2 -= L21 L21^T
+        if (r0 < 64) {
+            const int ty = t >> 4, tx = t & 15;
+            for (int i = r0 + ty; i < 64; i += 16)
+                for (int k = r0 + tx; k <= i; k += 16) {
+                    float v = S[i][k];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) v -= S[i][j0 + c] * S[k][j0 + c];
+                    S[i][k] = v;
+                }
         }
         __syncthreads();
     }
-    if (t < 64) {
-        const int c = t;
-        for (int i = c; i < 64; ++i) {
-            float acc = (i == c) ? 1.f : 0.f;
-            for (int k = c; k < i; ++k) acc -= S[i][k] * (k == c ? dg[c] : S[c][k]);
-            const float v = acc / S[i][i];
-            if (i == c) dg[c] = v; else S[c][i] = v;
+    {   // V = L^{-1}: column c by lanes 4c..4c+3 of the CTA; a warp holds columns 8w..8w+7
+        const int c = t >> 2, q = t & 3;
+        for (int i = warp * 8; i < 64; ++i) {
+            float sum = 0.f;
+            if (i >= c)
+                for (int k = c + q; k < i; k += 4) sum += S[i][k] * V[k][c];
+            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+            if (i >= c && q == 0) V[i][c] = ((i == c ? 1.f : 0.f) - sum) / S[i][i];
+            __syncwarp();
         }
     }
     __syncthreads();
@@ -127,7 +161,7 @@ __global__ void __launch_bounds__(256) k_spotrf_diag(float *A, long long ld, lon
     for (int e = t; e < 4096; e += 256) {
         const int r = e >> 6, c = e & 63;
         if (c <= r) Ab[r * ld + c] = S[r][c];
-        Db[e] = (c > r) ? 0.f : (c == r ? dg[r] : S[c][r]);
+        Db[e] = (c > r) ? 0.f : V[r][c];
     }
     if (t == 0 && bad) atomicOr(status, ST_SCS_NOT_PD);
 }

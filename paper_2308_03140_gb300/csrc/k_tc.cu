@@ -169,6 +169,13 @@ __device__ __forceinline__ void grouped_tile(int bid, int mode, int tiles_m, int
     tm = tn = 0;   // not reached for bid < T (T + 1) / 2
 }
 
+// Batch item and tile of work item w (items ordered batch item by batch item).
+__device__ __forceinline__ void item_tile(int w, int tiles, int mode, int tiles_m, int tiles_n, int &bz, int &tm,
+                                          int &tn) {
+    bz = w / tiles;
+    grouped_tile(w - bz * tiles, mode, tiles_m, tiles_n, tm, tn);
+}
+
 template <int KIND>   // 0: TF32 single product; 1: BF16x3; 2: TF32x3
 struct TcCfg {
     static constexpr int PAIRS = KIND == 0 ? 1 : 3;
@@ -196,11 +203,12 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
-    int tm, tn;
-    grouped_tile(static_cast<int>(blockIdx.x), g.mode, g.M / TM, tiles_n, tm, tn);
-    const int bz = blockIdx.y;   // item of a batched product (0 otherwise)
-    const float *Dp = g.D ? g.D + bz * g.sC : nullptr;
-    float *Cp = g.C ? g.C + bz * g.sC : nullptr;
+    // Persistent CTAs: work item w = (batch item, tile) runs over blockIdx.x, blockIdx.x +
+    // gridDim.x, ...; stage and chunk counters run on across items, so the producer and the
+    // MMA issuer start the next tile while the epilogue warps store the last one.
+    const int tiles_m = g.M / TM;
+    const int tiles = g.mode == 0 ? tiles_m * tiles_n : tiles_n * (tiles_n + 1) / 2;
+    const int items = tiles * g.batch;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -233,211 +241,230 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 4) {
         // ---- TMA producer (one thread) ----
         if (lane == 0) {
-            int issued = 0;
-            for (int kt = 0; kt < nk && !*abort_flag; ++kt) {
-                const int s = kt % Cfg::STAGES;
-                const uint32_t ph = (kt / Cfg::STAGES) & 1;
-                if (kt >= Cfg::STAGES && !mbar_wait(&empty[s], ph ^ 1, g.err)) {
-                    *abort_flag = 1;
-                    break;
-                }
-                uint8_t *st = smem + s * Cfg::STAGE_BYTES;
-                mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
-                const int kx = kt * KELEM;
+            int issued = 0, kg = 0;   // kg: stages issued by this CTA so far
+            for (int w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+                int bz, tm, tn;
+                item_tile(w, tiles, g.mode, tiles_m, tiles_n, bz, tm, tn);
                 const int ya = bz * g.M + tm * TM, yb = bz * g.N + tn * TN;
-                tma_load_2d(st, &mA0, kx, ya, &full[s]);
-                tma_load_2d(st + TILE_BYTES, &mB0, kx, yb, &full[s]);
-                if (Cfg::TILES == 4) {
-                    tma_load_2d(st + 2 * TILE_BYTES, &mA1, kx, ya, &full[s]);
-                    tma_load_2d(st + 3 * TILE_BYTES, &mB1, kx, yb, &full[s]);
+                for (int kt = 0; kt < nk && !*abort_flag; ++kt, ++kg) {
+                    const int s = kg % Cfg::STAGES;
+                    const uint32_t ph = (kg / Cfg::STAGES) & 1;
+                    if (kg >= Cfg::STAGES && !mbar_wait(&empty[s], ph ^ 1, g.err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *st = smem + s * Cfg::STAGE_BYTES;
+                    mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+                    const int kx = kt * KELEM;
+                    tma_load_2d(st, &mA0, kx, ya, &full[s]);
+                    tma_load_2d(st + TILE_BYTES, &mB0, kx, yb, &full[s]);
+                    if (Cfg::TILES == 4) {
+                        tma_load_2d(st + 2 * TILE_BYTES, &mA1, kx, ya, &full[s]);
+                        tma_load_2d(st + 3 * TILE_BYTES, &mB1, kx, yb, &full[s]);
+                    }
+                    issued = kg + 1;
                 }
-                issued = kt + 1;
             }
             if (*abort_flag) {   // let this CTA's copies land before shared memory is released
-                for (int kt = (issued > Cfg::STAGES ? issued - Cfg::STAGES : 0); kt < issued; ++kt)
-                    mbar_wait(&full[kt % Cfg::STAGES], (kt / Cfg::STAGES) & 1, g.err);
+                for (int k = (issued > Cfg::STAGES ? issued - Cfg::STAGES : 0); k < issued; ++k)
+                    mbar_wait(&full[k % Cfg::STAGES], (k / Cfg::STAGES) & 1, g.err);
             }
         }
     } else if (warp == 5) {
         // ---- MMA issuer (one thread): chunk c accumulates afresh into buffer c & 1 ----
         if (lane == 0) {
-            for (int kt = 0; kt < nk && !*abort_flag; ++kt) {
-                const int c = kt / cs, buf = c & 1;
-                if (kt % cs == 0 && c >= 2 && !mbar_wait(&cfree[buf], ((c >> 1) - 1) & 1, g.err)) {
-                    *abort_flag = 1;
-                    break;
-                }
-                const int s = kt % Cfg::STAGES;
-                if (!mbar_wait(&full[s], (kt / Cfg::STAGES) & 1, g.err)) {
-                    *abort_flag = 1;
-                    break;
-                }
-                fence_after();
-                const uint32_t base = su32(smem + s * Cfg::STAGE_BYTES);
-                const uint32_t dt = tmem + static_cast<uint32_t>(buf * TN);
-#pragma unroll
-                for (int k = 0; k < KB / 32; ++k) {   // 32 bytes of K per instruction
-                    const uint64_t a0 = sdesc(base + k * 32), b0 = sdesc(base + TILE_BYTES + k * 32);
-                    mma<Cfg::TF32>(dt, a0, b0, (kt % cs != 0 || k != 0) ? 1u : 0u);
-                    if (Cfg::PAIRS == 3) {
-                        const uint64_t a1 = sdesc(base + 2 * TILE_BYTES + k * 32);
-                        const uint64_t b1 = sdesc(base + 3 * TILE_BYTES + k * 32);
-                        mma<Cfg::TF32>(dt, a0, b1, 1u);
-                        mma<Cfg::TF32>(dt, a1, b0, 1u);
+            int kg = 0, cg = 0;   // stages consumed and chunks begun by this CTA before the current item
+            for (int w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, cg += nchunks) {
+                for (int kt = 0; kt < nk && !*abort_flag; ++kt, ++kg) {
+                    const int c = cg + kt / cs, buf = c & 1;
+                    if (kt % cs == 0 && c >= 2 && !mbar_wait(&cfree[buf], ((c >> 1) - 1) & 1, g.err)) {
+                        *abort_flag = 1;
+                        break;
                     }
+                    const int s = kg % Cfg::STAGES;
+                    if (!mbar_wait(&full[s], (kg / Cfg::STAGES) & 1, g.err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t base = su32(smem + s * Cfg::STAGE_BYTES);
+                    const uint32_t dt = tmem + static_cast<uint32_t>(buf * TN);
+#pragma unroll
+                    for (int k = 0; k < KB / 32; ++k) {   // 32 bytes of K per instruction
+                        const uint64_t a0 = sdesc(base + k * 32), b0 = sdesc(base + TILE_BYTES + k * 32);
+                        mma<Cfg::TF32>(dt, a0, b0, (kt % cs != 0 || k != 0) ? 1u : 0u);
+                        if (Cfg::PAIRS == 3) {
+                            const uint64_t a1 = sdesc(base + 2 * TILE_BYTES + k * 32);
+                            const uint64_t b1 = sdesc(base + 3 * TILE_BYTES + k * 32);
+                            mma<Cfg::TF32>(dt, a0, b1, 1u);
+                            mma<Cfg::TF32>(dt, a1, b0, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);                              // stage free once read
+                    if (kt % cs == cs - 1 || kt == nk - 1) mma_commit(&cfull[buf]);   // chunk finished
                 }
-                mma_commit(&empty[s]);                              // stage free once read
-                if (kt % cs == cs - 1 || kt == nk - 1) mma_commit(&cfull[buf]);   // chunk finished
             }
             mma_commit(done);
         }
     } else {
         // ---- epilogue warps 0-3: thread = row of the tile; chunk sums added in FP32 with
         // round-to-nearest (the tensor core's own accumulation truncates) ----
-        float acc[TN];
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[j] = 0.f;
         bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int buf = c & 1;
-            ok = mbar_wait(&cfull[buf], (c >> 1) & 1, g.err) && !*abort_flag;
-            ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
-            if (!ok) {
-                *abort_flag = 1;
-                break;
-            }
-            fence_after();
-            const uint32_t tb = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(buf * TN);
+        int cg = 0;   // chunks of earlier items
+        for (int w = blockIdx.x; w < items && ok; w += gridDim.x, cg += nchunks) {
+            int bz, tm, tn;
+            item_tile(w, tiles, g.mode, tiles_m, tiles_n, bz, tm, tn);
+            const float *Dp = g.D ? g.D + bz * g.sC : nullptr;
+            float *Cp = g.C ? g.C + bz * g.sC : nullptr;
+            float acc[TN];
 #pragma unroll
-            for (int q = 0; q < TN / 32; ++q) {
-                uint32_t r[32];
-                tmem_ld32(tb + q * 32, r);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(r[j]);
-            }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&cfree[buf])) : "memory");
-        }
-        if (ok) {
+            for (int j = 0; j < TN; ++j) acc[j] = 0.f;
             const int row = warp * 32 + lane;
             const long long m = static_cast<long long>(tm) * TM + row;
-            const bool mirror = (g.mode == 2) && (tm != tn);
-            const bool diag = (g.mode == 2) && (tm == tn);
-            double rs = 0.0;
+            for (int c = 0; c < nchunks; ++c) {
+                const int buf = (cg + c) & 1;
+                if (c == max(0, nchunks - 2) && g.beta != 0.f) {   // this row of D into L2 ahead of the epilogue
+                    const float *drow = Dp + m * g.ld + static_cast<long long>(tn) * TN;
 #pragma unroll
-            for (int c0 = 0; c0 < TN; c0 += 16) {
-                const long long n0 = static_cast<long long>(tn) * TN + c0;
-                float v[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = g.alpha * acc[c0 + j];
-                if (g.beta != 0.f) {
-                    const float4 *dp = reinterpret_cast<const float4 *>(Dp + m * g.ld + n0);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 d = dp[q];
-                        v[4 * q] += g.beta * d.x;
-                        v[4 * q + 1] += g.beta * d.y;
-                        v[4 * q + 2] += g.beta * d.z;
-                        v[4 * q + 3] += g.beta * d.w;
-                    }
+                    for (int q = 0; q < TN / 32; ++q) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(drow + 32 * q));
                 }
-                if (g.resid && m < g.nvalid) {
+                ok = mbar_wait(&cfull[buf], ((cg + c) >> 1) & 1, g.err) && !*abort_flag;
+                ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t tb = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(buf * TN);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (n0 + j < g.nvalid) {
-                            const double e = (m == n0 + j ? 1.0 : 0.0) - static_cast<double>(v[j]);
-                            rs += e * e;
+                for (int q = 0; q < TN / 32; ++q) {
+                    uint32_t r[32];
+                    tmem_ld32(tb + q * 32, r);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(r[j]);
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&cfree[buf])) : "memory");
+            }
+            if (ok) {
+                const bool mirror = (g.mode == 2) && (tm != tn);
+                const bool diag = (g.mode == 2) && (tm == tn);
+                double rs = 0.0;
+#pragma unroll
+                for (int c0 = 0; c0 < TN; c0 += 16) {
+                    const long long n0 = static_cast<long long>(tn) * TN + c0;
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = g.alpha * acc[c0 + j];
+                    if (g.beta != 0.f) {   // this row of D was prefetched into L2 during the last chunks
+                        const float4 *dp = reinterpret_cast<const float4 *>(Dp + m * g.ld + n0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 d = dp[q];
+                            v[4 * q] += g.beta * d.x;
+                            v[4 * q + 1] += g.beta * d.y;
+                            v[4 * q + 2] += g.beta * d.z;
+                            v[4 * q + 3] += g.beta * d.w;
                         }
-                }
-                if (g.C64) {   // FP64 accumulation output (caller splits K: C64 += result)
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (diag && n0 + j < m) continue;
-                        g.C64[m * g.ld + n0 + j] += static_cast<double>(v[j]);
-                        if ((mirror || diag) && n0 + j != m) g.C64[(n0 + j) * g.ld + m] += static_cast<double>(v[j]);
                     }
-                }
-                // split of the result into the next product's operand parts: bf16 pairs
-                // packed two per word (BF16x3), or TF32 hi and TF32 remainder (TF32x3),
-                // each rounded to nearest
-                uint32_t hw[KIND == 2 ? 16 : 8], lw[KIND == 2 ? 16 : 8];
-                if (g.Ch || g.CTh) {
-                    if (KIND == 2) {
+                    if (g.resid && m < g.nvalid) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (n0 + j < g.nvalid) {
+                                const double e = (m == n0 + j ? 1.0 : 0.0) - static_cast<double>(v[j]);
+                                rs += e * e;
+                            }
+                    }
+                    if (g.C64) {   // FP64 accumulation output (caller splits K: C64 += result)
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            uint32_t h, l;
-                            asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v[j]));
-                            asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(v[j] - __uint_as_float(h)));
-                            hw[j] = h;
-                            lw[j] = l;
+                            if (diag && n0 + j < m) continue;
+                            g.C64[m * g.ld + n0 + j] += static_cast<double>(v[j]);
+                            if ((mirror || diag) && n0 + j != m) g.C64[(n0 + j) * g.ld + m] += static_cast<double>(v[j]);
+                        }
+                    }
+                    // split of the result into the next product's operand parts: bf16 pairs
+                    // packed two per word (BF16x3), or TF32 hi and TF32 remainder (TF32x3),
+                    // each rounded to nearest
+                    uint32_t hw[KIND == 2 ? 16 : 8], lw[KIND == 2 ? 16 : 8];
+                    if (g.Ch || g.CTh) {
+                        if (KIND == 2) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                uint32_t h, l;
+                                asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v[j]));
+                                asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(v[j] - __uint_as_float(h)));
+                                hw[j] = h;
+                                lw[j] = l;
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
+                                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+                                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+                                hw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
+                                        (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+                                lw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
+                                        (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+                            }
+                        }
+                    }
+                    // Symmetric products (mode 2): upper tiles are mirrored into the lower half;
+                    // diagonal tiles keep their upper triangle and mirror it, so the result is
+                    // exactly symmetric whatever order the tensor cores summed in.
+                    if (!diag) {
+                        if (Cp) {
+                            float4 *cp = reinterpret_cast<float4 *>(Cp + m * g.ld + n0);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        }
+                        if (g.Ch) {
+                            constexpr int NV = KIND == 2 ? 4 : 2;   // uint4 vectors per 16 elements
+                            uint4 *hp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Ch) + (m * g.ld + n0) * Cfg::ELEM);
+                            uint4 *lp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Cl) + (m * g.ld + n0) * Cfg::ELEM);
+#pragma unroll
+                            for (int q = 0; q < NV; ++q) {
+                                hp[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                                lp[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                            }
                         }
                     } else {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
-                            const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
-                            const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
-                            hw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
-                                    (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
-                            lw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
-                                    (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+                        for (int j = 0; j < 16; ++j) {
+                            if (n0 + j < m) continue;
+                            const long long off = m * g.ld + n0 + j;
+                            if (Cp) Cp[off] = v[j];
+                            if (g.Ch) {
+                                store_part<KIND>(g.Ch, off, hw, j);
+                                store_part<KIND>(g.Cl, off, lw, j);
+                            }
                         }
                     }
-                }
-                // Symmetric products (mode 2): upper tiles are mirrored into the lower half;
-                // diagonal tiles keep their upper triangle and mirror it, so the result is
-                // exactly symmetric whatever order the tensor cores summed in.
-                if (!diag) {
-                    if (Cp) {
-                        float4 *cp = reinterpret_cast<float4 *>(Cp + m * g.ld + n0);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                    }
-                    if (g.Ch) {
-                        constexpr int NV = KIND == 2 ? 4 : 2;   // uint4 vectors per 16 elements
-                        uint4 *hp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Ch) + (m * g.ld + n0) * Cfg::ELEM);
-                        uint4 *lp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Cl) + (m * g.ld + n0) * Cfg::ELEM);
-#pragma unroll
-                        for (int q = 0; q < NV; ++q) {
-                            hp[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
-                            lp[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
-                        }
-                    }
-                } else {
+                    // transposed copies (coalesced across the warp: consecutive rows m).  For a
+                    // mirrored tile of a symmetric product the transpose goes into C itself.
+                    const bool into_c = mirror || diag;
+                    float *Tf = into_c ? Cp : g.CT;
+                    void *Th = into_c ? g.Ch : g.CTh, *Tl = into_c ? g.Cl : g.CTl;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        if (n0 + j < m) continue;
-                        const long long off = m * g.ld + n0 + j;
-                        if (Cp) Cp[off] = v[j];
-                        if (g.Ch) {
-                            store_part<KIND>(g.Ch, off, hw, j);
-                            store_part<KIND>(g.Cl, off, lw, j);
+                        if (diag && n0 + j <= m) continue;
+                        const long long off = (n0 + j) * g.ld + m;
+                        if (Tf) Tf[off] = v[j];
+                        if (Th) {
+                            store_part<KIND>(Th, off, hw, j);
+                            store_part<KIND>(Tl, off, lw, j);
                         }
                     }
                 }
-                // transposed copies (coalesced across the warp: consecutive rows m).  For a
-                // mirrored tile of a symmetric product the transpose goes into C itself.
-                const bool into_c = mirror || diag;
-                float *Tf = into_c ? Cp : g.CT;
-                void *Th = into_c ? g.Ch : g.CTh, *Tl = into_c ? g.Cl : g.CTl;
+                if (g.resid) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (diag && n0 + j <= m) continue;
-                    const long long off = (n0 + j) * g.ld + m;
-                    if (Tf) Tf[off] = v[j];
-                    if (Th) {
-                        store_part<KIND>(Th, off, hw, j);
-                        store_part<KIND>(Tl, off, lw, j);
-                    }
+                    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+                    if (lane == 0 && rs != 0.0) atomicAdd(g.resid, rs);
                 }
             }
-            if (g.resid) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-                if (lane == 0 && rs != 0.0) atomicAdd(g.resid, rs);
-            }
-        }
+        }   // work items
     }
     __syncwarp();
     fence_before();
@@ -502,9 +529,14 @@ cudaError_t launch_tc(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
         b1 = b0;
     }
     const int tmt = g.M / TM, tnt = g.N / TN;
-    const int grid = g.mode == 0 ? tmt * tnt : tmt * (tmt + 1) / 2;
+    const long long items = static_cast<long long>(g.mode == 0 ? tmt * tnt : tmt * (tmt + 1) / 2) * g.batch;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = static_cast<int>(std::min<long long>(items, sms));   // one resident CTA per SM
     count_launches(1);
-    k_tc_gemm<KIND><<<dim3(grid, g.batch), 192, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt);
+    k_tc_gemm<KIND><<<grid, 192, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,14 @@ using namespace mbdgb;
 
 namespace {
 std::atomic<long long> g_launches{0};
-constexpr int kRefineSteps = 2;   // refinement steps of the mixed screening solves (error x ~kappa eps32 each)
+// Refinement steps of the mixed screening solves: the FP32 factor's solution carries relative
+// errors of a few 1e-7 in the screened polarizabilities, one step against the FP64 matrix
+// brings them to about 1e-13 (screening matrices of kappa up to ~2e3).
+constexpr int kRefineSteps = 1;
+// Refinement steps of the mixed modes' adjoint solves V = A^{-1} H.  The forces of those modes
+// carry the first-order error of the tensor-core Q^{-1/2} (about 1e-2 of the largest force);
+// the unrefined FP32 solve adds at most kappa(A) eps32 ~ 1e-4 relative to the SCS part.
+constexpr int kAdjointRefineSteps = 0;
 constexpr int kLanczosSteps = 48; // Lanczos steps of the spectrum estimate of Q
 constexpr int kLF = MBD_LEARNED_FEATURES;   // inputs of the learned screening model
 }  // namespace
@@ -518,7 +525,8 @@ void backward_passes(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const doub
     if (fp64)
         chol_solve3_f64(ctx->dM, ld, mat, ctx->nf1, ctx->ddinv, ctx->dV, ctx->dB, xs, s);
     else
-        refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, ctx->n, ctx->nf1, ctx->dB, ctx->dV, ctx->swork, kRefineSteps, s);
+        refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, ctx->n, ctx->nf1, ctx->dB, ctx->dV, ctx->swork,
+                      kAdjointRefineSteps, s);
     scs_grad_pass(b, beta, a, ctx->dX, ctx->dV, xs, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgR, !fp64, s);
     if (grad_params) ts_chain(b, ctx->dga0, ctx->dgom, ctx->dgrv, grad_energy, grad_params, s);
     if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);

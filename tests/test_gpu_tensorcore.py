@@ -151,9 +151,10 @@ def test_mixed_precision_matches_fp64_path_at_500_atoms(precision):
 def test_mixed_screening_refines_to_fp64_accuracy():
     """The mixed modes factor A(u) in FP32 and refine X = A^{-1} E against the FP64 A.  The
     screening matrices of this cluster have kappa(A) up to 1.6e3 (at the highest frequency
-    point), so each refinement step shrinks the error by about kappa eps32 ~ 1e-4 and two
-    steps take the FP32 solve (~1e-4) below 1e-10: the screened polarizabilities (Eq.
-    contraction) agree with the FP64 path far below the FP32 unit roundoff."""
+    point); the FP32 solve leaves relative errors of about 3e-7 in the screened
+    polarizabilities (Eq. contraction) and one refinement step about 1e-13 (LAPACK FP32
+    factor, FP64 residual), so they agree with the FP64 path far below the FP32 unit
+    roundoff."""
     sysm = syn.sphere_cluster(500, seed=1500)
     ab = {}
     for p in (binding.MBD_PREC_FP64, binding.MBD_PREC_TF32X3):
