@@ -42,11 +42,13 @@ FP64_OVER_BF16 = 1.25 / 2250.0
 # (profiles/k_gemm_nn_finite2000.md), valid while k_dense.cu keeps the captured hash.
 GEMM_NN_TRAFFIC = {"bytes": 6.309694e9 + 0.289604352e9, "k_dense_sha16": "b0c1ebaacc02cc34",
                    "source": "profiles/k_gemm_nn_finite2000.md"}
-# DRAM bytes per k_tc_gemm launch (a symmetric TF32x3 Newton-Schulz product of the
-# 6000x6000 case) from the committed capture (profiles/k_tc_gemm_finite2000.md),
-# valid while k_tc.cu keeps the captured hash.
-TC_GEMM_TRAFFIC = {"bytes": 2.105201e9 + 0.413660928e9, "k_tc_sha16": "966f5e0533c95e2a",
-                   "launch": "symmetric Z' product, 1128 CTAs", "source": "profiles/k_tc_gemm_finite2000.md"}
+# DRAM bytes per k_tc_gemm launch (a symmetric TF32x3 Newton-Schulz product at order 6016,
+# the size of the 6000x6000 case, captured alone with --kernel tc_gemm_sym6016) from the
+# committed capture (profiles/k_tc_gemm_finite2000.md), valid while k_tc.cu keeps the
+# captured hash.
+TC_GEMM_TRAFFIC = {"bytes": 1.558883e9 + 0.407660544e9, "k_tc_sha16": "fbadf8fea91f516e",
+                   "launch": "symmetric Z' product, order 6016, 152 persistent CTAs",
+                   "source": "profiles/k_tc_gemm_finite2000.md"}
 
 
 def parse():
@@ -67,6 +69,10 @@ def parse():
     ap.add_argument("--cpu-sample-atoms", type=int, default=250,
                     help="atoms of the bounded oracle sample (same recipe, extrapolated by n^3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=("tc_gemm_sym6016",), default=None,
+                    help="time one kernel alone instead of the workload (a small case for profilers): "
+                         "tc_gemm_sym6016 = the symmetric TF32x3 Newton-Schulz product of order 6016 "
+                         "(k_tc_gemm mode 2, chunks of 2 stages), about 0.9 GB on the device")
     return ap.parse_args()
 
 
@@ -516,8 +522,52 @@ def run_batch(args):
     return 0
 
 
+def run_kernel(args):
+    """One kernel alone, --warmup + --steps launches, CUDA-event time per launch: the
+    symmetric TF32x3 product Z' = c3 P Z + c1 Z of the Newton-Schulz iteration at order
+    6016 (operands as TF32 hi/lo parts, FP32 output and its parts)."""
+    import torch
+    from paper_2308_03140_gb300 import binding
+    binding.load()
+    dev = torch.device("cuda:0")
+    n = 6016
+    g = torch.Generator(device="cpu").manual_seed(7)
+    S = torch.randn(n, n, generator=g, dtype=torch.float32) / n ** 0.5
+    S = (S + S.T).to(dev)
+    hi = ((S.view(torch.int32) + 0x1000) & ~0x1FFF).view(torch.float32)
+    lo = (S - hi).contiguous()
+    C = torch.empty(n, n, dtype=torch.float32, device=dev)
+    Ch, Cl = torch.empty_like(C), torch.empty_like(C)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def launch():
+        rc = binding.mbdk_gemm_tc(2, hi, hi, C, A1=lo, B1=lo, alpha=-0.5, beta=1.5, D=S, C_hi=Ch, C_lo=Cl,
+                                  mode=2, err=err, chunk_stages=2)
+        if rc:
+            raise RuntimeError(f"mbdk_gemm_tc returned {rc}")
+
+    for _ in range(args.warmup):
+        launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        launch()
+    e1.record()
+    torch.cuda.synchronize()
+    if err.item():
+        raise RuntimeError("tensor-core wait timed out")
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    flops = float(n) * n * (n + 1)   # algorithmic: upper triangle of a symmetric n x n x n product
+    print(json.dumps({"kernel": "k_tc_gemm<TF32x3> mode 2", "order": n, "launches": args.steps, "ms_per_launch": ms,
+                      "tflops_algorithmic": flops / (ms / 1e3) / 1e12}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel:
+        return run_kernel(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch4096":

@@ -147,6 +147,11 @@ void set_identity(double *Z, long long ld, cudaStream_t s);
 // vector: coef[2j] = alpha_j, coef[2j+1] = beta_j, j < steps.  work: 3 ld doubles.
 void lanczos_coefficients(const double *A, long long ld, int steps, double *work, double *coef,
                           cudaStream_t s);
+// As lanczos_coefficients, with the matrix-vector products in FP32 on an FP32 copy of A
+// written to A32 (ld x ld floats) and an FP32 copy of the Lanczos vector; the recurrence
+// (alpha, beta, orthogonalisation) stays FP64.  work: 3 ld doubles + ld floats.
+void lanczos_coefficients_f32(const double *A, float *A32, long long ld, int steps, double *work, double *coef,
+                              cudaStream_t s);
 // Maximum absolute row sum over rows 0..n-1 (Gershgorin bound), written to out[0].
 void max_abs_rowsum(const double *Q, long long ld, int n, double *out, cudaStream_t s);
 
@@ -191,10 +196,11 @@ void chain_screen(const AtomBufs &b, const MbdGradOut &o, double *h, double *g_a
 
 // SCS adjoint pair pass: with X = M^{-1} E and V = M^{-1} H per frequency, adds
 // -1/3 sum dM_pq (V X^T)_pq to dE/d alpha0, dE/d omega, dE/d R_vdW (g_a0, g_om, g_rv)
-// and dE/dR (gR, accumulated).  fp32: per-pair arithmetic in single precision (sums FP64),
-// for the reduced-precision modes.
+// and dE/dR (gR, accumulated).  With work32 (2 nf1 (xstride + N) floats) the per-pair
+// arithmetic runs in single precision on FP32 copies of X, V, sigma(iu) and alpha(iu) (sums
+// FP64), for the reduced-precision modes; with work32 = NULL, in FP64.
 void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, const double *V,
-                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR, bool fp32,
+                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR, float *work32,
                    cudaStream_t s);
 
 // TS-scaling chain to [4][N] parameter gradients, times *scale (device) if given.

@@ -5,6 +5,8 @@
 // These carry the cubic stages of the method: the screening solves of Eq. (scs) (one
 // factorisation per frequency point, Sec. 2.3) and the coupled Newton-Schulz iteration
 // for Q^{1/2} and Q^{-1/2} behind Eqs. (diagonalization), (mbd-energy), (mbd-gradient).
+#include <type_traits>
+
 #include "internal.h"
 
 namespace mbdgb {
@@ -245,16 +247,25 @@ __global__ void k_max_abs_rowsum(const double *Q, long long ld, int n, unsigned 
 }
 
 // ---- Lanczos estimates of the extreme eigenvalues of a symmetric matrix ----
-// y = A x for an ld x ld row-major A: one warp per row, coalesced row reads.
-__global__ void k_gemv(const double *A, long long ld, const double *x, double *y) {
+// y = A x for an ld x ld row-major A: one warp per row, coalesced row reads.  T = double,
+// or float for an FP32 copy of A with an FP32 copy of x (products and row sums in FP32).
+template <typename T>
+__global__ void k_gemv(const T *A, long long ld, const T *x, double *y) {
     const long long row = blockIdx.x * static_cast<long long>(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= ld) return;
-    const double *a = A + row * ld;
-    double acc = 0.0;
+    const T *a = A + row * ld;
+    T acc = 0;
     for (long long c = lane; c < ld; c += 32) acc += a[c] * x[c];
-    acc = warp_sum(acc);
-    if (lane == 0) y[row] = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[row] = static_cast<double>(acc);
+}
+
+__global__ void k_f64_to_f32(const double *A, long long total, float *B) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        B[e] = static_cast<float>(A[e]);
 }
 
 __device__ double block_sum1024(double v, double *sh) {
@@ -271,8 +282,8 @@ __device__ double block_sum1024(double v, double *sh) {
     return r;
 }
 
-// v = a fixed pseudo-random unit vector, vprev = 0.
-__global__ void __launch_bounds__(1024) k_lanczos_init(double *v, double *vprev, long long ld) {
+// v = a fixed pseudo-random unit vector, vprev = 0; v32 (if given) = (float) v.
+__global__ void __launch_bounds__(1024) k_lanczos_init(double *v, double *vprev, float *v32, long long ld) {
     __shared__ double sh[32];
     double ss = 0.0;
     for (long long p = threadIdx.x; p < ld; p += 1024) {
@@ -282,12 +293,16 @@ __global__ void __launch_bounds__(1024) k_lanczos_init(double *v, double *vprev,
         ss += x * x;
     }
     const double nrm = sqrt(block_sum1024(ss, sh));
-    for (long long p = threadIdx.x; p < ld; p += 1024) v[p] /= nrm;
+    for (long long p = threadIdx.x; p < ld; p += 1024) {
+        v[p] /= nrm;
+        if (v32) v32[p] = static_cast<float>(v[p]);
+    }
 }
 
 // One Lanczos step after w = A v: alpha = w.v; w -= alpha v + beta_prev vprev;
-// beta = |w|; vprev = v; v = w / beta.  coef[2j] = alpha, coef[2j+1] = beta.
-__global__ void __launch_bounds__(1024) k_lanczos_update(double *w, double *v, double *vprev, long long ld,
+// beta = |w|; vprev = v; v = w / beta (and v32 = (float) v if given).  coef[2j] = alpha,
+// coef[2j+1] = beta.
+__global__ void __launch_bounds__(1024) k_lanczos_update(double *w, double *v, double *vprev, float *v32, long long ld,
                                                          double *coef, int j) {
     __shared__ double sh[32];
     double d = 0.0;
@@ -305,6 +320,7 @@ __global__ void __launch_bounds__(1024) k_lanczos_update(double *w, double *v, d
     for (long long p = threadIdx.x; p < ld; p += 1024) {
         vprev[p] = v[p];
         v[p] = w[p] * inv;
+        if (v32) v32[p] = static_cast<float>(v[p]);
     }
     if (threadIdx.x == 0) {
         coef[2 * j] = alpha;
@@ -314,15 +330,31 @@ __global__ void __launch_bounds__(1024) k_lanczos_update(double *w, double *v, d
 
 }  // namespace
 
-void lanczos_coefficients(const double *A, long long ld, int steps, double *work, double *coef, cudaStream_t s) {
+// work: 3 ld doubles (v, vprev, w), then for T = float ld floats (the FP32 copy of v).
+template <typename T>
+void lanczos_run(const T *A, long long ld, int steps, double *work, double *coef, cudaStream_t s) {
     double *v = work, *vprev = work + ld, *w = work + 2 * ld;
+    float *v32 = std::is_same<T, float>::value ? reinterpret_cast<float *>(work + 3 * ld) : nullptr;
+    const T *x = std::is_same<T, float>::value ? reinterpret_cast<const T *>(v32) : reinterpret_cast<const T *>(v);
     count_launches(1);
-    k_lanczos_init<<<1, 1024, 0, s>>>(v, vprev, ld);
+    k_lanczos_init<<<1, 1024, 0, s>>>(v, vprev, v32, ld);
     for (int j = 0; j < steps; ++j) {
         count_launches(2);
-        k_gemv<<<static_cast<int>((ld + 7) / 8), 256, 0, s>>>(A, ld, v, w);
-        k_lanczos_update<<<1, 1024, 0, s>>>(w, v, vprev, ld, coef, j);
+        k_gemv<T><<<static_cast<int>((ld + 7) / 8), 256, 0, s>>>(A, ld, x, w);
+        k_lanczos_update<<<1, 1024, 0, s>>>(w, v, vprev, v32, ld, coef, j);
     }
+}
+
+void lanczos_coefficients(const double *A, long long ld, int steps, double *work, double *coef, cudaStream_t s) {
+    lanczos_run<double>(A, ld, steps, work, coef, s);
+}
+
+void lanczos_coefficients_f32(const double *A, float *A32, long long ld, int steps, double *work, double *coef,
+                              cudaStream_t s) {
+    count_launches(1);
+    k_f64_to_f32<<<static_cast<int>(std::min<long long>((ld * ld + 255) / 256, 152 * 16)), 256, 0, s>>>(A, ld * ld,
+                                                                                                      A32);
+    lanczos_run<float>(A32, ld, steps, work, coef, s);
 }
 
 void gemm_f64(const GemmArgs &g, cudaStream_t s) {

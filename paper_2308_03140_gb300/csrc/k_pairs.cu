@@ -305,9 +305,11 @@ template <> struct PairMath<float> {
     static __device__ __forceinline__ RadialF radial(float r, float s) { return pairs::tgg_radial_f(r, s); }
 };
 
+// X, V ([nf1][xstride]), sig and al ([nf1][N], sigma_i(iu) and alpha_i(iu)) are read in T:
+// the FP64 arrays, or FP32 copies of them in the reduced-precision modes.
 template <typename T>
-__global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, double a, const double *X,
-                                                  const double *V, long long xstride, double *g_a0,
+__global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, double a, const T *X, const T *V,
+                                                  const T *sig, const T *al, long long xstride, double *g_a0,
                                                   double *g_om, double *g_rv, double *gR) {
     extern __shared__ double gal_s[];   // [nf1][128]
     const int i = blockIdx.x, t = threadIdx.x;
@@ -323,14 +325,14 @@ __global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, doubl
         const T sr = T(1) - f.f;
         T pacc[4] = {0, 0, 0, 0};
         for (int k = 0; k < b.nf1; ++k) {
-            const double *Vk = V + k * xstride, *Xk = X + k * xstride;
+            const T *Vk = V + k * xstride, *Xk = X + k * xstride;
             T Ws[9];
             for (int x = 0; x < 3; ++x)
                 for (int y = 0; y < 3; ++y) {
-                    double w = 0.0;
+                    T w = 0;
                     for (int c = 0; c < 3; ++c)
                         w += Vk[9LL * i + 3 * x + c] * Xk[9LL * j + 3 * y + c] + Xk[9LL * i + 3 * x + c] * Vk[9LL * j + 3 * y + c];
-                    Ws[3 * x + y] = static_cast<T>(w);
+                    Ws[3 * x + y] = w;
                 }
             const T tr = Ws[0] + Ws[4] + Ws[8];
             T Wr[3], Wtr[3];
@@ -339,14 +341,14 @@ __global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, doubl
                 Wtr[x] = Ws[x] * r[0] + Ws[3 + x] * r[1] + Ws[6 + x] * r[2];
             }
             const T rWr = r[0] * Wr[0] + r[1] * Wr[1] + r[2] * Wr[2];
-            const double si = b.sig_u[k * b.N + i], sj = b.sig_u[k * b.N + j];
-            const double s = sqrt(si * si + sj * sj);
-            const auto q = PairMath<T>::radial(rho, static_cast<T>(s));
+            const T si = sig[k * b.N + i], sj = sig[k * b.N + j];
+            const T s = sqrt(si * si + sj * sj);
+            const auto q = PairMath<T>::radial(rho, s);
             const T WT = q.P * tr + q.W * rWr;            // <Ws, T^GG>
             const T WTs = q.dPs * tr + q.dWs * rWr;       // <Ws, dT^GG/ds>
             // ds/d alpha_i = (sigma_i / s) * sigma_i / (3 alpha_i)
-            const double dsda = si * si / (3.0 * s * b.al_u[k * b.N + i]);
-            gal_s[k * 128 + t] += -1.0 / 3.0 * static_cast<double>(sr * WTs) * dsda;
+            const T dsda = si * si / (T(3) * s * al[k * b.N + i]);
+            gal_s[k * 128 + t] += -1.0 / 3.0 * static_cast<double>(sr * WTs * dsda);
             pacc[0] += -f.df_dS * WT;
             for (int c = 0; c < 3; ++c) {
                 const T WdT = (q.dP * tr + q.dW * rWr) * r[c] * ir + q.W * (Wr[c] + Wtr[c]);
@@ -364,11 +366,11 @@ __global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, doubl
         const int k = t;
         double sacc = 0.0;
         for (int e = 0; e < 128; ++e) sacc += gal_s[k * 128 + e];
-        const double *Vk = V + k * xstride, *Xk = X + k * xstride;
+        const T *Vk = V + k * xstride, *Xk = X + k * xstride;
         double wd = 0.0;
-        for (int e = 0; e < 9; ++e) wd += Vk[9LL * i + e] * Xk[9LL * i + e];
-        const double al = b.al_u[k * b.N + i];
-        sacc += -1.0 / 3.0 * wd * (-1.0 / (al * al));
+        for (int e = 0; e < 9; ++e) wd += static_cast<double>(Vk[9LL * i + e]) * static_cast<double>(Xk[9LL * i + e]);
+        const double alk = b.al_u[k * b.N + i];
+        sacc += -1.0 / 3.0 * wd * (-1.0 / (alk * alk));
         gal_s[k * 128] = sacc;
     }
     __syncthreads();
@@ -387,6 +389,22 @@ __global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, doubl
         gR[3 * i] += acc[1];
         gR[3 * i + 1] += acc[2];
         gR[3 * i + 2] += acc[3];
+    }
+}
+
+// FP32 copies of X, V ([nf1][xstride] each) and of sigma(iu), alpha(iu) ([nf1][N] each),
+// packed in that order into w.
+__global__ void k_scs_grad_inputs_f32(const double *X, const double *V, const double *sig, const double *al,
+                                      long long nx, long long na, float *w) {
+    const long long total = 2 * nx + 2 * na;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        double v;
+        if (e < nx) v = X[e];
+        else if (e < 2 * nx) v = V[e - nx];
+        else if (e < 2 * nx + na) v = sig[e - 2 * nx];
+        else v = al[e - 2 * nx - na];
+        w[e] = static_cast<float>(v);
     }
 }
 
@@ -486,12 +504,20 @@ void chain_screen(const AtomBufs &b, const MbdGradOut &o, double *h, double *g_a
 }
 
 void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, const double *V,
-                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR, bool fp32,
+                   long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR, float *work32,
                    cudaStream_t s) {
     const size_t smem = sizeof(double) * b.nf1 * 128;
-    count_launches(1);
-    if (fp32) k_scs_grad<float><<<b.N, 128, smem, s>>>(b, beta, a, X, V, xstride, g_a0, g_om, g_rv, gR);
-    else k_scs_grad<double><<<b.N, 128, smem, s>>>(b, beta, a, X, V, xstride, g_a0, g_om, g_rv, gR);
+    if (work32) {
+        const long long nx = xstride * b.nf1, na = static_cast<long long>(b.nf1) * b.N;
+        float *X32 = work32, *V32 = work32 + nx, *sig32 = work32 + 2 * nx, *al32 = sig32 + na;
+        count_launches(2);
+        k_scs_grad_inputs_f32<<<cdiv(2 * nx + 2 * na, 256), 256, 0, s>>>(X, V, b.sig_u, b.al_u, nx, na, work32);
+        k_scs_grad<float><<<b.N, 128, smem, s>>>(b, beta, a, X32, V32, sig32, al32, xstride, g_a0, g_om, g_rv, gR);
+    } else {
+        count_launches(1);
+        k_scs_grad<double><<<b.N, 128, smem, s>>>(b, beta, a, X, V, b.sig_u, b.al_u, xstride, g_a0, g_om, g_rv,
+                                                 gR);
+    }
 }
 
 void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv,

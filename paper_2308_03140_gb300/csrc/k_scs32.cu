@@ -85,12 +85,13 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(const float *A, const float *B
 // matrix.  The factorisation is blocked by 16: warp 0 factors each 16x16 diagonal block
 // (warp-synchronous, one lane per row), one thread per row solves the rows below it, and
 // all threads apply the 16-term trailing update (3 block barriers per 16 columns).  The
-// inverse is formed by forward substitution on L X = I with four lanes per column, the
-// dot products split over the lanes and combined by shuffles.
+// inverse is blocked by 16 as well: the diagonal blocks by forward substitution in
+// registers, the blocks below them by two small block products per block row.
 __global__ void __launch_bounds__(256) k_spotrf_diag(float *A, long long ld, long long mstride, float *dinv,
                                                      long long dstride, int *status) {
     __shared__ float S[64][65];
     __shared__ float V[64][65];
+    __shared__ float Tp[3][16][17];
     __shared__ int bad;
     float *Ab = A + static_cast<long long>(blockIdx.x) * mstride;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -144,19 +145,41 @@ __global__ void __launch_bounds__(256) k_spotrf_diag(float *A, long long ld, lon
         }
         __syncthreads();
     }
-    {   // V = L^{-1}: column c by lanes 4c..4c+3 of the CTA; a warp holds columns 8w..8w+7
-        const int c = t >> 2, q = t & 3;
-        for (int i = warp * 8; i < 64; ++i) {
-            float sum = 0.f;
-            if (i >= c)
-                for (int k = c + q; k < i; k += 4) sum += S[i][k] * V[k][c];
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-            if (i >= c && q == 0) V[i][c] = ((i == c ? 1.f : 0.f) - sum) / S[i][i];
-            __syncwarp();
+    // V = L^{-1} by 16x16 blocks.  Diagonal blocks: warp w < 4 inverts block w, lane c < 16
+    // holding column c in registers (forward substitution).  Block rows I = 1..3 then follow
+    // from V_IJ = -V_II sum_{K=J}^{I-1} L_IK V_KJ (J < I), every element in parallel.
+    if (warp < 4 && lane < 16) {
+        const int b0 = 16 * warp, c = lane;
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            float sum = (i == c) ? 1.f : 0.f;
+#pragma unroll
+            for (int k = 0; k < i; ++k)
+                if (k >= c) sum -= S[b0 + i][b0 + k] * v[k];
+            v[i] = (i >= c) ? sum / S[b0 + i][b0 + i] : 0.f;
         }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) V[b0 + i][b0 + c] = v[i];
     }
     __syncthreads();
+    for (int I = 1; I < 4; ++I) {
+        for (int e = t; e < I * 256; e += 256) {   // Tp[J] = sum_K L_IK V_KJ
+            const int J = e >> 8, r = (e >> 4) & 15, cc = e & 15;
+            const int i = 16 * I + r, j = 16 * J + cc;
+            float sum = 0.f;
+            for (int k = 16 * J; k < 16 * I; ++k) sum += S[i][k] * V[k][j];
+            Tp[J][r][cc] = sum;
+        }
+        __syncthreads();
+        for (int e = t; e < I * 256; e += 256) {   // V_IJ = -V_II Tp[J]
+            const int J = e >> 8, r = (e >> 4) & 15, cc = e & 15;
+            float sum = 0.f;
+            for (int k = 0; k <= r; ++k) sum += V[16 * I + r][16 * I + k] * Tp[J][k][cc];
+            V[16 * I + r][16 * J + cc] = -sum;
+        }
+        __syncthreads();
+    }
     float *Db = dinv + static_cast<long long>(blockIdx.x) * dstride;
     for (int e = t; e < 4096; e += 256) {
         const int r = e >> 6, c = e & 63;

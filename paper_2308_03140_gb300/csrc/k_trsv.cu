@@ -9,7 +9,8 @@
 // one stream serialise the blocks; within a launch the work spreads over
 // (remaining rows / 64) CTAs per matrix, with coalesced reads of L.
 //
-// Forward:  y_I = D_I^{-1} b_I;  b_J -= L_JI y_I  (J > I; CTA slice = 64 rows of L),
+// Forward:  y_I = D_I^{-1} b_I;  b_J -= L_JI y_I  (J > I; CTA slice = 64 rows of L, four
+//           threads per row),
 //           b (the caller's array) is the running right-hand side, y goes to work.
 // Backward: x_I = D_I^{-T} y_I;  y_J -= L_IJ^T x_I (J < I; CTA slice = 64 columns),
 //           work is the running right-hand side, x goes to the caller's array.
@@ -19,13 +20,6 @@
 
 namespace mbdgb {
 namespace {
-
-template <typename T>
-__device__ __forceinline__ T wsum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // x (64x3, shared) = D^{-1} b_I (forward) or D^{-T} b_I (backward).  The 64x64 inverse is
 // first staged into shared memory with coalesced loads (all in flight at once), so the
@@ -57,31 +51,33 @@ __global__ void __launch_bounds__(256) k_trsv_fwd_block(const T *L, long long ld
     __shared__ T D[64][65], s[64][3], x[64][3];
     const long long I0 = static_cast<long long>(I) * 64;
     diag_solve<T, false>(dinv + b * dstride + static_cast<long long>(I) * 4096, Xb + 3 * I0, D, s, x);
-    // rows of this CTA: 64 rows starting after block I; warp w owns rows w, w + 8, ...
+    // rows of this CTA: 64 rows starting after block I; four threads per row, each taking
+    // 16 consecutive columns of the block, combined by two shuffles
     const long long r0 = I0 + 64 + static_cast<long long>(blockIdx.x) * 64;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (r0 < ld) {
-        T l0[8], l1[8];
+        const int rr = threadIdx.x >> 2, q = threadIdx.x & 3;
+        const T *Lq = Lb + (r0 + rr) * ld + I0 + 16 * q;
+        T l[16];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {   // issue all loads of the warp's rows first
-            const T *Lq = Lb + (r0 + warp + 8 * k) * ld + I0;
-            l0[k] = Lq[lane];
-            l1[k] = Lq[lane + 32];
+        for (int c = 0; c < 16; ++c) l[c] = Lq[c];
+        T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            a0 += l[c] * x[16 * q + c][0];
+            a1 += l[c] * x[16 * q + c][1];
+            a2 += l[c] * x[16 * q + c][2];
         }
-        const T y0a = x[lane][0], y0b = x[lane + 32][0], y1a = x[lane][1], y1b = x[lane + 32][1];
-        const T y2a = x[lane][2], y2b = x[lane + 32][2];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            T a0 = l0[k] * y0a + l1[k] * y0b;
-            T a1 = l0[k] * y1a + l1[k] * y1b;
-            T a2 = l0[k] * y2a + l1[k] * y2b;
-            a0 = wsum(a0); a1 = wsum(a1); a2 = wsum(a2);
-            if (lane == 0) {
-                const long long q = r0 + warp + 8 * k;
-                Xb[3 * q] -= a0;
-                Xb[3 * q + 1] -= a1;
-                Xb[3 * q + 2] -= a2;
-            }
+        for (int o = 1; o < 4; o <<= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (q == 0) {
+            T *xq = Xb + 3 * (r0 + rr);
+            xq[0] -= a0;
+            xq[1] -= a1;
+            xq[2] -= a2;
         }
     }
     // every CTA computed the same y_I; CTA 0 stores it

@@ -135,6 +135,7 @@ struct mbd_ctx {
     double *dM, *ddinv, *dX, *dV, *dB;
     float *sM = nullptr, *sdinv = nullptr, *swork = nullptr;   // FP32 factors of the mixed modes
     uint32_t *spanel = nullptr;   // TF32x3 parts of the factor panels (tensor-core trailing updates)
+    float *sgrad32 = nullptr;     // FP32 inputs of the reduced-precision SCS adjoint pair pass
     double *dQ, *dZ, *dP, *dY2, *dZ2;
     // mixed-precision Newton-Schulz buffers (ld x ld each)
     float *fY = nullptr, *fZ = nullptr, *fY2 = nullptr, *fZ2 = nullptr, *fP = nullptr, *fPT = nullptr;
@@ -332,9 +333,10 @@ int allocate(mbd_ctx *ctx) {
     bytes += 12 * split_mat;
     // FP32 screening factors, their diagonal-block inverses and solve workspace
     const size_t panel_words = 2 * nf1 * static_cast<size_t>(ld) * 256;
+    const size_t grad32 = 2 * nf1 * (3 * static_cast<size_t>(ld) + N);
     const size_t scs32 = prec != MBD_PREC_FP64
                              ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * 2 * nf1 * ld * 3) +
-                                   al(sizeof(uint32_t) * panel_words)
+                                   al(sizeof(uint32_t) * panel_words) + al(sizeof(float) * grad32)
                              : 0;
     bytes += scs32;
     // A slab large enough for the new size is re-carved in place (systems of varying size in
@@ -384,6 +386,8 @@ int allocate(mbd_ctx *ctx) {
         p += al(sizeof(float) * 2 * nf1 * ld * 3);
         ctx->spanel = reinterpret_cast<uint32_t *>(p);
         p += al(sizeof(uint32_t) * panel_words);
+        ctx->sgrad32 = reinterpret_cast<float *>(p);
+        p += al(sizeof(float) * grad32);
     }
     // Untouched parts of the factor buffers (strict upper triangles) are read by no
     // kernel; clearing them once keeps them finite.
@@ -527,7 +531,8 @@ void backward_passes(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const doub
     else
         refine_solve3(ctx->dM, ctx->sM, ctx->sdinv, ld, ctx->n, ctx->nf1, ctx->dB, ctx->dV, ctx->swork,
                       kAdjointRefineSteps, s);
-    scs_grad_pass(b, beta, a, ctx->dX, ctx->dV, xs, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgR, !fp64, s);
+    scs_grad_pass(b, beta, a, ctx->dX, ctx->dV, xs, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgR,
+                  fp64 ? nullptr : ctx->sgrad32, s);
     if (grad_params) ts_chain(b, ctx->dga0, ctx->dgom, ctx->dgrv, grad_energy, grad_params, s);
     if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
 }
@@ -965,7 +970,10 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     // spectrum; a 5 % margin keeps Y0's spectrum inside (0, 1]); the smallest gives the
     // lower bound for the scaled iteration, halved for safety.
     const int lz_steps = std::min(kLanczosSteps, static_cast<int>(ld));
-    lanczos_coefficients(ctx->dQ, ld, lz_steps, ctx->dP, ctx->dscal + 8, s);
+    if (ctx->opt.precision == MBD_PREC_FP64)
+        lanczos_coefficients(ctx->dQ, ld, lz_steps, ctx->dP, ctx->dscal + 8, s);
+    else   // the bounds need a few digits; the products read an FP32 copy of Q (in the FP32 Y buffer)
+        lanczos_coefficients_f32(ctx->dQ, ctx->fY, ld, lz_steps, ctx->dP, ctx->dscal + 8, s);
     std::vector<double> lz(2 * lz_steps);
     MBD_CUDA(cudaMemcpyAsync(lz.data(), ctx->dscal + 8, sizeof(double) * 2 * lz_steps, cudaMemcpyDeviceToHost, s),
              "newton_schulz");
