@@ -703,33 +703,32 @@ static int grad_forward(orc_state *S, const double *a0ref, const double *c6ref,
  * dE = -1/3 sum_pq dM_pq (V X^T)_pq (the same Eq. (scs) derivative dAbar = -Abar dM Abar,
  * contracted from the other side).  O(N^3) after the inverses.
  * Pinned against grad_forward and central differences. */
-static int grad_adjoint(orc_state *S, const double *a0ref, const double *c6ref,
-                        const double *rref, const double *ratio, double *gR, double *gp) {
-    int N = S->N, n = S->n, nf = S->nf;
-    double *g_a0 = calloc(N, sizeof(double)), *g_om = calloc(N, sizeof(double));
-    double *g_rv = calloc(N, sizeof(double));
-    double *g_ombar = calloc(N, sizeof(double)), *g_ab0 = calloc(N, sizeof(double));
-    double *g_rbar = calloc(N, sizeof(double)), *g_c = calloc(N, sizeof(double));
-    memset(gR, 0, sizeof(double) * 3 * N);
-    /* MBD part */
+/* MBD part of the adjoint gradient, Eq. (mbd-gradient) with reading R8: from Z = Q^{-1/2}
+ * of the coupled-oscillator matrix of the oscillators (ab0, omb) with damping radii rb,
+ * dE = 1/4 sum_pq Z_pq dQ_pq - 3/2 sum d omega.  Adds dE/d omega_i (g_omb), dE/d alpha0_i
+ * (g_ab0), dE/d R_damp,i (g_rb) and dE/dR_i (gR, [N][3]). */
+static void mbd_pair_adjoint(int N, const double *R, const double *ab0, const double *omb,
+                             const double *rb, const double *Z, double beta, double a,
+                             double *g_omb, double *g_ab0, double *g_rb, double *gR) {
+    int n = 3 * N;
+    double *g_c = calloc(N, sizeof(double));
     for (int i = 0; i < N; ++i) {
         double zd = 0.0;
-        for (int c = 0; c < 3; ++c) zd += S->Z[(size_t)(3 * i + c) * n + 3 * i + c];
-        g_ombar[i] += 0.25 * zd * 2.0 * S->ombar[i] - 1.5;
+        for (int c = 0; c < 3; ++c) zd += Z[(size_t)(3 * i + c) * n + 3 * i + c];
+        g_omb[i] += 0.25 * zd * 2.0 * omb[i] - 1.5;
     }
     for (int i = 0; i < N; ++i) {
-        double ci = S->ombar[i] * sqrt(S->abar0[i]);
+        double ci = omb[i] * sqrt(ab0[i]);
         for (int m = 0; m < N; ++m) {
             if (m == i) continue;
-            double r[3] = {S->R[3 * m] - S->R[3 * i], S->R[3 * m + 1] - S->R[3 * i + 1],
-                           S->R[3 * m + 2] - S->R[3 * i + 2]};
-            double cm = S->ombar[m] * sqrt(S->abar0[m]);
+            double r[3] = {R[3 * m] - R[3 * i], R[3 * m + 1] - R[3 * i + 1], R[3 * m + 2] - R[3 * i + 2]};
+            double cm = omb[m] * sqrt(ab0[m]);
             double P[9], dPdr[27], dPdS[9];
-            mbd_block_derivs(r, S->rbar[i] + S->rbar[m], S->beta, S->a, P, dPdr, dPdS);
+            mbd_block_derivs(r, rb[i] + rb[m], beta, a, P, dPdr, dPdS);
             double zP = 0.0, zS = 0.0, zr[3] = {0, 0, 0};
             for (int x = 0; x < 3; ++x)
                 for (int y = 0; y < 3; ++y) {
-                    double z = S->Z[(size_t)(3 * i + x) * n + 3 * m + y];
+                    double z = Z[(size_t)(3 * i + x) * n + 3 * m + y];
                     int t = 3 * x + y;
                     zP += z * P[t]; zS += z * dPdS[t];
                     for (int c = 0; c < 3; ++c) zr[c] += z * dPdr[9 * c + t];
@@ -737,8 +736,8 @@ static int grad_adjoint(orc_state *S, const double *a0ref, const double *c6ref,
             /* ordered block (i,m): 1/4 Z_{i,m} : d(c_i c_m P_im) */
             g_c[i] += 0.25 * cm * zP;
             g_c[m] += 0.25 * ci * zP;
-            g_rbar[i] += 0.25 * ci * cm * zS;
-            g_rbar[m] += 0.25 * ci * cm * zS;
+            g_rb[i] += 0.25 * ci * cm * zS;
+            g_rb[m] += 0.25 * ci * cm * zS;
             for (int c = 0; c < 3; ++c) {          /* r = R_m - R_i */
                 gR[3 * m + c] += 0.25 * ci * cm * zr[c];
                 gR[3 * i + c] -= 0.25 * ci * cm * zr[c];
@@ -746,10 +745,23 @@ static int grad_adjoint(orc_state *S, const double *a0ref, const double *c6ref,
         }
     }
     for (int i = 0; i < N; ++i) {
-        double sa = sqrt(S->abar0[i]);
-        g_ombar[i] += g_c[i] * sa;
-        g_ab0[i] += g_c[i] * S->ombar[i] / (2.0 * sa);
+        double sa = sqrt(ab0[i]);
+        g_omb[i] += g_c[i] * sa;
+        g_ab0[i] += g_c[i] * omb[i] / (2.0 * sa);
     }
+    free(g_c);
+}
+
+static int grad_adjoint(orc_state *S, const double *a0ref, const double *c6ref,
+                        const double *rref, const double *ratio, double *gR, double *gp) {
+    int N = S->N, n = S->n, nf = S->nf;
+    double *g_a0 = calloc(N, sizeof(double)), *g_om = calloc(N, sizeof(double));
+    double *g_rv = calloc(N, sizeof(double));
+    double *g_ombar = calloc(N, sizeof(double)), *g_ab0 = calloc(N, sizeof(double));
+    double *g_rbar = calloc(N, sizeof(double));
+    memset(gR, 0, sizeof(double) * 3 * N);
+    /* MBD part */
+    mbd_pair_adjoint(N, S->R, S->abar0, S->ombar, S->rbar, S->Z, S->beta, S->a, g_ombar, g_ab0, g_rbar, gR);
     /* chain through the screened parameters */
     double *h = calloc((size_t)(nf + 1) * N, sizeof(double));
     for (int i = 0; i < N; ++i) {
@@ -821,7 +833,7 @@ static int grad_adjoint(orc_state *S, const double *a0ref, const double *c6ref,
     }
     if (gp) ts_chain(N, a0ref, c6ref, rref, ratio, g_a0, g_om, g_rv, gp);
     free(X); free(V); free(h);
-    free(g_a0); free(g_om); free(g_rv); free(g_ombar); free(g_ab0); free(g_rbar); free(g_c);
+    free(g_a0); free(g_om); free(g_rv); free(g_ombar); free(g_ab0); free(g_rbar);
     return ORC_OK;
 }
 
@@ -840,5 +852,55 @@ int orc_mbd_rsscs_gradient(int N, const double *R, const double *a0ref, const do
         else rc = grad_adjoint(&S, a0ref, c6ref, rref, ratio, grad_coords, grad_params);
     }
     state_free(&S);
+    return rc;
+}
+
+/* MBD-NL (Sec. 2.2, paragraph MBD-NL): no screening step.  The oscillators are set
+ * directly from the free-atom reference and the ratios of a density polarizability
+ * functional, Eq. (mbd-nl-scaling): alpha0_i = alpha0_ref,i ra_i, omega_i = omega_ref,i rw_i,
+ * with omega_ref = 4 C6_ref / (3 alpha0_ref^2) the free atom's single-oscillator frequency
+ * (reading: the relation of Eq. ts-scaling), and the damping radii of Eq. (mbd-nl-rvdw),
+ * R_i = 5/2 alpha0_ref,i^{1/7} ra_i^{1/3}; then the MBD energy of Eq. (mbd-energy) with the
+ * Fermi-damped T^lr of Eq. (mbd-lr-dipole).  grad_coords [N][3] and grad_params [4][N]
+ * (d/d alpha0_ref, C6_ref, ra, rw) may both be NULL (energy only); params_out [3][N]
+ * (alpha0, omega, R) may be NULL. */
+int orc_mbd_nl(int N, const double *R, const double *a0ref, const double *c6ref, const double *ra,
+               const double *rw, double beta, double a, double *E, double *grad_coords,
+               double *grad_params, double *params_out) {
+    for (int i = 0; i < N; ++i)
+        if (!(a0ref[i] > 0.0) || !(c6ref[i] > 0.0) || !(ra[i] > 0.0) || !(rw[i] > 0.0)) return ORC_ERR_INPUT;
+    int n = 3 * N;
+    double *a0 = malloc(sizeof(double) * N), *om = malloc(sizeof(double) * N), *rd = malloc(sizeof(double) * N);
+    for (int i = 0; i < N; ++i) {
+        a0[i] = a0ref[i] * ra[i];
+        om[i] = 4.0 * c6ref[i] / (3.0 * a0ref[i] * a0ref[i]) * rw[i];
+        rd[i] = 2.5 * pow(a0ref[i], 1.0 / 7.0) * cbrt(ra[i]);
+    }
+    if (params_out)
+        for (int i = 0; i < N; ++i) {
+            params_out[i] = a0[i];
+            params_out[N + i] = om[i];
+            params_out[2 * N + i] = rd[i];
+        }
+    double *Q = malloc(sizeof(double) * (size_t)n * n);
+    int want_grad = grad_coords != NULL || grad_params != NULL;
+    double *Z = want_grad ? malloc(sizeof(double) * (size_t)n * n) : NULL;
+    orc_mbd_q(N, R, a0, om, rd, beta, a, Q);
+    int rc = orc_energy_from_q(N, Q, om, E, Z);
+    if (rc == ORC_OK && want_grad) {
+        double *g_om = calloc(N, sizeof(double)), *g_a0 = calloc(N, sizeof(double));
+        double *g_rd = calloc(N, sizeof(double)), *gR = calloc((size_t)3 * N, sizeof(double));
+        mbd_pair_adjoint(N, R, a0, om, rd, Z, beta, a, g_om, g_a0, g_rd, gR);
+        if (grad_coords) memcpy(grad_coords, gR, sizeof(double) * 3 * N);
+        if (grad_params)
+            for (int i = 0; i < N; ++i) {   /* chain through Eqs. (mbd-nl-scaling), (mbd-nl-rvdw) */
+                grad_params[i] = g_a0[i] * ra[i] - g_om[i] * 2.0 * om[i] / a0ref[i] + g_rd[i] * rd[i] / (7.0 * a0ref[i]);
+                grad_params[N + i] = g_om[i] * om[i] / c6ref[i];
+                grad_params[2 * N + i] = g_a0[i] * a0ref[i] + g_rd[i] * rd[i] / (3.0 * ra[i]);
+                grad_params[3 * N + i] = g_om[i] * om[i] / rw[i];
+            }
+        free(g_om); free(g_a0); free(g_rd); free(gR);
+    }
+    free(a0); free(om); free(rd); free(Q); free(Z);
     return rc;
 }

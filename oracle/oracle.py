@@ -63,6 +63,7 @@ def lib():
             L.orc_mbd_energy.argtypes = [i, _dp, _dp, _dp, _dp, d, d, P]
             L.orc_mbd_rsscs_energy.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, P, P]
             L.orc_mbd_rsscs_gradient.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, i, P, _dp, _dp]
+            L.orc_mbd_nl.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, P, P, P, P]
             L.alpha_iu.argtypes = [d, d, d]
             L.alpha_iu.restype = d
             # periodic
@@ -236,6 +237,25 @@ def mbd_rsscs_gradient(R, a0ref, c6ref, rref, ratio, beta=0.83, a=6.0, n_freq=15
                                       n_freq, 0 if mode == "forward" else 1, C.byref(E), gR, gp)
     _check(rc, "mbd_rsscs_gradient")
     return E.value, gR, gp
+
+
+def mbd_nl(R, a0ref, c6ref, ra, rw, beta=0.83, a=6.0, grad=False, detail=False):
+    """MBD-NL energy (Sec. 2.2, Eqs. mbd-nl-scaling, mbd-nl-rvdw): no screening, oscillators
+    from the free-atom reference (alpha0_ref, C6_ref) and the density-functional ratios
+    ra = alpha0_df/alpha0_df,ref, rw = omega_df/omega_df,ref.  grad: also dE/dR [N,3] and
+    dE/d(alpha0_ref, C6_ref, ra, rw) [4,N].  detail: also the oscillators (alpha0, omega,
+    R_damp) [3,N]."""
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    E = C.c_double()
+    gR, gp, par = np.zeros((N, 3)), np.zeros((4, N)), np.zeros((3, N))
+    ptr = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
+    rc = lib().orc_mbd_nl(N, R, _a(a0ref), _a(c6ref), _a(ra), _a(rw), beta, a, C.byref(E),
+                          ptr(gR) if grad else None, ptr(gp) if grad else None, ptr(par))
+    _check(rc, "mbd_nl")
+    out = (E.value, gR, gp) if grad else (E.value,)
+    if detail:
+        out = out + (par,)
+    return out if len(out) > 1 else out[0]
 
 
 def system_args(sys):
