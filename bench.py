@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--cpu-sample-atoms", type=int, default=250,
                     help="atoms of the bounded oracle sample (same recipe, extrapolated by n^3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--method", choices=("rsscs", "nl"), default="rsscs",
+                    help="rsscs: MBD@rsSCS (the headline); nl: MBD-NL (Sec. 2.2: no screening, oscillators "
+                         "from the free-atom reference and density-functional ratios drawn by "
+                         "synthetic.nl_ratios(N, seed=7000))")
     ap.add_argument("--kernel", choices=("tc_gemm_sym6016",), default=None,
                     help="time one kernel alone instead of the workload (a small case for profilers): "
                          "tc_gemm_sym6016 = the symmetric TF32x3 Newton-Schulz product of order 6016 "
@@ -153,9 +157,18 @@ def sample_system(workload: str, n_sample: int):
     return syn.sphere_cluster(n_sample, seed=1000)
 
 
-def oracle_solve(sysm):
+NL_SEED = 7000   # stream of the MBD-NL density-functional ratios of a workload
+
+
+def oracle_solve(sysm, method="rsscs"):
     """One energy+gradient by the CPU oracle (as it stands)."""
     import oracle as o
+    if method == "nl":
+        from paper_2308_03140_gb300 import synthetic as syn
+        ra, rw = syn.nl_ratios(sysm.n_atoms, NL_SEED)
+        if sysm.lattice is not None:
+            raise ValueError("the oracle's MBD-NL arm covers finite systems")
+        return o.mbd_nl(sysm.coords, sysm.alpha0_ref, sysm.c6_ref, ra, rw, grad=True)
     if sysm.lattice is not None:
         g, rc, kc = PERIODIC_EWALD
         return o.periodic_rsscs_gradient(sysm.coords, sysm.lattice, o.monkhorst_pack(sysm.k_grid),
@@ -163,12 +176,12 @@ def oracle_solve(sysm):
     return o.mbd_rsscs_gradient(*o.system_args(sysm), mode="adjoint")
 
 
-def cpu_baseline(workload: str, n_sample: int, n_target: int):
+def cpu_baseline(workload: str, n_sample: int, n_target: int, method: str = "rsscs"):
     """Times the CPU oracle (as it stands) on a same-recipe sample of n_sample atoms and
     extrapolates to n_target atoms by the cubic cost of its dense stages."""
     sysm = sample_system(workload, n_sample)
     t0 = time.perf_counter()
-    oracle_solve(sysm)
+    oracle_solve(sysm, method)
     dt = time.perf_counter() - t0
     scale = (n_target / n_sample) ** 3
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -187,11 +200,11 @@ def run_reference(args):
     n_s = min(args.cpu_sample_atoms, 200) if args.workload != "cell256" else 32
     sysm = sample_system(args.workload, n_s)
     for _ in range(args.warmup):
-        oracle_solve(sysm)
+        oracle_solve(sysm, args.method)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle_solve(sysm)
+        oracle_solve(sysm, args.method)
         times.append(time.perf_counter() - t0)
     dt = sum(times)
     scale = (n_target / n_s) ** 3
@@ -202,8 +215,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt * scale / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n_atoms": n_target, "n_freq": 15, "precision": "fp64",
-                       "sample_atoms": n_s},
+            "config": {"workload": args.workload, "method": "MBD-NL" if args.method == "nl" else "MBD@rsSCS",
+                       "n_atoms": n_target, "n_freq": 15, "precision": "fp64", "sample_atoms": n_s},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step one energy+gradient of a {n_s}-atom {kind} of the same "
                                        f"recipe, extrapolated by ({n_target}/{n_s})^3"},
@@ -244,8 +257,12 @@ def run_ours(args):
     if periodic and args.precision != "fp64":
         args.precision = "fp64"   # periodic systems run in FP64
     N = sysm.n_atoms
+    nl = args.method == "nl"
+    # per-atom parameter slots 3 and 4: R_vdW,ref and the volume ratio, or the MBD-NL ratios
+    p3, p4 = syn.nl_ratios(N, NL_SEED) if nl else (sysm.rvdw_ref, sysm.ratio)
+    scs_mode = binding.MBD_SCS_NL if nl else binding.MBD_SCS_PLAIN
     T = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
-    inp = [T(sysm.coords), T(sysm.alpha0_ref), T(sysm.c6_ref), T(sysm.rvdw_ref), T(sysm.ratio)]
+    inp = [T(sysm.coords), T(sysm.alpha0_ref), T(sysm.c6_ref), T(p3), T(p4)]
     energy = torch.zeros(1, dtype=torch.float64, device=dev)
     gR = torch.zeros(N, 3, dtype=torch.float64, device=dev)
     gp = torch.zeros(4, N, dtype=torch.float64, device=dev)
@@ -255,9 +272,9 @@ def run_ours(args):
                  "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3}[args.precision]
     ewald = dict(ewald_gamma=PERIODIC_EWALD[0], real_cutoff=PERIODIC_EWALD[1],
                  recip_cutoff=PERIODIC_EWALD[2]) if periodic else {}
-    m = binding.MBD(local, precision=precision, **ewald)
+    m = binding.MBD(local, precision=precision, scs_mode=scs_mode, **ewald)
     m.set_geometry(sysm.coords, sysm.lattice, sysm.k_grid)
-    m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, sysm.rvdw_ref, sysm.ratio)
+    m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, p3, p4)
 
     def step():
         m.evaluate_dev(*inp, energy, gR, gp, al, stream=stream)
@@ -291,7 +308,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         m.set_geometry(sysm.coords, sysm.lattice, sysm.k_grid)
-        m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, sysm.rvdw_ref, sysm.ratio)
+        m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, p3, p4)
         E_h, gR_h, gp_h, al_h = m.evaluate(True)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
@@ -304,7 +321,7 @@ def run_ours(args):
     # FP64 comparison arm (same workload and API; fewer steps: it is ~20x slower)
     fp64 = None
     if precision != binding.MBD_PREC_FP64 and args.fp64_steps > 0:
-        m64 = binding.MBD(local, precision=binding.MBD_PREC_FP64)
+        m64 = binding.MBD(local, precision=binding.MBD_PREC_FP64, scs_mode=scs_mode)
         m64.set_geometry(sysm.coords)
         e64 = torch.zeros(1, dtype=torch.float64, device=dev)
         g64 = torch.zeros(N, 3, dtype=torch.float64, device=dev)
@@ -369,7 +386,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == binding.MBD_PREC_FP64 else
         f"{args.precision}+f32+f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n_atoms": N, "matrix_order": n, "n_freq": 15,
+        "config": {"workload": args.workload, "method": "MBD-NL" if nl else "MBD@rsSCS", "n_atoms": N,
+                   "matrix_order": n, "n_freq": 15,
                    "precision": args.precision, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": ("inputs larger than L2: 16 screening matrices + 5 Newton-Schulz matrices of "
                           f"{8 * n * n / 1e6:.0f} MB each per step" if not periodic else
@@ -401,7 +419,9 @@ def run_ours(args):
         "ns_residual": st["ns_residual"], "correction_residual": st["correction_residual"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, 32 if periodic else args.cpu_sample_atoms, N)
+        if not (nl and periodic):
+            line["cpu_baseline"] = cpu_baseline(args.workload, 32 if periodic else args.cpu_sample_atoms, N,
+                                                args.method)
     if rank == 0:
         print(json.dumps(line), flush=True)
     m.close()

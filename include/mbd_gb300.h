@@ -82,13 +82,23 @@ typedef struct {
     /* Screening: MBD_SCS_PLAIN (the Dyson solves of Eq. (scs)) or MBD_SCS_LEARNED (the model
      * set by mbd_set_scs_model predicts alpha_bar(iu); when its estimated energy error per
      * atom exceeds learned_max_error (Ha, default 1e-6) the evaluation is redone with plain
-     * screening).  The learned model is not part of the paper.                          */
+     * screening).  The learned model is not part of the paper.
+     * MBD_SCS_NL selects MBD-NL (Sec. 2.2, paragraph MBD-NL): no screening; the oscillators
+     * are set directly by Eq. (mbd-nl-scaling), alpha0_i = alpha0_ref,i ra_i and
+     * omega_i = omega_ref,i rw_i with omega_ref = 4 c6_ref / (3 alpha0_ref^2), and the damping
+     * radii by Eq. (mbd-nl-rvdw), R_i = 5/2 alpha0_ref,i^(1/7) ra_i^(1/3), where
+     * ra = alpha0_df/alpha0_df,ref and rw = omega_df/omega_df,ref are the ratios of a density
+     * polarizability functional for the atom in the system and the free atom.  In this mode
+     * the third and fourth per-atom arrays of mbd_set_free_atom_params, mbd_evaluate_dev and
+     * mbd_backward_dev are ra and rw (in place of rvdw_ref and the volume ratio), and
+     * grad_params holds dE/d(alpha0_ref, c6_ref, ra, rw).  Finite and periodic systems.    */
     int scs_mode;
     double learned_max_error;
 } mbd_options;
 
 #define MBD_SCS_PLAIN 0
 #define MBD_SCS_LEARNED 1
+#define MBD_SCS_NL 2
 
 /* Fills *opt with the defaults above.  Returns MBD_ERR_INPUT if opt is NULL. */
 int mbd_default_options(mbd_options *opt);
@@ -166,7 +176,8 @@ int mbd_get_learned_stats(mbd_ctx *ctx, double *estimated_error, int *fell_back)
  * scale-rvdw-scs) with plain Dyson solves, for the geometry and parameters set above: host
  * outputs alpha_iu [n_freq+1][n_atoms] (screened), alpha_free_iu [n_freq+1][n_atoms] (the
  * unscreened alpha_i(iu) of Eq. dyn-pol), c6, omega, rvdw [n_atoms]; any may be NULL.
- * Finite and periodic (Gamma-point) systems. */
+ * Finite and periodic (Gamma-point) systems; MBD_ERR_UNSUPPORTED in MBD-NL mode, which
+ * has no screening step. */
 int mbd_screen(mbd_ctx *ctx, double *alpha_iu, double *alpha_free_iu, double *c6, double *omega, double *rvdw);
 
 /* Lattice gradient [3][3] (host) of the last gradient evaluation of a periodic system
@@ -176,7 +187,9 @@ int mbd_get_lattice_gradient(mbd_ctx *ctx, double *grad_lattice);
 
 /* Screening detail of the last successful evaluation, host arrays: alpha_iu
  * [n_freq+1][n_atoms] (row 0 is u = 0), c6 [n_atoms], omega [n_atoms] (screened
- * frequencies), rvdw [n_atoms] (screened damping radii).  Any may be NULL. */
+ * frequencies), rvdw [n_atoms] (screened damping radii).  Any may be NULL.  In MBD-NL mode
+ * these are the oscillators of Eqs. (mbd-nl-scaling), (mbd-nl-rvdw): alpha_iu =
+ * alpha0 / (1 + u^2/omega^2), c6 = 3/4 alpha0^2 omega, omega, and the damping radii. */
 int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega, double *rvdw);
 
 /* Statistics of the last evaluation: Newton-Schulz iterations, the scale s of

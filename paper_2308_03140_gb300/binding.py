@@ -39,7 +39,7 @@ class mbd_options(C.Structure):
                 ("precision", C.c_int), ("ns_tol", C.c_double), ("ns_max_iter", C.c_int),
                 ("tc_chunk_stages", C.c_int), ("ewald_gamma", C.c_double), ("real_cutoff", C.c_double),
                 ("recip_cutoff", C.c_double), ("scs_mode", C.c_int), ("learned_max_error", C.c_double)]
-MBD_SCS_PLAIN, MBD_SCS_LEARNED = 0, 1
+MBD_SCS_PLAIN, MBD_SCS_LEARNED, MBD_SCS_NL = 0, 1, 2
 
 
 class mbd_profile(C.Structure):
@@ -189,6 +189,13 @@ class MBD:
     def set_free_atom_params(self, alpha0_ref, c6_ref, rvdw_ref, volume_ratio):
         arrs = [_f64(x) for x in (alpha0_ref, c6_ref, rvdw_ref, volume_ratio)]
         self._check(self.lib.mbd_set_free_atom_params(self.h, *[_ptr(x) for x in arrs]))
+
+    def set_nl_params(self, alpha0_ref, c6_ref, alpha_ratio, omega_ratio):
+        """MBD-NL inputs (contexts created with scs_mode=MBD_SCS_NL): the free-atom reference
+        alpha0_ref, c6_ref and the density-functional ratios alpha0_df/alpha0_df,ref and
+        omega_df/omega_df,ref, passed in the third and fourth parameter slots of
+        mbd_set_free_atom_params."""
+        self.set_free_atom_params(alpha0_ref, c6_ref, alpha_ratio, omega_ratio)
 
     def evaluate(self, gradients: bool = True, param_gradients: bool = True):
         """Host-memory evaluation.  Returns (energy, grad_coords [N,3] | None,

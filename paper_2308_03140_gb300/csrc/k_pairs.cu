@@ -45,6 +45,52 @@ __global__ void k_prepare(AtomBufs b, int *status) {
     }
 }
 
+// MBD-NL oscillators (Sec. 2.2, paragraph MBD-NL): no screening.  Inputs per atom are
+// alpha0_ref (a0ref), C6_ref (c6ref), ra = alpha0_df/alpha0_df,ref (in rref) and
+// rw = omega_df/omega_df,ref (in ratio).  Eq. (mbd-nl-scaling): alpha0 = alpha0_ref ra,
+// omega = omega_ref rw with omega_ref = 4 C6_ref / (3 alpha0_ref^2); Eq. (mbd-nl-rvdw):
+// R = 5/2 alpha0_ref^(1/7) ra^(1/3).  They are written where the screened parameters go
+// (abar0, ombar, rbar; c6bar = 3/4 alpha0^2 omega; abar(iu) = alpha0 / (1 + u^2/omega^2))
+// and into a0, om, rv.
+__global__ void k_nl_params(AtomBufs b, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const double a0r = b.a0ref[i], c6r = b.c6ref[i], ra = b.rref[i], rw = b.ratio[i];
+    const double x = b.R[3 * i], y = b.R[3 * i + 1], z = b.R[3 * i + 2];
+    if (!(a0r > 0.0) || !(c6r > 0.0) || !(ra > 0.0) || !(rw > 0.0) || !isfinite(x) || !isfinite(y) ||
+        !isfinite(z) || !isfinite(a0r * c6r * ra * rw))
+        atomicOr(status, ST_INPUT);
+    const double a0 = a0r * ra, om = 4.0 * c6r / (3.0 * a0r * a0r) * rw;
+    const double rd = 2.5 * pow(a0r, 1.0 / 7.0) * cbrt(ra);
+    b.a0[i] = a0;
+    b.om[i] = om;
+    b.rv[i] = rd;
+    b.abar0[i] = a0;
+    b.ombar[i] = om;
+    b.rbar[i] = rd;
+    b.c6bar[i] = 0.75 * a0 * a0 * om;
+    for (int k = 0; k < b.nf1; ++k) {
+        const double uo = b.u[k] / om;
+        b.abar[k * b.N + i] = a0 / (1.0 + uo * uo);
+    }
+}
+
+// dE/d(alpha0_ref, C6_ref, ra, rw) [4][N] of MBD-NL from dE/d(alpha0, omega, R) of the
+// oscillators (the MBD pair pass), times *scale (device) if given.
+__global__ void k_nl_chain(AtomBufs b, const double *g_ab0, const double *g_om, const double *g_rd,
+                           const double *scale, double *gp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const int N = b.N;
+    const double w = scale ? scale[0] : 1.0;
+    const double a0r = b.a0ref[i], c6r = b.c6ref[i], ra = b.rref[i], rw = b.ratio[i];
+    const double om = b.ombar[i], rd = b.rbar[i];
+    gp[i] = w * (g_ab0[i] * ra - g_om[i] * 2.0 * om / a0r + g_rd[i] * rd / (7.0 * a0r));
+    gp[N + i] = w * (g_om[i] * om / c6r);
+    gp[2 * N + i] = w * (g_ab0[i] * a0r + g_rd[i] * rd / (3.0 * ra));
+    gp[3 * N + i] = w * (g_om[i] * om / rw);
+}
+
 // ---- screening matrices ------------------------------------------------------------
 // Thread (i, j) with j <= i writes block (i, j) of every frequency's matrix and its
 // mirror (j, i) (the blocks are symmetric 3x3 tensors): the factorisations read the lower
@@ -518,6 +564,16 @@ void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, co
         k_scs_grad<double><<<b.N, 128, smem, s>>>(b, beta, a, X, V, b.sig_u, b.al_u, xstride, g_a0, g_om, g_rv,
                                                  gR);
     }
+}
+
+void nl_params(const AtomBufs &b, int *status, cudaStream_t s) {
+    count_launches(1);
+    k_nl_params<<<cdiv(b.N, 128), 128, 0, s>>>(b, status);
+}
+
+void nl_chain(const AtomBufs &b, const MbdGradOut &o, const double *scale, double *gp, cudaStream_t s) {
+    count_launches(1);
+    k_nl_chain<<<cdiv(b.N, 128), 128, 0, s>>>(b, o.g_abar0, o.g_ombar, o.g_rbar, scale, gp);
 }
 
 void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv,

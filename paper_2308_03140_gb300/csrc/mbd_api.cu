@@ -523,6 +523,11 @@ void backward_passes(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const doub
     const double beta = ctx->opt.beta, a = ctx->opt.a;
     MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
     mbd_grad_pass(b, beta, a, ctx->Zlast, ld, ctx->zscale, go, s);
+    if (ctx->opt.scs_mode == MBD_SCS_NL) {   // MBD-NL: only the chain through Eqs. mbd-nl-*
+        if (grad_params) nl_chain(b, go, grad_energy, grad_params, s);
+        if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
+        return;
+    }
     const bool fp64 = ctx->opt.precision == MBD_PREC_FP64;
     chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, fp64 ? ctx->dV : ctx->dB, ld, xs, s);
     cudaMemsetAsync(ctx->dgom, 0, sizeof(double) * ctx->N, s);
@@ -727,6 +732,13 @@ void backward_periodic(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const do
     const PeriodicBufs pb = periodic_bufs(ctx);
     MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
     periodic_mbd_grad(b, pb, beta, a, ctx->Zlast, ld, ctx->zscale, go, ctx->dgc, ctx->dgA, s);
+    if (ctx->opt.scs_mode == MBD_SCS_NL) {   // MBD-NL: no screening to differentiate
+        if (grad_params) nl_chain(b, go, grad_energy, grad_params, s);
+        if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
+        scale_copy(ctx->dgA, 9, grad_energy, ctx->dgAout, s);
+        ctx->have_lattice_grad = true;
+        return;
+    }
     chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, ctx->dV, ld, xs, s);
     cudaMemsetAsync(ctx->dgom, 0, sizeof(double) * ctx->N, s);
     chol_solve3_f64(ctx->dM, ld, mat, ctx->nf1, ctx->ddinv, ctx->dV, ctx->dB, xs, s);
@@ -770,14 +782,19 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
     const PeriodicBufs pb = periodic_bufs(ctx);
     mark(ctx, s, e_start);
     MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_evaluate");
-    // ---- Gamma-point screening ----
-    prepare_atoms(b, ctx->dstatus, s);
-    structure_factors(b, pb, s);
-    build_scs_periodic(b, ctx->cell, beta, a, ctx->dM, ld, mat, ctx->dstatus, s);
-    cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
-    init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
-    chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
-    contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
+    // ---- Gamma-point screening (MBD-NL: the oscillators directly) ----
+    if (ctx->opt.scs_mode == MBD_SCS_NL) {
+        nl_params(b, ctx->dstatus, s);
+        structure_factors(b, pb, s);
+    } else {
+        prepare_atoms(b, ctx->dstatus, s);
+        structure_factors(b, pb, s);
+        build_scs_periodic(b, ctx->cell, beta, a, ctx->dM, ld, mat, ctx->dstatus, s);
+        cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
+        init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
+        chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
+        contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
+    }
     mark(ctx, s, e_scs);
     int rc = read_status(ctx, s, "screening");
     if (rc) return rc;
@@ -884,7 +901,7 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
             p.gemm_flops += sp.flops;
         }
         p.screening_ms = span_ms(e_start, e_scs);
-        p.screening_flops = nf1 * nd * nd * nd / 3.0;
+        p.screening_flops = ctx->opt.scs_mode == MBD_SCS_NL ? 0.0 : nf1 * nd * nd * nd / 3.0;
         p.newton_schulz_ms = span_ms(e_scs, e_ns);
         p.gradient_ms = span_ms(e_ns, e_grad);
         p.total_ms = span_ms(e_start, e_grad);
@@ -937,6 +954,8 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         if (ef != cudaSuccess) return cuda_fail(ctx, "learned_screening", ef);
         learned_alpha(N, ctx->members, nf1, ctx->dalu, ctx->dYl, ctx->dabar, ctx->dspread, s);
         screened_params(b, ctx->dstatus, s);
+    } else if (ctx->opt.scs_mode == MBD_SCS_NL) {   // MBD-NL: oscillators set directly, no screening
+        nl_params(b, ctx->dstatus, s);
     } else {
         prepare_atoms(b, ctx->dstatus, s);
         build_scs(b, beta, a, ctx->dM, ld, mat, ctx->dstatus, s);
@@ -1140,7 +1159,9 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         }
         if (e_corr) p.correction_ms = span_ms(e_corr, e_ns);
         p.screening_ms = span_ms(e_start, e_scs);
-        p.screening_flops = nf1 * nd * nd * nd / 3.0;   // FP64, or FP32 in the mixed modes
+        p.screening_flops = ctx->opt.scs_mode == MBD_SCS_NL
+                                ? 0.0
+                                : nf1 * nd * nd * nd / 3.0;   // FP64, or FP32 in the mixed modes
         p.newton_schulz_ms = span_ms(e_scs, e_ns);
         p.gradient_ms = span_ms(e_ns, e_grad);
         p.total_ms = span_ms(e_start, e_grad);
@@ -1178,7 +1199,8 @@ int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt) {
     if (opt) o = *opt; else mbd_default_options(&o);
     if (o.n_freq < 1 || o.n_freq + 1 > kMaxFreq || !(o.beta > 0) || !(o.a > 0) || o.ns_max_iter < 1 ||
         !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_TF32X3 || o.tc_chunk_stages < 0 ||
-        (o.scs_mode != MBD_SCS_PLAIN && o.scs_mode != MBD_SCS_LEARNED) || !(o.learned_max_error > 0))
+        (o.scs_mode != MBD_SCS_PLAIN && o.scs_mode != MBD_SCS_LEARNED && o.scs_mode != MBD_SCS_NL) ||
+        !(o.learned_max_error > 0))
         return MBD_ERR_INPUT;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev)
@@ -1388,6 +1410,8 @@ int mbd_screen(mbd_ctx *ctx, double *alpha_iu, double *alpha_free_iu, double *c6
     if (!ctx) return MBD_ERR_INPUT;
     if (!ctx->have_geom || !ctx->have_params)
         return fail(ctx, MBD_ERR_STATE, "mbd_screen", "set the geometry and the free-atom parameters first");
+    if (ctx->opt.scs_mode == MBD_SCS_NL)
+        return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_screen", "MBD-NL has no screening step");
     MBD_CUDA(cudaSetDevice(ctx->device), "mbd_screen");
     const int N = ctx->N, n = ctx->n, nf1 = ctx->nf1;
     const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;

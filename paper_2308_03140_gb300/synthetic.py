@@ -53,6 +53,16 @@ def draw_params(rng: np.random.Generator, n: int):
     return a0, c6, rv, vr
 
 
+def nl_ratios(n: int, seed: int):
+    """Density-functional ratios for MBD-NL inputs, drawn from their own stream (seed):
+    ra = alpha0_df/alpha0_df,ref ~ U[0.7, 1.0] (like the volume ratio: compression in the
+    system), then rw = omega_df/omega_df,ref ~ U[0.85, 1.2]."""
+    rng = np.random.default_rng(seed)
+    ra = rng.uniform(0.7, 1.0, n)
+    rw = rng.uniform(0.85, 1.2, n)
+    return ra, rw
+
+
 class _Grid:
     """Bucket grid for minimum-separation rejection sampling (open boundaries)."""
 
