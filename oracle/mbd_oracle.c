@@ -428,6 +428,58 @@ int orc_mbd_energy(int N, const double *R, const double *a0, const double *om,
     return rc;
 }
 
+/* MBD energy by the imaginary-frequency log formula, Eq. (log-formula), and its many-body
+ * orders, Eq. (rpa), for given oscillators (alpha0, omega) with damping radii rdamp:
+ *   E = 1/(2 pi) int_0^inf du ln det(I + A(u)),   A(u) = alpha(u)^{1/2} T^lr alpha(u)^{1/2}
+ * (the Hermitian form the paper allows under the trace), alpha_i(u) = alpha0_i/(1 + u^2/om_i^2),
+ * T^lr_ij = g_ij T(R_j - R_i) as in Q (reading R5), zero diagonal blocks;
+ *   E^(m) = -1/(2 pi) int du (-1)^m/m Tr A(u)^m,   m = 2..max_order -> orders[m - 2].
+ * The integral runs over the n_freq Gauss-Legendre nodes u_k > 0 of Sec. 3.3 with their
+ * weights.  ln det(I + A) = sum ln(1 + lambda) and Tr A^m = sum lambda^m over the
+ * eigenvalues of A (Jacobi).  ORC_ERR_NEG_EIGENVALUE if I + A is not positive definite. */
+int orc_mbd_log_energy(int N, const double *R, const double *a0, const double *om, const double *rdamp,
+                       double beta, double a, int nf, int max_order, double *E, double *orders) {
+    if (N < 1 || nf < 1 || max_order < 1) return ORC_ERR_INPUT;
+    int n = 3 * N;
+    double *u = malloc(sizeof(double) * (nf + 1)), *wu = malloc(sizeof(double) * (nf + 1));
+    double *A = malloc(sizeof(double) * (size_t)n * n), *V = malloc(sizeof(double) * (size_t)n * n);
+    double *lam = malloc(sizeof(double) * n), *al = malloc(sizeof(double) * N);
+    orc_sum sE = {0, 0};
+    orc_sum *so = calloc(max_order + 1, sizeof(orc_sum));
+    int rc = orc_freq_grid(nf, u, wu);
+    for (int k = 1; k <= nf && rc == ORC_OK; ++k) {
+        for (int i = 0; i < N; ++i) al[i] = alpha_iu(a0[i], om[i], u[k]);
+        memset(A, 0, sizeof(double) * (size_t)n * n);
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                if (j == i) continue;
+                double r[3] = {R[3 * j] - R[3 * i], R[3 * j + 1] - R[3 * i + 1], R[3 * j + 2] - R[3 * i + 2]};
+                double rr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                double T[9];
+                orc_T_bare(r, T);
+                double pre = sqrt(al[i] * al[j]) * orc_fermi(rr, rdamp[i] + rdamp[j], beta, a);
+                for (int x = 0; x < 3; ++x)
+                    for (int y = 0; y < 3; ++y) A[(size_t)(3 * i + x) * n + 3 * j + y] = pre * T[3 * x + y];
+            }
+        rc = orc_jacobi_eigh(n, A, lam, V);
+        for (int p = 0; p < n && rc == ORC_OK; ++p) {
+            if (!(1.0 + lam[p] > 0.0)) { rc = ORC_ERR_NEG_EIGENVALUE; break; }
+            ksum_add(&sE, wu[k] * log1p(lam[p]));
+            double lp = lam[p];   /* lambda^m */
+            for (int m = 2; m <= max_order; ++m) {
+                lp *= lam[p];
+                ksum_add(&so[m], wu[k] * ((m % 2 == 0) ? -lp : lp) / m);
+            }
+        }
+    }
+    if (rc == ORC_OK) {
+        *E = ksum_get(&sE) / (2.0 * ORC_PI);
+        for (int m = 2; m <= max_order; ++m) orders[m - 2] = ksum_get(&so[m]) / (2.0 * ORC_PI);
+    }
+    free(u); free(wu); free(A); free(V); free(lam); free(al); free(so);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Full MBD@rsSCS energy (finite) and its gradients.                          */
 /* ------------------------------------------------------------------------- */

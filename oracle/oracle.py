@@ -64,6 +64,7 @@ def lib():
             L.orc_mbd_rsscs_energy.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, P, P]
             L.orc_mbd_rsscs_gradient.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, i, P, _dp, _dp]
             L.orc_mbd_nl.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, P, P, P, P]
+            L.orc_mbd_log_energy.argtypes = [i, _dp, _dp, _dp, _dp, d, d, i, i, P, _dp]
             L.alpha_iu.argtypes = [d, d, d]
             L.alpha_iu.restype = d
             # periodic
@@ -237,6 +238,18 @@ def mbd_rsscs_gradient(R, a0ref, c6ref, rref, ratio, beta=0.83, a=6.0, n_freq=15
                                       n_freq, 0 if mode == "forward" else 1, C.byref(E), gR, gp)
     _check(rc, "mbd_rsscs_gradient")
     return E.value, gR, gp
+
+
+def mbd_log_energy(R, alpha0, omega, rdamp, beta=0.83, a=6.0, n_freq=15, max_order=2):
+    """MBD energy of given oscillators by the log formula (Eq. log-formula) on the n_freq-point
+    frequency grid, and its many-body orders E^(2..max_order) (Eq. rpa).  Returns
+    (E, orders [max_order - 1])."""
+    R = _a(R).reshape(-1, 3); N = R.shape[0]
+    E = C.c_double()
+    orders = np.zeros(max(max_order - 1, 1))
+    _check(lib().orc_mbd_log_energy(N, R, _a(alpha0), _a(omega), _a(rdamp), beta, a, n_freq, max_order,
+                                    C.byref(E), orders), "mbd_log_energy")
+    return E.value, orders[:max_order - 1]
 
 
 def mbd_nl(R, a0ref, c6ref, ra, rw, beta=0.83, a=6.0, grad=False, detail=False):
