@@ -73,10 +73,12 @@ def parse():
                     help="rsscs: MBD@rsSCS (the headline); nl: MBD-NL (Sec. 2.2: no screening, oscillators "
                          "from the free-atom reference and density-functional ratios drawn by "
                          "synthetic.nl_ratios(N, seed=7000))")
-    ap.add_argument("--kernel", choices=("tc_gemm_sym6016",), default=None,
-                    help="time one kernel alone instead of the workload (a small case for profilers): "
-                         "tc_gemm_sym6016 = the symmetric TF32x3 Newton-Schulz product of order 6016 "
-                         "(k_tc_gemm mode 2, chunks of 2 stages), about 0.9 GB on the device")
+    ap.add_argument("--kernel", choices=("tc_gemm_sym6016", "log_energy_finite2000"), default=None,
+                    help="time one kernel or route alone instead of the workload: tc_gemm_sym6016 = the "
+                         "symmetric TF32x3 Newton-Schulz product of order 6016 (k_tc_gemm mode 2, chunks of 2 "
+                         "stages; a small case for profilers, about 0.9 GB on the device); "
+                         "log_energy_finite2000 = the log-formula energy route (mbd_log_energy, orders 2) of the "
+                         "2000-atom cluster after a TF32x3 evaluation")
     return ap.parse_args()
 
 
@@ -584,8 +586,60 @@ def run_kernel(args):
     return 0
 
 
+def run_log_energy(args):
+    """The log-formula route (Eq. log-formula, FP64 Cholesky factors of I + A_k at the 15
+    nodes) of the 2000-atom cluster: --warmup + --steps calls after one TF32x3 evaluation,
+    host-clock time per call (the call synchronises), its Cholesky rate against the FP64
+    peak, the energy against the Newton-Schulz route, and the oracle's log route timed on a
+    100-atom sample of the same recipe (extrapolated by n^3)."""
+    from paper_2308_03140_gb300 import binding, build
+    from paper_2308_03140_gb300 import synthetic as syn
+    build.build()
+    binding.load()
+    sysm = syn.workload("finite2000")
+    m = binding.MBD(0, precision=binding.MBD_PREC_TF32X3)
+    m.set_geometry(sysm.coords)
+    m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, sysm.rvdw_ref, sysm.ratio)
+    E_ns = m.evaluate(False)[0]
+    for _ in range(args.warmup):
+        m.log_energy(2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        E_log, orders = m.log_energy(2)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    m.close()
+    ld = 6016
+    chol_flops = 15 * ld ** 3 / 3.0
+    peaks = measured_peaks()
+    bf16 = (peaks or {}).get("bf16_tflops_sustained") or 1700.0
+    fp64_peak = bf16 * FP64_OVER_BF16
+    line = {"kernel": "mbd_log_energy (k_build_lr_freq, batched FP64 Cholesky, k_logdiag_batch)",
+            "workload": "finite2000", "n_freq": 15, "calls": args.steps, "ms_per_call": 1e3 * dt,
+            "cholesky_tflops": chol_flops / dt / 1e12, "fp64_peak_tflops": fp64_peak,
+            "frac_of_fp64_peak": chol_flops / dt / 1e12 / fp64_peak,
+            "peak_source": ("of measured" if peaks else "of fallback") + ": bf16_tflops_sustained x nominal FP64/BF16 "
+                           "(1.25/2250)",
+            "energy_log_ha": E_log, "energy_ns_ha": E_ns, "delta_per_atom_ha": (E_log - E_ns) / sysm.n_atoms,
+            "pairwise_order_ha": float(orders[0])}
+    if not args.no_cpu_baseline:
+        import oracle as o
+        s100 = sample_system("finite2000", 100)
+        _, det = o.mbd_rsscs_energy(*o.system_args(s100), detail=True)
+        t1 = time.perf_counter()
+        o.mbd_log_energy(s100.coords, det["alpha_bar"][0], det["omega"], det["rvdw"], n_freq=15, max_order=2)
+        ts = time.perf_counter() - t1
+        line["cpu_baseline"] = {"value": 1.0 / (ts * (2000 / 100) ** 3), "unit": "calls/s",
+                                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                                "kind": "oracle", "sample": f"log route of a 100-atom cluster in {ts:.2f} s, "
+                                                            "extrapolated by (n/100)^3 to 2000 atoms"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel == "log_energy_finite2000":
+        return run_log_energy(args)
     if args.kernel:
         return run_kernel(args)
     if args.impl == "reference":

@@ -192,6 +192,22 @@ int mbd_get_lattice_gradient(mbd_ctx *ctx, double *grad_lattice);
  * alpha0 / (1 + u^2/omega^2), c6 = 3/4 alpha0^2 omega, omega, and the damping radii. */
 int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega, double *rvdw);
 
+/* MBD energy by the imaginary-frequency log formula, Eq. (log-formula), and its many-body
+ * orders, Eq. (rpa) -- a second route to the energy, for cross-checks and for the analysis
+ * of many-body contributions.  For the oscillators of the last successful evaluation
+ * (screened alpha_bar0, omega_bar and damping radii R_bar, or those of MBD-NL) and the
+ * coordinates set by mbd_set_geometry: *energy = 1/(2 pi) sum_k w_k ln det(I + A_k) with
+ * A_k = alpha(u_k)^(1/2) T^lr alpha(u_k)^(1/2), alpha_i(u) = alpha_bar0_i/(1 + u^2/omega_bar_i^2)
+ * and T^lr of Eq. (mbd-lr-dipole), over the n_freq Gauss-Legendre nodes u_k > 0 of the
+ * screening grid (Sec. 3.3) with their weights; orders[m - 2] = E^(m) =
+ * -1/(2 pi) sum_k w_k (-1)^m/m Tr A_k^m for m = 2..max_order (max_order 1..4; orders may be
+ * NULL when max_order is 1).  FP64 throughout (Cholesky factors of I + A_k; orders 3 and 4
+ * cost one n x n x n product per node).  Finite systems only.  The call reuses the screening
+ * buffers, so mbd_backward_dev needs a new evaluation afterwards.  MBD_ERR_STATE without a
+ * prior evaluation; MBD_ERR_SCS_NOT_PD if some I + A_k is not positive definite (dipole
+ * collapse). */
+int mbd_log_energy(mbd_ctx *ctx, int max_order, double *energy, double *orders);
+
 /* Statistics of the last evaluation: Newton-Schulz iterations, the scale s of
  * Y0 = Q/s, the final Frobenius norm of I - Z Y, and (mixed modes) the Frobenius norm of
  * Z Q Z - I in FP64 for the Z ~ Q^{-1/2} used (0 in FP64 mode).  Any may be NULL. */

@@ -26,7 +26,7 @@ MBD_PREC_FP64, MBD_PREC_TF32, MBD_PREC_BF16X3, MBD_PREC_TF32X3 = 0, 1, 2, 3
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
            "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_backward_dev",
            "mbd_get_lattice_gradient", "mbd_set_scs_model", "mbd_get_learned_stats", "mbd_screen",
-           "mbd_get_scs_detail",
+           "mbd_get_scs_detail", "mbd_log_energy",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
            "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
            "mbdk_cholesky_solve3_f64_noalloc", "mbdk_scs_features", "mbdk_mlp_forward", "mbdk_mlp_backward",
@@ -84,6 +84,7 @@ def load(path: str | None = None):
     L.mbd_get_learned_stats.argtypes = [vp, _P, C.POINTER(C.c_int)]
     L.mbd_screen.argtypes = [vp, _P, _P, _P, _P, _P]
     L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P, _P]
+    L.mbd_log_energy.argtypes = [vp, C.c_int, _P, _P]
     L.mbd_get_exception.argtypes = [vp, C.POINTER(C.c_int), C.c_char_p, C.c_char_p, sz]
     L.mbd_set_profiling.argtypes = [vp, i]
     L.mbd_get_profile.argtypes = [vp, C.POINTER(mbd_profile)]
@@ -283,6 +284,14 @@ class MBD:
         p = mbd_profile()
         self._check(self.lib.mbd_get_profile(self.h, C.byref(p)))
         return {k: getattr(p, k) for k, _ in mbd_profile._fields_}
+
+    def log_energy(self, max_order: int = 2):
+        """MBD energy by the log formula and its many-body orders for the oscillators of the
+        last evaluation (mbd_log_energy): returns (energy, orders [max_order - 1] = E^(2..))."""
+        E = C.c_double()
+        orders = np.zeros(max(max_order - 1, 1))
+        self._check(self.lib.mbd_log_energy(self.h, max_order, C.byref(E), _ptr(orders) if max_order > 1 else None))
+        return E.value, orders[:max_order - 1]
 
     def stats(self):
         it, sc, res, cr = C.c_int(), C.c_double(), C.c_double(), C.c_double()

@@ -211,6 +211,20 @@ void nl_params(const AtomBufs &b, int *status, cudaStream_t s);
 // *scale (device) if given.
 void nl_chain(const AtomBufs &b, const MbdGradOut &o, const double *scale, double *gp, cudaStream_t s);
 
+// Log-formula energy route (k_logdet.cu), Eqs. (log-formula), (rpa).  build_lr_freq: the nf
+// matrices A_k = alpha(u_k)^{1/2} T^lr alpha(u_k)^{1/2} of the oscillators abar0, ombar, rbar
+// on the nodes u_1..u_nf (b.u), ld x ld each, mstride apart, zero outside the 3N x 3N
+// block and on the diagonal blocks.  batch_dot: out[b] = <X_b, Y_b> over `per` elements.
+// add_identity_batch: A_b += I.  logdiag_batch: out[b] = sum_p ln L_b,pp (ST_SCS_NOT_PD on a
+// non-positive diagonal).
+cudaError_t build_lr_freq(const AtomBufs &b, double beta, double a, double *A, long long ld, long long mstride,
+                          int nf, int *status, cudaStream_t s);
+cudaError_t batch_dot(const double *X, const double *Y, long long per, long long stride, int batch, double *out,
+                      cudaStream_t s);
+void add_identity_batch(double *A, long long ld, long long mstride, int batch, cudaStream_t s);
+void logdiag_batch(const double *L, long long ld, long long mstride, int batch, double *out, int *status,
+                   cudaStream_t s);
+
 // TS-scaling chain to [4][N] parameter gradients, times *scale (device) if given.
 void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv,
               const double *scale, double *gp, cudaStream_t s);

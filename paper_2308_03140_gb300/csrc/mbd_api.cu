@@ -136,6 +136,7 @@ struct mbd_ctx {
     float *sM = nullptr, *sdinv = nullptr, *swork = nullptr;   // FP32 factors of the mixed modes
     uint32_t *spanel = nullptr;   // TF32x3 parts of the factor panels (tensor-core trailing updates)
     float *sgrad32 = nullptr;     // FP32 inputs of the reduced-precision SCS adjoint pair pass
+    double *dlog = nullptr;       // per-frequency sums of the log-formula route: ln det, Tr A^2..4
     double *dQ, *dZ, *dP, *dY2, *dZ2;
     // mixed-precision Newton-Schulz buffers (ld x ld each)
     float *fY = nullptr, *fZ = nullptr, *fY2 = nullptr, *fZ2 = nullptr, *fP = nullptr, *fPT = nullptr;
@@ -297,7 +298,7 @@ int allocate(mbd_ctx *ctx) {
         {&ctx->dR, 3 * N}, {&ctx->da0ref, N}, {&ctx->dc6ref, N}, {&ctx->drref, N}, {&ctx->dratio, N},
         {&ctx->da0, N}, {&ctx->dom, N}, {&ctx->drv, N}, {&ctx->dalu, nf1 * N}, {&ctx->dsigu, nf1 * N},
         {&ctx->dabar, nf1 * N}, {&ctx->dabar0, N}, {&ctx->dc6bar, N}, {&ctx->dombar, N},
-        {&ctx->drbar, N}, {&ctx->du, nf1}, {&ctx->dwu, nf1},
+        {&ctx->drbar, N}, {&ctx->du, nf1}, {&ctx->dwu, nf1}, {&ctx->dlog, 4 * nf1},
         {&ctx->ddinv, nf1 * nb * 4096}, {&ctx->dX, nf1 * ld * 3}, {&ctx->dV, nf1 * ld * 3},
         {&ctx->dB, nf1 * ld * 3},
         {&ctx->dh, nf1 * N}, {&ctx->dgomb, N}, {&ctx->dgab0, N}, {&ctx->dgrb, N}, {&ctx->dgR, 3 * N},
@@ -1464,6 +1465,54 @@ int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega
     if (c6) MBD_CUDA(cudaMemcpy(c6, ctx->dc6bar, sizeof(double) * N, cudaMemcpyDeviceToHost), "mbd_get_scs_detail");
     if (omega) MBD_CUDA(cudaMemcpy(omega, ctx->dombar, sizeof(double) * N, cudaMemcpyDeviceToHost), "mbd_get_scs_detail");
     if (rvdw) MBD_CUDA(cudaMemcpy(rvdw, ctx->drbar, sizeof(double) * N, cudaMemcpyDeviceToHost), "mbd_get_scs_detail");
+    return MBD_OK;
+}
+
+int mbd_log_energy(mbd_ctx *ctx, int max_order, double *energy, double *orders) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (!energy || max_order < 1 || max_order > 4 || (max_order > 1 && !orders))
+        return fail(ctx, MBD_ERR_INPUT, "mbd_log_energy", "energy is required; max_order 1..4; orders for max_order > 1");
+    if (ctx->periodic) return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_log_energy", "finite systems only");
+    if (!ctx->have_screening)
+        return fail(ctx, MBD_ERR_STATE, "mbd_log_energy", "no oscillators: evaluate the system first");
+    MBD_CUDA(cudaSetDevice(ctx->device), "mbd_log_energy");
+    cudaStream_t s = ctx->stream;
+    const int N = ctx->N, nf = ctx->nf1 - 1;
+    const long long ld = ctx->ld, mat = ld * ld;
+    MBD_CUDA(cudaMemcpyAsync(ctx->dR, ctx->hR.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s),
+             "mbd_log_energy");
+    MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_log_energy");
+    const AtomBufs b = atom_bufs(ctx, Inputs{ctx->dR, ctx->da0ref, ctx->dc6ref, ctx->drref, ctx->dratio});
+    double *A = ctx->dM + mat;   // the nodes u_1..u_nf in screening slots 1..nf
+    double *sums = ctx->dlog;    // [4][nf]: sum ln L_pp, Tr A^2, Tr A^3, Tr A^4
+    MBD_CUDA(build_lr_freq(b, ctx->opt.beta, ctx->opt.a, A, ld, mat, nf, ctx->dstatus, s), "mbd_log_energy");
+    if (max_order >= 2) MBD_CUDA(batch_dot(A, A, mat, mat, nf, sums + nf, s), "mbd_log_energy");   // A symmetric
+    if (max_order >= 3) {
+        const int M = static_cast<int>(ld);
+        for (int k = 0; k < nf; ++k) {   // P = A_k^2 (symmetric), then <P, A_k> and |P|^2
+            GemmArgs g{A + k * mat, A + k * mat, nullptr, ctx->dP, ld, ld, 0, ld, 0, 0, 0, 0, M, M, M, 1, 1.0, 0.0, 2, 0};
+            gemm_f64(g, s);
+            MBD_CUDA(batch_dot(ctx->dP, A + k * mat, mat, 0, 1, sums + 2 * nf + k, s), "mbd_log_energy");
+            if (max_order >= 4) MBD_CUDA(batch_dot(ctx->dP, ctx->dP, mat, 0, 1, sums + 3 * nf + k, s), "mbd_log_energy");
+        }
+    }
+    add_identity_batch(A, ld, mat, nf, s);
+    cholesky_f64(A, ld, mat, nf, ctx->ddinv, ctx->dstatus, s);
+    logdiag_batch(A, ld, mat, nf, sums, ctx->dstatus, s);
+    std::vector<double> h(4 * nf);
+    MBD_CUDA(cudaMemcpyAsync(h.data(), sums, sizeof(double) * 4 * nf, cudaMemcpyDeviceToHost, s), "mbd_log_energy");
+    ctx->have_forward = false;   // the screening buffers now hold these factors
+    int rc = read_status(ctx, s, "mbd_log_energy");
+    if (rc) return rc;
+    const double inv2pi = 1.0 / (2.0 * 3.141592653589793238462643383279502884);
+    double e = 0.0;
+    for (int k = 0; k < nf; ++k) e += ctx->hwu[k + 1] * 2.0 * h[k];   // ln det = 2 sum ln L_pp
+    *energy = e * inv2pi;
+    for (int m = 2; m <= max_order; ++m) {
+        double t = 0.0;
+        for (int k = 0; k < nf; ++k) t += ctx->hwu[k + 1] * h[(m - 1) * nf + k];
+        orders[m - 2] = -inv2pi * ((m % 2 == 0) ? 1.0 : -1.0) / m * t;   // -(-1)^m/m Tr A^m
+    }
     return MBD_OK;
 }
 
