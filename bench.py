@@ -194,6 +194,23 @@ def cpu_baseline(workload: str, n_sample: int, n_target: int, method: str = "rss
             "sample_seconds": dt}
 
 
+def reduce_max(x: float, world: int, device) -> float:
+    """The largest x over the ranks of the process group (x itself when world == 1): the
+    timed region of a multi-rank run ends when its slowest rank does."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(units_per_rank: int, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -247,12 +264,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
+        return reduce_max(x, world, dev)
 
     sysm = syn.workload(args.workload)
     periodic = sysm.lattice is not None
@@ -301,7 +313,7 @@ def run_ours(args):
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     st = m.stats()
     E = energy.item()
-    value = world * args.steps / (ms / 1e3)
+    value = whole_job_rate(args.steps, world, ms / 1e3)
 
     # end to end through the C ABI with host buffers
     m.set_profiling(False)
