@@ -185,8 +185,14 @@ void energy_trace(const double *Y, long long ld, int n, const double *ombar, int
 // MBD gradient pass (Eq. mbd-gradient): reads Z (Q^{-1/2} = zscale * Z) once.
 // Per atom: g_ombar (incl. the diagonal block and -3/2), g_abar0, g_rbar, gR [N][3].
 struct MbdGradOut { double *g_ombar, *g_abar0, *g_rbar, *gR; };
+// tq: per-atom Tr (Q^{1/2})_ii for dE/d omega_bar (second order in the error of Z), or NULL to
+// take it from Z itself.
 void mbd_grad_pass(const AtomBufs &b, double beta, double a, const double *Z, long long ld,
-                   double zscale, const MbdGradOut &o, cudaStream_t s);
+                   double zscale, const MbdGradOut &o, cudaStream_t s, const double *tq = nullptr);
+// tq_i = sqrt_s Tr(X_ii), X = (3 V - V W)/2, for V = (Q/s) Z and W = Z V in FP64 with
+// Z ~ (Q/s)^{-1/2}: Tr X_ii is second order in the error of Z (X ~ (Q/s)^{1/2}).
+void block_trace_sqrt(const double *V, const double *W, long long ld, int N, double sqrt_s, double *tq,
+                      cudaStream_t s);
 
 // Chain through Eqs. (casimir-polder), (scale-rvdw-scs): h[k][i] = dE/d abar_i(u_k),
 // and the direct parts of dE/d alpha0, dE/d R_vdW (g_a0, g_rv, overwritten).  Also

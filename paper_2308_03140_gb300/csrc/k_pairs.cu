@@ -265,8 +265,12 @@ __global__ void k_energy(const double *Y, long long ld, int n, const double *omb
 //                            g_rbar[i] += 1/2 c_i c_j dg/dS <G_ij, T>
 //                            gR[i]     -= 1/2 c_i c_j <G_ij, d(gT)/dr>,  r = R_j - R_i
 // (both blocks (i,j) and (j,i) of the symmetric sum are folded into the factor 1/2).
+// tq (optional): Tr (Q^{1/2})_ii per atom.  dE/d omega_bar_i = Tr (Z Q)_ii / (2 omega_bar_i) - 3/2
+// exactly (diagonal and coupling terms of dQ/d omega_bar_i); two terms of ~1.5 cancel there, so
+// a Z with a relative error e gives an absolute error ~e.  With tq (second order in the error
+// of Z) the difference is taken from it instead.
 __global__ void __launch_bounds__(128) k_mbd_grad(AtomBufs b, double beta, double a, const double *Z,
-                                                  long long ld, double zscale, MbdGradOut o) {
+                                                  long long ld, double zscale, MbdGradOut o, const double *tq) {
     const int i = blockIdx.x;
     const double ci = b.ombar[i] * sqrt(b.abar0[i]);
     const double Ri[3] = {b.R[3 * i], b.R[3 * i + 1], b.R[3 * i + 2]};
@@ -304,7 +308,8 @@ __global__ void __launch_bounds__(128) k_mbd_grad(AtomBufs b, double beta, doubl
         const double sa = sqrt(b.abar0[i]);
         const double trd = Z[(3LL * i) * ld + 3 * i] + Z[(3LL * i + 1) * ld + 3 * i + 1] +
                            Z[(3LL * i + 2) * ld + 3 * i + 2];
-        const double g_om = 0.25 * zscale * trd * 2.0 * b.ombar[i] - 1.5 + acc[0] * sa;
+        const double g_om = tq ? tq[i] / (2.0 * b.ombar[i]) - 1.5
+                               : 0.25 * zscale * trd * 2.0 * b.ombar[i] - 1.5 + acc[0] * sa;
         o.g_ombar[i] = g_om;
         o.g_abar0[i] = acc[0] * b.ombar[i] / (2.0 * sa);
         o.g_rbar[i] = acc[1];
@@ -535,9 +540,9 @@ void energy_trace(const double *Y, long long ld, int n, const double *ombar, int
 }
 
 void mbd_grad_pass(const AtomBufs &b, double beta, double a, const double *Z, long long ld,
-                   double zscale, const MbdGradOut &o, cudaStream_t s) {
+                   double zscale, const MbdGradOut &o, cudaStream_t s, const double *tq) {
     count_launches(1);
-    k_mbd_grad<<<b.N, 128, 0, s>>>(b, beta, a, Z, ld, zscale, o);
+    k_mbd_grad<<<b.N, 128, 0, s>>>(b, beta, a, Z, ld, zscale, o, tq);
 }
 
 void chain_screen(const AtomBufs &b, const MbdGradOut &o, double *h, double *g_a0, double *g_rv,

@@ -630,6 +630,27 @@ __global__ void k_split_panel_tf32(const float *A, long long ld, long long mstri
     }
 }
 
+// tq[i] = sqrt_s (3 Tr V_ii - Tr (V W)_ii) / 2 over the 3x3 diagonal block of atom i; one
+// warp per atom, (V W)_pp = sum_k V[p][k] W[k][p] with the rows of V read coalesced.
+__global__ void __launch_bounds__(128) k_block_trace_sqrt(const double *V, const double *W, long long ld, int N,
+                                                         double sqrt_s, double *tq) {
+    const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= N) return;
+    double acc = 0.0;
+    for (int x = 0; x < 3; ++x) {
+        const long long p = 3LL * i + x;
+        const double *vp = V + p * ld;
+        for (long long k = lane; k < ld; k += 32) acc += vp[k] * W[k * ld + p];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        const long long p = 3LL * i;
+        const double trv = V[p * ld + p] + V[(p + 1) * ld + p + 1] + V[(p + 2) * ld + p + 2];
+        tq[i] = sqrt_s * 0.5 * (3.0 * trv - acc);
+    }
+}
+
 // Out[p][q] = scale * A[p][p] * B[p][q] (row scaling by a diagonal, FP64).
 template <typename TA, typename TB>
 __global__ void k_diag_scale_rows(const TA *A, const TB *B, long long ld, double scale, double *Out) {
@@ -833,6 +854,12 @@ void split_tf32_f32(const float *Z, long long ld, int zero_diag, void *H, void *
     count_launches(1);
     k_split_tf32_f32<<<grid_for(ld * ld), 256, 0, s>>>(Z, ld * ld, ld, zero_diag, static_cast<uint32_t *>(H),
                                                        static_cast<uint32_t *>(L));
+}
+
+void block_trace_sqrt(const double *V, const double *W, long long ld, int N, double sqrt_s, double *tq,
+                      cudaStream_t s) {
+    count_launches(1);
+    k_block_trace_sqrt<<<(N + 3) / 4, 128, 0, s>>>(V, W, ld, N, sqrt_s, tq);
 }
 
 void split_panel_tf32(const float *A, long long ld, long long mstride, int batch, long long rows, int cols,

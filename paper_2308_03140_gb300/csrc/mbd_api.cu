@@ -137,6 +137,8 @@ struct mbd_ctx {
     uint32_t *spanel = nullptr;   // TF32x3 parts of the factor panels (tensor-core trailing updates)
     float *sgrad32 = nullptr;     // FP32 inputs of the reduced-precision SCS adjoint pair pass
     double *dlog = nullptr;       // per-frequency sums of the log-formula route: ln det, Tr A^2..4
+    double *dtq = nullptr;        // Tr (Q^{1/2})_ii per atom from the mixed modes' FP64 correction
+    bool tq_valid = false;
     double *dQ, *dZ, *dP, *dY2, *dZ2;
     // mixed-precision Newton-Schulz buffers (ld x ld each)
     float *fY = nullptr, *fZ = nullptr, *fY2 = nullptr, *fZ2 = nullptr, *fP = nullptr, *fPT = nullptr;
@@ -298,7 +300,7 @@ int allocate(mbd_ctx *ctx) {
         {&ctx->dR, 3 * N}, {&ctx->da0ref, N}, {&ctx->dc6ref, N}, {&ctx->drref, N}, {&ctx->dratio, N},
         {&ctx->da0, N}, {&ctx->dom, N}, {&ctx->drv, N}, {&ctx->dalu, nf1 * N}, {&ctx->dsigu, nf1 * N},
         {&ctx->dabar, nf1 * N}, {&ctx->dabar0, N}, {&ctx->dc6bar, N}, {&ctx->dombar, N},
-        {&ctx->drbar, N}, {&ctx->du, nf1}, {&ctx->dwu, nf1}, {&ctx->dlog, 4 * nf1},
+        {&ctx->drbar, N}, {&ctx->du, nf1}, {&ctx->dwu, nf1}, {&ctx->dlog, 4 * nf1}, {&ctx->dtq, N},
         {&ctx->ddinv, nf1 * nb * 4096}, {&ctx->dX, nf1 * ld * 3}, {&ctx->dV, nf1 * ld * 3},
         {&ctx->dB, nf1 * ld * 3},
         {&ctx->dh, nf1 * N}, {&ctx->dgomb, N}, {&ctx->dgab0, N}, {&ctx->dgrb, N}, {&ctx->dgR, 3 * N},
@@ -523,7 +525,7 @@ void backward_passes(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const doub
     const long long ld = ctx->ld, mat = ld * ld, xs = 3 * ld;
     const double beta = ctx->opt.beta, a = ctx->opt.a;
     MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
-    mbd_grad_pass(b, beta, a, ctx->Zlast, ld, ctx->zscale, go, s);
+    mbd_grad_pass(b, beta, a, ctx->Zlast, ld, ctx->zscale, go, s, ctx->tq_valid ? ctx->dtq : nullptr);
     if (ctx->opt.scs_mode == MBD_SCS_NL) {   // MBD-NL: only the chain through Eqs. mbd-nl-*
         if (grad_params) nl_chain(b, go, grad_energy, grad_params, s);
         if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
@@ -707,6 +709,9 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
         }
         energy_correction(ctx->dQ, 1.0 / sc, Zs, V64, W64, ld, n, std::sqrt(sc), ctx->dombar, N,
                           ctx->dscal + 8 + 2 * 64, energy_out, ctx->dscal + 3, s);
+        // diagonal blocks of Q^{1/2}, second order in the error of Zs, for dE/d omega_bar
+        block_trace_sqrt(V64, W64, ld, N, std::sqrt(sc), ctx->dtq, s);
+        ctx->tq_valid = true;
     }
     double *Zd = ctx->dZ;
     to_f64(Z.f, ld, 1.0 / std::sqrt(sc), Zd, s);   // Q^{-1/2} for the gradient
@@ -919,6 +924,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     const double beta = ctx->opt.beta, a = ctx->opt.a;
     ctx->have_result = false;
     ctx->have_screening = false;
+    ctx->tq_valid = false;
     ctx->ev_used = 0;
     ctx->prof = mbd_profile{};
     const long long launches0 = launch_count();
@@ -1099,7 +1105,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         // energy-error estimate from the adjoints h = dE/d alpha_bar(u) and the members' spread;
         // above the threshold the evaluation is redone with plain screening
         MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
-        mbd_grad_pass(b, beta, a, ctx->Zlast, ld, ctx->zscale, go, s);
+        mbd_grad_pass(b, beta, a, ctx->Zlast, ld, ctx->zscale, go, s, ctx->tq_valid ? ctx->dtq : nullptr);
         chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, ctx->dV, ld, xs, s);
         learned_estimate(N, nf1, ctx->dh, ctx->dspread, ctx->dscal + 5, s);
         double est = 0.0;

@@ -121,11 +121,10 @@ def _eval(sysm, precision):
 # looser bound and reported, not used for the headline.
 # Measured (GB300, 2-stage chunks, N = 500 / 2000): |dE|/N about 3.4e-6 (TF32), 6e-9
 # (BF16x3), 6e-9 (TF32x3) Ha/atom; largest force error 2.5 / 0.09 / 0.008 (N = 500) and
-# 20 / 0.17 / 0.011 (N = 2000) of the largest force.  Forces of the mixed modes take the
-# tensor-core Q^{-1/2} at first order (the energy only at second).  For TF32 and BF16x3 its
-# commutator drift dominates; for TF32x3 the pair terms over Z are accurate (MBD-NL forces at
-# 2000 atoms: 1.2e-8 Ha/bohr) and the error comes from dE/d omega_bar = 1/2 omega_bar Tr Z_ii
-# - 3/2, two terms of ~1.5 that cancel, which the chain into the screening carries to the forces.
+# 20 / 0.17 / 0.011 (N = 2000) of the largest force, the TF32x3 figure before dE/d omega_bar
+# was taken from the second-order block traces of Q^{1/2} (now 3.2e-6 of the largest force at
+# N = 2000).  Forces of the mixed modes take the tensor-core Q^{-1/2} at first order (the
+# energy only at second); for TF32 and BF16x3 its commutator drift dominates.
 E_BOUND = {binding.MBD_PREC_TF32: 2e-5, binding.MBD_PREC_BF16X3: 1e-6, binding.MBD_PREC_TF32X3: 1e-6}
 F_BOUND = {binding.MBD_PREC_TF32: 50.0, binding.MBD_PREC_BF16X3: 0.5, binding.MBD_PREC_TF32X3: 0.1}
 
