@@ -3,12 +3,16 @@
 //
 //   C = alpha * sum_p A_p B_p^T + beta * D      (FP32 accumulate in tensor memory)
 //
-// with K-major operands (rows of A and of B run along K).  Two operand kinds:
+// with K-major operands (rows of A and of B run along K).  Three operand kinds:
 //   TF32   one product, operands stored as FP32 (kind::tf32 uses their top 19 bits);
 //   BF16x3 three products A_hi B_hi + A_hi B_lo + A_lo B_hi, operands stored as bf16
-//          hi/lo pairs (X = X_hi + X_lo), about 16 significant bits per product.
-// One CTA (6 warps) computes one 128x128 output tile.  Operand tiles of 128 rows x 128
-// bytes are staged in shared memory by TMA (128-byte swizzle) through an mbarrier ring;
+//          hi/lo pairs (X = X_hi + X_lo), about 16 significant bits per product;
+//   TF32x3 the same three products with TF32 hi and TF32-rounded remainder parts.
+// The kernel is persistent: one CTA (6 warps) per SM loops over 128x128 output tiles (and
+// the items of a batched product), its stage and chunk counters running on across tiles so
+// that the next tile's loads and MMAs overlap the last tile's epilogue.  Operand tiles of
+// 128 rows x 128 bytes are staged in shared memory by TMA (128-byte swizzle) through an
+// mbarrier ring;
 // warp 4 issues the TMA loads, warp 5 issues tcgen05.mma.  K is split into chunks of
 // `chunk_stages` stages, each accumulated afresh in one of two 128-column TMEM buffers;
 // warps 0-3 (one tile row per thread) read each finished chunk back (tcgen05.ld 32x32b)
