@@ -17,6 +17,8 @@
 
 #include "../../include/mbd_gb300.h"
 #include "../../include/mbd_gb300_kernels.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using namespace mbdgb;
@@ -225,6 +227,20 @@ cudaEvent_t next_event(mbd_ctx *ctx) {
 }
 
 struct Span { cudaEvent_t a = nullptr, b = nullptr; double flops = 0.0; };
+
+// NVTX ranges of the evaluation stages on the host timeline (no-ops unless a profiler is
+// attached); the range open at any return is closed by the destructor.
+struct NvtxStages {
+    bool open = false;
+    void next(const char *name) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~NvtxStages() {
+        if (open) nvtxRangePop();
+    }
+};
 
 void mark(mbd_ctx *ctx, cudaStream_t s, cudaEvent_t &e) {
     if (!ctx->profiling) return;
@@ -786,6 +802,8 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
     };
     const AtomBufs b = atom_bufs(ctx, in);
     const PeriodicBufs pb = periodic_bufs(ctx);
+    NvtxStages nv;
+    nv.next("mbd screening (periodic)");
     mark(ctx, s, e_start);
     MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_evaluate");
     // ---- Gamma-point screening (MBD-NL: the oscillators directly) ----
@@ -802,6 +820,7 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
         contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
     }
     mark(ctx, s, e_scs);
+    nv.next("mbd coupled oscillators and Newton-Schulz");
     int rc = read_status(ctx, s, "screening");
     if (rc) return rc;
     ctx->have_screening = true;
@@ -891,6 +910,7 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
     ctx->Zlast = Z;
     ctx->zscale = 1.0 / ss;
     mark(ctx, s, e_ns);
+    nv.next("mbd gradient");
     if (want_grad) backward_periodic(ctx, s, b, nullptr, out.grad_coords, out.grad_params);
     if (out.alpha_scs)
         MBD_CUDA(cudaMemcpyAsync(out.alpha_scs, ctx->dabar0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s),
@@ -942,6 +962,8 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     const double flops_full = 2.0 * nd * nd * nd, flops_sym = nd * nd * (nd + 1.0);
     ctx->have_forward = false;
     const AtomBufs b = atom_bufs(ctx, in);
+    NvtxStages nv;
+    nv.next("mbd screening");
     mark(ctx, s, e_start);
     MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_evaluate");
     // ---- screening (Sec. 2.3) ----
@@ -979,6 +1001,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         contract_screen(b, ctx->dX, ld, xs, ctx->dstatus, s);
     }
     mark(ctx, s, e_scs);
+    nv.next("mbd coupled oscillators and Newton-Schulz");
     int rc = read_status(ctx, s, "screening");
     if (rc) return rc;
     ctx->have_screening = true;
@@ -1101,6 +1124,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         if (rc) return rc;
     }
     mark(ctx, s, e_ns);
+    nv.next("mbd gradient");
     if (learned) {
         // energy-error estimate from the adjoints h = dE/d alpha_bar(u) and the members' spread;
         // above the threshold the evaluation is redone with plain screening
