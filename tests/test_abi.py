@@ -45,3 +45,34 @@ def test_default_options(lib):
 def test_library_is_sm103a_only():
     # the build passes exactly one -gencode, for sm_103a
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _create(lib, **fields):
+    opt = binding.mbd_options()
+    lib.mbd_default_options(C.byref(opt))
+    for k, v in fields.items():
+        setattr(opt, k, v)
+    h = C.c_void_p()
+    return lib.mbd_create(C.byref(h), 0, C.byref(opt)), h
+
+
+@pytest.mark.parametrize("field,value", [("n_freq", 0), ("n_freq", 10 ** 6), ("beta", 0.0), ("a", -1.0),
+                                         ("ns_max_iter", 0), ("ns_tol", 0.0), ("precision", 9),
+                                         ("tc_chunk_stages", -1), ("scs_mode", 3), ("learned_max_error", 0.0)])
+def test_create_rejects_invalid_options_before_touching_the_device(lib, field, value):
+    rc, h = _create(lib, **{field: value})
+    assert rc == 1 and not h.value   # MBD_ERR_INPUT, no context
+
+
+def test_create_accepts_every_method_and_precision(lib):
+    # valid options pass validation; without a GPU the device query then fails (MBD_ERR_CUDA)
+    import torch
+    for mode in (binding.MBD_SCS_PLAIN, binding.MBD_SCS_LEARNED, binding.MBD_SCS_NL):
+        for prec in (binding.MBD_PREC_FP64, binding.MBD_PREC_TF32, binding.MBD_PREC_BF16X3, binding.MBD_PREC_TF32X3):
+            rc, h = _create(lib, scs_mode=mode, precision=prec)
+            if torch.cuda.is_available():
+                assert rc == 0
+                lib.mbd_destroy(h)
+            else:
+                assert rc == 6 and not h.value   # MBD_ERR_CUDA
+    assert lib.mbd_destroy(None) == 0
