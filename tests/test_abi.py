@@ -76,3 +76,18 @@ def test_create_accepts_every_method_and_precision(lib):
             else:
                 assert rc == 6 and not h.value   # MBD_ERR_CUDA
     assert lib.mbd_destroy(None) == 0
+
+
+def test_binding_marshalling():
+    import numpy as np
+    import torch
+    a = binding._f64([[1, 2, 3], [4, 5, 6]], (-1, 3))
+    assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == (2, 3)
+    b = binding._f64(np.arange(12.0).reshape(3, 4)[:, ::2])   # strided input is copied densely
+    assert b.flags.c_contiguous and b.tolist() == [[0.0, 2.0], [4.0, 6.0], [8.0, 10.0]]
+    with pytest.raises(ValueError):
+        binding._f64([1.0, 2.0], (-1, 3))
+    t = torch.zeros(4, 6, dtype=torch.float64)
+    assert binding._tptr(t).value == t.data_ptr() and binding._tptr(None) is None
+    with pytest.raises(ValueError):
+        binding._tptr(t.t())                                  # a transposed view is refused
