@@ -208,6 +208,16 @@ int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega
  * collapse). */
 int mbd_log_energy(mbd_ctx *ctx, int max_order, double *energy, double *orders);
 
+/* TS pairwise dispersion (Sec. 2.2: Eq. pairwise with the oscillators of Eq. ts-scaling and the
+ * damping of Eq. fermi-damping with steepness 20 and s_R = s_r, which depends on the
+ * short-range model) for the geometry and free-atom parameters set above:
+ * E = -1/2 sum_{i != j} C6_ij f_ij / R_ij^6, C6_ij = 3/2 alpha0_i alpha0_j / (1/omega_i + 1/omega_j).
+ * Host outputs: *energy (Ha), grad_coords [n_atoms][3] and grad_params [4][n_atoms]
+ * (dE/d alpha0_ref, c6_ref, rvdw_ref, volume ratio), either may be NULL.  FP64.  Finite
+ * systems only (MBD_ERR_UNSUPPORTED for cells and in MBD-NL mode).  The call reuses gradient
+ * scratch, so mbd_backward_dev needs a new evaluation afterwards. */
+int mbd_ts_energy(mbd_ctx *ctx, double s_r, double *energy, double *grad_coords, double *grad_params);
+
 /* Statistics of the last evaluation: Newton-Schulz iterations, the scale s of
  * Y0 = Q/s, the final Frobenius norm of I - Z Y, and (mixed modes) the Frobenius norm of
  * Z Q Z - I in FP64 for the Z ~ Q^{-1/2} used (0 in FP64 mode).  Any may be NULL. */

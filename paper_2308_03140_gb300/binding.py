@@ -26,7 +26,7 @@ MBD_PREC_FP64, MBD_PREC_TF32, MBD_PREC_BF16X3, MBD_PREC_TF32X3 = 0, 1, 2, 3
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
            "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_backward_dev",
            "mbd_get_lattice_gradient", "mbd_set_scs_model", "mbd_get_learned_stats", "mbd_screen",
-           "mbd_get_scs_detail", "mbd_log_energy",
+           "mbd_get_scs_detail", "mbd_log_energy", "mbd_ts_energy",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
            "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
            "mbdk_cholesky_solve3_f64_noalloc", "mbdk_scs_features", "mbdk_mlp_forward", "mbdk_mlp_backward",
@@ -85,6 +85,7 @@ def load(path: str | None = None):
     L.mbd_screen.argtypes = [vp, _P, _P, _P, _P, _P]
     L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P, _P]
     L.mbd_log_energy.argtypes = [vp, C.c_int, _P, _P]
+    L.mbd_ts_energy.argtypes = [vp, C.c_double, _P, _P, _P]
     L.mbd_get_exception.argtypes = [vp, C.POINTER(C.c_int), C.c_char_p, C.c_char_p, sz]
     L.mbd_set_profiling.argtypes = [vp, i]
     L.mbd_get_profile.argtypes = [vp, C.POINTER(mbd_profile)]
@@ -292,6 +293,16 @@ class MBD:
         orders = np.zeros(max(max_order - 1, 1))
         self._check(self.lib.mbd_log_energy(self.h, max_order, C.byref(E), _ptr(orders) if max_order > 1 else None))
         return E.value, orders[:max_order - 1]
+
+    def ts_energy(self, s_r: float = 0.94, gradients: bool = True):
+        """TS pairwise energy (mbd_ts_energy) of the system set above: (energy,
+        grad_coords [N,3] | None, grad_params [4,N] | None)."""
+        N = self.n_atoms
+        E = C.c_double()
+        gR = np.zeros((N, 3)) if gradients else None
+        gp = np.zeros((4, N)) if gradients else None
+        self._check(self.lib.mbd_ts_energy(self.h, s_r, C.byref(E), _ptr(gR), _ptr(gp)))
+        return E.value, gR, gp
 
     def stats(self):
         it, sc, res, cr = C.c_int(), C.c_double(), C.c_double(), C.c_double()

@@ -231,6 +231,12 @@ void add_identity_batch(double *A, long long ld, long long mstride, int batch, c
 void logdiag_batch(const double *L, long long ld, long long mstride, int batch, double *out, int *status,
                    cudaStream_t s);
 
+// TS pairwise dispersion (Eqs. pairwise, ts-scaling, fermi-damping with steepness 20 and
+// s_R = s_r) of the TS-scaled oscillators b.a0, b.om, b.rv (prepare_atoms): per-atom energy
+// eatom [N] (E = sum), dE/dR [N][3] and dE/d(a0, om, rv) of the scaled oscillators [N] each.
+void ts_pairs(const AtomBufs &b, double s_r, double *eatom, double *gR, double *ga0, double *gom, double *grv,
+              cudaStream_t s);
+
 // TS-scaling chain to [4][N] parameter gradients, times *scale (device) if given.
 void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv,
               const double *scale, double *gp, cudaStream_t s);

@@ -459,6 +459,46 @@ __global__ void k_scs_grad_inputs_f32(const double *X, const double *V, const do
     }
 }
 
+// TS pairwise dispersion (Sec. 2.2, Eq. pairwise with the TS oscillators of Eq. ts-scaling and
+// the damping of Eq. fermi-damping, steepness 20): one CTA per atom i, threads over j.  For
+// the pair (i, j) the energy is -C6_ij h(r), h = f/r^6, C6_ij = 3/2 a_i a_j w_i w_j / (w_i + w_j)
+// (the two ordered terms of -1/2 sum_{i != j}).  Per atom: eatom[i] = -1/2 sum_j C6_ij h_ij;
+// dE/dR_i = sum_j C6_ij h'(r) r_hat (r = R_j - R_i); dE/d a_i, dE/d w_i, dE/d R_vdW,i of the
+// TS-scaled oscillators (b.a0, b.om, b.rv) into ga0, gom, grv.
+__global__ void __launch_bounds__(128) k_ts_pairs(AtomBufs b, double s_r, double *eatom, double *gR, double *ga0,
+                                                  double *gom, double *grv) {
+    const int i = blockIdx.x;
+    const double ai = b.a0[i], wi = b.om[i], rvi = b.rv[i];
+    const double Ri[3] = {b.R[3 * i], b.R[3 * i + 1], b.R[3 * i + 2]};
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};   // e, gR x3, ga0, gom, grv
+    for (int j = threadIdx.x; j < b.N; j += 128) {
+        if (j == i) continue;
+        const double r[3] = {b.R[3 * j] - Ri[0], b.R[3 * j + 1] - Ri[1], b.R[3 * j + 2] - Ri[2]};
+        const double rho2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2], rho = sqrt(rho2);
+        const double aj = b.a0[j], wj = b.om[j];
+        const double c6 = 1.5 * ai * aj * wi * wj / (wi + wj);
+        const Fermi f = fermi(rho, rvi + b.rv[j], s_r, 20.0);
+        const double ir6 = 1.0 / (rho2 * rho2 * rho2);
+        const double h = f.f * ir6, dh = f.df_drho * ir6 - 6.0 * h / rho, dhS = f.df_dS * ir6;
+        acc[0] += -0.5 * c6 * h;
+        for (int c = 0; c < 3; ++c) acc[1 + c] += c6 * dh * r[c] / rho;
+        acc[4] += -h * c6 / ai;
+        acc[5] += -h * c6 * (1.0 / wi - 1.0 / (wi + wj));
+        acc[6] += -c6 * dhS;
+    }
+    __shared__ double scratch[4 * 7];
+    block_sum128<7>(acc, scratch);
+    if (threadIdx.x == 0) {
+        eatom[i] = acc[0];
+        gR[3 * i] = acc[1];
+        gR[3 * i + 1] = acc[2];
+        gR[3 * i + 2] = acc[3];
+        ga0[i] = acc[4];
+        gom[i] = acc[5];
+        grv[i] = acc[6];
+    }
+}
+
 __global__ void k_ts_chain(AtomBufs b, const double *g_a0, const double *g_om, const double *g_rv,
                            const double *scale, double *gp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -579,6 +619,12 @@ void nl_params(const AtomBufs &b, int *status, cudaStream_t s) {
 void nl_chain(const AtomBufs &b, const MbdGradOut &o, const double *scale, double *gp, cudaStream_t s) {
     count_launches(1);
     k_nl_chain<<<cdiv(b.N, 128), 128, 0, s>>>(b, o.g_abar0, o.g_ombar, o.g_rbar, scale, gp);
+}
+
+void ts_pairs(const AtomBufs &b, double s_r, double *eatom, double *gR, double *ga0, double *gom, double *grv,
+              cudaStream_t s) {
+    count_launches(1);
+    k_ts_pairs<<<b.N, 128, 0, s>>>(b, s_r, eatom, gR, ga0, gom, grv);
 }
 
 void ts_chain(const AtomBufs &b, const double *g_a0, const double *g_om, const double *g_rv,

@@ -1498,6 +1498,48 @@ int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega
     return MBD_OK;
 }
 
+int mbd_ts_energy(mbd_ctx *ctx, double s_r, double *energy, double *grad_coords, double *grad_params) {
+    if (!ctx) return MBD_ERR_INPUT;
+    if (!energy || !(s_r > 0.0)) return fail(ctx, MBD_ERR_INPUT, "mbd_ts_energy", "energy is required; s_r > 0");
+    if (!ctx->have_geom || !ctx->have_params)
+        return fail(ctx, MBD_ERR_STATE, "mbd_ts_energy", "set the geometry and the free-atom parameters first");
+    if (ctx->periodic) return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_ts_energy", "finite systems only");
+    if (ctx->opt.scs_mode == MBD_SCS_NL)
+        return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_ts_energy", "TS takes the free-atom parameters of Eq. ts-scaling");
+    MBD_CUDA(cudaSetDevice(ctx->device), "mbd_ts_energy");
+    const int N = ctx->N;
+    cudaStream_t s = ctx->stream;
+    MBD_CUDA(cudaMemcpyAsync(ctx->dR, ctx->hR.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s), "mbd_ts_energy");
+    MBD_CUDA(cudaMemcpyAsync(ctx->da0ref, ctx->ha0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_ts_energy");
+    MBD_CUDA(cudaMemcpyAsync(ctx->dc6ref, ctx->hc6.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_ts_energy");
+    MBD_CUDA(cudaMemcpyAsync(ctx->drref, ctx->hrr.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_ts_energy");
+    MBD_CUDA(cudaMemcpyAsync(ctx->dratio, ctx->hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "mbd_ts_energy");
+    MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_ts_energy");
+    const AtomBufs b = atom_bufs(ctx, Inputs{ctx->dR, ctx->da0ref, ctx->dc6ref, ctx->drref, ctx->dratio});
+    prepare_atoms(b, ctx->dstatus, s);   // TS-scaled oscillators (Eq. ts-scaling) and input checks
+    // scratch: per-atom energies in dh, dE/d(a0, om, rv) in dga0, dgom, dgrv; the next
+    // evaluation rewrites all of them before use
+    ts_pairs(b, s_r, ctx->dh, ctx->dgR, ctx->dga0, ctx->dgom, ctx->dgrv, s);
+    if (grad_params) ts_chain(b, ctx->dga0, ctx->dgom, ctx->dgrv, nullptr, ctx->dgp, s);
+    std::vector<double> ea(N);
+    MBD_CUDA(cudaMemcpyAsync(ea.data(), ctx->dh, sizeof(double) * N, cudaMemcpyDeviceToHost, s), "mbd_ts_energy");
+    if (grad_coords)
+        MBD_CUDA(cudaMemcpyAsync(grad_coords, ctx->dgR, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s), "mbd_ts_energy");
+    if (grad_params)
+        MBD_CUDA(cudaMemcpyAsync(grad_params, ctx->dgp, sizeof(double) * 4 * N, cudaMemcpyDeviceToHost, s), "mbd_ts_energy");
+    ctx->have_forward = false;   // the gradient scratch of the last evaluation was reused
+    int rc = read_status(ctx, s, "mbd_ts_energy");
+    if (rc) return rc;
+    double sum = 0.0, comp = 0.0;   // Neumaier sum of the per-atom energies
+    for (double x : ea) {
+        const double t = sum + x;
+        comp += std::fabs(sum) >= std::fabs(x) ? (sum - t) + x : (x - t) + sum;
+        sum = t;
+    }
+    *energy = sum + comp;
+    return MBD_OK;
+}
+
 int mbd_log_energy(mbd_ctx *ctx, int max_order, double *energy, double *orders) {
     if (!ctx) return MBD_ERR_INPUT;
     if (!energy || max_order < 1 || max_order > 4 || (max_order > 1 && !orders))
