@@ -94,7 +94,7 @@ def parse():
                     help="atoms of the bounded oracle sample (same recipe, extrapolated by n^3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--method", choices=("rsscs", "nl"), default="rsscs",
-                    help="rsscs: MBD@rsSCS (the headline); nl: MBD-NL (Sec. 2.2: no screening, oscillators "
+                    help="rsscs: MBD@rsSCS (the headline); nl: MBD-NL (Sec. 2.7: no screening, oscillators "
                          "from the free-atom reference and density-functional ratios drawn by "
                          "synthetic.nl_ratios(N, seed=7000))")
     ap.add_argument("--kernel", choices=("tc_gemm_sym6016", "log_energy_finite2000", "ts_finite2000"), default=None,

@@ -3,10 +3,10 @@
  *
  * The library evaluates the many-body-dispersion energy of the MBD@rsSCS method and its
  * analytic gradients (arXiv 2308.03140):
- *   - TS volume scaling of free-atom parameters, Eq. (ts-scaling), Sec. 2.6;
+ *   - TS volume scaling of free-atom parameters, Eq. (ts-scaling), Sec. 2.7;
  *   - range-separated self-consistent screening on an imaginary-frequency grid,
  *     Eqs. (scs), (contraction), (casimir-polder), (dyn-pol), (tgg), (mayer),
- *     (scs-sr-dipole), (scale-rvdw-scs), Secs. 2.3 and 2.6, grid of Sec. 3.3;
+ *     (scs-sr-dipole), (scale-rvdw-scs), Secs. 2.3 and 2.7, grid of Sec. 3.3;
  *   - the coupled-oscillator matrix Q, Eq. (q-matrix), and the energy, Eq. (mbd-energy),
  *     through Q^{1/2} and Q^{-1/2} from coupled Newton-Schulz iterations;
  *   - gradients, Eq. (mbd-gradient) and the SCS derivative of Eq. (scs-gradient) in
@@ -57,7 +57,7 @@ extern "C" {
 typedef struct mbd_ctx mbd_ctx;
 
 /* Options.  Defaults (mbd_default_options): n_freq 15 (Sec. 3.3), beta 0.83, a 6
- * (Sec. 2.6), precision FP64, ns_tol 1e-8 (Frobenius norm of I - Z Y at which one
+ * (Sec. 2.7), precision FP64, ns_tol 1e-8 (Frobenius norm of I - Z Y at which one
  * final Newton-Schulz step is taken; periodic systems: of all Bloch vectors' matrices
  * together), ns_max_iter 100, tc_chunk_stages 2, ewald_gamma, real_cutoff and
  * recip_cutoff 0 (automatic, see below). */
@@ -71,7 +71,7 @@ typedef struct {
     int tc_chunk_stages; /* mixed modes: K stages (32 TF32 or 64 bf16 elements each) per
                             tensor-memory accumulation; the partial sums are added in FP32
                             with round-to-nearest (default 2; 0 means 1)                  */
-    /* Periodic systems (Sec. 2.3, Ewald summation of the dipole tensor).  <= 0 selects:
+    /* Periodic systems (Sec. 2.2, Ewald summation of the dipole tensor).  <= 0 selects:
      * real_cutoff = 6/ewald_gamma; ewald_gamma = 6/real_cutoff when only the cutoff is
      * given, else 2.5/Omega^(1/3); recip_cutoff = 10 ewald_gamma.  real_cutoff (bohr) also
      * bounds the lattice sums of the damped tensors (screening and the damped-away part of
@@ -83,7 +83,7 @@ typedef struct {
      * set by mbd_set_scs_model predicts alpha_bar(iu); when its estimated energy error per
      * atom exceeds learned_max_error (Ha, default 1e-6) the evaluation is redone with plain
      * screening).  The learned model is not part of the paper.
-     * MBD_SCS_NL selects MBD-NL (Sec. 2.2, paragraph MBD-NL): no screening; the oscillators
+     * MBD_SCS_NL selects MBD-NL (Sec. 2.7, paragraph MBD-NL): no screening; the oscillators
      * are set directly by Eq. (mbd-nl-scaling), alpha0_i = alpha0_ref,i ra_i and
      * omega_i = omega_ref,i rw_i with omega_ref = 4 c6_ref / (3 alpha0_ref^2), and the damping
      * radii by Eq. (mbd-nl-rvdw), R_i = 5/2 alpha0_ref,i^(1/7) ra_i^(1/3), where
@@ -113,7 +113,7 @@ int mbd_destroy(mbd_ctx *ctx);
 /* Sets the system: n_atoms atoms at coords [n_atoms][3] (bohr, host memory), and for a
  * periodic system the lattice [3][3] (rows are the lattice vectors, bohr) and the
  * Monkhorst-Pack grid k_grid [3] (k-points (2m - n_c - 1)/(2 n_c) in fractional
- * reciprocal coordinates, m = 1..n_c, Sec. 2.3); lattice and k_grid are both NULL for a
+ * reciprocal coordinates, m = 1..n_c, Sec. 2.2); lattice and k_grid are both NULL for a
  * finite system.  Allocates the device workspace for that size.  Periodic systems run in
  * FP64 only (MBD_ERR_UNSUPPORTED for the reduced-precision modes). */
 int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const double *lattice,
@@ -172,7 +172,7 @@ int mbd_set_scs_model(mbd_ctx *ctx, int n_members, const void *params_fp16, cons
  * whether the evaluation fell back to plain screening (1) or kept the model's result (0). */
 int mbd_get_learned_stats(mbd_ctx *ctx, double *estimated_error, int *fell_back);
 
-/* Screening only (Sec. 2.3: Eqs. ts-scaling, scs, contraction, casimir-polder,
+/* Screening only (Secs. 2.3 and 2.7: Eqs. ts-scaling, scs, contraction, casimir-polder,
  * scale-rvdw-scs) with plain Dyson solves, for the geometry and parameters set above: host
  * outputs alpha_iu [n_freq+1][n_atoms] (screened), alpha_free_iu [n_freq+1][n_atoms] (the
  * unscreened alpha_i(iu) of Eq. dyn-pol), c6, omega, rvdw [n_atoms]; any may be NULL.
@@ -208,7 +208,7 @@ int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega
  * collapse). */
 int mbd_log_energy(mbd_ctx *ctx, int max_order, double *energy, double *orders);
 
-/* TS pairwise dispersion (Sec. 2.2: Eq. pairwise with the oscillators of Eq. ts-scaling and the
+/* TS pairwise dispersion (Secs. 2.6 and 2.7: Eq. pairwise with the oscillators of Eq. ts-scaling and the
  * damping of Eq. fermi-damping with steepness 20 and s_R = s_r, which depends on the
  * short-range model) for the geometry and free-atom parameters set above:
  * E = -1/2 sum_{i != j} C6_ij f_ij / R_ij^6, C6_ij = 3/2 alpha0_i alpha0_j / (1/omega_i + 1/omega_j).

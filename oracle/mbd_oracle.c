@@ -907,7 +907,7 @@ int orc_mbd_rsscs_gradient(int N, const double *R, const double *a0ref, const do
     return rc;
 }
 
-/* MBD-NL (Sec. 2.2, paragraph MBD-NL): no screening step.  The oscillators are set
+/* MBD-NL (Sec. 2.7, paragraph MBD-NL): no screening step.  The oscillators are set
  * directly from the free-atom reference and the ratios of a density polarizability
  * functional, Eq. (mbd-nl-scaling): alpha0_i = alpha0_ref,i ra_i, omega_i = omega_ref,i rw_i,
  * with omega_ref = 4 C6_ref / (3 alpha0_ref^2) the free atom's single-oscillator frequency

@@ -1,6 +1,6 @@
 /*
  * mbd_periodic.c -- plain, slow FP64 CPU oracle for periodic MBD@rsSCS (arXiv 2308.03140,
- * Sec. 2.3 "Periodic systems" and the Ewald summation of the dipole tensor).
+ * Sec. 2.2 "Periodic boundary conditions" and the Ewald summation of the dipole tensor).
  *
  * TEST INFRASTRUCTURE ONLY, like mbd_oracle.c: used by the tests, the package's smoke check
  * and the benchmark's CPU-baseline leg, never by the product path.  It shares no code with

@@ -253,7 +253,7 @@ def mbd_log_energy(R, alpha0, omega, rdamp, beta=0.83, a=6.0, n_freq=15, max_ord
 
 
 def mbd_nl(R, a0ref, c6ref, ra, rw, beta=0.83, a=6.0, grad=False, detail=False):
-    """MBD-NL energy (Sec. 2.2, Eqs. mbd-nl-scaling, mbd-nl-rvdw): no screening, oscillators
+    """MBD-NL energy (Sec. 2.7, Eqs. mbd-nl-scaling, mbd-nl-rvdw): no screening, oscillators
     from the free-atom reference (alpha0_ref, C6_ref) and the density-functional ratios
     ra = alpha0_df/alpha0_df,ref, rw = omega_df/omega_df,ref.  grad: also dE/dR [N,3] and
     dE/d(alpha0_ref, C6_ref, ra, rw) [4,N].  detail: also the oscillators (alpha0, omega,

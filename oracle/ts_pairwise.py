@@ -1,7 +1,7 @@
 """TS pairwise dispersion, CPU oracle (test infrastructure only; nothing in the product path
 imports it).
 
-Finite systems (Sec. 2.2, Eq. pairwise with the TS parametrization, Eqs. ts-scaling and
+Finite systems (Secs. 2.6 and 2.7, Eq. pairwise with the TS parametrization, Eqs. ts-scaling and
 fermi-damping):
     E = -1/2 sum_{i != j} C6_ij f_ij / R_ij^6,   C6_ij = 3/2 a_i a_j / (1/w_i + 1/w_j),
     a_i = alpha0_ref,i v_i, w_i = 4 C6_ref,i / (3 alpha0_ref,i^2), R_i = R_ref,i v_i^(1/3),
@@ -18,7 +18,7 @@ import math
 import numpy as np
 from scipy.special import erfc
 
-D_TS = 20.0   # steepness of the TS Fermi damping (Sec. 2.2, paragraph TS)
+D_TS = 20.0   # steepness of the TS Fermi damping (Sec. 2.7, paragraph TS)
 
 
 def ts_params(a0ref, c6ref, rref, ratio):

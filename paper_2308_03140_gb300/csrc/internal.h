@@ -209,7 +209,7 @@ void scs_grad_pass(const AtomBufs &b, double beta, double a, const double *X, co
                    long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR, float *work32,
                    cudaStream_t s);
 
-// MBD-NL (Sec. 2.2, Eqs. mbd-nl-scaling, mbd-nl-rvdw): the oscillators from the inputs
+// MBD-NL (Sec. 2.7, Eqs. mbd-nl-scaling, mbd-nl-rvdw): the oscillators from the inputs
 // alpha0_ref, C6_ref, ra (in rref) and rw (in ratio), written to abar0, ombar, rbar, c6bar,
 // abar (and a0, om, rv); ST_INPUT on non-positive or non-finite inputs.
 void nl_params(const AtomBufs &b, int *status, cudaStream_t s);

@@ -45,7 +45,7 @@ __global__ void k_prepare(AtomBufs b, int *status) {
     }
 }
 
-// MBD-NL oscillators (Sec. 2.2, paragraph MBD-NL): no screening.  Inputs per atom are
+// MBD-NL oscillators (Sec. 2.7, paragraph MBD-NL): no screening.  Inputs per atom are
 // alpha0_ref (a0ref), C6_ref (c6ref), ra = alpha0_df/alpha0_df,ref (in rref) and
 // rw = omega_df/omega_df,ref (in ratio).  Eq. (mbd-nl-scaling): alpha0 = alpha0_ref ra,
 // omega = omega_ref rw with omega_ref = 4 C6_ref / (3 alpha0_ref^2); Eq. (mbd-nl-rvdw):
@@ -459,7 +459,7 @@ __global__ void k_scs_grad_inputs_f32(const double *X, const double *V, const do
     }
 }
 
-// TS pairwise dispersion (Sec. 2.2, Eq. pairwise with the TS oscillators of Eq. ts-scaling and
+// TS pairwise dispersion (Secs. 2.6 and 2.7, Eq. pairwise with the TS oscillators of Eq. ts-scaling and
 // the damping of Eq. fermi-damping, steepness 20): one CTA per atom i, threads over j.  For
 // the pair (i, j) the energy is -C6_ij h(r), h = f/r^6, C6_ij = 3/2 a_i a_j w_i w_j / (w_i + w_j)
 // (the two ordered terms of -1/2 sum_{i != j}).  Per atom: eatom[i] = -1/2 sum_j C6_ij h_ij;

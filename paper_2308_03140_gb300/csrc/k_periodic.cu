@@ -1,5 +1,5 @@
-// Periodic MBD@rsSCS kernels for sm_103a (FP64): Sec. 2.3 (periodic systems) and the
-// Ewald summation of the dipole tensor.
+// Periodic MBD@rsSCS kernels for sm_103a (FP64): Sec. 2.2 (periodic boundary conditions)
+// and the Ewald summation of the dipole tensor.
 //
 //  structure_factors   S[g][i] = e^{i G_g . R_i} for every reciprocal vector in use
 //  build_scs_periodic  Gamma-point screening matrices: lattice sums of (1 - f) T^GG

@@ -3,7 +3,7 @@
 This module draws geometry and per-atom free-atom parameters only; it holds none of
 the MBD arithmetic, so both the CUDA path and the CPU oracle can take their inputs
 from it.  The paper's own systems (urethane supercells, Sec. 3.2; L7 complexes,
-Sec. 4) are not available, so clusters and cells with the same atom counts,
+Sec. 4.1) are not available, so clusters and cells with the same atom counts,
 densities and parameter ranges stand in for them.
 
 Parameter recipe (per atom, drawn in this order, independent uniforms):

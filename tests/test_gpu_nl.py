@@ -1,4 +1,4 @@
-"""GPU parity of MBD-NL (Sec. 2.2, paragraph MBD-NL: no screening, oscillators from
+"""GPU parity of MBD-NL (Sec. 2.7, paragraph MBD-NL: no screening, oscillators from
 Eqs. mbd-nl-scaling and mbd-nl-rvdw) through the C ABI against the CPU oracle
 (oracle/mbd_oracle.c: orc_mbd_nl).
 

@@ -1,4 +1,4 @@
-"""GPU parity of the periodic path (Sec. 2.3, Ewald summation) through the C ABI against the
+"""GPU parity of the periodic path (Sec. 2.2, Ewald summation) through the C ABI against the
 CPU oracle (oracle/mbd_periodic.c).
 
 Tolerances: energy 1e-10 relative; coordinate and lattice gradients 1e-8 Ha/bohr; parameter

@@ -1,4 +1,4 @@
-"""GPU parity of the TS pairwise energy and gradients (Sec. 2.2: Eqs. pairwise, ts-scaling,
+"""GPU parity of the TS pairwise energy and gradients (Secs. 2.6 and 2.7: Eqs. pairwise, ts-scaling,
 fermi-damping; mbd_ts_energy) against the CPU oracle (oracle/ts_pairwise.py).  FP64 on both
 sides: energy 1e-12 relative, coordinate gradients 1e-10 relative to the largest, parameter
 gradients 1e-10 relative to the largest of their kind."""

@@ -1,5 +1,5 @@
 """Pins of the log-formula energy route of the oracle (oracle/mbd_oracle.c:
-orc_mbd_log_energy; Sec. 2.1, Eqs. log-formula and rpa) against the diagonalization route,
+orc_mbd_log_energy; Sec. 2.5, Eqs. log-formula and rpa) against the diagonalization route,
 the closed-form pairwise (second-order) energy and the two-oscillator closed form.  CPU only."""
 import math
 

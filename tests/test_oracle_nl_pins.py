@@ -1,4 +1,4 @@
-"""Pins of the MBD-NL oracle (oracle/mbd_oracle.c: orc_mbd_nl; Sec. 2.2, paragraph MBD-NL,
+"""Pins of the MBD-NL oracle (oracle/mbd_oracle.c: orc_mbd_nl; Sec. 2.7, paragraph MBD-NL,
 Eqs. mbd-nl-scaling, mbd-nl-rvdw) against hand-computed parameters, the closed form of two
 coupled oscillators, central differences and invariances.  CPU only."""
 import math

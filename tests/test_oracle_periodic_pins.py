@@ -1,7 +1,7 @@
 """Pins of the periodic oracle (oracle/mbd_periodic.c) against what the mathematics fixes.
 
-Sec. 2.3 (periodic systems) and the Ewald summation of the dipole tensor.  Each pin is chosen
-so that a plausible slip (a wrong phase sign, a missing self term, a wrong reciprocal
+Sec. 2.2 (periodic boundary conditions) and the Ewald summation of the dipole tensor.
+Each pin is chosen so that a plausible slip (a wrong phase sign, a missing self term, a wrong reciprocal
 prefactor, a dropped image, a wrong lattice chain rule) fails it:
 - gamma-invariance of the Ewald sum (phase, prefactor, self term, erfc numerator);
 - Hermiticity and T(-q) = conj T(q);

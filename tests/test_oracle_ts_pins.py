@@ -1,5 +1,5 @@
-"""Pins of the TS pairwise oracle (oracle/ts_pairwise.py; Sec. 2.2, Eqs. pairwise, ts-scaling,
-fermi-damping, ts-ewald): closed forms, the Casimir-Polder quadrature of the combination
+"""Pins of the TS pairwise oracle (oracle/ts_pairwise.py; Secs. 2.6 and 2.7, Eqs. pairwise,
+ts-scaling, fermi-damping, ts-ewald): closed forms, the Casimir-Polder quadrature of the combination
 rule, central differences, the kernels of the Ewald split by numerical integration, gamma
 invariance and the plain lattice sum.  CPU only."""
 import math
