@@ -74,12 +74,13 @@ def ts_energy(R, a0ref, c6ref, rref, ratio, s_r=0.94, d=D_TS, grad=False):
 
 
 def _c6_chain(a0, om, gC6):
-    """dE/d a_i and dE/d w_i from dE/dC6_ij through C6_ij = 3/2 a_i a_j w_i w_j / (w_i + w_j)."""
+    """dE/d a_i and dE/d w_i from dE/dC6_ij through C6_ij = 3/2 a_i a_j w_i w_j / (w_i + w_j)
+    (for i = j the two factors of each kind give C6_ii' = 2 C6_ii/a_i and C6_ii/w_i)."""
     N = len(a0)
     ga0, gom = np.zeros(N), np.zeros(N)
     for i in range(N):
         for j in range(N):
-            if i == j or gC6[i, j] == 0.0:
+            if gC6[i, j] == 0.0:         # finite systems: no i = j term; periodic: the images
                 continue
             c = 1.5 * a0[i] * a0[j] * om[i] * om[j] / (om[i] + om[j])
             ga0[i] += gC6[i, j] * c / a0[i]
@@ -167,14 +168,97 @@ def damped_away_sum(R, A, rv, s_r, rc, d=D_TS):
     return Dm
 
 
-def ts_energy_periodic(R, A, a0ref, c6ref, rref, ratio, gamma, rc, kc, s_r=0.94, d=D_TS):
+def ts_energy_periodic(R, A, a0ref, c6ref, rref, ratio, gamma, rc, kc, s_r=0.94, d=D_TS, grad=False):
     """Periodic TS energy per cell by Eq. (ts-ewald) for the bare sum minus the damped-away
-    real-space part."""
+    real-space part.  With grad also dE/dR [N,3], dE/dA [3,3] (rows of A are the lattice
+    vectors; Cartesian positions, gamma and the cutoffs held fixed) and
+    dE/d(alpha0_ref, C6_ref, R_ref, v) [4,N]."""
     a0, om, rv = ts_params(a0ref, c6ref, rref, ratio)
     C6 = c6_matrix(a0, om)
     S = ewald_inverse_r6(R, A, gamma, rc, kc)
     Dm = damped_away_sum(R, A, rv, s_r, rc, d)
-    return -0.5 * float(np.sum(C6 * (S - Dm)))
+    E = -0.5 * float(np.sum(C6 * (S - Dm)))
+    if not grad:
+        return E
+    gR, gA, grv = _periodic_geometry_grad(R, A, C6, rv, gamma, rc, kc, s_r, d)
+    ga0, gom = _c6_chain(a0, om, -0.5 * (S - Dm))
+    return E, gR, gA, _ts_chain(a0ref, c6ref, rref, ratio, ga0, gom, grv)
+
+
+def _phi_r_prime(x):
+    """d phi_r / dx."""
+    e = np.exp(-x * x)
+    return (-6.0 / x ** 7 - 4.0 / x ** 5 - 1.0 / x ** 3) * e - 2.0 * x * phi_r(x)
+
+
+def _phi_k_prime(k):
+    """d phi_k / dk; the erfc term's derivative cancels against part of the Gaussian's."""
+    return math.pi ** 1.5 / 12.0 * (-4.0 * k * np.exp(-k * k / 4.0) - 0.5 * k * (4.0 - 2.0 * k * k) * np.exp(-k * k / 4.0)
+                                    + 3.0 * k * k * math.sqrt(math.pi) * erfc(k / 2.0) - k ** 3 * np.exp(-k * k / 4.0))
+
+
+def _periodic_geometry_grad(R, A, C6, rv, gamma, rc, kc, s_r, d):
+    """dE/dR, dE/dA and dE/dR_vdW of E = -1/2 sum_ij C6_ij (S_ij - Dm_ij), term by term:
+    real-space images h(r) = gamma^6 phi_r(gamma r) - (1 - f(r))/r^6 with R_nij = R_j + n A - R_i,
+    and reciprocal terms gamma^3 phi_k(|G|/gamma) cos(G . (R_j - R_i)) / Omega with
+    G = m B, B = 2 pi A^-T, Omega = |det A| (dB = -B dA^T B / (2 pi), dOmega = Omega A^-T dA)."""
+    R = np.asarray(R, float).reshape(-1, 3)
+    A = np.asarray(A, float)
+    N = len(R)
+    Om = abs(np.linalg.det(A))
+    AinvT = np.linalg.inv(A).T
+    Bm = 2.0 * math.pi * AinvT
+    nvec = _images_int(A, rc)
+    shifts = nvec @ A
+    mg = [int(math.ceil(kc * np.linalg.norm(A[c]) / (2.0 * math.pi))) + 1 for c in range(3)]
+    ms = np.array(np.meshgrid(*[np.arange(-m, m + 1) for m in mg], indexing="ij")).reshape(3, -1).T
+    G = ms @ Bm
+    G = G[np.linalg.norm(G, axis=1) < kc]
+    Gn = np.linalg.norm(G, axis=1)
+    gR = np.zeros((N, 3))
+    gA = np.zeros((3, 3))
+    grv = np.zeros(N)
+    for i in range(N):
+        for j in range(N):
+            c = -0.5 * C6[i, j]
+            # real space
+            rvec = R[j] + shifts - R[i]
+            rn = np.linalg.norm(rvec, axis=1)
+            sel = (rn > 1e-12) & (rn < rc)
+            r, v, n = rn[sel], rvec[sel], nvec[sel]
+            f, dfr, dfs = fermi(r, rv[i] + rv[j], s_r, d)
+            dh = gamma ** 7 * _phi_r_prime(gamma * r) + dfr / r ** 6 + 6.0 * (1.0 - f) / r ** 7
+            w = (c * dh / r)[:, None] * v            # dE/d(R_nij)
+            gR[j] += w.sum(0)
+            gR[i] -= w.sum(0)
+            gA += n.T @ w                            # d R_nij / d A_cd = n_c
+            gsum = c * np.sum(dfs / r ** 6)          # -(1 - f) term: d/d rsum of -(1-f) = +df/drsum
+            grv[i] += gsum
+            grv[j] += gsum
+            # reciprocal space
+            dij = R[j] - R[i]
+            ph = G @ dij
+            t = gamma ** 3 * phi_k(Gn / gamma) / Om
+            gk = np.zeros_like(G)
+            nz = Gn > 0
+            gk[nz] = (gamma ** 2 * _phi_k_prime(Gn[nz] / gamma) / Om * np.cos(ph[nz]) / Gn[nz])[:, None] * G[nz]
+            gk -= (t * np.sin(ph))[:, None] * dij[None, :]    # d term / d G
+            wsin = c * t * np.sin(ph)
+            gR[j] -= wsin @ G
+            gR[i] += wsin @ G
+            # d/dA_fc through G: dG_e = -sum G_c B_fe dA_fc / (2 pi); through Omega: -t/Omega dOmega
+            gA += -c * (Bm @ (gk.T @ G)) / (2.0 * math.pi)
+            gA += -c * np.sum(t * np.cos(ph)) * AinvT
+    return gR, gA, grv
+
+
+def _images_int(A, rc):
+    """Integer image vectors n with |n A| possibly below rc + the cell diameter (as _images)."""
+    A = np.asarray(A, float)
+    B = np.linalg.inv(A).T
+    diam = np.linalg.norm(A.sum(0)) + sum(np.linalg.norm(a) for a in A)
+    m = [int(math.ceil((rc + diam) * np.linalg.norm(B[c]))) for c in range(3)]
+    return np.array(np.meshgrid(*[np.arange(-mc, mc + 1) for mc in m], indexing="ij")).reshape(3, -1).T.astype(float)
 
 
 def ts_energy_periodic_direct(R, A, a0ref, c6ref, rref, ratio, r_big, s_r=0.94, d=D_TS):

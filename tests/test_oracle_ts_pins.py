@@ -131,3 +131,63 @@ def test_periodic_large_box_limit():
         diffs.append(E_box - E_fin)
     assert diffs[0] < 0 and abs(diffs[0]) < 1e-3 * abs(E_fin)
     assert 50 < diffs[0] / diffs[1] < 80
+
+
+def test_periodic_gradients_central_differences(cell):
+    # tight cutoffs so that no image or G vector crosses them within the difference step
+    R, A, p = cell
+    g, rc, kc = 0.3, 7 / 0.3, 12 * 0.3
+    E, gR, gA, gp = T.ts_energy_periodic(R, A, *p, g, rc, kc, s_r=S_R, grad=True)
+    assert E == pytest.approx(T.ts_energy_periodic(R, A, *p, g, rc, kc, s_r=S_R), rel=1e-15, abs=0)
+
+    def en(R_=R, A_=A, p_=p):
+        return T.ts_energy_periodic(R_, A_, *p_, g, rc, kc, s_r=S_R)
+    h = 1e-5
+    for i in range(len(R)):
+        for c in range(3):
+            Rp, Rm = R.copy(), R.copy()
+            Rp[i, c] += h
+            Rm[i, c] -= h
+            assert (en(R_=Rp) - en(R_=Rm)) / (2 * h) == pytest.approx(gR[i, c], abs=1e-8 * np.abs(gR).max())
+    for f in range(3):
+        for c in range(3):
+            Ap, Am = A.copy(), A.copy()
+            Ap[f, c] += h
+            Am[f, c] -= h
+            assert (en(A_=Ap) - en(A_=Am)) / (2 * h) == pytest.approx(gA[f, c], abs=1e-8 * np.abs(gA).max())
+    for q in range(4):
+        for k in range(len(R)):
+            hh = 1e-6 * p[q][k]
+            up = [x.copy() for x in p]
+            dn = [x.copy() for x in p]
+            up[q][k] += hh
+            dn[q][k] -= hh
+            assert (en(p_=up) - en(p_=dn)) / (2 * hh) == pytest.approx(gp[q, k], abs=1e-7 * np.abs(gp[q]).max())
+    assert np.abs(gR.sum(0)).max() < 1e-15
+
+
+def test_periodic_lattice_gradient_is_the_direct_sum_virial(cell):
+    # homogeneous strain R -> R (I + e), A -> A (I + e): dE/de = R^T gR + A^T gA, and for the
+    # plain lattice sum of -1/2 C6 f/r^6 the same derivative is the virial
+    # -1/2 sum C6 F'(r) r r^T / r (F = f/r^6) to r_big plus its continuum tail
+    # -1/2 C6 (-8 pi / (3 Omega r_big^3)) I; this route has no Ewald split at all
+    R, A, p = cell
+    _, gR, gA, _ = T.ts_energy_periodic(R, A, *p, 0.3, 7 / 0.3, 12 * 0.3, s_r=S_R, grad=True)
+    strain = R.T @ gR + A.T @ gA
+    a0, om, rv = T.ts_params(*p)
+    C6 = T.c6_matrix(a0, om)
+    Om = abs(np.linalg.det(A))
+    rb = 150.0
+    shifts = T._images(A, rb)
+    vir = np.zeros((3, 3))
+    for i in range(len(R)):
+        for j in range(len(R)):
+            v = R[j] + shifts - R[i]
+            r = np.linalg.norm(v, axis=1)
+            s = (r > 1e-12) & (r < rb)
+            v, r = v[s], r[s]
+            f, dfr, _ = T.fermi(r, rv[i] + rv[j], S_R)
+            vir += -0.5 * C6[i, j] * (((dfr / r ** 6 - 6 * f / r ** 7) / r)[:, None] * v).T @ v
+            vir += -0.5 * C6[i, j] * (-8 * math.pi / (3 * Om * rb ** 3)) * np.eye(3)
+    assert np.abs(strain - vir).max() < 1e-6 * np.abs(vir).max()
+    assert np.allclose(strain, strain.T, atol=1e-12 * np.abs(strain).max())
