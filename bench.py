@@ -97,13 +97,15 @@ def parse():
                     help="rsscs: MBD@rsSCS (the headline); nl: MBD-NL (Sec. 2.7: no screening, oscillators "
                          "from the free-atom reference and density-functional ratios drawn by "
                          "synthetic.nl_ratios(N, seed=7000))")
-    ap.add_argument("--kernel", choices=("tc_gemm_sym6016", "log_energy_finite2000", "ts_finite2000"), default=None,
+    ap.add_argument("--kernel", choices=("tc_gemm_sym6016", "log_energy_finite2000", "ts_finite2000", "ts_cell256"),
+                    default=None,
                     help="time one kernel or route alone instead of the workload: tc_gemm_sym6016 = the "
                          "symmetric TF32x3 Newton-Schulz product of order 6016 (k_tc_gemm mode 2, chunks of 2 "
                          "stages; a small case for profilers, about 0.9 GB on the device); "
                          "log_energy_finite2000 = the log-formula energy route (mbd_log_energy, orders 2) of the "
                          "2000-atom cluster after a TF32x3 evaluation; ts_finite2000 = the TS pairwise energy "
-                         "and gradients (mbd_ts_energy) of the 2000-atom cluster")
+                         "and gradients (mbd_ts_energy) of the 2000-atom cluster; ts_cell256 = the same per cell of "
+                         "the 256-atom triclinic cell with the lattice gradient (Eq. ts-ewald)")
     return ap.parse_args()
 
 
@@ -673,45 +675,79 @@ def run_log_energy(args):
 
 
 def run_ts(args):
-    """The TS pairwise energy and gradients (mbd_ts_energy, s_R = 0.94) of the 2000-atom cluster:
-    host-clock time per call, inputs uploaded and gradients read back each call; the pair
-    pass's rate against the FP64 rate (about 60 flop per ordered pair); the oracle's TS on an
-    800-atom sample of the same recipe, extrapolated by n^2."""
+    """The TS pairwise energy and gradients (mbd_ts_energy, s_R = 0.94): host-clock time per
+    call, inputs uploaded and gradients read back each call, and the pair pass's rate against
+    the FP64 rate.  ts_finite2000: the 2000-atom cluster (about 60 flop per ordered pair); the
+    oracle's TS on an 800-atom sample of the same recipe, extrapolated by n^2.  ts_cell256:
+    the 256-atom triclinic cell per cell, with the lattice gradient, by Eq. ts-ewald (gamma
+    0.2/bohr, real-space cutoff 30 bohr, reciprocal cutoff 2.0/bohr; about 60 flop per pair
+    image and 20 per pair and reciprocal vector); the oracle on the cell's first 32 atoms in
+    the same lattice, extrapolated by n^2."""
+    import numpy as np
+
     from paper_2308_03140_gb300 import binding, build
     from paper_2308_03140_gb300 import synthetic as syn
     build.build()
     binding.load()
-    sysm = syn.workload("finite2000")
+    cell = args.kernel == "ts_cell256"
+    sysm = syn.workload("cell256" if cell else "finite2000")
     N = sysm.n_atoms
     args_p = (sysm.alpha0_ref, sysm.c6_ref, sysm.rvdw_ref, sysm.ratio)
-    m = binding.MBD(0)
-    m.set_geometry(sysm.coords)
+    gamma, rc, kc = 0.2, 30.0, 2.0
+    if cell:
+        m = binding.MBD(0, ewald_gamma=gamma, real_cutoff=rc, recip_cutoff=kc)
+        m.set_geometry(sysm.coords, sysm.lattice, (1, 1, 1))   # the k-grid plays no part in TS
+    else:
+        m = binding.MBD(0)
+        m.set_geometry(sysm.coords)
     m.set_free_atom_params(*args_p)
     for _ in range(args.warmup):
-        m.ts_energy(0.94)
+        m.ts_energy(0.94, lattice=cell)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        E, gR, gp = m.ts_energy(0.94)
+        E = m.ts_energy(0.94, lattice=cell)[0]
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     m.close()
     peaks = measured_peaks()
     bf16 = (peaks or {}).get("bf16_tflops_sustained") or 1700.0
     fp64_peak = bf16 * FP64_OVER_BF16
-    flops = 60.0 * N * (N - 1)
-    line = {"kernel": "mbd_ts_energy (k_prepare, k_ts_pairs, k_ts_chain)", "workload": "finite2000",
+    if cell:
+        A = np.asarray(sysm.lattice)
+        vol = abs(np.linalg.det(A))
+        B = 2 * np.pi * np.linalg.inv(A).T
+        mm = [int(np.ceil(kc * np.linalg.norm(A[c]) / (2 * np.pi))) + 1 for c in range(3)]
+        ms = np.array(np.meshgrid(*[np.arange(-q, q + 1) for q in mm], indexing="ij")).reshape(3, -1).T
+        n_g = int(np.sum(np.linalg.norm(ms @ B, axis=1) < kc))
+        images = 4.0 / 3.0 * np.pi * rc ** 3 / vol
+        flops = float(N * N) * (60.0 * images + 20.0 * n_g)
+        kernel = "mbd_ts_energy (k_prepare, k_structure_factors, k_ts_gtable, k_ts_periodic, k_ts_chain)"
+    else:
+        flops = 60.0 * N * (N - 1)
+        kernel = "mbd_ts_energy (k_prepare, k_ts_pairs, k_ts_chain)"
+    line = {"kernel": kernel, "workload": "cell256" if cell else "finite2000",
             "calls": args.steps, "ms_per_call": 1e3 * dt, "solves_per_s": 1.0 / dt, "energy_ha": E,
             "alu_tflops_per_call": flops / dt / 1e12, "fp64_peak_tflops": fp64_peak,
             "frac_of_fp64_peak": flops / dt / 1e12 / fp64_peak,
             "note": "host-clock time per call including the uploads and the gradient read-back"}
+    if cell:
+        line["note"] += f"; {n_g} reciprocal vectors and ~{images:.1f} images per pair"
     if not args.no_cpu_baseline:
         from oracle import ts_pairwise as T
-        ns = 800
-        smp = sample_system("finite2000", ns)
-        t1 = time.perf_counter()
-        T.ts_energy(smp.coords, smp.alpha0_ref, smp.c6_ref, smp.rvdw_ref, smp.ratio, 0.94, grad=True)
+        if cell:
+            ns = 32
+            sub = [a[:ns] for a in (sysm.coords,) + args_p]
+            t1 = time.perf_counter()
+            T.ts_energy_periodic(sub[0], sysm.lattice, *sub[1:], gamma, rc, kc, s_r=0.94, grad=True)
+            what = f"periodic TS of the cell's first {ns} atoms (same lattice)"
+        else:
+            ns = 800
+            smp = sample_system("finite2000", ns)
+            t1 = time.perf_counter()
+            T.ts_energy(smp.coords, smp.alpha0_ref, smp.c6_ref, smp.rvdw_ref, smp.ratio, 0.94, grad=True)
+            what = f"TS of an {ns}-atom cluster"
         ts = time.perf_counter() - t1
         line["cpu_baseline"] = {"value": 1.0 / (ts * (N / ns) ** 2), "unit": "solves/s", "cores": 1,
-                                "kind": "oracle", "sample": f"TS of an {ns}-atom cluster in {ts:.2f} s (numpy), "
+                                "kind": "oracle", "sample": f"{what} in {ts:.2f} s (numpy), "
                                                             f"extrapolated by (n/{ns})^2 to {N} atoms"}
     print(json.dumps(line), flush=True)
     return 0
@@ -721,7 +757,7 @@ def main():
     args = parse()
     if args.kernel == "log_energy_finite2000":
         return run_log_energy(args)
-    if args.kernel == "ts_finite2000":
+    if args.kernel in ("ts_finite2000", "ts_cell256"):
         return run_ts(args)
     if args.kernel:
         return run_kernel(args)

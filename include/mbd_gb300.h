@@ -208,15 +208,22 @@ int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega
  * collapse). */
 int mbd_log_energy(mbd_ctx *ctx, int max_order, double *energy, double *orders);
 
-/* TS pairwise dispersion (Secs. 2.6 and 2.7: Eq. pairwise with the oscillators of Eq. ts-scaling and the
- * damping of Eq. fermi-damping with steepness 20 and s_R = s_r, which depends on the
- * short-range model) for the geometry and free-atom parameters set above:
+/* TS pairwise dispersion (Secs. 2.6 and 2.7: Eq. pairwise with the oscillators of Eq.
+ * ts-scaling and the damping of Eq. fermi-damping with steepness 20 and s_R = s_r, which
+ * depends on the short-range model) for the geometry and free-atom parameters set above:
  * E = -1/2 sum_{i != j} C6_ij f_ij / R_ij^6, C6_ij = 3/2 alpha0_i alpha0_j / (1/omega_i + 1/omega_j).
- * Host outputs: *energy (Ha), grad_coords [n_atoms][3] and grad_params [4][n_atoms]
- * (dE/d alpha0_ref, c6_ref, rvdw_ref, volume ratio), either may be NULL.  FP64.  Finite
- * systems only (MBD_ERR_UNSUPPORTED for cells and in MBD-NL mode).  The call reuses gradient
+ * For a cell (mbd_set_geometry with a lattice; the k-grid is not used) E is per cell and the
+ * sum runs over j in the cell and all lattice images: the Ewald sum of 1/R^6 of Eq. ts-ewald
+ * (gamma, real_cutoff, recip_cutoff of the options, the G = 0 term included, self term
+ * -gamma^6/6) minus the real-space sum of (1 - f)/R^6 within real_cutoff.
+ * Host outputs: *energy (Ha), grad_coords [n_atoms][3], grad_lattice [3][3] (dE/dA with A's
+ * rows the lattice vectors and the Cartesian coordinates held fixed; cells only, else
+ * MBD_ERR_UNSUPPORTED) and grad_params [4][n_atoms] (dE/d alpha0_ref, c6_ref, rvdw_ref,
+ * volume ratio); any gradient may be NULL.  FP64.  MBD_ERR_UNSUPPORTED in MBD-NL mode;
+ * MBD_ERR_INPUT for non-positive parameters or coincident atoms.  The call reuses gradient
  * scratch, so mbd_backward_dev needs a new evaluation afterwards. */
-int mbd_ts_energy(mbd_ctx *ctx, double s_r, double *energy, double *grad_coords, double *grad_params);
+int mbd_ts_energy(mbd_ctx *ctx, double s_r, double *energy, double *grad_coords, double *grad_lattice,
+                  double *grad_params);
 
 /* Statistics of the last evaluation: Newton-Schulz iterations, the scale s of
  * Y0 = Q/s, the final Frobenius norm of I - Z Y, and (mixed modes) the Frobenius norm of

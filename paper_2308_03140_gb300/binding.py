@@ -85,7 +85,7 @@ def load(path: str | None = None):
     L.mbd_screen.argtypes = [vp, _P, _P, _P, _P, _P]
     L.mbd_get_stats.argtypes = [vp, C.POINTER(C.c_int), _P, _P, _P]
     L.mbd_log_energy.argtypes = [vp, C.c_int, _P, _P]
-    L.mbd_ts_energy.argtypes = [vp, C.c_double, _P, _P, _P]
+    L.mbd_ts_energy.argtypes = [vp, C.c_double, _P, _P, _P, _P]
     L.mbd_get_exception.argtypes = [vp, C.POINTER(C.c_int), C.c_char_p, C.c_char_p, sz]
     L.mbd_set_profiling.argtypes = [vp, i]
     L.mbd_get_profile.argtypes = [vp, C.POINTER(mbd_profile)]
@@ -294,15 +294,17 @@ class MBD:
         self._check(self.lib.mbd_log_energy(self.h, max_order, C.byref(E), _ptr(orders) if max_order > 1 else None))
         return E.value, orders[:max_order - 1]
 
-    def ts_energy(self, s_r: float = 0.94, gradients: bool = True):
-        """TS pairwise energy (mbd_ts_energy) of the system set above: (energy,
-        grad_coords [N,3] | None, grad_params [4,N] | None)."""
+    def ts_energy(self, s_r: float = 0.94, gradients: bool = True, lattice: bool = False):
+        """TS pairwise energy (mbd_ts_energy) of the system set above, per cell for a periodic
+        system: (energy, grad_coords [N,3] | None, grad_params [4,N] | None), and with
+        lattice=True (cells only) also grad_lattice [3,3] as a fourth item."""
         N = self.n_atoms
         E = C.c_double()
         gR = np.zeros((N, 3)) if gradients else None
         gp = np.zeros((4, N)) if gradients else None
-        self._check(self.lib.mbd_ts_energy(self.h, s_r, C.byref(E), _ptr(gR), _ptr(gp)))
-        return E.value, gR, gp
+        gA = np.zeros((3, 3)) if lattice else None
+        self._check(self.lib.mbd_ts_energy(self.h, s_r, C.byref(E), _ptr(gR), _ptr(gA), _ptr(gp)))
+        return (E.value, gR, gp, gA) if lattice else (E.value, gR, gp)
 
     def stats(self):
         it, sc, res, cr = C.c_int(), C.c_double(), C.c_double(), C.c_double()

@@ -298,6 +298,13 @@ void scs_grad_periodic(const AtomBufs &b, const CellGeom &c, double beta, double
                        const double *V, long long xstride, double *g_a0, double *g_om, double *g_rv, double *gR,
                        double *gA_part, double *gA, cudaStream_t s);
 
+// Periodic TS dispersion (k_ts_periodic.cu; the sum of Eq. ts-ewald minus the damped-away
+// part) of the TS-scaled oscillators, from the structure factors p.S of the current
+// coordinates: per-atom energy eatom [N], dE/dR [N][3], dE/d(a0, om, rv) [N] each and the
+// lattice gradient gA [9] (gA_part: 9N doubles of workspace; tab: 2 nG doubles).
+void ts_periodic(const AtomBufs &b, const PeriodicBufs &p, double s_r, double *tab, double *eatom, double *gR,
+                 double *ga0, double *gom, double *grv, double *gA_part, double *gA, int *status, cudaStream_t s);
+
 // ---- learned screening model (k_learned.cu) ---------------------------------------
 int learned_param_count();
 void scs_features(int n_atoms, int n_sys, const int *offsets, const double *R, const double *a0ref,

@@ -154,7 +154,7 @@ struct mbd_ctx {
     std::vector<double> hkq, hG;
     std::vector<int> hglist, hgcount;
     double *dkq = nullptr, *dG = nullptr, *dcoef = nullptr, *dlzw = nullptr, *dgA = nullptr, *dgAout = nullptr,
-           *dgApart = nullptr, *dgc = nullptr;
+           *dgApart = nullptr, *dgc = nullptr, *dtsg = nullptr;
     int *dglist = nullptr, *dgcount = nullptr;
     double2 *dS = nullptr;
     bool have_lattice_grad = false;
@@ -332,6 +332,7 @@ int allocate(mbd_ctx *ctx) {
         plan.push_back({&ctx->dgAout, 9});
         plan.push_back({&ctx->dgApart, 9 * N});
         plan.push_back({&ctx->dgc, N});
+        plan.push_back({&ctx->dtsg, 2LL * ctx->nG});
         plan.push_back({reinterpret_cast<double **>(&ctx->dS), 2LL * ctx->nG * N});
         plan.push_back({reinterpret_cast<double **>(&ctx->dglist), (nk * ctx->maxG + 1) / 2});
         plan.push_back({reinterpret_cast<double **>(&ctx->dgcount), (nk + 1) / 2});
@@ -1498,12 +1499,14 @@ int mbd_get_scs_detail(mbd_ctx *ctx, double *alpha_iu, double *c6, double *omega
     return MBD_OK;
 }
 
-int mbd_ts_energy(mbd_ctx *ctx, double s_r, double *energy, double *grad_coords, double *grad_params) {
+int mbd_ts_energy(mbd_ctx *ctx, double s_r, double *energy, double *grad_coords, double *grad_lattice,
+                  double *grad_params) {
     if (!ctx) return MBD_ERR_INPUT;
     if (!energy || !(s_r > 0.0)) return fail(ctx, MBD_ERR_INPUT, "mbd_ts_energy", "energy is required; s_r > 0");
     if (!ctx->have_geom || !ctx->have_params)
         return fail(ctx, MBD_ERR_STATE, "mbd_ts_energy", "set the geometry and the free-atom parameters first");
-    if (ctx->periodic) return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_ts_energy", "finite systems only");
+    if (grad_lattice && !ctx->periodic)
+        return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_ts_energy", "no lattice gradient for finite systems");
     if (ctx->opt.scs_mode == MBD_SCS_NL)
         return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_ts_energy", "TS takes the free-atom parameters of Eq. ts-scaling");
     MBD_CUDA(cudaSetDevice(ctx->device), "mbd_ts_energy");
@@ -1517,14 +1520,24 @@ int mbd_ts_energy(mbd_ctx *ctx, double s_r, double *energy, double *grad_coords,
     MBD_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), s), "mbd_ts_energy");
     const AtomBufs b = atom_bufs(ctx, Inputs{ctx->dR, ctx->da0ref, ctx->dc6ref, ctx->drref, ctx->dratio});
     prepare_atoms(b, ctx->dstatus, s);   // TS-scaled oscillators (Eq. ts-scaling) and input checks
-    // scratch: per-atom energies in dh, dE/d(a0, om, rv) in dga0, dgom, dgrv; the next
-    // evaluation rewrites all of them before use
-    ts_pairs(b, s_r, ctx->dh, ctx->dgR, ctx->dga0, ctx->dgom, ctx->dgrv, s);
+    // scratch: per-atom energies in dh, dE/d(a0, om, rv) in dga0, dgom, dgrv (and for a cell
+    // the lattice parts in dgApart, their sum in dgA); the next evaluation rewrites all of
+    // them before use
+    if (ctx->periodic) {
+        const PeriodicBufs pb = periodic_bufs(ctx);
+        structure_factors(b, pb, s);   // e^{i G.R_i} of the current coordinates
+        ts_periodic(b, pb, s_r, ctx->dtsg, ctx->dh, ctx->dgR, ctx->dga0, ctx->dgom, ctx->dgrv, ctx->dgApart,
+                    ctx->dgA, ctx->dstatus, s);
+    } else {
+        ts_pairs(b, s_r, ctx->dh, ctx->dgR, ctx->dga0, ctx->dgom, ctx->dgrv, s);
+    }
     if (grad_params) ts_chain(b, ctx->dga0, ctx->dgom, ctx->dgrv, nullptr, ctx->dgp, s);
     std::vector<double> ea(N);
     MBD_CUDA(cudaMemcpyAsync(ea.data(), ctx->dh, sizeof(double) * N, cudaMemcpyDeviceToHost, s), "mbd_ts_energy");
     if (grad_coords)
         MBD_CUDA(cudaMemcpyAsync(grad_coords, ctx->dgR, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s), "mbd_ts_energy");
+    if (grad_lattice)
+        MBD_CUDA(cudaMemcpyAsync(grad_lattice, ctx->dgA, sizeof(double) * 9, cudaMemcpyDeviceToHost, s), "mbd_ts_energy");
     if (grad_params)
         MBD_CUDA(cudaMemcpyAsync(grad_params, ctx->dgp, sizeof(double) * 4 * N, cudaMemcpyDeviceToHost, s), "mbd_ts_energy");
     ctx->have_forward = false;   // the gradient scratch of the last evaluation was reused

@@ -91,3 +91,14 @@ def test_binding_marshalling():
     assert binding._tptr(t).value == t.data_ptr() and binding._tptr(None) is None
     with pytest.raises(ValueError):
         binding._tptr(t.t())                                  # a transposed view is refused
+
+
+def test_null_context_calls_return_input_error(lib):
+    # every context call checks its handle before any device work; this also exercises the
+    # argument marshalling of each signature (ctypes raises on a count mismatch)
+    E = C.c_double()
+    assert lib.mbd_ts_energy(None, 0.94, C.byref(E), None, None, None) == 1
+    assert lib.mbd_log_energy(None, 2, C.byref(E), None) == 1
+    assert lib.mbd_evaluate(None, C.byref(E), None, None, None, None) == 1
+    with pytest.raises(TypeError):
+        lib.mbd_ts_energy(None, 0.94, C.byref(E), None, None)      # the old five-argument form
