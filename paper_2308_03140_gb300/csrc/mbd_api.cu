@@ -29,11 +29,16 @@ std::atomic<long long> g_launches{0};
 // errors of a few 1e-7 in the screened polarizabilities, one step against the FP64 matrix
 // brings them to about 1e-13 (screening matrices of kappa up to ~2e3).
 constexpr int kRefineSteps = 1;
-// Refinement steps of the mixed modes' adjoint solves V = A^{-1} H.  The forces of those modes
-// carry the first-order error of the tensor-core Q^{-1/2} (about 1e-2 of the largest force);
-// the unrefined FP32 solve adds at most kappa(A) eps32 ~ 1e-4 relative to the SCS part.
+// Refinement steps of the mixed modes' adjoint solves V = A^{-1} H: the unrefined FP32 solve
+// errs by at most kappa(A) eps32 ~ 1e-4 relative to the SCS part of the gradient; the TF32x3
+// force error measured at 2000 atoms with it (3e-6 of the largest force) is well inside that.
 constexpr int kAdjointRefineSteps = 0;
 constexpr int kLanczosSteps = 48; // Lanczos steps of the spectrum estimate of Q
+// Precision floor of the TF32x3 Newton-Schulz iteration per unit of sqrt(n): |I - Z Y|_F
+// settles at about 1.04e-7 sqrt(n) (8.1e-6 at n = 6000).  A step taken from a residual r whose
+// exact successor bound 0.875 r^2 lies below this is the last useful one.  The coarser kinds
+// (TF32, BF16x3) reach their floors above it and stop by the halving test alone.
+constexpr double kMixedFloor = 1e-7;
 constexpr int kLF = MBD_LEARNED_FEATURES;   // inputs of the learned screening model
 }  // namespace
 
@@ -637,10 +642,13 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
                             "Q has a non-positive eigenvalue (polarization catastrophe)");
             }
         }
-        // The tensor-core phase ends at its precision floor: below ns_tol, or when a step
-        // taken from inside the quadratic basin (|I - P| < 0.5, where an exact step gives at
-        // most 3/4 |I - P|^2) fails to halve the residual.
-        const bool last = it > 0 && (resid < ctx->opt.ns_tol || (prev < 0.5 && resid > 0.5 * prev));
+        // The tensor-core phase ends at its precision floor: below ns_tol; when a step taken
+        // from inside the quadratic basin (|I - P| < 0.5) fails to halve the residual; or when
+        // the step about to be taken cannot leave more than the floor.  For an eigenvalue
+        // x = 1 - e of P the plain step (al = 1) leaves 1 - x' = 3/4 e^2 + 1/4 e^3, so from
+        // |I - P|_F = r < 0.5 the next residual is at most 0.875 r^2 in exact arithmetic.
+        const bool last = it > 0 && (resid < ctx->opt.ns_tol || (prev < 0.5 && resid > 0.5 * prev) ||
+                                     (resid < 0.5 && 0.875 * resid * resid < kMixedFloor * std::sqrt(nd)));
         double al = 1.0;
         if (!last && lbound < 0.999) al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
         const double c1 = 1.5 * al, c3 = -0.5 * al * al * al;

@@ -115,7 +115,7 @@ def test_finite2000_tf32x3_energy_and_forces(finite_ref):
     ab_tc = m.scs_detail()["alpha_bar"]
     m.close()
     assert abs(E - E_ref) / s.n_atoms <= 1e-7, (E, E_ref)
-    # FP32 factorization refined twice against the FP64 screening matrices
+    # FP32 factorization, the solve refined once against the FP64 screening matrices
     assert np.allclose(ab_tc, ab, rtol=1e-10, atol=0)
     m64, E64, gR64, _ = gpu(s)
     m64.close()
