@@ -14,6 +14,8 @@
 #ifndef MBD_GB300_KERNELS_H
 #define MBD_GB300_KERNELS_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -58,6 +60,25 @@ int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float al
                  const void *A1, long long lda, const void *B0, const void *B1, long long ldb, float beta,
                  const float *D, float *C, void *C_hi, void *C_lo, float *CT, long long ldc, int chunk_stages,
                  int *err);
+
+/* C = alpha * A * op(B) + beta * D, FP64-accurate, on the TF32 tensor path by error-free
+ * splitting (the paper has none: its FP64 products run on CPUs; this serves GB300, whose FP64
+ * rate is a small fraction of its tensor rate).  A is M x K (lda); trans_b = 1: op(B) = B^T
+ * with B N x K; trans_b = 0: op(B) = B with B K x N (ldb); C and D are M x N (ldc, ldd), D
+ * may be NULL when beta == 0 and may be C itself.  Each row of A and each column of op(B) is
+ * scaled by a power of two and cut into 9 slices of 6 bits, stored exactly as FP32; the 53
+ * slice products of weight p + q <= 9 run as TF32 tensor-core GEMMs over K in pieces of at
+ * most 1024, where every partial sum is an integer below 2^22 times a power of two and so
+ * exact in FP32, and each piece is added into C in FP64.  The result carries the rounding
+ * of those FP64 additions and a truncation below 2^-54 of each operand row or column's
+ * largest entry (as an FP64 product's own rounding); rows and columns whose largest
+ * entries' product is below 2^-60 lose low slices to FP32 underflow.  M and N multiples of
+ * 128, K of 64, ldc of 8.  work: device buffer of mbdk_gemm_f64_split_work_bytes(M, N, K)
+ * bytes (9 (M + N) K floats and M + N ints).  err as in mbdk_gemm_tc. */
+size_t mbdk_gemm_f64_split_work_bytes(int M, int N, int K);
+int mbdk_gemm_f64_split(void *stream, int trans_b, int M, int N, int K, double alpha, const double *A,
+                        long long lda, const double *B, long long ldb, double beta, const double *D, long long ldd,
+                        double *C, long long ldc, void *work, int *err);
 
 /* Allocation-free factor-and-solve (the paper has no counterpart; this serves callers
  * that cannot let a library allocate device memory -- codes that give the whole GPU to

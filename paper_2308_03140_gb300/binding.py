@@ -28,7 +28,7 @@ EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry
            "mbd_get_lattice_gradient", "mbd_set_scs_model", "mbd_get_learned_stats", "mbd_screen",
            "mbd_get_scs_detail", "mbd_log_energy", "mbd_ts_energy",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
-           "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
+           "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_gemm_f64_split", "mbdk_gemm_f64_split_work_bytes", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
            "mbdk_cholesky_solve3_f64_noalloc", "mbdk_scs_features", "mbdk_mlp_forward", "mbdk_mlp_backward",
            "mbdk_mse_grad", "mbdk_adam_step", "mbdk_gather_rows")
 LEARNED_FEATURES, LEARNED_OUTPUTS, LEARNED_PARAMS = 74, 16, 28176
@@ -102,8 +102,11 @@ def load(path: str | None = None):
     L.mbdk_mse_grad.argtypes = [vp, ll, vp, vp, vp, vp]
     L.mbdk_adam_step.argtypes = [vp, ll, vp, vp, vp, vp, i, f, vp]
     L.mbdk_gather_rows.argtypes = [vp, ll, i, vp, vp, vp]
+    L.mbdk_gemm_f64_split.argtypes = [vp, i, i, i, i, d, vp, ll, vp, ll, d, vp, ll, vp, ll, vp, vp]
+    L.mbdk_gemm_f64_split_work_bytes.argtypes = [i, i, i]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int
+    L.mbdk_gemm_f64_split_work_bytes.restype = C.c_size_t
     _lib = L
     return L
 
@@ -343,6 +346,28 @@ def mbdk_gemm_tc(kind, A0, B0, C_out=None, A1=None, B1=None, alpha=1.0, beta=0.0
     return L.mbdk_gemm_tc(_stream(A0, stream), kind, mode, M, N, K, alpha, _tptr(A0), _tptr(A1), A0.stride(0),
                           _tptr(B0), _tptr(B1), B0.stride(0), beta, _tptr(D), _tptr(C_out), _tptr(C_hi),
                           _tptr(C_lo), _tptr(CT), ref.stride(0), chunk_stages, _tptr(err))
+
+
+def mbdk_gemm_f64_split(A, B, C_out, alpha=1.0, beta=0.0, D=None, trans_b=True, work=None, err=None,
+                        stream=None):
+    """C_out = alpha A op(B) + beta D, FP64-accurate on the TF32 tensor cores by error-free
+    splitting (see mbdk_gemm_f64_split in the header); torch float64 CUDA tensors, M and N
+    multiples of 128, K of 64.  work (uint8 CUDA tensor of mbdk_gemm_f64_split_work_bytes)
+    and err (int32 CUDA tensor) are allocated here when not given."""
+    import torch
+    L = load()
+    M, K = A.shape
+    N = B.shape[0] if trans_b else B.shape[1]
+    if work is None:
+        work = torch.empty(int(L.mbdk_gemm_f64_split_work_bytes(M, N, K)), dtype=torch.uint8, device=A.device)
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    rc = L.mbdk_gemm_f64_split(_stream(A, stream), int(bool(trans_b)), M, N, K, alpha, _tptr(A), A.stride(0),
+                               _tptr(B), B.stride(0), beta, _tptr(D), D.stride(0) if D is not None else 0,
+                               _tptr(C_out), C_out.stride(0), _tptr(work), _tptr(err))
+    if rc:
+        raise MBDError(rc, "mbdk_gemm_f64_split", "launch rejected")
+    return err
 
 
 def mbdk_cholesky_f64(A, dinv, status, stream=None):

@@ -56,6 +56,14 @@ struct TcArgs {
     long long sC = 0;
 };
 cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_t s);
+// FP64-accurate C = alpha A op(B) + beta D (k_split64.cu): the operands cut into exact TF32
+// slices (split64.cuh), the slice products on the tensor cores (tc_gemm kind 0) over K in
+// exact pieces, summed into C in FP64.  trans_b: op(B) = B^T with B N x K, else B is K x N.
+// M, N multiples of 128, K of 64, ldc of 8; D may be C; work: gemm_f64_split_work_bytes.
+size_t gemm_f64_split_work_bytes(int M, int N, int K);
+cudaError_t gemm_f64_split(int trans_b, int M, int N, int K, double alpha, const double *A, long long lda,
+                           const double *B, long long ldb, double beta, const double *D, long long ldd, double *C,
+                           long long ldc, void *work, int *err, cudaStream_t s);
 // Mixed-precision helpers: Y = scale Q (FP32 and, if Yh, bf16 hi/lo) and Z = I;
 // Z = a I + b P; Zd = scale Zf in FP64; and the variational energy
 // E = (1/4)(3 Tr V - sum V o W) - 3/2 sum omega (work: 608 doubles).

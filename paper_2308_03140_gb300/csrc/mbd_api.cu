@@ -1671,6 +1671,24 @@ int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float al
     return e == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
 }
 
+size_t mbdk_gemm_f64_split_work_bytes(int M, int N, int K) {
+    if (M <= 0 || N <= 0 || K <= 0) return 0;
+    return gemm_f64_split_work_bytes(M, N, K);
+}
+
+int mbdk_gemm_f64_split(void *stream, int trans_b, int M, int N, int K, double alpha, const double *A,
+                        long long lda, const double *B, long long ldb, double beta, const double *D, long long ldd,
+                        double *C, long long ldc, void *work, int *err) {
+    if (M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 128 || K % 64 || !A || !B || !C || !work || !err ||
+        (beta != 0.0 && !D) || ldc % 8 || lda < K || ldb < (trans_b ? K : N) || ldc < N ||
+        (D && D != C && ldd < N) || (trans_b != 0 && trans_b != 1))
+        return MBD_ERR_INPUT;
+    const cudaError_t e = gemm_f64_split(trans_b, M, N, K, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc, work, err,
+                                         static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorInvalidValue) return MBD_ERR_INPUT;
+    return e == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
+}
+
 int mbdk_cholesky_f64(void *stream, double *A, long long ld, int batch, double *dinv, int *status) {
     if (ld <= 0 || ld % kTile || batch < 1 || !A || !dinv || !status) return MBD_ERR_INPUT;
     cholesky_f64(A, ld, ld * ld, batch, dinv, status, static_cast<cudaStream_t>(stream));

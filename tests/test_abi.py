@@ -17,7 +17,7 @@ def declared_symbols():
         if fn.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"^\s*int\s+(mbdk?_\w+)\s*\(", txt, flags=re.M))
+            names |= set(re.findall(r"^\s*(?:int|size_t)\s+(mbdk?_\w+)\s*\(", txt, flags=re.M))
     return names
 
 
@@ -102,3 +102,13 @@ def test_null_context_calls_return_input_error(lib):
     assert lib.mbd_evaluate(None, C.byref(E), None, None, None, None) == 1
     with pytest.raises(TypeError):
         lib.mbd_ts_energy(None, 0.94, C.byref(E), None, None)      # the old five-argument form
+
+
+def test_split_gemm_entry_checks_arguments_before_any_device_work(lib):
+    # sizes are validated first (no device call); the workspace size is plain arithmetic
+    assert lib.mbdk_gemm_f64_split_work_bytes(128, 256, 64) == 9 * (128 + 256) * 64 * 4 + (128 + 256) * 4
+    assert lib.mbdk_gemm_f64_split_work_bytes(0, 256, 64) == 0
+    args = dict(trans_b=1, M=128, N=96, K=64)   # N not a multiple of 128
+    rc = lib.mbdk_gemm_f64_split(None, args["trans_b"], args["M"], args["N"], args["K"], 1.0, None, 64, None, 64,
+                                 0.0, None, 0, None, 96, None, None)
+    assert rc == 1
