@@ -97,7 +97,8 @@ def parse():
                     help="rsscs: MBD@rsSCS (the headline); nl: MBD-NL (Sec. 2.7: no screening, oscillators "
                          "from the free-atom reference and density-functional ratios drawn by "
                          "synthetic.nl_ratios(N, seed=7000))")
-    ap.add_argument("--kernel", choices=("tc_gemm_sym6016", "log_energy_finite2000", "ts_finite2000", "ts_cell256"),
+    ap.add_argument("--kernel", choices=("tc_gemm_sym6016", "log_energy_finite2000", "ts_finite2000", "ts_cell256",
+                                         "gemm_f64_split6016"),
                     default=None,
                     help="time one kernel or route alone instead of the workload: tc_gemm_sym6016 = the "
                          "symmetric TF32x3 Newton-Schulz product of order 6016 (k_tc_gemm mode 2, chunks of 2 "
@@ -105,7 +106,8 @@ def parse():
                          "log_energy_finite2000 = the log-formula energy route (mbd_log_energy, orders 2) of the "
                          "2000-atom cluster after a TF32x3 evaluation; ts_finite2000 = the TS pairwise energy "
                          "and gradients (mbd_ts_energy) of the 2000-atom cluster; ts_cell256 = the same per cell of "
-                         "the 256-atom triclinic cell with the lattice gradient (Eq. ts-ewald)")
+                         "the 256-atom triclinic cell with the lattice gradient (Eq. ts-ewald); "
+                         "gemm_f64_split6016 = the FP64-accurate split GEMM against the FP64 GEMM at order 6016")
     return ap.parse_args()
 
 
@@ -624,6 +626,53 @@ def run_kernel(args):
     return 0
 
 
+def run_split_gemm(args):
+    """The FP64-accurate split GEMM (mbdk_gemm_f64_split) at order 6016 against the FP64
+    tensor-pipe GEMM (mbdk_gemm_f64) on the same operands (a symmetric matrix of the scale of
+    the Newton-Schulz iterates, times itself): CUDA-event time per call of each, algorithmic
+    TFLOP/s (2 n^3), and the largest difference between the two results in units of
+    sum_k |A_ik| |B_kj| (both are FP64-accurate, so a few 2^-53)."""
+    import torch
+    from paper_2308_03140_gb300 import binding
+    binding.load()
+    dev = torch.device("cuda:0")
+    n = 6016
+    g = torch.Generator(device="cpu").manual_seed(11)
+    S = torch.randn(n, n, generator=g, dtype=torch.float64) / n ** 0.5
+    S = (S + S.T).to(dev)
+    C1 = torch.empty(n, n, dtype=torch.float64, device=dev)
+    C2 = torch.empty_like(C1)
+    work = torch.empty(int(binding.load().mbdk_gemm_f64_split_work_bytes(n, n, n)), dtype=torch.uint8, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / max(args.steps, 1)
+
+    ms_split = timed(lambda: binding.mbdk_gemm_f64_split(S, S, C1, trans_b=True, work=work, err=err))
+    ms_f64 = timed(lambda: binding.mbdk_gemm_f64(S, S, C2, trans_b=True))
+    if err.item():
+        raise RuntimeError("tensor-core wait timed out")
+    absS = S.abs()
+    scale = absS @ absS.T
+    diff = float(((C1 - C2).abs() / scale).max()) / 2.0 ** -53
+    flops = 2.0 * n ** 3
+    print(json.dumps({"kernel": "mbdk_gemm_f64_split (k_row_exponents, k_row_slices, 318 x k_tc_gemm<TF32>)",
+                      "order": n, "calls": args.steps, "ms_per_call": ms_split,
+                      "tflops_algorithmic": flops / (ms_split / 1e3) / 1e12, "fp64_gemm_ms_per_call": ms_f64,
+                      "fp64_gemm_tflops": flops / (ms_f64 / 1e3) / 1e12, "speedup_vs_fp64_gemm": ms_f64 / ms_split,
+                      "max_diff_ulps_of_abs_product": diff}))
+    return 0
+
+
 def run_log_energy(args):
     """The log-formula route (Eq. log-formula, FP64 Cholesky factors of I + A_k at the 15
     nodes) of the 2000-atom cluster: --warmup + --steps calls after one TF32x3 evaluation,
@@ -759,6 +808,8 @@ def main():
         return run_log_energy(args)
     if args.kernel in ("ts_finite2000", "ts_cell256"):
         return run_ts(args)
+    if args.kernel == "gemm_f64_split6016":
+        return run_split_gemm(args)
     if args.kernel:
         return run_kernel(args)
     if args.impl == "reference":
