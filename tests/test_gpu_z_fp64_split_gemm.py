@@ -1,0 +1,66 @@
+"""GPU test of the FP64-accurate split GEMM (mbdk_gemm_f64_split: operands cut into exact
+TF32 slices, slice products on the tcgen05 tensor cores, exact FP32 partial sums added in
+FP64) against the exact product computed on the host in extended precision.  Its slicing and
+an exact emulation of the product are checked on the CPU in test_split64_host.py, which
+also fixes the tolerances used here."""
+import numpy as np
+import pytest
+
+from paper_2308_03140_gb300 import binding, build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    binding.load()
+
+
+def _dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("trans_b", [True, False])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 1152), (384, 128, 2112)])
+def test_gemm_f64_split_is_fp64_accurate(M, N, K, trans_b):
+    # FP64-accurate products on the TF32 tensor cores by error-free slicing: against the
+    # exact product (long double on the host) within a few FP64 roundings of |A||B|, for
+    # rows and columns of very different size, K over one and several 1024 pieces
+    import torch
+    rng = np.random.default_rng(M + N + K)
+    A = rng.normal(size=(M, K)) * np.exp(rng.uniform(-6, 6, size=(M, 1)))
+    B = rng.normal(size=(N, K)) * np.exp(rng.uniform(-6, 6, size=(N, 1)))
+    exact = (A.astype(np.longdouble) @ B.T.astype(np.longdouble)).astype(np.float64)
+    scale = np.abs(A) @ np.abs(B).T
+    Bop = B if trans_b else np.ascontiguousarray(B.T)
+    dA, dB = torch.tensor(A, device=_dev()), torch.tensor(Bop, device=_dev())
+    C = torch.full((M, N), 7.0, dtype=torch.float64, device=_dev())
+    err = binding.mbdk_gemm_f64_split(dA, dB, C, trans_b=trans_b)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    got = C.cpu().numpy()
+    # an FP64 GEMM of these operands errs by up to ~3.5 ulps of |A||B|; the exact emulation of
+    # this algorithm on the host gives 4.1 (K = 64) and 1.7 (K = 1152)
+    assert np.all(np.abs(got - exact) <= 8 * 2.0 ** -53 * scale), np.abs((got - exact) / scale).max()
+    # alpha, beta, and D aliasing C: C = -0.5 A B^T + 1.5 C
+    D = rng.normal(size=(M, N))
+    C2 = torch.tensor(D, device=_dev())
+    binding.mbdk_gemm_f64_split(dA, dB, C2, alpha=-0.5, beta=1.5, D=C2, trans_b=trans_b)
+    C3 = torch.zeros(M, N, dtype=torch.float64, device=_dev())
+    binding.mbdk_gemm_f64_split(dA, dB, C3, alpha=-0.5, beta=1.5, D=torch.tensor(D, device=_dev()), trans_b=trans_b)
+    torch.cuda.synchronize()
+    ref = -0.5 * exact + 1.5 * D
+    tol = 12 * 2.0 ** -53 * (0.5 * scale + 1.5 * np.abs(D))
+    assert np.all(np.abs(C2.cpu().numpy() - ref) <= tol) and np.all(np.abs(C3.cpu().numpy() - ref) <= tol)
+
+
+def test_gemm_f64_split_rejects_bad_shapes():
+    import torch
+    A = torch.zeros(128, 64, dtype=torch.float64, device=_dev())
+    B = torch.zeros(96, 64, dtype=torch.float64, device=_dev())     # N not a multiple of 128
+    C = torch.zeros(128, 96, dtype=torch.float64, device=_dev())
+    with pytest.raises(binding.MBDError) as e:
+        binding.mbdk_gemm_f64_split(A, B, C)
+    assert e.value.code == 1
