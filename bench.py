@@ -87,7 +87,7 @@ def parse():
                          "screening model beside plain screening")
     ap.add_argument("--batch-clusters", type=int, default=64,
                     help="batch4096: clusters of the batch evaluated per step (the first ones of the recipe)")
-    ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64"), default="tf32x3",
+    ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64", "fp64split"), default="tf32x3",
                     help="matrix-function arithmetic of the timed arm (the FP64 path is measured beside it)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison arm (0: skip)")
     ap.add_argument("--cpu-sample-atoms", type=int, default=250,
@@ -312,7 +312,8 @@ def run_ours(args):
     al = torch.zeros(N, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
     precision = {"fp64": binding.MBD_PREC_FP64, "tf32": binding.MBD_PREC_TF32,
-                 "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3}[args.precision]
+                 "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3,
+                 "fp64split": binding.MBD_PREC_FP64_SPLIT}[args.precision]
     ewald = dict(ewald_gamma=PERIODIC_EWALD[0], real_cutoff=PERIODIC_EWALD[1],
                  recip_cutoff=PERIODIC_EWALD[2]) if periodic else {}
     m = binding.MBD(local, precision=precision, scs_mode=scs_mode, **ewald)
@@ -396,7 +397,15 @@ def run_ours(args):
     bf16_sus = peaks.get("bf16_tflops_sustained") if peaks else None
     src = "of measured" if bf16_sus else "of fallback"
     bf16_sus = bf16_sus or 1700.0
-    if precision == binding.MBD_PREC_FP64:
+    if precision == binding.MBD_PREC_FP64_SPLIT:
+        # the FP64-accurate split products: 53 TF32 slice products per algorithmic product
+        kernel = "k_tc_gemm<TF32> slice products of the split FP64 GEMM (Newton-Schulz products)"
+        k_ms, k_flops, k_launches = gemm_ms, gemm_flops, gemm_launches
+        peak = bf16_sus * 0.5 / 53
+        peak_src = (f"{src}: bf16_tflops_sustained x nominal TF32/BF16 rate (0.5) / 53 slice products per "
+                    "algorithmic product")
+        traffic = None
+    elif precision == binding.MBD_PREC_FP64:
         # dominant kernel: the FP64 tensor-path Newton-Schulz products
         kernel = "k_gemm_nn (FP64 mma.sync m8n8k4, Newton-Schulz products)"
         k_ms, k_flops, k_launches = gemm_ms, gemm_flops, gemm_launches
@@ -492,7 +501,8 @@ def run_batch(args):
     systems = syn.cluster_batch(K)
     model = np.load(os.path.join(ROOT, "paper_2308_03140_gb300", "learned_scs_model.npz"))
     precision = {"fp64": binding.MBD_PREC_FP64, "tf32": binding.MBD_PREC_TF32,
-                 "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3}[args.precision]
+                 "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3,
+                 "fp64split": binding.MBD_PREC_FP64_SPLIT}[args.precision]
     arms = {"plain": dict(), "learned": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e-6),
             "learned_no_fallback": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e300)}
     ctxs = {}

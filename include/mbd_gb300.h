@@ -53,6 +53,8 @@ extern "C" {
 #define MBD_PREC_TF32 1           /* TF32 tensor-core products, FP64 correction      */
 #define MBD_PREC_BF16X3 2         /* bf16 hi/lo split products (3 per GEMM), FP64 correction */
 #define MBD_PREC_TF32X3 3         /* TF32 hi/lo split products (3 per GEMM), FP64 correction */
+#define MBD_PREC_FP64_SPLIT 4     /* as FP64, the Newton-Schulz products FP64-accurate on the TF32
+                                     tensor cores by error-free splitting (finite systems) */
 
 typedef struct mbd_ctx mbd_ctx;
 
@@ -115,7 +117,8 @@ int mbd_destroy(mbd_ctx *ctx);
  * Monkhorst-Pack grid k_grid [3] (k-points (2m - n_c - 1)/(2 n_c) in fractional
  * reciprocal coordinates, m = 1..n_c, Sec. 2.2); lattice and k_grid are both NULL for a
  * finite system.  Allocates the device workspace for that size.  Periodic systems run in
- * FP64 only (MBD_ERR_UNSUPPORTED for the reduced-precision modes). */
+ * FP64 only (MBD_ERR_UNSUPPORTED for the reduced-precision modes and for
+ * MBD_PREC_FP64_SPLIT). */
 int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const double *lattice,
                      const int *k_grid);
 

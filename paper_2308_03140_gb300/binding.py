@@ -20,7 +20,7 @@ MBD_OK = 0
 ERRORS = {1: "MBD_ERR_INPUT", 2: "MBD_ERR_NEG_EIGENVALUE", 3: "MBD_ERR_SCS_NEG_ALPHA",
           4: "MBD_ERR_SCS_NOT_PD", 5: "MBD_ERR_NOT_CONVERGED", 6: "MBD_ERR_CUDA",
           7: "MBD_ERR_STATE", 8: "MBD_ERR_UNSUPPORTED", 9: "MBD_ERR_SCRATCH_LIMIT"}
-MBD_PREC_FP64, MBD_PREC_TF32, MBD_PREC_BF16X3, MBD_PREC_TF32X3 = 0, 1, 2, 3
+MBD_PREC_FP64, MBD_PREC_TF32, MBD_PREC_BF16X3, MBD_PREC_TF32X3, MBD_PREC_FP64_SPLIT = 0, 1, 2, 3, 4
 
 # Every symbol declared in include/mbd_gb300.h.
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",

@@ -60,8 +60,9 @@ cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_
 // slices (split64.cuh), the slice products on the tensor cores (tc_gemm kind 0) over K in
 // exact pieces, summed into C in FP64.  trans_b: op(B) = B^T with B N x K, else B is K x N.
 // M, N multiples of 128, K of 64, ldc of 8; D may be C; work: gemm_f64_split_work_bytes.
+// mode 0: every tile; mode 2 (M == N): upper tiles mirrored, for symmetric products.
 size_t gemm_f64_split_work_bytes(int M, int N, int K);
-cudaError_t gemm_f64_split(int trans_b, int M, int N, int K, double alpha, const double *A, long long lda,
+cudaError_t gemm_f64_split(int trans_b, int mode, int M, int N, int K, double alpha, const double *A, long long lda,
                            const double *B, long long ldb, double beta, const double *D, long long ldd, double *C,
                            long long ldc, void *work, int *err, cudaStream_t s);
 // Mixed-precision helpers: Y = scale Q (FP32 and, if Yh, bf16 hi/lo) and Z = I;

@@ -100,9 +100,10 @@ size_t gemm_f64_split_work_bytes(int M, int N, int K) {
            sizeof(int) * (static_cast<size_t>(M) + N);
 }
 
-cudaError_t gemm_f64_split(int trans_b, int M, int N, int K, double alpha, const double *A, long long lda,
+cudaError_t gemm_f64_split(int trans_b, int mode, int M, int N, int K, double alpha, const double *A, long long lda,
                            const double *B, long long ldb, double beta, const double *D, long long ldd, double *C,
                            long long ldc, void *work, int *err, cudaStream_t s) {
+    if ((mode != 0 && mode != 2) || (mode == 2 && M != N)) return cudaErrorInvalidValue;
     float *SA = static_cast<float *>(work);
     float *SB = SA + static_cast<size_t>(kSlices) * M * K;
     int *eA = reinterpret_cast<int *>(SB + static_cast<size_t>(kSlices) * N * K);
@@ -141,7 +142,7 @@ cudaError_t gemm_f64_split(int trans_b, int M, int N, int K, double alpha, const
                 const int kc = std::min(split64::kSplitChunk, K - k0);
                 TcOperands op{SA + p * sa + k0, nullptr, SB + q * sb + k0, nullptr, K, K};
                 TcArgs g{M, N, kc, 1.f, 0.f, nullptr, ldc, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                         nullptr, 0, 0, err};
+                         nullptr, 0, mode, err};
                 g.C64 = C;
                 e = tc_gemm(0, op, g, s);
                 if (e != cudaSuccess) return e;

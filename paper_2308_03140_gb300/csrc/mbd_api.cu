@@ -40,6 +40,9 @@ constexpr int kLanczosSteps = 48; // Lanczos steps of the spectrum estimate of Q
 // (TF32, BF16x3) reach their floors above it and stop by the halving test alone.
 constexpr double kMixedFloor = 1e-7;
 constexpr int kLF = MBD_LEARNED_FEATURES;   // inputs of the learned screening model
+// The FP64 path (screening, bounds, Newton-Schulz, gradients in FP64), with its Newton-Schulz
+// products on the DMMA pipe (MBD_PREC_FP64) or FP64-accurate on the TF32 tensor cores.
+inline bool fp64_path(int precision) { return precision == MBD_PREC_FP64 || precision == MBD_PREC_FP64_SPLIT; }
 }  // namespace
 
 void mbdgb::count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -158,6 +161,7 @@ struct mbd_ctx {
     CellGeom cell{};
     std::vector<double> hkq, hG;
     std::vector<int> hglist, hgcount;
+    void *dsplit = nullptr;   // slices of the split FP64 GEMM (MBD_PREC_FP64_SPLIT)
     double *dkq = nullptr, *dG = nullptr, *dcoef = nullptr, *dlzw = nullptr, *dgA = nullptr, *dgAout = nullptr,
            *dgApart = nullptr, *dgc = nullptr, *dtsg = nullptr;
     int *dglist = nullptr, *dgcount = nullptr;
@@ -354,12 +358,17 @@ int allocate(mbd_ctx *ctx) {
     const size_t mat32 = mat / 2, mat16 = mat / 4;
     const int prec = ctx->opt.precision;
     const size_t split_mat = prec == MBD_PREC_BF16X3 ? mat16 : (prec == MBD_PREC_TF32X3 ? mat32 : 0);
-    if (prec != MBD_PREC_FP64) bytes += 6 * mat32;
+    if (!fp64_path(prec)) bytes += 6 * mat32;
+    const size_t split_work = prec == MBD_PREC_FP64_SPLIT ? al(gemm_f64_split_work_bytes(static_cast<int>(ld),
+                                                                                          static_cast<int>(ld),
+                                                                                          static_cast<int>(ld)))
+                                                          : 0;
+    bytes += split_work;
     bytes += 12 * split_mat;
     // FP32 screening factors, their diagonal-block inverses and solve workspace
     const size_t panel_words = 2 * nf1 * static_cast<size_t>(ld) * 256;
     const size_t grad32 = 2 * nf1 * (3 * static_cast<size_t>(ld) + N);
-    const size_t scs32 = prec != MBD_PREC_FP64
+    const size_t scs32 = !fp64_path(prec)
                              ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * 2 * nf1 * ld * 3) +
                                    al(sizeof(uint32_t) * panel_words) + al(sizeof(float) * grad32)
                              : 0;
@@ -387,7 +396,11 @@ int allocate(mbd_ctx *ctx) {
         *m = reinterpret_cast<double *>(p);
         p += matq;
     }
-    if (prec != MBD_PREC_FP64) {
+    if (split_work) {
+        ctx->dsplit = p;
+        p += split_work;
+    }
+    if (!fp64_path(prec)) {
         float **f32[6] = {&ctx->fY, &ctx->fZ, &ctx->fY2, &ctx->fZ2, &ctx->fP, &ctx->fPT};
         for (auto m : f32) {
             *m = reinterpret_cast<float *>(p);
@@ -553,7 +566,7 @@ void backward_passes(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const doub
         if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
         return;
     }
-    const bool fp64 = ctx->opt.precision == MBD_PREC_FP64;
+    const bool fp64 = fp64_path(ctx->opt.precision);
     chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, fp64 ? ctx->dV : ctx->dB, ld, xs, s);
     cudaMemsetAsync(ctx->dgom, 0, sizeof(double) * ctx->N, s);
     if (fp64)
@@ -959,11 +972,18 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     const long long launches0 = launch_count();
     cudaEvent_t e_start = nullptr, e_scs = nullptr, e_ns = nullptr, e_grad = nullptr, e_corr = nullptr;
     std::vector<Span> gemms, tc_spans;
+    cudaError_t split_err = cudaSuccess;   // first launch error of the split FP64 GEMM
     auto timed_gemm = [&](const GemmArgs &g, double flops) {
         Span sp;
         sp.flops = flops;
         mark(ctx, s, sp.a);
-        gemm_f64(g, s);
+        if (ctx->opt.precision == MBD_PREC_FP64_SPLIT) {
+            const cudaError_t e = gemm_f64_split(g.trans_b, g.mode, g.M, g.N, g.K, g.alpha, g.A, g.lda, g.B, g.ldb,
+                                                 g.beta, g.D, g.ldd, g.C, g.ldc, ctx->dsplit, ctx->dstatus, s);
+            if (e != cudaSuccess && split_err == cudaSuccess) split_err = e;
+        } else {
+            gemm_f64(g, s);
+        }
         mark(ctx, s, sp.b);
         if (ctx->profiling) gemms.push_back(sp);
     };
@@ -997,7 +1017,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     } else {
         prepare_atoms(b, ctx->dstatus, s);
         build_scs(b, beta, a, ctx->dM, ld, mat, ctx->dstatus, s);
-        if (ctx->opt.precision == MBD_PREC_FP64) {
+        if (fp64_path(ctx->opt.precision)) {
             cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
             init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
             chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
@@ -1028,7 +1048,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     // spectrum; a 5 % margin keeps Y0's spectrum inside (0, 1]); the smallest gives the
     // lower bound for the scaled iteration, halved for safety.
     const int lz_steps = std::min(kLanczosSteps, static_cast<int>(ld));
-    if (ctx->opt.precision == MBD_PREC_FP64)
+    if (fp64_path(ctx->opt.precision))
         lanczos_coefficients(ctx->dQ, ld, lz_steps, ctx->dP, ctx->dscal + 8, s);
     else   // the bounds need a few digits; the products read an FP32 copy of Q (in the FP32 Y buffer)
         lanczos_coefficients_f32(ctx->dQ, ctx->fY, ld, lz_steps, ctx->dP, ctx->dscal + 8, s);
@@ -1059,7 +1079,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     double lbound = std::sqrt(std::max(0.5 * th_min / sc, 1e-12));   // lower bound on sqrt(eig(Z Y))
     const double ss = std::sqrt(sc);
     double *energy_out = out.energy ? out.energy : ctx->dscal;
-    if (ctx->opt.precision == MBD_PREC_FP64) {
+    if (fp64_path(ctx->opt.precision)) {
         double *Y = ctx->dQ, *Z = ctx->dZ, *P = ctx->dP, *Y2 = ctx->dY2, *Z2 = ctx->dZ2;
         scale_matrix(Y, ld, 1.0 / sc, s);
         set_identity(Z, ld, s);
@@ -1123,6 +1143,13 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         }
         ctx->ns_iter = it;
         ctx->ns_resid = resid;
+        if (split_err != cudaSuccess) return cuda_fail(ctx, "newton_schulz_split", split_err);
+        if (ctx->opt.precision == MBD_PREC_FP64_SPLIT) {   // tensor-core waits are bounded: check them
+            int st = 0;
+            MBD_CUDA(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s), "newton_schulz");
+            MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
+            if (st & ST_TC_TIMEOUT) return fail(ctx, MBD_ERR_CUDA, "newton_schulz_split", "tensor-core GEMM wait timed out");
+        }
         if (!converged)
             return fail(ctx, MBD_ERR_NOT_CONVERGED, "newton_schulz", "iteration cap reached");
         energy_trace(Y, ld, n, ctx->dombar, N, ss, energy_out, s);
@@ -1238,7 +1265,7 @@ int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt) {
     mbd_options o;
     if (opt) o = *opt; else mbd_default_options(&o);
     if (o.n_freq < 1 || o.n_freq + 1 > kMaxFreq || !(o.beta > 0) || !(o.a > 0) || o.ns_max_iter < 1 ||
-        !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_TF32X3 || o.tc_chunk_stages < 0 ||
+        !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_FP64_SPLIT || o.tc_chunk_stages < 0 ||
         (o.scs_mode != MBD_SCS_PLAIN && o.scs_mode != MBD_SCS_LEARNED && o.scs_mode != MBD_SCS_NL) ||
         !(o.learned_max_error > 0))
         return MBD_ERR_INPUT;
@@ -1467,7 +1494,7 @@ int mbd_screen(mbd_ctx *ctx, double *alpha_iu, double *alpha_free_iu, double *c6
     prepare_atoms(b, ctx->dstatus, s);
     if (ctx->periodic) build_scs_periodic(b, ctx->cell, ctx->opt.beta, ctx->opt.a, ctx->dM, ld, mat, ctx->dstatus, s);
     else build_scs(b, ctx->opt.beta, ctx->opt.a, ctx->dM, ld, mat, ctx->dstatus, s);
-    if (ctx->opt.precision == MBD_PREC_FP64 || ctx->periodic) {
+    if (fp64_path(ctx->opt.precision) || ctx->periodic) {
         cholesky_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dstatus, s);
         init_rhs_identity(ctx->dX, ld, n, nf1, xs, s);
         chol_solve3_f64(ctx->dM, ld, mat, nf1, ctx->ddinv, ctx->dX, ctx->dB, xs, s);
@@ -1612,7 +1639,7 @@ int mbd_log_energy(mbd_ctx *ctx, int max_order, double *energy, double *orders) 
 int mbd_get_stats(mbd_ctx *ctx, int *ns_iterations, double *ns_scale, double *ns_residual,
                   double *correction_residual) {
     if (!ctx) return MBD_ERR_INPUT;
-    if (correction_residual) *correction_residual = ctx->opt.precision == MBD_PREC_FP64 ? 0.0 : ctx->corr_resid;
+    if (correction_residual) *correction_residual = fp64_path(ctx->opt.precision) ? 0.0 : ctx->corr_resid;
     if (ns_iterations) *ns_iterations = ctx->ns_iter;
     if (ns_scale) *ns_scale = ctx->ns_scale;
     if (ns_residual) *ns_residual = ctx->ns_resid;
@@ -1683,7 +1710,7 @@ int mbdk_gemm_f64_split(void *stream, int trans_b, int M, int N, int K, double a
         (beta != 0.0 && !D) || ldc % 8 || lda < K || ldb < (trans_b ? K : N) || ldc < N ||
         (D && D != C && ldd < N) || (trans_b != 0 && trans_b != 1))
         return MBD_ERR_INPUT;
-    const cudaError_t e = gemm_f64_split(trans_b, M, N, K, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc, work, err,
+    const cudaError_t e = gemm_f64_split(trans_b, 0, M, N, K, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc, work, err,
                                          static_cast<cudaStream_t>(stream));
     if (e == cudaErrorInvalidValue) return MBD_ERR_INPUT;
     return e == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;

@@ -68,7 +68,8 @@ def test_create_accepts_every_method_and_precision(lib):
     # valid options pass validation; without a GPU the device query then fails (MBD_ERR_CUDA)
     import torch
     for mode in (binding.MBD_SCS_PLAIN, binding.MBD_SCS_LEARNED, binding.MBD_SCS_NL):
-        for prec in (binding.MBD_PREC_FP64, binding.MBD_PREC_TF32, binding.MBD_PREC_BF16X3, binding.MBD_PREC_TF32X3):
+        for prec in (binding.MBD_PREC_FP64, binding.MBD_PREC_TF32, binding.MBD_PREC_BF16X3, binding.MBD_PREC_TF32X3,
+                     binding.MBD_PREC_FP64_SPLIT):
             rc, h = _create(lib, scs_mode=mode, precision=prec)
             if torch.cuda.is_available():
                 assert rc == 0

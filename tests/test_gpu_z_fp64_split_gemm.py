@@ -1,12 +1,15 @@
 """GPU test of the FP64-accurate split GEMM (mbdk_gemm_f64_split: operands cut into exact
 TF32 slices, slice products on the tcgen05 tensor cores, exact FP32 partial sums added in
-FP64) against the exact product computed on the host in extended precision.  Its slicing and
-an exact emulation of the product are checked on the CPU in test_split64_host.py, which
-also fixes the tolerances used here."""
+FP64) against the exact product computed on the host in extended precision, and the FP64
+path with its Newton-Schulz products on it (MBD_PREC_FP64_SPLIT) against the oracle and the
+plain FP64 path.  Its slicing and an exact emulation of the product are checked on the CPU in
+test_split64_host.py, which also fixes the tolerances used here."""
 import numpy as np
 import pytest
 
+import oracle as o
 from paper_2308_03140_gb300 import binding, build
+from paper_2308_03140_gb300 import synthetic as syn
 
 pytestmark = pytest.mark.gpu
 
@@ -64,3 +67,22 @@ def test_gemm_f64_split_rejects_bad_shapes():
     with pytest.raises(binding.MBDError) as e:
         binding.mbdk_gemm_f64_split(A, B, C)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("workload", ["finite32", "n90"])
+def test_fp64_split_path_matches_oracle_and_fp64_path(workload):
+    sysm = syn.workload("finite32") if workload == "finite32" else syn.sphere_cluster(90, seed=1090)
+    E_ref, gR_ref, gp_ref = o.mbd_rsscs_gradient(*o.system_args(sysm), mode="adjoint")
+    out = {}
+    for prec in (binding.MBD_PREC_FP64, binding.MBD_PREC_FP64_SPLIT):
+        with binding.MBD(0, precision=prec) as m:
+            m.set_geometry(sysm.coords)
+            m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, sysm.rvdw_ref, sysm.ratio)
+            out[prec] = m.evaluate(True)[:3] + (m.stats(),)
+    E, gR, gp, st = out[binding.MBD_PREC_FP64_SPLIT]
+    E64, gR64, gp64, st64 = out[binding.MBD_PREC_FP64]
+    assert abs(E - E_ref) <= 1e-10 * abs(E_ref), (E, E_ref)
+    assert np.abs(gR - gR_ref).max() <= 1e-8 * np.abs(gR_ref).max()
+    # both paths are FP64-accurate; E is a small difference of terms of order sum(omega)
+    assert abs(E - E64) <= 1e-11 * abs(E64) and np.abs(gR - gR64).max() <= 1e-9 * np.abs(gR64).max()
+    assert abs(st["ns_iterations"] - st64["ns_iterations"]) <= 1
