@@ -1045,8 +1045,11 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     if (!(sc > 0.0) || !std::isfinite(sc)) return fail(ctx, MBD_ERR_INPUT, "newton_schulz", "invalid Q scale");
     // Lanczos estimates of the extreme eigenvalues of Q (workspace: rows of P).  The
     // largest tightens the scale s of Y0 = Q/s (Lanczos converges fast at the top of the
-    // spectrum; a 5 % margin keeps Y0's spectrum inside (0, 1]); the smallest gives the
-    // lower bound for the scaled iteration, halved for safety.
+    // spectrum; a 5 % margin keeps Y0's spectrum inside (0, 1]).  The smallest converges
+    // slowly: after 48 steps its Ritz value is 3-6 times the smallest eigenvalue of Q
+    // (500-2000 atom clusters), so a quarter of it is the lower bound of the scaled
+    // iteration.  A bound on either side of the true one only costs steps (see below); on the
+    // spectra of those clusters a quarter takes one step fewer than a half.
     const int lz_steps = std::min(kLanczosSteps, static_cast<int>(ld));
     if (fp64_path(ctx->opt.precision))
         lanczos_coefficients(ctx->dQ, ld, lz_steps, ctx->dP, ctx->dscal + 8, s);
@@ -1076,7 +1079,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         ubound = 1.05;
     }
     ctx->ns_scale = sc;
-    double lbound = std::sqrt(std::max(0.5 * th_min / sc, 1e-12));   // lower bound on sqrt(eig(Z Y))
+    double lbound = std::sqrt(std::max(0.25 * th_min / sc, 1e-12));   // lower bound on sqrt(eig(Z Y))
     const double ss = std::sqrt(sc);
     double *energy_out = out.energy ? out.energy : ctx->dscal;
     if (fp64_path(ctx->opt.precision)) {
@@ -1113,8 +1116,9 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
             // eigenvalues of P in [l^2, u^2], T = (al/2)(3 I - al^2 P) maps x to
             // f(x) = (al x/2)(3 - al^2 x^2); al^2 = 3/(u^2 + u l + l^2) gives f(l) = f(u), so
             // [l, u] goes onto [f(l), 1].  f stays positive for x < sqrt(3)/al, so any l
-            // below the true bound (and any u above it) only costs speed.  al = 1 near
-            // convergence.
+            // below the true bound (and any u above it) only costs speed; an l above it does
+            // too, since f is increasing on (0, l] (l <= 1/al) with f(x)/x >= al >= 1 there, so
+            // smaller eigenvalues still grow every step.  al = 1 near convergence.
             double al = 1.0;
             if (!last && lbound < 0.999)
                 al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
