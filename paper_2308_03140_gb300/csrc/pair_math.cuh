@@ -1,5 +1,6 @@
-// Device helpers shared by the pair kernels (k_pairs.cu, k_periodic.cu): the Fermi
-// damping function, the radial parts of the dipole tensors and warp/block sums.
+// Helpers shared by the pair kernels (k_pairs.cu, k_periodic.cu): the Fermi damping
+// function, the radial parts of the dipole tensors (host and device, so that the CPU tests
+// can evaluate the kernels' own formulas) and warp/block sums (device).
 // The dipole tensors are written T_ab = P delta_ab + W r_a r_b with radial P, W.
 #pragma once
 #include "internal.h"
@@ -35,7 +36,7 @@ __device__ void block_sum128(double (&v)[NV], double *scratch /* [4][NV] */) {
 // Fermi function of Eq. (fermi-damping) and its derivatives with respect to the pair
 // distance rho and the radius sum S.
 struct Fermi { double f, df_drho, df_dS; };
-__device__ __forceinline__ Fermi fermi(double rho, double S, double beta, double a) {
+__host__ __device__ __forceinline__ Fermi fermi(double rho, double S, double beta, double a) {
     const double x = rho / (beta * S);
     const double f = 1.0 / (1.0 + exp(-a * (x - 1.0)));
     const double dfx = a * f * (1.0 - f);
@@ -45,7 +46,7 @@ __device__ __forceinline__ Fermi fermi(double rho, double S, double beta, double
 // Radial parts of T^GG(r; s) (Eq. tgg): P = F1/r^3, W = (2 z^2 Th - 3 F1)/r^5 with
 // z = r/s, Th = 2 z e^{-z^2}/sqrt(pi), F1 = erf z - Th; and d/dr, d/ds of both.
 struct Radial { double P, W, dP, dW, dPs, dWs; };
-__device__ __forceinline__ Radial tgg_radial(double rho, double s) {
+__host__ __device__ __forceinline__ Radial tgg_radial(double rho, double s) {
     const double z = rho / s, z2 = z * z;
     const double th = kTwoOverSqrtPi * z * exp(-z2);
     const double F1 = erf(z) - th;
@@ -63,7 +64,7 @@ __device__ __forceinline__ Radial tgg_radial(double rho, double s) {
 
 // Bare dipole tensor T = -grad grad 1/r, Eq. (dipole): P = 1/r^3, W = -3/r^5, and d/dr.
 struct RadialT { double P, W, dP, dW; };
-__device__ __forceinline__ RadialT bare_radial(double rho) {
+__host__ __device__ __forceinline__ RadialT bare_radial(double rho) {
     const double ir = 1.0 / rho, ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
     return {ir3, -3.0 * ir5, -3.0 * ir3 * ir, 15.0 * ir5 * ir};
 }
@@ -71,7 +72,7 @@ __device__ __forceinline__ RadialT bare_radial(double rho) {
 // erfc-screened dipole tensor -grad grad erfc(gamma r)/r (Eq. terfc with the numerator
 // -r_a r_b C + delta r^2 B): P = B/r^3, W = -C/r^5, x = gamma r, e = 2x e^{-x^2}/sqrt(pi),
 // B = erfc x + e, C = 3 erfc x + e (3 + 2x^2); dB/dx = -2x e, dC/dx = -4x^3 e.
-__device__ __forceinline__ RadialT erfc_radial(double rho, double gamma) {
+__host__ __device__ __forceinline__ RadialT erfc_radial(double rho, double gamma) {
     const double x = gamma * rho, ex = kTwoOverSqrtPi * x * exp(-x * x), ec = erfc(x);
     const double Bx = ec + ex, Cx = 3.0 * ec + ex * (3.0 + 2.0 * x * x);
     const double ir = 1.0 / rho, ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
@@ -82,14 +83,14 @@ __device__ __forceinline__ RadialT erfc_radial(double rho, double gamma) {
 // Single-precision versions of fermi and tgg_radial for the pair passes of the
 // reduced-precision modes (same formulas).
 struct FermiF { float f, df_drho, df_dS; };
-__device__ __forceinline__ FermiF fermi_f(float rho, float S, float beta, float a) {
+__host__ __device__ __forceinline__ FermiF fermi_f(float rho, float S, float beta, float a) {
     const float x = rho / (beta * S);
     const float f = 1.0f / (1.0f + expf(-a * (x - 1.0f)));
     const float dfx = a * f * (1.0f - f);
     return {f, dfx / (beta * S), -dfx * x / S};
 }
 struct RadialF { float P, W, dP, dW, dPs, dWs; };
-__device__ __forceinline__ RadialF tgg_radial_f(float rho, float s) {
+__host__ __device__ __forceinline__ RadialF tgg_radial_f(float rho, float s) {
     const float z = rho / s, z2 = z * z;
     const float th = static_cast<float>(kTwoOverSqrtPi) * z * expf(-z2);
     const float F1 = erff(z) - th;

@@ -1,0 +1,117 @@
+"""The radial formulas of the pair kernels (csrc/pair_math.cuh, evaluated on the host through
+tests/pair_math_host.cu) against the oracle's dipole tensors and damping function (Eqs.
+dipole, tgg, terfc, fermi-damping): T = P I + W r r^T equals the oracle's T, T^GG and T^erfc,
+the radial derivatives equal central differences of the oracle's tensors, and the FP32
+versions of the reduced-precision modes agree with the FP64 ones to FP32 accuracy.  CPU only."""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as o
+from paper_2308_03140_gb300 import build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2308_03140_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def host():
+    out = os.path.join(HERE, "_build")
+    os.makedirs(out, exist_ok=True)
+    so = os.path.join(out, "pair_math_host.so")
+    src = os.path.join(HERE, "pair_math_host.cu")
+    deps = [src, os.path.join(CSRC, "pair_math.cuh"), os.path.join(CSRC, "internal.h")]
+    if not os.path.exists(so) or any(os.path.getmtime(d) > os.path.getmtime(so) for d in deps):
+        cmd = [build.nvcc(), *build.ARCH, "-O2", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", f"-I{CSRC}", src,
+               "-o", so]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        assert res.returncode == 0, res.stderr
+    lib = C.CDLL(so)
+    d, f = C.c_double, C.c_float
+    lib.host_fermi.argtypes = [d, d, d, d, C.c_void_p]
+    lib.host_fermi_f.argtypes = [f, f, f, f, C.c_void_p]
+    lib.host_tgg.argtypes = [d, d, C.c_void_p]
+    lib.host_tgg_f.argtypes = [f, f, C.c_void_p]
+    lib.host_bare.argtypes = [d, C.c_void_p]
+    lib.host_erfc.argtypes = [d, d, C.c_void_p]
+    return lib
+
+
+def call(fn, *args, n, dtype=np.float64):
+    out = np.zeros(n, dtype=dtype)
+    fn(*args, out.ctypes.data_as(C.c_void_p))
+    return out
+
+
+def tensor(P, W, r):
+    return P * np.eye(3) + W * np.outer(r, r)
+
+
+def rvecs():
+    rng = np.random.default_rng(4)
+    for rho in (0.9, 2.3, 4.0, 7.5, 15.0):
+        v = rng.normal(size=3)
+        yield rho * v / np.linalg.norm(v)
+
+
+def fd_tensor(fn, r, h=1e-6):
+    return np.array([(fn(r + h * e) - fn(r - h * e)) / (2 * h) for e in np.eye(3)])   # [c][a][b]
+
+
+def radial_deriv_tensor(P, W, dP, dW, r):
+    rho = np.linalg.norm(r)
+    out = []
+    for c in range(3):
+        e = np.eye(3)[c]
+        out.append(dP * r[c] / rho * np.eye(3) + dW * r[c] / rho * np.outer(r, r) + W * (np.outer(e, r) + np.outer(r, e)))
+    return np.array(out)
+
+
+def test_bare_and_gaussian_dipole_tensors(host):
+    for r in rvecs():
+        rho = np.linalg.norm(r)
+        P, W, dP, dW = call(host.host_bare, rho, n=4)
+        assert np.allclose(tensor(P, W, r), o.T_bare(r), rtol=1e-14, atol=0)
+        ref = fd_tensor(o.T_bare, r)
+        assert np.allclose(radial_deriv_tensor(P, W, dP, dW, r), ref, atol=1e-7 * np.abs(ref).max())
+        for s in (0.6, 1.5, 3.0):
+            P, W, dP, dW, dPs, dWs = call(host.host_tgg, rho, s, n=6)
+            T = o.T_gg(r, s)
+            assert np.allclose(tensor(P, W, r), T, rtol=1e-13, atol=1e-15 * np.abs(T).max())
+            ref = fd_tensor(lambda x: o.T_gg(x, s), r)
+            assert np.allclose(radial_deriv_tensor(P, W, dP, dW, r), ref, atol=1e-7 * np.abs(ref).max())
+            h = 1e-6 * s
+            refs = (o.T_gg(r, s + h) - o.T_gg(r, s - h)) / (2 * h)
+            # far beyond the width the s-derivative is ~e^{-z^2}: compare on the tensor's scale
+            assert np.allclose(tensor(dPs, dWs, r), refs, atol=1e-7 * np.abs(refs).max() + 1e-9 * np.abs(T).max() / s)
+            # FP32: W = (2 z^2 Th - 3 F1)/r^5 cancels at short range, costing a few digits
+            Pf = call(host.host_tgg_f, np.float32(rho), np.float32(s), n=6, dtype=np.float32)
+            assert np.allclose(Pf[:2], [P, W], rtol=2e-4, atol=2e-6 * max(abs(P), abs(W)))
+
+
+def test_erfc_screened_tensor(host):
+    for r in rvecs():
+        rho = np.linalg.norm(r)
+        for g in (0.15, 0.3, 0.6):
+            P, W, dP, dW = call(host.host_erfc, rho, g, n=4)
+            T = o.T_erfc(r, g)
+            assert np.allclose(tensor(P, W, r), T, rtol=1e-12, atol=1e-14 * np.abs(T).max() + 1e-300)
+            ref = fd_tensor(lambda x: o.T_erfc(x, g), r)
+            assert np.allclose(radial_deriv_tensor(P, W, dP, dW, r), ref, atol=1e-7 * np.abs(ref).max() + 1e-300)
+
+
+def test_fermi_damping(host):
+    for rho, S, beta, a in ((3.0, 7.0, 0.83, 6.0), (6.5, 7.0, 0.83, 6.0), (12.0, 6.2, 0.94, 20.0), (5.5, 6.2, 0.94, 20.0)):
+        f, dfr, dfs = call(host.host_fermi, rho, S, beta, a, n=3)
+        assert f == pytest.approx(o.fermi(rho, S, beta, a), rel=1e-14, abs=1e-300)
+        h = 1e-6
+        assert dfr == pytest.approx((o.fermi(rho + h, S, beta, a) - o.fermi(rho - h, S, beta, a)) / (2 * h), rel=1e-7,
+                                    abs=1e-8)
+        assert dfs == pytest.approx((o.fermi(rho, S + h, beta, a) - o.fermi(rho, S - h, beta, a)) / (2 * h), rel=1e-7,
+                                    abs=1e-8)
+        ff = call(host.host_fermi_f, np.float32(rho), np.float32(S), np.float32(beta), np.float32(a), n=3,
+                  dtype=np.float32)
+        assert np.allclose(ff, [f, dfr, dfs], rtol=1e-5, atol=1e-6)
