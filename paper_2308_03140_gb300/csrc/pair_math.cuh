@@ -46,8 +46,24 @@ __host__ __device__ __forceinline__ Fermi fermi(double rho, double S, double bet
 // Radial parts of T^GG(r; s) (Eq. tgg): P = F1/r^3, W = (2 z^2 Th - 3 F1)/r^5 with
 // z = r/s, Th = 2 z e^{-z^2}/sqrt(pi), F1 = erf z - Th; and d/dr, d/ds of both.
 struct Radial { double P, W, dP, dW, dPs, dWs; };
+// Beyond z = 8 the Gaussian parts vanish in FP64: erf z rounds to 1 and 2 z e^{-z^2}/sqrt(pi)
+// < 1.5e-27, so P, W, dP, dW are those of the bare tensor to the last bit and s dP/ds,
+// s dW/ds are below 1e-22 of dP, dW; the far branch skips erf and exp.
+constexpr double kGaussFar = 8.0;
+constexpr float kGaussFarF = 5.0f;   // FP32: erff(5) rounds to 1, 2 z e^{-z^2}/sqrt(pi) < 1e-10
 __host__ __device__ __forceinline__ Radial tgg_radial(double rho, double s) {
     const double z = rho / s, z2 = z * z;
+    if (z > kGaussFar) {
+        const double ir = 1.0 / rho, ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+        Radial o;
+        o.P = ir3;
+        o.W = -3.0 * ir5;
+        o.dP = -3.0 * ir3 * ir;
+        o.dW = 15.0 * ir5 * ir;
+        o.dPs = 0.0;
+        o.dWs = 0.0;
+        return o;
+    }
     const double th = kTwoOverSqrtPi * z * exp(-z2);
     const double F1 = erf(z) - th;
     const double G = 2.0 * z2 * th - 3.0 * F1;
@@ -92,6 +108,17 @@ __host__ __device__ __forceinline__ FermiF fermi_f(float rho, float S, float bet
 struct RadialF { float P, W, dP, dW, dPs, dWs; };
 __host__ __device__ __forceinline__ RadialF tgg_radial_f(float rho, float s) {
     const float z = rho / s, z2 = z * z;
+    if (z > kGaussFarF) {
+        const float ir = 1.0f / rho, ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+        RadialF o;
+        o.P = ir3;
+        o.W = -3.0f * ir5;
+        o.dP = -3.0f * ir3 * ir;
+        o.dW = 15.0f * ir5 * ir;
+        o.dPs = 0.0f;
+        o.dWs = 0.0f;
+        return o;
+    }
     const float th = static_cast<float>(kTwoOverSqrtPi) * z * expf(-z2);
     const float F1 = erff(z) - th;
     const float G = 2.0f * z2 * th - 3.0f * F1;

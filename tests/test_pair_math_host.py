@@ -115,3 +115,25 @@ def test_fermi_damping(host):
         ff = call(host.host_fermi_f, np.float32(rho), np.float32(S), np.float32(beta), np.float32(a), n=3,
                   dtype=np.float32)
         assert np.allclose(ff, [f, dfr, dfs], rtol=1e-5, atol=1e-6)
+
+
+def test_gaussian_tensor_far_branch_is_exact(host):
+    # beyond z = r/s = 8 the Gaussian parts round away in FP64: the far branch returns the bare
+    # tensor's radial parts, which the full formula reproduces to the last bit (host libm), and
+    # it joins the full formula continuously at the boundary
+    for s in (0.7, 1.3, 2.1):
+        for z in (8.0000001, 9.0, 13.0, 40.0):
+            rho = z * s
+            far = call(host.host_tgg, rho, s, n=6)
+            bare = call(host.host_bare, rho, n=4)
+            assert np.array_equal(far[:4], bare) and far[4] == 0.0 and far[5] == 0.0
+            x = np.array([rho, 0.0, 0.0])
+            T = o.T_gg(x, s)
+            assert np.allclose(tensor(far[0], far[1], x), T, rtol=2e-15, atol=0)
+        inside = call(host.host_tgg, 7.9999999 * s, s, n=6)   # the full formula just inside
+        assert np.allclose(inside[:4], call(host.host_bare, 7.9999999 * s, n=4), rtol=1e-15, atol=0)
+        assert abs(inside[4]) < 1e-22 * abs(inside[2]) * s and abs(inside[5]) < 1e-22 * abs(inside[3]) * s
+        for z in (5.0001, 6.0, 11.0):   # FP32 branch beyond z = 5
+            rf = call(host.host_tgg_f, np.float32(z * s), np.float32(s), n=6, dtype=np.float32)
+            assert rf[4] == 0.0 and rf[5] == 0.0
+            assert np.allclose(rf[:4], call(host.host_bare, float(np.float32(z * s)), n=4), rtol=1e-6, atol=0)
