@@ -374,6 +374,10 @@ __global__ void __launch_bounds__(128) k_scs_grad(AtomBufs b, double beta, doubl
         const T rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), ir = T(1) / rho;
         const auto f = PairMath<T>::fermi(rho, static_cast<T>(b.rv[i] + b.rv[j]), static_cast<T>(beta), static_cast<T>(a));
         const T sr = T(1) - f.f;
+        // Far pairs whose damping has rounded to f = 1 (1 - f = 0 and both derivatives 0)
+        // contribute exact zeros at every frequency: beyond ~3.8 beta (R_i + R_j) in FP32,
+        // ~7.1 in FP64.
+        if (sr == T(0) && f.df_drho == T(0) && f.df_dS == T(0)) continue;
         T pacc[4] = {0, 0, 0, 0};
         for (int k = 0; k < b.nf1; ++k) {
             const T *Vk = V + k * xstride, *Xk = X + k * xstride;

@@ -630,6 +630,7 @@ __global__ void __launch_bounds__(128) k_scs_grad_periodic(AtomBufs b, CellGeom 
                         const double rho = sqrt(rho2), ir = 1.0 / rho;
                         const Fermi f = fermi(rho, S, beta, a);
                         const double sr = 1.0 - f.f;
+                        if (sr == 0.0 && f.df_drho == 0.0 && f.df_dS == 0.0) continue;   // exact zeros
                         double Wr[3], Wtr[3];
                         for (int xx = 0; xx < 3; ++xx) {
                             Wr[xx] = Ws[3 * xx] * r[0] + Ws[3 * xx + 1] * r[1] + Ws[3 * xx + 2] * r[2];

@@ -137,3 +137,18 @@ def test_gaussian_tensor_far_branch_is_exact(host):
             rf = call(host.host_tgg_f, np.float32(z * s), np.float32(s), n=6, dtype=np.float32)
             assert rf[4] == 0.0 and rf[5] == 0.0
             assert np.allclose(rf[:4], call(host.host_bare, float(np.float32(z * s)), n=4), rtol=1e-6, atol=0)
+
+
+def test_far_damping_rounds_to_one_with_zero_derivatives(host):
+    # the SCS adjoint pair passes skip pairs whose damping has rounded to f = 1: then 1 - f
+    # and both derivatives are exactly zero, so every term of the pair is an exact zero
+    beta, a, S = 0.83, 6.0, 7.0
+    for eta in (7.2, 9.0, 20.0):            # FP64: e^{-6 (eta - 1)} below half an ulp of 1
+        f, dfr, dfs = call(host.host_fermi, eta * beta * S, S, beta, a, n=3)
+        assert f == 1.0 and dfr == 0.0 and dfs == 0.0
+    for eta in (3.8, 5.0, 9.0):             # FP32: below 2^-24 from eta ~ 3.77
+        ff = call(host.host_fermi_f, np.float32(eta * beta * S), np.float32(S), np.float32(beta), np.float32(a), n=3,
+                  dtype=np.float32)
+        assert ff[0] == 1.0 and ff[1] == 0.0 and ff[2] == 0.0
+    f, dfr, dfs = call(host.host_fermi, 6.0 * beta * S, S, beta, a, n=3)   # nearer: small but nonzero
+    assert f < 1.0 and dfr > 0.0 and dfs < 0.0
