@@ -25,7 +25,8 @@ extern "C" {
  * with B K x N (ldb).  C and D are M x N (ldc, ldd).  D may be NULL when beta == 0 and
  * may alias C.  mode 0 computes every 64x64 tile; mode 1 only tiles on or below the
  * diagonal (M == N); mode 2 only tiles on or above it and mirrors them into the lower
- * half (M == N, for products that are symmetric).  Leading dimensions must be even
+ * half (M == N, for products that are symmetric); mode 3 as mode 2 with the mirrored
+ * entries negated (antisymmetric results).  Leading dimensions must be even
  * (16-byte aligned rows).  The matrices must not overlap C except D == C. */
 int mbdk_gemm_f64(void *stream, int trans_b, int mode, int M, int N, int K, double alpha,
                   const double *A, long long lda, const double *B, long long ldb, double beta,

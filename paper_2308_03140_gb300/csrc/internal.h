@@ -288,8 +288,10 @@ void caxpby_identity(double *Z, const double *P, long long ld, int nk, double a,
 void cfrob_dev_identity(const double *P, long long ld, int n, int nk, double *out, cudaStream_t s);
 void cmax_abs_rowsum(const double *Q, long long ld, int nk, double *out, cudaStream_t s);
 // C = alpha A B + beta D for nk planar complex matrices (4 real FP64 GEMMs; D may be C).
+// herm: the result is Hermitian (as Y Z Y, Z Y Z for Hermitian Y, Z): upper tiles only,
+// mirrored (real part symmetric, imaginary part antisymmetric).
 void cgemm_f64(const double *A, const double *B, const double *D, double *C, long long ld, int nk, double alpha,
-               double beta, cudaStream_t s);
+               double beta, bool herm, cudaStream_t s);
 // Lanczos coefficients of every Q_k: coef[k][2j] = alpha_j, coef[k][2j+1] = beta_j.
 // work: 3 nk 2 ld doubles.
 void clanczos_coefficients(const double *Q, long long ld, int nk, int steps, double *work, double *coef,

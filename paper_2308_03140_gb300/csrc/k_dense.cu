@@ -114,7 +114,10 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs &g, int tiles_n) {
     }
     double *C = g.C + b * g.sC;
     const double *D = g.D ? g.D + b * g.sD : nullptr;
-    const bool mirror = (g.mode == 2) && (tm != tn);
+    // modes 2 and 3: upper tiles, mirrored into the lower half (mode 3 with a sign change,
+    // for antisymmetric results such as the imaginary part of a Hermitian product)
+    const bool mirror = (g.mode >= 2) && (tm != tn);
+    const double msign = g.mode == 3 ? -1.0 : 1.0;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -129,8 +132,8 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs &g, int tiles_n) {
             }
             *reinterpret_cast<double2 *>(C + m * g.ldc + n) = make_double2(v0, v1);
             if (mirror) {
-                C[n * g.ldc + m] = v0;
-                C[(n + 1) * g.ldc + m] = v1;
+                C[n * g.ldc + m] = msign * v0;
+                C[(n + 1) * g.ldc + m] = msign * v1;
             }
         }
 }

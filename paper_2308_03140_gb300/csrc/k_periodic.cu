@@ -752,17 +752,22 @@ void cmax_abs_rowsum(const double *Q, long long ld, int nk, double *out, cudaStr
 }
 
 void cgemm_f64(const double *A, const double *B, const double *D, double *C, long long ld, int nk, double alpha,
-               double beta, cudaStream_t s) {
+               double beta, bool herm, cudaStream_t s) {
     const long long m2 = ld * ld, st = 2 * m2;
     const int M = static_cast<int>(ld);
     const double *Ar = A, *Ai = A + m2, *Br = B, *Bi = B + m2;
     const double *Dr = D, *Di = D ? D + m2 : nullptr;
     double *Cr = C, *Ci = C + m2;
-    // Re C = alpha (Ar Br - Ai Bi) + beta Re D;  Im C = alpha (Ar Bi + Ai Br) + beta Im D
-    gemm_f64(GemmArgs{Ar, Br, Dr, Cr, ld, ld, ld, ld, st, st, st, st, M, M, M, nk, alpha, beta, 0, 0}, s);
-    gemm_f64(GemmArgs{Ai, Bi, Cr, Cr, ld, ld, ld, ld, st, st, st, st, M, M, M, nk, -alpha, 1.0, 0, 0}, s);
-    gemm_f64(GemmArgs{Ar, Bi, Di, Ci, ld, ld, ld, ld, st, st, st, st, M, M, M, nk, alpha, beta, 0, 0}, s);
-    gemm_f64(GemmArgs{Ai, Br, Ci, Ci, ld, ld, ld, ld, st, st, st, st, M, M, M, nk, alpha, 1.0, 0, 0}, s);
+    // Re C = alpha (Ar Br - Ai Bi) + beta Re D;  Im C = alpha (Ar Bi + Ai Br) + beta Im D.
+    // A Hermitian result has a symmetric real part and an antisymmetric imaginary part: each
+    // of the two products that build a part then computes only the upper tiles of the partial
+    // sum (the second reads the first's upper tiles through D = C) and mirrors them, with a
+    // sign change for the imaginary part.
+    const int mr = herm ? 2 : 0, mi = herm ? 3 : 0;
+    gemm_f64(GemmArgs{Ar, Br, Dr, Cr, ld, ld, ld, ld, st, st, st, st, M, M, M, nk, alpha, beta, mr, 0}, s);
+    gemm_f64(GemmArgs{Ai, Bi, Cr, Cr, ld, ld, ld, ld, st, st, st, st, M, M, M, nk, -alpha, 1.0, mr, 0}, s);
+    gemm_f64(GemmArgs{Ar, Bi, Di, Ci, ld, ld, ld, ld, st, st, st, st, M, M, M, nk, alpha, beta, mi, 0}, s);
+    gemm_f64(GemmArgs{Ai, Br, Ci, Ci, ld, ld, ld, ld, st, st, st, st, M, M, M, nk, alpha, 1.0, mi, 0}, s);
 }
 
 void clanczos_coefficients(const double *Q, long long ld, int nk, int steps, double *work, double *coef,

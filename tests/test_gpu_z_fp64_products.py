@@ -1,4 +1,5 @@
-"""GPU test of the FP64-accurate split GEMM (mbdk_gemm_f64_split: operands cut into exact
+"""GPU tests of FP64 products: the antisymmetric mirror mode of the FP64 GEMM (mode 3, for the
+imaginary parts of Hermitian products), and the FP64-accurate split GEMM (mbdk_gemm_f64_split: operands cut into exact
 TF32 slices, slice products on the tcgen05 tensor cores, exact FP32 partial sums added in
 FP64) against the exact product computed on the host in extended precision, and the FP64
 path with its Newton-Schulz products on it (MBD_PREC_FP64_SPLIT) against the oracle and the
@@ -86,3 +87,25 @@ def test_fp64_split_path_matches_oracle_and_fp64_path(workload):
     # both paths are FP64-accurate; E is a small difference of terms of order sum(omega)
     assert abs(E - E64) <= 1e-11 * abs(E64) and np.abs(gR - gR64).max() <= 1e-9 * np.abs(gR64).max()
     assert abs(st["ns_iterations"] - st64["ns_iterations"]) <= 1
+
+
+def test_gemm_f64_antisymmetric_mirror_mode():
+    # S K S with S symmetric and K antisymmetric is antisymmetric: mode 3 computes the upper
+    # tiles and writes their negatives below; P = K S first (mode 0, non-transposed path)
+    import torch
+    n = 192
+    g = torch.Generator(device="cpu").manual_seed(3)
+    X = torch.randn(n, n, generator=g, dtype=torch.float64)
+    S, K = (X + X.T).to(_dev()), (X - X.T).to(_dev())
+    P = torch.empty(n, n, dtype=torch.float64, device=_dev())
+    binding.mbdk_gemm_f64(K, S, P, mode=0, trans_b=False)
+    C = torch.full((n, n), float("nan"), dtype=torch.float64, device=_dev())
+    D = torch.randn(n, n, generator=g, dtype=torch.float64)
+    D = (D - D.T).to(_dev())
+    binding.mbdk_gemm_f64(S, P, C, alpha=0.5, beta=2.0, D=D, mode=3, trans_b=False)
+    torch.cuda.synchronize()
+    ref = 0.5 * (S @ K @ S) + 2.0 * D
+    assert torch.allclose(C, ref, rtol=1e-12, atol=1e-10)
+    tiles = torch.arange(n, device=_dev()) // 64
+    lower = tiles[:, None] > tiles[None, :]
+    assert torch.equal(C[lower], -C.T[lower])          # mirrored entries are exact negatives

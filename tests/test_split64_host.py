@@ -4,7 +4,7 @@ slices: the slices are exact FP32 (and TF32) values that add up to each entry wi
 2^-54 of its row's largest; every partial sum the tensor cores form over a K piece is an
 integer multiple of its unit below 2^22, so FP32 holds it exactly; and the sum of the kept
 slice products equals the FP64 product to FP64 accuracy.  CPU only; the device product is
-checked in test_gpu_z_fp64_split_gemm.py."""
+checked in test_gpu_z_fp64_products.py."""
 import ctypes as C
 import os
 import subprocess
