@@ -20,6 +20,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
+#include "ns_schedule.h"
 
 using namespace mbdgb;
 
@@ -659,18 +660,10 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
                             "Q has a non-positive eigenvalue (polarization catastrophe)");
             }
         }
-        // The tensor-core phase ends at its precision floor: below ns_tol; when a step taken
-        // from inside the quadratic basin (|I - P| < 0.5) fails to halve the residual; or when
-        // the step about to be taken cannot leave more than the floor.  For an eigenvalue
-        // x = 1 - e of P the plain step (al = 1) leaves 1 - x' = 3/4 e^2 + 1/4 e^3, so from
-        // |I - P|_F = r < 0.5 the next residual is at most 0.875 r^2 in exact arithmetic.
-        const bool last = it > 0 && (resid < ctx->opt.ns_tol || (prev < 0.5 && resid > 0.5 * prev) ||
-                                     (resid < 0.5 && 0.875 * resid * resid < kMixedFloor * std::sqrt(nd)));
-        double al = 1.0;
-        if (!last && lbound < 0.999) al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
-        const double c1 = 1.5 * al, c3 = -0.5 * al * al * al;
-        lbound = std::min(1.0, 0.5 * al * lbound * (3.0 - al * al * lbound * lbound));
-        ubound = 1.0;
+        // The tensor-core phase ends at its precision floor (ns::mixed_last).
+        const bool last = it > 0 && ns::mixed_last(resid, prev, ctx->opt.ns_tol, kMixedFloor * std::sqrt(nd));
+        const ns::Coeffs cf = ns::step(lbound, ubound, last);
+        const double c1 = cf.c1, c3 = cf.c3;
         {   // Y' = c1 Y + c3 Y P = NT(Y, P^T): symmetric
             TcOperands op{Y.op0(split), Y.op1(split), PTk.op0(split), PTk.op1(split), ld, ld};
             TcArgs g{M, M, M, static_cast<float>(c3), static_cast<float>(c1), Y.f, ld, Y2.f,
@@ -887,7 +880,7 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
         ubound = 1.05;
     }
     ctx->ns_scale = sc;
-    double lbound = std::sqrt(std::max(0.5 * th_min / sc, 1e-12));
+    double lbound = ns::lower_bound(th_min, sc, 0.5);   // the smallest over all Bloch vectors
     const double ss = std::sqrt(sc);
     // ---- batched complex coupled Newton-Schulz (same scaled steps as the finite path) ----
     double *Y = ctx->dQ, *Z = ctx->dZ, *P = ctx->dP, *Y2 = ctx->dY2, *Z2 = ctx->dZ2;
@@ -914,11 +907,8 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
                         "Q(q) has a non-positive eigenvalue (polarization catastrophe)");
         }
         const bool last = resid < ctx->opt.ns_tol;
-        double al = 1.0;
-        if (!last && lbound < 0.999) al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
-        const double c1 = 1.5 * al, c3 = -0.5 * al * al * al;
-        lbound = std::min(1.0, 0.5 * al * lbound * (3.0 - al * al * lbound * lbound));
-        ubound = 1.0;
+        const ns::Coeffs cf = ns::step(lbound, ubound, last);
+        const double c1 = cf.c1, c3 = cf.c3;
         timed_cgemm(Y, Pk, Y, Y2, c3, c1, kHermitianNs);   // Y' = c1 Y + c3 Y P (Hermitian: Y Z Y)
         if (it == 0) caxpby_identity(Z2, Pk, ld, nk, c1, c3, s);
         else timed_cgemm(Pk, Z, Z, Z2, c3, c1, kHermitianNs);   // Z' = c1 Z + c3 P Z (Hermitian: Z Y Z)
@@ -1085,7 +1075,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         ubound = 1.05;
     }
     ctx->ns_scale = sc;
-    double lbound = std::sqrt(std::max(0.25 * th_min / sc, 1e-12));   // lower bound on sqrt(eig(Z Y))
+    double lbound = ns::lower_bound(th_min, sc);   // lower bound on sqrt(eig(Z Y))
     const double ss = std::sqrt(sc);
     double *energy_out = out.energy ? out.energy : ctx->dscal;
     if (fp64_path(ctx->opt.precision)) {
@@ -1118,19 +1108,8 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
                             "Q has a non-positive eigenvalue (polarization catastrophe)");
             }
             const bool last = resid < ctx->opt.ns_tol;
-            // Scaled step (sign-function form of the coupled iteration): with x^2 the
-            // eigenvalues of P in [l^2, u^2], T = (al/2)(3 I - al^2 P) maps x to
-            // f(x) = (al x/2)(3 - al^2 x^2); al^2 = 3/(u^2 + u l + l^2) gives f(l) = f(u), so
-            // [l, u] goes onto [f(l), 1].  f stays positive for x < sqrt(3)/al, so any l
-            // below the true bound (and any u above it) only costs speed; an l above it does
-            // too, since f is increasing on (0, l] (l <= 1/al) with f(x)/x >= al >= 1 there, so
-            // smaller eigenvalues still grow every step.  al = 1 near convergence.
-            double al = 1.0;
-            if (!last && lbound < 0.999)
-                al = std::sqrt(3.0 / (ubound * ubound + ubound * lbound + lbound * lbound));
-            const double c1 = 1.5 * al, c3 = -0.5 * al * al * al;
-            lbound = std::min(1.0, 0.5 * al * lbound * (3.0 - al * al * lbound * lbound));
-            ubound = 1.0;
+            const ns::Coeffs cf = ns::step(lbound, ubound, last);   // scaled step (ns_schedule.h)
+            const double c1 = cf.c1, c3 = cf.c3;
             // Y' = Y T, Z' = T Z: Y' = c1 Y + c3 Y (Z Y) and Z' = c1 Z + c3 (Z Y) Z.  Y Z Y and
             // Z Y Z are symmetric for any symmetric Y, Z, so only their upper tiles are
             // computed.  (Using P^T in place of P, i.e. Y Y Z, breaks the coupling and makes
