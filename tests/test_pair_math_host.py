@@ -152,3 +152,29 @@ def test_far_damping_rounds_to_one_with_zero_derivatives(host):
         assert ff[0] == 1.0 and ff[1] == 0.0 and ff[2] == 0.0
     f, dfr, dfs = call(host.host_fermi, 6.0 * beta * S, S, beta, a, n=3)   # nearer: small but nonzero
     assert f < 1.0 and dfr > 0.0 and dfs < 0.0
+
+
+def test_screening_matrix_with_the_far_branch_matches_the_oracle(host):
+    # the screening matrices of a 300-atom cluster at all 16 grid points, formed with the
+    # kernel's formulas (far branch of T^GG included), against the oracle's builder
+    from paper_2308_03140_gb300 import synthetic as syn
+    s = syn.sphere_cluster(300, seed=1300)
+    a0, om, rv = s.alpha0_ref * s.ratio, 4 * s.c6_ref / (3 * s.alpha0_ref ** 2), s.rvdw_ref * np.cbrt(s.ratio)
+    u, _ = o.freq_grid(15)
+    R = np.ascontiguousarray(s.coords)
+    host.host_scs_matrix.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                     C.c_double, C.c_void_p]
+    n = 3 * len(R)
+    far = 0
+    for k in range(16):
+        al = np.ascontiguousarray(a0 / (1 + u[k] ** 2 / om ** 2))
+        sig = np.ascontiguousarray(np.cbrt(np.sqrt(2 / np.pi) * al / 3))
+        M = np.zeros((n, n))
+        host.host_scs_matrix(len(R), R.ctypes.data_as(C.c_void_p), al.ctypes.data_as(C.c_void_p),
+                             sig.ctypes.data_as(C.c_void_p), np.ascontiguousarray(rv).ctypes.data_as(C.c_void_p),
+                             0.83, 6.0, M.ctypes.data_as(C.c_void_p))
+        ref = o.scs_matrix(R, al, rv)
+        assert np.abs(M - ref).max() <= 1e-14 * np.abs(ref).max(), k
+        d = np.linalg.norm(R[:, None] - R[None], axis=-1)
+        far += np.sum(d / np.sqrt(sig[:, None] ** 2 + sig[None] ** 2) > 8)
+    assert far > 0.5 * 16 * len(R) ** 2     # most pair-frequency evaluations took the far branch
