@@ -178,3 +178,33 @@ def predict_alpha_bar(Xs, members, alpha_u):
 def estimated_error_per_atom(h, spread):
     """|dE| estimate per atom: sum_{i,u} |dE/d alpha_bar_i(u)| s_i(u) / N."""
     return float(np.abs(h * spread).sum() / h.shape[1])
+
+
+# ---- per-frequency Dyson moments (the inputs a second feature set adds) -----------------
+def dyson_moments(R, a0, om, rv, u, orders=3, beta=0.83, a=6.0):
+    """Terms of the Dyson series of Eq. scs at each frequency u_k.  With A(u) = alpha(u)^-1 +
+    B(u), B_ij = (1 - f_ij) T^GG_ij at the widths of alpha(u) (Eqs. scs-sr-dipole, tgg,
+    mayer), A^-1 = sum_q (-alpha B)^q alpha, so the contraction of Eq. contraction reads
+        alpha_bar_i(u) / alpha_i(u) = sum_q (-1)^q m_q,i(u),   m_q,i = Tr H^(q)_i / 3,
+        H^(0)_i = I,   H^(q)_i = sum_{j != i} alpha_j(u) B_ij(u) H^(q-1)_j   (q-hop sums).
+    Returns m [len(u), N, orders] for q = 1..orders, one pair at a time (no cutoff)."""
+    from oracle import oracle as orc
+    R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
+    N = R.shape[0]
+    out = np.zeros((len(u), N, orders))
+    for k, uk in enumerate(u):
+        al = a0 / (1.0 + uk * uk / om ** 2)
+        sig = orc_sigma(al)
+        B = {}
+        for i in range(N):
+            for j in range(N):
+                if j != i:
+                    r = R[j] - R[i]
+                    d = np.linalg.norm(r)
+                    B[i, j] = (1.0 - orc.fermi(d, rv[i] + rv[j], beta, a)) * orc.T_gg(r, np.hypot(sig[i], sig[j]))
+        H = [np.eye(3) for _ in range(N)]
+        for q in range(orders):
+            Hn = [sum((al[j] * B[i, j] @ H[j] for j in range(N) if j != i), np.zeros((3, 3))) for i in range(N)]
+            H = Hn
+            out[k, :, q] = [np.trace(h) / 3.0 for h in H]
+    return out

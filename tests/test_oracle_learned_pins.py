@@ -129,3 +129,51 @@ def test_fp16_rounding_is_round_to_nearest():
     P = [(np.array([[1.0 + 2 ** -12]]), np.array([0.1]))]
     W, b = L.round_fp16(P)[0]
     assert W[0, 0] == 1.0 and b[0] == np.float16(0.1).astype(np.float64)
+
+
+def test_dyson_moments_two_atoms_closed_form():
+    # one pair: B_01 = B_10 = B (even in r), so H^(1)_0 = a_1 B, H^(2)_0 = a_1 a_0 B^2,
+    # H^(3)_0 = a_1^2 a_0 B^3 at each frequency
+    from oracle import oracle as orc
+    R = np.array([[0.0, 0.0, 0.0], [0.0, 3.3, 4.4]])
+    a0, om, rv = np.array([7.0, 9.0]), np.array([0.4, 0.6]), np.array([3.1, 3.6])
+    u = np.array([0.0, 0.3, 2.0])
+    m = L.dyson_moments(R, a0, om, rv, u)
+    for k, uk in enumerate(u):
+        al = a0 / (1 + uk ** 2 / om ** 2)
+        s = np.hypot(*L.orc_sigma(al))
+        Bm = (1 - orc.fermi(5.5, 6.7, 0.83, 6.0)) * orc.T_gg(R[1] - R[0], s)
+        t1, t2, t3 = (np.trace(np.linalg.matrix_power(Bm, p)) / 3 for p in (1, 2, 3))
+        assert np.allclose(m[k, :, 0], [al[1] * t1, al[0] * t1], rtol=1e-13)
+        assert np.allclose(m[k, :, 1], [al[0] * al[1] * t2] * 2, rtol=1e-13)
+        assert np.allclose(m[k, :, 2], [al[1] ** 2 * al[0] * t3, al[0] ** 2 * al[1] * t3], rtol=1e-13)
+
+
+def test_dyson_series_converges_to_the_screening():
+    # a dilute cluster (weak coupling): from the first order on, the partial sums
+    # 1 - m1 + m2 - m3 + m4 approach the exact screened alpha_bar / alpha of the oracle, each
+    # order closer than the one before (here 2.6e-2, 3.3e-3, 8.9e-4, 1.7e-4)
+    import oracle as o
+    rng = np.random.default_rng(8)
+    R = rng.uniform(0, 16, (6, 3))
+    a0, om, rv = rng.uniform(3, 6, 6), rng.uniform(0.4, 0.9, 6), rng.uniform(3, 4, 6)
+    u, _ = o.freq_grid(15)
+    ab = o.scs(R, a0, om, rv)                                    # [16, N], exact screening
+    m = L.dyson_moments(R, a0, om, rv, u, orders=4)
+    al = a0[None] / (1 + u[:, None] ** 2 / om[None] ** 2)
+    exact = ab / al
+    errs = [np.abs(exact - (1 + sum((-1) ** (q + 1) * m[..., q] for q in range(Q)))).max() for Q in range(1, 5)]
+    assert errs[0] > errs[1] > errs[2] > errs[3] and errs[3] < 1e-2 * errs[0]
+
+
+def test_dyson_moments_invariances():
+    rng = np.random.default_rng(9)
+    R = rng.uniform(0, 9, (4, 3))
+    a0, om, rv = rng.uniform(4, 12, 4), rng.uniform(0.3, 1.2, 4), rng.uniform(3, 4, 4)
+    u = np.array([0.0, 0.6, 5.0])
+    m = L.dyson_moments(R, a0, om, rv, u)
+    th = 0.7
+    Rot = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    assert np.allclose(L.dyson_moments(R @ Rot.T + 3.0, a0, om, rv, u), m, rtol=1e-11, atol=1e-15)
+    p = np.array([2, 0, 3, 1])
+    assert np.allclose(L.dyson_moments(R[p], a0[p], om[p], rv[p], u), m[:, p], rtol=1e-12, atol=1e-15)
