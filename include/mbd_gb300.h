@@ -149,15 +149,23 @@ int mbd_evaluate_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
                      const double *volume_ratio, double *energy, double *grad_coords,
                      double *grad_params, double *alpha_scs);
 
+/* Number of successful evaluations (mbd_evaluate, mbd_evaluate_dev) of the context so far;
+ * after an evaluation it is that evaluation's number, which mbd_backward_dev checks.
+ * MBD_ERR_INPUT if ctx or count is NULL. */
+int mbd_get_evaluation_count(const mbd_ctx *ctx, long long *count);
+
 /* Hand-written backward of the last evaluation (the analytic gradient of Sec. 2.4 as a
  * reverse-mode pass): from the device state the last mbd_evaluate or mbd_evaluate_dev
  * left in the context (screening factors, M^{-1} 1 and Q^{-1/2}), computes
  * grad_energy[0] * dE/dX for coordinates (grad_coords [n_atoms][3]) and free-atom
  * parameters (grad_params [4][n_atoms]); either may be NULL.  All pointers are device
- * pointers; grad_energy may be NULL (factor 1).  The inputs must be the ones of that
- * evaluation (same values; they are read again).  MBD_ERR_STATE if no evaluation has
- * succeeded since the context was created or its geometry last reallocated. */
-int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coords,
+ * pointers; grad_energy may be NULL (factor 1).  `evaluation` is the number
+ * (mbd_get_evaluation_count, read right after the forward call) of the evaluation to
+ * differentiate: MBD_ERR_STATE if the context's last evaluation is another one, whose state
+ * has replaced it (0 skips the check).  The inputs must be the ones of that evaluation (same
+ * values; they are read again).  MBD_ERR_STATE if no evaluation has succeeded since the
+ * context was created or its geometry last reallocated. */
+int mbd_backward_dev(mbd_ctx *ctx, void *stream, long long evaluation, int n_atoms, const double *coords,
                      const double *alpha0_ref, const double *c6_ref, const double *rvdw_ref,
                      const double *volume_ratio, const double *grad_energy, double *grad_coords,
                      double *grad_params);

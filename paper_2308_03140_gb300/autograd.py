@@ -24,6 +24,7 @@ class MBDEnergyFunction(torch.autograd.Function):
         energy = torch.empty(1, dtype=torch.float64, device=coords.device)
         calc.evaluate_dev(*ins, energy)
         ctx.calc = calc
+        ctx.evaluation = calc.evaluation_count()
         ctx.save_for_backward(*ins)
         return energy[0]
 
@@ -36,7 +37,12 @@ class MBDEnergyFunction(torch.autograd.Function):
         gR = torch.empty(N, 3, dtype=torch.float64, device=ins[0].device) if need_r else None
         gp = torch.empty(4, N, dtype=torch.float64, device=ins[0].device) if need_p else None
         ge = grad_e.detach().to(torch.float64).reshape(1).contiguous()
-        ctx.calc.backward_dev(*ins, grad_energy=ge, grad_coords=gR, grad_params=gp)
+        if ctx.calc.evaluation_count() != ctx.evaluation:
+            # another forward on the same context has replaced this one's device state (e.g.
+            # E = f(x1) + f(x2)): evaluate these inputs again before differentiating
+            ctx.calc.evaluate_dev(*ins, torch.empty(1, dtype=torch.float64, device=ins[0].device))
+            ctx.evaluation = ctx.calc.evaluation_count()
+        ctx.calc.backward_dev(*ins, grad_energy=ge, grad_coords=gR, grad_params=gp, evaluation=ctx.evaluation)
         out = [gR] + ([gp[k] for k in range(4)] if need_p else [None] * 4)
         return (*out, None)
 

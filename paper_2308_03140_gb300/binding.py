@@ -25,6 +25,7 @@ MBD_PREC_FP64, MBD_PREC_TF32, MBD_PREC_BF16X3, MBD_PREC_TF32X3, MBD_PREC_FP64_SP
 # Every symbol declared in include/mbd_gb300.h.
 EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry",
            "mbd_set_free_atom_params", "mbd_evaluate", "mbd_evaluate_dev", "mbd_backward_dev",
+           "mbd_get_evaluation_count",
            "mbd_get_lattice_gradient", "mbd_set_scs_model", "mbd_get_learned_stats", "mbd_screen",
            "mbd_get_scs_detail", "mbd_log_energy", "mbd_ts_energy",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
@@ -77,7 +78,8 @@ def load(path: str | None = None):
     L.mbd_set_free_atom_params.argtypes = [vp, _P, _P, _P, _P]
     L.mbd_evaluate.argtypes = [vp, _P, _P, _P, _P, _P]
     L.mbd_evaluate_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
-    L.mbd_backward_dev.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.mbd_backward_dev.argtypes = [vp, vp, C.c_longlong, i, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.mbd_get_evaluation_count.argtypes = [vp, C.POINTER(C.c_longlong)]
     L.mbd_get_scs_detail.argtypes = [vp, _P, _P, _P, _P]
     L.mbd_get_lattice_gradient.argtypes = [vp, _P]
     L.mbd_set_scs_model.argtypes = [vp, i, vp, vp, vp]
@@ -262,14 +264,23 @@ class MBD:
                                        _tptr(grad_params), _tptr(alpha_scs))
         self._check(rc)
 
+    def evaluation_count(self):
+        """Number of successful evaluations of this context (the last one's number)."""
+        c = C.c_longlong()
+        self._check(self.lib.mbd_get_evaluation_count(self.h, C.byref(c)))
+        return c.value
+
     def backward_dev(self, coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio, grad_energy=None,
-                     grad_coords=None, grad_params=None, stream=None):
+                     grad_coords=None, grad_params=None, stream=None, evaluation=0):
         """Hand-written backward of the last evaluation (device tensors, outputs
-        preallocated): grad_energy * dE/dX for coordinates and parameters."""
+        preallocated): grad_energy * dE/dX for coordinates and parameters.  `evaluation`:
+        the number of the evaluation to differentiate (evaluation_count() after it; 0: the
+        last, unchecked)."""
         import torch
         if stream is None:
             stream = torch.cuda.current_stream(coords.device)
-        rc = self.lib.mbd_backward_dev(self.h, C.c_void_p(stream.cuda_stream), int(coords.shape[0]),
+        rc = self.lib.mbd_backward_dev(self.h, C.c_void_p(stream.cuda_stream), int(evaluation),
+                                       int(coords.shape[0]),
                                        _tptr(coords), _tptr(alpha0_ref), _tptr(c6_ref), _tptr(rvdw_ref),
                                        _tptr(volume_ratio), _tptr(grad_energy), _tptr(grad_coords),
                                        _tptr(grad_params))

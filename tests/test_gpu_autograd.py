@@ -60,3 +60,43 @@ def test_backward_without_forward_is_an_error():
         with pytest.raises(binding.MBDError) as e:
             m.backward_dev(*ins, grad_coords=gR)
         assert e.value.code == 7
+
+
+def test_two_forwards_on_one_context_before_backward():
+    # E = f(x1) + f(x2) on one module: the second forward replaces the device state of the
+    # first, so the first's backward must evaluate again, not differentiate the second state
+    import torch
+    from paper_2308_03140_gb300.autograd import MBDEnergy
+    s1 = syn.cube_cluster(6, 8.0, 2.5, seed=31)
+    s2 = syn.cube_cluster(6, 8.0, 2.5, seed=32)
+    mod = MBDEnergy(6)
+    x1, x2 = _tensors(s1), _tensors(s2)
+    E = mod(*x1) + 2.0 * mod(*x2)
+    E.backward()
+    for sysm, x, w in ((s1, x1, 1.0), (s2, x2, 2.0)):
+        _, gR_ref, gp_ref = o.mbd_rsscs_gradient(*o.system_args(sysm), mode="adjoint")
+        assert np.max(np.abs(x[0].grad.cpu().numpy() - w * gR_ref)) <= 3e-8
+        for k in range(4):
+            assert np.max(np.abs(x[k + 1].grad.cpu().numpy() - w * gp_ref[k])) <= 3e-8 * max(1.0, np.abs(gp_ref[k]).max())
+
+
+def test_backward_of_a_replaced_evaluation_is_an_error():
+    import torch
+    s1 = syn.cube_cluster(4, 7.0, 2.5, seed=41)
+    s2 = syn.cube_cluster(4, 7.0, 2.5, seed=42)
+    x1, x2 = _tensors(s1, requires_grad=False), _tensors(s2, requires_grad=False)
+    dev = x1[0].device
+    with binding.MBD(0) as m:
+        m.set_geometry(s1.coords)
+        e = torch.empty(1, dtype=torch.float64, device=dev)
+        m.evaluate_dev(*x1, e)
+        first = m.evaluation_count()
+        m.evaluate_dev(*x2, e)
+        assert m.evaluation_count() == first + 1
+        gR = torch.empty(4, 3, dtype=torch.float64, device=dev)
+        with pytest.raises(binding.MBDError) as err:
+            m.backward_dev(*x1, grad_coords=gR, evaluation=first)
+        assert err.value.code == 7   # MBD_ERR_STATE
+        m.backward_dev(*x2, grad_coords=gR, evaluation=first + 1)
+        _, gR_ref, _ = o.mbd_rsscs_gradient(*o.system_args(s2), mode="adjoint")
+        assert np.max(np.abs(gR.cpu().numpy() - gR_ref)) <= 3e-8
