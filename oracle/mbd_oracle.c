@@ -804,58 +804,61 @@ static void mbd_pair_adjoint(int N, const double *R, const double *ab0, const do
     free(g_c);
 }
 
-static int grad_adjoint(orc_state *S, const double *a0ref, const double *c6ref,
-                        const double *rref, const double *ratio, double *gR, double *gp) {
-    int N = S->N, n = S->n, nf = S->nf;
-    double *g_a0 = calloc(N, sizeof(double)), *g_om = calloc(N, sizeof(double));
-    double *g_rv = calloc(N, sizeof(double));
+/* MBD part of the adjoint gradient and the chain through the screened parameters,
+ * Eqs. (mbd-gradient), (casimir-polder), (scale-rvdw-scs), from Z = Q^{-1/2}:
+ * gR, g_a0, g_rv (written) get the MBD pair terms and the direct parts of R_bar =
+ * R_vdW (abar0/alpha0)^(1/3); h[k*N + i] = dE/d alpha_bar_i(u_k) (written) for k = 0..nf. */
+void orc_mbd_chain(int N, int nf, const double *R, const double *a0, const double *rv,
+                   const double *alpha_bar, const double *abar0, const double *c6bar,
+                   const double *ombar, const double *rbar, const double *wu, const double *Z,
+                   double beta, double a, double *h, double *g_a0, double *g_rv, double *gR) {
     double *g_ombar = calloc(N, sizeof(double)), *g_ab0 = calloc(N, sizeof(double));
     double *g_rbar = calloc(N, sizeof(double));
     memset(gR, 0, sizeof(double) * 3 * N);
-    /* MBD part */
-    mbd_pair_adjoint(N, S->R, S->abar0, S->ombar, S->rbar, S->Z, S->beta, S->a, g_ombar, g_ab0, g_rbar, gR);
-    /* chain through the screened parameters */
-    double *h = calloc((size_t)(nf + 1) * N, sizeof(double));
+    mbd_pair_adjoint(N, R, abar0, ombar, rbar, Z, beta, a, g_ombar, g_ab0, g_rbar, gR);
     for (int i = 0; i < N; ++i) {
-        double ab0 = S->abar0[i], x = ab0 / S->a0[i];
+        double ab0 = abar0[i], x = ab0 / a0[i];
         double g_c6 = g_ombar[i] * 4.0 / (3.0 * ab0 * ab0);
-        double gab0 = g_ab0[i] - g_ombar[i] * 8.0 * S->c6bar[i] / (3.0 * ab0 * ab0 * ab0)
-                    + g_rbar[i] * S->rv[i] / (3.0 * cbrt(x) * cbrt(x) * S->a0[i]);
-        g_a0[i] += -g_rbar[i] * S->rv[i] / (3.0 * cbrt(x) * cbrt(x)) * ab0 / (S->a0[i] * S->a0[i]);
-        g_rv[i] += g_rbar[i] * cbrt(x);
+        double gab0 = g_ab0[i] - g_ombar[i] * 8.0 * c6bar[i] / (3.0 * ab0 * ab0 * ab0)
+                    + g_rbar[i] * rv[i] / (3.0 * cbrt(x) * cbrt(x) * a0[i]);
+        g_a0[i] = -g_rbar[i] * rv[i] / (3.0 * cbrt(x) * cbrt(x)) * ab0 / (a0[i] * a0[i]);
+        g_rv[i] = g_rbar[i] * cbrt(x);
         h[i] = gab0;
         for (int k = 1; k <= nf; ++k)
-            h[(size_t)k * N + i] = g_c6 * 3.0 / ORC_PI * S->wu[k] * 2.0 * S->alpha_bar[(size_t)k * N + i];
+            h[(size_t)k * N + i] = g_c6 * 3.0 / ORC_PI * wu[k] * 2.0 * alpha_bar[(size_t)k * N + i];
     }
-    /* SCS adjoint, per frequency */
-    double *X = malloc(sizeof(double) * 3 * n), *V = malloc(sizeof(double) * 3 * n);
+    free(g_ombar); free(g_ab0); free(g_rbar);
+}
+
+/* SCS part of the adjoint gradient, Eq. (scs-gradient) in adjoint form: per frequency u_k,
+ * with X = M^{-1} E and V = M^{-1} H (n x 3 each, X[k][p][c], V[k][p][c]; H[p][c] =
+ * h_k[p/3] delta_{p%3,c}), dE = -1/3 sum_pq dM_pq (V X^T)_pq, accumulated into g_a0, g_om,
+ * g_rv (through alpha_i(u) of Eq. dyn-pol and the damping radii) and gR. */
+void orc_scs_adjoint_pass(int N, int nf, const double *R, const double *a0, const double *om,
+                          const double *rv, const double *u, double beta, double a,
+                          const double *X_all, const double *V_all, double *g_a0, double *g_om,
+                          double *g_rv, double *gR) {
+    int n = 3 * N;
+    double *gal = malloc(sizeof(double) * N);
     for (int k = 0; k <= nf; ++k) {
-        const double *Ab = S->Abar + (size_t)k * n * n;
-        double u = S->u[k];
-        for (int p = 0; p < n; ++p)
-            for (int c = 0; c < 3; ++c) {
-                double x = 0.0, v = 0.0;
-                for (int jj = 0; jj < N; ++jj) {
-                    x += Ab[(size_t)p * n + 3 * jj + c];
-                    v += Ab[(size_t)p * n + 3 * jj + c] * h[(size_t)k * N + jj];
-                }
-                X[3 * p + c] = x; V[3 * p + c] = v;
-            }
-        /* W = V X^T; dE = -1/3 sum_pq dM_pq W_pq.  gal[i] collects dE/d alpha_i(u). */
-        double *gal = calloc(N, sizeof(double));
+        const double *X = X_all + (size_t)k * 3 * n, *V = V_all + (size_t)k * 3 * n;
+        double uk = u[k];
+        memset(gal, 0, sizeof(double) * N);
+        /* W = V X^T; gal[i] collects dE/d alpha_i(u).  Rows i run in parallel; every
+         * contribution is summed by the reduction. */
+#pragma omp parallel for schedule(dynamic) reduction(+ : gal[:N], g_rv[:N], gR[:3 * N])
         for (int i = 0; i < N; ++i) {
-            double ali = alpha_iu(S->a0[i], S->om[i], u);
+            double ali = alpha_iu(a0[i], om[i], uk);
             double wd = 0.0;
             for (int c = 0; c < 3; ++c)
                 for (int cc = 0; cc < 3; ++cc) wd += V[3 * (3 * i + c) + cc] * X[3 * (3 * i + c) + cc];
             gal[i] += -1.0 / 3.0 * wd * (-1.0 / (ali * ali));   /* d(1/alpha) = -dalpha/alpha^2 */
             for (int m = 0; m < N; ++m) {
                 if (m == i) continue;
-                double r[3] = {S->R[3 * m] - S->R[3 * i], S->R[3 * m + 1] - S->R[3 * i + 1],
-                               S->R[3 * m + 2] - S->R[3 * i + 2]};
-                double alm = alpha_iu(S->a0[m], S->om[m], u);
+                double r[3] = {R[3 * m] - R[3 * i], R[3 * m + 1] - R[3 * i + 1], R[3 * m + 2] - R[3 * i + 2]};
+                double alm = alpha_iu(a0[m], om[m], uk);
                 double dBdr[27], dBda[9], dBdb[9], dBdS[9];
-                scs_block_derivs(r, ali, alm, S->rv[i] + S->rv[m], S->beta, S->a, dBdr, dBda, dBdb, dBdS);
+                scs_block_derivs(r, ali, alm, rv[i] + rv[m], beta, a, dBdr, dBda, dBdb, dBdS);
                 double wa = 0.0, wb = 0.0, wS = 0.0, wr[3] = {0, 0, 0};
                 for (int x = 0; x < 3; ++x)
                     for (int y = 0; y < 3; ++y) {
@@ -877,15 +880,44 @@ static int grad_adjoint(orc_state *S, const double *a0ref, const double *c6ref,
             }
         }
         for (int i = 0; i < N; ++i) {
-            double q = 1.0 + u * u / (S->om[i] * S->om[i]);
+            double q = 1.0 + uk * uk / (om[i] * om[i]);
             g_a0[i] += gal[i] / q;
-            g_om[i] += gal[i] * S->a0[i] * 2.0 * u * u / (S->om[i] * S->om[i] * S->om[i]) / (q * q);
+            g_om[i] += gal[i] * a0[i] * 2.0 * uk * uk / (om[i] * om[i] * om[i]) / (q * q);
         }
-        free(gal);
     }
+    free(gal);
+}
+
+/* Adjoint gradient: the MBD pair pass and chain (orc_mbd_chain), X = M^{-1} E and
+ * V = M^{-1} H from the full screened polarizabilities Abar = M^{-1} of the forward pass,
+ * the SCS pass (orc_scs_adjoint_pass), and the chain through the TS scaling. */
+static int grad_adjoint(orc_state *S, const double *a0ref, const double *c6ref,
+                        const double *rref, const double *ratio, double *gR, double *gp) {
+    int N = S->N, n = S->n, nf = S->nf;
+    double *g_a0 = calloc(N, sizeof(double)), *g_om = calloc(N, sizeof(double));
+    double *g_rv = calloc(N, sizeof(double));
+    double *h = calloc((size_t)(nf + 1) * N, sizeof(double));
+    orc_mbd_chain(N, nf, S->R, S->a0, S->rv, S->alpha_bar, S->abar0, S->c6bar, S->ombar, S->rbar, S->wu,
+                  S->Z, S->beta, S->a, h, g_a0, g_rv, gR);
+    double *X = malloc(sizeof(double) * (size_t)(nf + 1) * 3 * n);
+    double *V = malloc(sizeof(double) * (size_t)(nf + 1) * 3 * n);
+    for (int k = 0; k <= nf; ++k) {
+        const double *Ab = S->Abar + (size_t)k * n * n;
+        double *Xk = X + (size_t)k * 3 * n, *Vk = V + (size_t)k * 3 * n;
+        for (int p = 0; p < n; ++p)
+            for (int c = 0; c < 3; ++c) {
+                double x = 0.0, v = 0.0;
+                for (int jj = 0; jj < N; ++jj) {
+                    x += Ab[(size_t)p * n + 3 * jj + c];
+                    v += Ab[(size_t)p * n + 3 * jj + c] * h[(size_t)k * N + jj];
+                }
+                Xk[3 * p + c] = x; Vk[3 * p + c] = v;
+            }
+    }
+    orc_scs_adjoint_pass(N, nf, S->R, S->a0, S->om, S->rv, S->u, S->beta, S->a, X, V, g_a0, g_om, g_rv, gR);
     if (gp) ts_chain(N, a0ref, c6ref, rref, ratio, g_a0, g_om, g_rv, gp);
     free(X); free(V); free(h);
-    free(g_a0); free(g_om); free(g_rv); free(g_ombar); free(g_ab0); free(g_rbar);
+    free(g_a0); free(g_om); free(g_rv);
     return ORC_OK;
 }
 

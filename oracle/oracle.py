@@ -65,6 +65,13 @@ def lib():
             L.orc_mbd_rsscs_gradient.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, i, i, P, _dp, _dp]
             L.orc_mbd_nl.argtypes = [i, _dp, _dp, _dp, _dp, _dp, d, d, P, P, P, P]
             L.orc_mbd_log_energy.argtypes = [i, _dp, _dp, _dp, _dp, d, d, i, i, P, _dp]
+            L.orc_mbd_chain.argtypes = [i, i, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, d, d,
+                                        _dp, _dp, _dp, _dp]
+            L.orc_mbd_chain.restype = None
+            L.orc_scs_adjoint_pass.argtypes = [i, i, _dp, _dp, _dp, _dp, _dp, d, d, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_scs_adjoint_pass.restype = None
+            L.ts_chain.argtypes = [i, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.ts_chain.restype = None
             L.alpha_iu.argtypes = [d, d, d]
             L.alpha_iu.restype = d
             # periodic
@@ -238,6 +245,33 @@ def mbd_rsscs_gradient(R, a0ref, c6ref, rref, ratio, beta=0.83, a=6.0, n_freq=15
                                       n_freq, 0 if mode == "forward" else 1, C.byref(E), gR, gp)
     _check(rc, "mbd_rsscs_gradient")
     return E.value, gR, gp
+
+
+def gradient_from_dense_steps(R, a0ref, c6ref, rref, ratio, alpha_bar, X, Z, solve, beta=0.83, a=6.0, n_freq=15):
+    """The oracle's adjoint gradient (Eqs. mbd-gradient, scs-gradient) with its two dense steps
+    supplied by the caller: X [nf+1, n, 3] = M(u_k)^{-1} E and Z = Q^{-1/2} (n x n), and
+    solve(k, H) -> M(u_k)^{-1} H for the adjoint right-hand sides.  Every other step (TS
+    scaling, screened parameters, the MBD pair pass and chain, the SCS pair pass, the TS
+    chain) is the oracle's.  Returns dE/dR [N,3], dE/d(alpha0_ref, C6_ref, R_ref, ratio) [4,N]."""
+    R = _a(R).reshape(-1, 3); N = R.shape[0]; n = 3 * N; nf = n_freq
+    a0, om, rv = ts_scaling(a0ref, c6ref, rref, ratio)
+    u, wu = freq_grid(nf)
+    rc, (abar0, c6bar, ombar, rbar) = screened_params(alpha_bar, a0, rv, nf)
+    _check(rc, "gradient_from_dense_steps")
+    h = np.zeros((nf + 1) * N); g_a0, g_om, g_rv, gR = np.zeros(N), np.zeros(N), np.zeros(N), np.zeros(3 * N)
+    lib().orc_mbd_chain(N, nf, R, a0, rv, _a(alpha_bar), abar0, c6bar, ombar, rbar, wu, _a(Z), beta, a, h, g_a0,
+                        g_rv, gR)
+    h = h.reshape(nf + 1, N)
+    V = np.zeros((nf + 1, n, 3))
+    for k in range(nf + 1):
+        H = np.zeros((n, 3))
+        for c in range(3):
+            H[c::3, c] = h[k]
+        V[k] = solve(k, H)
+    lib().orc_scs_adjoint_pass(N, nf, R, a0, om, rv, u, beta, a, _a(X), _a(V), g_a0, g_om, g_rv, gR)
+    gp = np.zeros(4 * N)
+    lib().ts_chain(N, _a(a0ref), _a(c6ref), _a(rref), _a(ratio), g_a0, g_om, g_rv, gp)
+    return gR.reshape(N, 3), gp.reshape(4, N)
 
 
 def mbd_log_energy(R, alpha0, omega, rdamp, beta=0.83, a=6.0, n_freq=15, max_order=2):

@@ -98,6 +98,41 @@ def test_tc_gemm_symmetric_mirror_and_split_output(kind):
         assert torch.equal(Ch.cpu(), Ch.cpu().T) and torch.equal(Cl.cpu(), Cl.cpu().T)
 
 
+@pytest.mark.parametrize("kind", [0, 2])
+def test_tc_gemm_lower_tiles_only(kind):
+    # mode 1: C = beta D + alpha S S^T on the tiles on or below the diagonal; the tiles above
+    # it are not written (the FP32 Cholesky's trailing update reads only the lower triangle)
+    import torch
+    dev = torch.device("cuda:0")
+    n, K = 512, 256
+    g = torch.Generator(device="cpu").manual_seed(5)
+    S = torch.randn(n, K, generator=g, dtype=torch.float32)
+    D = torch.randn(n, n, generator=g, dtype=torch.float32)
+    C = torch.full((n, n), float("nan"), dtype=torch.float32, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    if kind == 0:
+        rc = binding.mbdk_gemm_tc(0, S.to(dev), S.to(dev), C, alpha=-1.0, beta=1.0, D=D.to(dev), mode=1, err=err,
+                                  chunk_stages=2)
+    else:
+        Sh, Sl = _split(S, kind)
+        rc = binding.mbdk_gemm_tc(kind, Sh.to(dev), Sh.to(dev), C, A1=Sl.to(dev), B1=Sl.to(dev), alpha=-1.0,
+                                  beta=1.0, D=D.to(dev), mode=1, err=err, chunk_stages=2)
+    torch.cuda.synchronize()
+    assert rc == 0 and err.item() == 0
+    Cc = C.cpu().double()
+    ref = D.double() - S.double() @ S.double().T
+    scale = (S.double().abs() @ S.double().abs().T).max().item()
+    T = n // 128
+    for tm in range(T):
+        for tn in range(T):
+            blk = Cc[tm * 128:(tm + 1) * 128, tn * 128:(tn + 1) * 128]
+            if tm >= tn:
+                err_t = (blk - ref[tm * 128:(tm + 1) * 128, tn * 128:(tn + 1) * 128]).abs().max().item() / scale
+                assert err_t < TOL[kind], (tm, tn, err_t)
+            else:
+                assert torch.isnan(blk).all(), (tm, tn)
+
+
 def test_tc_gemm_rejects_bad_shapes():
     import torch
     dev = torch.device("cuda:0")
@@ -115,18 +150,31 @@ def _eval(sysm, precision):
         return E, gR, gp, m.stats()
 
 
-# Stated per-mode bounds.  BF16x3 and TF32x3 meet |dE| <= 1e-6 Ha/atom; TF32 runs the
-# iteration on 10-bit products, whose rounding breaks the coupling invariant Y = Y0 Z by
-# more than the FP64 correction can remove (a commutator error), so it is held to a
-# looser bound and reported, not used for the headline.
-# Measured (GB300, 2-stage chunks, N = 500 / 2000): |dE|/N about 3.4e-6 (TF32), 6e-9
-# (BF16x3), 6e-9 (TF32x3) Ha/atom; largest force error 2.5 / 0.09 / 0.008 (N = 500) and
-# 20 / 0.17 / 0.011 (N = 2000) of the largest force, the TF32x3 figure before dE/d omega_bar
-# was taken from the second-order block traces of Q^{1/2} (now 3.2e-6 of the largest force at
-# N = 2000).  Forces of the mixed modes take the tensor-core Q^{-1/2} at first order (the
-# energy only at second); for TF32 and BF16x3 its commutator drift dominates.
-E_BOUND = {binding.MBD_PREC_TF32: 2e-5, binding.MBD_PREC_BF16X3: 1e-6, binding.MBD_PREC_TF32X3: 1e-6}
-F_BOUND = {binding.MBD_PREC_TF32: 50.0, binding.MBD_PREC_BF16X3: 0.5, binding.MBD_PREC_TF32X3: 0.1}
+# Stated per-mode bounds, a few times the measured errors.  BF16x3 and TF32x3 meet
+# |dE| <= 1e-6 Ha/atom with forces and parameter gradients of stated accuracy; TF32 runs the
+# iteration on 10-bit products, whose rounding breaks the coupling invariant Y = Y0 Z by more
+# than the FP64 correction can remove (a commutator error): its energy is held to a looser
+# bound and its forces are not usable (energy-only mode, bounded only by their order of
+# magnitude).
+# Measured on GB300 against the FP64 path at 2000 atoms: |dE|/N 6.8e-9 (BF16x3) and 5.8e-9
+# (TF32x3) Ha/atom; largest force error 7.9e-5 (BF16x3) and 4.9e-6 (TF32x3) of the largest
+# force; parameter gradients 2.1e-7 and 1.5e-8 (absolute).  Forces of the mixed modes take
+# the tensor-core Q^{-1/2} at first order (the energy and dE/d omega_bar only at second).
+E_BOUND = {binding.MBD_PREC_TF32: 2e-5, binding.MBD_PREC_BF16X3: 1e-7, binding.MBD_PREC_TF32X3: 5e-8}
+F_BOUND = {binding.MBD_PREC_TF32: 50.0, binding.MBD_PREC_BF16X3: 5e-4, binding.MBD_PREC_TF32X3: 5e-5}
+# parameter gradients, relative to the largest of each of the four rows
+P_BOUND = {binding.MBD_PREC_TF32: None, binding.MBD_PREC_BF16X3: 5e-4, binding.MBD_PREC_TF32X3: 5e-5}
+
+
+def _check_mixed(precision, N, E, E_ref, gR, gR_ref, gp, gp_ref, st):
+    de = abs(E - E_ref) / N
+    fr = np.max(np.abs(gR - gR_ref)) / np.max(np.abs(gR_ref))
+    pr = max(np.max(np.abs(gp[k] - gp_ref[k])) / np.max(np.abs(gp_ref[k])) for k in range(4))
+    print(f"precision {precision} N {N}: |dE|/N {de:.3e} Ha, force err {fr:.3e} of max, param err {pr:.3e} of max")
+    assert de <= E_BOUND[precision], (E, E_ref, st)
+    assert fr <= F_BOUND[precision], (fr, st)
+    if P_BOUND[precision] is not None:
+        assert pr <= P_BOUND[precision], (pr, st)
 
 
 @pytest.mark.parametrize("precision", [binding.MBD_PREC_TF32, binding.MBD_PREC_BF16X3, binding.MBD_PREC_TF32X3])
@@ -135,9 +183,7 @@ def test_mixed_precision_energy_vs_oracle(precision, workload):
     sysm = syn.workload("finite32") if workload == "finite32" else syn.sphere_cluster(90, seed=1090)
     E_ref, gR_ref, gp_ref = o.mbd_rsscs_gradient(*o.system_args(sysm), mode="adjoint")
     E, gR, gp, st = _eval(sysm, precision)
-    N = sysm.n_atoms
-    assert abs(E - E_ref) / N <= E_BOUND[precision], (E, E_ref, st)
-    assert np.max(np.abs(gR - gR_ref)) <= F_BOUND[precision] * np.max(np.abs(gR_ref)) + 1e-12, st
+    _check_mixed(precision, sysm.n_atoms, E, E_ref, gR, gR_ref, gp, gp_ref, st)
 
 
 @pytest.mark.parametrize("precision", [binding.MBD_PREC_TF32, binding.MBD_PREC_BF16X3, binding.MBD_PREC_TF32X3])
@@ -145,8 +191,7 @@ def test_mixed_precision_matches_fp64_path_at_500_atoms(precision):
     sysm = syn.sphere_cluster(500, seed=1500)
     E64, gR64, gp64, _ = _eval(sysm, binding.MBD_PREC_FP64)
     E, gR, gp, st = _eval(sysm, precision)
-    assert abs(E - E64) / 500 <= E_BOUND[precision], (E, E64, st)
-    assert np.max(np.abs(gR - gR64)) <= F_BOUND[precision] * np.max(np.abs(gR64)), st
+    _check_mixed(precision, 500, E, E64, gR, gR64, gp, gp64, st)
 
 
 def test_mixed_screening_refines_to_fp64_accuracy():

@@ -283,3 +283,30 @@ def test_gradient_invariances(small_grad):
     assert np.abs(gR.sum(0)).max() < 1e-15          # translation
     torque = np.cross(args[0], gR).sum(0)
     assert np.abs(torque).max() < 1e-14             # rotation
+
+
+def test_gradient_from_dense_steps_equals_the_adjoint_gradient():
+    # the 2000-atom reference gradient takes the oracle's adjoint pieces with LAPACK dense steps;
+    # on a small cluster it must equal the oracle's own gradient (Gauss-Jordan, Jacobi)
+    sy = syn.cube_cluster(10, 11.0, 2.5, seed=77)
+    args = o.system_args(sy)
+    E_ref, gR_ref, gp_ref = o.mbd_rsscs_gradient(*args, mode="adjoint")
+    R, a0r, c6r, rr, v = args
+    a0, om, rv = o.ts_scaling(a0r, c6r, rr, v)
+    u, _ = o.freq_grid(15)
+    n = 3 * sy.n_atoms
+    E3 = np.zeros((n, 3))
+    for c in range(3):
+        E3[c::3, c] = 1.0
+    Ms = [o.scs_matrix(R, o.dyn_alpha(a0, om, u[k]), rv) for k in range(16)]
+    X = np.array([np.linalg.solve(M, E3) for M in Ms])
+    ab = (X[:, 0::3, 0] + X[:, 1::3, 1] + X[:, 2::3, 2]) / 3.0
+    rc, (abar0, c6bar, ombar, rbar) = o.screened_params(ab, a0, rv)
+    lam, C = np.linalg.eigh(o.mbd_q(R, abar0, ombar, rbar))
+    Z = (C / np.sqrt(lam)) @ C.T
+    gR, gp = o.gradient_from_dense_steps(R, a0r, c6r, rr, v, ab, X, Z, lambda k, H: np.linalg.solve(Ms[k], H))
+    # LAPACK against Jacobi / Gauss-Jordan: ~1e-11 of the largest component (rounding of Z and
+    # of the solves, through the cancellations of the force sums)
+    assert np.allclose(gR, gR_ref, rtol=0, atol=1e-9 * np.abs(gR_ref).max())
+    for k in range(4):
+        assert np.allclose(gp[k], gp_ref[k], rtol=0, atol=1e-9 * np.abs(gp_ref[k]).max())
