@@ -1,12 +1,15 @@
 #!/usr/bin/env python3
 """Benchmark: MBD@rsSCS energy + analytic gradient solves per second on GB300.
 
-One step = one full evaluation (TS scaling, screening at 16 frequency points, Q,
-coupled Newton-Schulz Q^{+-1/2}, energy, and all gradients) of the 2000-atom finite
-cluster (0.08 atoms/A^3, minimum separation 2.2 bohr; Q is 6000 x 6000), inputs
-resident in HBM.  `e2e` repeats the measurement through the C ABI with host buffers
-(host-to-device copies of the inputs and device-to-host copies of energy, gradients
-and screened polarizabilities inside the timed region).
+One step = one full evaluation (TS scaling, screening at 16 frequency points, Q, coupled
+Newton-Schulz Q^{+-1/2}, energy, and all gradients) of the 8000-atom finite cluster
+(0.08 atoms/A^3, minimum separation 2.2 bohr; Q is 24000 x 24000) in BF16x3 arithmetic,
+inputs resident in HBM.  `e2e` repeats the measurement through the C ABI with host buffers
+(host-to-device copies of the inputs and device-to-host copies of energy, gradients and
+screened polarizabilities inside the timed region).  Beside it, on the same inputs: the
+TF32x3 arm, the FP64 path (one evaluation) against which each arm's energy, force and
+parameter-gradient errors are stated, and the 2000-atom cluster (Q 6000 x 6000) in both
+forms with its own FP64 arm.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -31,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MBD energy+gradient solves/s & TFLOP/s vs FP64 GPU path at |ΔE|≤1e-6 Ha/atom"
 UNIT = "solves/s"
-WORKLOAD = "finite2000"
+WORKLOAD = "finite8000"
 # Ewald split, real-space and reciprocal cutoffs of the periodic workload (real-space cutoff
 # 30 bohr; gamma = 6/30, k_c = 10 gamma)
 PERIODIC_EWALD = (0.2, 30.0, 2.0)
@@ -59,9 +62,10 @@ def gemm_region_sha16(path):
 # the size of the 6000x6000 case, captured alone with --kernel tc_gemm_sym6016) from the
 # committed capture (profiles/k_tc_gemm_finite2000.md), valid while the GEMM's own source in
 # k_tc.cu (tile constants through the tc_gemm dispatcher) keeps the captured hash.
-TC_GEMM_TRAFFIC = {"bytes": 1.558883e9 + 0.407660544e9, "k_tc_region_sha16": "7b8f28f7af13cca9",
-                   "launch": "symmetric Z' product, order 6016, 152 persistent CTAs",
-                   "source": "profiles/k_tc_gemm_finite2000.md"}
+TC_GEMM_TRAFFIC = {("tf32x3", "finite2000"): {"bytes": 1.558883e9 + 0.407660544e9,
+                                               "k_tc_region_sha16": "7b8f28f7af13cca9",
+                                               "launch": "symmetric Z' product, order 6016, 152 persistent CTAs",
+                                               "source": "profiles/k_tc_gemm_finite2000.md"}}
 
 
 def tc_region_sha16(path):
@@ -87,9 +91,17 @@ def parse():
                          "screening model beside plain screening")
     ap.add_argument("--batch-clusters", type=int, default=64,
                     help="batch4096: clusters of the batch evaluated per step (the first ones of the recipe)")
-    ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64", "fp64split"), default="tf32x3",
+    ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64", "fp64split"), default="bf16x3",
                     help="matrix-function arithmetic of the timed arm (the FP64 path is measured beside it)")
-    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison arm (0: skip)")
+    ap.add_argument("--also", default="tf32x3",
+                    help="comma-separated further arithmetic arms timed on the same workload ('' for none)")
+    ap.add_argument("--other-steps", type=int, default=3, help="timed steps of each further arm (1 warm-up)")
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed steps of the FP64 comparison arm (0: skip; no warm-up at 4000 atoms or more)")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement (at most --steps)")
+    ap.add_argument("--extra-workload", default="finite2000",
+                    help="a second finite workload measured the same way after the first ('' for none)")
+    ap.add_argument("--extra-fp64-steps", type=int, default=2, help="timed FP64 steps of the second workload")
     ap.add_argument("--cpu-sample-atoms", type=int, default=250,
                     help="atoms of the bounded oracle sample (same recipe, extrapolated by n^3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -108,7 +120,12 @@ def parse():
                          "and gradients (mbd_ts_energy) of the 2000-atom cluster; ts_cell256 = the same per cell of "
                          "the 256-atom triclinic cell with the lattice gradient (Eq. ts-ewald); "
                          "gemm_f64_split6016 = the FP64-accurate split GEMM against the FP64 GEMM at order 6016")
-    return ap.parse_args()
+    args = ap.parse_args()
+    args.also = [x for x in args.also.split(",") if x]
+    for x in args.also:
+        if x not in ("bf16x3", "tf32x3", "tf32", "fp64split"):
+            ap.error(f"--also: unknown arithmetic {x}")
+    return args
 
 
 def dist_info():
@@ -220,7 +237,7 @@ def cpu_baseline(workload: str, n_sample: int, n_target: int, method: str = "rss
     return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"energy+gradient of a {n_sample}-atom {kind} of the same recipe in "
                       f"{dt:.2f} s, extrapolated by (n/{n_sample})^3 to {n_target} atoms",
-            "sample_seconds": dt}
+            "sample_seconds": dt, "extrapolated": True}
 
 
 def reduce_max(x: float, world: int, device) -> float:
@@ -259,18 +276,163 @@ def run_reference(args):
     value = args.steps / (dt * scale)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     kind = "cell" if sysm.lattice is not None else "cluster"
+    from paper_2308_03140_gb300 import synthetic as syn
+    full = syn.workload(args.workload)
+    sample = (f"each step one energy+gradient of a {n_s}-atom {kind} of the same recipe (measured: "
+              f"{1e3 * dt / args.steps:.0f} ms per step), extrapolated by ({n_target}/{n_s})^3 to the workload")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt * scale / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "ms_per_step_extrapolated": 1e3 * dt * scale / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": args.workload, "method": "MBD-NL" if args.method == "nl" else "MBD@rsSCS",
-                       "n_atoms": n_target, "n_freq": 15, "precision": "fp64", "sample_atoms": n_s},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step one energy+gradient of a {n_s}-atom {kind} of the same "
-                                       f"recipe, extrapolated by ({n_target}/{n_s})^3"},
+            "precision": "fp64", "data": "synthetic",
+            "config": workload_config(args.workload, args.method, n_target, world, full.lattice is not None, full),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "sample_atoms": n_s, "extrapolated": True},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def workload_config(workload, method, n_atoms, world, periodic=False, sysm=None):
+    """The workload's description, shared by both arms of the bench (so their configs match)."""
+    import numpy as np
+    n = 3 * n_atoms
+    cfg = {"workload": workload, "method": "MBD-NL" if method == "nl" else "MBD@rsSCS", "n_atoms": n_atoms,
+           "matrix_order": n, "n_freq": 15,
+           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+    if periodic:
+        nk = int(np.prod(sysm.k_grid))
+        cfg["l2"] = (f"inputs larger than L2: 5 Newton-Schulz sets of {nk} complex {n}x{n} matrices "
+                     f"({16 * n * n * nk / 1e6:.0f} MB each set)")
+        cfg.update({"lattice_bohr": np.asarray(sysm.lattice).round(4).tolist(), "k_grid": list(sysm.k_grid),
+                    "ewald_gamma": PERIODIC_EWALD[0], "real_cutoff_bohr": PERIODIC_EWALD[1],
+                    "recip_cutoff_per_bohr": PERIODIC_EWALD[2]})
+    else:
+        cfg["l2"] = (f"inputs larger than L2: 16 screening matrices + 5 Newton-Schulz matrices of "
+                     f"{8 * n * n / 1e6:.0f} MB each per step")
+    return cfg
+
+
+PRECISIONS = ("fp64", "tf32", "bf16x3", "tf32x3", "fp64split")
+
+
+def precision_code(binding, name):
+    return {"fp64": binding.MBD_PREC_FP64, "tf32": binding.MBD_PREC_TF32, "bf16x3": binding.MBD_PREC_BF16X3,
+            "tf32x3": binding.MBD_PREC_TF32X3, "fp64split": binding.MBD_PREC_FP64_SPLIT}[name]
+
+
+def time_arm(binding, dev, stream, sysm, p3, p4, precision, scs_mode, steps, warmup, barrier=None,
+             max_over_ranks=None, clocks=None):
+    """One context, `warmup` untimed and `steps` timed device evaluations (energy and all
+    gradients, inputs resident in HBM) bracketed by CUDA events on the launch stream.
+    Returns the timing, the last results (host copies) and the per-step profiles."""
+    import numpy as np
+    import torch
+    N = sysm.n_atoms
+    periodic = sysm.lattice is not None
+    T = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
+    inp = [T(sysm.coords), T(sysm.alpha0_ref), T(sysm.c6_ref), T(p3), T(p4)]
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    gR = torch.zeros(N, 3, dtype=torch.float64, device=dev)
+    gp = torch.zeros(4, N, dtype=torch.float64, device=dev)
+    al = torch.zeros(N, dtype=torch.float64, device=dev)
+    ewald = dict(ewald_gamma=PERIODIC_EWALD[0], real_cutoff=PERIODIC_EWALD[1],
+                 recip_cutoff=PERIODIC_EWALD[2]) if periodic else {}
+    m = binding.MBD(dev.index or 0, precision=precision, scs_mode=scs_mode, **ewald)
+    m.set_geometry(sysm.coords, sysm.lattice, sysm.k_grid)
+    m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, p3, p4)
+
+    def step():
+        m.evaluate_dev(*inp, energy, gR, gp, al, stream=stream)
+
+    for _ in range(warmup):
+        step()
+    m.set_profiling(True)
+    if barrier:
+        barrier()
+    torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    profs = []
+    for _ in range(steps):
+        step()
+        profs.append(m.profile())
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks else None
+    if barrier:
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if max_over_ranks:
+        ms = max_over_ranks(ms)
+    m.set_profiling(False)
+    out = {"ms": ms, "steps": steps, "warmup": warmup, "energy": energy.item(), "gR": gR.cpu().numpy().copy(),
+           "gp": gp.cpu().numpy().copy(), "profs": profs, "stats": m.stats(), "clocks": clk, "ctx": m}
+    return out
+
+
+def errors_vs(arm, ref, N):
+    """Per-result error of an arm against the FP64 path on the same inputs."""
+    import numpy as np
+    gpr = np.abs(ref["gp"]).max(axis=1)
+    return {"delta_e_per_atom_ha": (arm["energy"] - ref["energy"]) / N,
+            "max_force_err_ha_bohr": float(np.abs(arm["gR"] - ref["gR"]).max()),
+            "max_force_ha_bohr": float(np.abs(ref["gR"]).max()),
+            "max_force_err_rel": float(np.abs(arm["gR"] - ref["gR"]).max() / np.abs(ref["gR"]).max()),
+            "max_param_grad_err": float(np.abs(arm["gp"] - ref["gp"]).max()),
+            "max_param_grad_err_rel": [float(np.abs(arm["gp"][k] - ref["gp"][k]).max() / gpr[k]) for k in range(4)]}
+
+
+def roofline_of(binding, args_precision, precision, profs, ms, steps, workload):
+    """Roofline of the dominant kernel of an arm from the library's CUDA-event profile."""
+    gemm_ms = sum(p["gemm_ms"] for p in profs)
+    gemm_flops = sum(p["gemm_flops"] for p in profs)
+    gemm_launches = sum(p["gemm_launches"] for p in profs)
+    peaks = measured_peaks()
+    bf16_sus = peaks.get("bf16_tflops_sustained") if peaks else None
+    src = "of measured" if bf16_sus else "of fallback"
+    bf16_sus = bf16_sus or 1700.0
+    if precision == binding.MBD_PREC_FP64_SPLIT:
+        kernel = "k_tc_gemm<TF32> slice products of the split FP64 GEMM (Newton-Schulz products)"
+        k_ms, k_flops, k_launches = gemm_ms, gemm_flops, gemm_launches
+        peak = bf16_sus * 0.5 / 53
+        peak_src = (f"{src}: bf16_tflops_sustained x nominal TF32/BF16 rate (0.5) / 53 slice products per "
+                    "algorithmic product")
+        traffic, tsrc = None, None
+    elif precision == binding.MBD_PREC_FP64:
+        kernel = "k_gemm_nn (FP64 mma.sync m8n8k4, Newton-Schulz products)"
+        k_ms, k_flops, k_launches = gemm_ms, gemm_flops, gemm_launches
+        peak = bf16_sus * FP64_OVER_BF16
+        peak_src = f"{src}: bf16_tflops_sustained x nominal FP64/BF16 ratio (1.25/2250)"
+        cur = gemm_region_sha16(os.path.join(ROOT, "paper_2308_03140_gb300", "csrc", "k_dense.cu"))
+        ok = workload == "finite2000" and cur == GEMM_NN_TRAFFIC["k_gemm_region_sha16"]
+        traffic, tsrc = (GEMM_NN_TRAFFIC["bytes"], GEMM_NN_TRAFFIC["source"]) if ok else (None, None)
+    else:
+        kernel = "k_tc_gemm (tcgen05 + TMA + TMEM; Newton-Schulz and correction products)"
+        k_ms = sum(p["tc_ms"] for p in profs)
+        k_flops = sum(p["tc_flops"] for p in profs)
+        k_launches = sum(p["tc_launches"] for p in profs)
+        per_kind = {binding.MBD_PREC_TF32: (0.5, 1, "TF32"), binding.MBD_PREC_BF16X3: (1.0, 3, "BF16x3"),
+                    binding.MBD_PREC_TF32X3: (0.5, 3, "TF32x3")}[precision]
+        peak = bf16_sus * per_kind[0] / per_kind[1]
+        peak_src = (f"{src}: bf16_tflops_sustained x nominal {per_kind[2][:4]}/BF16 rate ({per_kind[0]}) / "
+                    f"{per_kind[1]} tensor products per algorithmic product")
+        cur = tc_region_sha16(os.path.join(ROOT, "paper_2308_03140_gb300", "csrc", "k_tc.cu"))
+        rec = TC_GEMM_TRAFFIC.get((args_precision, workload))
+        traffic, tsrc = ((rec["bytes"], rec["source"]) if rec and cur == rec["k_tc_region_sha16"] else (None, None))
+    achieved = k_flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
+    return {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu capture)", "traffic_launch": tsrc, "peak_source": peak_src,
+            "launches_per_step": k_launches / steps, "avg_launch_ms": k_ms / max(k_launches, 1),
+            "flops_per_launch": k_flops / max(k_launches, 1), "share_of_step": k_ms / ms if ms > 0 else None}
+
+
+def stage_means(profs):
+    return {k: statistics.mean(p[k] for p in profs) for k in
+            ("screening_ms", "newton_schulz_ms", "correction_ms", "gradient_ms", "total_ms")}
 
 
 def run_ours(args):
@@ -304,183 +466,134 @@ def run_ours(args):
     # per-atom parameter slots 3 and 4: R_vdW,ref and the volume ratio, or the MBD-NL ratios
     p3, p4 = syn.nl_ratios(N, NL_SEED) if nl else (sysm.rvdw_ref, sysm.ratio)
     scs_mode = binding.MBD_SCS_NL if nl else binding.MBD_SCS_PLAIN
-    T = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
-    inp = [T(sysm.coords), T(sysm.alpha0_ref), T(sysm.c6_ref), T(p3), T(p4)]
-    energy = torch.zeros(1, dtype=torch.float64, device=dev)
-    gR = torch.zeros(N, 3, dtype=torch.float64, device=dev)
-    gp = torch.zeros(4, N, dtype=torch.float64, device=dev)
-    al = torch.zeros(N, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    precision = {"fp64": binding.MBD_PREC_FP64, "tf32": binding.MBD_PREC_TF32,
-                 "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3,
-                 "fp64split": binding.MBD_PREC_FP64_SPLIT}[args.precision]
-    ewald = dict(ewald_gamma=PERIODIC_EWALD[0], real_cutoff=PERIODIC_EWALD[1],
-                 recip_cutoff=PERIODIC_EWALD[2]) if periodic else {}
-    m = binding.MBD(local, precision=precision, scs_mode=scs_mode, **ewald)
-    m.set_geometry(sysm.coords, sysm.lattice, sysm.k_grid)
-    m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, p3, p4)
-
-    def step():
-        m.evaluate_dev(*inp, energy, gR, gp, al, stream=stream)
-
-    for _ in range(args.warmup):
-        step()
-    m.set_profiling(True)
-    barrier()
-    torch.cuda.synchronize(dev)
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    profs = []
-    for _ in range(args.steps):
-        step()
-        profs.append(m.profile())
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    clk = clocks.stop()
-    barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1))
-    st = m.stats()
-    E = energy.item()
+    precision = precision_code(binding, args.precision)
+    main = time_arm(binding, dev, stream, sysm, p3, p4, precision, scs_mode, args.steps, args.warmup, barrier,
+                    max_over_ranks, ClockSampler(local))
+    m = main["ctx"]
+    ms = main["ms"]
     value = whole_job_rate(args.steps, world, ms / 1e3)
 
-    # end to end through the C ABI with host buffers
-    m.set_profiling(False)
+    # end to end through the C ABI with host buffers: inputs uploaded, energy and gradients
+    # read back inside the timed region, every step
+    e2e_steps = min(args.steps, args.e2e_steps)
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         m.set_geometry(sysm.coords, sysm.lattice, sysm.k_grid)
         m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, p3, p4)
         E_h, gR_h, gp_h, al_h = m.evaluate(True)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT, "steps": e2e_steps,
            "h2d_bytes_per_step": 8 * (3 * N + 4 * N),
            "d2h_bytes_per_step": 8 * (1 + 3 * N + 4 * N + N + (9 if periodic else 0))}
     if periodic:
         e2e["h2d_bytes_per_step"] += 8 * 9 + 4 * 3   # lattice and k-grid
+    st = main["stats"]
+    profs = main["profs"]
+    m.close()
+    main["ctx"] = None
+    torch.cuda.empty_cache()
 
-    gR_t, gp_t = gR.detach().cpu().numpy().copy(), gp.detach().cpu().numpy().copy()
-    # FP64 comparison arm (same workload and API; fewer steps: it is ~20x slower)
-    fp64 = None
-    if precision != binding.MBD_PREC_FP64 and args.fp64_steps > 0:
-        m64 = binding.MBD(local, precision=binding.MBD_PREC_FP64, scs_mode=scs_mode)
-        m64.set_geometry(sysm.coords)
-        e64 = torch.zeros(1, dtype=torch.float64, device=dev)
-        g64 = torch.zeros(N, 3, dtype=torch.float64, device=dev)
-        p64 = torch.zeros(4, N, dtype=torch.float64, device=dev)
-        m64.evaluate_dev(*inp, e64, g64, p64, None, stream=stream)   # warm-up
-        torch.cuda.synchronize(dev)
-        a0_, a1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0_.record(stream)
-        for _ in range(args.fp64_steps):
-            m64.evaluate_dev(*inp, e64, g64, p64, None, stream=stream)
-        a1_.record(stream)
-        torch.cuda.synchronize(dev)
-        ms64 = max_over_ranks(a0_.elapsed_time(a1_))
-        E64 = e64.item()
-        g64n, p64n = g64.cpu().numpy(), p64.cpu().numpy()
-        fp64 = {"value": world * args.fp64_steps / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
-                "steps": args.fp64_steps, "warmup": 1, "energy_ha": E64,
-                "delta_e_per_atom_ha": (E - E64) / N,
-                "max_force_err_ha_bohr": float(abs(gR_t - g64n).max()),
-                "max_force_ha_bohr": float(abs(g64n).max()),
-                "max_param_grad_err": float(abs(gp_t - p64n).max())}
-        m64.close()
-
-    gemm_ms = sum(p["gemm_ms"] for p in profs)
-    gemm_flops = sum(p["gemm_flops"] for p in profs)
-    gemm_launches = sum(p["gemm_launches"] for p in profs)
-    launches = sum(p["launches"] for p in profs)
-    peaks = measured_peaks()
-    bf16_sus = peaks.get("bf16_tflops_sustained") if peaks else None
-    src = "of measured" if bf16_sus else "of fallback"
-    bf16_sus = bf16_sus or 1700.0
-    if precision == binding.MBD_PREC_FP64_SPLIT:
-        # the FP64-accurate split products: 53 TF32 slice products per algorithmic product
-        kernel = "k_tc_gemm<TF32> slice products of the split FP64 GEMM (Newton-Schulz products)"
-        k_ms, k_flops, k_launches = gemm_ms, gemm_flops, gemm_launches
-        peak = bf16_sus * 0.5 / 53
-        peak_src = (f"{src}: bf16_tflops_sustained x nominal TF32/BF16 rate (0.5) / 53 slice products per "
-                    "algorithmic product")
-        traffic = None
-    elif precision == binding.MBD_PREC_FP64:
-        # dominant kernel: the FP64 tensor-path Newton-Schulz products
-        kernel = "k_gemm_nn (FP64 mma.sync m8n8k4, Newton-Schulz products)"
-        k_ms, k_flops, k_launches = gemm_ms, gemm_flops, gemm_launches
-        peak = bf16_sus * FP64_OVER_BF16
-        peak_src = f"{src}: bf16_tflops_sustained x nominal FP64/BF16 ratio (1.25/2250)"
-        cur = gemm_region_sha16(os.path.join(ROOT, "paper_2308_03140_gb300", "csrc", "k_dense.cu"))
-        traffic = (GEMM_NN_TRAFFIC["bytes"] if args.workload == "finite2000" and
-                   cur == GEMM_NN_TRAFFIC["k_gemm_region_sha16"] else None)
-    else:
-        # tcgen05 GEMMs of the iteration and of the correction
-        kernel = "k_tc_gemm (tcgen05 + TMA + TMEM; Newton-Schulz and correction products)"
-        k_ms = sum(p["tc_ms"] for p in profs)
-        k_flops = sum(p["tc_flops"] for p in profs)
-        k_launches = sum(p["tc_launches"] for p in profs)
-        per_kind = {binding.MBD_PREC_TF32: (0.5, 1, "TF32"), binding.MBD_PREC_BF16X3: (1.0, 3, "BF16x3"),
-                    binding.MBD_PREC_TF32X3: (0.5, 3, "TF32x3")}[precision]
-        peak = bf16_sus * per_kind[0] / per_kind[1]
-        peak_src = (f"{src}: bf16_tflops_sustained x nominal {per_kind[2][:4]}/BF16 rate ({per_kind[0]}) / "
-                    f"{per_kind[1]} tensor products per algorithmic product")
-        cur = tc_region_sha16(os.path.join(ROOT, "paper_2308_03140_gb300", "csrc", "k_tc.cu"))
-        traffic = (TC_GEMM_TRAFFIC["bytes"] if precision == binding.MBD_PREC_TF32X3 and args.workload == "finite2000"
-                   and cur == TC_GEMM_TRAFFIC["k_tc_region_sha16"] else None)
-    achieved = k_flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
-    n = 3 * N
-    exec_flops = sum(p["gemm_flops"] + p["tc_flops"] + p["screening_flops"] for p in profs) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == binding.MBD_PREC_FP64 else
-        f"{args.precision}+f32+f64",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "method": "MBD-NL" if nl else "MBD@rsSCS", "n_atoms": N,
-                   "matrix_order": n, "n_freq": 15,
-                   "precision": args.precision, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": ("inputs larger than L2: 16 screening matrices + 5 Newton-Schulz matrices of "
-                          f"{8 * n * n / 1e6:.0f} MB each per step" if not periodic else
-                          f"inputs larger than L2: 5 Newton-Schulz sets of {len(sysm.k_grid and range(int(np.prod(sysm.k_grid))))} "
-                          f"complex {n}x{n} matrices ({16 * n * n * int(np.prod(sysm.k_grid)) / 1e6:.0f} MB each set)"),
-                   **({"lattice_bohr": np.asarray(sysm.lattice).round(4).tolist(), "k_grid": list(sysm.k_grid),
-                       "ewald_gamma": PERIODIC_EWALD[0], "real_cutoff_bohr": PERIODIC_EWALD[1],
-                       "recip_cutoff_per_bohr": PERIODIC_EWALD[2]} if periodic else {})},
-        "tflops": exec_flops / (ms / args.steps / 1e3) / 1e12,
-        # the work the method needs at least (finite systems): 16 Cholesky factorisations with
-        # their 3-RHS solves (none for MBD-NL) and ~9 n^3 for an eigendecomposition of Q
-        "tflops_algorithmic_min": (None if periodic else
-                                   ((0.0 if nl else 16.0 * (n ** 3 / 3.0 + 12.0 * n ** 2)) + 9.0 * n ** 3)
-                                   / (ms / args.steps / 1e3) / 1e12),
-        "roofline": {"kernel": kernel, "bound": "tensor",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "traffic_unit": "bytes per launch (ncu capture)",
-                     "traffic_launch": (None if traffic is None else
-                                        (TC_GEMM_TRAFFIC if precision != binding.MBD_PREC_FP64 else
-                                         GEMM_NN_TRAFFIC)["source"]),
-                     "peak_source": peak_src,
-                     "launches_per_step": k_launches / args.steps,
-                     "avg_launch_ms": k_ms / max(k_launches, 1),
-                     "flops_per_launch": k_flops / max(k_launches, 1),
-                     "share_of_step": k_ms / ms if ms > 0 else None},
-        "fp64_path": fp64,
-        "e2e": e2e,
-        "clocks": clk,
-        "gpu_launches": launches,
-        "energy_ha": E, "energy_per_atom_ha": E / N, "ns_iterations": st["ns_iterations"],
-        "stage_ms": {k: statistics.mean(p[k] for p in profs) for k in
-                     ("screening_ms", "newton_schulz_ms", "correction_ms", "gradient_ms", "total_ms")},
-        "ns_residual": st["ns_residual"], "correction_residual": st["correction_residual"],
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == binding.MBD_PREC_FP64 else f"{args.precision}+f32+f64",
+        "precision": args.precision, "data": "synthetic",
+        "config": workload_config(args.workload, args.method, N, world, periodic, sysm),
     }
+    exec_flops = sum(p["gemm_flops"] + p["tc_flops"] + p["screening_flops"] for p in profs) / args.steps
+    n = 3 * N
+    line["tflops"] = exec_flops / (ms / args.steps / 1e3) / 1e12
+    # the work the method needs at least (finite systems): 16 Cholesky factorisations with
+    # their 3-RHS solves (none for MBD-NL) and ~9 n^3 for an eigendecomposition of Q
+    line["tflops_algorithmic_min"] = (None if periodic else
+                                      ((0.0 if nl else 16.0 * (n ** 3 / 3.0 + 12.0 * n ** 2)) + 9.0 * n ** 3)
+                                      / (ms / args.steps / 1e3) / 1e12)
+    line["roofline"] = roofline_of(binding, args.precision, precision, profs, ms, args.steps, args.workload)
+    line["e2e"] = e2e
+    line["clocks"] = main["clocks"]
+    line["gpu_launches"] = sum(p["launches"] for p in profs)
+    line["energy_ha"] = main["energy"]
+    line["energy_per_atom_ha"] = main["energy"] / N
+    line["ns_iterations"] = st["ns_iterations"]
+    line["stage_ms"] = stage_means(profs)
+    line["ns_residual"] = st["ns_residual"]
+    line["correction_residual"] = st["correction_residual"]
+
+    # other arithmetic on the same workload (same API, fewer steps), then the FP64 path, against
+    # which every arm's error is stated
+    arms = {}
+    for other in args.also:
+        if other == args.precision or periodic:
+            continue
+        a = time_arm(binding, dev, stream, sysm, p3, p4, precision_code(binding, other), scs_mode,
+                     max(1, args.other_steps), 1, barrier, max_over_ranks)
+        a["ctx"].close()
+        arms[other] = a
+        torch.cuda.empty_cache()
+    fp64 = None
+    if precision != binding.MBD_PREC_FP64 and args.fp64_steps > 0:
+        fw = 0 if N >= 4000 else 1   # the large cluster's FP64 evaluation takes minutes: no warm-up
+        f = time_arm(binding, dev, stream, sysm, p3, p4, binding.MBD_PREC_FP64, scs_mode, args.fp64_steps, fw,
+                     barrier, max_over_ranks)
+        f["ctx"].close()
+        torch.cuda.empty_cache()
+        fp64 = {"value": world * args.fp64_steps / (f["ms"] / 1e3), "unit": UNIT,
+                "ms_per_step": f["ms"] / args.fp64_steps, "steps": args.fp64_steps, "warmup": fw,
+                "energy_ha": f["energy"], "ns_iterations": f["stats"]["ns_iterations"],
+                "stage_ms": stage_means(f["profs"]),
+                "roofline": roofline_of(binding, "fp64", binding.MBD_PREC_FP64, f["profs"], f["ms"],
+                                        args.fp64_steps, args.workload),
+                "errors_of": {args.precision: errors_vs(main, f, N),
+                              **{k: errors_vs(a, f, N) for k, a in arms.items()}}}
+    line["fp64_path"] = fp64
+    line["other_precisions"] = {k: {"value": world * a["steps"] / (a["ms"] / 1e3), "unit": UNIT,
+                                    "ms_per_step": a["ms"] / a["steps"], "steps": a["steps"], "warmup": 1,
+                                    "energy_ha": a["energy"], "ns_iterations": a["stats"]["ns_iterations"],
+                                    "stage_ms": stage_means(a["profs"]),
+                                    "roofline": roofline_of(binding, k, precision_code(binding, k), a["profs"],
+                                                            a["ms"], a["steps"], args.workload)}
+                                for k, a in arms.items()}
+    # a second finite workload (the 2000-atom cluster) measured the same way
+    xw = args.extra_workload
+    if xw and xw != args.workload and not periodic:
+        xs = syn.workload(xw)
+        xp3, xp4 = syn.nl_ratios(xs.n_atoms, NL_SEED) if nl else (xs.rvdw_ref, xs.ratio)
+        sec = {"config": workload_config(xw, args.method, xs.n_atoms, world)}
+        xarms = {}
+        for name in [args.precision] + [a for a in args.also if a != args.precision]:
+            a = time_arm(binding, dev, stream, xs, xp3, xp4, precision_code(binding, name), scs_mode, args.steps,
+                         args.warmup, barrier, max_over_ranks)
+            a["ctx"].close()
+            xarms[name] = a
+            sec[name] = {"value": world * args.steps / (a["ms"] / 1e3), "unit": UNIT,
+                         "ms_per_step": a["ms"] / args.steps, "steps": args.steps, "warmup": args.warmup,
+                         "energy_ha": a["energy"], "ns_iterations": a["stats"]["ns_iterations"],
+                         "stage_ms": stage_means(a["profs"]),
+                         "roofline": roofline_of(binding, name, precision_code(binding, name), a["profs"], a["ms"],
+                                                 args.steps, xw)}
+        if args.extra_fp64_steps > 0:
+            f = time_arm(binding, dev, stream, xs, xp3, xp4, binding.MBD_PREC_FP64, scs_mode, args.extra_fp64_steps,
+                         1, barrier, max_over_ranks)
+            f["ctx"].close()
+            sec["fp64_path"] = {"value": world * args.extra_fp64_steps / (f["ms"] / 1e3), "unit": UNIT,
+                                "ms_per_step": f["ms"] / args.extra_fp64_steps, "steps": args.extra_fp64_steps,
+                                "warmup": 1, "energy_ha": f["energy"], "ns_iterations": f["stats"]["ns_iterations"],
+                                "stage_ms": stage_means(f["profs"]),
+                                "roofline": roofline_of(binding, "fp64", binding.MBD_PREC_FP64, f["profs"], f["ms"],
+                                                        args.extra_fp64_steps, xw),
+                                "errors_of": {k: errors_vs(a, f, xs.n_atoms) for k, a in xarms.items()}}
+        torch.cuda.empty_cache()
+        line[xw] = sec
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if not (nl and periodic):
             line["cpu_baseline"] = cpu_baseline(args.workload, 32 if periodic else args.cpu_sample_atoms, N,
                                                 args.method)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    m.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

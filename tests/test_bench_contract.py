@@ -6,6 +6,8 @@ import subprocess
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
 
 
 def _line(*extra):
@@ -26,7 +28,9 @@ def test_reference_line_has_the_contract_keys():
             assert k in d, k
         assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
         assert d["unit"] == "solves/s" and d["steps"] == 1 and d["warmup"] == 0
-        assert d["config"]["workload"] == "finite2000"
+        assert d["config"]["workload"] == "finite8000"
+        # the reference arm describes the workload exactly as the GPU arm does
+        assert d["config"] == bench.workload_config("finite8000", method, 8000, 1)
         assert d["config"]["method"] == ("MBD-NL" if method == "nl" else "MBD@rsSCS")
         cb = d["cpu_baseline"]
         assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
