@@ -53,8 +53,9 @@ int mbdk_chol_solve3_f64(void *stream, const double *L, long long ld, int batch,
  * N x K (ldb); D (FP32, may be NULL when beta == 0), C (FP32, may be NULL), C_hi/C_lo
  * (split of the result in the kind's part format, kinds 1 and 2, may be NULL) and CT (FP32 transpose of the result, mode 0
  * and M == N only, may be NULL) share the leading dimension ldc.  M and N multiples of 128, K of 64,
- * leading dimensions multiples of 8.  mode 0: all tiles; mode 2: upper tiles mirrored
- * (M == N, symmetric results).  chunk_stages: K stages (32 TF32 / 64 bf16 elements) per
+ * leading dimensions multiples of 8.  mode 0: all tiles; mode 1: tiles on or below the
+ * diagonal only, not mirrored (M == N); mode 2: upper tiles mirrored (M == N, symmetric
+ * results).  chunk_stages: K stages (32 TF32 / 64 bf16 elements) per
  * tensor-memory accumulation, partial sums added in FP32 with round-to-nearest (0: all of
  * K in one accumulation).  err (device int) gets bit 8 set if a wait timed out. */
 int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float alpha, const void *A0,

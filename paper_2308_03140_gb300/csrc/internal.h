@@ -26,7 +26,9 @@ enum : int {
 // C = alpha sum_p A_p B_p^T + beta D on 128x128 tiles.  kind 0: TF32, operands FP32
 // (A0, B0); kind 1: BF16x3, operands bf16 hi/lo pairs (A0 = A_hi, A1 = A_lo, same for
 // B); kind 2: TF32x3, operands TF32-rounded hi and FP32 remainder lo (32-bit each).  A is M x K, B is N x K (row pitch lda, ldb elements); C, D, transposes share ld.
-// mode 0: all tiles; mode 2: upper tiles mirrored (symmetric products).  Optional
+// mode 0: all tiles; mode 1: tiles on or below the diagonal only, not mirrored (square; for
+// updates of which only the lower triangle is read); mode 2: upper tiles mirrored (symmetric
+// products).  Optional
 // outputs: C (FP32), Ch/Cl (bf16 hi/lo), CT/CTh/CTl (transposes, mode 0 only), and
 // resid += sum over the leading nvalid x nvalid block of (delta - C)^2 (mode 0 only).
 // Timeouts set ST_TC_TIMEOUT in *err.
@@ -134,13 +136,13 @@ void trsv_blocked(const T *L, long long ld, long long mstride, int batch, const 
 // Cholesky with FP32 diagonal-block inverses; then X = A^{-1} B by FP32 solves and
 // `steps` iterative-refinement steps with residuals from the FP64 matrix (full, both
 // triangles; rows >= n are padding).  work: 2 * batch * 3 ld floats.
-// The factorisation is blocked in panels of 256 columns (the first panel takes ld mod 256
-// when that is not 0, so every trailing matrix is a multiple of 128): inside a panel 64-wide
+// The factorisation is blocked in panels of kScsPanel columns (the first panel takes
+// ld mod kScsPanel when that is not 0, so every trailing matrix is a multiple of 128): inside a panel 64-wide
 // steps on the SIMT cores, the trailing update A22 -= L21 L21^T on the tensor cores
-// (TF32x3, k_tc_gemm).  panel: scratch of 2 * batch * ld * 256 32-bit words.  A32 must
-// start symmetric (both triangles): the tensor-core update reads the upper triangle of
-// A22 and writes both.  Tensor-core timeouts set ST_TC_TIMEOUT in *status; a launch error
-// is returned.
+// (TF32x3, k_tc_gemm, tiles of the lower triangle only).  panel: scratch of
+// 2 * batch * ld * kScsPanel 32-bit words.  Only the lower triangle of A32 is read or
+// written.  Tensor-core timeouts set ST_TC_TIMEOUT in *status; a launch error is returned.
+constexpr int kScsPanel = 512;
 cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv,
                                   uint32_t *panel, int *status, cudaStream_t s);
 void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,

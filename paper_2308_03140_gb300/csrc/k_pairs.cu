@@ -92,42 +92,64 @@ __global__ void k_nl_chain(AtomBufs b, const double *g_ab0, const double *g_om, 
 }
 
 // ---- screening matrices ------------------------------------------------------------
-// Thread (i, j) with j <= i writes block (i, j) of every frequency's matrix and its
-// mirror (j, i) (the blocks are symmetric 3x3 tensors): the factorisations read the lower
-// triangle, the residuals of the refined solves the full matrix.  Rows >= n: identity.
-__global__ void k_build_scs(AtomBufs b, double beta, double a, double *M, long long ld,
-                            long long mstride, int *status) {
-    const int j = blockIdx.x * 32 + threadIdx.x;
-    const int i = blockIdx.y * 8 + threadIdx.y;
-    if (i >= b.N || j > i) return;
-    if (i == j) {
-        for (int k = 0; k < b.nf1; ++k) {
-            double *Mk = M + k * mstride;
+// A CTA of 32 x 8 threads takes atoms j0..j0+31 (x) against i0..i0+7 (y); thread (i, j) with
+// j < i computes block (i, j) of every frequency's matrix and writes it in its rows (32
+// consecutive blocks of a row per warp), then the CTA writes the mirrored blocks (j, i) --
+// the blocks are symmetric 3x3 tensors, and r -> -r leaves them unchanged -- from a shared
+// tile, so that those rows too are written in contiguous runs.  Thread (i, i) writes the
+// diagonal block 1/alpha_i(u) I.  The factorisations read the lower triangle, the residuals
+// of the refined solves the full matrix.  Rows >= n: identity (k_pad_identity).
+__global__ void __launch_bounds__(256) k_build_scs(AtomBufs b, double beta, double a, double *M, long long ld,
+                                                   long long mstride, int *status) {
+    const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 8;
+    if (j0 > i0 + 7) return;   // the whole tile lies above the diagonal
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+    const int j = j0 + tx, i = i0 + ty;
+    const bool pair = i < b.N && j < i, diag = i < b.N && j == i;
+    __shared__ double T[24][97];
+    double r[3] = {0.0, 0.0, 0.0}, rho = 1.0, sr = 0.0;
+    if (pair) {
+        r[0] = b.R[3 * j] - b.R[3 * i];
+        r[1] = b.R[3 * j + 1] - b.R[3 * i + 1];
+        r[2] = b.R[3 * j + 2] - b.R[3 * i + 2];
+        rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (!(rho > 1e-8)) atomicOr(status, ST_INPUT);
+        sr = 1.0 - fermi(rho, b.rv[i] + b.rv[j], beta, a).f;
+    }
+    for (int k = 0; k < b.nf1; ++k) {
+        double *Mk = M + k * mstride;
+        double v[9];
+        if (pair) {
+            const double si = b.sig_u[k * b.N + i], sj = b.sig_u[k * b.N + j];
+            const Radial tg = tgg_radial(rho, sqrt(si * si + sj * sj));
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                double *row = Mk + (3LL * i + x) * ld + 3 * j;
+#pragma unroll
+                for (int y = 0; y < 3; ++y) {
+                    v[3 * x + y] = sr * ((x == y ? tg.P : 0.0) + tg.W * r[x] * r[y]);
+                    row[y] = v[3 * x + y];
+                }
+            }
+        } else if (diag) {
             const double d = 1.0 / b.al_u[k * b.N + i];
             for (int x = 0; x < 3; ++x)
                 for (int y = 0; y < 3; ++y) Mk[(3LL * i + x) * ld + 3 * i + y] = (x == y) ? d : 0.0;
         }
-        return;
-    }
-    const double rx = b.R[3 * j] - b.R[3 * i], ry = b.R[3 * j + 1] - b.R[3 * i + 1],
-                 rz = b.R[3 * j + 2] - b.R[3 * i + 2];
-    const double rho = sqrt(rx * rx + ry * ry + rz * rz);
-    if (!(rho > 1e-8)) atomicOr(status, ST_INPUT);
-    const Fermi fd = fermi(rho, b.rv[i] + b.rv[j], beta, a);
-    const double sr = 1.0 - fd.f;
-    const double r[3] = {rx, ry, rz};
-    for (int k = 0; k < b.nf1; ++k) {
-        const double si = b.sig_u[k * b.N + i], sj = b.sig_u[k * b.N + j];
-        const Radial t = tgg_radial(rho, sqrt(si * si + sj * sj));
-        double *Mk = M + k * mstride;
-        for (int x = 0; x < 3; ++x) {
-            double *row = Mk + (3LL * i + x) * ld + 3 * j;
-            double *mir = Mk + (3LL * j + x) * ld + 3 * i;
-            for (int y = 0; y < 3; ++y) {
-                const double v = sr * ((x == y ? t.P : 0.0) + t.W * r[x] * r[y]);
-                row[y] = v;
-                mir[y] = v;
-            }
+        __syncthreads();   // the last frequency's mirror reads are done
+        if (pair) {
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+#pragma unroll
+                for (int y = 0; y < 3; ++y) T[3 * ty + x][3 * tx + y] = v[3 * x + y];
+        }
+        __syncthreads();
+        // mirrored blocks (j, i): 96 rows 3 j + x by 24 columns 3 i + y of this tile
+        for (int e = t; e < 96 * 24; e += 256) {
+            const int row = e / 24, col = e - 24 * row;
+            const int jl = row / 3, x = row - 3 * jl, il = col / 3, y = col - 3 * il;
+            const int jj = j0 + jl, ii = i0 + il;
+            if (ii < b.N && jj < ii) Mk[(3LL * jj + x) * ld + 3 * ii + y] = T[3 * il + x][3 * jl + y];
         }
     }
 }
@@ -534,7 +556,7 @@ void build_scs(const AtomBufs &b, double beta, double a, double *M, long long ld
                int *status, cudaStream_t s) {
     dim3 grid(cdiv(b.N, 32), cdiv(b.N, 8));
     count_launches(1);
-    k_build_scs<<<grid, dim3(32, 8), 0, s>>>(b, beta, a, M, ld, mstride, status);
+    k_build_scs<<<grid, dim3(32, 8), 0, s>>>(b, beta, a, M, ld, mstride, status);   // 18.6 KB static shared
     const int n = 3 * b.N;
     if (ld > n) {
         count_launches(1);

@@ -281,7 +281,7 @@ cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, i
     const long long mstride = ld * ld, dstride = (ld / T64) * 4096;
     count_launches(1);
     k_to_f32<<<gridn(mstride * batch), 256, 0, s>>>(A64, mstride * batch, A32);
-    constexpr int kPanel = 256;
+    constexpr int kPanel = kScsPanel;
     const int first = static_cast<int>(ld % kPanel) ? static_cast<int>(ld % kPanel) : kPanel;
     for (long long p0 = 0; p0 < ld;) {
         const int pw = p0 == 0 ? first : kPanel;   // panel columns [p0, p0 + pw)
@@ -303,13 +303,13 @@ cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, i
         const long long t0 = p0 + pw, rem = ld - t0;   // trailing matrix [t0, ld)^2
         if (rem > 0) {
             // A22 -= L21 L21^T with L21 = A[t0:, p0:t0] as TF32x3 parts on the tensor cores;
-            // the upper tiles of A22 are computed and mirrored
+            // only the tiles of the lower triangle of A22 (the part the factorisation reads)
             uint32_t *H = panel, *L = panel + static_cast<long long>(batch) * rem * pw;
             split_panel_tf32(A32 + t0 * ld + p0, ld, mstride, batch, rem, pw, H, L, s);
             float *A22 = A32 + t0 * ld + t0;
             TcOperands op{H, L, H, L, pw, pw};
             TcArgs g{static_cast<int>(rem), static_cast<int>(rem), pw, -1.f, 1.f, A22, ld, A22, nullptr, nullptr,
-                     nullptr, nullptr, nullptr, nullptr, 0, 2, status};
+                     nullptr, nullptr, nullptr, nullptr, 0, 1, status};
             g.chunk_stages = 2;
             g.batch = batch;
             g.sC = mstride;

@@ -33,6 +33,7 @@
 #include <cudaTypedefs.h>
 
 #include "internal.h"
+#include "tc_tiles.cuh"
 
 namespace mbdgb {
 namespace {
@@ -134,50 +135,13 @@ __device__ __forceinline__ void store_part(void *base, long long off, const uint
         static_cast<unsigned short *>(base)[off] = static_cast<unsigned short>(w[j >> 1] >> (16 * (j & 1)));
 }
 
-// Tile of CTA `bid` in a grouped order, so that the CTAs resident at one time share operand
-// panels in L2.  mode 0 (tiles_m x tiles_n tiles): groups of kGroup tile rows, walked column
-// by column inside a group.  mode 2 (upper triangle tm <= tn of a square T x T grid): kGroup x
-// kGroup super-tiles of the triangle taken in order, column-major inside each.
-constexpr int kGroup = 8;
-__device__ __forceinline__ void grouped_tile(int bid, int mode, int tiles_m, int tiles_n, int &tm, int &tn) {
-    if (mode == 0) {
-        const int per_group = kGroup * tiles_n;
-        const int g = bid / per_group, first = g * kGroup;
-        const int rows = min(kGroup, tiles_m - first), local = bid - g * per_group;
-        tm = first + local % rows;
-        tn = local / rows;
-        return;
-    }
-    const int T = tiles_n, S = (T + kGroup - 1) / kGroup;
-    int left = bid;
-    for (int R = 0; R < S; ++R) {        // super column of tn
-        const int nr = min(kGroup, T - R * kGroup);
-        for (int C = 0; C <= R; ++C) {   // super row of tm
-            const int nc = min(kGroup, T - C * kGroup);
-            const int cnt = (C == R) ? nc * (nc + 1) / 2 : nc * nr;
-            if (left < cnt) {
-                if (C == R) {            // triangle of the diagonal super-tile: local c <= r
-                    int r = 0;
-                    while ((r + 1) * (r + 2) / 2 <= left) ++r;
-                    tn = R * kGroup + r;
-                    tm = C * kGroup + (left - r * (r + 1) / 2);
-                } else {
-                    tm = C * kGroup + left % nc;
-                    tn = R * kGroup + left / nc;
-                }
-                return;
-            }
-            left -= cnt;
-        }
-    }
-    tm = tn = 0;   // not reached for bid < T (T + 1) / 2
-}
-
-// Batch item and tile of work item w (items ordered batch item by batch item).
+// Batch item and tile of work item w (items ordered batch item by batch item; tiles in the
+// grouped order of tc_tiles.cuh, so that the CTAs resident at one time share operand panels in
+// L2).
 __device__ __forceinline__ void item_tile(int w, int tiles, int mode, int tiles_m, int tiles_n, int &bz, int &tm,
                                           int &tn) {
     bz = w / tiles;
-    grouped_tile(w - bz * tiles, mode, tiles_m, tiles_n, tm, tn);
+    tctiles::grouped_tile(w - bz * tiles, mode, tiles_m, tiles_n, tm, tn);
 }
 
 template <int KIND>   // 0: TF32 single product; 1: BF16x3; 2: TF32x3
@@ -190,6 +154,131 @@ struct TcCfg {
     static constexpr bool TF32 = KIND != 1;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512;
 };
+
+// Epilogue of one 128 x 128 tile for the thread owning row m: alpha/beta with D, the
+// optional outputs (FP32, split parts, FP64 accumulation, transposes, mirrored writes of the
+// symmetric products) and the residual sum.  Warp-uniform: every lane of a warp handles a row
+// of the same tile.
+template <int KIND>
+__device__ __forceinline__ void tile_epilogue(const TcArgs &g, const float (&acc)[TN], long long m, int tm, int tn,
+                                              const float *Dp, float *Cp, int lane) {
+    using Cfg = TcCfg<KIND>;
+    const bool mirror = (g.mode == 2) && (tm != tn);
+    const bool diag = (g.mode == 2) && (tm == tn);
+    double rs = 0.0;
+#pragma unroll
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+        const long long n0 = static_cast<long long>(tn) * TN + c0;
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = g.alpha * acc[c0 + j];
+        if (g.beta != 0.f) {   // this row of D was prefetched into L2 during the last chunks
+            const float4 *dp = reinterpret_cast<const float4 *>(Dp + m * g.ld + n0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 d = dp[q];
+                v[4 * q] += g.beta * d.x;
+                v[4 * q + 1] += g.beta * d.y;
+                v[4 * q + 2] += g.beta * d.z;
+                v[4 * q + 3] += g.beta * d.w;
+            }
+        }
+        if (g.resid && m < g.nvalid) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (n0 + j < g.nvalid) {
+                    const double e = (m == n0 + j ? 1.0 : 0.0) - static_cast<double>(v[j]);
+                    rs += e * e;
+                }
+        }
+        if (g.C64) {   // FP64 accumulation output (caller splits K: C64 += result)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (diag && n0 + j < m) continue;
+                g.C64[m * g.ld + n0 + j] += static_cast<double>(v[j]);
+                if ((mirror || diag) && n0 + j != m) g.C64[(n0 + j) * g.ld + m] += static_cast<double>(v[j]);
+            }
+        }
+        // split of the result into the next product's operand parts: bf16 pairs
+        // packed two per word (BF16x3), or TF32 hi and TF32 remainder (TF32x3),
+        // each rounded to nearest
+        uint32_t hw[KIND == 2 ? 16 : 8], lw[KIND == 2 ? 16 : 8];
+        if (g.Ch || g.CTh) {
+            if (KIND == 2) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    uint32_t h, l;
+                    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v[j]));
+                    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(v[j] - __uint_as_float(h)));
+                    hw[j] = h;
+                    lw[j] = l;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+                    hw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
+                            (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+                    lw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
+                            (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+                }
+            }
+        }
+        // Symmetric products (mode 2): upper tiles are mirrored into the lower half;
+        // diagonal tiles keep their upper triangle and mirror it, so the result is
+        // exactly symmetric whatever order the tensor cores summed in.
+        if (!diag) {
+            if (Cp) {
+                float4 *cp = reinterpret_cast<float4 *>(Cp + m * g.ld + n0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+            if (g.Ch) {
+                constexpr int NV = KIND == 2 ? 4 : 2;   // uint4 vectors per 16 elements
+                uint4 *hp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Ch) + (m * g.ld + n0) * Cfg::ELEM);
+                uint4 *lp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Cl) + (m * g.ld + n0) * Cfg::ELEM);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    hp[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                    lp[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (n0 + j < m) continue;
+                const long long off = m * g.ld + n0 + j;
+                if (Cp) Cp[off] = v[j];
+                if (g.Ch) {
+                    store_part<KIND>(g.Ch, off, hw, j);
+                    store_part<KIND>(g.Cl, off, lw, j);
+                }
+            }
+        }
+        // transposed copies (coalesced across the warp: consecutive rows m).  For a
+        // mirrored tile of a symmetric product the transpose goes into C itself.
+        const bool into_c = mirror || diag;
+        float *Tf = into_c ? Cp : g.CT;
+        void *Th = into_c ? g.Ch : g.CTh, *Tl = into_c ? g.Cl : g.CTl;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (diag && n0 + j <= m) continue;
+            const long long off = (n0 + j) * g.ld + m;
+            if (Tf) Tf[off] = v[j];
+            if (Th) {
+                store_part<KIND>(Th, off, hw, j);
+                store_part<KIND>(Tl, off, lw, j);
+            }
+        }
+    }
+    if (g.resid) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        if (lane == 0 && rs != 0.0) atomicAdd(g.resid, rs);
+    }
+}
 
 template <int KIND>
 __global__ void __launch_bounds__(192, 1)
@@ -211,7 +300,7 @@ __global__ void __launch_bounds__(192, 1)
     // gridDim.x, ...; stage and chunk counters run on across items, so the producer and the
     // MMA issuer start the next tile while the epilogue warps store the last one.
     const int tiles_m = g.M / TM;
-    const int tiles = g.mode == 0 ? tiles_m * tiles_n : tiles_n * (tiles_n + 1) / 2;
+    const int tiles = tctiles::tile_count(g.mode, tiles_m, tiles_n);
     const int items = tiles * g.batch;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -351,123 +440,7 @@ __global__ void __launch_bounds__(192, 1)
                 __syncwarp();
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&cfree[buf])) : "memory");
             }
-            if (ok) {
-                const bool mirror = (g.mode == 2) && (tm != tn);
-                const bool diag = (g.mode == 2) && (tm == tn);
-                double rs = 0.0;
-#pragma unroll
-                for (int c0 = 0; c0 < TN; c0 += 16) {
-                    const long long n0 = static_cast<long long>(tn) * TN + c0;
-                    float v[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = g.alpha * acc[c0 + j];
-                    if (g.beta != 0.f) {   // this row of D was prefetched into L2 during the last chunks
-                        const float4 *dp = reinterpret_cast<const float4 *>(Dp + m * g.ld + n0);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float4 d = dp[q];
-                            v[4 * q] += g.beta * d.x;
-                            v[4 * q + 1] += g.beta * d.y;
-                            v[4 * q + 2] += g.beta * d.z;
-                            v[4 * q + 3] += g.beta * d.w;
-                        }
-                    }
-                    if (g.resid && m < g.nvalid) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (n0 + j < g.nvalid) {
-                                const double e = (m == n0 + j ? 1.0 : 0.0) - static_cast<double>(v[j]);
-                                rs += e * e;
-                            }
-                    }
-                    if (g.C64) {   // FP64 accumulation output (caller splits K: C64 += result)
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (diag && n0 + j < m) continue;
-                            g.C64[m * g.ld + n0 + j] += static_cast<double>(v[j]);
-                            if ((mirror || diag) && n0 + j != m) g.C64[(n0 + j) * g.ld + m] += static_cast<double>(v[j]);
-                        }
-                    }
-                    // split of the result into the next product's operand parts: bf16 pairs
-                    // packed two per word (BF16x3), or TF32 hi and TF32 remainder (TF32x3),
-                    // each rounded to nearest
-                    uint32_t hw[KIND == 2 ? 16 : 8], lw[KIND == 2 ? 16 : 8];
-                    if (g.Ch || g.CTh) {
-                        if (KIND == 2) {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                uint32_t h, l;
-                                asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v[j]));
-                                asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(v[j] - __uint_as_float(h)));
-                                hw[j] = h;
-                                lw[j] = l;
-                            }
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
-                                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
-                                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
-                                hw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
-                                        (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
-                                lw[q] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
-                                        (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
-                            }
-                        }
-                    }
-                    // Symmetric products (mode 2): upper tiles are mirrored into the lower half;
-                    // diagonal tiles keep their upper triangle and mirror it, so the result is
-                    // exactly symmetric whatever order the tensor cores summed in.
-                    if (!diag) {
-                        if (Cp) {
-                            float4 *cp = reinterpret_cast<float4 *>(Cp + m * g.ld + n0);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                        }
-                        if (g.Ch) {
-                            constexpr int NV = KIND == 2 ? 4 : 2;   // uint4 vectors per 16 elements
-                            uint4 *hp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Ch) + (m * g.ld + n0) * Cfg::ELEM);
-                            uint4 *lp = reinterpret_cast<uint4 *>(static_cast<char *>(g.Cl) + (m * g.ld + n0) * Cfg::ELEM);
-#pragma unroll
-                            for (int q = 0; q < NV; ++q) {
-                                hp[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
-                                lp[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (n0 + j < m) continue;
-                            const long long off = m * g.ld + n0 + j;
-                            if (Cp) Cp[off] = v[j];
-                            if (g.Ch) {
-                                store_part<KIND>(g.Ch, off, hw, j);
-                                store_part<KIND>(g.Cl, off, lw, j);
-                            }
-                        }
-                    }
-                    // transposed copies (coalesced across the warp: consecutive rows m).  For a
-                    // mirrored tile of a symmetric product the transpose goes into C itself.
-                    const bool into_c = mirror || diag;
-                    float *Tf = into_c ? Cp : g.CT;
-                    void *Th = into_c ? g.Ch : g.CTh, *Tl = into_c ? g.Cl : g.CTl;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (diag && n0 + j <= m) continue;
-                        const long long off = (n0 + j) * g.ld + m;
-                        if (Tf) Tf[off] = v[j];
-                        if (Th) {
-                            store_part<KIND>(Th, off, hw, j);
-                            store_part<KIND>(Tl, off, lw, j);
-                        }
-                    }
-                }
-                if (g.resid) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-                    if (lane == 0 && rs != 0.0) atomicAdd(g.resid, rs);
-                }
-            }
+            if (ok) tile_epilogue<KIND>(g, acc, m, tm, tn, Dp, Cp, lane);
         }   // work items
     }
     __syncwarp();
@@ -547,8 +520,8 @@ cudaError_t launch_tc(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
 }  // namespace
 
 cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_t s) {
-    if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.M % TM || g.N % TN || g.K % 64 || (g.mode != 0 && g.mode != 2) ||
-        (g.mode == 2 && (g.M != g.N || g.CT || g.CTh || g.resid)) || ((g.CT || g.CTh) && g.M != g.N) ||
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.M % TM || g.N % TN || g.K % 64 || g.mode < 0 || g.mode > 2 ||
+        (g.mode != 0 && (g.M != g.N || g.CT || g.CTh || g.resid)) || ((g.CT || g.CTh) && g.M != g.N) ||
         g.ld % 8 || op.lda % 8 || op.ldb % 8 ||
         !g.err || (g.beta != 0.f && !g.D) || (g.Ch && !g.Cl) || (g.CTh && !g.CTl) || kind < 0 || kind > 2 ||
         (kind != 0 && (!op.A1 || !op.B1)) || (kind == 0 && (g.Ch || g.CTh)) || g.batch < 1 || g.batch > 65535 ||

@@ -197,6 +197,7 @@ struct mbd_ctx {
     bool have_screening = false;
     // state of the last forward evaluation, kept for mbd_backward_dev
     bool have_forward = false;
+    long long eval_count = 0;  // successful evaluations of this context so far
     double *Zlast = nullptr;   // Newton-Schulz Z (Q^{-1/2} = zscale * Z)
     double zscale = 0.0;
     // exception
@@ -371,7 +372,7 @@ int allocate(mbd_ctx *ctx) {
     bytes += split_work;
     bytes += 12 * split_mat;
     // FP32 screening factors, their diagonal-block inverses and solve workspace
-    const size_t panel_words = 2 * nf1 * static_cast<size_t>(ld) * 256;
+    const size_t panel_words = 2 * nf1 * static_cast<size_t>(ld) * kScsPanel;
     const size_t grad32 = 2 * nf1 * (3 * static_cast<size_t>(ld) + N);
     const size_t scs32 = !fp64_path(prec)
                              ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * 2 * nf1 * ld * 3) +
@@ -952,6 +953,7 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
     }
     ctx->have_result = true;
     ctx->have_forward = true;
+    ++ctx->eval_count;
     return MBD_OK;
 }
 
@@ -1224,6 +1226,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     }
     ctx->have_result = true;
     ctx->have_forward = true;
+    ++ctx->eval_count;
     return MBD_OK;
 }
 
@@ -1416,13 +1419,22 @@ int mbd_evaluate_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coor
     return run(ctx, s, in, o, want_grad);
 }
 
-int mbd_backward_dev(mbd_ctx *ctx, void *stream, int n_atoms, const double *coords,
+int mbd_get_evaluation_count(const mbd_ctx *ctx, long long *count) {
+    if (!ctx || !count) return MBD_ERR_INPUT;
+    *count = ctx->eval_count;
+    return MBD_OK;
+}
+
+int mbd_backward_dev(mbd_ctx *ctx, void *stream, long long evaluation, int n_atoms, const double *coords,
                      const double *alpha0_ref, const double *c6_ref, const double *rvdw_ref,
                      const double *volume_ratio, const double *grad_energy, double *grad_coords,
                      double *grad_params) {
     if (!ctx) return MBD_ERR_INPUT;
     if (!ctx->have_forward)
         return fail(ctx, MBD_ERR_STATE, "mbd_backward_dev", "no forward evaluation to differentiate");
+    if (evaluation != 0 && evaluation != ctx->eval_count)
+        return fail(ctx, MBD_ERR_STATE, "mbd_backward_dev",
+                    "the context's last evaluation is not the one to differentiate (evaluate it again first)");
     if (ctx->last_learned)
         return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_backward_dev",
                     "the last evaluation used learned screening; request its gradients from the evaluation");
