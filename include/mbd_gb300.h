@@ -61,8 +61,8 @@ typedef struct mbd_ctx mbd_ctx;
 /* Options.  Defaults (mbd_default_options): n_freq 15 (Sec. 3.3), beta 0.83, a 6
  * (Sec. 2.7), precision FP64, ns_tol 1e-8 (Frobenius norm of I - Z Y at which one
  * final Newton-Schulz step is taken; periodic systems: of all Bloch vectors' matrices
- * together), ns_max_iter 100, tc_chunk_stages 2, ewald_gamma, real_cutoff and
- * recip_cutoff 0 (automatic, see below). */
+ * together), ns_max_iter 100, tc_chunk_stages 0 (per kind), ewald_gamma, real_cutoff and
+ * recip_cutoff 0 (automatic, see below), learned_max_error 1e-6, mixed_max_error 1e-7. */
 typedef struct {
     int n_freq;          /* Gauss-Legendre points of the Casimir-Polder integral     */
     double beta;         /* damping scale s_R of the Fermi function, Eq. (fermi-damping) */
@@ -72,7 +72,8 @@ typedef struct {
     int ns_max_iter;
     int tc_chunk_stages; /* mixed modes: K stages (32 TF32 or 64 bf16 elements each) per
                             tensor-memory accumulation; the partial sums are added in FP32
-                            with round-to-nearest (default 2; 0 means 1)                  */
+                            with round-to-nearest (0, the default: 8 for BF16x3, 2 for TF32
+                            and TF32x3)                                                   */
     /* Periodic systems (Sec. 2.2, Ewald summation of the dipole tensor).  <= 0 selects:
      * real_cutoff = 6/ewald_gamma; ewald_gamma = 6/real_cutoff when only the cutoff is
      * given, else 2.5/Omega^(1/3); recip_cutoff = 10 ewald_gamma.  real_cutoff (bohr) also
@@ -96,6 +97,12 @@ typedef struct {
      * grad_params holds dE/d(alpha0_ref, c6_ref, ra, rw).  Finite and periodic systems.    */
     int scs_mode;
     double learned_max_error;
+    /* BF16x3 and TF32x3: largest accepted estimate of the energy error per atom (Ha) left by
+     * the tensor-core Z ~ Q^{-1/2} after the FP64 correction, (3/16) sqrt(s) r^2 / N with
+     * r = |Z Q Z - I|_F (the correction's error is second order in that of Z; default 1e-7).
+     * Above it the evaluation fails with MBD_ERR_NOT_CONVERGED (for instance a Q so badly
+     * conditioned that the reduced-precision iteration cannot resolve it; the FP64 path can). */
+    double mixed_max_error;
 } mbd_options;
 
 #define MBD_SCS_PLAIN 0

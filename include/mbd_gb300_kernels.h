@@ -63,6 +63,14 @@ int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float al
                  const float *D, float *C, void *C_hi, void *C_lo, float *CT, long long ldc, int chunk_stages,
                  int *err);
 
+/* Runs the tensor-core GEMM's bounded wait (the budget every wait of mbdk_gemm_tc and of the
+ * mixed-precision evaluation has, about 2 s there) on an mbarrier that nothing arrives at,
+ * with a budget of spin_cycles SM clock cycles (1 .. 2^32): the wait gives up and sets bit 8
+ * (the timeout bit) in the device int *err, which the caller reads after synchronising.  It
+ * tests the timeout path without a fault or a hang.  MBD_ERR_INPUT for a budget out of range
+ * or a NULL err. */
+int mbdk_tc_wait_check(void *stream, long long spin_cycles, int *err);
+
 /* C = alpha * A * op(B) + beta * D, FP64-accurate, on the TF32 tensor path by error-free
  * splitting (the paper has none: its FP64 products run on CPUs; this serves GB300, whose FP64
  * rate is a small fraction of its tensor rate).  A is M x K (lda); trans_b = 1: op(B) = B^T
@@ -95,7 +103,9 @@ int mbdk_gemm_f64_split(void *stream, int trans_b, int M, int N, int K, double a
  * calls no allocating routine.  Limit: batch * ((ld/64) * 4096 + 3 * ld) <= 2^21; larger
  * requests return MBD_ERR_SCRATCH_LIMIT before any work is launched.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device current, so
- * make that first call before any stream capture.  All calls on a device share the
+ * make that first call before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset of that device the library must be unloaded and loaded
+ * again before the next call.  All calls on a device share the
  * array and it keeps the last call's contents; calls whose work overlaps on the GPU
  * race on it and must be serialised by the caller.  status as in mbdk_cholesky_f64. */
 #define MBD_ERR_SCRATCH_LIMIT 9

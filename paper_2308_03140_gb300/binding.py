@@ -29,7 +29,7 @@ EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry
            "mbd_get_lattice_gradient", "mbd_set_scs_model", "mbd_get_learned_stats", "mbd_screen",
            "mbd_get_scs_detail", "mbd_log_energy", "mbd_ts_energy",
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
-           "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_gemm_f64_split", "mbdk_gemm_f64_split_work_bytes", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
+           "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_tc_wait_check", "mbdk_gemm_f64_split", "mbdk_gemm_f64_split_work_bytes", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
            "mbdk_cholesky_solve3_f64_noalloc", "mbdk_scs_features", "mbdk_mlp_forward", "mbdk_mlp_backward",
            "mbdk_mse_grad", "mbdk_adam_step", "mbdk_gather_rows")
 LEARNED_FEATURES, LEARNED_OUTPUTS, LEARNED_PARAMS = 74, 16, 28176
@@ -39,7 +39,8 @@ class mbd_options(C.Structure):
     _fields_ = [("n_freq", C.c_int), ("beta", C.c_double), ("a", C.c_double),
                 ("precision", C.c_int), ("ns_tol", C.c_double), ("ns_max_iter", C.c_int),
                 ("tc_chunk_stages", C.c_int), ("ewald_gamma", C.c_double), ("real_cutoff", C.c_double),
-                ("recip_cutoff", C.c_double), ("scs_mode", C.c_int), ("learned_max_error", C.c_double)]
+                ("recip_cutoff", C.c_double), ("scs_mode", C.c_int), ("learned_max_error", C.c_double),
+                ("mixed_max_error", C.c_double)]
 MBD_SCS_PLAIN, MBD_SCS_LEARNED, MBD_SCS_NL = 0, 1, 2
 
 
@@ -96,6 +97,7 @@ def load(path: str | None = None):
     L.mbdk_cholesky_f64.argtypes = [vp, vp, ll, i, vp, vp]
     f = C.c_float
     L.mbdk_gemm_tc.argtypes = [vp, i, i, i, i, i, f, vp, vp, ll, vp, vp, ll, f, vp, vp, vp, vp, vp, ll, i, vp]
+    L.mbdk_tc_wait_check.argtypes = [vp, ll, vp]
     L.mbdk_chol_solve3_f64.argtypes = [vp, vp, ll, i, vp, vp, vp]
     L.mbdk_cholesky_solve3_f64_noalloc.argtypes = [vp, vp, ll, i, vp, vp]
     L.mbdk_scs_features.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -140,7 +142,8 @@ class MBD:
     def __init__(self, device: int = 0, n_freq: int = 15, beta: float = 0.83, a: float = 6.0,
                  ns_tol: float = 1e-8, ns_max_iter: int = 100, precision: int = MBD_PREC_FP64,
                  tc_chunk_stages: int | None = None, ewald_gamma: float = 0.0, real_cutoff: float = 0.0,
-                 recip_cutoff: float = 0.0, scs_mode: int = MBD_SCS_PLAIN, learned_max_error: float = 1e-6):
+                 recip_cutoff: float = 0.0, scs_mode: int = MBD_SCS_PLAIN, learned_max_error: float = 1e-6,
+                 mixed_max_error: float = 1e-7):
         self.lib = load()
         opt = mbd_options()
         self.lib.mbd_default_options(C.byref(opt))
@@ -150,6 +153,7 @@ class MBD:
             opt.tc_chunk_stages = tc_chunk_stages
         opt.ewald_gamma, opt.real_cutoff, opt.recip_cutoff = ewald_gamma, real_cutoff, recip_cutoff
         opt.scs_mode, opt.learned_max_error = scs_mode, learned_max_error
+        opt.mixed_max_error = mixed_max_error
         h = C.c_void_p()
         rc = self.lib.mbd_create(C.byref(h), device, C.byref(opt))
         if rc:
@@ -357,6 +361,13 @@ def mbdk_gemm_tc(kind, A0, B0, C_out=None, A1=None, B1=None, alpha=1.0, beta=0.0
     return L.mbdk_gemm_tc(_stream(A0, stream), kind, mode, M, N, K, alpha, _tptr(A0), _tptr(A1), A0.stride(0),
                           _tptr(B0), _tptr(B1), B0.stride(0), beta, _tptr(D), _tptr(C_out), _tptr(C_hi),
                           _tptr(C_lo), _tptr(CT), ref.stride(0), chunk_stages, _tptr(err))
+
+
+def mbdk_tc_wait_check(err, spin_cycles, stream=None):
+    """The tensor-core GEMM's bounded wait on a barrier nothing arrives at (see the header):
+    err is an int32 CUDA tensor; returns the C return code."""
+    L = load()
+    return L.mbdk_tc_wait_check(_stream(err, stream), int(spin_cycles), _tptr(err))
 
 
 def mbdk_gemm_f64_split(A, B, C_out, alpha=1.0, beta=0.0, D=None, trans_b=True, work=None, err=None,

@@ -58,6 +58,9 @@ struct TcArgs {
     long long sC = 0;
 };
 cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_t s);
+// The GEMM's bounded mbarrier wait on a barrier nothing arrives at, with a budget of `budget`
+// clock cycles: sets ST_TC_TIMEOUT in *err when it gives up.
+cudaError_t tc_wait_probe(long long budget, int *err, cudaStream_t s);
 // FP64-accurate C = alpha A op(B) + beta D (k_split64.cu): the operands cut into exact TF32
 // slices (split64.cuh), the slice products on the tensor cores (tc_gemm kind 0) over K in
 // exact pieces, summed into C in FP64.  trans_b: op(B) = B^T with B N x K, else B is K x N.
@@ -298,13 +301,24 @@ void cgemm_f64(const double *A, const double *B, const double *D, double *C, lon
 // work: 3 nk 2 ld doubles.
 void clanczos_coefficients(const double *Q, long long ld, int nk, int steps, double *work, double *coef,
                            cudaStream_t s);
+// Mixed modes on a cell: the real symmetric embedding M = [[Re, -Im], [Im, Re]] of planar slot k
+// of Q (order 2n in an lde x lde matrix, padded), the planar slot k of Z from the embedded
+// Ze ~ M^{-1/2}, and E = 1/(2 nk) sum_k ek[k] - 3/4 sum omega_bar from the embedded energies.
+void embed_hermitian(const double *Q, long long ld, int n, int k, double *M, long long lde, cudaStream_t s);
+void extract_hermitian(const double *Ze, long long lde, int n, double *Z, long long ld, int k, cudaStream_t s);
+void periodic_mixed_energy(const double *ek, int nk, const double *ombar, int N, double *out, cudaStream_t s);
 // E = sqrt_s/(2 nk) sum_k Re Tr Y_k - 3/2 sum omega_bar (compensated).
 void energy_trace_periodic(const double *Y, long long ld, int n, int nk, const double *ombar, int N,
                            double sqrt_s, double *out, cudaStream_t s);
 // MBD gradient of the periodic energy from Z_k (Q(q_k)^{-1/2} = zscale Z_k): per atom
 // g_ombar, g_abar0, g_rbar, gR (o), and dE/dA accumulated into gA [9].  work: 2N doubles.
+// tq: (1/nk) sum_q Re Tr (Q(q)^{1/2})_ii per atom for dE/d omega_bar (second order in the error of
+// Z), or NULL to take it from Z.
 void periodic_mbd_grad(const AtomBufs &b, const PeriodicBufs &p, double beta, double a, const double *Z,
-                       long long ld, double zscale, const MbdGradOut &o, double *work, double *gA, cudaStream_t s);
+                       long long ld, double zscale, const MbdGradOut &o, double *work, double *gA, cudaStream_t s,
+                       const double *tq = nullptr);
+// out[i] = (1/rows) sum_r x[r][i] for a rows x N array (compensated).
+void mean_rows(const double *x, int rows, int N, double *out, cudaStream_t s);
 // SCS adjoint pair pass over lattice images (as scs_grad_pass), with the lattice part
 // accumulated into gA [9].  gA_part: N x 9 doubles of workspace.
 void scs_grad_periodic(const AtomBufs &b, const CellGeom &c, double beta, double a, const double *X,

@@ -12,7 +12,7 @@
 //     alpha0_i^2 m2, alpha0_i^2 m3;
 //   MLP 74 -> 128 -> 128 -> 16 on standardised features, SiLU activations, FP16 weights and
 //     biases, FP32 accumulation; output y_k = log(alpha_bar(u_k) / alpha(u_k)).
-// Parameter layout of one ensemble member (FP16): W1 [68][128], b1 [128], W2 [128][128],
+// Parameter layout of one ensemble member (FP16): W1 [74][128], b1 [128], W2 [128][128],
 // b2 [128], W3 [128][16], b3 [16] (W[in][out], row-major), kParams halves in all.
 #include <cuda_fp16.h>
 
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(128) k_mlp_forward(int B, const float *X, cons
 }
 
 // Backward of sum(dY * Y): grid (ceil(B / 32), members), 128 threads.  Needs the cache of the
-// forward pass.  dX (optional) [member][B][68]: gradient with respect to the raw features.
+// forward pass.  dX (optional) [member][B][74]: gradient with respect to the raw features.
 // grad (optional) [member][kParams] FP32, accumulated (atomic adds of per-CTA sums).
 __global__ void __launch_bounds__(128) k_mlp_backward(int B, const float *X, const float *mean, const float *stdv,
                                                       const __half *params, const float *zcache, const float *dY,

@@ -570,10 +570,12 @@ __global__ void __launch_bounds__(256) k_mbd_grad_periodic(AtomBufs b, PeriodicB
     for (int e = 0; e < 9; ++e) atomicAdd(&gA[e], cij * zA[e]);
 }
 
-// g_ombar = zscale/(4 nk) sum_k Re Tr Z_k[i,i] 2 omega_bar_i - 3/2 + g_c sqrt(abar0);
+// g_ombar = zscale/(4 nk) sum_k Re Tr Z_k[i,i] 2 omega_bar_i - 3/2 + g_c sqrt(abar0), or, with tq_i
+// = (1/nk) sum_k Re Tr (Q(q_k)^{1/2})_ii given, the same derivative as tq_i / (2 omega_bar_i) - 3/2
+// (the diagonal and coupling terms of dQ/d omega_bar_i together, second order in the error of Z);
 // g_abar0 = g_c omega_bar / (2 sqrt(abar0)).
 __global__ void k_mbd_grad_periodic_finalize(AtomBufs b, const double *Z, long long ld, int nk, double zscale,
-                                             const double *g_c, MbdGradOut o) {
+                                             const double *g_c, MbdGradOut o, const double *tq) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
     double d = 0.0;
@@ -582,8 +584,23 @@ __global__ void k_mbd_grad_periodic_finalize(AtomBufs b, const double *Z, long l
         for (int xx = 0; xx < 3; ++xx) d += Zr[(3LL * i + xx) * ld + 3 * i + xx];
     }
     const double sa = sqrt(b.abar0[i]);
-    o.g_ombar[i] = 0.25 * zscale / nk * d * 2.0 * b.ombar[i] - 1.5 + g_c[i] * sa;
+    o.g_ombar[i] = tq ? tq[i] / (2.0 * b.ombar[i]) - 1.5
+                      : 0.25 * zscale / nk * d * 2.0 * b.ombar[i] - 1.5 + g_c[i] * sa;
     o.g_abar0[i] = g_c[i] * b.ombar[i] / (2.0 * sa);
+}
+
+// out[i] = (1/rows) sum_r x[r][i] (compensated).
+__global__ void k_mean_rows(const double *x, int rows, int N, double *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double s = 0.0, c = 0.0;
+    for (int r = 0; r < rows; ++r) {
+        double t, e;
+        two_sum(s, x[static_cast<long long>(r) * N + i], t, e);
+        s = t;
+        c += e;
+    }
+    out[i] = (s + c) / rows;
 }
 
 // ---- SCS adjoint over lattice images -------------------------------------------------
@@ -724,6 +741,88 @@ void build_q_periodic(const AtomBufs &b, const PeriodicBufs &p, double beta, dou
     }
 }
 
+namespace {
+// Real symmetric embedding of the Hermitian Q(q_k) = A + iB (planar, slot k): M = [[A, -B],
+// [B, A]] of order 2n in an lde x lde matrix, padded with the diagonal entry A_00 (inside the
+// spectrum) and zero couplings.  Its eigenvalues are those of Q(q_k), each twice.
+__global__ void k_embed_hermitian(const double *Q, long long ld, int n, int k, double *M, long long lde) {
+    const double *Re = Q + static_cast<long long>(k) * 2 * ld * ld, *Im = Re + ld * ld;
+    const long long total = lde * lde;
+    const double pad = Re[0];
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long r = e / lde, c = e % lde;
+        double v;
+        if (r < 2LL * n && c < 2LL * n) {
+            const long long rr = r < n ? r : r - n, cc = c < n ? c : c - n;
+            const double a = Re[rr * ld + cc], b = Im[rr * ld + cc];
+            v = (r < n) == (c < n) ? a : (r < n ? -b : b);
+        } else {
+            v = r == c ? pad : 0.0;
+        }
+        M[e] = v;
+    }
+}
+// Planar slot k of Z (Re, Im) from the embedded matrix function Ze ~ M^{-1/2} =
+// [[Re, -Im], [Im, Re]]: the first block column; zero outside the n x n block.
+__global__ void k_extract_hermitian(const double *Ze, long long lde, int n, double *Z, long long ld, int k) {
+    double *Re = Z + static_cast<long long>(k) * 2 * ld * ld, *Im = Re + ld * ld;
+    const long long total = ld * ld;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long r = e / ld, c = e % ld;
+        const bool in = r < n && c < n;
+        Re[e] = in ? Ze[r * lde + c] : 0.0;
+        Im[e] = in ? Ze[(r + n) * lde + c] : 0.0;
+    }
+}
+// E = 1/(2 nk) sum_k e_k - 3/4 sum omega_bar, where e_k = 1/2 Tr M_k^{1/2} - 3/2 sum omega_bar is
+// the mixed modes' corrected energy of the embedded matrix of Bloch vector k (Tr M_k^{1/2} =
+// 2 Tr Q(q_k)^{1/2}); compensated sums.
+__global__ void k_periodic_mixed_energy(const double *ek, int nk, const double *ombar, int N, double *out) {
+    double s = 0.0, cc = 0.0;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        double t, er;
+        two_sum(s, 0.5 * ek[k] / nk, t, er);
+        s = t; cc += er;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double t, er;
+        two_sum(s, -0.75 * ombar[i], t, er);
+        s = t; cc += er;
+    }
+    __shared__ double ss[256], sc2[256];
+    ss[threadIdx.x] = s;
+    sc2[threadIdx.x] = cc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0, C = 0.0;
+        for (int q = 0; q < blockDim.x; ++q) {
+            double t, er;
+            two_sum(S, ss[q], t, er);
+            S = t;
+            C += er + sc2[q];
+        }
+        out[0] = S + C;
+    }
+}
+}  // namespace
+
+void embed_hermitian(const double *Q, long long ld, int n, int k, double *M, long long lde, cudaStream_t s) {
+    count_launches(1);
+    k_embed_hermitian<<<1216, 256, 0, s>>>(Q, ld, n, k, M, lde);
+}
+
+void extract_hermitian(const double *Ze, long long lde, int n, double *Z, long long ld, int k, cudaStream_t s) {
+    count_launches(1);
+    k_extract_hermitian<<<1216, 256, 0, s>>>(Ze, lde, n, Z, ld, k);
+}
+
+void periodic_mixed_energy(const double *ek, int nk, const double *ombar, int N, double *out, cudaStream_t s) {
+    count_launches(1);
+    k_periodic_mixed_energy<<<1, 256, 0, s>>>(ek, nk, ombar, N, out);
+}
+
 void cscale(double *Y, long long ld, int nk, double scale, cudaStream_t s) {
     count_launches(1);
     k_scale_all<<<1216, 256, 0, s>>>(Y, static_cast<long long>(nk) * 2 * ld * ld, scale);
@@ -788,8 +887,14 @@ void energy_trace_periodic(const double *Y, long long ld, int n, int nk, const d
     k_energy_periodic<<<1, 256, 0, s>>>(Y, ld, n, nk, ombar, N, 0.5 * sqrt_s / nk, out);
 }
 
+void mean_rows(const double *x, int rows, int N, double *out, cudaStream_t s) {
+    count_launches(1);
+    k_mean_rows<<<cdiv(N, 128), 128, 0, s>>>(x, rows, N, out);
+}
+
 void periodic_mbd_grad(const AtomBufs &b, const PeriodicBufs &p, double beta, double a, const double *Z,
-                       long long ld, double zscale, const MbdGradOut &o, double *work, double *gA, cudaStream_t s) {
+                       long long ld, double zscale, const MbdGradOut &o, double *work, double *gA, cudaStream_t s,
+                       const double *tq) {
     double *g_c = work;
     cudaMemsetAsync(g_c, 0, sizeof(double) * b.N, s);
     cudaMemsetAsync(o.g_rbar, 0, sizeof(double) * b.N, s);
@@ -799,7 +904,7 @@ void periodic_mbd_grad(const AtomBufs &b, const PeriodicBufs &p, double beta, do
     count_launches(2);
     k_mbd_grad_periodic<<<dim3(ntile * (ntile + 1) / 2, p.nk), 256, 0, s>>>(b, p, beta, a, Z, ld, zscale, ntile, g_c,
                                                                             o.g_rbar, o.gR, gA);
-    k_mbd_grad_periodic_finalize<<<cdiv(b.N, 128), 128, 0, s>>>(b, Z, ld, p.nk, zscale, g_c, o);
+    k_mbd_grad_periodic_finalize<<<cdiv(b.N, 128), 128, 0, s>>>(b, Z, ld, p.nk, zscale, g_c, o, tq);
 }
 
 void scs_grad_periodic(const AtomBufs &b, const CellGeom &c, double beta, double a, const double *X,

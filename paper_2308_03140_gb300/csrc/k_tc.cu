@@ -14,7 +14,7 @@
 // 128 rows x 128 bytes are staged in shared memory by TMA (128-byte swizzle) through an
 // mbarrier ring;
 // warp 4 issues the TMA loads, warp 5 issues tcgen05.mma.  K is split into chunks of
-// `chunk_stages` stages, each accumulated afresh in one of two 128-column TMEM buffers;
+// `chunk_stages` stages, each accumulated afresh in one of kBufs 128-column TMEM buffers;
 // warps 0-3 (one tile row per thread) read each finished chunk back (tcgen05.ld 32x32b)
 // and add it to FP32 registers with round-to-nearest while the next chunk accumulates.
 // The tensor core's own accumulation truncates: its bias grows with the number of terms
@@ -27,6 +27,8 @@
 // flag, stops issuing work, waits (bounded) for its own TMA copies and MMAs, frees its
 // tensor memory and returns.
 #include <algorithm>
+#include <cstdlib>
+#include <string>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -42,6 +44,10 @@ constexpr int TM = 128, TN = 128;
 constexpr int KB = 128;                         // bytes of K per stage per row (one swizzle atom)
 constexpr int TILE_BYTES = TM * KB;             // 16 KB
 constexpr long long kSpinCycles = 4000000000LL; // ~2 s at 2 GHz
+// Tensor-memory accumulation buffers of TN columns each (all 512 columns of the SM): chunk c
+// accumulates in buffer c % kBufs, so the MMAs run up to kBufs - 1 chunks ahead of the
+// epilogue warps that drain them.
+constexpr int kBufs = 4;
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -62,10 +68,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait on an mbarrier phase; false (and the error flag raised) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err, long long budget = kSpinCycles) {
     const long long t0 = clock64();
     while (!mbar_try(b, parity)) {
-        if (clock64() - t0 > kSpinCycles) {
+        if (clock64() - t0 > budget) {
             atomicOr(err, ST_TC_TIMEOUT);
             return false;
         }
@@ -290,9 +296,9 @@ __global__ void __launch_bounds__(192, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
     uint64_t *empty = full + Cfg::STAGES;
-    uint64_t *cfull = empty + Cfg::STAGES;   // [2] accumulator buffer holds a finished chunk
-    uint64_t *cfree = cfull + 2;             // [2] epilogue has drained the buffer
-    uint64_t *done = cfree + 2;              // every MMA issued has completed
+    uint64_t *cfull = empty + Cfg::STAGES;   // [kBufs] accumulator buffer holds a finished chunk
+    uint64_t *cfree = cfull + kBufs;         // [kBufs] epilogue has drained the buffer
+    uint64_t *done = cfree + kBufs;          // every MMA issued has completed
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kBufs; ++b) {
             mbar_init(&cfull[b], 1);
             mbar_init(&cfree[b], 4);   // one arrival per epilogue warp
         }
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
-                     "r"(2 * TN));
+                     "r"(kBufs * TN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     fence_before();
@@ -364,13 +370,13 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
     } else if (warp == 5) {
-        // ---- MMA issuer (one thread): chunk c accumulates afresh into buffer c & 1 ----
+        // ---- MMA issuer (one thread): chunk c accumulates afresh into buffer c % kBufs ----
         if (lane == 0) {
             int kg = 0, cg = 0;   // stages consumed and chunks begun by this CTA before the current item
             for (int w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, cg += nchunks) {
                 for (int kt = 0; kt < nk && !*abort_flag; ++kt, ++kg) {
-                    const int c = cg + kt / cs, buf = c & 1;
-                    if (kt % cs == 0 && c >= 2 && !mbar_wait(&cfree[buf], ((c >> 1) - 1) & 1, g.err)) {
+                    const int c = cg + kt / cs, buf = c % kBufs;
+                    if (kt % cs == 0 && c >= kBufs && !mbar_wait(&cfree[buf], ((c / kBufs) - 1) & 1, g.err)) {
                         *abort_flag = 1;
                         break;
                     }
@@ -415,13 +421,13 @@ __global__ void __launch_bounds__(192, 1)
             const int row = warp * 32 + lane;
             const long long m = static_cast<long long>(tm) * TM + row;
             for (int c = 0; c < nchunks; ++c) {
-                const int buf = (cg + c) & 1;
+                const int buf = (cg + c) % kBufs;
                 if (c == max(0, nchunks - 2) && g.beta != 0.f) {   // this row of D into L2 ahead of the epilogue
                     const float *drow = Dp + m * g.ld + static_cast<long long>(tn) * TN;
 #pragma unroll
                     for (int q = 0; q < TN / 32; ++q) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(drow + 32 * q));
                 }
-                ok = mbar_wait(&cfull[buf], ((cg + c) >> 1) & 1, g.err) && !*abort_flag;
+                ok = mbar_wait(&cfull[buf], ((cg + c) / kBufs) & 1, g.err) && !*abort_flag;
                 ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
                 if (!ok) {
                     *abort_flag = 1;
@@ -451,7 +457,320 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) mbar_wait(done, 0, g.err);
         __syncwarp();
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * TN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kBufs * TN));
+    }
+}
+
+// ---- CTA-pair form (tcgen05 cta_group::2) ----------------------------------------------
+// A cluster of two CTAs computes a pair tile of 256 x 128 (tile rows 2 TP and 2 TP + 1 of
+// tile column tn, tc_tiles.cuh): CTA r stages A rows [256 TP + 128 r, +128) and B rows
+// [128 tn + 64 r, +64) of every K stage in its own shared memory (TMA, 128-byte swizzle); the
+// even CTA issues tcgen05.mma.cta_group::2 with M = 256, N = 128, which takes the A halves and
+// the B halves of both CTAs and accumulates rows 128 r .. 128 r + 127 of the pair tile in
+// CTA r's tensor memory.  A CTA then stages 48 KB of operands per K stage (split kinds) for
+// the MMA work that 64 KB feeds in the single-CTA form, and four stages fit where three do.
+// Barriers in each CTA's shared memory:
+//   full[s]   (even CTA) the bytes of stage s of both CTAs landed: the even CTA's producer
+//             expects both CTAs' bytes, and the odd CTA's loads count their bytes on the even
+//             CTA's barrier (cta_group::2 form of the TMA load);
+//   empty[s]  the MMAs reading stage s completed (the even CTA commits to both CTAs);
+//   cfull[b]  a chunk finished in tensor-memory buffer b (committed to both);
+//   cfree[b]  (even CTA) the eight epilogue warps of the pair drained buffer b;
+//   done      every MMA issued completed (committed to both).
+// Every wait is bounded as in the single-CTA form; on a timeout the CTA raises the error
+// flag and stops, and its peer's waits run out in turn.  Both CTAs leave through a cluster
+// barrier, so neither exits while the other can still signal its shared memory.
+template <int KIND>
+struct TcCfg2 {
+    static constexpr int PAIRS = KIND == 0 ? 1 : 3;
+    static constexpr int B_BYTES = TILE_BYTES / 2;   // 64 rows x 128 bytes
+    static constexpr int OFF_B0 = TILE_BYTES, OFF_A1 = TILE_BYTES + B_BYTES, OFF_B1 = 2 * TILE_BYTES + B_BYTES;
+    static constexpr int STAGE_BYTES = (KIND == 0 ? 1 : 2) * (TILE_BYTES + B_BYTES);
+    static constexpr int STAGES = KIND == 0 ? 8 : 4;
+    static constexpr int ELEM = KIND == 1 ? 2 : 4;
+    static constexpr bool TF32 = KIND != 1;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512;
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+// Address in the shared::cluster window of the same shared-memory object in CTA `rank`.
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(a) : "r"(local), "r"(rank));
+    return a;
+}
+__device__ __forceinline__ void remote_arrive(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_cl(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (cluster-scope acquire: arrivals may come from the peer CTA).
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t *b, uint32_t parity, int *err) {
+    const long long t0 = clock64();
+    while (!mbar_try_cl(b, parity)) {
+        if (clock64() - t0 > kSpinCycles) {
+            atomicOr(err, ST_TC_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+// TMA load into this CTA's shared memory whose completion is counted on an mbarrier of either
+// CTA of the pair (shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            su32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// Instruction descriptor of the pair MMA: M = 256 (two CTAs), N = TN.
+__host__ __device__ constexpr uint32_t idesc2(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(TN >> 3) << 17) | (static_cast<uint32_t>(256 >> 4) << 24);
+}
+template <bool TF32>
+__device__ __forceinline__ void mma2(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    if (TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(idesc2(2)), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(idesc2(1)), "r"(acc));
+}
+// Arrival on an mbarrier (own or peer, shared::cluster address) once every prior MMA of this
+// thread has completed.
+__device__ __forceinline__ void commit2(uint32_t cluster_addr) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(cluster_addr)
+                 : "memory");
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm2(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+               const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs g,
+               int tiles_n) {
+    using Cfg = TcCfg2<KIND>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+    uint64_t *empty = full + Cfg::STAGES;
+    uint64_t *cfull = empty + Cfg::STAGES;
+    uint64_t *cfree = cfull + kBufs;
+    uint64_t *done = cfree + kBufs;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const uint32_t rank = cluster_rank();
+    const bool lead = rank == 0;
+    const int cl = static_cast<int>(blockIdx.x >> 1), ncl = static_cast<int>(gridDim.x >> 1);
+    const int tiles_m = g.M / TM;
+    const int ptiles = tctiles::pair_tile_count(g.mode, tiles_m, tiles_n);
+    const int items = ptiles * g.batch;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < kBufs; ++b) {
+            mbar_init(&cfull[b], 1);
+            mbar_init(&cfree[b], 8);   // four epilogue warps in each CTA of the pair
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    if (warp == 0) {   // both CTAs of the pair allocate, at the same tensor-memory address
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
+                     "r"(kBufs * TN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;\n");
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync();   // both CTAs' barriers exist before either signals the other
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nk = static_cast<int>((static_cast<long long>(g.K) * Cfg::ELEM) / KB);
+    const int cs = (g.chunk_stages > 0 && g.chunk_stages < nk) ? g.chunk_stages : nk;
+    const int nchunks = (nk + cs - 1) / cs;
+    constexpr int KELEM = KB / Cfg::ELEM;
+
+    if (warp == 4) {
+        // ---- TMA producer of this CTA's halves (one thread); every stage's bytes are counted on
+        // the even CTA's full[s] ----
+        if (lane == 0) {
+            int issued = 0, kg = 0;
+            const uint32_t full_pair = peer_addr(su32(&full[0]), 0);
+            for (int w = cl; w < items && !*abort_flag; w += ncl) {
+                const int bz = w / ptiles;
+                int TP, tn;
+                tctiles::pair_tile(w - bz * ptiles, g.mode, tiles_m, tiles_n, TP, tn);
+                const int ya = bz * g.M + (2 * TP + static_cast<int>(rank)) * TM;
+                const int yb = bz * g.N + tn * TN + static_cast<int>(rank) * (TN / 2);
+                for (int kt = 0; kt < nk && !*abort_flag; ++kt, ++kg) {
+                    const int s = kg % Cfg::STAGES;
+                    const uint32_t ph = (kg / Cfg::STAGES) & 1;
+                    if (kg >= Cfg::STAGES && !mbar_wait_cl(&empty[s], ph ^ 1, g.err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *st = smem + s * Cfg::STAGE_BYTES;
+                    if (lead) mbar_expect_tx(&full[s], 2 * Cfg::STAGE_BYTES);   // both CTAs' bytes
+                    const uint32_t fb = full_pair + static_cast<uint32_t>(s) * 8u;
+                    const int kx = kt * KELEM;
+                    tma_load_2d_pair(st, &mA0, kx, ya, fb);
+                    tma_load_2d_pair(st + Cfg::OFF_B0, &mB0, kx, yb, fb);
+                    if (KIND != 0) {
+                        tma_load_2d_pair(st + Cfg::OFF_A1, &mA1, kx, ya, fb);
+                        tma_load_2d_pair(st + Cfg::OFF_B1, &mB1, kx, yb, fb);
+                    }
+                    issued = kg + 1;
+                }
+            }
+            if (*abort_flag) {
+                // let the copies land before shared memory is released: the even CTA waits for
+                // the stages it expected (they count both CTAs' bytes); the odd CTA, which cannot
+                // observe the even CTA's barriers, gives its last copies a bounded time to land
+                if (lead) {
+                    for (int k = (issued > Cfg::STAGES ? issued - Cfg::STAGES : 0); k < issued; ++k)
+                        mbar_wait(&full[k % Cfg::STAGES], (k / Cfg::STAGES) & 1, g.err, kSpinCycles / 8);
+                } else {
+                    const long long t0 = clock64();
+                    while (clock64() - t0 < 2000000LL) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0 && lead) {
+            // ---- MMA issuer of the pair (even CTA) ----
+            const uint32_t peer = 1;
+            int kg = 0, cg = 0;
+            for (int w = cl; w < items && !*abort_flag; w += ncl, cg += nchunks) {
+                for (int kt = 0; kt < nk && !*abort_flag; ++kt, ++kg) {
+                    const int c = cg + kt / cs, buf = c % kBufs;
+                    if (kt % cs == 0 && c >= kBufs && !mbar_wait_cl(&cfree[buf], ((c / kBufs) - 1) & 1, g.err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    const int s = kg % Cfg::STAGES;
+                    if (!mbar_wait_cl(&full[s], (kg / Cfg::STAGES) & 1, g.err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t base = su32(smem + s * Cfg::STAGE_BYTES);
+                    const uint32_t dt = tmem + static_cast<uint32_t>(buf * TN);
+#pragma unroll
+                    for (int k = 0; k < KB / 32; ++k) {
+                        const uint64_t a0 = sdesc(base + k * 32), b0 = sdesc(base + Cfg::OFF_B0 + k * 32);
+                        mma2<Cfg::TF32>(dt, a0, b0, (kt % cs != 0 || k != 0) ? 1u : 0u);
+                        if (Cfg::PAIRS == 3) {
+                            const uint64_t a1 = sdesc(base + Cfg::OFF_A1 + k * 32);
+                            const uint64_t b1 = sdesc(base + Cfg::OFF_B1 + k * 32);
+                            mma2<Cfg::TF32>(dt, a0, b1, 1u);
+                            mma2<Cfg::TF32>(dt, a1, b0, 1u);
+                        }
+                    }
+                    commit2(su32(&empty[s]));
+                    commit2(peer_addr(su32(&empty[s]), peer));
+                    if (kt % cs == cs - 1 || kt == nk - 1) {
+                        commit2(su32(&cfull[buf]));
+                        commit2(peer_addr(su32(&cfull[buf]), peer));
+                    }
+                }
+            }
+            commit2(su32(done));
+            commit2(peer_addr(su32(done), peer));
+        }
+    } else {
+        // ---- epilogue warps 0-3 of each CTA: thread = row of this CTA's tile ----
+        bool ok = true;
+        int cg = 0;
+        const uint32_t cfree_pair = lead ? su32(&cfree[0]) : peer_addr(su32(&cfree[0]), 0);
+        for (int w = cl; w < items && ok; w += ncl, cg += nchunks) {
+            const int bz = w / ptiles;
+            int TP, tn;
+            tctiles::pair_tile(w - bz * ptiles, g.mode, tiles_m, tiles_n, TP, tn);
+            const int tm = 2 * TP + static_cast<int>(rank);
+            const bool write = tctiles::pair_tile_valid(g.mode, tiles_m, TP, tn, static_cast<int>(rank));
+            const float *Dp = g.D ? g.D + bz * g.sC : nullptr;
+            float *Cp = g.C ? g.C + bz * g.sC : nullptr;
+            float acc[TN];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[j] = 0.f;
+            const int row = warp * 32 + lane;
+            const long long m = static_cast<long long>(tm) * TM + row;
+            for (int c = 0; c < nchunks; ++c) {
+                const int buf = (cg + c) % kBufs;
+                if (write && c == max(0, nchunks - 2) && g.beta != 0.f) {
+                    const float *drow = Dp + m * g.ld + static_cast<long long>(tn) * TN;
+#pragma unroll
+                    for (int q = 0; q < TN / 32; ++q) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(drow + 32 * q));
+                }
+                ok = mbar_wait_cl(&cfull[buf], ((cg + c) / kBufs) & 1, g.err) && !*abort_flag;
+                ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t tb = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(buf * TN);
+#pragma unroll
+                for (int q = 0; q < TN / 32; ++q) {
+                    uint32_t r[32];
+                    tmem_ld32(tb + q * 32, r);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(r[j]);
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) remote_arrive(cfree_pair + static_cast<uint32_t>(buf) * 8u);
+            }
+            if (ok && write) tile_epilogue<KIND>(g, acc, m, tm, tn, Dp, Cp, lane);
+        }
+    }
+    __syncwarp();
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        // every MMA of the pair must have completed before this CTA's tensor memory is freed
+        if (lane == 0) mbar_wait_cl(done, 0, g.err);
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kBufs * TN));
+    }
+    __syncthreads();
+    cluster_sync();   // the peer no longer signals this CTA's shared memory
+}
+
+// The GEMM's bounded wait on a barrier that nothing arrives at: it gives up after `budget`
+// cycles and raises ST_TC_TIMEOUT, as a GEMM wait does.  One thread; nothing in flight.
+__global__ void k_wait_probe(long long budget, int *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        mbar_wait(&bar, 0, err, budget);
     }
 }
 
@@ -470,13 +789,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // Tensor map of a row-major rows x cols matrix (row pitch ld elements), box of 128 rows
 // by 128 bytes, 128-byte swizzle.
-bool make_map(CUtensorMap *m, const void *base, int kind, long long rows, long long cols, long long ld) {
+bool make_map(CUtensorMap *m, const void *base, int kind, long long rows, long long cols, long long ld,
+              int box_rows = TM) {
     auto fn = encode_fn();
     if (!fn || !base) return false;
     const int elem = kind == 1 ? 2 : 4;
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * elem)};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(KB / elem), static_cast<cuuint32_t>(TM)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(KB / elem), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t es[2] = {1, 1};
     return fn(m, kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
               const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -517,7 +837,78 @@ cudaError_t launch_tc(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// CTA-pair launch: clusters of two CTAs, one pair per two SMs, as many pairs as fit at once
+// (persistent), each looping over pair tiles.
+template <int KIND>
+cudaError_t launch_tc2(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
+    using Cfg = TcCfg2<KIND>;
+    static int max_clusters = 0;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attrs[1];
+    attrs[0].id = cudaLaunchAttributeClusterDimension;
+    attrs[0].val.clusterDim.x = 2;
+    attrs[0].val.clusterDim.y = 1;
+    attrs[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = Cfg::SMEM;
+    cfg.stream = s;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 1;
+    if (!max_clusters) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm2<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        cfg.gridDim = dim3(static_cast<unsigned>(sms & ~1), 1, 1);
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, k_tc_gemm2<KIND>, &cfg);
+        if (e != cudaSuccess) return e;
+        if (n < 1) return cudaErrorInvalidConfiguration;
+        max_clusters = n;
+    }
+    CUtensorMap a0, a1, b0, b1;
+    const long long lda = op.lda, ldb = op.ldb;
+    const long long rows_a = static_cast<long long>(g.batch) * g.M, rows_b = static_cast<long long>(g.batch) * g.N;
+    if (!make_map(&a0, op.A0, KIND, rows_a, g.K, lda, TM) || !make_map(&b0, op.B0, KIND, rows_b, g.K, ldb, TN / 2))
+        return cudaErrorInvalidValue;
+    if (KIND != 0) {
+        if (!make_map(&a1, op.A1, KIND, rows_a, g.K, lda, TM) || !make_map(&b1, op.B1, KIND, rows_b, g.K, ldb, TN / 2))
+            return cudaErrorInvalidValue;
+    } else {
+        a1 = a0;
+        b1 = b0;
+    }
+    const int tmt = g.M / TM, tnt = g.N / TN;
+    const long long items = static_cast<long long>(tctiles::pair_tile_count(g.mode, tmt, tnt)) * g.batch;
+    const int clusters = static_cast<int>(std::min<long long>(items, max_clusters));
+    cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters), 1, 1);
+    count_launches(1);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_gemm2<KIND>, a0, a1, b0, b1, g, tnt);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// The single-CTA form unless MBDGB_TC_FORM=pair is set in the environment (the pair form, for
+// comparison).
+bool use_pairs() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("MBDGB_TC_FORM");
+        v = (e && std::string(e) == "pair") ? 1 : 0;
+    }
+    return v == 1;
+}
+
 }  // namespace
+
+cudaError_t tc_wait_probe(long long budget, int *err, cudaStream_t s) {
+    if (budget < 1 || budget > (1LL << 32) || !err) return cudaErrorInvalidValue;
+    count_launches(1);
+    k_wait_probe<<<1, 32, 0, s>>>(budget, err);
+    return cudaGetLastError();
+}
 
 cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.M % TM || g.N % TN || g.K % 64 || g.mode < 0 || g.mode > 2 ||
@@ -527,6 +918,11 @@ cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_
         (kind != 0 && (!op.A1 || !op.B1)) || (kind == 0 && (g.Ch || g.CTh)) || g.batch < 1 || g.batch > 65535 ||
         (g.batch > 1 && (g.Ch || g.CT || g.CTh || g.C64 || g.resid || g.sC < static_cast<long long>(g.M) * g.ld)))
         return cudaErrorInvalidValue;
+    if (use_pairs()) {
+        if (kind == 0) return launch_tc2<0>(op, g, s);
+        if (kind == 1) return launch_tc2<1>(op, g, s);
+        return launch_tc2<2>(op, g, s);
+    }
     if (kind == 0) return launch_tc<0>(op, g, s);
     if (kind == 1) return launch_tc<1>(op, g, s);
     return launch_tc<2>(op, g, s);

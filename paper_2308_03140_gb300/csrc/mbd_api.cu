@@ -159,6 +159,10 @@ struct mbd_ctx {
     float *fY = nullptr, *fZ = nullptr, *fY2 = nullptr, *fZ2 = nullptr, *fP = nullptr, *fPT = nullptr;
     void *hY[2] = {}, *hZ[2] = {}, *hY2[2] = {}, *hZ2[2] = {}, *hP[2] = {}, *hPT[2] = {};   // split operands
     double corr_resid = 0.0;   // |Zd Q Zd - I|_F of the mixed modes' correction
+    // mixed modes on a cell: each Hermitian Q(q) as the real symmetric [[Re, -Im], [Im, Re]] of
+    // order 2n (leading dimension lde), its FP64 workspaces
+    long long lde = 0;
+    double *eM = nullptr, *eV = nullptr, *eW = nullptr, *eVT = nullptr, *eZ = nullptr;
     double *dh, *dgomb, *dgab0, *dgrb, *dgR, *dga0, *dgom, *dgrv, *dgp;
     // periodic systems: cell, Bloch vectors and reciprocal lattice (host lists, device copies)
     bool periodic = false;
@@ -361,10 +365,16 @@ int allocate(mbd_ctx *ctx) {
     // Q (= Y), Z, P, Y', Z': real, or nk planar complex matrices for a periodic system
     const size_t matq = ctx->periodic ? mat * 2 * static_cast<size_t>(nk) : mat;
     bytes += 5 * matq;
-    const size_t mat32 = mat / 2, mat16 = mat / 4;
     const int prec = ctx->opt.precision;
+    // the mixed modes' iteration buffers: the matrix order, or the order of a cell's embedded
+    // Hermitian matrices
+    const long long ldm = ctx->periodic ? ctx->lde : ld;
+    const size_t mat32 = sizeof(float) * static_cast<size_t>(ldm) * ldm, mat16 = mat32 / 2;
     const size_t split_mat = prec == MBD_PREC_BF16X3 ? mat16 : (prec == MBD_PREC_TF32X3 ? mat32 : 0);
     if (!fp64_path(prec)) bytes += 6 * mat32;
+    const size_t emat = sizeof(double) * static_cast<size_t>(ctx->lde) * ctx->lde;
+    const bool embed = ctx->periodic && !fp64_path(prec);
+    if (embed) bytes += 5 * emat;
     const size_t split_work = prec == MBD_PREC_FP64_SPLIT ? al(gemm_f64_split_work_bytes(static_cast<int>(ld),
                                                                                           static_cast<int>(ld),
                                                                                           static_cast<int>(ld)))
@@ -374,9 +384,10 @@ int allocate(mbd_ctx *ctx) {
     // FP32 screening factors, their diagonal-block inverses and solve workspace
     const size_t panel_words = 2 * nf1 * static_cast<size_t>(ld) * kScsPanel;
     const size_t grad32 = 2 * nf1 * (3 * static_cast<size_t>(ld) + N);
-    const size_t scs32 = !fp64_path(prec)
-                             ? nf1 * mat32 + al(sizeof(float) * nf1 * nb * 4096) + al(sizeof(float) * 2 * nf1 * ld * 3) +
-                                   al(sizeof(uint32_t) * panel_words) + al(sizeof(float) * grad32)
+    const size_t scs32 = !fp64_path(prec) && !ctx->periodic   // cells screen in FP64 (Gamma point)
+                             ? nf1 * (mat / 2) + al(sizeof(float) * nf1 * nb * 4096) +
+                                   al(sizeof(float) * 2 * nf1 * ld * 3) + al(sizeof(uint32_t) * panel_words) +
+                                   al(sizeof(float) * grad32)
                              : 0;
     bytes += scs32;
     // A slab large enough for the new size is re-carved in place (systems of varying size in
@@ -421,9 +432,16 @@ int allocate(mbd_ctx *ctx) {
                 p += split_mat;
             }
     }
+    if (embed) {
+        double **em[5] = {&ctx->eM, &ctx->eV, &ctx->eW, &ctx->eVT, &ctx->eZ};
+        for (auto m : em) {
+            *m = reinterpret_cast<double *>(p);
+            p += emat;
+        }
+    }
     if (scs32) {
         ctx->sM = reinterpret_cast<float *>(p);
-        p += nf1 * mat32;
+        p += nf1 * (mat / 2);
         ctx->sdinv = reinterpret_cast<float *>(p);
         p += al(sizeof(float) * nf1 * nb * 4096);
         ctx->swork = reinterpret_cast<float *>(p);
@@ -608,13 +626,26 @@ struct MixMat {
     const void *op1(bool split) const { return split ? static_cast<const void *>(l) : static_cast<const void *>(f); }
 };
 
+// The matrix of one mixed-precision matrix function and where its results go: Q (FP64,
+// symmetric, ld x ld, valid n x n, decoupled padding), the FP64 workspaces V and W (ld^2
+// doubles each) and VT (ld^2 doubles), the FP64 output Zd ~ Q^{-1/2}, and (if tq is not NULL)
+// the traces of the first N diagonal 3x3 blocks of Q^{1/2}, second order in the error of Zd.
+struct MixProblem {
+    const double *Q;
+    long long ld;
+    int n;
+    double *V, *W, *VT, *Zd;
+    double *tq;
+};
+
 // Mixed-precision coupled Newton-Schulz (same scaled steps as the FP64 loop) on the
 // tensor cores, stopped at the precision floor, then the FP64 correction:
 // Zd = Z/sqrt(s) ~ Q^{-1/2}, V = Q Zd, W = Zd V, E = (3 Tr V - sum V o W)/4 - 3/2 sum w.
-int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, double ubound, double *energy_out,
-                        std::vector<Span> &spans, cudaEvent_t &e_corr) {
-    const long long ld = ctx->ld;
-    const int n = ctx->n, N = ctx->N, M = static_cast<int>(ld);
+// The FP32 and split-part buffers of the context hold the iteration (ld^2 elements each).
+int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, const MixProblem &pr, double sc, double lbound, double ubound,
+                        double *energy_out, std::vector<Span> &spans, cudaEvent_t &e_corr) {
+    const long long ld = pr.ld;
+    const int n = pr.n, N = ctx->N, M = static_cast<int>(ld);
     const int kind = ctx->opt.precision == MBD_PREC_TF32 ? 0 : (ctx->opt.precision == MBD_PREC_BF16X3 ? 1 : 2);
     const bool split = kind != 0;
     const double nd = static_cast<double>(n);
@@ -622,8 +653,12 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
     MixMat Y{ctx->fY, ctx->hY[0], ctx->hY[1]}, Z{ctx->fZ, ctx->hZ[0], ctx->hZ[1]};
     MixMat Y2{ctx->fY2, ctx->hY2[0], ctx->hY2[1]}, Z2{ctx->fZ2, ctx->hZ2[0], ctx->hZ2[1]};
     MixMat P{ctx->fP, ctx->hP[0], ctx->hP[1]}, PT{ctx->fPT, ctx->hPT[0], ctx->hPT[1]};
-    mixed_init(kind, ctx->dQ, ld, 1.0 / sc, Y.f, split ? Y.h : nullptr, Y.l, Z.f, Z.h, Z.l, s);
-    const int cstages = ctx->opt.tc_chunk_stages > 0 ? ctx->opt.tc_chunk_stages : 1;
+    mixed_init(kind, pr.Q, ld, 1.0 / sc, Y.f, split ? Y.h : nullptr, Y.l, Z.f, Z.h, Z.l, s);
+    // K stages per tensor-memory accumulation: the option, or the kind's default (BF16x3: 8,
+    // i.e. 512 products per FP32 sum in tensor memory; TF32 and TF32x3: 2, i.e. 64 products)
+    const int cstages = ctx->opt.tc_chunk_stages > 0 ? ctx->opt.tc_chunk_stages : (kind == 1 ? 8 : 2);
+    // the correction's TF32x3 products keep short accumulations whatever the iteration's kind
+    constexpr int kCorrectionChunk = 2;
     auto tc = [&](const TcOperands &op, TcArgs g, double flops) -> int {
         Span sp;
         sp.flops = flops;
@@ -713,12 +748,12 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
         // the full Zs feed the first product; offdiag(Zs) (reusing the Q parts) and Vs^T the
         // second.
         float *Qh = Y.f, *Ql = Y2.f, *Zs_h = P.f, *Zs_l = PT.f, *Zh = Qh, *Zl = Ql;
-        float *VTh = reinterpret_cast<float *>(ctx->dY2), *VTl = VTh + ld * ld;
-        double *V64 = ctx->dP, *W64 = ctx->dZ2;
+        float *VTh = reinterpret_cast<float *>(pr.VT), *VTl = VTh + ld * ld;
+        double *V64 = pr.V, *W64 = pr.W;
         const float *Zs = Z.f;
-        split_tf32_f64(ctx->dQ, ld, 1.0 / sc, 1, Qh, Ql, s);
+        split_tf32_f64(pr.Q, ld, 1.0 / sc, 1, Qh, Ql, s);
         split_tf32_f32(Zs, ld, 0, Zs_h, Zs_l, s);
-        diag_scale_rows_f64(ctx->dQ, Zs, ld, 1.0 / sc, V64, s);
+        diag_scale_rows_f64(pr.Q, Zs, ld, 1.0 / sc, V64, s);
         auto tc64 = [&](const TcOperands &op, const TcArgs &g) -> int {   // timed like the iteration's products
             Span sp;
             sp.flops = flops_full;
@@ -731,7 +766,7 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
         {   // Vs += offdiag(Q/s) Zs = NT(offdiag(Q/s), Zs) (Zs symmetric)
             TcOperands op{Qh, Ql, Zs_h, Zs_l, ld, ld};
             TcArgs g{M, M, M, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                     0, 0, ctx->dstatus, V64, cstages};
+                     0, 0, ctx->dstatus, V64, kCorrectionChunk};
             if (int rc = tc64(op, g)) return rc;
         }
         split_tf32_f64_t(V64, ld, 1.0, VTh, VTl, s);
@@ -740,16 +775,15 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
         {   // Ws += offdiag(Zs) Vs = NT(offdiag(Zs), Vs^T)
             TcOperands op{Zh, Zl, VTh, VTl, ld, ld};
             TcArgs g{M, M, M, 1.f, 0.f, nullptr, ld, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                     0, 0, ctx->dstatus, W64, cstages};
+                     0, 0, ctx->dstatus, W64, kCorrectionChunk};
             if (int rc = tc64(op, g)) return rc;
         }
-        energy_correction(ctx->dQ, 1.0 / sc, Zs, V64, W64, ld, n, std::sqrt(sc), ctx->dombar, N,
+        energy_correction(pr.Q, 1.0 / sc, Zs, V64, W64, ld, n, std::sqrt(sc), ctx->dombar, N,
                           ctx->dscal + 8 + 2 * 64, energy_out, ctx->dscal + 3, s);
-        // diagonal blocks of Q^{1/2}, second order in the error of Zs, for dE/d omega_bar
-        block_trace_sqrt(V64, W64, ld, N, std::sqrt(sc), ctx->dtq, s);
-        ctx->tq_valid = true;
+        if (pr.tq)   // diagonal blocks of Q^{1/2}, second order in the error of Zs, for dE/d omega_bar
+            block_trace_sqrt(V64, W64, ld, N, std::sqrt(sc), pr.tq, s);
     }
-    double *Zd = ctx->dZ;
+    double *Zd = pr.Zd;
     to_f64(Z.f, ld, 1.0 / std::sqrt(sc), Zd, s);   // Q^{-1/2} for the gradient
     double c2 = 0.0;
     MBD_CUDA(cudaMemcpyAsync(&c2, ctx->dscal + 3, sizeof(double), cudaMemcpyDeviceToHost, s), "correction");
@@ -759,6 +793,12 @@ int newton_schulz_mixed(mbd_ctx *ctx, cudaStream_t s, double sc, double lbound, 
     MBD_CUDA(cudaStreamSynchronize(s), "correction");
     if (st2 & ST_TC_TIMEOUT) return fail(ctx, MBD_ERR_CUDA, "correction", "tensor-core GEMM wait timed out");
     ctx->corr_resid = c2;
+    // The corrected energy is second order in the error of Zs: with Zs = (Q/s)^{-1/2} (I + F),
+    // Ws - I ~ 2F and the error of Tr Q^{1/2}/2 is about (3/4) Tr(Q^{1/2} F^2) <= (3/16) sqrt(s) r^2.
+    // The split kinds claim the 1e-6 Ha/atom bar; a Z too poor for it is reported, not used.
+    if (split && !(3.0 / 16.0 * std::sqrt(sc) * c2 * c2 / (n / 3) <= ctx->opt.mixed_max_error))
+        return fail(ctx, MBD_ERR_NOT_CONVERGED, "correction",
+                    "the tensor-core Q^{-1/2} is too inaccurate for the energy bar (mixed_max_error)");
     ctx->Zlast = Zd;
     ctx->zscale = 1.0;
     return MBD_OK;
@@ -773,7 +813,8 @@ void backward_periodic(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const do
     const double beta = ctx->opt.beta, a = ctx->opt.a;
     const PeriodicBufs pb = periodic_bufs(ctx);
     MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
-    periodic_mbd_grad(b, pb, beta, a, ctx->Zlast, ld, ctx->zscale, go, ctx->dgc, ctx->dgA, s);
+    periodic_mbd_grad(b, pb, beta, a, ctx->Zlast, ld, ctx->zscale, go, ctx->dgc, ctx->dgA, s,
+                      ctx->tq_valid ? ctx->dtq : nullptr);
     if (ctx->opt.scs_mode == MBD_SCS_NL) {   // MBD-NL: no screening to differentiate
         if (grad_params) nl_chain(b, go, grad_energy, grad_params, s);
         if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
@@ -805,6 +846,7 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
     ctx->have_screening = false;
     ctx->have_forward = false;
     ctx->have_lattice_grad = false;
+    ctx->tq_valid = false;
     ctx->ev_used = 0;
     ctx->prof = mbd_profile{};
     const long long launches0 = launch_count();
@@ -854,6 +896,66 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
     rc = read_status(ctx, s, "coupled_oscillator_matrix");
     if (rc) return rc;
     if (!(sc > 0.0) || !std::isfinite(sc)) return fail(ctx, MBD_ERR_INPUT, "newton_schulz", "invalid Q scale");
+    double *energy_out = out.energy ? out.energy : ctx->dscal;
+    std::vector<Span> tc_spans;
+    if (!fp64_path(ctx->opt.precision)) {
+        // ---- mixed modes: each Hermitian Q(q) as its real symmetric embedding [[Re, -Im],
+        // [Im, Re]] (the same spectrum, twice) through the finite mixed-precision matrix function:
+        // tensor-core iteration with its own scale and bounds, FP64 correction of the energy ----
+        cudaEvent_t e_corr = nullptr;
+        const long long lde = ctx->lde;
+        const int ne = 2 * n, lzs = std::min(kLanczosSteps, static_cast<int>(lde));
+        int it_max = 0;
+        double res_max = 0.0, corr_max = 0.0, sc_max = 0.0;
+        std::vector<double> lzk(2 * lzs);
+        for (int k = 0; k < nk; ++k) {
+            embed_hermitian(ctx->dQ, ld, n, k, ctx->eM, lde, s);
+            max_abs_rowsum(ctx->eM, lde, static_cast<int>(lde), ctx->dscal + 1, s);
+            double sk = 0.0;
+            MBD_CUDA(cudaMemcpyAsync(&sk, ctx->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s), "newton_schulz");
+            lanczos_coefficients_f32(ctx->eM, ctx->fY, lde, lzs, ctx->eV, ctx->dscal + 8, s);
+            MBD_CUDA(cudaMemcpyAsync(lzk.data(), ctx->dscal + 8, sizeof(double) * 2 * lzs, cudaMemcpyDeviceToHost, s),
+                     "newton_schulz");
+            MBD_CUDA(cudaStreamSynchronize(s), "newton_schulz");
+            if (!(sk > 0.0) || !std::isfinite(sk)) return fail(ctx, MBD_ERR_INPUT, "newton_schulz", "invalid Q scale");
+            double lo = 0.0, hi = sk;
+            {
+                std::vector<double> da, db;
+                for (int j = 0; j < lzs; ++j) {
+                    da.push_back(lzk[2 * j]);
+                    if (j + 1 < lzs) db.push_back(lzk[2 * j + 1]);
+                    if (!(lzk[2 * j + 1] > 1e-14 * sk)) break;
+                }
+                db.resize(da.empty() ? 0 : da.size() - 1);
+                if (!da.empty()) tridiag_extremes(da, db, lo, hi);
+            }
+            double ub = 1.0;
+            if (std::isfinite(hi) && hi > 0.0 && 1.05 * hi < sk) {
+                sk = 1.05 * hi;
+                ub = 1.05;
+            }
+            double lb = ns::lower_estimate(lo, sk);   // an estimate (ns_schedule.h)
+            // Re Tr (Q(q_k)^{1/2})_ii: the first N diagonal blocks of M_k^{1/2}, into row k of dlzw
+            const MixProblem pr{ctx->eM, lde, ne, ctx->eV, ctx->eW, ctx->eVT, ctx->eZ,
+                                ctx->dlzw + static_cast<long long>(k) * N};
+            const int rk = newton_schulz_mixed(ctx, s, pr, sk, lb, ub, ctx->dcoef + k, tc_spans, e_corr);
+            if (rk) return rk;
+            extract_hermitian(ctx->eZ, lde, n, ctx->dZ, ld, k, s);
+            it_max = std::max(it_max, ctx->ns_iter);
+            res_max = std::max(res_max, ctx->ns_resid);
+            corr_max = std::max(corr_max, ctx->corr_resid);
+            sc_max = std::max(sc_max, sk);
+        }
+        ctx->ns_iter = it_max;
+        ctx->ns_resid = res_max;
+        ctx->corr_resid = corr_max;
+        ctx->ns_scale = sc_max;
+        periodic_mixed_energy(ctx->dcoef, nk, ctx->dombar, N, energy_out, s);
+        mean_rows(ctx->dlzw, nk, N, ctx->dtq, s);   // (1/nk) sum_q Re Tr (Q(q)^{1/2})_ii
+        ctx->tq_valid = true;
+        ctx->Zlast = ctx->dZ;
+        ctx->zscale = 1.0;
+    } else {
     const int lz_steps = std::min(kLanczosSteps, static_cast<int>(2 * ld));
     clanczos_coefficients(ctx->dQ, ld, nk, lz_steps, ctx->dlzw, ctx->dcoef, s);
     std::vector<double> lz(static_cast<size_t>(nk) * 2 * lz_steps);
@@ -881,7 +983,9 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
         ubound = 1.05;
     }
     ctx->ns_scale = sc;
-    double lbound = ns::lower_bound(th_min, sc, 0.5);   // the smallest over all Bloch vectors
+    // the smallest over all Bloch vectors; an estimate, which may lie above the true bound
+    // (that costs steps only, ns_schedule.h)
+    double lbound = ns::lower_estimate(th_min, sc, 0.5);
     const double ss = std::sqrt(sc);
     // ---- batched complex coupled Newton-Schulz (same scaled steps as the finite path) ----
     double *Y = ctx->dQ, *Z = ctx->dZ, *P = ctx->dP, *Y2 = ctx->dY2, *Z2 = ctx->dZ2;
@@ -924,10 +1028,10 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
     ctx->ns_iter = it;
     ctx->ns_resid = resid;
     if (!converged) return fail(ctx, MBD_ERR_NOT_CONVERGED, "newton_schulz", "iteration cap reached");
-    double *energy_out = out.energy ? out.energy : ctx->dscal;
     energy_trace_periodic(Y, ld, n, nk, ctx->dombar, N, ss, energy_out, s);
     ctx->Zlast = Z;
     ctx->zscale = 1.0 / ss;
+    }
     mark(ctx, s, e_ns);
     nv.next("mbd gradient");
     if (want_grad) backward_periodic(ctx, s, b, nullptr, out.grad_coords, out.grad_params);
@@ -944,6 +1048,11 @@ int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &
         for (const Span &sp : gemms) {
             p.gemm_ms += span_ms(sp.a, sp.b);
             p.gemm_flops += sp.flops;
+        }
+        p.tc_launches = static_cast<int>(tc_spans.size());
+        for (const Span &sp : tc_spans) {
+            p.tc_ms += span_ms(sp.a, sp.b);
+            p.tc_flops += sp.flops;
         }
         p.screening_ms = span_ms(e_start, e_scs);
         p.screening_flops = ctx->opt.scs_mode == MBD_SCS_NL ? 0.0 : nf1 * nd * nd * nd / 3.0;
@@ -1077,7 +1186,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         ubound = 1.05;
     }
     ctx->ns_scale = sc;
-    double lbound = ns::lower_bound(th_min, sc);   // lower bound on sqrt(eig(Z Y))
+    double lbound = ns::lower_estimate(th_min, sc);   // estimated lower bound on sqrt(eig(Z Y))
     const double ss = std::sqrt(sc);
     double *energy_out = out.energy ? out.energy : ctx->dscal;
     if (fp64_path(ctx->opt.precision)) {
@@ -1147,8 +1256,10 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         ctx->Zlast = Z;
         ctx->zscale = 1.0 / ss;
     } else {
-        rc = newton_schulz_mixed(ctx, s, sc, lbound, ubound, energy_out, tc_spans, e_corr);
+        const MixProblem pr{ctx->dQ, ld, n, ctx->dP, ctx->dZ2, ctx->dY2, ctx->dZ, ctx->dtq};
+        rc = newton_schulz_mixed(ctx, s, pr, sc, lbound, ubound, energy_out, tc_spans, e_corr);
         if (rc) return rc;
+        ctx->tq_valid = true;
     }
     mark(ctx, s, e_ns);
     nv.next("mbd gradient");
@@ -1242,12 +1353,13 @@ int mbd_default_options(mbd_options *opt) {
     opt->precision = MBD_PREC_FP64;
     opt->ns_tol = 1e-8;
     opt->ns_max_iter = 100;
-    opt->tc_chunk_stages = 2;
+    opt->tc_chunk_stages = 0;
     opt->ewald_gamma = 0.0;
     opt->real_cutoff = 0.0;
     opt->recip_cutoff = 0.0;
     opt->scs_mode = MBD_SCS_PLAIN;
     opt->learned_max_error = 1e-6;
+    opt->mixed_max_error = 1e-7;
     return MBD_OK;
 }
 
@@ -1259,7 +1371,7 @@ int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt) {
     if (o.n_freq < 1 || o.n_freq + 1 > kMaxFreq || !(o.beta > 0) || !(o.a > 0) || o.ns_max_iter < 1 ||
         !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_FP64_SPLIT || o.tc_chunk_stages < 0 ||
         (o.scs_mode != MBD_SCS_PLAIN && o.scs_mode != MBD_SCS_LEARNED && o.scs_mode != MBD_SCS_NL) ||
-        !(o.learned_max_error > 0))
+        !(o.learned_max_error > 0) || !(o.mixed_max_error > 0))
         return MBD_ERR_INPUT;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev)
@@ -1307,8 +1419,9 @@ int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const doub
     const bool periodic = lattice != nullptr;
     PeriodicSetup ps;
     if (periodic) {
-        if (ctx->opt.precision != MBD_PREC_FP64)
-            return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_set_geometry", "periodic systems run in FP64 only");
+        if (ctx->opt.precision == MBD_PREC_FP64_SPLIT)
+            return fail(ctx, MBD_ERR_UNSUPPORTED, "mbd_set_geometry",
+                        "periodic systems run in FP64 or in the tensor-core modes, not with split FP64 products");
         const int rc = periodic_setup(ctx->opt, lattice, k_grid, ps);
         if (rc) return fail(ctx, rc, "mbd_set_geometry", ps.msg);
     }
@@ -1318,6 +1431,7 @@ int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const doub
     ctx->N = n_atoms;
     ctx->n = 3 * n_atoms;
     ctx->ld = (ctx->n + 127) / 128 * 128;   // 128: the tensor-core tile (also a multiple of 64)
+    ctx->lde = (2LL * ctx->n + 127) / 128 * 128;
     ctx->nb = static_cast<int>(ctx->ld / kTile);
     ctx->hR.assign(coords, coords + 3 * n_atoms);
     ctx->periodic = periodic;
@@ -1695,6 +1809,12 @@ int mbdk_gemm_tc(void *stream, int kind, int mode, int M, int N, int K, float al
     TcArgs g{M, N, K, alpha, beta, D, ldc, C, C_hi, C_lo, CT, nullptr, nullptr, nullptr, 0, mode, err, nullptr,
              chunk_stages};
     const cudaError_t e = tc_gemm(kind, op, g, static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorInvalidValue) return MBD_ERR_INPUT;
+    return e == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
+}
+
+int mbdk_tc_wait_check(void *stream, long long spin_cycles, int *err) {
+    const cudaError_t e = tc_wait_probe(spin_cycles, err, static_cast<cudaStream_t>(stream));
     if (e == cudaErrorInvalidValue) return MBD_ERR_INPUT;
     return e == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
 }

@@ -31,7 +31,8 @@ std::mutex g_scratch_mutex;
 
 // Device address of g_chol_scratch on the current device.  In host code the array's
 // name is only a host-side stand-in, so the address is looked up once per device with
-// that device current, and cached.
+// that device current, and cached for the life of the process (a cudaDeviceReset of the
+// device invalidates it; the header asks callers to reload the library after one).
 int scratch_address(double **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MBD_ERR_CUDA;

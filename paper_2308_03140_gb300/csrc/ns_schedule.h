@@ -27,10 +27,11 @@ inline Coeffs step(double &l, double &u, bool last) {
     return c;
 }
 
-// Lower bound on sqrt(eig(Y0)), Y0 = Q/s, from the smallest Ritz value of a 48-step Lanczos
-// run on Q.  That value converges slowly: it is 3-6 times the smallest eigenvalue of Q at
-// 500-2000 atoms, and on those spectra a quarter of it takes one step fewer than a half.
-inline double lower_bound(double ritz_min, double s, double fraction = 0.25) {
+// Estimated lower bound on sqrt(eig(Y0)), Y0 = Q/s, from the smallest Ritz value of a 48-step
+// Lanczos run on Q.  That value converges slowly: it is 3-6 times the smallest eigenvalue of Q
+// at 500-2000 atoms, so a fraction of it may still lie above the true bound (which costs steps
+// only, see above); on those spectra a quarter of it takes one step fewer than a half.
+inline double lower_estimate(double ritz_min, double s, double fraction = 0.25) {
     return std::sqrt(std::max(fraction * ritz_min / s, 1e-12));
 }
 

@@ -25,12 +25,17 @@ constexpr int kSliceBits = 6;
 constexpr int kSlices = 9;          // 54 bits of each operand
 constexpr int kSplitChunk = 1024;   // K per tensor-core product: 2^(2 kSliceBits) 1024 = 2^22
 
-// Exponent e with |x| 2^-e < 1 for every |x| <= amax (0 for amax == 0).
+// Exponent e with |x| 2^-e < 1 for every |x| <= amax (0 for amax == 0), at least kMinExponent:
+// the last slice's unit 2^{e - b kSlices} then stays an FP32 normal number (>= 2^-126), which
+// the tensor cores do not flush.  A row whose largest element lies below 2^kMinExponent is
+// sliced at that exponent: its slices are still exact, and it keeps an absolute accuracy of
+// 2^-126 instead of a relative one.
+constexpr int kMinExponent = -126 + kSliceBits * kSlices;   // -72
 __host__ __device__ inline int scale_exponent(double amax) {
     if (!(amax > 0.0)) return 0;
     int e;
     frexp(amax, &e);
-    return e;
+    return e < kMinExponent ? kMinExponent : e;
 }
 
 // The slices of x for the row exponent e: out[p] = a_p 2^{e - b (p+1)} (FP32, exact).

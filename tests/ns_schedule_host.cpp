@@ -23,7 +23,7 @@ extern "C" int ns_scalar_run(const double *lam, int n, double ritz_min, double f
     const double s = 1.05 * lmax;
     std::vector<double> x(lam, lam + n);
     for (double &v : x) v /= s;
-    double l = ns::lower_bound(ritz_min, s, fraction), u = 1.05, prev = 1e300;
+    double l = ns::lower_estimate(ritz_min, s, fraction), u = 1.05, prev = 1e300;
     int it = 0;
     for (; it < 200; ++it) {
         bool last = false;

@@ -102,7 +102,7 @@ def test_periodic_input_errors():
         with pytest.raises(binding.MBDError) as e:
             m.set_geometry(R, A, (0, 2, 2))
         assert e.value.code == 1
-    with binding.MBD(0, precision=binding.MBD_PREC_TF32X3) as m:
+    with binding.MBD(0, precision=binding.MBD_PREC_FP64_SPLIT) as m:
         with pytest.raises(binding.MBDError) as e:
             m.set_geometry(R, A, (2, 2, 2))
         assert e.value.code == 8
@@ -120,3 +120,56 @@ def test_periodic_lattice_gradient_state():
             m.lattice_gradient()
         m.evaluate(True)
         assert np.all(np.isfinite(m.lattice_gradient()))
+
+
+# Mixed modes on a cell: each Hermitian Q(q) as its real symmetric embedding through the finite
+# tensor-core matrix function with the FP64 correction.  Bounds a few times the errors measured
+# at the 256-atom cell (printed by the test): energy per atom, and the coordinate, lattice and
+# parameter gradients relative to their largest components (the gradients take the
+# tensor-core Q(q)^{-1/2} at first order).
+MIXED_CELL = {binding.MBD_PREC_TF32X3: (5e-8, 5e-4), binding.MBD_PREC_BF16X3: (1e-7, 5e-3)}
+
+
+def _mixed_vs(R, A, p, grid, gamma, rc, kc, precision, E_ref, gR_ref, gA_ref, gp_ref):
+    with binding.MBD(0, precision=precision, ewald_gamma=gamma, real_cutoff=rc, recip_cutoff=kc) as m:
+        m.set_geometry(R, A, grid)
+        m.set_free_atom_params(*p)
+        E, gR, gp, al = m.evaluate(True)
+        gA = m.lattice_gradient()
+        st = m.stats()
+    N = R.shape[0]
+    de = abs(E - E_ref) / N
+    fr = np.abs(gR - gR_ref).max() / np.abs(gR_ref).max()
+    lr = np.abs(gA - gA_ref).max() / np.abs(gA_ref).max()
+    pr = max(np.abs(gp[k] - gp_ref[k]).max() / np.abs(gp_ref[k]).max() for k in range(4))
+    print(f"cell N {N} precision {precision}: |dE|/N {de:.3e}, force {fr:.3e}, lattice {lr:.3e}, params {pr:.3e}, "
+          f"iterations {st['ns_iterations']}")
+    e_b, g_b = MIXED_CELL[precision]
+    assert de <= e_b, (E, E_ref, st)
+    assert fr <= g_b and lr <= g_b and pr <= g_b, (fr, lr, pr)
+    return st
+
+
+@pytest.mark.parametrize("precision", [binding.MBD_PREC_TF32X3, binding.MBD_PREC_BF16X3])
+@pytest.mark.parametrize("N,edge,grid,seed", [(8, 10.0, (2, 2, 2), 12), (45, 15.0, (2, 1, 2), 14)])
+def test_periodic_mixed_modes_against_the_oracle(N, edge, grid, seed, precision):
+    R, A, p = small_cell(N, edge, seed)
+    gamma, rc, kc = 0.3, 6.5 / 0.3, 11 * 0.3
+    kap = o.monkhorst_pack(grid)
+    E_ref = o.periodic_rsscs_energy(R, A, kap, *p, gamma, rc, kc)
+    _, gR_ref, gA_ref, gp_ref = o.periodic_rsscs_gradient(R, A, kap, *p, gamma, rc, kc)
+    _mixed_vs(R, A, p, grid, gamma, rc, kc, precision, E_ref, gR_ref, gA_ref, gp_ref)
+
+
+@pytest.mark.parametrize("precision", [binding.MBD_PREC_TF32X3, binding.MBD_PREC_BF16X3])
+def test_periodic_mixed_modes_at_the_256_atom_cell(precision):
+    # against the oracle-checked FP64 path on the same cell (64 Bloch vectors)
+    s = syn.workload("cell256")
+    g, rc, kc = 0.2, 30.0, 2.0
+    with binding.MBD(0, ewald_gamma=g, real_cutoff=rc, recip_cutoff=kc) as m:
+        m.set_geometry(s.coords, s.lattice, s.k_grid)
+        m.set_free_atom_params(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
+        E64, gR64, gp64, _ = m.evaluate(True)
+        gA64 = m.lattice_gradient()
+    _mixed_vs(s.coords, s.lattice, (s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio), s.k_grid, g, rc, kc, precision,
+              E64, gR64, gA64, gp64)

@@ -96,3 +96,20 @@ def test_emulated_split_product_is_fp64_accurate(host):
     fp64 = np.abs(A @ B - exact) / scale                  # an FP64 GEMM's own error, in units of |A||B|
     err = np.abs(Cacc - exact) / scale
     assert err.max() <= 2 * fp64.max() + 2.0 ** -52 and err.max() <= 8 * 2.0 ** -53
+
+
+def test_tiny_rows_keep_normal_slices(host):
+    # a row whose largest element lies below 2^-72 is sliced at exponent -72, so that the last
+    # slice's unit 2^-126 is still an FP32 normal (the tensor cores flush subnormals): every
+    # non-zero slice value is normal, the slices are exact, and the row is rebuilt to 2^-126
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(4, 50))
+    A[1] *= 1e-25
+    A[2] *= 1e-35
+    e, S = slices(host, A)
+    assert e[1] == -72 and e[2] == -72
+    nz = S[S != 0].astype(np.float64)
+    assert np.all(np.abs(nz) >= 2.0 ** -126)
+    recon = S.astype(np.float64).sum(0)
+    assert np.all(np.abs(recon[1:3] - A[1:3]) <= 2.0 ** -126)
+    assert np.all(np.abs(recon[[0, 3]] - A[[0, 3]]) <= 2.0 ** -53 * np.abs(A[[0, 3]]).max(1, keepdims=True))
