@@ -40,10 +40,9 @@ constexpr int kLanczosSteps = 48; // Lanczos steps of the spectrum estimate of Q
 // exact successor bound 0.875 r^2 lies below this is the last useful one.  The coarser kinds
 // (TF32, BF16x3) reach their floors above it and stop by the halving test alone.
 constexpr double kMixedFloor = 1e-7;
-// Periodic Newton-Schulz: take Y' and Z' as Hermitian products (upper tiles only, real part
-// mirrored, imaginary part mirrored with a sign change), a third fewer flops per step.  Off
-// until it has been measured against the full products on a GPU.
-constexpr bool kHermitianNs = false;
+// Periodic Newton-Schulz (FP64): Y' and Z' as Hermitian products (upper tiles only, real part
+// mirrored, imaginary part mirrored with a sign change), a third fewer flops per step.
+constexpr bool kHermitianNs = true;
 constexpr int kLF = MBD_LEARNED_FEATURES;   // inputs of the learned screening model
 // The FP64 path (screening, bounds, Newton-Schulz, gradients in FP64), with its Newton-Schulz
 // products on the DMMA pipe (MBD_PREC_FP64) or FP64-accurate on the TF32 tensor cores.
