@@ -86,9 +86,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=("finite2000", "cell256", "finite8000", "batch4096"), default=WORKLOAD,
-                    help="finite2000: the headline cluster; cell256: the periodic cell (FP64 only); "
+                    help="finite2000: the 2000-atom cluster; cell256: the periodic cell (64 Bloch vectors); "
                          "finite8000: the large cluster; batch4096: the varlen cluster batch with the learned "
                          "screening model beside plain screening")
+    ap.add_argument("--order", type=int, default=6016, help="--kernel tc_gemm_sym: matrix order (multiple of 128)")
     ap.add_argument("--batch-clusters", type=int, default=64,
                     help="batch4096: clusters of the batch evaluated per step (the first ones of the recipe)")
     ap.add_argument("--precision", choices=("bf16x3", "tf32x3", "tf32", "fp64", "fp64split"), default="bf16x3",
@@ -99,22 +100,26 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed steps of the FP64 comparison arm (0: skip; no warm-up at 4000 atoms or more)")
     ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement (at most --steps)")
-    ap.add_argument("--extra-workload", default="finite2000",
-                    help="a second finite workload measured the same way after the first ('' for none)")
-    ap.add_argument("--extra-fp64-steps", type=int, default=2, help="timed FP64 steps of the second workload")
-    ap.add_argument("--cpu-sample-atoms", type=int, default=250,
+    ap.add_argument("--extra-workload", default="finite2000,cell256,batch4096",
+                    help="comma-separated further workloads measured after the first ('' for none): finite2000 "
+                         "and cell256 in the timed arm's and --also arithmetic with their own FP64 arm; batch4096 "
+                         "= --batch-clusters clusters of the varlen batch, plain against learned screening")
+    ap.add_argument("--extra-steps", type=int, default=5, help="timed steps of each further workload (1 warm-up)")
+    ap.add_argument("--extra-fp64-steps", type=int, default=1, help="timed FP64 steps of each further workload")
+    ap.add_argument("--cpu-sample-atoms", type=int, default=320,
                     help="atoms of the bounded oracle sample (same recipe, extrapolated by n^3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--method", choices=("rsscs", "nl"), default="rsscs",
                     help="rsscs: MBD@rsSCS (the headline); nl: MBD-NL (Sec. 2.7: no screening, oscillators "
                          "from the free-atom reference and density-functional ratios drawn by "
                          "synthetic.nl_ratios(N, seed=7000))")
-    ap.add_argument("--kernel", choices=("tc_gemm_sym6016", "log_energy_finite2000", "ts_finite2000", "ts_cell256",
+    ap.add_argument("--kernel", choices=("tc_gemm_sym", "tc_gemm_sym6016", "log_energy_finite2000", "ts_finite2000", "ts_cell256",
                                          "gemm_f64_split6016"),
                     default=None,
-                    help="time one kernel or route alone instead of the workload: tc_gemm_sym6016 = the "
-                         "symmetric TF32x3 Newton-Schulz product of order 6016 (k_tc_gemm mode 2, chunks of 2 "
-                         "stages; a small case for profilers, about 0.9 GB on the device); "
+                    help="time one kernel or route alone instead of the workload: tc_gemm_sym = the "
+                         "symmetric Newton-Schulz product in the --precision split kind (bf16x3 or tf32x3) at order "
+                         "--order (k_tc_gemm mode 2, the library chunk lengths; at 6016 a small case for profilers, about "
+                         "0.9 GB on the device; tc_gemm_sym6016 is the same at 6016); "
                          "log_energy_finite2000 = the log-formula energy route (mbd_log_energy, orders 2) of the "
                          "2000-atom cluster after a TF32x3 evaluation; ts_finite2000 = the TS pairwise energy "
                          "and gradients (mbd_ts_energy) of the 2000-atom cluster; ts_cell256 = the same per cell of "
@@ -122,6 +127,10 @@ def parse():
                          "gemm_f64_split6016 = the FP64-accurate split GEMM against the FP64 GEMM at order 6016")
     args = ap.parse_args()
     args.also = [x for x in args.also.split(",") if x]
+    args.extra_workload = [x for x in args.extra_workload.split(",") if x]
+    for x in args.extra_workload:
+        if x not in ("finite2000", "cell256", "finite8000", "batch4096"):
+            ap.error(f"--extra-workload: unknown workload {x}")
     for x in args.also:
         if x not in ("bf16x3", "tf32x3", "tf32", "fp64split"):
             ap.error(f"--also: unknown arithmetic {x}")
@@ -369,7 +378,8 @@ def time_arm(binding, dev, stream, sysm, p3, p4, precision, scs_mode, steps, war
         ms = max_over_ranks(ms)
     m.set_profiling(False)
     out = {"ms": ms, "steps": steps, "warmup": warmup, "energy": energy.item(), "gR": gR.cpu().numpy().copy(),
-           "gp": gp.cpu().numpy().copy(), "profs": profs, "stats": m.stats(), "clocks": clk, "ctx": m}
+           "gp": gp.cpu().numpy().copy(), "profs": profs, "stats": m.stats(), "clocks": clk, "ctx": m,
+           "gA": m.lattice_gradient() if periodic else None}
     return out
 
 
@@ -382,7 +392,9 @@ def errors_vs(arm, ref, N):
             "max_force_ha_bohr": float(np.abs(ref["gR"]).max()),
             "max_force_err_rel": float(np.abs(arm["gR"] - ref["gR"]).max() / np.abs(ref["gR"]).max()),
             "max_param_grad_err": float(np.abs(arm["gp"] - ref["gp"]).max()),
-            "max_param_grad_err_rel": [float(np.abs(arm["gp"][k] - ref["gp"][k]).max() / gpr[k]) for k in range(4)]}
+            "max_param_grad_err_rel": [float(np.abs(arm["gp"][k] - ref["gp"][k]).max() / gpr[k]) for k in range(4)],
+            **({"max_lattice_grad_err_rel": float(np.abs(arm["gA"] - ref["gA"]).max() / np.abs(ref["gA"]).max())}
+               if arm.get("gA") is not None and ref.get("gA") is not None else {})}
 
 
 def roofline_of(binding, args_precision, precision, profs, ms, steps, workload):
@@ -459,8 +471,8 @@ def run_ours(args):
 
     sysm = syn.workload(args.workload)
     periodic = sysm.lattice is not None
-    if periodic and args.precision != "fp64":
-        args.precision = "fp64"   # periodic systems run in FP64
+    if periodic and args.precision == "fp64split":
+        args.precision = "fp64"   # cells have no split-FP64 path
     N = sysm.n_atoms
     nl = args.method == "nl"
     # per-atom parameter slots 3 and 4: R_vdW,ref and the volume ratio, or the MBD-NL ratios
@@ -527,7 +539,7 @@ def run_ours(args):
     # which every arm's error is stated
     arms = {}
     for other in args.also:
-        if other == args.precision or periodic:
+        if other == args.precision or (periodic and other == "fp64split"):
             continue
         a = time_arm(binding, dev, stream, sysm, p3, p4, precision_code(binding, other), scs_mode,
                      max(1, args.other_steps), 1, barrier, max_over_ranks)
@@ -557,24 +569,34 @@ def run_ours(args):
                                     "roofline": roofline_of(binding, k, precision_code(binding, k), a["profs"],
                                                             a["ms"], a["steps"], args.workload)}
                                 for k, a in arms.items()}
-    # a second finite workload (the 2000-atom cluster) measured the same way
-    xw = args.extra_workload
-    if xw and xw != args.workload and not periodic:
+    # further workloads (the 2000-atom cluster, the 256-atom cell), each measured the same way
+    # with fewer steps, and the varlen cluster batch with the learned screening beside plain
+    for xw in args.extra_workload:
+        if xw == args.workload:
+            continue
+        if xw == "batch4096":
+            if not nl:
+                line[xw] = batch_section(binding, local, args, args.precision)
+            continue
         xs = syn.workload(xw)
+        xper = xs.lattice is not None
         xp3, xp4 = syn.nl_ratios(xs.n_atoms, NL_SEED) if nl else (xs.rvdw_ref, xs.ratio)
-        sec = {"config": workload_config(xw, args.method, xs.n_atoms, world)}
+        sec = {"config": workload_config(xw, args.method, xs.n_atoms, world, xper, xs)}
         xarms = {}
+        xk = max(1, min(args.steps, args.extra_steps))
         for name in [args.precision] + [a for a in args.also if a != args.precision]:
-            a = time_arm(binding, dev, stream, xs, xp3, xp4, precision_code(binding, name), scs_mode, args.steps,
-                         args.warmup, barrier, max_over_ranks)
+            if xper and name == "fp64split":
+                continue
+            a = time_arm(binding, dev, stream, xs, xp3, xp4, precision_code(binding, name), scs_mode, xk, 1,
+                         barrier, max_over_ranks)
             a["ctx"].close()
             xarms[name] = a
-            sec[name] = {"value": world * args.steps / (a["ms"] / 1e3), "unit": UNIT,
-                         "ms_per_step": a["ms"] / args.steps, "steps": args.steps, "warmup": args.warmup,
+            sec[name] = {"value": world * xk / (a["ms"] / 1e3), "unit": UNIT,
+                         "ms_per_step": a["ms"] / xk, "steps": xk, "warmup": 1,
                          "energy_ha": a["energy"], "ns_iterations": a["stats"]["ns_iterations"],
                          "stage_ms": stage_means(a["profs"]),
                          "roofline": roofline_of(binding, name, precision_code(binding, name), a["profs"], a["ms"],
-                                                 args.steps, xw)}
+                                                 xk, xw)}
         if args.extra_fp64_steps > 0:
             f = time_arm(binding, dev, stream, xs, xp3, xp4, binding.MBD_PREC_FP64, scs_mode, args.extra_fp64_steps,
                          1, barrier, max_over_ranks)
@@ -600,27 +622,19 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
-    """Varlen cluster batch: energy + coordinate gradients per cluster through the library API,
-    plain screening against the learned model (with its fallback at 1e-6 Ha/atom, and without
-    fallback), on the same clusters."""
+def batch_section(binding, local, args, precision_name):
+    """The first --batch-clusters clusters of the varlen batch (sizes U{50..500}): energy +
+    coordinate gradients per cluster through the library API, plain screening against the learned
+    model with its fallback at 1e-6 Ha/atom and without fallback, on the same clusters; one pass
+    per arm after one warm-up pass.  Device time from the library's profile, host time around
+    each pass (inputs uploaded and outputs read back for every cluster)."""
     import numpy as np
     import torch
-    from paper_2308_03140_gb300 import binding, build
     from paper_2308_03140_gb300 import synthetic as syn
-    rank, world, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    torch.cuda.set_device(local)
-    build.build()
-    binding.load()
     K = args.batch_clusters
     systems = syn.cluster_batch(K)
     model = np.load(os.path.join(ROOT, "paper_2308_03140_gb300", "learned_scs_model.npz"))
-    precision = {"fp64": binding.MBD_PREC_FP64, "tf32": binding.MBD_PREC_TF32,
-                 "bf16x3": binding.MBD_PREC_BF16X3, "tf32x3": binding.MBD_PREC_TF32X3,
-                 "fp64split": binding.MBD_PREC_FP64_SPLIT}[args.precision]
+    precision = precision_code(binding, precision_name)
     arms = {"plain": dict(), "learned": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e-6),
             "learned_no_fallback": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e300)}
     ctxs = {}
@@ -628,14 +642,14 @@ def run_batch(args):
         m = binding.MBD(local, precision=precision, **opt)
         if name != "plain":
             m.set_scs_model(model["params16"], model["mean"], model["std"])
+        m.set_profiling(True)
         ctxs[name] = m
-
     launches = {}
 
     def one_pass(name, record=None):
         m = ctxs[name]
         dev_ms, fb = 0.0, 0
-        for i, s in enumerate(systems):
+        for s in systems:
             m.set_geometry(s.coords)
             m.set_free_atom_params(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
             E, gR, _, _ = m.evaluate(True, param_gradients=(name == "plain"))
@@ -648,65 +662,62 @@ def run_batch(args):
                 record.append((E, gR))
         return dev_ms, fb
 
-    for m in ctxs.values():
-        m.set_profiling(True)
-    results = {}
-    ref = []
-    one_pass("plain", ref)                       # reference energies and forces (also a warm-up)
+    results, ref = {}, []
+    one_pass("plain", ref)   # reference energies and forces (also the plain arm's warm-up)
     for name in arms:
-        for _ in range(args.warmup):
-            one_pass(name)
+        if name != "plain":
+            one_pass(name)   # warm-up
         torch.cuda.synchronize()
-        clocks = ClockSampler(local) if name == "learned" else None
-        if clocks:
-            clocks.start()
         launches[name] = 0
+        rec = []
         t0 = time.perf_counter()
-        dev_ms, fb, rec = 0.0, 0, []
-        for _ in range(args.steps):
-            d, f = one_pass(name, rec if not rec else None)
-            dev_ms += d
-            fb += f
+        dev_ms, fb = one_pass(name, rec)
         wall = time.perf_counter() - t0
-        results[name] = {"solves_per_s_device": K * args.steps / (dev_ms / 1e3), "solves_per_s_e2e": K * args.steps / wall,
-                         "fallback_fraction": fb / (K * args.steps) if name != "plain" else None,
-                         "clocks": clocks.stop() if clocks else None}
+        results[name] = {"solves_per_s_device": K / (dev_ms / 1e3), "solves_per_s_e2e": K / wall,
+                         "fallback_fraction": fb / K if name != "plain" else None, "gpu_launches": launches[name]}
         if name != "plain":
             dE = [abs(e - er) / s.n_atoms for (e, _), (er, _), s in zip(rec, ref, systems)]
             dF = [float(np.abs(g - gr).max()) for (_, g), (_, gr) in zip(rec, ref)]
-            results[name].update({"mean_abs_de_per_atom_ha": float(np.mean(dE)), "max_abs_de_per_atom_ha": float(np.max(dE)),
+            results[name].update({"mean_abs_de_per_atom_ha": float(np.mean(dE)),
+                                  "max_abs_de_per_atom_ha": float(np.max(dE)),
+                                  "fraction_within_1e-6": float(np.mean(np.array(dE) <= 1e-6)),
                                   "max_force_err_ha_bohr": float(np.max(dF))})
     for m in ctxs.values():
         m.close()
-    n_mean = float(np.mean([s.n_atoms for s in systems]))
+    return {"config": {"workload": "batch4096", "clusters": K, "mean_atoms": float(np.mean([s.n_atoms for s in systems])),
+                       "sizes": "U{50..500}, the first clusters of the 4096-cluster recipe", "precision": precision_name,
+                       "learned_model": "paper_2308_03140_gb300/learned_scs_model.npz (4 members, trained on 20000 "
+                                        "perturbed plain-screening solves)"},
+            "arms": results}
+
+
+def run_batch(args):
+    """The varlen cluster batch alone (see batch_section), as one JSON line whose value is the
+    learned arm's device solves/s."""
+    import numpy as np
+    import torch
+    from paper_2308_03140_gb300 import binding, build
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    build.build()
+    binding.load()
+    clocks = ClockSampler(local)
+    clocks.start()
+    sec = batch_section(binding, local, args, args.precision)
+    clk = clocks.stop()
+    res = sec["arms"]
+    K = args.batch_clusters
     line = {
-        "metric": METRIC, "value": results["learned"]["solves_per_s_device"], "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * K / results["learned"]["solves_per_s_device"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": f"{args.precision}+f32+f16", "data": "synthetic",
-        "config": {"workload": "batch4096", "clusters_per_step": K, "mean_atoms": n_mean,
-                   "sizes": "U{50..500}, the first clusters of the 4096-cluster recipe", "precision": args.precision,
-                   "learned_model": "paper_2308_03140_gb300/learned_scs_model.npz (4 members, trained on 20000 "
-                                    "perturbed plain-screening solves)",
-                   "l2": "per-cluster working sets below L2; timed as whole evaluations per cluster"},
-        "arms": results,
-        "e2e": {"value": results["learned"]["solves_per_s_e2e"], "unit": UNIT,
-                "h2d_bytes_per_step": int(8 * sum(7 * s.n_atoms for s in systems)),
-                "d2h_bytes_per_step": int(8 * sum(1 + 3 * s.n_atoms + s.n_atoms for s in systems))},
-        "clocks": results["learned"]["clocks"],
-        "gpu_launches": launches.get("learned", 0),
+        "metric": METRIC, "value": res["learned"]["solves_per_s_device"], "unit": UNIT, "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * K / res["learned"]["solves_per_s_device"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"{args.precision}+f32+f16",
+        "data": "synthetic", "config": sec["config"], "arms": res,
+        "e2e": {"value": res["learned"]["solves_per_s_e2e"], "unit": UNIT},
+        "clocks": clk, "gpu_launches": res["learned"]["gpu_launches"],
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        small = next(s for s in systems if s.n_atoms <= 250)
-        import oracle as o
-        t0 = time.perf_counter()
-        o.mbd_rsscs_gradient(*o.system_args(small), mode="adjoint")
-        dt = time.perf_counter() - t0
-        scale = (n_mean / small.n_atoms) ** 3
-        line["cpu_baseline"] = {"value": 1.0 / (dt * scale), "unit": UNIT,
-                                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
-                                "kind": "oracle", "sample": f"plain energy+gradient of one {small.n_atoms}-atom cluster "
-                                f"of the batch in {dt:.2f} s, extrapolated by (n/{small.n_atoms})^3 to the mean size"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -714,25 +725,35 @@ def run_batch(args):
 
 def run_kernel(args):
     """One kernel alone, --warmup + --steps launches, CUDA-event time per launch: the
-    symmetric TF32x3 product Z' = c3 P Z + c1 Z of the Newton-Schulz iteration at order
-    6016 (operands as TF32 hi/lo parts, FP32 output and its parts)."""
+    symmetric split product Z' = c3 P Z + c1 Z of the Newton-Schulz iteration (k_tc_gemm mode
+    2, the library's accumulation lengths: 8 stages for bf16x3, 2 for tf32x3) at order --order
+    (default 6016, the 2000-atom cluster's), operands
+    as hi/lo parts of the --precision kind (bf16x3 or tf32x3), FP32 output and its parts."""
     import torch
     from paper_2308_03140_gb300 import binding
     binding.load()
     dev = torch.device("cuda:0")
-    n = 6016
+    n = args.order
+    kind = 1 if args.precision == "bf16x3" else 2
     g = torch.Generator(device="cpu").manual_seed(7)
     S = torch.randn(n, n, generator=g, dtype=torch.float32) / n ** 0.5
     S = (S + S.T).to(dev)
-    hi = ((S.view(torch.int32) + 0x1000) & ~0x1FFF).view(torch.float32)
-    lo = (S - hi).contiguous()
+    if kind == 2:
+        hi = ((S.view(torch.int32) + 0x1000) & ~0x1FFF).view(torch.float32)
+        lo = (S - hi).contiguous()
+        pdt = torch.float32
+    else:
+        hi = S.to(torch.bfloat16)
+        lo = (S - hi.float()).to(torch.bfloat16)
+        pdt = torch.bfloat16
     C = torch.empty(n, n, dtype=torch.float32, device=dev)
-    Ch, Cl = torch.empty_like(C), torch.empty_like(C)
+    Ch, Cl = torch.empty(n, n, dtype=pdt, device=dev), torch.empty(n, n, dtype=pdt, device=dev)
     err = torch.zeros(1, dtype=torch.int32, device=dev)
+    chunk = 8 if kind == 1 else 2   # the library's accumulation lengths for the kind
 
     def launch():
-        rc = binding.mbdk_gemm_tc(2, hi, hi, C, A1=lo, B1=lo, alpha=-0.5, beta=1.5, D=S, C_hi=Ch, C_lo=Cl,
-                                  mode=2, err=err, chunk_stages=2)
+        rc = binding.mbdk_gemm_tc(kind, hi, hi, C, A1=lo, B1=lo, alpha=-0.5, beta=1.5, D=S, C_hi=Ch, C_lo=Cl,
+                                  mode=2, err=err, chunk_stages=chunk)
         if rc:
             raise RuntimeError(f"mbdk_gemm_tc returned {rc}")
 
@@ -749,8 +770,9 @@ def run_kernel(args):
         raise RuntimeError("tensor-core wait timed out")
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     flops = float(n) * n * (n + 1)   # algorithmic: upper triangle of a symmetric n x n x n product
-    print(json.dumps({"kernel": "k_tc_gemm<TF32x3> mode 2", "order": n, "launches": args.steps, "ms_per_launch": ms,
-                      "tflops_algorithmic": flops / (ms / 1e3) / 1e12}))
+    form = os.environ.get("MBDGB_TC_FORM", "single")
+    print(json.dumps({"kernel": f"k_tc_gemm ({form} form) <{args.precision}> mode 2", "order": n, "chunk_stages": chunk,
+                      "launches": args.steps, "ms_per_launch": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}))
     return 0
 
 

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) k_build_scs(AtomBufs b, double beta, doub
     const int j = j0 + tx, i = i0 + ty;
     const bool pair = i < b.N && j < i, diag = i < b.N && j == i;
     __shared__ double T[24][97];
-    double r[3] = {0.0, 0.0, 0.0}, rho = 1.0, sr = 0.0;
+    double r[3] = {0.0, 0.0, 0.0}, rho = 1.0, sr = 0.0, far_P = 0.0, far_W = 0.0, far2 = 0.0;
     if (pair) {
         r[0] = b.R[3 * j] - b.R[3 * i];
         r[1] = b.R[3 * j + 1] - b.R[3 * i + 1];
@@ -115,19 +115,31 @@ __global__ void __launch_bounds__(256) k_build_scs(AtomBufs b, double beta, doub
         rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
         if (!(rho > 1e-8)) atomicOr(status, ST_INPUT);
         sr = 1.0 - fermi(rho, b.rv[i] + b.rv[j], beta, a).f;
+        // the bare tensor's radial parts, which T^GG equals beyond rho/s = kGaussFar (the far
+        // branch of tgg_radial), once per pair for every frequency
+        const double ir = 1.0 / rho, ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+        far_P = ir3;
+        far_W = -3.0 * ir5;
+        far2 = rho * rho / (kGaussFar * kGaussFar);   // s^2 below this: the far branch
     }
     for (int k = 0; k < b.nf1; ++k) {
         double *Mk = M + k * mstride;
         double v[9];
         if (pair) {
             const double si = b.sig_u[k * b.N + i], sj = b.sig_u[k * b.N + j];
-            const Radial tg = tgg_radial(rho, sqrt(si * si + sj * sj));
+            const double s2 = si * si + sj * sj;
+            double P = far_P, W = far_W;
+            if (!(s2 < far2)) {
+                const Radial tg = tgg_radial(rho, sqrt(s2));
+                P = tg.P;
+                W = tg.W;
+            }
 #pragma unroll
             for (int x = 0; x < 3; ++x) {
                 double *row = Mk + (3LL * i + x) * ld + 3 * j;
 #pragma unroll
                 for (int y = 0; y < 3; ++y) {
-                    v[3 * x + y] = sr * ((x == y ? tg.P : 0.0) + tg.W * r[x] * r[y]);
+                    v[3 * x + y] = sr * ((x == y ? P : 0.0) + W * r[x] * r[y]);
                     row[y] = v[3 * x + y];
                 }
             }
