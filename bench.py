@@ -58,14 +58,15 @@ def gemm_region_sha16(path):
     a = next(k for k, l in enumerate(lines) if l.startswith("void gemm_f64("))
     b = next(k for k in range(a, len(lines)) if lines[k] == "}")
     return hashlib.sha256("\n".join(lines[i:j + 1] + lines[a:b + 1]).encode()).hexdigest()[:16]
-# DRAM bytes per k_tc_gemm launch (a symmetric TF32x3 Newton-Schulz product at order 6016,
-# the size of the 6000x6000 case, captured alone with --kernel tc_gemm_sym6016) from the
-# committed capture (profiles/k_tc_gemm_finite2000.md), valid while the GEMM's own source in
-# k_tc.cu (tile constants through the tc_gemm dispatcher) keeps the captured hash.
-TC_GEMM_TRAFFIC = {("tf32x3", "finite2000"): {"bytes": 1.558883e9 + 0.407660544e9,
-                                               "k_tc_region_sha16": "7b8f28f7af13cca9",
-                                               "launch": "symmetric Z' product, order 6016, 152 persistent CTAs",
-                                               "source": "profiles/k_tc_gemm_finite2000.md"}}
+# DRAM bytes per k_tc_gemm launch from committed captures, keyed by (precision, workload): a
+# symmetric BF16x3 Newton-Schulz product at order 6016 (the 2000-atom cluster's shape, taken
+# alone with --kernel tc_gemm_sym --order 6016; profiles/k_tc_gemm_bf16x3_order6016.md), valid
+# while the GEMM's own source in k_tc.cu (tile constants through the tc_gemm dispatcher)
+# keeps the captured hash.
+TC_GEMM_TRAFFIC = {("bf16x3", "finite2000"): {"bytes": 813.996032e6 + 255.913472e6,
+                                               "k_tc_region_sha16": "4185c6e8fef21eae",
+                                               "launch": "symmetric product, order 6016, 152 persistent CTAs",
+                                               "source": "profiles/k_tc_gemm_bf16x3_order6016.md"}}
 
 
 def tc_region_sha16(path):

@@ -4,6 +4,8 @@
 // Single-CTA form (k_tc_gemm): work item -> one 128 x 128 tile (tm, tn).
 // CTA-pair form (k_tc_gemm2, tcgen05 cta_group::2): work item -> a pair tile of 256 x 128,
 // tile rows 2 TP and 2 TP + 1 (one per CTA of the pair) of tile column tn.
+// Wide form (k_tc_gemm_w): work item -> a wide tile of 128 x 256, tile row tm, tile columns
+// 2 TPn and 2 TPn + 1 (one per half of the CTA's epilogue warps): the transposed pairs.
 //
 // Modes: 0 every tile; 1 the tiles on or below the diagonal (tm >= tn); 2 the tiles on or
 // above it (tm <= tn).  Modes 1 and 2 are square (tiles_m == tiles_n).  A pair tile of mode 1
@@ -163,6 +165,26 @@ __host__ __device__ inline bool pair_tile_valid(int mode, int tiles_m, int TP, i
     if (mode == 1) return tm >= tn;
     if (mode == 2) return tm <= tn;
     return true;
+}
+
+// ---- wide tiles (128 x 256: tile row tm, tile columns 2 TPn and 2 TPn + 1) --------------
+// The transpose of the CTA-pair decomposition: pairs of tile columns.  A wide tile of mode 2
+// (upper) is kept when either half lies on or above the diagonal (2 TPn + 1 >= tm), of mode 1
+// (lower) when either lies on or below it (2 TPn <= tm).
+__host__ __device__ inline int transposed_mode(int mode) { return mode == 2 ? 1 : (mode == 1 ? 2 : 0); }
+
+__host__ __device__ inline int wide_tile_count(int mode, int tiles_m, int tiles_n) {
+    return pair_tile_count(transposed_mode(mode), tiles_n, tiles_m);
+}
+
+// Wide tile (tm, TPn) of work item `bid` (0 <= bid < wide_tile_count).
+__host__ __device__ inline void wide_tile(int bid, int mode, int tiles_m, int tiles_n, int &tm, int &TPn) {
+    pair_tile(bid, transposed_mode(mode), tiles_n, tiles_m, TPn, tm);
+}
+
+// Whether half h (0, 1) of wide tile (tm, TPn), the 128 x 128 tile (tm, 2 TPn + h), is written.
+__host__ __device__ inline bool wide_half_valid(int mode, int tiles_n, int tm, int TPn, int h) {
+    return pair_tile_valid(transposed_mode(mode), tiles_n, TPn, tm, h);
 }
 
 }  // namespace tctiles

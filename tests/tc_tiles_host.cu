@@ -15,3 +15,10 @@ extern "C" void host_pair_tile(int bid, int mode, int tiles_m, int tiles_n, int 
 extern "C" int host_pair_tile_valid(int mode, int tiles_m, int TP, int tn, int rank) {
     return pair_tile_valid(mode, tiles_m, TP, tn, rank) ? 1 : 0;
 }
+extern "C" int host_wide_tile_count(int mode, int tm, int tn) { return wide_tile_count(mode, tm, tn); }
+extern "C" void host_wide_tile(int bid, int mode, int tiles_m, int tiles_n, int *out) {
+    wide_tile(bid, mode, tiles_m, tiles_n, out[0], out[1]);
+}
+extern "C" int host_wide_half_valid(int mode, int tiles_n, int tm, int TPn, int h) {
+    return wide_half_valid(mode, tiles_n, tm, TPn, h) ? 1 : 0;
+}

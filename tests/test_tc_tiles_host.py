@@ -79,3 +79,27 @@ def test_pair_tiles_cover_the_mode_once(host, mode):
         # every pair tile writes at least one tile (no idle work items)
         assert all(host.host_pair_tile_valid(mode, tm_n, TP, tn, 0) or host.host_pair_tile_valid(mode, tm_n, TP, tn, 1)
                    for TP, tn in pairs)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_wide_tiles_cover_the_mode_once(host, mode):
+    host.host_wide_tile.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
+    out = (C.c_int * 2)()
+    for tm_n, tn_n in SIZES:
+        if mode and tm_n != tn_n:
+            continue
+        cnt = host.host_wide_tile_count(mode, tm_n, tn_n)
+        tiles, written = [], []
+        for w in range(cnt):
+            host.host_wide_tile(w, mode, tm_n, tn_n, out)
+            tm, TPn = out[0], out[1]
+            assert 0 <= tm < tm_n and 0 <= TPn < (tn_n + 1) // 2, (mode, tm_n, w, tm, TPn)
+            tiles.append((tm, TPn))
+            for h in (0, 1):
+                if host.host_wide_half_valid(mode, tn_n, tm, TPn, h):
+                    written.append((tm, 2 * TPn + h))
+        assert len(set(tiles)) == len(tiles), (mode, tm_n)
+        assert len(set(written)) == len(written), (mode, tm_n)
+        assert set(written) == required(mode, tm_n, tn_n), (mode, tm_n, tn_n)
+        assert all(host.host_wide_half_valid(mode, tn_n, tm, TPn, 0) or host.host_wide_half_valid(mode, tn_n, tm, TPn, 1)
+                   for tm, TPn in tiles)
