@@ -114,13 +114,15 @@ def parse():
                     help="rsscs: MBD@rsSCS (the headline); nl: MBD-NL (Sec. 2.7: no screening, oscillators "
                          "from the free-atom reference and density-functional ratios drawn by "
                          "synthetic.nl_ratios(N, seed=7000))")
-    ap.add_argument("--kernel", choices=("tc_gemm_sym", "tc_gemm_sym6016", "log_energy_finite2000", "ts_finite2000", "ts_cell256",
-                                         "gemm_f64_split6016"),
+    ap.add_argument("--kernel", choices=("tc_gemm_sym", "tc_gemm_sym6016", "tc_gemm_update", "log_energy_finite2000",
+                                         "ts_finite2000", "ts_cell256", "gemm_f64_split6016"),
                     default=None,
                     help="time one kernel or route alone instead of the workload: tc_gemm_sym = the "
                          "symmetric Newton-Schulz product in the --precision split kind (bf16x3 or tf32x3) at order "
                          "--order (k_tc_gemm mode 2, the library chunk lengths; at 6016 a small case for profilers, about "
-                         "0.9 GB on the device; tc_gemm_sym6016 is the same at 6016); "
+                         "0.9 GB on the device; tc_gemm_sym6016 is the same at 6016); tc_gemm_update = the "
+                         "trailing update of the screening's FP32 Cholesky, C = D - L21 L21^T on the lower tiles of "
+                         "order --order with a 512-column panel (k_tc_gemm mode 1, one matrix); "
                          "log_energy_finite2000 = the log-formula energy route (mbd_log_energy, orders 2) of the "
                          "2000-atom cluster after a TF32x3 evaluation; ts_finite2000 = the TS pairwise energy "
                          "and gradients (mbd_ts_energy) of the 2000-atom cluster; ts_cell256 = the same per cell of "
@@ -729,16 +731,22 @@ def run_kernel(args):
     symmetric split product Z' = c3 P Z + c1 Z of the Newton-Schulz iteration (k_tc_gemm mode
     2, the library's accumulation lengths: 8 stages for bf16x3, 2 for tf32x3) at order --order
     (default 6016, the 2000-atom cluster's), operands
-    as hi/lo parts of the --precision kind (bf16x3 or tf32x3), FP32 output and its parts."""
+    as hi/lo parts of the --precision kind (bf16x3 or tf32x3), FP32 output and its parts; or
+    (--kernel tc_gemm_update) the screening's trailing update C -= L21 L21^T of a 512-column
+    panel on the lower tiles (mode 1, 2-stage accumulation, in place)."""
     import torch
     from paper_2308_03140_gb300 import binding
     binding.load()
     dev = torch.device("cuda:0")
     n = args.order
     kind = 1 if args.precision == "bf16x3" else 2
+    update = args.kernel == "tc_gemm_update"
+    K = 512 if update else n
     g = torch.Generator(device="cpu").manual_seed(7)
-    S = torch.randn(n, n, generator=g, dtype=torch.float32) / n ** 0.5
-    S = (S + S.T).to(dev)
+    S = torch.randn(n, K, generator=g, dtype=torch.float32) / K ** 0.5
+    if not update:
+        S = (S + S.T)
+    S = S.to(dev)
     if kind == 2:
         hi = ((S.view(torch.int32) + 0x1000) & ~0x1FFF).view(torch.float32)
         lo = (S - hi).contiguous()
@@ -748,15 +756,25 @@ def run_kernel(args):
         lo = (S - hi.float()).to(torch.bfloat16)
         pdt = torch.bfloat16
     C = torch.empty(n, n, dtype=torch.float32, device=dev)
-    Ch, Cl = torch.empty(n, n, dtype=pdt, device=dev), torch.empty(n, n, dtype=pdt, device=dev)
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     chunk = 8 if kind == 1 else 2   # the library's accumulation lengths for the kind
+    if update:
+        chunk = 2   # the screening's accumulation length
+        C.copy_(torch.randn(n, n, generator=g, dtype=torch.float32).to(dev))
 
-    def launch():
-        rc = binding.mbdk_gemm_tc(kind, hi, hi, C, A1=lo, B1=lo, alpha=-0.5, beta=1.5, D=S, C_hi=Ch, C_lo=Cl,
-                                  mode=2, err=err, chunk_stages=chunk)
-        if rc:
-            raise RuntimeError(f"mbdk_gemm_tc returned {rc}")
+        def launch():   # C = C - S S^T on the lower tiles (in place, as the factorisation does)
+            rc = binding.mbdk_gemm_tc(kind, hi, hi, C, A1=lo, B1=lo, alpha=-1.0, beta=1.0, D=C, mode=1, err=err,
+                                      chunk_stages=chunk)
+            if rc:
+                raise RuntimeError(f"mbdk_gemm_tc returned {rc}")
+    else:
+        Ch, Cl = torch.empty(n, n, dtype=pdt, device=dev), torch.empty(n, n, dtype=pdt, device=dev)
+
+        def launch():
+            rc = binding.mbdk_gemm_tc(kind, hi, hi, C, A1=lo, B1=lo, alpha=-0.5, beta=1.5, D=S, C_hi=Ch, C_lo=Cl,
+                                      mode=2, err=err, chunk_stages=chunk)
+            if rc:
+                raise RuntimeError(f"mbdk_gemm_tc returned {rc}")
 
     for _ in range(args.warmup):
         launch()
@@ -770,10 +788,15 @@ def run_kernel(args):
     if err.item():
         raise RuntimeError("tensor-core wait timed out")
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    flops = float(n) * n * (n + 1)   # algorithmic: upper triangle of a symmetric n x n x n product
-    form = os.environ.get("MBDGB_TC_FORM", "single")
-    print(json.dumps({"kernel": f"k_tc_gemm ({form} form) <{args.precision}> mode 2", "order": n, "chunk_stages": chunk,
-                      "launches": args.steps, "ms_per_launch": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}))
+    if update:   # algorithmic: the lower tiles (tm >= tn) of the n x n x 512 product
+        t = n // 128
+        flops = 2.0 * 128 * 128 * K * t * (t + 1) / 2
+    else:        # algorithmic: upper triangle of a symmetric n x n x n product
+        flops = float(n) * n * (n + 1)
+    form = os.environ.get("MBDGB_TC_FORM", "wide")
+    print(json.dumps({"kernel": f"k_tc_gemm ({form} form) <{args.precision}> mode {1 if update else 2}", "order": n,
+                      "K": K, "chunk_stages": chunk, "launches": args.steps, "ms_per_launch": ms,
+                      "tflops_algorithmic": flops / (ms / 1e3) / 1e12}))
     return 0
 
 

@@ -461,6 +461,232 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+// ---- wide form: 128 x 256 tiles -------------------------------------------------------------
+// One CTA per SM computes 128 x 256 tiles (tile row tm, tile columns 2 TPn and 2 TPn + 1;
+// tc_tiles.cuh): each K stage holds 128 rows of A and 256 of B (96 KB for the split kinds, two
+// stages), and one tcgen05.mma with N = 256 does the work of two 128 x 128 ones, so every
+// barrier handshake and TMA box of the ring feeds twice the MMA work.  Each chunk accumulates
+// in one of two 256-column TMEM buffers; eight epilogue warps drain them, warp w taking the
+// TMEM lane quarter w % 4 and the column half w / 4 (128 sums per thread), and store each half
+// as a 128 x 128 tile.  Warp 8 issues the TMA loads, warp 9 the MMAs; warps 10 and 11 complete
+// the third warpgroup.  Registers: the launch gives 168 per thread (384 x 168 = 64512, three
+// warps on each SM sub-partition); the epilogue warpgroups raise theirs to EPI_REGS and the
+// third lowers its to 504 - 2 EPI_REGS, so the sum stays the launch's.
+constexpr int TNW = 256;
+constexpr int kWideBufs = 2;
+#ifndef EPI_REGS_OVERRIDE
+constexpr int EPI_REGS = 208;
+#else
+constexpr int EPI_REGS = EPI_REGS_OVERRIDE;
+#endif
+static_assert(EPI_REGS % 8 == 0 && 2 * EPI_REGS + (504 - 2 * EPI_REGS) == 504 && 504 - 2 * EPI_REGS >= 24,
+              "register shares of the wide GEMM must add up to the launch's 168 per thread");
+template <int KIND>
+struct TcCfgW {
+    static constexpr int PAIRS = KIND == 0 ? 1 : 3;
+    static constexpr int B_BYTES = TNW * KB;   // 32 KB
+    static constexpr int OFF_B0 = TILE_BYTES, OFF_A1 = TILE_BYTES + B_BYTES, OFF_B1 = 2 * TILE_BYTES + B_BYTES;
+    static constexpr int STAGE_BYTES = (KIND == 0 ? 1 : 2) * (TILE_BYTES + B_BYTES);
+    static constexpr int STAGES = KIND == 0 ? 4 : 2;
+    static constexpr int ELEM = KIND == 1 ? 2 : 4;
+    static constexpr bool TF32 = KIND != 1;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512;
+};
+__host__ __device__ constexpr uint32_t idescw(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(TNW >> 3) << 17) |
+           (static_cast<uint32_t>(TM >> 4) << 24);
+}
+template <bool TF32>
+__device__ __forceinline__ void mmaw(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    if (TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(idescw(2)), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(idescw(1)), "r"(acc));
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(384, 1)
+    k_tc_gemm_w(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs g,
+                int tiles_n) {
+    using Cfg = TcCfgW<KIND>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+    uint64_t *empty = full + Cfg::STAGES;
+    uint64_t *cfull = empty + Cfg::STAGES;
+    uint64_t *cfree = cfull + kWideBufs;
+    uint64_t *done = cfree + kWideBufs;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int tiles_m = g.M / TM;
+    const int wtiles = tctiles::wide_tile_count(g.mode, tiles_m, tiles_n);
+    const int items = wtiles * g.batch;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < kWideBufs; ++b) {
+            mbar_init(&cfull[b], 1);
+            mbar_init(&cfree[b], 8);   // one arrival per epilogue warp
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
+                     "r"(kWideBufs * TNW));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nk = static_cast<int>((static_cast<long long>(g.K) * Cfg::ELEM) / KB);
+    const int cs = (g.chunk_stages > 0 && g.chunk_stages < nk) ? g.chunk_stages : nk;
+    const int nchunks = (nk + cs - 1) / cs;
+    constexpr int KELEM = KB / Cfg::ELEM;
+
+    if (warp >= 8) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(504 - 2 * EPI_REGS));
+        if (warp == 8 && lane == 0) {
+            // ---- TMA producer ----
+            int issued = 0, kg = 0;
+            for (int w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+                const int bz = w / wtiles;
+                int tm, TPn;
+                tctiles::wide_tile(w - bz * wtiles, g.mode, tiles_m, tiles_n, tm, TPn);
+                const int ya = bz * g.M + tm * TM, yb = bz * g.N + TPn * TNW;
+                for (int kt = 0; kt < nk && !*abort_flag; ++kt, ++kg) {
+                    const int s = kg % Cfg::STAGES;
+                    const uint32_t ph = (kg / Cfg::STAGES) & 1;
+                    if (kg >= Cfg::STAGES && !mbar_wait(&empty[s], ph ^ 1, g.err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *st = smem + s * Cfg::STAGE_BYTES;
+                    mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+                    const int kx = kt * KELEM;
+                    tma_load_2d(st, &mA0, kx, ya, &full[s]);
+                    tma_load_2d(st + Cfg::OFF_B0, &mB0, kx, yb, &full[s]);
+                    if (KIND != 0) {
+                        tma_load_2d(st + Cfg::OFF_A1, &mA1, kx, ya, &full[s]);
+                        tma_load_2d(st + Cfg::OFF_B1, &mB1, kx, yb, &full[s]);
+                    }
+                    issued = kg + 1;
+                }
+            }
+            if (*abort_flag) {   // let this CTA's copies land before shared memory is released
+                for (int k = (issued > Cfg::STAGES ? issued - Cfg::STAGES : 0); k < issued; ++k)
+                    mbar_wait(&full[k % Cfg::STAGES], (k / Cfg::STAGES) & 1, g.err);
+            }
+        } else if (warp == 9 && lane == 0) {
+            // ---- MMA issuer: chunk c accumulates afresh into buffer c % kWideBufs ----
+            int kg = 0, cg = 0;
+            for (int w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, cg += nchunks) {
+                for (int kt = 0; kt < nk && !*abort_flag; ++kt, ++kg) {
+                    const int c = cg + kt / cs, buf = c % kWideBufs;
+                    if (kt % cs == 0 && c >= kWideBufs &&
+                        !mbar_wait(&cfree[buf], ((c / kWideBufs) - 1) & 1, g.err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    const int s = kg % Cfg::STAGES;
+                    if (!mbar_wait(&full[s], (kg / Cfg::STAGES) & 1, g.err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t base = su32(smem + s * Cfg::STAGE_BYTES);
+                    const uint32_t dt = tmem + static_cast<uint32_t>(buf * TNW);
+#pragma unroll
+                    for (int k = 0; k < KB / 32; ++k) {
+                        const uint64_t a0 = sdesc(base + k * 32), b0 = sdesc(base + Cfg::OFF_B0 + k * 32);
+                        mmaw<Cfg::TF32>(dt, a0, b0, (kt % cs != 0 || k != 0) ? 1u : 0u);
+                        if (Cfg::PAIRS == 3) {
+                            const uint64_t a1 = sdesc(base + Cfg::OFF_A1 + k * 32);
+                            const uint64_t b1 = sdesc(base + Cfg::OFF_B1 + k * 32);
+                            mmaw<Cfg::TF32>(dt, a0, b1, 1u);
+                            mmaw<Cfg::TF32>(dt, a1, b0, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                    if (kt % cs == cs - 1 || kt == nk - 1) mma_commit(&cfull[buf]);
+                }
+            }
+            mma_commit(done);
+        }
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(EPI_REGS));
+        // ---- epilogue warps 0-7: lane quarter q, column half h; thread = row of the tile ----
+        const int q = warp & 3, h = warp >> 2;
+        bool ok = true;
+        int cg = 0;
+        for (int w = blockIdx.x; w < items && ok; w += gridDim.x, cg += nchunks) {
+            const int bz = w / wtiles;
+            int tm, TPn;
+            tctiles::wide_tile(w - bz * wtiles, g.mode, tiles_m, tiles_n, tm, TPn);
+            const int tn = 2 * TPn + h;
+            const bool write = tctiles::wide_half_valid(g.mode, tiles_n, tm, TPn, h);
+            const float *Dp = g.D ? g.D + bz * g.sC : nullptr;
+            float *Cp = g.C ? g.C + bz * g.sC : nullptr;
+            float acc[TN];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[j] = 0.f;
+            const int row = q * 32 + lane;
+            const long long m = static_cast<long long>(tm) * TM + row;
+            for (int c = 0; c < nchunks; ++c) {
+                const int buf = (cg + c) % kWideBufs;
+                if (write && c == max(0, nchunks - 2) && g.beta != 0.f) {
+                    const float *drow = Dp + m * g.ld + static_cast<long long>(tn) * TN;
+#pragma unroll
+                    for (int qq = 0; qq < TN / 32; ++qq) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(drow + 32 * qq));
+                }
+                ok = mbar_wait(&cfull[buf], ((cg + c) / kWideBufs) & 1, g.err) && !*abort_flag;
+                ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t tb = tmem + (static_cast<uint32_t>(q * 32) << 16) +
+                                    static_cast<uint32_t>(buf * TNW + h * TN);
+#pragma unroll
+                for (int qq = 0; qq < TN / 32; ++qq) {
+                    uint32_t r[32];
+                    tmem_ld32(tb + qq * 32, r);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[qq * 32 + j] += __uint_as_float(r[j]);
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&cfree[buf])) : "memory");
+            }
+            if (ok && write) tile_epilogue<KIND>(g, acc, m, tm, tn, Dp, Cp, lane);
+        }
+    }
+    __syncwarp();
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        if (lane == 0) mbar_wait(done, 0, g.err);
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kWideBufs * TNW));
+    }
+}
+
 // ---- CTA-pair form (tcgen05 cta_group::2) ----------------------------------------------
 // A cluster of two CTAs computes a pair tile of 256 x 128 (tile rows 2 TP and 2 TP + 1 of
 // tile column tn, tc_tiles.cuh): CTA r stages A rows [256 TP + 128 r, +128) and B rows
@@ -837,6 +1063,39 @@ cudaError_t launch_tc(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int KIND>
+cudaError_t launch_tcw(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
+    using Cfg = TcCfgW<KIND>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_w<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap a0, a1, b0, b1;
+    const long long lda = op.lda, ldb = op.ldb;
+    const long long rows_a = static_cast<long long>(g.batch) * g.M, rows_b = static_cast<long long>(g.batch) * g.N;
+    if (!make_map(&a0, op.A0, KIND, rows_a, g.K, lda, TM) || !make_map(&b0, op.B0, KIND, rows_b, g.K, ldb, TNW))
+        return cudaErrorInvalidValue;
+    if (KIND != 0) {
+        if (!make_map(&a1, op.A1, KIND, rows_a, g.K, lda, TM) || !make_map(&b1, op.B1, KIND, rows_b, g.K, ldb, TNW))
+            return cudaErrorInvalidValue;
+    } else {
+        a1 = a0;
+        b1 = b0;
+    }
+    const int tmt = g.M / TM, tnt = g.N / TN;
+    const long long items = static_cast<long long>(tctiles::wide_tile_count(g.mode, tmt, tnt)) * g.batch;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = static_cast<int>(std::min<long long>(items, sms));
+    count_launches(1);
+    k_tc_gemm_w<KIND><<<grid, 384, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt);
+    return cudaGetLastError();
+}
+
 // CTA-pair launch: clusters of two CTAs, one pair per two SMs, as many pairs as fit at once
 // (persistent), each looping over pair tiles.
 template <int KIND>
@@ -890,15 +1149,17 @@ cudaError_t launch_tc2(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// The single-CTA form unless MBDGB_TC_FORM=pair is set in the environment (the pair form, for
-// comparison).
-bool use_pairs() {
+// Form of the GEMM: MBDGB_TC_FORM in the environment selects "wide" (128 x 256 tiles),
+// "single" (128 x 128 tiles, one CTA) or "pair" (256 x 128 tiles on a CTA pair); the default is
+// the wide form.
+int tc_form() {
     static int v = -1;
     if (v < 0) {
         const char *e = std::getenv("MBDGB_TC_FORM");
-        v = (e && std::string(e) == "pair") ? 1 : 0;
+        const std::string f = e ? std::string(e) : std::string();
+        v = f == "pair" ? 2 : (f == "single" ? 1 : 0);
     }
-    return v == 1;
+    return v;
 }
 
 }  // namespace
@@ -918,7 +1179,13 @@ cudaError_t tc_gemm(int kind, const TcOperands &op, const TcArgs &g, cudaStream_
         (kind != 0 && (!op.A1 || !op.B1)) || (kind == 0 && (g.Ch || g.CTh)) || g.batch < 1 || g.batch > 65535 ||
         (g.batch > 1 && (g.Ch || g.CT || g.CTh || g.C64 || g.resid || g.sC < static_cast<long long>(g.M) * g.ld)))
         return cudaErrorInvalidValue;
-    if (use_pairs()) {
+    const int form = tc_form();
+    if (form == 0) {
+        if (kind == 0) return launch_tcw<0>(op, g, s);
+        if (kind == 1) return launch_tcw<1>(op, g, s);
+        return launch_tcw<2>(op, g, s);
+    }
+    if (form == 2) {
         if (kind == 0) return launch_tc2<0>(op, g, s);
         if (kind == 1) return launch_tc2<1>(op, g, s);
         return launch_tc2<2>(op, g, s);

@@ -98,13 +98,15 @@ def test_tc_gemm_symmetric_mirror_and_split_output(kind):
         assert torch.equal(Ch.cpu(), Ch.cpu().T) and torch.equal(Cl.cpu(), Cl.cpu().T)
 
 
-@pytest.mark.parametrize("kind", [0, 2])
-def test_tc_gemm_lower_tiles_only(kind):
+@pytest.mark.parametrize("n", [512, 640])
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_tc_gemm_lower_tiles_only(kind, n):
     # mode 1: C = beta D + alpha S S^T on the tiles on or below the diagonal; the tiles above
-    # it are not written (the FP32 Cholesky's trailing update reads only the lower triangle)
+    # it are not written (the FP32 Cholesky's trailing update reads only the lower triangle);
+    # an odd tile count leaves the wide form a last tile pair with one half outside the matrix
     import torch
     dev = torch.device("cuda:0")
-    n, K = 512, 256
+    K = 256
     g = torch.Generator(device="cpu").manual_seed(5)
     S = torch.randn(n, K, generator=g, dtype=torch.float32)
     D = torch.randn(n, n, generator=g, dtype=torch.float32)
@@ -131,6 +133,20 @@ def test_tc_gemm_lower_tiles_only(kind):
                 assert err_t < TOL[kind], (tm, tn, err_t)
             else:
                 assert torch.isnan(blk).all(), (tm, tn)
+
+
+@pytest.mark.parametrize("form", ["single", "pair"])
+def test_tc_gemm_other_forms(form):
+    # the 128x128 and CTA-pair forms (MBDGB_TC_FORM, read once per process) pass the same
+    # GEMM tests as the default wide form, in a process of their own
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ, MBDGB_TC_FORM=form)
+    r = subprocess.run([sys.executable, "-m", "pytest", __file__, "-q", "-m", "gpu", "-x", "-p", "no:cacheprovider",
+                        "-k", "tc_gemm_full or tc_gemm_symmetric or tc_gemm_lower"], env=env, capture_output=True,
+                       text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
 
 
 def test_tc_gemm_rejects_bad_shapes():
