@@ -58,15 +58,16 @@ def gemm_region_sha16(path):
     a = next(k for k, l in enumerate(lines) if l.startswith("void gemm_f64("))
     b = next(k for k in range(a, len(lines)) if lines[k] == "}")
     return hashlib.sha256("\n".join(lines[i:j + 1] + lines[a:b + 1]).encode()).hexdigest()[:16]
-# DRAM bytes per k_tc_gemm launch from committed captures, keyed by (precision, workload): a
-# symmetric BF16x3 Newton-Schulz product at order 6016 (the 2000-atom cluster's shape, taken
-# alone with --kernel tc_gemm_sym --order 6016; profiles/k_tc_gemm_bf16x3_order6016.md), valid
-# while the GEMM's own source in k_tc.cu (tile constants through the tc_gemm dispatcher)
-# keeps the captured hash.
-TC_GEMM_TRAFFIC = {("bf16x3", "finite2000"): {"bytes": 813.996032e6 + 255.913472e6,
-                                               "k_tc_region_sha16": "4185c6e8fef21eae",
-                                               "launch": "symmetric product, order 6016, 152 persistent CTAs",
-                                               "source": "profiles/k_tc_gemm_bf16x3_order6016.md"}}
+# DRAM bytes per tensor-core GEMM launch from committed captures, keyed by (precision,
+# workload): the mean over the 28 Newton-Schulz and 2 correction products of one BF16x3 step
+# of the 8000-atom cluster (1-pass dram__bytes capture of the full-size step;
+# profiles/launches_finite8000_bf16x3.md), valid while the GEMM's own source in k_tc.cu (tile
+# constants through the tc_gemm dispatcher) keeps the captured hash.
+TC_GEMM_TRAFFIC = {("bf16x3", "finite8000"): {"bytes": 52.086940919e9,
+                                               "k_tc_region_sha16": "18d849742118a1e8",
+                                               "launch": "mean of the 30 Newton-Schulz and correction products "
+                                                         "of one step, order 24064",
+                                               "source": "profiles/launches_finite8000_bf16x3.md"}}
 
 
 def tc_region_sha16(path):
@@ -638,7 +639,9 @@ def batch_section(binding, local, args, precision_name):
     systems = syn.cluster_batch(K)
     model = np.load(os.path.join(ROOT, "paper_2308_03140_gb300", "learned_scs_model.npz"))
     precision = precision_code(binding, precision_name)
-    arms = {"plain": dict(), "learned": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e-6),
+    scale = float(model["estimate_scale"]) if "estimate_scale" in model.files else 1.0
+    arms = {"plain": dict(), "learned": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e-6,
+                                             learned_estimate_scale=scale),
             "learned_no_fallback": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e300)}
     ctxs = {}
     for name, opt in arms.items():
@@ -690,7 +693,7 @@ def batch_section(binding, local, args, precision_name):
     return {"config": {"workload": "batch4096", "clusters": K, "mean_atoms": float(np.mean([s.n_atoms for s in systems])),
                        "sizes": "U{50..500}, the first clusters of the 4096-cluster recipe", "precision": precision_name,
                        "learned_model": "paper_2308_03140_gb300/learned_scs_model.npz (4 members, trained on 20000 "
-                                        "perturbed plain-screening solves)"},
+                                        "perturbed plain-screening solves)", "estimate_scale": scale},
             "arms": results}
 
 

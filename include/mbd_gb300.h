@@ -62,7 +62,8 @@ typedef struct mbd_ctx mbd_ctx;
  * (Sec. 2.7), precision FP64, ns_tol 1e-8 (Frobenius norm of I - Z Y at which one
  * final Newton-Schulz step is taken; periodic systems: of all Bloch vectors' matrices
  * together), ns_max_iter 100, tc_chunk_stages 0 (per kind), ewald_gamma, real_cutoff and
- * recip_cutoff 0 (automatic, see below), learned_max_error 1e-6, mixed_max_error 1e-7. */
+ * recip_cutoff 0 (automatic, see below), learned_max_error 1e-6, mixed_max_error 1e-7,
+ * learned_estimate_scale 1. */
 typedef struct {
     int n_freq;          /* Gauss-Legendre points of the Casimir-Polder integral     */
     double beta;         /* damping scale s_R of the Fermi function, Eq. (fermi-damping) */
@@ -85,7 +86,8 @@ typedef struct {
     /* Screening: MBD_SCS_PLAIN (the Dyson solves of Eq. (scs)) or MBD_SCS_LEARNED (the model
      * set by mbd_set_scs_model predicts alpha_bar(iu); when its estimated energy error per
      * atom exceeds learned_max_error (Ha, default 1e-6) the evaluation is redone with plain
-     * screening).  The learned model is not part of the paper.
+     * screening; the model's features and outputs use the 15-point grid, so learned mode
+     * needs n_freq = 15).  The learned model is not part of the paper.
      * MBD_SCS_NL selects MBD-NL (Sec. 2.7, paragraph MBD-NL): no screening; the oscillators
      * are set directly by Eq. (mbd-nl-scaling), alpha0_i = alpha0_ref,i ra_i and
      * omega_i = omega_ref,i rw_i with omega_ref = 4 c6_ref / (3 alpha0_ref^2), and the damping
@@ -103,6 +105,10 @@ typedef struct {
      * Above it the evaluation fails with MBD_ERR_NOT_CONVERGED (for instance a Q so badly
      * conditioned that the reduced-precision iteration cannot resolve it; the FP64 path can). */
     double mixed_max_error;
+    /* MBD_SCS_LEARNED: factor on the ensemble's error estimate (mbd_set_scs_model), fitted
+     * with the model on held-out clusters so that the scaled estimate bounds the true error of
+     * most of them (default 1, the unscaled estimate; must be positive).                 */
+    double learned_estimate_scale;
 } mbd_options;
 
 #define MBD_SCS_PLAIN 0
@@ -179,9 +185,10 @@ int mbd_backward_dev(mbd_ctx *ctx, void *stream, long long evaluation, int n_ato
 
 /* Learned screening model for MBD_SCS_LEARNED (host arrays, copied): n_members ensemble
  * members of MBD_LEARNED_PARAMS FP16 values each (layout in include/mbd_gb300_kernels.h),
- * feature mean and std [MBD_LEARNED_FEATURES = 74] (FP32).  The prediction is the members' mean of
- * y = log(alpha_bar/alpha); their spread s_i(u) gives the energy-error estimate
- * sum_{i,u} |dE/d alpha_bar_i(u)| s_i(u) / N.  Finite systems only; energies and coordinate
+ * feature mean and std [MBD_LEARNED_FEATURES = 122] (FP32).  The prediction is the members' mean of
+ * y = log(alpha_bar/alpha); the spread of the members' first-order energies gives the
+ * energy-error estimate c std_m( sum_{i,u} dE/d alpha_bar_i(u) (alpha_bar_m,i(u) - mean over
+ * members) ) / N, alpha_bar_m = alpha exp(y_m), c = learned_estimate_scale.  Finite systems only; energies and coordinate
  * gradients (through the network and the features); a request for parameter gradients in
  * learned mode returns MBD_ERR_UNSUPPORTED. */
 int mbd_set_scs_model(mbd_ctx *ctx, int n_members, const void *params_fp16, const float *mean, const float *std);

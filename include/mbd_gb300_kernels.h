@@ -127,33 +127,39 @@ int mbdk_cholesky_solve3_f64_noalloc(void *stream, double *A, long long ld, int 
  * (the terms of the Dyson series of Eq. scs at u = 0): with B_ij = (1 - f_ij) T^GG_ij
  * (Eqs. scs-sr-dipole, tgg, mayer, fermi-damping; beta 0.83, a 6) and
  * M_i = sum_{j, d<24} alpha0_j B_ij: m1 = Tr M_i / 3, m2 = Tr(sum_j alpha0_j B_ij M_j) / 3,
- * m3 = Tr(M_i M_i) / 3, alpha0_i m1, alpha0_i^2 m2, alpha0_i^2 m3.
- * Network: MLP 74 -> 128 -> 128 -> 16 on standardised features (x - mean) / std, SiLU
+ * m3 = Tr(M_i M_i) / 3, alpha0_i m1, alpha0_i^2 m2, alpha0_i^2 m3; then the terms of the
+ * Dyson series of Eq. scs at the 16 grid points u_k (u_0 = 0 and the 15 nodes of Eq.
+ * casimir-polder, Sec. 3.3): with alpha_j(u) of Eq. dyn-pol and B_ij(u) = (1 - f_ij) T^GG_ij
+ * at the widths of alpha(u) (Eq. mayer), H^(0)_i = I and H^(q)_i = sum_{j != i} alpha_j(u)
+ * B_ij(u) H^(q-1)_j over all atoms of the system, feature 74 + 3 k + q - 1 is
+ * Tr H^(q)_i(u_k) / 3 for q = 1, 2, 3 (pair arithmetic in FP32, sums over partners in FP64).
+ * Network: MLP 122 -> 128 -> 128 -> 16 on standardised features (x - mean) / std, SiLU
  * activations, FP16 weights and biases, FP32 accumulation.  One ensemble member's
- * parameters are MBD_LEARNED_PARAMS halves: W1 [74][128], b1 [128], W2 [128][128], b2 [128],
+ * parameters are MBD_LEARNED_PARAMS halves: W1 [122][128], b1 [128], W2 [128][128], b2 [128],
  * W3 [128][16], b3 [16] (W[in][out], row-major); members are stored one after another. */
-#define MBD_LEARNED_FEATURES 74
+#define MBD_LEARNED_FEATURES 122
 #define MBD_LEARNED_OUTPUTS 16
-#define MBD_LEARNED_PARAMS 28176
+#define MBD_LEARNED_PARAMS 34320
+#define MBD_LEARNED_WORK 144   /* FP64 words of mbdk_scs_features scratch per atom */
 
 /* Features of n_atoms atoms of n_systems systems stored one after another: system s holds
  * atoms offsets[s] .. offsets[s+1]-1 (offsets [n_systems + 1], offsets[0] = 0,
  * offsets[n_systems] = n_atoms).  coords [n_atoms][3] (bohr) and the free-atom parameters
- * [n_atoms] each as in mbd_set_free_atom_params (FP64); X [n_atoms][74] (FP32); work
- * [n_atoms][6] FP64 scratch (the moments M_i). */
+ * [n_atoms] each as in mbd_set_free_atom_params (FP64); X [n_atoms][122] (FP32); work
+ * [n_atoms][MBD_LEARNED_WORK] FP64 words of scratch (the moments M_i and the Dyson terms). */
 int mbdk_scs_features(void *stream, int n_atoms, int n_systems, const int *offsets, const double *coords,
                       const double *alpha0_ref, const double *c6_ref, const double *rvdw_ref,
                       const double *volume_ratio, float *X, double *work);
 
-/* Forward pass of n_members members on n_atoms rows of raw features X [n_atoms][74]:
- * Y [n_members][n_atoms][16]; mean, std [74]; params_fp16 [n_members][MBD_LEARNED_PARAMS].
+/* Forward pass of n_members members on n_atoms rows of raw features X [n_atoms][122]:
+ * Y [n_members][n_atoms][16]; mean, std [122]; params_fp16 [n_members][MBD_LEARNED_PARAMS].
  * zcache (optional, [n_members][2][n_atoms][128] FP32) keeps the pre-activations of both
  * hidden layers for mbdk_mlp_backward. */
 int mbdk_mlp_forward(void *stream, int n_atoms, int n_members, const float *X, const float *mean,
                      const float *std, const void *params_fp16, float *Y, float *zcache);
 
 /* Backward pass of sum(dY * Y) after mbdk_mlp_forward with a zcache, dY [n_members][n_atoms]
- * [16]: dX (optional) [n_members][n_atoms][74] receives the gradient with respect to the raw
+ * [16]: dX (optional) [n_members][n_atoms][122] receives the gradient with respect to the raw
  * features; grad (optional) [n_members][MBD_LEARNED_PARAMS] FP32 is ACCUMULATED with the
  * gradient with respect to the parameters (clear it first for a fresh gradient). */
 int mbdk_mlp_backward(void *stream, int n_atoms, int n_members, const float *X, const float *mean,
@@ -169,6 +175,11 @@ int mbdk_mse_grad(void *stream, long long n, const float *y, const float *t, flo
  * rounded to FP16 (to nearest). */
 int mbdk_adam_step(void *stream, long long n, float *params, const float *grad, float *m, float *v, int step,
                    float lr, void *params_fp16);
+
+/* Training targets of the model: Y [n_atoms][16] (FP32) = log(alpha_bar[k][i] /
+ * alpha_free[k][i]) from the screened and free polarizabilities [16][n_atoms] (FP64) of one
+ * system at the 16 grid points. */
+int mbdk_learned_targets(void *stream, int n_atoms, const double *alpha_bar, const double *alpha_free, float *Y);
 
 /* dst[r][c] = src[idx[r]][c] for r < rows, c < width (FP32). */
 int mbdk_gather_rows(void *stream, long long rows, int width, const int *idx, const float *src, float *dst);

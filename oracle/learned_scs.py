@@ -5,7 +5,7 @@ CPU leg, never by the product path; it shares no code with the CUDA kernels.
 
 The paper has no learned part; the model below is this project's reading of the task it
 stands in for (the screening of Eqs. scs and contraction, Sec. 2.3):
-- features of atom i (74): for every other atom j of the same system at distance d < 24 bohr,
+- features of atom i (122): for every other atom j of the same system at distance d < 24 bohr,
   alpha0_j fc(d) G_m(d) summed over j, for 64 Gaussians G_m(d) = exp(-(d - mu_m)^2 / (2 w^2)),
   mu_m = (m + 1/2) w, w = 0.375 bohr (4 radial shells of 6 bohr x 16 Gaussians, width =
   spacing), fc(d) = (1 + cos(pi d / 24)) / 2 (smooth cutoff); then the atom's own TS-scaled
@@ -14,13 +14,18 @@ stands in for (the screening of Eqs. scs and contraction, Sec. 2.3):
   (1 - f_ij) T^GG_ij (the SCS coupling of Eq. scs-sr-dipole, widths of Eq. mayer),
   m1 = Tr M_i / 3 (first order), m2 = Tr(sum_j alpha0_j (1 - f_ij) T^GG_ij M_j) / 3 (second
   order, two hops), m3 = Tr(M_i M_i) / 3, each also times alpha0_i (m1) or alpha0_i^2 (m2, m3);
+  then the Dyson moments at every grid point (48 more): m_q,i(u_k) of dyson_moments below for
+  q = 1, 2, 3 and the 16 points u_0 = 0, u_1..u_15 of Eq. (casimir-polder)'s grid, stored
+  as feature 74 + 3 k + q - 1 (no distance cutoff);
 - standardisation x' = (x - mean) / std with stored mean and std;
-- MLP 74 -> 128 -> 128 -> 16, SiLU activations, FP16 weights (rounded; the oracle evaluates
+- MLP 122 -> 128 -> 128 -> 16, SiLU activations, FP16 weights (rounded; the oracle evaluates
   them exactly in FP64);
 - output y_k = log(alpha_bar_i(u_k) / alpha_i(u_k)) at the 16 grid points (u_0 = 0);
-- ensemble of members: the prediction is the mean of y over members; the spread s_i(u) of the
-  predicted alpha_bar over members gives the energy error estimate
-  |dE| ~ sum_{i,u} |dE/d alpha_bar_i(u)| s_i(u) (the adjoints of the screened-parameter chain).
+- ensemble of members: the prediction is the mean of y over members; the energy error
+  estimate is the members' spread of their first-order energies, std_m of
+  sum_{i,u} dE/d alpha_bar_i(u) (alpha_bar_m,i(u) - mean over members) with
+  alpha_bar_m = alpha exp(y_m) (the adjoints of the screened-parameter chain), per atom and
+  times a scale fitted on held-out systems.
 """
 from __future__ import annotations
 
@@ -30,7 +35,9 @@ N_SHELL, N_GAUSS = 4, 16
 SHELL = 6.0
 CUTOFF = N_SHELL * SHELL
 WIDTH = SHELL / N_GAUSS
-N_FEAT = N_SHELL * N_GAUSS + 4 + 6
+N_FREQ_POINTS, N_HOPS = 16, 3
+N_FEAT_STATIC = N_SHELL * N_GAUSS + 4 + 6
+N_FEAT = N_FEAT_STATIC + N_FREQ_POINTS * N_HOPS
 HIDDEN = 128
 N_OUT = 16
 LAYERS = ((N_FEAT, HIDDEN), (HIDDEN, HIDDEN), (HIDDEN, N_OUT))
@@ -59,13 +66,30 @@ def orc_sigma(alpha):
     return np.cbrt(np.sqrt(2.0 / np.pi) * alpha / 3.0)
 
 
+def grid_points():
+    """The 16 frequencies of the moments: u_0 = 0 and the 15 nodes of the Casimir-Polder grid."""
+    import oracle as o
+    return o.freq_grid(N_FREQ_POINTS - 1)[0]
+
+
 def features(R, a0, om, rv, ratio):
-    """Raw features [N, 74] of one system (TS-scaled a0, om, rv), by the definition above,
+    """Raw features [N, 122] of one system (TS-scaled a0, om, rv), by the definition above,
     one atom pair at a time."""
     R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
     N = R.shape[0]
-    mu = centers()
     X = np.zeros((N, N_FEAT))
+    X[:, :N_FEAT_STATIC] = static_features(R, a0, om, rv, ratio)
+    m = dyson_moments(R, a0, om, rv, grid_points(), orders=N_HOPS)   # [16, N, 3]
+    X[:, N_FEAT_STATIC:] = m.transpose(1, 0, 2).reshape(N, N_FREQ_POINTS * N_HOPS)
+    return X
+
+
+def static_features(R, a0, om, rv, ratio):
+    """The first 74 features (radial Gaussians, own parameters, static moments)."""
+    R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
+    N = R.shape[0]
+    mu = centers()
+    X = np.zeros((N, N_FEAT_STATIC))
     M = np.zeros((N, 3, 3))
     B = {}
     for i in range(N):
@@ -129,7 +153,7 @@ def round_fp16(params):
 
 
 def forward(Xs, params):
-    """MLP on standardised features Xs [B, 74]; params [(W [in, out], b [out])] x 3.
+    """MLP on standardised features Xs [B, 122]; params [(W [in, out], b [out])] x 3.
     Returns y [B, 16] and the cache for backward."""
     z1 = Xs @ params[0][0] + params[0][1]
     h1 = silu(z1)
@@ -175,9 +199,13 @@ def predict_alpha_bar(Xs, members, alpha_u):
     return ab.T, ab_m.std(0).T
 
 
-def estimated_error_per_atom(h, spread):
-    """|dE| estimate per atom: sum_{i,u} |dE/d alpha_bar_i(u)| s_i(u) / N."""
-    return float(np.abs(h * spread).sum() / h.shape[1])
+def estimated_error_per_atom(h, alpha_u, ys, scale=1.0):
+    """|dE| estimate per atom: scale * std over members m of
+    D_m = sum_{u,i} h[u, i] alpha_u[u, i] (exp(y_m[i, u]) - mean_m' exp(y_m'[i, u])), over N.
+    h, alpha_u [16, N]; ys [M, N, 16]."""
+    v = np.exp(np.transpose(ys, (0, 2, 1)))                      # [M, 16, N]
+    D = (h[None] * alpha_u[None] * (v - v.mean(0))).sum(axis=(1, 2))
+    return float(scale * np.sqrt(np.mean(D ** 2)) / h.shape[1])
 
 
 # ---- per-frequency Dyson moments (the inputs a second feature set adds) -----------------

@@ -31,8 +31,8 @@ EXPORTS = ("mbd_default_options", "mbd_create", "mbd_destroy", "mbd_set_geometry
            "mbd_get_stats", "mbd_get_exception", "mbd_set_profiling", "mbd_get_profile",
            "mbdk_gemm_f64", "mbdk_gemm_tc", "mbdk_tc_wait_check", "mbdk_gemm_f64_split", "mbdk_gemm_f64_split_work_bytes", "mbdk_cholesky_f64", "mbdk_chol_solve3_f64",
            "mbdk_cholesky_solve3_f64_noalloc", "mbdk_scs_features", "mbdk_mlp_forward", "mbdk_mlp_backward",
-           "mbdk_mse_grad", "mbdk_adam_step", "mbdk_gather_rows")
-LEARNED_FEATURES, LEARNED_OUTPUTS, LEARNED_PARAMS = 74, 16, 28176
+           "mbdk_mse_grad", "mbdk_adam_step", "mbdk_learned_targets", "mbdk_gather_rows")
+LEARNED_FEATURES, LEARNED_OUTPUTS, LEARNED_PARAMS, LEARNED_WORK = 122, 16, 34320, 144
 
 
 class mbd_options(C.Structure):
@@ -40,7 +40,7 @@ class mbd_options(C.Structure):
                 ("precision", C.c_int), ("ns_tol", C.c_double), ("ns_max_iter", C.c_int),
                 ("tc_chunk_stages", C.c_int), ("ewald_gamma", C.c_double), ("real_cutoff", C.c_double),
                 ("recip_cutoff", C.c_double), ("scs_mode", C.c_int), ("learned_max_error", C.c_double),
-                ("mixed_max_error", C.c_double)]
+                ("mixed_max_error", C.c_double), ("learned_estimate_scale", C.c_double)]
 MBD_SCS_PLAIN, MBD_SCS_LEARNED, MBD_SCS_NL = 0, 1, 2
 
 
@@ -106,6 +106,7 @@ def load(path: str | None = None):
     L.mbdk_mse_grad.argtypes = [vp, ll, vp, vp, vp, vp]
     L.mbdk_adam_step.argtypes = [vp, ll, vp, vp, vp, vp, i, f, vp]
     L.mbdk_gather_rows.argtypes = [vp, ll, i, vp, vp, vp]
+    L.mbdk_learned_targets.argtypes = [vp, i, vp, vp, vp]
     L.mbdk_gemm_f64_split.argtypes = [vp, i, i, i, i, d, vp, ll, vp, ll, d, vp, ll, vp, ll, vp, vp]
     L.mbdk_gemm_f64_split_work_bytes.argtypes = [i, i, i]
     for name in EXPORTS:
@@ -143,7 +144,7 @@ class MBD:
                  ns_tol: float = 1e-8, ns_max_iter: int = 100, precision: int = MBD_PREC_FP64,
                  tc_chunk_stages: int | None = None, ewald_gamma: float = 0.0, real_cutoff: float = 0.0,
                  recip_cutoff: float = 0.0, scs_mode: int = MBD_SCS_PLAIN, learned_max_error: float = 1e-6,
-                 mixed_max_error: float = 1e-7):
+                 mixed_max_error: float = 1e-7, learned_estimate_scale: float = 1.0):
         self.lib = load()
         opt = mbd_options()
         self.lib.mbd_default_options(C.byref(opt))
@@ -154,6 +155,7 @@ class MBD:
         opt.ewald_gamma, opt.real_cutoff, opt.recip_cutoff = ewald_gamma, real_cutoff, recip_cutoff
         opt.scs_mode, opt.learned_max_error = scs_mode, learned_max_error
         opt.mixed_max_error = mixed_max_error
+        opt.learned_estimate_scale = learned_estimate_scale
         h = C.c_void_p()
         rc = self.lib.mbd_create(C.byref(h), device, C.byref(opt))
         if rc:
@@ -429,12 +431,12 @@ def _chk(rc, name):
 
 def mbdk_scs_features(offsets, coords, alpha0_ref, c6_ref, rvdw_ref, volume_ratio, X, work=None, stream=None):
     """Learned-model features X [n_atoms, LEARNED_FEATURES] (float32 CUDA) of systems stored
-    back to back (offsets int32 [n_systems + 1]); inputs float64 CUDA tensors; work [n_atoms, 6]
-    float64 scratch (allocated here with torch when not given)."""
+    back to back (offsets int32 [n_systems + 1]); inputs float64 CUDA tensors; work
+    [n_atoms, LEARNED_WORK] float64 scratch (allocated here with torch when not given)."""
     import torch
     L = load()
     if work is None:
-        work = torch.empty(X.shape[0], 6, dtype=torch.float64, device=X.device)
+        work = torch.empty(X.shape[0], LEARNED_WORK, dtype=torch.float64, device=X.device)
     _chk(L.mbdk_scs_features(_stream(X, stream), X.shape[0], offsets.shape[0] - 1, _tptr(offsets), _tptr(coords),
                              _tptr(alpha0_ref), _tptr(c6_ref), _tptr(rvdw_ref), _tptr(volume_ratio), _tptr(X),
                              _tptr(work)), "mbdk_scs_features")
@@ -464,6 +466,13 @@ def mbdk_adam_step(params, grad, m, v, step, lr, params16=None, stream=None):
     L = load()
     _chk(L.mbdk_adam_step(_stream(params, stream), params.numel(), _tptr(params), _tptr(grad), _tptr(m), _tptr(v),
                           int(step), float(lr), _tptr(params16)), "mbdk_adam_step")
+
+
+def mbdk_learned_targets(alpha_bar, alpha_free, Y, stream=None):
+    """Y [n_atoms, 16] (float32 CUDA) = log(alpha_bar / alpha_free) of [16, n_atoms] float64 CUDA tensors."""
+    L = load()
+    _chk(L.mbdk_learned_targets(_stream(Y, stream), Y.shape[0], _tptr(alpha_bar), _tptr(alpha_free), _tptr(Y)),
+         "mbdk_learned_targets")
 
 
 def mbdk_gather_rows(idx, src, dst, stream=None):

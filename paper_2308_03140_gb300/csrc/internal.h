@@ -145,7 +145,7 @@ void trsv_blocked(const T *L, long long ld, long long mstride, int batch, const 
 // (TF32x3, k_tc_gemm, tiles of the lower triangle only).  panel: scratch of
 // 2 * batch * ld * kScsPanel 32-bit words.  Only the lower triangle of A32 is read or
 // written.  Tensor-core timeouts set ST_TC_TIMEOUT in *status; a launch error is returned.
-constexpr int kScsPanel = 512;
+constexpr int kScsPanel = 1024;
 cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv,
                                   uint32_t *panel, int *status, cudaStream_t s);
 void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,
@@ -314,9 +314,11 @@ void energy_trace_periodic(const double *Y, long long ld, int n, int nk, const d
 // g_ombar, g_abar0, g_rbar, gR (o), and dE/dA accumulated into gA [9].  work: 2N doubles.
 // tq: (1/nk) sum_q Re Tr (Q(q)^{1/2})_ii per atom for dE/d omega_bar (second order in the error of
 // Z), or NULL to take it from Z.
+// f32_recip: the reciprocal-space sum in FP32 (chunk sums added in FP64), for the mixed
+// modes, whose Z ~ Q^{-1/2} is accurate to far less than FP32 rounding.
 void periodic_mbd_grad(const AtomBufs &b, const PeriodicBufs &p, double beta, double a, const double *Z,
                        long long ld, double zscale, const MbdGradOut &o, double *work, double *gA, cudaStream_t s,
-                       const double *tq = nullptr);
+                       const double *tq = nullptr, bool f32_recip = false);
 // out[i] = (1/rows) sum_r x[r][i] for a rows x N array (compensated).
 void mean_rows(const double *x, int rows, int N, double *out, cudaStream_t s);
 // SCS adjoint pair pass over lattice images (as scs_grad_pass), with the lattice part
@@ -333,12 +335,18 @@ void ts_periodic(const AtomBufs &b, const PeriodicBufs &p, double s_r, double *t
                  double *ga0, double *gom, double *grv, double *gA_part, double *gA, int *status, cudaStream_t s);
 
 // ---- learned screening model (k_learned.cu) ---------------------------------------
+// FP64 words per atom of the features' work (scs_features: static moments, then the FP32
+// state of the Dyson block) and of the learned forces' work (learned_forces).
+constexpr int kLearnedWork = 144;
+constexpr int kLearnedAdjointWork = 243;
 int learned_param_count();
 void scs_features(int n_atoms, int n_sys, const int *offsets, const double *R, const double *a0ref,
                   const double *c6ref, const double *rref, const double *ratio, float *X, double *work,
                   cudaStream_t s);
+// MLP forward on the tensor cores; err (optional, device int) receives ST_TC_TIMEOUT if a wait
+// runs out (the outputs are then NaN).
 cudaError_t mlp_forward(int B, int members, const float *X, const float *mean, const float *stdv,
-                        const void *params16, float *Y, float *zcache, cudaStream_t s);
+                        const void *params16, float *Y, float *zcache, cudaStream_t s, int *err = nullptr);
 cudaError_t mlp_backward(int B, int members, const float *X, const float *mean, const float *stdv,
                          const void *params16, const float *zcache, const float *dY, float *dX, float *grad,
                          cudaStream_t s);
@@ -351,12 +359,16 @@ void gather_rows(long long rows, int width, const int *idx, const float *src, fl
 void learned_alpha(int N, int members, int nf1, const double *al_u, const float *Y, double *abar, double *spread,
                    cudaStream_t s);
 // Learned path gradients: dY[m][i][k] = h[k][i] alpha_bar[k][i] / members (member outputs'
-// upstream gradient); gR[i] += dE/dR_i through the features, from dX [members][N][74]
-// (mlp_backward), the moments M [N][6] of scs_features and workspace adjoint [N][6].
+// upstream gradient); gR[i] += dE/dR_i through the features of one system (offsets [0, N]),
+// from dX [members][N][122] (mlp_backward), the work [N][kLearnedWork] that scs_features
+// filled and workspace adjoint [N][kLearnedAdjointWork].
 void learned_dy(int N, int members, int nf1, const double *h, const double *abar, float *dY, cudaStream_t s);
-void learned_forces(int N, const double *R, const double *a0ref, const double *rref, const double *ratio,
-                    const double *moments, const float *dX, int members, double *adjoint, double *gR, cudaStream_t s);
-// out[0] = sum_{k,i} |h[k][i]| spread[k][i] / N (the energy-error estimate per atom).
-void learned_estimate(int N, int nf1, const double *h, const double *spread, double *out, cudaStream_t s);
+void learned_forces(int N, const int *offsets, const double *R, const double *a0ref, const double *rref,
+                    const double *ratio, double *work, const float *dX, int members, double *adjoint, double *gR,
+                    cudaStream_t s);
+// out[0] = scale std_m(D_m) / N, D_m = sum_{k,i} h[k][i] alpha_i(u_k) (e^{Y[m][i][k]} - its mean over
+// the members): the energy-error estimate per atom from the members' first-order energies.
+void learned_estimate(int N, int nf1, int members, double scale, const double *h, const double *al_u,
+                      const float *Y, double *out, cudaStream_t s);
 
 }  // namespace mbdgb

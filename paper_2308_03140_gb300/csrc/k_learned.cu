@@ -9,23 +9,32 @@
 //     static screening moments: M_i = sum_j alpha0_j B_ij, B_ij = (1 - f_ij) T^GG_ij at u = 0
 //     (Eqs. scs-sr-dipole, tgg, mayer, fermi-damping), m1 = Tr M_i / 3,
 //     m2 = Tr(sum_j alpha0_j B_ij M_j) / 3, m3 = Tr(M_i M_i) / 3, and alpha0_i m1,
-//     alpha0_i^2 m2, alpha0_i^2 m3;
-//   MLP 74 -> 128 -> 128 -> 16 on standardised features, SiLU activations, FP16 weights and
+//     alpha0_i^2 m2, alpha0_i^2 m3; then (48 more) the terms of the Dyson series of Eq. scs at
+//     the 16 grid points u_k (u_0 = 0 and the 15 Casimir-Polder nodes): with alpha_j(u) of
+//     Eq. dyn-pol, B_ij(u) = (1 - f_ij) T^GG_ij at the widths of alpha(u), H^(0)_i = I and
+//     H^(q)_i = sum_{j != i} alpha_j(u) B_ij(u) H^(q-1)_j, feature 74 + 3 k + q - 1 is
+//     m_q,i(u_k) = Tr H^(q)_i / 3 (q = 1, 2, 3; all atoms of the system, no cutoff; FP32
+//     pair arithmetic, FP64 warp sums);
+//   MLP 122 -> 128 -> 128 -> 16 on standardised features, SiLU activations, FP16 weights and
 //     biases, FP32 accumulation; output y_k = log(alpha_bar(u_k) / alpha(u_k)).
-// Parameter layout of one ensemble member (FP16): W1 [74][128], b1 [128], W2 [128][128],
+// Parameter layout of one ensemble member (FP16): W1 [122][128], b1 [128], W2 [128][128],
 // b2 [128], W3 [128][16], b3 [16] (W[in][out], row-major), kParams halves in all.
 #include <cuda_fp16.h>
 
+#include "freq_grid.h"
 #include "internal.h"
 #include "pair_math.cuh"
+#include "tc_ops.cuh"
 
 namespace mbdgb {
 namespace {
 
+using namespace tcops;
 using pairs::Fermi;
 using pairs::Radial;
 
-constexpr int kF = 74, kH = 128, kO = 16;
+constexpr int kFS = 74, kNU = 16, kNQ = 3;   // static features; grid points and hops of the Dyson block
+constexpr int kF = kFS + kNU * kNQ, kH = 128, kO = 16;
 constexpr int oW1 = 0, ob1 = oW1 + kF * kH, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
               ob3 = oW3 + kH * kO, kParams = ob3 + kO;
 constexpr int kTA = 32;          // atoms per CTA of the MLP kernels
@@ -70,33 +79,43 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// One warp per atom; lane l accumulates Gaussians l and l + 32, and the lanes share the
-// partner atoms for the moment M_i (written to Mw [n_atoms][6], FP64).
-__global__ void k_features(int n_atoms, int n_sys, const int *offsets, const double *R, const double *a0ref,
-                           const double *c6ref, const double *rref, const double *ratio, float *X, double *Mw) {
-    const int atom = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (atom >= n_atoms) return;
+__device__ __forceinline__ double block_sum128(double v, double *sh) {   // 128 threads, result in all
+    v = warp_sum_d(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    return sh[0] + sh[1] + sh[2] + sh[3];
+}
+
+// One CTA of 128 threads per atom.  Thread t accumulates Gaussian t % 64 over the partners
+// j = j0 + t / 64, + 2, ... (the Gaussian in FP32 from the FP64 distance offset d - mu, the sum in
+// FP64); the threads also share the partners of the moment M_i (FP64, written to Mw [n][6]).
+__global__ void __launch_bounds__(128) k_features(int n_atoms, int n_sys, const int *offsets, const double *R,
+                                                  const double *a0ref, const double *c6ref, const double *rref,
+                                                  const double *ratio, float *X, double *Mw) {
+    __shared__ double part[2][64];
+    __shared__ double red[4];
+    const int atom = blockIdx.x, t = threadIdx.x;
     const int s = system_of(offsets, n_sys, atom);
     const int j0 = offsets[s], j1 = offsets[s + 1];
     const double xi = R[3 * atom], yi = R[3 * atom + 1], zi = R[3 * atom + 2];
-    const double mu0 = (lane + 0.5) * kWidth, mu1 = (lane + 32.5) * kWidth, i2w2 = 0.5 / (kWidth * kWidth);
-    double acc0 = 0.0, acc1 = 0.0;
-    for (int j = j0; j < j1; ++j) {
+    const int gidx = t & 63;
+    const double mu = (gidx + 0.5) * kWidth;
+    const float i2w2 = static_cast<float>(0.5 / (kWidth * kWidth));
+    double acc = 0.0;
+    for (int j = j0 + (t >> 6); j < j1; j += 2) {
         if (j == atom) continue;
         const double dx = R[3 * j] - xi, dy = R[3 * j + 1] - yi, dz = R[3 * j + 2] - zi;
         const double d = sqrt(dx * dx + dy * dy + dz * dz);
         if (d >= kCut) continue;
-        const double w = a0ref[j] * ratio[j] * 0.5 * (1.0 + cos(kPiL * d / kCut));
-        acc0 += w * exp(-(d - mu0) * (d - mu0) * i2w2);
-        acc1 += w * exp(-(d - mu1) * (d - mu1) * i2w2);
+        const float w = static_cast<float>(a0ref[j] * ratio[j]) * 0.5f * (1.0f + cospif(static_cast<float>(d / kCut)));
+        const float u = static_cast<float>(d - mu);
+        acc += static_cast<double>(w * expf(-u * u * i2w2));
     }
-    float *x = X + static_cast<long long>(atom) * kF;
-    x[lane] = static_cast<float>(acc0);
-    x[lane + 32] = static_cast<float>(acc1);
+    part[t >> 6][gidx] = acc;
     const double a0i = a0ref[atom] * ratio[atom], rvi = rref[atom] * cbrt(ratio[atom]);
     double M[6] = {0, 0, 0, 0, 0, 0};
-    for (int j = j0 + lane; j < j1; j += 32) {
+    for (int j = j0 + t; j < j1; j += 128) {
         if (j == atom) continue;
         const double r[3] = {R[3 * j] - xi, R[3 * j + 1] - yi, R[3 * j + 2] - zi};
         const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
@@ -106,8 +125,10 @@ __global__ void k_features(int n_atoms, int n_sys, const int *offsets, const dou
         scs_coupling(r, d, a0i, a0j, rvi, rref[j] * cbrt(ratio[j]), B);
         for (int e = 0; e < 6; ++e) M[e] += a0j * B[e];
     }
-    for (int e = 0; e < 6; ++e) M[e] = warp_sum_d(M[e]);
-    if (lane == 0) {
+    for (int e = 0; e < 6; ++e) M[e] = block_sum128(M[e], red);
+    float *x = X + static_cast<long long>(atom) * kF;
+    if (t < 64) x[t] = static_cast<float>(part[0][t] + part[1][t]);
+    if (t == 0) {
         const double a0r = a0ref[atom], v = ratio[atom];
         x[64] = static_cast<float>(a0i);
         x[65] = static_cast<float>(4.0 * c6ref[atom] / (3.0 * a0r * a0r));
@@ -156,6 +177,303 @@ __global__ void k_feature_moments(int n_atoms, int n_sys, const int *offsets, co
     }
 }
 
+// ---- Dyson block of the features (per grid point; FP32 pair arithmetic) -----------------
+// Work of the forward pass (FP32, after the n x 6 FP64 static moments): P [n] (TS-scaled
+// alpha0, omega, R_vdW), AS [16][n] (alpha(u_k), sigma(u_k)^2), H1 [16][n][6] (symmetric
+// H^(1)), H2 [16][n][9] (H^(2), row-major).  The backward adds GQ [16][n] (dL/dm_q, q = 1..3),
+// G2 [16][n][6] and G1 [16][n][9] (adjoints of H^(2), H^(1)) and FP [16][n][3] (FP64 partial
+// forces per grid point).
+struct GridU2 { float u2[kNU]; };
+struct DysonFwd {
+    float4 *P;
+    float2 *AS;
+    float *H1, *H2;
+};
+__host__ __device__ inline DysonFwd dyson_fwd(double *work, int n) {
+    float *f = reinterpret_cast<float *>(work + 6LL * n);
+    DysonFwd w;
+    w.P = reinterpret_cast<float4 *>(f);
+    w.AS = reinterpret_cast<float2 *>(f + 4LL * n);
+    w.H1 = f + 36LL * n;
+    w.H2 = f + 132LL * n;
+    return w;
+}
+struct DysonAdj {
+    float4 *GQ;
+    float *G2, *G1;
+    double *FP;
+};
+__host__ __device__ inline DysonAdj dyson_adj(double *adj, int n) {
+    float *f = reinterpret_cast<float *>(adj + 6LL * n);
+    DysonAdj w;
+    w.GQ = reinterpret_cast<float4 *>(f);
+    w.G2 = f + 64LL * n;
+    w.G1 = f + 160LL * n;
+    w.FP = adj + 6LL * n + 152LL * n;
+    return w;
+}
+static_assert(6 + 276 / 2 == kLearnedWork, "forward work per atom");
+static_assert(6 + 304 / 2 + 48 + 37 == kLearnedAdjointWork, "adjoint work per atom");
+
+// 1 - f of the Fermi damping (beta 0.83, a 6) as e / (1 + e), e = exp(-a (d / (beta S) - 1)), and
+// its derivative in d: the small values far beyond the damping radius keep their digits.
+struct DampF { float sr, dsr; };
+__device__ __forceinline__ DampF damp_f(float d, float S) {
+    const float bS = 0.83f * S, e = expf(-6.0f * (d / bS - 1.0f));
+    const float f = 1.0f / (1.0f + e), sr = e * f;
+    return {sr, -6.0f * f * sr / bS};
+}
+
+// B = (1 - f) T^GG at separation r (|r| = d), width sqrt(sig2), as xx, yy, zz, xy, xz, yz.
+__device__ __forceinline__ void dyson_coupling(const float *r, float d, float S, float sig2, float *B) {
+    const DampF g = damp_f(d, S);
+    const pairs::RadialF t = pairs::tgg_radial_f(d, sqrtf(sig2));
+    const float P = g.sr * t.P, W = g.sr * t.W;
+    B[0] = P + W * r[0] * r[0];
+    B[1] = P + W * r[1] * r[1];
+    B[2] = P + W * r[2] * r[2];
+    B[3] = W * r[0] * r[1];
+    B[4] = W * r[0] * r[2];
+    B[5] = W * r[1] * r[2];
+}
+
+// sym 3x3 (6) times sym 3x3 (6) -> general row-major (9)
+__device__ __forceinline__ void symsym(const float *A, const float *B, float *C) {
+    const float a[9] = {A[0], A[3], A[4], A[3], A[1], A[5], A[4], A[5], A[2]};
+    const float b[9] = {B[0], B[3], B[4], B[3], B[1], B[5], B[4], B[5], B[2]};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) C[3 * r + c] = a[3 * r] * b[c] + a[3 * r + 1] * b[3 + c] + a[3 * r + 2] * b[6 + c];
+}
+
+// The warp of grid point k and atom i: e = k n + i over the 16 n warps (consecutive warps take
+// consecutive atoms of one grid point, so a CTA's warps read the same partner data).
+struct WarpItem { int k, i, j0, j1; bool ok; };
+__device__ __forceinline__ WarpItem warp_item(int n, int n_sys, const int *offsets) {
+    const long long e = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    WarpItem w{0, 0, 0, 0, false};
+    if (e >= static_cast<long long>(kNU) * n) return w;
+    w.k = static_cast<int>(e / n);
+    w.i = static_cast<int>(e % n);
+    const int s = system_of(offsets, n_sys, w.i);
+    w.j0 = offsets[s];
+    w.j1 = offsets[s + 1];
+    w.ok = true;
+    return w;
+}
+__device__ __forceinline__ void sep(const double *R, int i, int j, float *r, float &d) {
+    r[0] = static_cast<float>(R[3 * j] - R[3 * i]);
+    r[1] = static_cast<float>(R[3 * j + 1] - R[3 * i + 1]);
+    r[2] = static_cast<float>(R[3 * j + 2] - R[3 * i + 2]);
+    d = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+}
+template <int M>
+__device__ __forceinline__ void warp_sum_store(const float *acc, float *out) {   // FP64 sums over the lanes
+#pragma unroll
+    for (int e = 0; e < M; ++e) {
+        const double v = warp_sum_d(static_cast<double>(acc[e]));
+        if ((threadIdx.x & 31) == 0) out[e] = static_cast<float>(v);
+    }
+}
+
+// P and AS: thread per (k, i).
+__global__ void k_dyson_prep(int n, const double *a0ref, const double *c6ref, const double *rref, const double *ratio,
+                             GridU2 g, double *work) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e >= static_cast<long long>(kNU) * n) return;
+    const int k = static_cast<int>(e / n), i = static_cast<int>(e % n);
+    const DysonFwd w = dyson_fwd(work, n);
+    const double a0 = a0ref[i] * ratio[i], om = 4.0 * c6ref[i] / (3.0 * a0ref[i] * a0ref[i]);
+    if (k == 0) w.P[i] = make_float4(static_cast<float>(a0), static_cast<float>(om),
+                                     static_cast<float>(rref[i] * cbrt(ratio[i])), 0.0f);
+    const double al = a0 / (1.0 + static_cast<double>(g.u2[k]) / (om * om));
+    const double sg = cbrt(sqrt(2.0 / kPiL) / 3.0 * al);
+    w.AS[e] = make_float2(static_cast<float>(al), static_cast<float>(sg * sg));
+}
+
+// Trace of B = (1 - f) T^GG at width sqrt(sig2): T^GG's trace is its Gaussian part alone,
+// 2 z^2 th / d^3 (z = d / s, th = 2 z e^{-z^2} / sqrt(pi)), which the sum of its diagonal in FP32
+// would leave to the cancellation of 3 P against W d^2.
+__device__ __forceinline__ float dyson_trace(float d, float S, float sig2) {
+    const float z = d * rsqrtf(sig2);
+    if (z > pairs::kGaussFarF) return 0.0f;
+    const float th = 1.1283791670955126f * z * expf(-z * z);
+    return damp_f(d, S).sr * 2.0f * z * z * th / (d * d * d);
+}
+
+// HOP 1: H1_i = sum_j alpha_j B_ij (its trace from dyson_trace); HOP 2: H2_i = sum_j alpha_j
+// B_ij H1_j; HOP 3: the trace of sum_j alpha_j B_ij H2_j.  X[i][74 + 3k + HOP - 1] = Tr / 3.
+template <int HOP>
+__global__ void k_dyson_hop(int n, int n_sys, const int *offsets, const double *R, double *work, float *X) {
+    const WarpItem it = warp_item(n, n_sys, offsets);
+    if (!it.ok) return;
+    const int lane = threadIdx.x & 31, i = it.i, k = it.k;
+    const DysonFwd w = dyson_fwd(work, n);
+    const float rvi = w.P[i].z, sgi = w.AS[static_cast<long long>(k) * n + i].y;
+    constexpr int M = HOP == 1 ? 7 : (HOP == 2 ? 9 : 1);   // HOP 1: H1 and its trace
+    float acc[M];
+#pragma unroll
+    for (int e = 0; e < M; ++e) acc[e] = 0.0f;
+    for (int j = it.j0 + lane; j < it.j1; j += 32) {
+        if (j == i) continue;
+        float r[3], d, B[6];
+        sep(R, i, j, r, d);
+        const float2 as = w.AS[static_cast<long long>(k) * n + j];
+        dyson_coupling(r, d, rvi + w.P[j].z, sgi + as.y, B);
+        if (HOP == 1) {
+#pragma unroll
+            for (int e = 0; e < 6; ++e) acc[e] += as.x * B[e];
+            acc[6] += as.x * dyson_trace(d, rvi + w.P[j].z, sgi + as.y);
+        } else if (HOP == 2) {
+            const float *h = w.H1 + (static_cast<long long>(k) * n + j) * 6;
+            const float hj[6] = {h[0], h[1], h[2], h[3], h[4], h[5]};
+            float BH[9];
+            symsym(B, hj, BH);
+#pragma unroll
+            for (int e = 0; e < 9; ++e) acc[e] += as.x * BH[e];
+        } else {
+            const float *h = w.H2 + (static_cast<long long>(k) * n + j) * 9;   // Tr(B H) = sum B o H (B symmetric)
+            acc[0] += as.x * (B[0] * h[0] + B[1] * h[4] + B[2] * h[8] + B[3] * (h[1] + h[3]) + B[4] * (h[2] + h[6]) +
+                              B[5] * (h[5] + h[7]));
+        }
+    }
+    float out[M];
+    warp_sum_store<M>(acc, out);
+    if (lane == 0) {
+        float tr;
+        if (HOP == 1) {
+            float *h = w.H1 + (static_cast<long long>(k) * n + i) * 6;
+            for (int e = 0; e < 6; ++e) h[e] = out[e];
+            tr = out[6];
+        } else if (HOP == 2) {
+            float *h = w.H2 + (static_cast<long long>(k) * n + i) * 9;
+            for (int e = 0; e < 9; ++e) h[e] = out[e];
+            tr = out[0] + out[4] + out[8];
+        } else {
+            tr = out[0];
+        }
+        X[static_cast<long long>(i) * kF + kFS + 3 * k + HOP - 1] = tr / 3.0f;
+    }
+}
+
+// Backward of L = sum_{i,k,q} g_q,i(k) m_q,i(k), g = the members' summed feature gradient:
+// GQ [k][i] = (g1, g2, g3).
+__global__ void k_dyson_adj_prep(int n, int members, const float *dX, double *adj) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e >= static_cast<long long>(kNU) * n) return;
+    const int k = static_cast<int>(e / n), i = static_cast<int>(e % n);
+    float g[3] = {0.0f, 0.0f, 0.0f};
+    for (int m = 0; m < members; ++m)
+        for (int q = 0; q < 3; ++q) g[q] += dX[(static_cast<long long>(m) * n + i) * kF + kFS + 3 * k + q];
+    dyson_adj(adj, n).GQ[e] = make_float4(g[0], g[1], g[2], 0.0f);
+}
+
+// Adjoints of the hops (B_li = B_il): STEP 2: G2_i = g2_i I/3 + alpha_i sum_l B_il g3_l / 3
+// (symmetric); STEP 1: G1_i = g1_i I/3 + alpha_i sum_l B_il G2_l.
+template <int STEP>
+__global__ void k_dyson_adj(int n, int n_sys, const int *offsets, const double *R, double *work, double *adj) {
+    const WarpItem it = warp_item(n, n_sys, offsets);
+    if (!it.ok) return;
+    const int lane = threadIdx.x & 31, i = it.i, k = it.k;
+    const DysonFwd w = dyson_fwd(work, n);
+    const DysonAdj a = dyson_adj(adj, n);
+    const float rvi = w.P[i].z;
+    const float2 asi = w.AS[static_cast<long long>(k) * n + i];
+    constexpr int M = STEP == 2 ? 6 : 9;
+    float acc[M];
+#pragma unroll
+    for (int e = 0; e < M; ++e) acc[e] = 0.0f;
+    for (int l = it.j0 + lane; l < it.j1; l += 32) {
+        if (l == i) continue;
+        float r[3], d, B[6];
+        sep(R, i, l, r, d);
+        dyson_coupling(r, d, rvi + w.P[l].z, asi.y + w.AS[static_cast<long long>(k) * n + l].y, B);
+        if (STEP == 2) {
+            const float g3 = a.GQ[static_cast<long long>(k) * n + l].z / 3.0f;
+#pragma unroll
+            for (int e = 0; e < 6; ++e) acc[e] += g3 * B[e];
+        } else {
+            const float *g = a.G2 + (static_cast<long long>(k) * n + l) * 6;
+            const float gl[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
+            float BG[9];
+            symsym(B, gl, BG);
+#pragma unroll
+            for (int e = 0; e < 9; ++e) acc[e] += BG[e];
+        }
+    }
+    float out[M];
+    warp_sum_store<M>(acc, out);
+    if (lane == 0) {
+        const float4 gq = a.GQ[static_cast<long long>(k) * n + i];
+        const float diag = (STEP == 2 ? gq.y : gq.x) / 3.0f;
+        if (STEP == 2) {
+            float *g = a.G2 + (static_cast<long long>(k) * n + i) * 6;
+            for (int e = 0; e < 6; ++e) g[e] = asi.x * out[e] + (e < 3 ? diag : 0.0f);
+        } else {
+            float *g = a.G1 + (static_cast<long long>(k) * n + i) * 9;
+            for (int e = 0; e < 9; ++e) g[e] = asi.x * out[e] + (e % 4 == 0 ? diag : 0.0f);
+        }
+    }
+}
+
+// Abar_ij = dL/dA_ij (A_ij = alpha_j B_ij) = G1_i + G2_i H1_j + (g3_i / 3) H2_j^T (row-major).
+__device__ __forceinline__ void abar(const float *G1, const float *G2, float g3, const float *H1, const float *H2,
+                                     float *out) {
+    float GH[9];
+    symsym(G2, H1, GH);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[3 * r + c] = G1[3 * r + c] + GH[3 * r + c] + g3 * H2[3 * c + r];
+}
+
+// FP[k][i] = dL/dR_i through grid point k: -sum_j <C_ij, dB/dr (r = R_j - R_i)> with C_ij the
+// symmetric part of alpha_j Abar_ij + alpha_i Abar_ji.
+__global__ void k_dyson_forces(int n, int n_sys, const int *offsets, const double *R, double *work, double *adj) {
+    const WarpItem it = warp_item(n, n_sys, offsets);
+    if (!it.ok) return;
+    const int lane = threadIdx.x & 31, i = it.i, k = it.k;
+    const DysonFwd w = dyson_fwd(work, n);
+    const DysonAdj a = dyson_adj(adj, n);
+    const long long ki = static_cast<long long>(k) * n + i;
+    const float rvi = w.P[i].z;
+    const float2 asi = w.AS[ki];
+    float G1i[9], G2i[6], H1i[6], H2i[9];
+    for (int e = 0; e < 9; ++e) G1i[e] = a.G1[ki * 9 + e], H2i[e] = w.H2[ki * 9 + e];
+    for (int e = 0; e < 6; ++e) G2i[e] = a.G2[ki * 6 + e], H1i[e] = w.H1[ki * 6 + e];
+    const float g3i = a.GQ[ki].z / 3.0f;
+    float f[3] = {0.0f, 0.0f, 0.0f};
+    for (int j = it.j0 + lane; j < it.j1; j += 32) {
+        if (j == i) continue;
+        const long long kj = static_cast<long long>(k) * n + j;
+        float r[3], d;
+        sep(R, i, j, r, d);
+        const float2 asj = w.AS[kj];
+        float Aij[9], Aji[9];
+        abar(G1i, G2i, g3i, w.H1 + kj * 6, w.H2 + kj * 9, Aij);
+        abar(a.G1 + kj * 9, a.G2 + kj * 6, a.GQ[kj].z / 3.0f, H1i, H2i, Aji);
+        float M[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) M[e] = asj.x * Aij[e] + asi.x * Aji[e];
+        const float C[6] = {M[0], M[4], M[8], 0.5f * (M[1] + M[3]), 0.5f * (M[2] + M[6]), 0.5f * (M[5] + M[7])};
+        // <C, B> = sr (P tr C + W r.C.r); its gradient in r
+        const DampF g = damp_f(d, rvi + w.P[j].z);
+        const pairs::RadialF t = pairs::tgg_radial_f(d, sqrtf(asi.y + asj.y));
+        const float Cr[3] = {C[0] * r[0] + C[3] * r[1] + C[4] * r[2], C[3] * r[0] + C[1] * r[1] + C[5] * r[2],
+                             C[4] * r[0] + C[5] * r[1] + C[2] * r[2]};
+        const float tr = C[0] + C[1] + C[2], rCr = r[0] * Cr[0] + r[1] * Cr[1] + r[2] * Cr[2];
+        const float ir = 1.0f / d, CT = t.P * tr + t.W * rCr;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            f[c] -= g.dsr * r[c] * ir * CT + g.sr * ((t.dP * tr + t.dW * rCr) * r[c] * ir + 2.0f * t.W * Cr[c]);
+    }
+    for (int c = 0; c < 3; ++c) {
+        const double v = warp_sum_d(static_cast<double>(f[c]));
+        if (lane == 0) a.FP[ki * 3 + c] = v;
+    }
+}
+
 // Shared layout of the MLP kernels: weights (FP16), standardised inputs, two hidden layers.
 struct MlpSmem {
     __half *W;
@@ -182,59 +500,139 @@ __device__ __forceinline__ void load_params_and_inputs(const MlpSmem &m, const _
     __syncthreads();
 }
 
-// z1, h1 and z2, h2 for the CTA's atoms (thread t owns hidden unit t).
-__device__ __forceinline__ void hidden_layers(const MlpSmem &m, float *z1_out, float *z2_out, int a0, int B) {
-    const int t = threadIdx.x;
-    float acc[kTA];
-    const float b1 = __half2float(m.W[ob1 + t]);
-#pragma unroll
-    for (int a = 0; a < kTA; ++a) acc[a] = b1;
-    for (int k = 0; k < kF; ++k) {
-        const float w = __half2float(m.W[oW1 + k * kH + t]);
-#pragma unroll
-        for (int a = 0; a < kTA; ++a) acc[a] += m.Xs[a * kF + k] * w;
+// ---- MLP forward on the tensor cores (tcgen05, kind::tf32) ---------------------------------
+// One CTA of 128 threads per 128 atoms and ensemble member; thread t owns atom a0 + t, which is
+// TMEM lane t of the accumulator.  Each layer Z = H W + b (M = 128 atoms, K = 128 inputs, the
+// 122 features padded with zeros, N = 128 or 16) is one chain of tcgen05.mma: the FP32
+// activations as TF32 hi + lo parts (hi = rna(h), lo = rna(h - hi)) against the weights,
+// whose FP16 values are exact in TF32, H_hi W + H_lo W accumulated in TMEM.  The operands are
+// written to shared memory by the threads in the K-major 128-byte-swizzled layout: element
+// (row r, k) in slab k / 32 (r x 128 bytes each), 16-byte chunk ((k % 32) / 4) xor (r % 8).
+constexpr int kMT = 128;                 // atoms per CTA
+constexpr int kSlab = kMT * 128;         // bytes of one 32-element K slab of a 128-row operand
+constexpr size_t kMlpTcSmem = 3 * 4 * static_cast<size_t>(kSlab) + 1024 + 64;
+static_assert(kF <= 128 && kH == 128 && kO == 16, "layer shapes of the tensor-core MLP");
+
+__device__ __forceinline__ uint32_t swz(int r, int k) {
+    const int kk = k & 31;
+    return static_cast<uint32_t>((k >> 5) * kSlab + r * 128 + ((((kk >> 2) ^ (r & 7)) << 4) | ((kk & 3) << 2)));
+}
+__host__ __device__ constexpr uint32_t mlp_idesc(int n) {   // FP32 accumulator, TF32 A and B, K-major, M = 128
+    return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(kMT >> 4) << 24);
+}
+__device__ __forceinline__ void mlp_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void put_split(uint8_t *hi, uint8_t *lo, int r, int k, float v) {
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v));
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(l) : "f"(v - __uint_as_float(h)));
+    *reinterpret_cast<uint32_t *>(hi + swz(r, k)) = h;
+    *reinterpret_cast<uint32_t *>(lo + swz(r, k)) = l;
+}
+// B operand of a layer: row n = output unit, K = input (W is stored [in][out]); rows n < nout.
+__device__ __forceinline__ void put_weights(uint8_t *Bs, const __half *W, int nin, int nout) {
+    for (int e = threadIdx.x; e < nout * 128; e += blockDim.x) {
+        const int k = e / nout, n = e % nout;   // consecutive threads: consecutive outputs of one input
+        const float w = k < nin ? __half2float(W[k * nout + n]) : 0.0f;
+        *reinterpret_cast<float *>(Bs + swz(n, k)) = w;
     }
-#pragma unroll
-    for (int a = 0; a < kTA; ++a) {
-        m.h1[a * kH + t] = silu(acc[a]);
-        if (z1_out && a0 + a < B) z1_out[static_cast<long long>(a0 + a) * kH + t] = acc[a];
-    }
+}
+// The layer's MMA chain (one thread) and its completion on bar; all threads wait (bounded).
+__device__ __forceinline__ bool mlp_layer(uint32_t tmem, uint8_t *Ahi, uint8_t *Alo, uint8_t *Bs, int n,
+                                          uint64_t *bar, uint32_t phase, int *err) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    fence_before();
     __syncthreads();
-    const float b2 = __half2float(m.W[ob2 + t]);
-#pragma unroll
-    for (int a = 0; a < kTA; ++a) acc[a] = b2;
-    for (int k = 0; k < kH; ++k) {
-        const float w = __half2float(m.W[oW2 + k * kH + t]);
-#pragma unroll
-        for (int a = 0; a < kTA; ++a) acc[a] += m.h1[a * kH + k] * w;
+    fence_after();
+    if (threadIdx.x == 0) {
+        const uint32_t id = mlp_idesc(n);
+        for (int sl = 0; sl < 4; ++sl)
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t b = sdesc(su32(Bs + sl * kSlab + kk * 32));   // rows n < N of each slab
+                mlp_mma(tmem, sdesc(su32(Ahi + sl * kSlab + kk * 32)), b, id, (sl | kk) != 0 ? 1u : 0u);
+                mlp_mma(tmem, sdesc(su32(Alo + sl * kSlab + kk * 32)), b, id, 1u);
+            }
+        mma_commit(bar);
     }
-#pragma unroll
-    for (int a = 0; a < kTA; ++a) {
-        m.h2[a * kH + t] = silu(acc[a]);
-        if (z2_out && a0 + a < B) z2_out[static_cast<long long>(a0 + a) * kH + t] = acc[a];
-    }
-    __syncthreads();
+    const bool ok = mbar_wait(bar, phase, err);
+    fence_after();
+    return __syncthreads_and(ok) != 0;   // uniform over the CTA: every later barrier is reached by all
 }
 
-// grid (ceil(B / 32), members), 128 threads.  Y [member][B][16]; optional cache
-// z [member][2][B][128] (pre-activations of both hidden layers).
-__global__ void __launch_bounds__(128) k_mlp_forward(int B, const float *X, const float *mean, const float *stdv,
-                                                     const __half *params, float *Y, float *zcache) {
-    extern __shared__ __align__(16) char smem[];
-    const MlpSmem m = mlp_smem(smem);
-    const int member = blockIdx.y, a0 = blockIdx.x * kTA, t = threadIdx.x;
-    load_params_and_inputs(m, params + static_cast<long long>(member) * kParams, X, mean, stdv, a0, B);
+// grid (ceil(B / 128), members), 128 threads.  Y [member][B][16]; optional cache
+// z [member][2][B][128] (pre-activations of both hidden layers).  A wait that times out raises
+// ST_TC_TIMEOUT in *err and leaves NaN outputs.
+__global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(int B, const float *X, const float *mean,
+                                                           const float *stdv, const __half *params, float *Y,
+                                                           float *zcache, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *Ahi = smem, *Alo = smem + 4 * kSlab, *Bs = smem + 8 * kSlab;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 12 * kSlab);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int member = blockIdx.y, t = threadIdx.x, warp = t >> 5, a = blockIdx.x * kMT + t;
+    const __half *P = params + static_cast<long long>(member) * kParams;
+    if (t == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
+                     "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    // layer 1 operands: standardised features of this thread's atom, W1
+    for (int k = 0; k < 128; ++k) {
+        const float x = (a < B && k < kF) ? (X[static_cast<long long>(a) * kF + k] - mean[k]) / stdv[k] : 0.0f;
+        put_split(Ahi, Alo, t, k, x);
+    }
+    put_weights(Bs, P + oW1, kF, kH);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot + (static_cast<uint32_t>(warp * 32) << 16);
     float *z1 = zcache ? zcache + static_cast<long long>(member) * 2 * B * kH : nullptr;
     float *z2 = zcache ? z1 + static_cast<long long>(B) * kH : nullptr;
-    hidden_layers(m, z1, z2, a0, B);
-    // output layer: thread t computes (atom t / 16 + 8 q, output t % 16), q = 0..3
-    const int o = t % kO;
-    const float b3 = __half2float(m.W[ob3 + o]);
-    for (int q = 0; q < kTA * kO / 128; ++q) {
-        const int a = t / kO + 8 * q;
-        float acc = b3;
-        for (int k = 0; k < kH; ++k) acc += m.h2[a * kH + k] * __half2float(m.W[oW3 + k * kO + o]);
-        if (a0 + a < B) Y[(static_cast<long long>(member) * B + a0 + a) * kO + o] = acc;
+    uint32_t phase = 0;
+    bool ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, kH, bar, phase, err);
+    // hidden layers: z = acc + b -> cache; h = silu(z) -> the next layer's A operand
+    for (int layer = 0; layer < 2 && ok; ++layer) {
+        const __half *bias = P + (layer == 0 ? ob1 : ob2);
+        float *zc = layer == 0 ? z1 : z2;
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + c0, r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float z = __uint_as_float(r[j]) + __half2float(bias[c0 + j]);
+                if (zc && a < B) zc[static_cast<long long>(a) * kH + c0 + j] = z;
+                put_split(Ahi, Alo, t, c0 + j, a < B ? silu(z) : 0.0f);
+            }
+        }
+        fence_before();
+        __syncthreads();   // every thread's reads of TMEM and of the weights are done
+        if (layer == 0) put_weights(Bs, P + oW2, kH, kH);
+        else put_weights(Bs, P + oW3, kH, kO);
+        phase ^= 1;
+        ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, layer == 0 ? kH : kO, bar, phase, err);
+    }
+    // output layer: y = acc + b3 (16 columns).  The TMEM load is warp-collective: every lane
+    // takes part (ok is uniform over the CTA), only the rows of real atoms are stored.
+    uint32_t r[32];
+    if (ok) tmem_ld32(tmem, r);   // columns 16..31 are not part of the product
+    if (a < B) {
+        float *y = Y + (static_cast<long long>(member) * B + a) * kO;
+        for (int o = 0; o < kO; ++o) y[o] = ok ? __uint_as_float(r[o]) + __half2float(P[ob3 + o]) : __int_as_float(0x7fc00000);
+    }
+    if (!ok && t == 0) mbar_wait(bar, phase, err, kSpinCycles / 8);   // let a late chain finish before freeing TMEM
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(*tmem_slot), "r"(128));
     }
 }
 
@@ -358,6 +756,14 @@ __global__ void k_adam(long long n, float *p, const float *g, float *mm, float *
     }
 }
 
+// Y[i][k] = log(alpha_bar[k][i] / alpha_free[k][i]), the model's target (FP32).
+__global__ void k_learned_targets(int n, const double *abar, const double *afree, float *Y) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e >= static_cast<long long>(n) * kO) return;
+    const int i = static_cast<int>(e / kO), k = static_cast<int>(e % kO);
+    Y[e] = static_cast<float>(log(abar[static_cast<long long>(k) * n + i] / afree[static_cast<long long>(k) * n + i]));
+}
+
 __global__ void k_gather_rows(long long rows, int width, const int *idx, const float *src, float *dst) {
     const long long total = rows * width;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
@@ -389,18 +795,39 @@ __global__ void k_learned_alpha(int N, int members, int nf1, const double *al_u,
     spread[e] = sqrt(s2 / members);
 }
 
-__global__ void k_learned_estimate(int n, int N, const double *h, const double *spread, double *out) {
+// The energy-error estimate per atom: scale x the members' standard deviation of their
+// first-order energies, D_m = sum_{k,i} h[k][i] alpha_i(u_k) (e^{y_m,i,k} - mean_m' e^{y_m',i,k}),
+// over N.  One CTA of 1024 threads; the deviations are summed member by member (no cancellation
+// against the mean energy).
+__global__ void k_learned_estimate(int N, int nf1, int members, double scale, const double *h, const double *al_u,
+                                   const float *Y, double *out) {
     __shared__ double sh[32];
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) acc += fabs(h[e] * spread[e]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-    __syncthreads();
+    __shared__ double Dm[64];
+    const int n = N * nf1;
+    for (int m = 0; m < members; ++m) {
+        double acc = 0.0;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int k = e / N, i = e % N;
+            const float *y = Y + static_cast<long long>(i) * kO + k;
+            float mean = 0.0f;
+            for (int q = 0; q < members; ++q) mean += expf(y[static_cast<long long>(q) * N * kO]);
+            mean /= static_cast<float>(members);
+            acc += h[e] * al_u[e] * static_cast<double>(expf(y[static_cast<long long>(m) * N * kO]) - mean);
+        }
+        acc = warp_sum_d(acc);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (blockDim.x >> 5); ++w) t += sh[w];
+            Dm[m] = t;
+        }
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (blockDim.x >> 5); ++w) t += sh[w];
-        out[0] = t / N;
+        double v = 0.0;
+        for (int m = 0; m < members; ++m) v += Dm[m] * Dm[m];
+        out[0] = scale * sqrt(v / members) / N;
     }
 }
 
@@ -415,24 +842,33 @@ __global__ void k_learned_dy(int N, int members, int nf1, const double *h, const
     dY[e] = k < nf1 ? static_cast<float>(h[k * N + i] * abar[k * N + i] / members) : 0.0f;
 }
 
-// Upstream gradients of the moments of atom i from the summed feature gradient gx.
+// The members' summed gradient of the 74 static features: gs [N][74] (FP32).
+__global__ void k_learned_gsum(int N, int members, const float *dX, float *gs) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e >= static_cast<long long>(N) * kFS) return;
+    const int i = static_cast<int>(e / kFS), k = static_cast<int>(e % kFS);
+    float g = 0.0f;
+    for (int m = 0; m < members; ++m) g += dX[(static_cast<long long>(m) * N + i) * kF + k];
+    gs[e] = g;
+}
+
+// Upstream gradients of the static moments of atom i.
 struct MomentGrad { double g1, g2, g3; };
-__device__ __forceinline__ MomentGrad moment_grad(const float *dX, int members, int N, int i, double a0i) {
-    double g[6] = {0, 0, 0, 0, 0, 0};
-    for (int m = 0; m < members; ++m)
-        for (int e = 0; e < 6; ++e) g[e] += dX[(static_cast<long long>(m) * N + i) * kF + 68 + e];
+__device__ __forceinline__ MomentGrad moment_grad(const float *gs, int i, double a0i) {
+    const float *g = gs + static_cast<long long>(i) * kFS + 68;
     return {g[0] + a0i * g[3], g[1] + a0i * a0i * g[4], g[2] + a0i * a0i * g[5]};
 }
 
-// A_i = dE/dM_i = g1_i I/3 + 2 g3_i M_i/3 + (alpha0_i/3) sum_k g2_k B_ik (one warp per atom).
-__global__ void k_moment_adjoint(int N, const double *R, const double *a0ref, const double *rref, const double *ratio,
-                                 const double *Mw, const float *dX, int members, double *Aw) {
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= N) return;
+// A_i = dE/dM_i = g1_i I/3 + 2 g3_i M_i/3 + (alpha0_i/3) sum_k g2_k B_ik (one CTA of 128
+// threads per atom).
+__global__ void __launch_bounds__(128) k_moment_adjoint(int N, const double *R, const double *a0ref,
+                                                        const double *rref, const double *ratio, const double *Mw,
+                                                        const float *gs, double *Aw) {
+    __shared__ double red[4];
+    const int i = blockIdx.x, t = threadIdx.x;
     const double a0i = a0ref[i] * ratio[i], rvi = rref[i] * cbrt(ratio[i]);
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = lane; k < N; k += 32) {
+    for (int k = t; k < N; k += 128) {
         if (k == i) continue;
         const double r[3] = {R[3 * k] - R[3 * i], R[3 * k + 1] - R[3 * i + 1], R[3 * k + 2] - R[3 * i + 2]};
         const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
@@ -440,12 +876,12 @@ __global__ void k_moment_adjoint(int N, const double *R, const double *a0ref, co
         const double a0k = a0ref[k] * ratio[k];
         double B[6];
         scs_coupling(r, d, a0i, a0k, rvi, rref[k] * cbrt(ratio[k]), B);
-        const double g2k = moment_grad(dX, members, N, k, a0k).g2;
+        const double g2k = moment_grad(gs, k, a0k).g2;
         for (int e = 0; e < 6; ++e) acc[e] += g2k * B[e];
     }
-    for (int e = 0; e < 6; ++e) acc[e] = warp_sum_d(acc[e]);
-    if (lane == 0) {
-        const MomentGrad gi = moment_grad(dX, members, N, i, a0i);
+    for (int e = 0; e < 6; ++e) acc[e] = block_sum128(acc[e], red);
+    if (t == 0) {
+        const MomentGrad gi = moment_grad(gs, i, a0i);
         const double *M = Mw + 6LL * i;
         for (int e = 0; e < 6; ++e)
             Aw[6LL * i + e] = (e < 3 ? gi.g1 / 3.0 : 0.0) + 2.0 * gi.g3 * M[e] / 3.0 + a0i / 3.0 * acc[e];
@@ -470,50 +906,56 @@ __device__ __forceinline__ void coupling_grad(const double *r, double d, double 
         out[c] = -f.df_drho * r[c] * ir * CT + sr * ((t.dP * tr + t.dW * rCr) * r[c] * ir + 2.0 * t.W * Cr[c]);
 }
 
-// gR[i] += dE/dR_i through the features (one warp per atom, fixed order):
-//   radial:  -sum_j sum_k (gx_ik alpha0_j + gx_jk alpha0_i) phi_k'(d_ij) r^_ij
+// gR[i] += dE/dR_i through the features (one CTA of 128 threads per atom, fixed order):
+//   radial:  -sum_j sum_k (gx_ik alpha0_j + gx_jk alpha0_i) phi_k'(d_ij) r^_ij (phi_k in FP32)
 //   moments: -sum_j <C_ij + C_ji, dB/dr (r_ij)>,  C_ij = alpha0_j (A_i + g2_i M_j / 3)
-__global__ void k_learned_forces(int N, const double *R, const double *a0ref, const double *rref,
-                                 const double *ratio, const double *Mw, const double *Aw, const float *dX,
-                                 int members, double *gR) {
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= N) return;
+//   Dyson block: the partial forces FP [16][N][3] of k_dyson_forces, in grid-point order.
+__global__ void __launch_bounds__(128) k_learned_forces(int N, const double *R, const double *a0ref,
+                                                        const double *rref, const double *ratio, const double *Mw,
+                                                        const double *Aw, const float *gs, const double *FP,
+                                                        double *gR) {
+    __shared__ float gi_s[64];
+    __shared__ double red[4];
+    const int i = blockIdx.x, t = threadIdx.x;
     const double a0i = a0ref[i] * ratio[i], rvi = rref[i] * cbrt(ratio[i]);
-    const double g2i = moment_grad(dX, members, N, i, a0i).g2;
+    if (t < 64) gi_s[t] = gs[static_cast<long long>(i) * kFS + t];
+    __syncthreads();
+    const double g2i = moment_grad(gs, i, a0i).g2;
     const double *Mi = Mw + 6LL * i, *Ai = Aw + 6LL * i;
-    const double i2w2 = 0.5 / (kWidth * kWidth);
+    const float i2w2 = static_cast<float>(0.5 / (kWidth * kWidth));
     double f[3] = {0, 0, 0};
-    for (int j = lane; j < N; j += 32) {
+    for (int j = t; j < N; j += 128) {
         if (j == i) continue;
         const double r[3] = {R[3 * j] - R[3 * i], R[3 * j + 1] - R[3 * i + 1], R[3 * j + 2] - R[3 * i + 2]};
         const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
         if (d >= kCut) continue;
         const double a0j = a0ref[j] * ratio[j], rvj = rref[j] * cbrt(ratio[j]);
         // radial features
-        const double fc = 0.5 * (1.0 + cos(kPiL * d / kCut)), dfc = -0.5 * kPiL / kCut * sin(kPiL * d / kCut);
-        double s = 0.0;
+        const float df = static_cast<float>(d), x = df / static_cast<float>(kCut);
+        const float fc = 0.5f * (1.0f + cospif(x)), dfc = -0.5f * static_cast<float>(kPiL / kCut) * sinpif(x);
+        const float *gj = gs + static_cast<long long>(j) * kFS;
+        const float a0jf = static_cast<float>(a0j), a0if = static_cast<float>(a0i);
+        float sr = 0.0f;
         for (int k = 0; k < 64; ++k) {
-            double gi = 0.0, gj = 0.0;
-            for (int m = 0; m < members; ++m) {
-                gi += dX[(static_cast<long long>(m) * N + i) * kF + k];
-                gj += dX[(static_cast<long long>(m) * N + j) * kF + k];
-            }
-            const double mu = (k + 0.5) * kWidth, G = exp(-(d - mu) * (d - mu) * i2w2);
-            s += (gi * a0j + gj * a0i) * (dfc * G + fc * G * (-(d - mu) * 2.0 * i2w2));
+            const float u = static_cast<float>(d - (k + 0.5) * kWidth), G = expf(-u * u * i2w2);
+            sr += (gi_s[k] * a0jf + gj[k] * a0if) * G * (dfc - fc * u * 2.0f * i2w2);
         }
-        for (int c = 0; c < 3; ++c) f[c] -= s * r[c] / d;
+        for (int c = 0; c < 3; ++c) f[c] -= static_cast<double>(sr) * r[c] / d;
         // moments
-        const double g2j = moment_grad(dX, members, N, j, a0j).g2;
+        const double g2j = moment_grad(gs, j, a0j).g2;
         const double *Mj = Mw + 6LL * j, *Aj = Aw + 6LL * j;
         double C[6], dB[3];
         for (int e = 0; e < 6; ++e) C[e] = a0j * (Ai[e] + g2i * Mj[e] / 3.0) + a0i * (Aj[e] + g2j * Mi[e] / 3.0);
         coupling_grad(r, d, a0i, a0j, rvi, rvj, C, dB);
         for (int c = 0; c < 3; ++c) f[c] -= dB[c];
     }
-    for (int c = 0; c < 3; ++c) f[c] = warp_sum_d(f[c]);
-    if (lane == 0)
-        for (int c = 0; c < 3; ++c) gR[3 * i + c] += f[c];
+    for (int c = 0; c < 3; ++c) f[c] = block_sum128(f[c], red);
+    if (t == 0)
+        for (int c = 0; c < 3; ++c) {
+            double fd = 0.0;   // the Dyson block's grid points, in order
+            for (int k = 0; k < kNU; ++k) fd += FP[(static_cast<long long>(k) * N + i) * 3 + c];
+            gR[3 * i + c] += f[c] + fd;
+        }
 }
 
 inline int cdiv(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
@@ -527,11 +969,19 @@ void learned_dy(int N, int members, int nf1, const double *h, const double *abar
     k_learned_dy<<<cdiv(static_cast<long long>(members) * N * kO, 256), 256, 0, s>>>(N, members, nf1, h, abar, dY);
 }
 
-void learned_forces(int N, const double *R, const double *a0ref, const double *rref, const double *ratio,
-                    const double *moments, const float *dX, int members, double *adjoint, double *gR, cudaStream_t s) {
-    count_launches(2);
-    k_moment_adjoint<<<cdiv(N, 8), 256, 0, s>>>(N, R, a0ref, rref, ratio, moments, dX, members, adjoint);
-    k_learned_forces<<<cdiv(N, 8), 256, 0, s>>>(N, R, a0ref, rref, ratio, moments, adjoint, dX, members, gR);
+void learned_forces(int N, const int *offsets, const double *R, const double *a0ref, const double *rref,
+                    const double *ratio, double *work, const float *dX, int members, double *adjoint, double *gR,
+                    cudaStream_t s) {
+    const int wb = cdiv(static_cast<long long>(kNU) * N, 8), tb = cdiv(static_cast<long long>(kNU) * N, 256);
+    float *gs = reinterpret_cast<float *>(adjoint + 206LL * N);   // [N][74] after the Dyson adjoints
+    count_launches(7);
+    k_dyson_adj_prep<<<tb, 256, 0, s>>>(N, members, dX, adjoint);
+    k_learned_gsum<<<cdiv(static_cast<long long>(N) * kFS, 256), 256, 0, s>>>(N, members, dX, gs);
+    k_dyson_adj<2><<<wb, 256, 0, s>>>(N, 1, offsets, R, work, adjoint);
+    k_dyson_adj<1><<<wb, 256, 0, s>>>(N, 1, offsets, R, work, adjoint);
+    k_dyson_forces<<<wb, 256, 0, s>>>(N, 1, offsets, R, work, adjoint);
+    k_moment_adjoint<<<N, 128, 0, s>>>(N, R, a0ref, rref, ratio, work, gs, adjoint);
+    k_learned_forces<<<N, 128, 0, s>>>(N, R, a0ref, rref, ratio, work, adjoint, gs, dyson_adj(adjoint, N).FP, gR);
 }
 
 void learned_alpha(int N, int members, int nf1, const double *al_u, const float *Y, double *abar, double *spread,
@@ -541,27 +991,50 @@ void learned_alpha(int N, int members, int nf1, const double *al_u, const float 
                                                                                spread);
 }
 
-void learned_estimate(int N, int nf1, const double *h, const double *spread, double *out, cudaStream_t s) {
+void learned_estimate(int N, int nf1, int members, double scale, const double *h, const double *al_u,
+                      const float *Y, double *out, cudaStream_t s) {
     count_launches(1);
-    k_learned_estimate<<<1, 1024, 0, s>>>(N * nf1, N, h, spread, out);
+    k_learned_estimate<<<1, 1024, 0, s>>>(N, nf1, members, scale, h, al_u, Y, out);
 }
 
 void scs_features(int n_atoms, int n_sys, const int *offsets, const double *R, const double *a0ref,
                   const double *c6ref, const double *rref, const double *ratio, float *X, double *work,
                   cudaStream_t s) {
-    count_launches(2);
-    k_features<<<cdiv(n_atoms, 8), 256, 0, s>>>(n_atoms, n_sys, offsets, R, a0ref, c6ref, rref, ratio, X, work);
+    static GridU2 grid = [] {   // u_k^2 of the 16 points: 0 and the 15 Casimir-Polder nodes
+        std::vector<double> u, wu;
+        casimir_polder_grid(kNU - 1, u, wu);
+        GridU2 g;
+        for (int k = 0; k < kNU; ++k) g.u2[k] = static_cast<float>(u[k] * u[k]);
+        return g;
+    }();
+    const int wb = cdiv(static_cast<long long>(kNU) * n_atoms, 8), tb = cdiv(static_cast<long long>(kNU) * n_atoms, 256);
+    count_launches(6);
+    k_features<<<n_atoms, 128, 0, s>>>(n_atoms, n_sys, offsets, R, a0ref, c6ref, rref, ratio, X, work);
     k_feature_moments<<<cdiv(n_atoms, 8), 256, 0, s>>>(n_atoms, n_sys, offsets, R, a0ref, rref, ratio, work, X);
+    k_dyson_prep<<<tb, 256, 0, s>>>(n_atoms, a0ref, c6ref, rref, ratio, grid, work);
+    k_dyson_hop<1><<<wb, 256, 0, s>>>(n_atoms, n_sys, offsets, R, work, X);
+    k_dyson_hop<2><<<wb, 256, 0, s>>>(n_atoms, n_sys, offsets, R, work, X);
+    k_dyson_hop<3><<<wb, 256, 0, s>>>(n_atoms, n_sys, offsets, R, work, X);
 }
 
 cudaError_t mlp_forward(int B, int members, const float *X, const float *mean, const float *stdv,
-                        const void *params16, float *Y, float *zcache, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kMlpSmem));
+                        const void *params16, float *Y, float *zcache, cudaStream_t s, int *err) {
+    static int *own_err = nullptr;   // the timeout flag when the caller passes none
+    if (!err) {
+        if (!own_err) {
+            cudaError_t e = cudaMalloc(&own_err, sizeof(int));
+            if (e != cudaSuccess) return e;
+            e = cudaMemset(own_err, 0, sizeof(int));
+            if (e != cudaSuccess) return e;
+        }
+        err = own_err;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kMlpTcSmem));
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_mlp_forward<<<dim3(cdiv(B, kTA), members), 128, kMlpSmem, s>>>(
-        B, X, mean, stdv, static_cast<const __half *>(params16), Y, zcache);
+    k_mlp_forward_tc<<<dim3(cdiv(B, kMT), members), 128, kMlpTcSmem, s>>>(
+        B, X, mean, stdv, static_cast<const __half *>(params16), Y, zcache, err);
     return cudaGetLastError();
 }
 
@@ -644,6 +1117,14 @@ int mbdk_adam_step(void *stream, long long n, float *params, const float *grad, 
                    float lr, void *params_fp16) {
     if (n < 1 || step < 1 || !params || !grad || !m || !v || !(lr > 0.0f)) return MBD_ERR_INPUT;
     mbdgb::adam_step(n, params, grad, m, v, step, lr, params_fp16, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
+}
+
+int mbdk_learned_targets(void *stream, int n_atoms, const double *alpha_bar, const double *alpha_free, float *Y) {
+    if (n_atoms < 1 || !alpha_bar || !alpha_free || !Y) return MBD_ERR_INPUT;
+    mbdgb::count_launches(1);
+    mbdgb::k_learned_targets<<<static_cast<int>((16LL * n_atoms + 255) / 256), 256, 0,
+                               static_cast<cudaStream_t>(stream)>>>(n_atoms, alpha_bar, alpha_free, Y);
     return cudaGetLastError() == cudaSuccess ? MBD_OK : MBD_ERR_CUDA;
 }
 

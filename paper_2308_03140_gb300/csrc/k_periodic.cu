@@ -126,6 +126,37 @@ __device__ __forceinline__ void tile_pair(int t, int ntile, int &I, int &J) {
     J = I + t;
 }
 
+// The reduced-precision staging of the gradient's reciprocal sum (F32: the mixed modes).
+template <typename R> struct Vec2;
+template <> struct Vec2<double> { using T = double2; };
+template <> struct Vec2<float> { using T = float2; };
+template <typename R>
+__device__ __forceinline__ void stage_chunk_r(const PeriodicBufs &p, int N, const double *q, const int *gl, int g0,
+                                              int m, int I, int J, R (*sk)[3], R *sc, R *sf, typename Vec2<R>::T (*sSi)[kQT],
+                                              typename Vec2<R>::T (*sSj)[kQT], R *sG) {
+    const double pre = 4.0 * kPi / p.cell.vol, i4g2 = 0.25 / (p.cell.gamma * p.cell.gamma);
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+        const int gi = gl[g0 + e];
+        const double kx = p.G[3 * gi] + q[0], ky = p.G[3 * gi + 1] + q[1], kz = p.G[3 * gi + 2] + q[2];
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        sk[e][0] = static_cast<R>(kx); sk[e][1] = static_cast<R>(ky); sk[e][2] = static_cast<R>(kz);
+        sc[e] = static_cast<R>(pre * exp(-k2 * i4g2) / k2);
+        sf[e] = static_cast<R>(2.0 / k2 + 2.0 * i4g2);
+        sG[3 * e] = static_cast<R>(p.G[3 * gi]);
+        sG[3 * e + 1] = static_cast<R>(p.G[3 * gi + 1]);
+        sG[3 * e + 2] = static_cast<R>(p.G[3 * gi + 2]);
+    }
+    for (int e = threadIdx.x; e < m * 2 * kQT; e += blockDim.x) {
+        const int gg = e / (2 * kQT), aa = e % (2 * kQT);
+        const int atom = aa < kQT ? I * kQT + aa : J * kQT + aa - kQT;
+        const double2 v = atom < N ? p.S[static_cast<long long>(gl[g0 + gg]) * N + atom] : make_double2(0.0, 0.0);
+        typename Vec2<R>::T w;
+        w.x = static_cast<R>(v.x);
+        w.y = static_cast<R>(v.y);
+        if (aa < kQT) sSi[gg][aa] = w; else sSj[gg][aa - kQT] = w;
+    }
+}
+
 // Stage chunk [g0, g0 + m) of Bloch vector k's reciprocal list: k-vectors, the coefficient
 // (4 pi/Omega) e^{-k^2/4 gamma^2}/k^2 and the structure factors of the tile's atoms.
 __device__ __forceinline__ void stage_chunk(const PeriodicBufs &p, int N, const double *q, const int *gl, int g0,
@@ -440,6 +471,10 @@ __global__ void k_energy_periodic(const double *Y, long long ld, int n, int nk, 
 //   zA = Re <conj zs, dT^lr/dA>,
 // then g_c[i] += c_j zT, g_c[j] += c_i zT, g_rbar[i,j] += c_i c_j zS, gR[j] += c_i c_j zx,
 // gR[i] -= c_i c_j zx, gA += c_i c_j zA (c_i = omega_bar_i sqrt(abar0_i)).
+// Real-space sums in FP64; the reciprocal sum in R (double, or float for the mixed modes,
+// whose Z carries errors far above FP32 rounding), each chunk of kGC vectors summed in R and
+// added into FP64 totals.
+template <typename R>
 __global__ void __launch_bounds__(256) k_mbd_grad_periodic(AtomBufs b, PeriodicBufs p, double beta, double a,
                                                            const double *Z, long long ld, double zscale, int ntile,
                                                            double *g_c, double *g_rbar, double *gR, double *gA) {
@@ -507,41 +542,54 @@ __global__ void __launch_bounds__(256) k_mbd_grad_periodic(AtomBufs b, PeriodicB
                 }
     }
     // reciprocal space
-    __shared__ double sk[kGC][3], sc[kGC], sG[3 * kGC];
-    __shared__ double2 sSi[kGC][kQT], sSj[kGC][kQT];
+    using R2 = typename Vec2<R>::T;
+    __shared__ R sk[kGC][3], sc[kGC], sf[kGC], sG[3 * kGC];
+    __shared__ R2 sSi[kGC][kQT], sSj[kGC][kQT];
     const int cnt = p.gcount[kq];
     const int *gl = p.glist + static_cast<long long>(kq) * p.maxG;
-    const double h2 = 0.5 / (c.gamma * c.gamma);
+    R zrr[6], zir[6];
+    for (int e = 0; e < 6; ++e) {
+        zrr[e] = static_cast<R>(zr[e]);
+        zir[e] = static_cast<R>(zi[e]);
+    }
     for (int g0 = 0; g0 < cnt; g0 += kGC) {
         const int m = min(kGC, cnt - g0);
         __syncthreads();
-        stage_chunk(p, b.N, q, gl, g0, m, I, J, sk, sc, sSi, sSj, sG);
+        stage_chunk_r<R>(p, b.N, q, gl, g0, m, I, J, sk, sc, sf, sSi, sSj, sG);
         __syncthreads();
-        if (valid)
+        if (valid) {
+            R su_c = 0, M1_c[3] = {0, 0, 0}, M2_c[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int gg = 0; gg < m; ++gg) {
-                const double2 si = sSi[gg][ty], sj = sSj[gg][tx];
-                const double er = si.x * sj.x + si.y * sj.y, ei = si.x * sj.y - si.y * sj.x;   // e^{i G.x}
-                const double cf = sc[gg];
-                const double kv[3] = {sk[gg][0], sk[gg][1], sk[gg][2]};
-                double us[6], vs[6];
+                const R2 si = sSi[gg][ty], sj = sSj[gg][tx];
+                const R er = si.x * sj.x + si.y * sj.y, ei = si.x * sj.y - si.y * sj.x;   // e^{i G.x}
+                const R cf = sc[gg];
+                const R kv[3] = {sk[gg][0], sk[gg][1], sk[gg][2]};
+                R us[6], vs[6];
+#pragma unroll
                 for (int e = 0; e < 6; ++e) {
-                    us[e] = zr[e] * er + zi[e] * ei;
-                    vs[e] = zr[e] * ei - zi[e] * er;
+                    us[e] = zrr[e] * er + zir[e] * ei;
+                    vs[e] = zrr[e] * ei - zir[e] * er;
                 }
-                double uk[3], vk[3];
-                sym_mv(us, kv, uk);
-                sym_mv(vs, kv, vk);
-                const double kuk = kv[0] * uk[0] + kv[1] * uk[1] + kv[2] * uk[2];
-                const double kvk = kv[0] * vk[0] + kv[1] * vk[1] + kv[2] * vk[2];
-                const double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
-                su += cf * kuk;
-                const double cv = cf * kvk, f2 = kuk * (2.0 / k2 + h2);
+                const R uk[3] = {us[0] * kv[0] + us[3] * kv[1] + us[4] * kv[2], us[3] * kv[0] + us[1] * kv[1] + us[5] * kv[2],
+                                 us[4] * kv[0] + us[5] * kv[1] + us[2] * kv[2]};
+                const R vk[3] = {vs[0] * kv[0] + vs[3] * kv[1] + vs[4] * kv[2], vs[3] * kv[0] + vs[1] * kv[1] + vs[5] * kv[2],
+                                 vs[4] * kv[0] + vs[5] * kv[1] + vs[2] * kv[2]};
+                const R kuk = kv[0] * uk[0] + kv[1] * uk[1] + kv[2] * uk[2];
+                const R kvk = kv[0] * vk[0] + kv[1] * vk[1] + kv[2] * vk[2];
+                su_c += cf * kuk;
+                const R cv = cf * kvk, f2 = kuk * sf[gg];   // sf = 2/k^2 + 1/(2 gamma^2)
+#pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    M1[d] += sG[3 * gg + d] * cv;
-                    const double De = cf * (2.0 * uk[d] - f2 * kv[d]);   // D_e at e = d
-                    for (int dd = 0; dd < 3; ++dd) M2[3 * dd + d] += kv[dd] * De;   // M2[d'][e] = k_d' D_e
+                    M1_c[d] += sG[3 * gg + d] * cv;
+                    const R De = cf * (R(2) * uk[d] - f2 * kv[d]);   // D_e at e = d
+#pragma unroll
+                    for (int dd = 0; dd < 3; ++dd) M2_c[3 * dd + d] += kv[dd] * De;   // M2[d'][e] = k_d' D_e
                 }
             }
+            su += static_cast<double>(su_c);
+            for (int d = 0; d < 3; ++d) M1[d] += static_cast<double>(M1_c[d]);
+            for (int e = 0; e < 9; ++e) M2[e] += static_cast<double>(M2_c[e]);
+        }
     }
     if (!valid) return;
     zT += su;
@@ -894,7 +942,7 @@ void mean_rows(const double *x, int rows, int N, double *out, cudaStream_t s) {
 
 void periodic_mbd_grad(const AtomBufs &b, const PeriodicBufs &p, double beta, double a, const double *Z,
                        long long ld, double zscale, const MbdGradOut &o, double *work, double *gA, cudaStream_t s,
-                       const double *tq) {
+                       const double *tq, bool f32_recip) {
     double *g_c = work;
     cudaMemsetAsync(g_c, 0, sizeof(double) * b.N, s);
     cudaMemsetAsync(o.g_rbar, 0, sizeof(double) * b.N, s);
@@ -902,8 +950,11 @@ void periodic_mbd_grad(const AtomBufs &b, const PeriodicBufs &p, double beta, do
     cudaMemsetAsync(gA, 0, sizeof(double) * 9, s);
     const int ntile = cdiv(b.N, kQT);
     count_launches(2);
-    k_mbd_grad_periodic<<<dim3(ntile * (ntile + 1) / 2, p.nk), 256, 0, s>>>(b, p, beta, a, Z, ld, zscale, ntile, g_c,
-                                                                            o.g_rbar, o.gR, gA);
+    const dim3 grid(ntile * (ntile + 1) / 2, p.nk);
+    if (f32_recip)
+        k_mbd_grad_periodic<float><<<grid, 256, 0, s>>>(b, p, beta, a, Z, ld, zscale, ntile, g_c, o.g_rbar, o.gR, gA);
+    else
+        k_mbd_grad_periodic<double><<<grid, 256, 0, s>>>(b, p, beta, a, Z, ld, zscale, ntile, g_c, o.g_rbar, o.gR, gA);
     k_mbd_grad_periodic_finalize<<<cdiv(b.N, 128), 128, 0, s>>>(b, Z, ld, p.nk, zscale, g_c, o, tq);
 }
 

@@ -20,6 +20,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
+#include "freq_grid.h"
 #include "ns_schedule.h"
 
 using namespace mbdgb;
@@ -53,44 +54,6 @@ void mbdgb::count_launches(int k) { g_launches.fetch_add(k, std::memory_order_re
 long long mbdgb::launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
-
-// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n, started from the
-// asymptotic root estimate of Tricomi.  Ascending nodes.
-void legendre_rule(int n, std::vector<double> &x, std::vector<double> &w) {
-    x.assign(n, 0.0);
-    w.assign(n, 0.0);
-    const double pi = 3.141592653589793238462643383279502884;
-    for (int k = 1; k <= n; ++k) {
-        double t = std::cos(pi * (4.0 * k - 1.0) / (4.0 * n + 2.0)) *
-                   (1.0 - 1.0 / (8.0 * n * n) + 1.0 / (8.0 * n * n * n));
-        double deriv = 1.0;
-        for (int it = 0; it < 64; ++it) {
-            double pm1 = 1.0, p = t;   // P_0, P_1
-            for (int m = 2; m <= n; ++m) {
-                const double pn = ((2.0 * m - 1.0) * t * p - (m - 1.0) * pm1) / m;
-                pm1 = p;
-                p = pn;
-            }
-            if (n == 1) { p = t; pm1 = 1.0; }
-            deriv = n * (pm1 - t * p) / (1.0 - t * t);
-            const double step = p / deriv;
-            t -= step;
-            if (std::fabs(step) <= 1e-17) break;
-        }
-        {
-            double pm1 = 1.0, p = t;
-            for (int m = 2; m <= n; ++m) {
-                const double pn = ((2.0 * m - 1.0) * t * p - (m - 1.0) * pm1) / m;
-                pm1 = p;
-                p = pn;
-            }
-            if (n == 1) { p = t; pm1 = 1.0; }
-            deriv = n * (pm1 - t * p) / (1.0 - t * t);
-        }
-        x[n - k] = t;
-        w[n - k] = 2.0 / ((1.0 - t * t) * deriv * deriv);
-    }
-}
 
 // Number of eigenvalues below x of the symmetric tridiagonal matrix (diag a, offdiag b)
 // by the Sturm sequence of its LDL^T pivots.
@@ -286,8 +249,9 @@ int ensure_learned(mbd_ctx *ctx) {
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     if (!ctx->lslab || ctx->lN != N || ctx->lM != M) {
         const size_t bytes = al(2 * P * M) + al(sizeof(float) * 2 * kLF) + al(sizeof(float) * kLF * N) +
-                             al(sizeof(float) * M * N * 16) + al(sizeof(double) * nf1 * N) + al(sizeof(double) * 6 * N) +
-                             al(sizeof(double) * 6 * N) + al(sizeof(float) * M * 2 * N * 128) +
+                             al(sizeof(float) * M * N * 16) + al(sizeof(double) * nf1 * N) +
+                             al(sizeof(double) * kLearnedWork * N) + al(sizeof(double) * kLearnedAdjointWork * N) +
+                             al(sizeof(float) * M * 2 * N * 128) +
                              al(sizeof(float) * M * N * kLF) + al(sizeof(int) * 2);
         cudaError_t e = cudaSuccess;
         if (!ctx->lslab || ctx->lbytes < bytes) {   // re-carved in place when large enough
@@ -303,8 +267,8 @@ int ensure_learned(mbd_ctx *ctx) {
         ctx->dfeat = reinterpret_cast<float *>(p); p += al(sizeof(float) * kLF * N);
         ctx->dYl = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * N * 16);
         ctx->dspread = reinterpret_cast<double *>(p); p += al(sizeof(double) * nf1 * N);
-        ctx->dmoments = reinterpret_cast<double *>(p); p += al(sizeof(double) * 6 * N);
-        ctx->dadj = reinterpret_cast<double *>(p); p += al(sizeof(double) * 6 * N);
+        ctx->dmoments = reinterpret_cast<double *>(p); p += al(sizeof(double) * kLearnedWork * N);
+        ctx->dadj = reinterpret_cast<double *>(p); p += al(sizeof(double) * kLearnedAdjointWork * N);
         ctx->dzc = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * 2 * N * 128);
         ctx->dXl = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * N * kLF);
         ctx->doffs = reinterpret_cast<int *>(p);
@@ -812,8 +776,9 @@ void backward_periodic(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const do
     const double beta = ctx->opt.beta, a = ctx->opt.a;
     const PeriodicBufs pb = periodic_bufs(ctx);
     MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
+    const bool mixed = ctx->opt.precision != MBD_PREC_FP64 && ctx->opt.precision != MBD_PREC_FP64_SPLIT;
     periodic_mbd_grad(b, pb, beta, a, ctx->Zlast, ld, ctx->zscale, go, ctx->dgc, ctx->dgA, s,
-                      ctx->tq_valid ? ctx->dtq : nullptr);
+                      ctx->tq_valid ? ctx->dtq : nullptr, mixed);
     if (ctx->opt.scs_mode == MBD_SCS_NL) {   // MBD-NL: no screening to differentiate
         if (grad_params) nl_chain(b, go, grad_energy, grad_params, s);
         if (grad_coords) scale_copy(ctx->dgR, 3 * ctx->N, grad_energy, grad_coords, s);
@@ -1268,7 +1233,8 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         MbdGradOut go{ctx->dgomb, ctx->dgab0, ctx->dgrb, ctx->dgR};
         mbd_grad_pass(b, beta, a, ctx->Zlast, ld, ctx->zscale, go, s, ctx->tq_valid ? ctx->dtq : nullptr);
         chain_screen(b, go, ctx->dh, ctx->dga0, ctx->dgrv, ctx->dV, ld, xs, s);
-        learned_estimate(N, nf1, ctx->dh, ctx->dspread, ctx->dscal + 5, s);
+        learned_estimate(N, nf1, ctx->members, ctx->opt.learned_estimate_scale, ctx->dh, ctx->dalu, ctx->dYl,
+                         ctx->dscal + 5, s);
         double est = 0.0;
         MBD_CUDA(cudaMemcpyAsync(&est, ctx->dscal + 5, sizeof(double), cudaMemcpyDeviceToHost, s), "learned_screening");
         MBD_CUDA(cudaStreamSynchronize(s), "learned_screening");
@@ -1299,8 +1265,8 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
             const cudaError_t eb = mlp_backward(N, ctx->members, ctx->dfeat, ctx->dmeanstd, ctx->dmeanstd + kLF,
                                                 ctx->dmodel, ctx->dzc, ctx->dYl, ctx->dXl, nullptr, s);
             if (eb != cudaSuccess) return cuda_fail(ctx, "learned_screening", eb);
-            learned_forces(N, in.R, in.a0ref, in.rref, in.ratio, ctx->dmoments, ctx->dXl, ctx->members, ctx->dadj,
-                           ctx->dgR, s);
+            learned_forces(N, ctx->doffs, in.R, in.a0ref, in.rref, in.ratio, ctx->dmoments, ctx->dXl, ctx->members,
+                           ctx->dadj, ctx->dgR, s);
             if (out.grad_coords) scale_copy(ctx->dgR, 3 * N, nullptr, out.grad_coords, s);
         }
     }
@@ -1359,6 +1325,7 @@ int mbd_default_options(mbd_options *opt) {
     opt->scs_mode = MBD_SCS_PLAIN;
     opt->learned_max_error = 1e-6;
     opt->mixed_max_error = 1e-7;
+    opt->learned_estimate_scale = 1.0;
     return MBD_OK;
 }
 
@@ -1370,7 +1337,8 @@ int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt) {
     if (o.n_freq < 1 || o.n_freq + 1 > kMaxFreq || !(o.beta > 0) || !(o.a > 0) || o.ns_max_iter < 1 ||
         !(o.ns_tol > 0) || o.precision < MBD_PREC_FP64 || o.precision > MBD_PREC_FP64_SPLIT || o.tc_chunk_stages < 0 ||
         (o.scs_mode != MBD_SCS_PLAIN && o.scs_mode != MBD_SCS_LEARNED && o.scs_mode != MBD_SCS_NL) ||
-        !(o.learned_max_error > 0) || !(o.mixed_max_error > 0))
+        !(o.learned_max_error > 0) || !(o.mixed_max_error > 0) || !(o.learned_estimate_scale > 0) ||
+        !std::isfinite(o.learned_estimate_scale) || (o.scs_mode == MBD_SCS_LEARNED && o.n_freq != 15))
         return MBD_ERR_INPUT;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev)
@@ -1379,14 +1347,7 @@ int mbd_create(mbd_ctx **out, int cuda_device, const mbd_options *opt) {
     c->device = cuda_device;
     c->opt = o;
     c->nf1 = o.n_freq + 1;
-    std::vector<double> x, w;
-    legendre_rule(o.n_freq, x, w);
-    c->hu.assign(c->nf1, 0.0);
-    c->hwu.assign(c->nf1, 0.0);
-    for (int k = 0; k < o.n_freq; ++k) {   // u = 0.6 (1+x)/(1-x), du = 1.2/(1-x)^2 dx (Sec. 3.3)
-        c->hu[k + 1] = 0.6 * (1.0 + x[k]) / (1.0 - x[k]);
-        c->hwu[k + 1] = w[k] * 1.2 / ((1.0 - x[k]) * (1.0 - x[k]));
-    }
+    casimir_polder_grid(o.n_freq, c->hu, c->hwu);
     if (cudaSetDevice(cuda_device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete c;

@@ -2,14 +2,16 @@
 library's own kernels, and packing for mbd_set_scs_model.
 
 The paper has no learned part.  The model (features, network, output encoding) is described
-in include/mbd_gb300_kernels.h: per-atom features of the local geometry, an MLP
-74 -> 128 -> 128 -> 16 with FP16 weights and FP32 accumulation, output
-y = log(alpha_bar(iu) / alpha(iu)) on the 16 grid points, an ensemble whose spread drives the
-fallback to plain screening.  Training minimises the mean squared error of y against the
-plain-screening targets with Adam; every forward, backward, loss and update step runs in the
-library's kernels (mbdk_scs_features, mbdk_mlp_forward/backward, mbdk_mse_grad,
+in include/mbd_gb300_kernels.h: per-atom features of the local geometry and of the first
+terms of the Dyson series at every grid point, an MLP 122 -> 128 -> 128 -> 16 with FP16
+weights and FP32 accumulation, output y = log(alpha_bar(iu) / alpha(iu)) on the 16 grid
+points, an ensemble whose spread drives the fallback to plain screening.  Training minimises
+the mean squared error of y against the plain-screening targets with Adam; every forward,
+backward, loss and update step and the targets run in the library's kernels
+(mbdk_scs_features, mbdk_learned_targets, mbdk_mlp_forward/backward, mbdk_mse_grad,
 mbdk_adam_step, mbdk_gather_rows); PyTorch provides device memory, and the feature
-standardisation statistics are computed once on the host.
+standardisation statistics are computed once on the host.  The error estimate's scale is
+fitted on held-out clusters after training (calibrate).
 """
 from __future__ import annotations
 
@@ -62,11 +64,14 @@ def training_data(systems, device: int = 0):
         m.set_geometry(s.coords)
         m.set_free_atom_params(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
         d = m.screen()
-        targets.append(np.ascontiguousarray(np.log(d["alpha_bar"] / d["alpha_free"]).T))
+        ab = torch.tensor(d["alpha_bar"], dtype=torch.float64, device=dev).contiguous()
+        af = torch.tensor(d["alpha_free"], dtype=torch.float64, device=dev).contiguous()
+        Yk = torch.empty(s.n_atoms, 16, dtype=torch.float32, device=dev)
+        binding.mbdk_learned_targets(ab, af, Yk)
+        targets.append(Yk)
         feats.append(features([s], dev))
     m.close()
-    Y = torch.tensor(np.ascontiguousarray(np.concatenate(targets)), dtype=torch.float32, device=dev).contiguous()
-    return torch.cat(feats).contiguous(), Y
+    return torch.cat(feats).contiguous(), torch.cat(targets).contiguous()
 
 
 def features(systems, dev):
@@ -93,14 +98,19 @@ class Ensemble:
         self.mean = torch.zeros(F, dtype=torch.float32, device=self.dev)
         self.std = torch.ones(F, dtype=torch.float32, device=self.dev)
         self.seed = seed
+        self.estimate_scale = 1.0
 
     def set_standardisation(self, X):
-        """Feature mean and standard deviation over the training set (a floor of 1e-3 keeps
-        constant features finite)."""
+        """Feature mean and standard deviation over the training set; the floor 1e-5 |mean| +
+        1e-12 keeps constant features finite without flattening the small Dyson terms of the
+        high frequencies (down to ~1e-9), while values below 1e-12 (the Gaussian tail of the
+        first-order term for far pairs) stay near zero after standardisation."""
         import torch
         Xh = X.cpu().numpy().astype(np.float64)
-        self.mean = torch.tensor(Xh.mean(0), dtype=torch.float32, device=self.dev)
-        self.std = torch.tensor(np.maximum(Xh.std(0), 1e-3), dtype=torch.float32, device=self.dev)
+        mu = Xh.mean(0)
+        self.mean = torch.tensor(mu, dtype=torch.float32, device=self.dev)
+        self.std = torch.tensor(np.maximum(Xh.std(0), 1e-5 * np.abs(mu) + 1e-12), dtype=torch.float32, device=self.dev)
+        self.estimate_scale = 1.0
 
     def fit(self, X, Y, steps: int = 2000, batch: int = 4096, lr: float = 2e-3, log_every: int = 0):
         """Adam on the mean squared error of y; every member draws its own batches.
@@ -149,16 +159,20 @@ class Ensemble:
 
     def save(self, path: str):
         p16, mean, std = self.model()
-        np.savez(path, params16=p16, mean=mean, std=std)
+        np.savez(path, params16=p16, mean=mean, std=std, estimate_scale=np.float64(self.estimate_scale))
 
 
-def evaluate_accuracy(ens, systems, device: int = 0, threshold: float = 1e-6):
-    """Learned against plain screening (FP64 path) on the systems: per system |dE|/N, the
-    estimate per atom and whether the learned evaluation would fall back at `threshold`."""
+def evaluate_accuracy(ens, systems, device: int = 0, threshold: float = 1e-6, scale: float | None = None,
+                      precision: int = binding.MBD_PREC_TF32X3):
+    """Learned against plain screening (the same matrix function, `precision`) on the systems:
+    per system |dE|/N, the estimate per atom at the estimate scale (the ensemble's when None)
+    and whether the learned evaluation would fall back at `threshold`."""
     p16, mean, std = ens.model()
+    scale = ens.estimate_scale if scale is None else scale
     rows = []
-    with binding.MBD(device) as plain, binding.MBD(device, scs_mode=binding.MBD_SCS_LEARNED,
-                                                   learned_max_error=1e300) as lm:
+    with binding.MBD(device, precision=precision) as plain, \
+            binding.MBD(device, precision=precision, scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e300,
+                        learned_estimate_scale=scale) as lm:
         lm.set_scs_model(p16, mean, std)
         for s in systems:
             for m in (plain, lm):
@@ -169,6 +183,16 @@ def evaluate_accuracy(ens, systems, device: int = 0, threshold: float = 1e-6):
             est = lm.learned_stats()["estimated_error_per_atom"]
             rows.append((s.n_atoms, abs(E1 - E0) / s.n_atoms, est, est > threshold))
     return rows
+
+
+def calibrate(ens, systems, quantile: float = 0.95, device: int = 0):
+    """Scale of the error estimate: the `quantile` of |dE|/N over the unscaled estimate on
+    held-out systems, so that the scaled estimate bounds the true error on that fraction of
+    them.  Sets ens.estimate_scale and returns it."""
+    rows = evaluate_accuracy(ens, systems, device=device, scale=1.0)
+    ratio = np.array([r[1] / r[2] for r in rows if r[2] > 0])
+    ens.estimate_scale = float(np.quantile(ratio, quantile)) if ratio.size else 1.0
+    return ens.estimate_scale
 
 
 def main(argv=None):
@@ -185,6 +209,9 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--eval", type=int, default=64, help="held-out clusters of the batch recipe")
+    ap.add_argument("--calib", type=int, default=256,
+                    help="held-out perturbed clusters (seeds after the training set's) that fit the estimate scale")
+    ap.add_argument("--quantile", type=float, default=0.95)
     ap.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     build.build()
@@ -201,6 +228,10 @@ def main(argv=None):
     ens.set_standardisation(X)
     hist = ens.fit(X, Y, steps=a.steps, batch=a.batch, lr=a.lr, log_every=500)
     t2 = time.time()
+    if a.calib:
+        scale = calibrate(ens, [perturbed_cluster(a.solves + 50_000 + i) for i in range(a.calib)], a.quantile)
+        print(f"estimate scale {scale:.3f} ({a.quantile:.2f} quantile of |dE| / estimate over {a.calib} clusters, "
+              f"{time.time() - t2:.1f} s)", flush=True)
     ens.save(a.out)
     var = float(((Y - Y.mean(0)) ** 2).mean())
     print(f"training set: {a.solves} solves, {X.shape[0]} atoms, {t1 - t0:.1f} s; training {t2 - t1:.1f} s; "
@@ -210,8 +241,10 @@ def main(argv=None):
         err = np.array([r[1] for r in rows])
         est = np.array([r[2] for r in rows])
         fb = np.mean([r[3] for r in rows])
+        ok = np.mean([(r[1] <= 1e-6) for r in rows if not r[3]]) if not all(r[3] for r in rows) else float("nan")
         print(f"held-out {len(rows)} clusters: |dE|/atom mean {err.mean():.3e} max {err.max():.3e}; "
-              f"estimate mean {est.mean():.3e}; fallback fraction at 1e-6: {fb:.2f}", flush=True)
+              f"within 1e-6: {np.mean(err <= 1e-6):.2f}; estimate mean {est.mean():.3e}; fallback fraction at "
+              f"1e-6: {fb:.2f}; accepted clusters within 1e-6: {ok:.2f}", flush=True)
 
 
 if __name__ == "__main__":

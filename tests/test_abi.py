@@ -59,10 +59,16 @@ def _create(lib, **fields):
 @pytest.mark.parametrize("field,value", [("n_freq", 0), ("n_freq", 10 ** 6), ("beta", 0.0), ("a", -1.0),
                                          ("ns_max_iter", 0), ("ns_tol", 0.0), ("precision", 9),
                                          ("tc_chunk_stages", -1), ("scs_mode", 3), ("learned_max_error", 0.0),
-                                         ("mixed_max_error", 0.0)])
+                                         ("mixed_max_error", 0.0), ("learned_estimate_scale", 0.0),
+                                         ("learned_estimate_scale", float("inf"))])
 def test_create_rejects_invalid_options_before_touching_the_device(lib, field, value):
     rc, h = _create(lib, **{field: value})
     assert rc == 1 and not h.value   # MBD_ERR_INPUT, no context
+
+
+def test_learned_mode_needs_the_models_frequency_grid(lib):
+    rc, h = _create(lib, scs_mode=binding.MBD_SCS_LEARNED, n_freq=10)
+    assert rc == 1 and not h.value
 
 
 def test_create_accepts_every_method_and_precision(lib):

@@ -27,15 +27,28 @@ def test_two_atom_features_closed_form():
     Bm = (1 - orc.fermi(5.5, 3.1 + 3.6, 0.83, 6.0)) * orc.T_gg(R[1] - R[0], s)
     tr, tr2 = np.trace(Bm), np.trace(Bm @ Bm)
     # two hops: alpha0_j B (alpha0_i B) = 63 B^2 for either atom
-    assert np.allclose(X[0, 68:], [9 * tr / 3, 63 * tr2 / 3, 81 * tr2 / 3, 7 * 9 * tr / 3,
+    assert np.allclose(X[0, 68:74], [9 * tr / 3, 63 * tr2 / 3, 81 * tr2 / 3, 7 * 9 * tr / 3,
                                    49 * 63 * tr2 / 3, 49 * 81 * tr2 / 3], rtol=1e-12)
     assert np.allclose(X[1, 68:71], [7 * tr / 3, 63 * tr2 / 3, 49 * tr2 / 3], rtol=1e-12)
+    # per-frequency Dyson block, feature 74 + 3 k + q - 1: at u_k the widths and couplings of
+    # alpha(u_k) = a0 / (1 + u_k^2 / om^2); one pair gives H^(q)_0 = a_1^ceil(q/2) a_0^floor(q/2) B^q
+    import oracle as o
+    u, _ = o.freq_grid(15)
+    assert X.shape == (2, 122) and u[0] == 0.0
+    for k, uk in enumerate(u):
+        al = a0 / (1 + uk ** 2 / om ** 2)
+        Bk = (1 - orc.fermi(5.5, 6.7, 0.83, 6.0)) * orc.T_gg(R[1] - R[0], np.hypot(*L.orc_sigma(al)))
+        t = [np.trace(np.linalg.matrix_power(Bk, q)) / 3 for q in (1, 2, 3)]
+        assert np.allclose(X[0, 74 + 3 * k:77 + 3 * k], [al[1] * t[0], al[0] * al[1] * t[1], al[1] ** 2 * al[0] * t[2]],
+                           rtol=1e-12)
+        assert np.allclose(X[1, 74 + 3 * k:77 + 3 * k], [al[0] * t[0], al[0] * al[1] * t[1], al[0] ** 2 * al[1] * t[2]],
+                           rtol=1e-12)
 
 
 def test_features_vanish_beyond_cutoff_and_are_continuous_there():
     a0, om, rv, v = np.ones(2) * 6, np.ones(2) * 0.5, np.ones(2) * 3.5, np.ones(2)
     far = L.features(np.array([[0, 0, 0], [0, 0, 24.0]]), a0, om, rv, v)
-    assert np.all(far[:, :64] == 0) and np.all(far[:, 68:] == 0)
+    assert np.all(far[:, :64] == 0) and np.all(far[:, 68:74] == 0)   # the Dyson block has no cutoff
     near = L.features(np.array([[0, 0, 0], [0, 0, 24.0 - 1e-6]]), a0, om, rv, v)
     assert np.abs(near[:, :64]).max() < 1e-10                  # smooth cutoff: fc(24) = fc'(24) = 0
 
@@ -61,7 +74,7 @@ def test_feature_jacobian_vs_fd():
         for c in range(3):
             Rp, Rm = R.copy(), R.copy()
             Rp[k, c] += h; Rm[k, c] -= h
-            fd = (L.features(Rp, a0, om, rv, v) - L.features(Rm, a0, om, rv, v))[:, :64] / (2 * h)
+            fd = (L.static_features(Rp, a0, om, rv, v) - L.static_features(Rm, a0, om, rv, v))[:, :64] / (2 * h)
             assert np.abs(fd - J[:, :, k, c]).max() < 1e-7 * max(1.0, np.abs(J).max())
 
 
@@ -122,7 +135,14 @@ def test_ensemble_prediction_and_estimate():
     ab0, _ = L.predict_alpha_bar(X, [zero], alpha_u)
     assert np.allclose(ab0, alpha_u)                            # y = 0: no screening
     h = rng.normal(size=(16, 5))
-    assert L.estimated_error_per_atom(h, np.ones((16, 5))) == pytest.approx(np.abs(h).sum() / 5)
+    ys = np.stack([L.forward(X, P)[0]] * 3)
+    assert L.estimated_error_per_atom(h, alpha_u, ys) < 1e-14   # identical members: no spread (rounding only)
+    # two members apart in one entry (u = 3, atom 2) by delta: D = -+ h alpha (e^delta - 1) / 2
+    y2 = np.zeros((2, 5, 16))
+    y2[1, 2, 3] = 0.3
+    ref = abs(h[3, 2] * alpha_u[3, 2] * (np.exp(0.3) - 1.0)) / 2.0 / 5
+    assert L.estimated_error_per_atom(h, alpha_u, y2) == pytest.approx(ref, rel=1e-13)
+    assert L.estimated_error_per_atom(h, alpha_u, y2, scale=0.2) == pytest.approx(0.2 * ref, rel=1e-13)
 
 
 def test_fp16_rounding_is_round_to_nearest():
