@@ -63,8 +63,8 @@ def gemm_region_sha16(path):
 # of the 8000-atom cluster (1-pass dram__bytes capture of the full-size step;
 # profiles/launches_finite8000_bf16x3.md), valid while the GEMM's own source in k_tc.cu (tile
 # constants through the tc_gemm dispatcher) keeps the captured hash.
-TC_GEMM_TRAFFIC = {("bf16x3", "finite8000"): {"bytes": 52.086940919e9,
-                                               "k_tc_region_sha16": "18d849742118a1e8",
+TC_GEMM_TRAFFIC = {("bf16x3", "finite8000"): {"bytes": 52.238774485e9,
+                                               "k_tc_region_sha16": "eb40cbc36ad4f016",
                                                "launch": "mean of the 30 Newton-Schulz and correction products "
                                                          "of one step, order 24064",
                                                "source": "profiles/launches_finite8000_bf16x3.md"}}
@@ -102,6 +102,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed steps of the FP64 comparison arm (0: skip; no warm-up at 4000 atoms or more)")
     ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement (at most --steps)")
+    ap.add_argument("--learned-arm", type=int, default=1,
+                    help="1: the finite extra workloads also time the learned screening (no fallback) beside plain")
     ap.add_argument("--extra-workload", default="finite2000,cell256,batch4096",
                     help="comma-separated further workloads measured after the first ('' for none): finite2000 "
                          "and cell256 in the timed arm's and --also arithmetic with their own FP64 arm; batch4096 "
@@ -335,10 +337,12 @@ def precision_code(binding, name):
 
 
 def time_arm(binding, dev, stream, sysm, p3, p4, precision, scs_mode, steps, warmup, barrier=None,
-             max_over_ranks=None, clocks=None):
+             max_over_ranks=None, clocks=None, learned=None):
     """One context, `warmup` untimed and `steps` timed device evaluations (energy and all
-    gradients, inputs resident in HBM) bracketed by CUDA events on the launch stream.
-    Returns the timing, the last results (host copies) and the per-step profiles."""
+    gradients, inputs resident in HBM) bracketed by CUDA events on the launch stream.  With
+    `learned` (the model file's arrays) the screening is the learned model's, without its
+    fallback, and the gradients are the coordinate ones (learned mode has no parameter
+    gradients).  Returns the timing, the last results (host copies) and the per-step profiles."""
     import numpy as np
     import torch
     N = sysm.n_atoms
@@ -351,7 +355,12 @@ def time_arm(binding, dev, stream, sysm, p3, p4, precision, scs_mode, steps, war
     al = torch.zeros(N, dtype=torch.float64, device=dev)
     ewald = dict(ewald_gamma=PERIODIC_EWALD[0], real_cutoff=PERIODIC_EWALD[1],
                  recip_cutoff=PERIODIC_EWALD[2]) if periodic else {}
-    m = binding.MBD(dev.index or 0, precision=precision, scs_mode=scs_mode, **ewald)
+    lopt = dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e300) if learned is not None else \
+        dict(scs_mode=scs_mode)
+    m = binding.MBD(dev.index or 0, precision=precision, **lopt, **ewald)
+    if learned is not None:
+        m.set_scs_model(learned["params16"], learned["mean"], learned["std"])
+        gp = None
     m.set_geometry(sysm.coords, sysm.lattice, sysm.k_grid)
     m.set_free_atom_params(sysm.alpha0_ref, sysm.c6_ref, p3, p4)
 
@@ -382,7 +391,8 @@ def time_arm(binding, dev, stream, sysm, p3, p4, precision, scs_mode, steps, war
         ms = max_over_ranks(ms)
     m.set_profiling(False)
     out = {"ms": ms, "steps": steps, "warmup": warmup, "energy": energy.item(), "gR": gR.cpu().numpy().copy(),
-           "gp": gp.cpu().numpy().copy(), "profs": profs, "stats": m.stats(), "clocks": clk, "ctx": m,
+           "gp": gp.cpu().numpy().copy() if gp is not None else None, "profs": profs, "stats": m.stats(),
+           "clocks": clk, "ctx": m,
            "gA": m.lattice_gradient() if periodic else None}
     return out
 
@@ -391,12 +401,14 @@ def errors_vs(arm, ref, N):
     """Per-result error of an arm against the FP64 path on the same inputs."""
     import numpy as np
     gpr = np.abs(ref["gp"]).max(axis=1)
+    params = {} if arm["gp"] is None else {
+        "max_param_grad_err": float(np.abs(arm["gp"] - ref["gp"]).max()),
+        "max_param_grad_err_rel": [float(np.abs(arm["gp"][k] - ref["gp"][k]).max() / gpr[k]) for k in range(4)]}
     return {"delta_e_per_atom_ha": (arm["energy"] - ref["energy"]) / N,
             "max_force_err_ha_bohr": float(np.abs(arm["gR"] - ref["gR"]).max()),
             "max_force_ha_bohr": float(np.abs(ref["gR"]).max()),
             "max_force_err_rel": float(np.abs(arm["gR"] - ref["gR"]).max() / np.abs(ref["gR"]).max()),
-            "max_param_grad_err": float(np.abs(arm["gp"] - ref["gp"]).max()),
-            "max_param_grad_err_rel": [float(np.abs(arm["gp"][k] - ref["gp"][k]).max() / gpr[k]) for k in range(4)],
+            **params,
             **({"max_lattice_grad_err_rel": float(np.abs(arm["gA"] - ref["gA"]).max() / np.abs(ref["gA"]).max())}
                if arm.get("gA") is not None and ref.get("gA") is not None else {})}
 
@@ -601,6 +613,16 @@ def run_ours(args):
                          "stage_ms": stage_means(a["profs"]),
                          "roofline": roofline_of(binding, name, precision_code(binding, name), a["profs"], a["ms"],
                                                  xk, xw)}
+        if not xper and not nl and args.learned_arm:   # the learned screening (no fallback) with the same matrix function
+            model = np.load(os.path.join(ROOT, "paper_2308_03140_gb300", "learned_scs_model.npz"))
+            a = time_arm(binding, dev, stream, xs, xp3, xp4, precision_code(binding, args.precision), scs_mode, xk, 1,
+                         barrier, max_over_ranks, learned=model)
+            a["ctx"].close()
+            name = f"learned_{args.precision}"
+            xarms[name] = a
+            sec[name] = {"value": world * xk / (a["ms"] / 1e3), "unit": UNIT, "ms_per_step": a["ms"] / xk,
+                         "steps": xk, "warmup": 1, "energy_ha": a["energy"], "gradients": "energy and coordinates",
+                         "stage_ms": stage_means(a["profs"])}
         if args.extra_fp64_steps > 0:
             f = time_arm(binding, dev, stream, xs, xp3, xp4, binding.MBD_PREC_FP64, scs_mode, args.extra_fp64_steps,
                          1, barrier, max_over_ranks)
@@ -642,11 +664,12 @@ def batch_section(binding, local, args, precision_name):
     scale = float(model["estimate_scale"]) if "estimate_scale" in model.files else 1.0
     arms = {"plain": dict(), "learned": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e-6,
                                              learned_estimate_scale=scale),
-            "learned_no_fallback": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e300)}
+            "learned_no_fallback": dict(scs_mode=binding.MBD_SCS_LEARNED, learned_max_error=1e300),
+            "plain_fp64": dict(precision=binding.MBD_PREC_FP64)}
     ctxs = {}
     for name, opt in arms.items():
-        m = binding.MBD(local, precision=precision, **opt)
-        if name != "plain":
+        m = binding.MBD(local, **{"precision": precision, **opt})
+        if opt.get("scs_mode") == binding.MBD_SCS_LEARNED:
             m.set_scs_model(model["params16"], model["mean"], model["std"])
         m.set_profiling(True)
         ctxs[name] = m
@@ -658,17 +681,17 @@ def batch_section(binding, local, args, precision_name):
         for s in systems:
             m.set_geometry(s.coords)
             m.set_free_atom_params(s.alpha0_ref, s.c6_ref, s.rvdw_ref, s.ratio)
-            E, gR, _, _ = m.evaluate(True, param_gradients=(name == "plain"))
+            E, gR, _, _ = m.evaluate(True, param_gradients=name.startswith("plain"))
             prof = m.profile()
             dev_ms += prof["total_ms"]
             launches[name] = launches.get(name, 0) + prof["launches"]
-            if name != "plain":
+            if name.startswith("learned"):
                 fb += int(m.learned_stats()["fell_back"])
             if record is not None:
                 record.append((E, gR))
         return dev_ms, fb
 
-    results, ref = {}, []
+    results, ref, records = {}, [], {}
     one_pass("plain", ref)   # reference energies and forces (also the plain arm's warm-up)
     for name in arms:
         if name != "plain":
@@ -680,14 +703,21 @@ def batch_section(binding, local, args, precision_name):
         dev_ms, fb = one_pass(name, rec)
         wall = time.perf_counter() - t0
         results[name] = {"solves_per_s_device": K / (dev_ms / 1e3), "solves_per_s_e2e": K / wall,
-                         "fallback_fraction": fb / K if name != "plain" else None, "gpu_launches": launches[name]}
+                         "fallback_fraction": fb / K if name.startswith("learned") else None,
+                         "gpu_launches": launches[name]}
+        records[name] = rec
+
+    def errors(rec, against):
+        dE = [abs(e - er) / s.n_atoms for (e, _), (er, _), s in zip(rec, against, systems)]
+        dF = [float(np.abs(g - gr).max()) for (_, g), (_, gr) in zip(rec, against)]
+        return {"mean_abs_de_per_atom_ha": float(np.mean(dE)), "max_abs_de_per_atom_ha": float(np.max(dE)),
+                "fraction_within_1e-6": float(np.mean(np.array(dE) <= 1e-6)), "max_force_err_ha_bohr": float(np.max(dF))}
+
+    for name in arms:   # against plain screening with the same matrix function, and against the FP64 path
         if name != "plain":
-            dE = [abs(e - er) / s.n_atoms for (e, _), (er, _), s in zip(rec, ref, systems)]
-            dF = [float(np.abs(g - gr).max()) for (_, g), (_, gr) in zip(rec, ref)]
-            results[name].update({"mean_abs_de_per_atom_ha": float(np.mean(dE)),
-                                  "max_abs_de_per_atom_ha": float(np.max(dE)),
-                                  "fraction_within_1e-6": float(np.mean(np.array(dE) <= 1e-6)),
-                                  "max_force_err_ha_bohr": float(np.max(dF))})
+            results[name].update(errors(records[name], ref))
+        if name != "plain_fp64":
+            results[name]["vs_fp64_path"] = errors(records[name], records["plain_fp64"])
     for m in ctxs.values():
         m.close()
     return {"config": {"workload": "batch4096", "clusters": K, "mean_atoms": float(np.mean([s.n_atoms for s in systems])),

@@ -584,10 +584,13 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(int B, const float *X
                      "r"(128));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    // layer 1 operands: standardised features of this thread's atom, W1
-    for (int k = 0; k < 128; ++k) {
-        const float x = (a < B && k < kF) ? (X[static_cast<long long>(a) * kF + k] - mean[k]) / stdv[k] : 0.0f;
-        put_split(Ahi, Alo, t, k, x);
+    // layer 1 operands: the standardised features of the CTA's atoms (read row by row, the
+    // threads along the features), W1
+    const int a0 = blockIdx.x * kMT;
+    for (int e = t; e < kMT * 128; e += kMT) {
+        const int row = e >> 7, k = e & 127, ar = a0 + row;
+        const float x = (ar < B && k < kF) ? (X[static_cast<long long>(ar) * kF + k] - mean[k]) / stdv[k] : 0.0f;
+        put_split(Ahi, Alo, row, k, x);
     }
     put_weights(Bs, P + oW1, kF, kH);
     fence_before();

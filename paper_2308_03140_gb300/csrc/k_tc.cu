@@ -28,72 +28,33 @@
 // tensor memory and returns.
 #include <algorithm>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include "internal.h"
+#include "tc_ops.cuh"
 #include "tc_tiles.cuh"
 
 namespace mbdgb {
 namespace {
 
+using namespace tcops;
+
 constexpr int TM = 128, TN = 128;
 constexpr int KB = 128;                         // bytes of K per stage per row (one swizzle atom)
 constexpr int TILE_BYTES = TM * KB;             // 16 KB
-constexpr long long kSpinCycles = 4000000000LL; // ~2 s at 2 GHz
 // Tensor-memory accumulation buffers of TN columns each (all 512 columns of the SM): chunk c
 // accumulates in buffer c % kBufs, so the MMAs run up to kBufs - 1 chunks ahead of the
 // epilogue warps that drain them.
 constexpr int kBufs = 4;
 
-__device__ __forceinline__ uint32_t su32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait on an mbarrier phase; false (and the error flag raised) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err, long long budget = kSpinCycles) {
-    const long long t0 = clock64();
-    while (!mbar_try(b, parity)) {
-        if (clock64() - t0 > budget) {
-            atomicOr(err, ST_TC_TIMEOUT);
-            return false;
-        }
-    }
-    return true;
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
-            su32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(su32(bar))
-        : "memory");
-}
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-    d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused for swizzled K-major)
-    d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset
-    d |= static_cast<uint64_t>(1) << 46;            // descriptor version
-    d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
-    return d;
-}
 // Instruction descriptor: FP32 accumulator, A/B format fmt (1 = bf16, 2 = tf32), both
 // K-major, N = TN, M = TM.
 __host__ __device__ constexpr uint32_t idesc(uint32_t fmt) {
@@ -113,25 +74,6 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
                 tmem),
             "l"(a), "l"(b), "r"(idesc(1)), "r"(acc));
 }
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
-
 // Element j of a packed split row (bf16 pairs for KIND 1, 32-bit words for KIND 2).
 template <int KIND>
 __device__ __forceinline__ void store_part(void *base, long long off, const uint32_t *w, int j) {
@@ -475,7 +417,7 @@ __global__ void __launch_bounds__(192, 1)
 constexpr int TNW = 256;
 constexpr int kWideBufs = 2;
 #ifndef EPI_REGS_OVERRIDE
-constexpr int EPI_REGS = 208;
+constexpr int EPI_REGS = 240;
 #else
 constexpr int EPI_REGS = EPI_REGS_OVERRIDE;
 #endif
@@ -514,7 +456,7 @@ template <int KIND>
 __global__ void __launch_bounds__(384, 1)
     k_tc_gemm_w(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                 const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs g,
-                int tiles_n) {
+                int tiles_n, const int2 *tile_of) {
     using Cfg = TcCfgW<KIND>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -566,7 +508,11 @@ __global__ void __launch_bounds__(384, 1)
             for (int w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
                 const int bz = w / wtiles;
                 int tm, TPn;
-                tctiles::wide_tile(w - bz * wtiles, g.mode, tiles_m, tiles_n, tm, TPn);
+                {
+                    const int2 c = tile_of[w - bz * wtiles];   // (tm, TPn) of the item, tabulated on the host
+                    tm = c.x;
+                    TPn = c.y;
+                }
                 const int ya = bz * g.M + tm * TM, yb = bz * g.N + TPn * TNW;
                 for (int kt = 0; kt < nk && !*abort_flag; ++kt, ++kg) {
                     const int s = kg % Cfg::STAGES;
@@ -636,7 +582,11 @@ __global__ void __launch_bounds__(384, 1)
         for (int w = blockIdx.x; w < items && ok; w += gridDim.x, cg += nchunks) {
             const int bz = w / wtiles;
             int tm, TPn;
-            tctiles::wide_tile(w - bz * wtiles, g.mode, tiles_m, tiles_n, tm, TPn);
+            {
+                    const int2 c = tile_of[w - bz * wtiles];   // (tm, TPn) of the item, tabulated on the host
+                    tm = c.x;
+                    TPn = c.y;
+                }
             const int tn = 2 * TPn + h;
             const bool write = tctiles::wide_half_valid(g.mode, tiles_n, tm, TPn, h);
             const float *Dp = g.D ? g.D + bz * g.sC : nullptr;
@@ -1063,6 +1013,36 @@ cudaError_t launch_tc(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// (tm, TPn) of every wide-tile work item of (mode, tiles_m, tiles_n), computed on the host by
+// the decomposition of tc_tiles.cuh and kept on the device for the life of the process (one
+// table per shape and device): the kernel's threads then look their tile up instead of walking
+// the super-tiles, which costs the single producer thread thousands of cycles per tile.
+cudaError_t wide_tile_table(int dev, int mode, int tiles_m, int tiles_n, const int2 **out) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int>, int2 *> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(dev, mode, tiles_m, tiles_n);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    const int n = tctiles::wide_tile_count(mode, tiles_m, tiles_n);
+    std::vector<int2> h(static_cast<size_t>(n));
+    for (int b = 0; b < n; ++b) tctiles::wide_tile(b, mode, tiles_m, tiles_n, h[b].x, h[b].y);
+    int2 *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int2) * std::max(n, 1));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(d, h.data(), sizeof(int2) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return e;
+    }
+    cache[key] = d;
+    *out = d;
+    return cudaSuccess;
+}
+
 template <int KIND>
 cudaError_t launch_tcw(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     using Cfg = TcCfgW<KIND>;
@@ -1091,8 +1071,11 @@ cudaError_t launch_tcw(const TcOperands &op, const TcArgs &g, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int grid = static_cast<int>(std::min<long long>(items, sms));
+    const int2 *table = nullptr;
+    e = wide_tile_table(dev, g.mode, tmt, tnt, &table);
+    if (e != cudaSuccess) return e;
     count_launches(1);
-    k_tc_gemm_w<KIND><<<grid, 384, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt);
+    k_tc_gemm_w<KIND><<<grid, 384, Cfg::SMEM, s>>>(a0, a1, b0, b1, g, tnt, table);
     return cudaGetLastError();
 }
 
