@@ -766,7 +766,7 @@ def run_kernel(args):
     (default 6016, the 2000-atom cluster's), operands
     as hi/lo parts of the --precision kind (bf16x3 or tf32x3), FP32 output and its parts; or
     (--kernel tc_gemm_update) the screening's trailing update C -= L21 L21^T of a 512-column
-    panel on the lower tiles (mode 1, 2-stage accumulation, in place)."""
+    panel on the lower tiles (mode 1, 8-stage accumulation as in the factorisation, in place)."""
     import torch
     from paper_2308_03140_gb300 import binding
     binding.load()
@@ -792,7 +792,7 @@ def run_kernel(args):
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     chunk = 8 if kind == 1 else 2   # the library's accumulation lengths for the kind
     if update:
-        chunk = 2   # the screening's accumulation length
+        chunk = 8   # the screening's accumulation length
         C.copy_(torch.randn(n, n, generator=g, dtype=torch.float32).to(dev))
 
         def launch():   # C = C - S S^T on the lower tiles (in place, as the factorisation does)

@@ -310,7 +310,7 @@ cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, i
             TcOperands op{H, L, H, L, pw, pw};
             TcArgs g{static_cast<int>(rem), static_cast<int>(rem), pw, -1.f, 1.f, A22, ld, A22, nullptr, nullptr,
                      nullptr, nullptr, nullptr, nullptr, 0, 1, status};
-            g.chunk_stages = 2;
+            g.chunk_stages = 8;   // 256 TF32 products per TMEM sum: the refinement absorbs the truncation
             g.batch = batch;
             g.sC = mstride;
             const cudaError_t e = tc_gemm(2, op, g, s);
