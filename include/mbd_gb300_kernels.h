@@ -161,7 +161,9 @@ int mbdk_mlp_forward(void *stream, int n_atoms, int n_members, const float *X, c
 /* Backward pass of sum(dY * Y) after mbdk_mlp_forward with a zcache, dY [n_members][n_atoms]
  * [16]: dX (optional) [n_members][n_atoms][122] receives the gradient with respect to the raw
  * features; grad (optional) [n_members][MBD_LEARNED_PARAMS] FP32 is ACCUMULATED with the
- * gradient with respect to the parameters (clear it first for a fresh gradient). */
+ * gradient with respect to the parameters (clear it first for a fresh gradient).  Without grad
+ * the products run on the tensor cores (TF32 hi/lo parts against the exact FP16 weights, as
+ * the forward), with grad in FP32 on the CUDA cores. */
 int mbdk_mlp_backward(void *stream, int n_atoms, int n_members, const float *X, const float *mean,
                       const float *std, const void *params_fp16, const float *zcache, const float *dY,
                       float *dX, float *grad);

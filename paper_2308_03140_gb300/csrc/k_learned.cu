@@ -639,6 +639,94 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(int B, const float *X
     }
 }
 
+// B operand of a backward product: W used as stored ([in][out], row n = input unit), rows
+// n < nin, K = the outputs k < nout (zero beyond).
+__device__ __forceinline__ void put_weights_rows(uint8_t *Bs, const __half *W, int nin, int nout) {
+    for (int e = threadIdx.x; e < 128 * 128; e += blockDim.x) {
+        const int n = e >> 7, k = e & 127;   // consecutive threads: consecutive outputs of one row
+        const float w = (n < nin && k < nout) ? __half2float(W[n * nout + k]) : 0.0f;
+        *reinterpret_cast<float *>(Bs + swz(n, k)) = w;
+    }
+}
+
+// Gradient of sum(dY * Y) with respect to the raw features on the tensor cores (the data
+// path of the backward, without parameter gradients): dh2 = dY W3^T, dz2 = dh2 silu'(z2),
+// dh1 = dz2 W2^T, dz1 = dh1 silu'(z1), dX = (dz1 W1^T) / std, each product as in the forward
+// (TF32 hi/lo parts of the FP32 left factor against the exact weights, FP32 accumulation in
+// TMEM).  grid (ceil(B / 128), members), 128 threads; zcache from the forward; a wait that
+// times out raises ST_TC_TIMEOUT in *err and leaves NaN in dX.
+__global__ void __launch_bounds__(128, 1) k_mlp_backward_dx_tc(int B, const float *stdv, const __half *params,
+                                                               const float *zcache, const float *dY, float *dX,
+                                                               int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *Ahi = smem, *Alo = smem + 4 * kSlab, *Bs = smem + 8 * kSlab;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 12 * kSlab);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int member = blockIdx.y, t = threadIdx.x, warp = t >> 5, a0 = blockIdx.x * kMT, a = a0 + t;
+    const __half *P = params + static_cast<long long>(member) * kParams;
+    const float *z1 = zcache + static_cast<long long>(member) * 2 * B * kH, *z2 = z1 + static_cast<long long>(B) * kH;
+    if (t == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
+                     "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    // dY rows of the CTA's atoms (K = the 16 outputs), W3 by rows
+    for (int e = t; e < kMT * 128; e += kMT) {
+        const int row = e >> 7, k = e & 127, ar = a0 + row;
+        const float v = (ar < B && k < kO) ? dY[(static_cast<long long>(member) * B + ar) * kO + k] : 0.0f;
+        put_split(Ahi, Alo, row, k, v);
+    }
+    put_weights_rows(Bs, P + oW3, kH, kO);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot + (static_cast<uint32_t>(warp * 32) << 16);
+    uint32_t phase = 0;
+    bool ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, kH, bar, phase, err);
+    for (int layer = 0; layer < 2 && ok; ++layer) {   // dz2 from dh2, then dz1 from dh1
+        const float *zc = layer == 0 ? z2 : z1;
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + c0, r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float dz = a < B ? __uint_as_float(r[j]) * dsilu(zc[static_cast<long long>(a) * kH + c0 + j]) : 0.0f;
+                put_split(Ahi, Alo, t, c0 + j, dz);
+            }
+        }
+        fence_before();
+        __syncthreads();   // every thread's reads of TMEM and of the weights are done
+        if (layer == 0) put_weights_rows(Bs, P + oW2, kH, kH);
+        else put_weights_rows(Bs, P + oW1, kF, kH);
+        phase ^= 1;
+        ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, kH, bar, phase, err);
+    }
+    // dX = acc / std over the 122 features (TMEM loads on every lane, stores for real atoms)
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+        uint32_t r[32];
+        if (ok) tmem_ld32(tmem + c0, r);
+        if (a < B)
+            for (int j = 0; j < 32; ++j) {
+                const int n = c0 + j;
+                if (n < kF)
+                    dX[(static_cast<long long>(member) * B + a) * kF + n] =
+                        ok ? __uint_as_float(r[j]) / stdv[n] : __int_as_float(0x7fc00000);
+            }
+    }
+    if (!ok && t == 0) mbar_wait(bar, phase, err, kSpinCycles / 8);   // let a late chain finish before freeing TMEM
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(*tmem_slot), "r"(128));
+    }
+}
+
 // Backward of sum(dY * Y): grid (ceil(B / 32), members), 128 threads.  Needs the cache of the
 // forward pass.  dX (optional) [member][B][74]: gradient with respect to the raw features.
 // grad (optional) [member][kParams] FP32, accumulated (atomic adds of per-CTA sums).
@@ -1044,6 +1132,22 @@ cudaError_t mlp_forward(int B, int members, const float *X, const float *mean, c
 cudaError_t mlp_backward(int B, int members, const float *X, const float *mean, const float *stdv,
                          const void *params16, const float *zcache, const float *dY, float *dX, float *grad,
                          cudaStream_t s) {
+    if (!grad) {   // the data path alone (the learned forces): on the tensor cores
+        static int *own_err = nullptr;
+        if (!own_err) {
+            cudaError_t e = cudaMalloc(&own_err, sizeof(int));
+            if (e != cudaSuccess) return e;
+            e = cudaMemset(own_err, 0, sizeof(int));
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_backward_dx_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kMlpTcSmem));
+        if (e != cudaSuccess) return e;
+        count_launches(1);
+        k_mlp_backward_dx_tc<<<dim3(cdiv(B, kMT), members), 128, kMlpTcSmem, s>>>(
+            B, stdv, static_cast<const __half *>(params16), zcache, dY, dX, own_err);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaFuncSetAttribute(k_mlp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kMlpSmem));
     if (e != cudaSuccess) return e;

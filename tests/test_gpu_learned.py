@@ -90,6 +90,8 @@ def test_mlp_forward_backward_match_oracle(B):
     dX = torch.zeros(2, B, F, dtype=torch.float32, device=DEV)
     grad = torch.zeros(2, binding.LEARNED_PARAMS, dtype=torch.float32, device=DEV)
     binding.mbdk_mlp_backward(Xg, mg, sg, pg, z, T(dY, torch.float32), dX, grad)
+    dX_tc = torch.zeros(2, B, F, dtype=torch.float32, device=DEV)   # the data path alone: tensor cores
+    binding.mbdk_mlp_backward(Xg, mg, sg, pg, z, T(dY, torch.float32), dX_tc, None)
     for mi in range(2):
         y, cache = LS.forward(Xs, P[mi])
         Yg = Y[mi].cpu().numpy()
@@ -100,6 +102,7 @@ def test_mlp_forward_backward_match_oracle(B):
         assert np.abs(gg - g_ref).max() <= 2e-5 * max(1.0, np.abs(g_ref).max())
         dX_ref = dXs / std.astype(np.float32)
         assert np.abs(dX[mi].cpu().numpy() - dX_ref).max() <= 2e-5 * max(1.0, np.abs(dX_ref).max())
+        assert np.abs(dX_tc[mi].cpu().numpy() - dX_ref).max() <= 2e-5 * max(1.0, np.abs(dX_ref).max())
 
 
 def test_mse_adam_and_gather_match_oracle():
