@@ -141,11 +141,16 @@ void trsv_blocked(const T *L, long long ld, long long mstride, int batch, const 
 // triangles; rows >= n are padding).  work: 2 * batch * 3 ld floats.
 // The factorisation is blocked in panels of kScsPanel columns (the first panel takes
 // ld mod kScsPanel when that is not 0, so every trailing matrix is a multiple of 128): inside a panel 64-wide
-// steps on the SIMT cores, the trailing update A22 -= L21 L21^T on the tensor cores
-// (TF32x3, k_tc_gemm, tiles of the lower triangle only).  panel: scratch of
-// 2 * batch * ld * kScsPanel 32-bit words.  Only the lower triangle of A32 is read or
-// written.  Tensor-core timeouts set ST_TC_TIMEOUT in *status; a launch error is returned.
+// steps on the SIMT cores over sub-panels of kScsSub columns, the rest of the panel updated
+// after each sub-panel on the tensor cores, and the trailing update A22 -= L21 L21^T on the
+// tensor cores (TF32x3, k_tc_gemm, tiles of the lower triangle only).  panel: scratch of
+// 2 * batch * ld * kScsPanel 32-bit words.  Only the lower triangle of A32 is read; tiles
+// that cross the diagonal are written whole.  Tensor-core timeouts set ST_TC_TIMEOUT in
+// *status; a launch error is returned.
 constexpr int kScsPanel = 1024;
+// Inside a panel, sub-panels of kScsSub columns are factorised by the 64-wide steps and the
+// panel's columns right of each are updated on the tensor cores (a product of K = kScsSub).
+constexpr int kScsSub = 512;
 cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv,
                                   uint32_t *panel, int *status, cudaStream_t s);
 void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,

@@ -285,20 +285,45 @@ cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, i
     const int first = static_cast<int>(ld % kPanel) ? static_cast<int>(ld % kPanel) : kPanel;
     for (long long p0 = 0; p0 < ld;) {
         const int pw = p0 == 0 ? first : kPanel;   // panel columns [p0, p0 + pw)
-        // right-looking 64-wide steps restricted to the panel's columns
-        for (long long k0 = p0; k0 < p0 + pw; k0 += T64) {
-            const int k = static_cast<int>(k0 / T64);
-            count_launches(1);
-            k_spotrf_diag<<<batch, 256, 0, s>>>(A32 + k0 * ld + k0, ld, mstride, dinv + k * 4096LL, dstride, status);
-            const int rem = static_cast<int>(ld - k0 - T64);   // rows below the diagonal block
-            if (rem <= 0) continue;
-            float *A21 = A32 + (k0 + T64) * ld + k0;
-            sgemm_nt(A21, dinv + k * 4096LL, A21, ld, 64, ld, mstride, dstride, mstride, rem, 64, 64, batch, 1.f, 0.f,
-                     0, s);
-            const int w = static_cast<int>(p0 + pw - k0 - T64);   // panel columns right of the block
-            if (w > 0)
-                sgemm_nt(A21, A21, A21 + T64, ld, ld, ld, mstride, mstride, mstride, rem, w, 64, batch, -1.f, 1.f, 0,
-                         s);
+        for (long long s0 = p0; s0 < p0 + pw; s0 += kScsSub) {
+            const long long s1 = std::min<long long>(s0 + kScsSub, p0 + pw);   // sub-panel columns [s0, s1)
+            // right-looking 64-wide steps restricted to the sub-panel's columns
+            for (long long k0 = s0; k0 < s1; k0 += T64) {
+                const int k = static_cast<int>(k0 / T64);
+                count_launches(1);
+                k_spotrf_diag<<<batch, 256, 0, s>>>(A32 + k0 * ld + k0, ld, mstride, dinv + k * 4096LL, dstride,
+                                                    status);
+                const int rem = static_cast<int>(ld - k0 - T64);   // rows below the diagonal block
+                if (rem <= 0) continue;
+                float *A21 = A32 + (k0 + T64) * ld + k0;
+                sgemm_nt(A21, dinv + k * 4096LL, A21, ld, 64, ld, mstride, dstride, mstride, rem, 64, 64, batch, 1.f,
+                         0.f, 0, s);
+                const int w = static_cast<int>(s1 - k0 - T64);   // sub-panel columns right of the block
+                if (w > 0)
+                    sgemm_nt(A21, A21, A21 + T64, ld, ld, ld, mstride, mstride, mstride, rem, w, 64, batch, -1.f, 1.f,
+                             0, s);
+            }
+            // the panel's columns right of the sub-panel, A[s1:, s1:p0+pw) -= L[s1:, s0:s1) L[s1:p0+pw, s0:s1)^T,
+            // on the tensor cores (TF32x3 parts; every tile of the block, whose part above the
+            // diagonal the factorisation does not read)
+            const int wr = static_cast<int>(p0 + pw - s1);
+            if (wr > 0) {
+                const long long r1 = ld - s1;
+                const int sw = static_cast<int>(s1 - s0);
+                uint32_t *HA = panel, *LA = panel + static_cast<long long>(batch) * r1 * sw;
+                uint32_t *HB = LA + static_cast<long long>(batch) * r1 * sw, *LB = HB + static_cast<long long>(batch) * wr * sw;
+                split_panel_tf32(A32 + s1 * ld + s0, ld, mstride, batch, r1, sw, HA, LA, s);
+                split_panel_tf32(A32 + s1 * ld + s0, ld, mstride, batch, wr, sw, HB, LB, s);
+                float *C = A32 + s1 * ld + s1;
+                TcOperands op{HA, LA, HB, LB, sw, sw};
+                TcArgs g{static_cast<int>(r1), wr, sw, -1.f, 1.f, C, ld, C, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, 0, 0, status};
+                g.chunk_stages = 8;
+                g.batch = batch;
+                g.sC = mstride;
+                const cudaError_t e = tc_gemm(2, op, g, s);
+                if (e != cudaSuccess) return e;
+            }
         }
         const long long t0 = p0 + pw, rem = ld - t0;   // trailing matrix [t0, ld)^2
         if (rem > 0) {
