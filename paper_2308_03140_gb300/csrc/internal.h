@@ -349,12 +349,17 @@ void scs_features(int n_atoms, int n_sys, const int *offsets, const double *R, c
                   const double *c6ref, const double *rref, const double *ratio, float *X, double *work,
                   cudaStream_t s);
 // MLP forward on the tensor cores; err (optional, device int) receives ST_TC_TIMEOUT if a wait
-// runs out (the outputs are then NaN).
+// runs out (the outputs are then NaN).  packed (optional): the weights in the kernels' shared-
+// memory layout, kLearnedPackedFloats per member, from mlp_pack (else the kernels convert
+// the FP16 parameters themselves).
+constexpr long long kLearnedPackedFloats = 6LL * 128 * 128;
+cudaError_t mlp_pack(int members, const void *params16, float *packed, cudaStream_t s);
 cudaError_t mlp_forward(int B, int members, const float *X, const float *mean, const float *stdv,
-                        const void *params16, float *Y, float *zcache, cudaStream_t s, int *err = nullptr);
+                        const void *params16, float *Y, float *zcache, cudaStream_t s, int *err = nullptr,
+                        const float *packed = nullptr);
 cudaError_t mlp_backward(int B, int members, const float *X, const float *mean, const float *stdv,
                          const void *params16, const float *zcache, const float *dY, float *dX, float *grad,
-                         cudaStream_t s);
+                         cudaStream_t s, const float *packed = nullptr);
 void mse_grad(long long n, const float *y, const float *t, float *dy, double *loss, cudaStream_t s);
 void adam_step(long long n, float *p, const float *g, float *m, float *v, int step, float lr, void *p16,
                cudaStream_t s);

@@ -512,6 +512,7 @@ constexpr int kMT = 128;                 // atoms per CTA
 constexpr int kSlab = kMT * 128;         // bytes of one 32-element K slab of a 128-row operand
 constexpr size_t kMlpTcSmem = 3 * 4 * static_cast<size_t>(kSlab) + 1024 + 64;
 static_assert(kF <= 128 && kH == 128 && kO == 16, "layer shapes of the tensor-core MLP");
+static_assert(6LL * kSlab == kLearnedPackedFloats, "packed weight images: six of 128 x 128 FP32");
 
 __device__ __forceinline__ uint32_t swz(int r, int k) {
     const int kk = k & 31;
@@ -540,6 +541,57 @@ __device__ __forceinline__ void put_weights(uint8_t *Bs, const __half *W, int ni
         *reinterpret_cast<float *>(Bs + swz(n, k)) = w;
     }
 }
+// The six B operands of the tensor-core MLP of each member in their shared-memory layout
+// (FP32, 64 KB each, zero where the layer has no row or input): 0-2 the forward's W1^T, W2^T,
+// W3^T (rows = outputs), 3-5 the backward's W3, W2, W1 (rows = inputs).  Built once per model;
+// the kernels then fetch each with one bulk copy.
+constexpr int kImgFloats = 4 * kSlab / 4;
+__global__ void k_mlp_pack(int members, const __half *params, float *packed) {
+    const long long total = static_cast<long long>(members) * 6 * 128 * 128;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(e / (6 * 128 * 128)), img = static_cast<int>((e / (128 * 128)) % 6);
+        const int n = static_cast<int>((e >> 7) & 127), k = static_cast<int>(e & 127);
+        const __half *P = params + static_cast<long long>(m) * kParams;
+        float w = 0.0f;
+        switch (img) {
+            case 0: w = k < kF ? __half2float(P[oW1 + k * kH + n]) : 0.0f; break;             // W1^T
+            case 1: w = __half2float(P[oW2 + k * kH + n]); break;                             // W2^T
+            case 2: w = n < kO ? __half2float(P[oW3 + k * kO + n]) : 0.0f; break;             // W3^T
+            case 3: w = k < kO ? __half2float(P[oW3 + n * kO + k]) : 0.0f; break;             // W3
+            case 4: w = __half2float(P[oW2 + n * kH + k]); break;                             // W2
+            default: w = n < kF ? __half2float(P[oW1 + n * kH + k]) : 0.0f; break;            // W1
+        }
+        packed[(static_cast<long long>(m) * 6 + img) * kImgFloats + swz(n, k) / 4] = w;
+    }
+}
+
+// Weights of the next product into Bs: one bulk copy of the packed image (thread 0 issues it,
+// every thread waits for it before the MMA) or, without packed images, the threads' own
+// converting writes.
+struct WeightLoad {
+    uint64_t *bar;
+    uint32_t phase;
+    bool pending;
+};
+__device__ __forceinline__ void weights_issue(uint8_t *Bs, const float *img, WeightLoad &wl) {
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(wl.bar, 4 * kSlab);
+        bulk_load(Bs, img, 4 * kSlab, wl.bar);
+    }
+    wl.pending = true;
+}
+__device__ __forceinline__ bool weights_wait(WeightLoad &wl, int *err) {
+    const bool ok = mbar_wait(wl.bar, wl.phase, err);
+    wl.phase ^= 1;
+    wl.pending = false;
+    return ok;
+}
+// Before the CTA exits: a copy still in flight (a wait that gave up earlier) must land first.
+__device__ __forceinline__ void weights_drain(WeightLoad &wl, int *err) {
+    if (wl.pending && threadIdx.x == 0) mbar_wait(wl.bar, wl.phase, err, kSpinCycles / 8);
+}
+
 // The layer's MMA chain (one thread) and its completion on bar; all threads wait (bounded).
 __device__ __forceinline__ bool mlp_layer(uint32_t tmem, uint8_t *Ahi, uint8_t *Alo, uint8_t *Bs, int n,
                                           uint64_t *bar, uint32_t phase, int *err) {
@@ -567,18 +619,23 @@ __device__ __forceinline__ bool mlp_layer(uint32_t tmem, uint8_t *Ahi, uint8_t *
 // ST_TC_TIMEOUT in *err and leaves NaN outputs.
 __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(int B, const float *X, const float *mean,
                                                            const float *stdv, const __half *params, float *Y,
-                                                           float *zcache, int *err) {
+                                                           float *zcache, const float *packed, int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *Ahi = smem, *Alo = smem + 4 * kSlab, *Bs = smem + 8 * kSlab;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 12 * kSlab);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    WeightLoad wl{bar + 1, 0, false};
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
     const int member = blockIdx.y, t = threadIdx.x, warp = t >> 5, a = blockIdx.x * kMT + t;
     const __half *P = params + static_cast<long long>(member) * kParams;
+    const float *img = packed ? packed + static_cast<long long>(member) * 6 * kImgFloats : nullptr;
     if (t == 0) {
         mbar_init(bar, 1);
+        mbar_init(wl.bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    __syncthreads();
+    if (img) weights_issue(Bs, img, wl);   // W1^T under the writes of the features
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
                      "r"(128));
@@ -592,15 +649,18 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(int B, const float *X
         const float x = (ar < B && k < kF) ? (X[static_cast<long long>(ar) * kF + k] - mean[k]) / stdv[k] : 0.0f;
         put_split(Ahi, Alo, row, k, x);
     }
-    put_weights(Bs, P + oW1, kF, kH);
+    bool ok = true;
+    if (img) ok = weights_wait(wl, err);
+    else put_weights(Bs, P + oW1, kF, kH);
     fence_before();
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;
     fence_after();
     const uint32_t tmem = *tmem_slot + (static_cast<uint32_t>(warp * 32) << 16);
     float *z1 = zcache ? zcache + static_cast<long long>(member) * 2 * B * kH : nullptr;
     float *z2 = zcache ? z1 + static_cast<long long>(B) * kH : nullptr;
     uint32_t phase = 0;
-    bool ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, kH, bar, phase, err);
+    if (ok) ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, kH, bar, phase, err);
+    if (ok && img) weights_issue(Bs, img + kImgFloats, wl);   // W2^T under the epilogue
     // hidden layers: z = acc + b -> cache; h = silu(z) -> the next layer's A operand
     for (int layer = 0; layer < 2 && ok; ++layer) {
         const __half *bias = P + (layer == 0 ? ob1 : ob2);
@@ -617,10 +677,13 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(int B, const float *X
         }
         fence_before();
         __syncthreads();   // every thread's reads of TMEM and of the weights are done
-        if (layer == 0) put_weights(Bs, P + oW2, kH, kH);
+        if (img) ok = weights_wait(wl, err);
+        else if (layer == 0) put_weights(Bs, P + oW2, kH, kH);
         else put_weights(Bs, P + oW3, kH, kO);
+        ok = __syncthreads_and(ok) != 0;
         phase ^= 1;
-        ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, layer == 0 ? kH : kO, bar, phase, err);
+        if (ok) ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, layer == 0 ? kH : kO, bar, phase, err);
+        if (ok && img && layer == 0) weights_issue(Bs, img + 2 * kImgFloats, wl);   // W3^T under the epilogue
     }
     // output layer: y = acc + b3 (16 columns).  The TMEM load is warp-collective: every lane
     // takes part (ok is uniform over the CTA), only the rows of real atoms are stored.
@@ -631,6 +694,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(int B, const float *X
         for (int o = 0; o < kO; ++o) y[o] = ok ? __uint_as_float(r[o]) + __half2float(P[ob3 + o]) : __int_as_float(0x7fc00000);
     }
     if (!ok && t == 0) mbar_wait(bar, phase, err, kSpinCycles / 8);   // let a late chain finish before freeing TMEM
+    weights_drain(wl, err);
     fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -657,19 +721,24 @@ __device__ __forceinline__ void put_weights_rows(uint8_t *Bs, const __half *W, i
 // times out raises ST_TC_TIMEOUT in *err and leaves NaN in dX.
 __global__ void __launch_bounds__(128, 1) k_mlp_backward_dx_tc(int B, const float *stdv, const __half *params,
                                                                const float *zcache, const float *dY, float *dX,
-                                                               int *err) {
+                                                               const float *packed, int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *Ahi = smem, *Alo = smem + 4 * kSlab, *Bs = smem + 8 * kSlab;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 12 * kSlab);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    WeightLoad wl{bar + 1, 0, false};
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
     const int member = blockIdx.y, t = threadIdx.x, warp = t >> 5, a0 = blockIdx.x * kMT, a = a0 + t;
     const __half *P = params + static_cast<long long>(member) * kParams;
+    const float *img = packed ? packed + (static_cast<long long>(member) * 6 + 3) * kImgFloats : nullptr;
     const float *z1 = zcache + static_cast<long long>(member) * 2 * B * kH, *z2 = z1 + static_cast<long long>(B) * kH;
     if (t == 0) {
         mbar_init(bar, 1);
+        mbar_init(wl.bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    __syncthreads();
+    if (img) weights_issue(Bs, img, wl);   // W3 by rows under the writes of dY
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
                      "r"(128));
@@ -681,13 +750,16 @@ __global__ void __launch_bounds__(128, 1) k_mlp_backward_dx_tc(int B, const floa
         const float v = (ar < B && k < kO) ? dY[(static_cast<long long>(member) * B + ar) * kO + k] : 0.0f;
         put_split(Ahi, Alo, row, k, v);
     }
-    put_weights_rows(Bs, P + oW3, kH, kO);
+    bool ok = true;
+    if (img) ok = weights_wait(wl, err);
+    else put_weights_rows(Bs, P + oW3, kH, kO);
     fence_before();
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;
     fence_after();
     const uint32_t tmem = *tmem_slot + (static_cast<uint32_t>(warp * 32) << 16);
     uint32_t phase = 0;
-    bool ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, kH, bar, phase, err);
+    if (ok) ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, kH, bar, phase, err);
+    if (ok && img) weights_issue(Bs, img + kImgFloats, wl);   // W2 under the epilogue
     for (int layer = 0; layer < 2 && ok; ++layer) {   // dz2 from dh2, then dz1 from dh1
         const float *zc = layer == 0 ? z2 : z1;
         for (int c0 = 0; c0 < kH; c0 += 32) {
@@ -701,10 +773,13 @@ __global__ void __launch_bounds__(128, 1) k_mlp_backward_dx_tc(int B, const floa
         }
         fence_before();
         __syncthreads();   // every thread's reads of TMEM and of the weights are done
-        if (layer == 0) put_weights_rows(Bs, P + oW2, kH, kH);
+        if (img) ok = weights_wait(wl, err);
+        else if (layer == 0) put_weights_rows(Bs, P + oW2, kH, kH);
         else put_weights_rows(Bs, P + oW1, kF, kH);
+        ok = __syncthreads_and(ok) != 0;
         phase ^= 1;
-        ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, kH, bar, phase, err);
+        if (ok) ok = mlp_layer(*tmem_slot, Ahi, Alo, Bs, kH, bar, phase, err);
+        if (ok && img && layer == 0) weights_issue(Bs, img + 2 * kImgFloats, wl);   // W1 under the epilogue
     }
     // dX = acc / std over the 122 features (TMEM loads on every lane, stores for real atoms)
     for (int c0 = 0; c0 < kH; c0 += 32) {
@@ -719,6 +794,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_backward_dx_tc(int B, const floa
             }
     }
     if (!ok && t == 0) mbar_wait(bar, phase, err, kSpinCycles / 8);   // let a late chain finish before freeing TMEM
+    weights_drain(wl, err);
     fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -1108,8 +1184,15 @@ void scs_features(int n_atoms, int n_sys, const int *offsets, const double *R, c
     k_dyson_hop<3><<<wb, 256, 0, s>>>(n_atoms, n_sys, offsets, R, work, X);
 }
 
+cudaError_t mlp_pack(int members, const void *params16, float *packed, cudaStream_t s) {
+    count_launches(1);
+    k_mlp_pack<<<std::min(cdiv(static_cast<long long>(members) * 6 * 128 * 128, 256), 2432), 256, 0, s>>>(
+        members, static_cast<const __half *>(params16), packed);
+    return cudaGetLastError();
+}
+
 cudaError_t mlp_forward(int B, int members, const float *X, const float *mean, const float *stdv,
-                        const void *params16, float *Y, float *zcache, cudaStream_t s, int *err) {
+                        const void *params16, float *Y, float *zcache, cudaStream_t s, int *err, const float *packed) {
     static int *own_err = nullptr;   // the timeout flag when the caller passes none
     if (!err) {
         if (!own_err) {
@@ -1125,13 +1208,13 @@ cudaError_t mlp_forward(int B, int members, const float *X, const float *mean, c
     if (e != cudaSuccess) return e;
     count_launches(1);
     k_mlp_forward_tc<<<dim3(cdiv(B, kMT), members), 128, kMlpTcSmem, s>>>(
-        B, X, mean, stdv, static_cast<const __half *>(params16), Y, zcache, err);
+        B, X, mean, stdv, static_cast<const __half *>(params16), Y, zcache, packed, err);
     return cudaGetLastError();
 }
 
 cudaError_t mlp_backward(int B, int members, const float *X, const float *mean, const float *stdv,
                          const void *params16, const float *zcache, const float *dY, float *dX, float *grad,
-                         cudaStream_t s) {
+                         cudaStream_t s, const float *packed) {
     if (!grad) {   // the data path alone (the learned forces): on the tensor cores
         static int *own_err = nullptr;
         if (!own_err) {
@@ -1145,7 +1228,7 @@ cudaError_t mlp_backward(int B, int members, const float *X, const float *mean, 
         if (e != cudaSuccess) return e;
         count_launches(1);
         k_mlp_backward_dx_tc<<<dim3(cdiv(B, kMT), members), 128, kMlpTcSmem, s>>>(
-            B, stdv, static_cast<const __half *>(params16), zcache, dY, dX, own_err);
+            B, stdv, static_cast<const __half *>(params16), zcache, dY, dX, packed, own_err);
         return cudaGetLastError();
     }
     cudaError_t e = cudaFuncSetAttribute(k_mlp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,

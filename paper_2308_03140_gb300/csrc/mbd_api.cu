@@ -150,6 +150,7 @@ struct mbd_ctx {
     float *dmeanstd = nullptr, *dfeat = nullptr, *dYl = nullptr;
     double *dspread = nullptr, *dmoments = nullptr, *dadj = nullptr;
     float *dzc = nullptr, *dXl = nullptr;   // MLP cache and feature gradient (learned forces)
+    float *dpacked = nullptr;               // the members' weights in the MLP kernels' layout
     int *doffs = nullptr;
     double learned_est = 0.0;
     int learned_fallback = 0;
@@ -252,7 +253,8 @@ int ensure_learned(mbd_ctx *ctx) {
                              al(sizeof(float) * M * N * 16) + al(sizeof(double) * nf1 * N) +
                              al(sizeof(double) * kLearnedWork * N) + al(sizeof(double) * kLearnedAdjointWork * N) +
                              al(sizeof(float) * M * 2 * N * 128) +
-                             al(sizeof(float) * M * N * kLF) + al(sizeof(int) * 2);
+                             al(sizeof(float) * M * N * kLF) + al(sizeof(float) * M * kLearnedPackedFloats) +
+                             al(sizeof(int) * 2);
         cudaError_t e = cudaSuccess;
         if (!ctx->lslab || ctx->lbytes < bytes) {   // re-carved in place when large enough
             if (ctx->lslab) cudaFree(ctx->lslab);
@@ -271,6 +273,7 @@ int ensure_learned(mbd_ctx *ctx) {
         ctx->dadj = reinterpret_cast<double *>(p); p += al(sizeof(double) * kLearnedAdjointWork * N);
         ctx->dzc = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * 2 * N * 128);
         ctx->dXl = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * N * kLF);
+        ctx->dpacked = reinterpret_cast<float *>(p); p += al(sizeof(float) * M * kLearnedPackedFloats);
         ctx->doffs = reinterpret_cast<int *>(p);
         const int offs[2] = {0, N};
         e = cudaMemcpy(ctx->doffs, offs, sizeof(offs), cudaMemcpyHostToDevice);
@@ -284,6 +287,8 @@ int ensure_learned(mbd_ctx *ctx) {
         if (e == cudaSuccess) e = cudaMemcpy(ctx->dmeanstd, ctx->hmean.data(), sizeof(float) * kLF, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(ctx->dmeanstd + kLF, ctx->hstd.data(), sizeof(float) * kLF, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = mlp_pack(M, ctx->dmodel, ctx->dpacked, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_fail(ctx, "learned_screening", e);
         ctx->model_dirty = false;
     }
@@ -1079,7 +1084,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
         prepare_atoms(b, ctx->dstatus, s);
         scs_features(N, 1, ctx->doffs, in.R, in.a0ref, in.c6ref, in.rref, in.ratio, ctx->dfeat, ctx->dmoments, s);
         const cudaError_t ef = mlp_forward(N, ctx->members, ctx->dfeat, ctx->dmeanstd, ctx->dmeanstd + kLF, ctx->dmodel,
-                                           ctx->dYl, want_grad ? ctx->dzc : nullptr, s);
+                                           ctx->dYl, want_grad ? ctx->dzc : nullptr, s, nullptr, ctx->dpacked);
         if (ef != cudaSuccess) return cuda_fail(ctx, "learned_screening", ef);
         learned_alpha(N, ctx->members, nf1, ctx->dalu, ctx->dYl, ctx->dabar, ctx->dspread, s);
         screened_params(b, ctx->dstatus, s);
@@ -1263,7 +1268,7 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
             // the members' outputs, the network and the features
             learned_dy(N, ctx->members, nf1, ctx->dh, ctx->dabar, ctx->dYl, s);
             const cudaError_t eb = mlp_backward(N, ctx->members, ctx->dfeat, ctx->dmeanstd, ctx->dmeanstd + kLF,
-                                                ctx->dmodel, ctx->dzc, ctx->dYl, ctx->dXl, nullptr, s);
+                                                ctx->dmodel, ctx->dzc, ctx->dYl, ctx->dXl, nullptr, s, ctx->dpacked);
             if (eb != cudaSuccess) return cuda_fail(ctx, "learned_screening", eb);
             learned_forces(N, ctx->doffs, in.R, in.a0ref, in.rref, in.ratio, ctx->dmoments, ctx->dXl, ctx->members,
                            ctx->dadj, ctx->dgR, s);

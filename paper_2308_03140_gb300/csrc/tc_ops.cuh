@@ -58,6 +58,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
     return d;
 }
+// Bulk copy (TMA, untiled) of `bytes` from global to shared memory, completing on bar;
+// both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
                  : "memory");
