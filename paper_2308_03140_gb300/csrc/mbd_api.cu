@@ -36,6 +36,14 @@ constexpr int kRefineSteps = 1;
 // force error measured at 2000 atoms with it (3e-6 of the largest force) is well inside that.
 constexpr int kAdjointRefineSteps = 0;
 constexpr int kLanczosSteps = 48; // Lanczos steps of the spectrum estimate of Q
+// ... and in the mixed modes for Q of order <= kLanczosSmallOrder: on the spectra of clusters of
+// 70-500 atoms the mixed loop, which stops at its precision floor, takes the same number of
+// steps (8-9) from a 24-step estimate as from a 48-step one (the lower estimate is then 3-10
+// times higher, which only shortens the first steps), while the 24 steps save 48 of the
+// evaluation's ~190 launches.  The FP64 loop, which converges further, can take one step
+// more from it (11 against 10 on a 500-atom cluster) and keeps the 48.
+constexpr int kLanczosStepsSmall = 24;
+constexpr long long kLanczosSmallOrder = 2048;
 // Precision floor of the TF32x3 Newton-Schulz iteration per unit of sqrt(n): |I - Z Y|_F
 // settles at about 1.04e-7 sqrt(n) (8.1e-6 at n = 6000).  A step taken from a residual r whose
 // exact successor bound 0.875 r^2 lies below this is the last useful one.  The coarser kinds
@@ -1126,7 +1134,8 @@ int run(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool
     // (500-2000 atom clusters), so a quarter of it is the lower bound of the scaled
     // iteration.  A bound on either side of the true one only costs steps (see below); on the
     // spectra of those clusters a quarter takes one step fewer than a half.
-    const int lz_steps = std::min(kLanczosSteps, static_cast<int>(ld));
+    const bool short_run = !fp64_path(ctx->opt.precision) && ld <= kLanczosSmallOrder;
+    const int lz_steps = std::min(short_run ? kLanczosStepsSmall : kLanczosSteps, static_cast<int>(ld));
     if (fp64_path(ctx->opt.precision))
         lanczos_coefficients(ctx->dQ, ld, lz_steps, ctx->dP, ctx->dscal + 8, s);
     else   // the bounds need a few digits; the products read an FP32 copy of Q (in the FP32 Y buffer)

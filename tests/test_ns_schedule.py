@@ -76,7 +76,9 @@ def spectrum():
         be.append(beta)
         vp, v = v, w / beta
     ritz = np.linalg.eigvalsh(np.diag(al) + np.diag(be[:-1], 1) + np.diag(be[:-1], -1))
-    return lam, ritz.min()
+    k = 24   # the library's shorter run for matrices of order <= 2048 (this one: 1500)
+    ritz24 = np.linalg.eigvalsh(np.diag(al[:k]) + np.diag(be[:k - 1], 1) + np.diag(be[:k - 1], -1))
+    return lam, ritz.min(), ritz24.min()
 
 
 def run(lib, lam, ritz, fraction, mixed, tol, floor_el):
@@ -99,7 +101,7 @@ def test_plain_step_bound_and_scaled_step_below_its_bound():
 
 
 def test_schedule_on_the_spectrum(host, spectrum):
-    lam, ritz = spectrum
+    lam, ritz, ritz24 = spectrum
     assert 2.5 < ritz / lam.min() < 4          # the Lanczos minimum lags the spectrum's bottom
     # mixed loop with the TF32x3 precision floor: the floor test stops it at 9 steps, one
     # step below the old half-minimum bound, with the exact residual below the floor
@@ -113,3 +115,10 @@ def test_schedule_on_the_spectrum(host, spectrum):
     for frac in (4.0, 1e-3):
         it_x, r_x = run(host, lam, ritz, frac, 0, 1e-8, 0.0)
         assert r_x < 1e-13 and it_x <= it64 + 6
+    # the 24-step estimate that the mixed modes use for matrices of order <= 2048: a higher Ritz
+    # minimum and no more steps of the mixed loop (the FP64 loop, which keeps 48, would take one more)
+    assert ritz24 > ritz
+    it24, r24 = run(host, lam, ritz24, 0.25, 1, 1e-8, 1.04e-7)
+    assert it24 <= it and r24 < 1.04e-7 * np.sqrt(len(lam))
+    it24_64, r24_64 = run(host, lam, ritz24, 0.25, 0, 1e-8, 0.0)
+    assert it24_64 <= it64 + 1 and r24_64 < 1e-13
