@@ -150,7 +150,7 @@ void trsv_blocked(const T *L, long long ld, long long mstride, int batch, const 
 constexpr int kScsPanel = 1024;
 // Inside a panel, sub-panels of kScsSub columns are factorised by the 64-wide steps and the
 // panel's columns right of each are updated on the tensor cores (a product of K = kScsSub).
-constexpr int kScsSub = 512;
+constexpr int kScsSub = 256;
 cudaError_t cholesky_f32_from_f64(const double *A64, float *A32, long long ld, int batch, float *dinv,
                                   uint32_t *panel, int *status, cudaStream_t s);
 void refine_solve3(const double *A64, const float *L32, const float *dinv, long long ld, int n, int batch,
