@@ -48,7 +48,9 @@ extern "C" {
  * iterations on the 5th-generation tensor cores with FP32 accumulation, then one FP64
  * correction: with Z ~ Q^{-1/2}, V = Q Z and W = Z V (FP64), Tr Q^{1/2} is taken as
  * (3 Tr V - sum V o W)/2, whose error is second order in the error of Z; the energy
- * subtraction and all sums stay in FP64 with compensation.  Gradients use Z. */
+ * subtraction and all sums stay in FP64 with compensation.  Gradients use Z.  In the same
+ * modes the screening matrices are factored in FP32 (tensor-core TF32x3 updates) and each
+ * solution is refined once against the FP64 matrix. */
 #define MBD_PREC_FP64 0           /* plain FP64 throughout                           */
 #define MBD_PREC_TF32 1           /* TF32 tensor-core products, FP64 correction      */
 #define MBD_PREC_BF16X3 2         /* bf16 hi/lo split products (3 per GEMM), FP64 correction */
@@ -130,8 +132,9 @@ int mbd_destroy(mbd_ctx *ctx);
  * Monkhorst-Pack grid k_grid [3] (k-points (2m - n_c - 1)/(2 n_c) in fractional
  * reciprocal coordinates, m = 1..n_c, Sec. 2.2); lattice and k_grid are both NULL for a
  * finite system.  Allocates the device workspace for that size.  Periodic systems run in
- * FP64 only (MBD_ERR_UNSUPPORTED for the reduced-precision modes and for
- * MBD_PREC_FP64_SPLIT). */
+ * FP64 or in the tensor-core modes (TF32, BF16X3, TF32X3: each Q(q) through its real
+ * symmetric embedding); MBD_PREC_FP64_SPLIT returns MBD_ERR_UNSUPPORTED here for them, and
+ * learned screening returns it at evaluation. */
 int mbd_set_geometry(mbd_ctx *ctx, int n_atoms, const double *coords, const double *lattice,
                      const int *k_grid);
 

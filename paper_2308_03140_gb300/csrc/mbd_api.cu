@@ -811,8 +811,9 @@ void backward_periodic(mbd_ctx *ctx, cudaStream_t s, const AtomBufs &b, const do
 }
 
 // Periodic evaluation (Secs. 2.2 and 2.3): Gamma-point screening, Q(q) for every Bloch vector of
-// the grid, batched complex coupled Newton-Schulz (FP64, 4 real GEMMs per complex
-// product), E = (1/nk) sum_q 1/2 Tr Q(q)^{1/2} - 3/2 sum omega_bar.
+// the grid, batched complex coupled Newton-Schulz (FP64, 4 real GEMMs per complex product;
+// the tensor-core modes take each Q(q) as its real symmetric embedding through the finite
+// matrix function), E = (1/nk) sum_q 1/2 Tr Q(q)^{1/2} - 3/2 sum omega_bar.
 int run_periodic(mbd_ctx *ctx, cudaStream_t s, const Inputs &in, const Outputs &out, bool want_grad) {
     if (ctx->opt.scs_mode == MBD_SCS_LEARNED)
         return fail(ctx, MBD_ERR_UNSUPPORTED, "learned_screening", "learned screening is for finite systems");
