@@ -42,7 +42,7 @@ extern "C" {
 #define MBD_ERR_NOT_CONVERGED 5   /* Newton-Schulz iteration cap reached             */
 #define MBD_ERR_CUDA 6            /* CUDA runtime error                              */
 #define MBD_ERR_STATE 7           /* call order (geometry/parameters not set)        */
-#define MBD_ERR_UNSUPPORTED 8     /* option not available in this build              */
+#define MBD_ERR_UNSUPPORTED 8     /* option not supported for this system or mode    */
 
 /* Arithmetic of the matrix function Q^{+-1/2}.  The mixed modes run the Newton-Schulz
  * iterations on the 5th-generation tensor cores with FP32 accumulation, then one FP64
