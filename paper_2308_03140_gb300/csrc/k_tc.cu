@@ -8,9 +8,14 @@
 //   BF16x3 three products A_hi B_hi + A_hi B_lo + A_lo B_hi, operands stored as bf16
 //          hi/lo pairs (X = X_hi + X_lo), about 16 significant bits per product;
 //   TF32x3 the same three products with TF32 hi and TF32-rounded remainder parts.
-// The kernel is persistent: one CTA (6 warps) per SM loops over 128x128 output tiles (and
-// the items of a batched product), its stage and chunk counters running on across tiles so
-// that the next tile's loads and MMAs overlap the last tile's epilogue.  Operand tiles of
+// Three forms of the kernel share the operand staging, the chunked accumulation and the
+// epilogue: the wide form (the default: 128 x 256 tiles, 12 warps per CTA, its work items
+// read from a host-computed table; "wide form" below), the 128 x 128 form described in this
+// paragraph, and the CTA-pair form (256 x 128 tiles on two CTAs, cta_group::2; "CTA-pair
+// form" below); tc_gemm picks one by MBDGB_TC_FORM.
+// Each is persistent: one CTA (6 warps in the 128 x 128 form) per SM loops over output tiles
+// (and the items of a batched product), its stage and chunk counters running on across tiles
+// so that the next tile's loads and MMAs overlap the last tile's epilogue.  Operand tiles of
 // 128 rows x 128 bytes are staged in shared memory by TMA (128-byte swizzle) through an
 // mbarrier ring;
 // warp 4 issues the TMA loads, warp 5 issues tcgen05.mma.  K is split into chunks of
