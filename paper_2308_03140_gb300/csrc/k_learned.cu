@@ -2,7 +2,7 @@
 //
 // The paper has no learned part; the model stands in for the screening of Eqs. (scs) and
 // (contraction) (Sec. 2.3):
-//   features (74 per atom): for every other atom j of the same system at distance d < 24 bohr,
+//   features (122 per atom): for every other atom j of the same system at distance d < 24 bohr,
 //     alpha0_j fc(d) exp(-(d - mu_m)^2 / (2 w^2)), m = 0..63, mu_m = (m + 1/2) w, w = 0.375
 //     bohr (4 shells of 6 bohr x 16 Gaussians), fc(d) = (1 + cos(pi d / 24)) / 2; then the
 //     atom's own TS-scaled alpha0, omega, R_vdW (Eq. ts-scaling) and volume ratio; then the

@@ -1,9 +1,12 @@
 // Mixed-precision screening solves for Eq. (scs): the matrices A(u) = alpha(u)^{-1} +
-// T^scs (one per frequency point, Sec. 2.3) are factorised in FP32 (SIMT FFMA: the
-// FP32 rate of this part is about 70x its FP64 rate), and A X = B is solved by iterative
-// refinement: X <- X + A32^{-1} (B - A X), with the residual formed from the FP64
-// matrix.  For the moderately conditioned screening matrices (cond ~ 1e1 - 2e3) the FP32
-// solution is within a few 1e-7 and each step gains six digits or more.
+// T^scs (one per frequency point, Sec. 2.3) are factorised in FP32, blocked in panels of
+// kScsPanel columns, each panel in sub-panels of kScsSub columns: 64-wide right-looking
+// steps inside a sub-panel on the CUDA cores (SIMT FFMA), the panel's columns right of each
+// sub-panel and the trailing matrix after each panel updated on the tensor cores (TF32x3
+// parts, k_tc.cu).  A X = B is then solved by iterative refinement:
+// X <- X + A32^{-1} (B - A X), with the residual formed from the FP64 matrix.  For the
+// moderately conditioned screening matrices (cond ~ 1e1 - 2e3) the FP32 solution is within a
+// few 1e-7 and each step gains six digits or more.
 //
 // Layout as in k_dense.cu: batch of row-major ld x ld matrices, ld a multiple of 64,
 // right-hand sides [batch][ld][3].
