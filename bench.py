@@ -8,8 +8,10 @@ inputs resident in HBM.  `e2e` repeats the measurement through the C ABI with ho
 (host-to-device copies of the inputs and device-to-host copies of energy, gradients and
 screened polarizabilities inside the timed region).  Beside it, on the same inputs: the
 TF32x3 arm, the FP64 path (one evaluation) against which each arm's energy, force and
-parameter-gradient errors are stated, and the 2000-atom cluster (Q 6000 x 6000) in both
-forms with its own FP64 arm.
+parameter-gradient errors are stated; then further workloads, each with its own FP64 arm:
+the 2000-atom cluster (Q 6000 x 6000: BF16x3, TF32x3 and the learned screening), the
+256-atom cell with 64 Bloch vectors, and a batch of clusters of 50-500 atoms with plain and
+learned screening (with and without its fallback).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
