@@ -253,7 +253,8 @@ def cpu_baseline(workload: str, n_sample: int, n_target: int, method: str = "rss
     kind = "cell" if sysm.lattice is not None else "cluster"
     return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"energy+gradient of a {n_sample}-atom {kind} of the same recipe in "
-                      f"{dt:.2f} s, extrapolated by (n/{n_sample})^3 to {n_target} atoms",
+                      f"{dt:.2f} s, extrapolated by (n/{n_sample})^3 to {n_target} atoms (the oracle's cost "
+                      f"grows faster than n^3 at these sizes, so the extrapolated rate is an upper bound)",
             "sample_seconds": dt, "extrapolated": True}
 
 
@@ -296,7 +297,8 @@ def run_reference(args):
     from paper_2308_03140_gb300 import synthetic as syn
     full = syn.workload(args.workload)
     sample = (f"each step one energy+gradient of a {n_s}-atom {kind} of the same recipe (measured: "
-              f"{1e3 * dt / args.steps:.0f} ms per step), extrapolated by ({n_target}/{n_s})^3 to the workload")
+              f"{1e3 * dt / args.steps:.0f} ms per step), extrapolated by ({n_target}/{n_s})^3 to the workload "
+              f"(the oracle's cost grows faster than n^3 at these sizes, so the extrapolated rate is an upper bound)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "ms_per_step_extrapolated": 1e3 * dt * scale / args.steps,

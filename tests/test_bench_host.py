@@ -94,3 +94,11 @@ def test_errors_against_the_fp64_path():
     e2 = bench.errors_vs(arm2, dict(ref, gA=np.eye(3)), N)
     assert "max_param_grad_err" not in e2
     assert e2["max_lattice_grad_err_rel"] == pytest.approx(1e-3)
+
+
+def test_cpu_baseline_object():
+    # the GPU arm's cpu_baseline on a tiny sample: the contract's keys, the extrapolation labelled
+    cb = bench.cpu_baseline("finite8000", 12, 8000)
+    assert cb["kind"] == "oracle" and cb["unit"] == "solves/s" and cb["cores"] >= 1
+    assert cb["extrapolated"] is True and "12-atom cluster" in cb["sample"] and "upper bound" in cb["sample"]
+    assert cb["value"] == pytest.approx(1.0 / (cb["sample_seconds"] * (8000 / 12) ** 3))
