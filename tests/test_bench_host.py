@@ -102,3 +102,37 @@ def test_cpu_baseline_object():
     assert cb["kind"] == "oracle" and cb["unit"] == "solves/s" and cb["cores"] >= 1
     assert cb["extrapolated"] is True and "12-atom cluster" in cb["sample"] and "upper bound" in cb["sample"]
     assert cb["value"] == pytest.approx(1.0 / (cb["sample_seconds"] * (8000 / 12) ** 3))
+
+
+def test_clock_sampler_parses_the_nvidia_smi_rows(tmp_path):
+    # rows as `nvidia-smi --format=csv,noheader,nounits` prints them for the sampler's fields
+    rows = ["0, 2055, 2070, 1100.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 2040, 2070, 1380.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 900.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    p = tmp_path / "clocks.csv"
+    p.write_text("\n".join(rows) + "\n")
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs = bench.ClockSampler(0)
+    cs.proc, cs.path = _Proc(), str(p)
+    c = cs.stop()
+    assert c["sm_mhz"] == 2055.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"] and c["power_w_max"] == pytest.approx(1380.2)
+    assert not os.path.exists(p)
+    assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    import subprocess
+    base = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0",
+            "--gpus", "2"]
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
+    r = subprocess.run(base, capture_output=True, text=True, cwd=ROOT, env=env, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
