@@ -34,7 +34,7 @@ def _rank(rank, world, port, out):
 
 def test_two_rank_max_and_whole_job_rate():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:   # no fork of this multi-threaded process
         out = mgr.dict()
         mp.start_processes(_rank, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
         res = dict(out)
