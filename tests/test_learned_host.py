@@ -1,6 +1,6 @@
 """Host parts of the learned-screening trainer (no GPU): the initial parameters' layout (the
 order mbd_set_scs_model reads: W1, b1, W2, b2, W3, b3 per member), and the training clusters'
-recipe (sizes, seeds disjoint from the evaluation batch, the stated perturbations)."""
+recipe (sizes, the base cluster of seed 100000 + i, the stated perturbations)."""
 import numpy as np
 
 from paper_2308_03140_gb300 import binding, learned
